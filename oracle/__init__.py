@@ -1,0 +1,237 @@
+"""FP64 CPU oracle for the 2D forward/adjoint harmonic radiance Monte Carlo
+(Hochuli, Powell, Arridge & Cox, arXiv 1608.05238).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the plain, slow, obviously correct
+statement of what the method computes; the CUDA library is checked against
+it.  Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` may import or call anything here.  It shares no code with the
+CUDA path: the transport lives in ``mcr_oracle.c`` (plain C, FP64), the
+pixelwise functionals (H, epsilon, gradients) in :mod:`oracle.functionals`
+(numpy, FP64).
+
+Pins (what fixes each function independently of itself) live in
+``tests/test_oracle_*.py``; see the list in the design doc.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mcr_oracle.c")
+_LIB = os.path.join(_HERE, "libmcr_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PENCIL, LINE, ISO_POINT = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle into ``oracle/libmcr_oracle.so`` (gcc, FP64, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=gnu11", "-shared", "-fPIC",
+               "-pthread", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Medium(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("nz", C.c_int32), ("dx", C.c_double), ("g", C.c_double),
+                ("mua", C.POINTER(C.c_double)), ("mus", C.POINTER(C.c_double))]
+
+
+class _Source(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("x0", C.c_double), ("z0", C.c_double), ("x1", C.c_double),
+                ("z1", C.c_double), ("dir_x", C.c_double), ("dir_z", C.c_double), ("power", C.c_double)]
+
+
+class _Run(C.Structure):
+    _fields_ = [("K", C.c_int32), ("n_threads", C.c_int32), ("n_packets", C.c_uint64),
+                ("first_packet", C.c_uint64), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
+                ("max_scatter", C.c_uint32), ("max_events", C.c_uint32), ("w_threshold", C.c_double),
+                ("roulette_p", C.c_float)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("launched", "flights", "collisions", "segments", "escapes",
+                                          "rr_kill", "rr_survive", "scatter_limit", "event_limit")] + \
+               [(n, C.c_double) for n in ("launched_w", "escaped_w", "rr_net_w", "absorbed_w", "killed_w")]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            lib.orc_forward_raw.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run),
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(_Stats)]
+            lib.orc_forward_raw.restype = C.c_int
+            lib.orc_volume_raw.argtypes = [C.POINTER(_Medium), C.POINTER(C.c_float), C.POINTER(_Run), C.c_int,
+                                           C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(_Stats),
+                                           C.POINTER(C.c_double)]
+            lib.orc_volume_raw.restype = C.c_int
+            lib.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+            lib.orc_philox4x32_10.restype = None
+            lib.orc_hg_angle.argtypes = [C.c_double, C.c_double]
+            lib.orc_hg_angle.restype = C.c_double
+            lib.orc_hg_phase.argtypes = [C.c_double, C.c_double]
+            lib.orc_hg_phase.restype = C.c_double
+            lib.orc_volume_pick.argtypes = [C.POINTER(C.c_float), C.c_int64, C.c_uint64, C.c_uint32, C.c_uint64]
+            lib.orc_volume_pick.restype = C.c_int64
+            _lib = lib
+    return _lib
+
+
+@dataclass
+class RunParams:
+    """Per-run knobs shared by the forward and adjoint oracles."""
+    K: int
+    n_packets: int
+    seed: int = 0
+    stream_id: int = 0
+    first_packet: int = 0
+    max_scatter: int = 0xFFFFFFFF
+    max_events: int = 10_000_000
+    w_threshold: float = 1e-4
+    roulette_p: float = 0.1
+    n_threads: int = 0
+
+
+@dataclass
+class Result:
+    coeff: np.ndarray        # [2K+1, nz, nx] normalised radiance coefficients (a0, a1, b1, ...)
+    a0_var: np.ndarray | None  # [nz, nx] sample variance of the a0 estimate (same normalisation)
+    stats: dict
+    source_strength: float
+
+
+def _medium(mua, mus, dx, g):
+    mua = np.ascontiguousarray(mua, dtype=np.float64)
+    mus = np.ascontiguousarray(mus, dtype=np.float64)
+    assert mua.shape == mus.shape and mua.ndim == 2
+    m = _Medium(mua.shape[1], mua.shape[0], float(dx), float(g),
+                mua.ctypes.data_as(C.POINTER(C.c_double)), mus.ctypes.data_as(C.POINTER(C.c_double)))
+    return m, (mua, mus)
+
+
+def _run(p: RunParams):
+    nt = p.n_threads or (os.cpu_count() or 1)
+    nt = max(1, min(nt, max(1, p.n_packets)))
+    return _Run(p.K, nt, p.n_packets, p.first_packet, p.seed, p.stream_id, p.max_scatter, p.max_events,
+                p.w_threshold, p.roulette_p)
+
+
+def _stats_dict(st: _Stats) -> dict:
+    return {n: getattr(st, n) for n, _ in _Stats._fields_}
+
+
+def _finish(raw, sq, n_packets, S, dx, st) -> Result:
+    A = dx * dx
+    norm = S / (n_packets * A) if n_packets > 0 else 0.0
+    coeff = raw * norm
+    var = None
+    if sq is not None and n_packets > 1:
+        # a0 = (S/A) mean_p X_p with X_p the per-packet track-weight sum in the pixel;
+        # its variance is (S/A)^2 Var(X) / N_p with the unbiased Var(X).
+        mean = raw[0] / n_packets
+        var = np.maximum(sq / n_packets - mean * mean, 0.0) / (n_packets - 1) * (S / A) ** 2
+    return Result(coeff, var, _stats_dict(st), S)
+
+
+def forward(mua, mus, dx, g, source: dict, run: RunParams, with_variance: bool = False) -> Result:
+    """Forward harmonic radiance MC (Sec. 3, 3.1) from a pencil, line or isotropic point source.
+
+    ``source``: dict(kind=PENCIL|LINE|ISO_POINT, x0, z0, x1, z1, dir_x, dir_z, power=1).
+    Returns coefficients a_0, a_n, b_n (Eqs. 9-11) normalised by power / (N_p dx^2).
+    """
+    lib = _load()
+    m, keep = _medium(mua, mus, dx, g)
+    s = _Source(int(source["kind"]), float(source.get("x0", 0.0)), float(source.get("z0", 0.0)),
+                float(source.get("x1", 0.0)), float(source.get("z1", 0.0)), float(source.get("dir_x", 0.0)),
+                float(source.get("dir_z", 1.0)), float(source.get("power", 1.0)))
+    nz, nx = keep[0].shape
+    Cc = 2 * run.K + 1
+    raw = np.zeros((Cc, nz, nx), dtype=np.float64)
+    sq = np.zeros((nz, nx), dtype=np.float64) if with_variance else None
+    st = _Stats()
+    rc = lib.orc_forward_raw(C.byref(m), C.byref(s), C.byref(_run(run)),
+                             raw.ctypes.data_as(C.POINTER(C.c_double)),
+                             sq.ctypes.data_as(C.POINTER(C.c_double)) if sq is not None else None, C.byref(st))
+    if rc != 0:
+        raise ValueError(f"oracle forward: status {rc}")
+    return _finish(raw, sq, run.n_packets, s.power, dx, st)
+
+
+def volume(mua, mus, dx, g, q, run: RunParams, adjoint: bool = True, with_variance: bool = False) -> Result:
+    """MC from the signed volumetric isotropic source ``q`` ([nz, nx] float32, per unit area and angle).
+
+    ``adjoint=True`` is the adjoint model of Sec. 4 / Sec. 6: the tally is taken at theta + pi, so
+    the result holds the adjoint coefficients a*_n, b*_n.  ``adjoint=False`` tallies at theta (a
+    plain forward run from a volumetric source).
+    """
+    lib = _load()
+    m, keep = _medium(mua, mus, dx, g)
+    q = np.ascontiguousarray(q, dtype=np.float32)
+    nz, nx = keep[0].shape
+    assert q.shape == (nz, nx)
+    Cc = 2 * run.K + 1
+    raw = np.zeros((Cc, nz, nx), dtype=np.float64)
+    sq = np.zeros((nz, nx), dtype=np.float64) if with_variance else None
+    st = _Stats()
+    S = C.c_double(0.0)
+    rc = lib.orc_volume_raw(C.byref(m), q.ctypes.data_as(C.POINTER(C.c_float)), C.byref(_run(run)),
+                            1 if adjoint else 0, raw.ctypes.data_as(C.POINTER(C.c_double)),
+                            sq.ctypes.data_as(C.POINTER(C.c_double)) if sq is not None else None,
+                            C.byref(st), C.byref(S))
+    if rc != 0:
+        raise ValueError(f"oracle volume: status {rc}")
+    return _finish(raw, sq, run.n_packets, S.value, dx, st)
+
+
+def adjoint(mua, mus, dx, g, qstar, run: RunParams, with_variance: bool = False) -> Result:
+    """Adjoint harmonic radiance MC (Sec. 4, Sec. 6) from q* (per unit area and unit angle)."""
+    return volume(mua, mus, dx, g, qstar, run, adjoint=True, with_variance=with_variance)
+
+
+def philox4x32_10(counter, key) -> np.ndarray:
+    """Philox4x32-10 block for a 4-word counter and 2-word key (Salmon et al., SC'11)."""
+    lib = _load()
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in counter])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    lib.orc_philox4x32_10(c, k, o)
+    return np.array(list(o), dtype=np.uint32)
+
+
+def u01(words) -> np.ndarray:
+    """Map 32-bit words to the uniforms ((x >> 9) + 1/2) 2^-23 used by both paths."""
+    w = np.asarray(words, dtype=np.uint64)
+    return ((w >> np.uint64(9)).astype(np.float64) + 0.5) * 2.0 ** -23
+
+
+def hg_angle(g: float, u) -> np.ndarray:
+    """Scattering angle of Eq. 7 for uniforms ``u`` (vectorised over u)."""
+    lib = _load()
+    u = np.atleast_1d(np.asarray(u, dtype=np.float64))
+    return np.array([lib.orc_hg_angle(float(g), float(v)) for v in u])
+
+
+def hg_phase(g: float, dtheta) -> np.ndarray:
+    """2D Henyey-Greenstein phase function of Eq. 6."""
+    lib = _load()
+    d = np.atleast_1d(np.asarray(dtheta, dtype=np.float64))
+    return np.array([lib.orc_hg_phase(float(g), float(v)) for v in d])
+
+
+def volume_pick(q, seed: int, stream_id: int, packet: int) -> int:
+    """Flat pixel index that the volumetric sampler draws for packet ``packet``."""
+    lib = _load()
+    q = np.ascontiguousarray(q, dtype=np.float32)
+    return int(lib.orc_volume_pick(q.ctypes.data_as(C.POINTER(C.c_float)), q.size, seed, stream_id, packet))

@@ -1,0 +1,532 @@
+/*
+ * mcr_oracle.c -- plain, slow, FP64 CPU oracle for the 2D forward and adjoint
+ * harmonic radiance Monte Carlo of Hochuli, Powell, Arridge & Cox,
+ * "Quantitative photoacoustic tomography using forward and adjoint Monte
+ * Carlo models of radiance" (arXiv 1608.05238).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness reference against
+ * which the CUDA path is checked.  Only the test-suite, the smoke check and
+ * the CPU-baseline leg of the benchmark may build, load or call it.  It shares
+ * no code, header, table or helper with the CUDA library.
+ *
+ * What it computes, step by step, in the order of the paper (Section 3):
+ *   launch a packet ("photon") of weight W from the source;
+ *   sample a free path from mu_s only;                         (Sec. 3, text)
+ *   along the path, pixel by pixel, deposit the weight lost to absorption
+ *   and attenuate W <- W exp(-mu_a s);                          (Sec. 3, text)
+ *   tally the deposit into the harmonic coefficients a_0, a_n, b_n of the
+ *   pixel at the packet's direction theta;              (Sec. 3.1, Eq. 9-11)
+ *   at the end of the path, scatter by the 2D Henyey-Greenstein angle
+ *   theta_s = 2 atan((1-g)/(1+g) tan(pi U));                      (Eq. 7)
+ *   repeat until the weight falls below a threshold.            (Sec. 3, text)
+ * The adjoint run (Sec. 4, Sec. 6) launches isotropically from a volumetric,
+ * signed source q*(x) with the position uniform over the source pixel, and
+ * its tally is taken at theta + pi (the adjoint radiance looks back along
+ * the path; see the readings below).
+ *
+ * Readings of the paper taken here (where it is silent or garbled):
+ *  - Free path: the paper prints s = U/mu_s; read as s = -ln(U)/mu_s, an
+ *    exponential free path with absorption applied as continuous weight
+ *    loss (absorption weighting).
+ *  - Tally quantity: the coefficients hold RADIANCE, so that a_0 is the
+ *    fluence (Sec. 5) and H = mu_a a_0 (Sec. 2).  Each pixel segment of
+ *    length l deposits its track weight t = W (1 - exp(-mu_a l)) / mu_a
+ *    (= W l when mu_a = 0), i.e. the absorbed weight dW divided by mu_a,
+ *    normalised by N_p and the pixel area.
+ *  - Adjoint direction: with psi(x,s) = phi*(x,-s), psi solves the forward
+ *    RTE (Eq. 12 vs Eq. 5, HG symmetric), so the adjoint coefficients are
+ *    tallied at theta + pi: a*_n = (-1)^n a_n^psi, b*_n = (-1)^n b_n^psi.
+ *  - Termination: the paper's threshold on |W| (Sec. 6) is completed by
+ *    Russian roulette (survive with probability p, W <- W/p) so that the
+ *    estimate stays unbiased.
+ *  - Adjoint source sampling: the source pixel is drawn with probability
+ *    proportional to |q*_i| (uniform pixel areas), quantised to integers
+ *    relative to max|q*| with 2^32 levels, and the packet weight is
+ *    sign(q*_i); the total source strength is S = 2 pi A sum|q*| (q* is per
+ *    unit area and unit angle and isotropic).
+ *
+ * Conventions.  x = column (lateral), z = row (depth, z = 0 the top edge).
+ * Pixel (ix, iz) covers [ix dx, (ix+1) dx) x [iz dx, (iz+1) dx); a source
+ * point exactly on the far edge belongs to the last pixel.  The direction
+ * angle theta is measured from the +z axis: s = (sin theta, cos theta) =
+ * (s_x, s_z) (Sec. 3.1).  Coefficient channel c: c = 0 is a_0, c = 2n-1 is
+ * a_n, c = 2n is b_n; output layout [2K+1][nz][nx].
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11),
+ * written here from its published definition.  Key (seed_lo, seed_hi ^
+ * stream_id), counter (packet_lo, packet_hi, event, 0).  Event 0 and 1 are
+ * the launch; flight k >= 1 uses event k+1 (word 0 -> free path, word 1 ->
+ * scattering angle, word 2 -> roulette).  A 32-bit word x maps to the
+ * uniform u = ((x >> 9) + 1/2) 2^-23, which is exact in FP32 and FP64.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PENCIL 0
+#define ORC_LINE 1
+#define ORC_ISO_POINT 2
+#define ORC_VOLUME 3 /* internal: volumetric isotropic source (adjoint) */
+
+#define ORC_OK 0
+#define ORC_ERR_ARG -1
+#define ORC_ERR_NOMEM -3
+
+typedef struct {
+  int32_t nx, nz;
+  double dx;          /* pixel side, mm */
+  double g;           /* HG anisotropy */
+  const double *mua;  /* [nz][nx], 1/mm */
+  const double *mus;  /* [nz][nx], 1/mm */
+} orc_medium;
+
+typedef struct {
+  int32_t kind;
+  double x0, z0, x1, z1; /* mm */
+  double dir_x, dir_z;   /* unit direction for pencil / line */
+  double power;          /* total source power */
+} orc_source;
+
+typedef struct {
+  int32_t K;
+  int32_t n_threads;
+  uint64_t n_packets;
+  uint64_t first_packet;
+  uint64_t seed;
+  uint32_t stream_id;
+  uint32_t max_scatter; /* a packet is killed at its collision number max_scatter+1 */
+  uint32_t max_events;  /* flights per packet before it is ended */
+  double w_threshold;   /* roulette when |W| < w_threshold |W0| */
+  float roulette_p;     /* survival probability (FP32 so both paths compare alike) */
+} orc_run;
+
+typedef struct {
+  uint64_t launched, flights, collisions, segments, escapes;
+  uint64_t rr_kill, rr_survive, scatter_limit, event_limit;
+  double launched_w, escaped_w, rr_net_w, absorbed_w, killed_w;
+} orc_stats;
+
+/* ---------------------------------------------------------------- Philox */
+static void orc_philox_round(uint32_t c[4], const uint32_t k[2]) {
+  const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+  const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+  const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+  const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+  const uint32_t n0 = hi1 ^ c[1] ^ k[0];
+  const uint32_t n2 = hi0 ^ c[3] ^ k[1];
+  c[0] = n0;
+  c[1] = lo1;
+  c[2] = n2;
+  c[3] = lo0;
+}
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+  uint32_t k[2] = {key[0], key[1]};
+  for (int r = 0; r < 10; ++r) {
+    orc_philox_round(c, k);
+    k[0] += 0x9E3779B9u; /* Weyl key schedule */
+    k[1] += 0xBB67AE85u;
+  }
+  memcpy(out, c, sizeof(c));
+}
+
+static double orc_u01(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
+
+/* ------------------------------------------------------------ HG (Eq. 7) */
+double orc_hg_angle(double g, double u) {
+  return 2.0 * atan((1.0 - g) / (1.0 + g) * tan(M_PI * u));
+}
+
+/* 2D Henyey-Greenstein phase function of Eq. 6, P(dtheta). */
+double orc_hg_phase(double g, double dtheta) {
+  return (1.0 / (2.0 * M_PI)) * (1.0 - g * g) / (1.0 + g * g - 2.0 * g * cos(dtheta));
+}
+
+static double orc_wrap(double th) {
+  while (th > M_PI) th -= 2.0 * M_PI;
+  while (th <= -M_PI) th += 2.0 * M_PI;
+  return th;
+}
+
+/* --------------------------------------------- volumetric source sampling */
+typedef struct {
+  const float *q;     /* [nz][nx] signed source density */
+  uint64_t *cdf;      /* inclusive prefix sum of quantised |q| */
+  uint64_t total;
+  double qmax;
+} orc_volsrc;
+
+static int orc_volsrc_build(orc_volsrc *vs, const float *q, int64_t npix) {
+  vs->q = q;
+  vs->cdf = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(npix > 0 ? npix : 1));
+  if (!vs->cdf) return ORC_ERR_NOMEM;
+  double qmax = 0.0;
+  for (int64_t i = 0; i < npix; ++i) {
+    double a = fabs((double)q[i]);
+    if (a > qmax) qmax = a;
+  }
+  vs->qmax = qmax;
+  uint64_t run = 0;
+  for (int64_t i = 0; i < npix; ++i) {
+    uint64_t w = 0;
+    if (qmax > 0.0) w = (uint64_t)floor(fabs((double)q[i]) / qmax * 4294967296.0);
+    run += w;
+    vs->cdf[i] = run;
+  }
+  vs->total = run;
+  return ORC_OK;
+}
+
+/* smallest i with cdf[i] > target */
+static int64_t orc_volsrc_pick(const orc_volsrc *vs, int64_t npix, uint32_t w0, uint32_t w1) {
+  const uint64_t r48 = ((uint64_t)w0 << 16) | (uint64_t)(w1 >> 16);
+  const uint64_t target = (uint64_t)(((unsigned __int128)r48 * (unsigned __int128)vs->total) >> 48);
+  int64_t lo = 0, hi = npix - 1;
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (vs->cdf[mid] > target)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+/* ------------------------------------------------------------ one thread */
+typedef struct {
+  const orc_medium *med;
+  const orc_source *src;
+  const orc_volsrc *vol;
+  const orc_run *run;
+  int adjoint;
+  uint64_t p_begin, p_end;
+  double *tally;   /* [C][npix] sums of t cos/sin */
+  double *sq;      /* [npix] sum over packets of (per-packet a_0 sum)^2, or NULL */
+  double *pk;      /* [npix] current packet's a_0 sums */
+  int64_t *touched;
+  int64_t n_touched;
+  orc_stats st;
+} orc_job;
+
+static void orc_deposit(orc_job *j, int64_t pix, double t, double theta_tally) {
+  const int K = j->run->K;
+  const int64_t npix = (int64_t)j->med->nx * j->med->nz;
+  double *T = j->tally;
+  T[pix] += t; /* a_0: Eq. 9 */
+  for (int n = 1; n <= K; ++n) {
+    T[(int64_t)(2 * n - 1) * npix + pix] += t * cos(n * theta_tally); /* a_n: Eq. 10 */
+    T[(int64_t)(2 * n) * npix + pix] += t * sin(n * theta_tally);     /* b_n: Eq. 11 */
+  }
+  if (j->sq) {
+    if (j->pk[pix] == 0.0) j->touched[j->n_touched++] = pix;
+    j->pk[pix] += t;
+  }
+}
+
+static void orc_packet(orc_job *j, uint64_t p) {
+  const orc_medium *m = j->med;
+  const orc_run *r = j->run;
+  const int nx = m->nx, nz = m->nz;
+  const double dx = m->dx;
+  const int64_t npix = (int64_t)nx * nz;
+  const uint32_t key[2] = {(uint32_t)r->seed, (uint32_t)(r->seed >> 32) ^ r->stream_id};
+  uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0u, 0u};
+  uint32_t b0[4], b1[4], b[4];
+  orc_philox4x32_10(ctr, key, b0);
+  ctr[2] = 1u;
+  orc_philox4x32_10(ctr, key, b1);
+
+  /* ---- launch */
+  double x, z, theta, W0 = 1.0;
+  int ix, iz;
+  const orc_source *s = j->src;
+  switch (j->vol ? ORC_VOLUME : s->kind) {
+    case ORC_PENCIL:
+      x = s->x0;
+      z = s->z0;
+      theta = atan2(s->dir_x, s->dir_z);
+      break;
+    case ORC_LINE: {
+      const double u = orc_u01(b0[0]);
+      x = s->x0 + u * (s->x1 - s->x0);
+      z = s->z0 + u * (s->z1 - s->z0);
+      theta = atan2(s->dir_x, s->dir_z);
+      break;
+    }
+    case ORC_ISO_POINT:
+      x = s->x0;
+      z = s->z0;
+      theta = orc_wrap(2.0 * M_PI * orc_u01(b0[2]));
+      break;
+    default: { /* ORC_VOLUME */
+      const int64_t pix = orc_volsrc_pick(j->vol, npix, b0[0], b0[1]);
+      const int pxi = (int)(pix % nx), pzi = (int)(pix / nx);
+      x = (pxi + orc_u01(b1[0])) * dx;
+      z = (pzi + orc_u01(b1[1])) * dx;
+      theta = orc_wrap(2.0 * M_PI * orc_u01(b0[2]));
+      W0 = j->vol->q[pix] < 0.0f ? -1.0 : 1.0;
+      break;
+    }
+  }
+  double W = W0;
+  j->st.launched++;
+  j->st.launched_w += W0;
+
+  const double Wmax = nx * dx, Dmax = nz * dx;
+  if (!(x >= 0.0 && x <= Wmax && z >= 0.0 && z <= Dmax)) {
+    j->st.escapes++;
+    j->st.escaped_w += W;
+    return;
+  }
+  ix = (int)floor(x / dx);
+  iz = (int)floor(z / dx);
+  if (ix >= nx) ix = nx - 1;
+  if (iz >= nz) iz = nz - 1;
+
+  uint32_t flight = 0, n_scatter = 0;
+  for (;;) {
+    /* ---- a new free flight: s = -ln(U)/mu_s, as optical depth tau */
+    if (flight >= r->max_events) {
+      j->st.event_limit++;
+      j->st.killed_w += W;
+      break;
+    }
+    ++flight;
+    j->st.flights++;
+    ctr[2] = flight + 1u;
+    orc_philox4x32_10(ctr, key, b);
+    double tau = -log(orc_u01(b[0]));
+    int escaped = 0;
+    for (;;) {
+      const int64_t pix = (int64_t)iz * nx + ix;
+      const double mua = m->mua[pix], mus = m->mus[pix];
+      const double sx = sin(theta), sz = cos(theta);
+      double dist_x = INFINITY, dist_z = INFINITY;
+      if (sx > 0.0) dist_x = ((ix + 1) * dx - x) / sx;
+      if (sx < 0.0) dist_x = (ix * dx - x) / sx;
+      if (sz > 0.0) dist_z = ((iz + 1) * dx - z) / sz;
+      if (sz < 0.0) dist_z = (iz * dx - z) / sz;
+      if (dist_x < 0.0) dist_x = 0.0;
+      if (dist_z < 0.0) dist_z = 0.0;
+      const double d_edge = dist_x < dist_z ? dist_x : dist_z;
+      const double d_coll = mus > 0.0 ? tau / mus : INFINITY;
+      const int collide = d_coll < d_edge;
+      const double l = collide ? d_coll : d_edge;
+      /* deposit the track weight of this pixel segment (Sec. 3 + Eq. 9-11) */
+      const double t = mua > 0.0 ? -W * expm1(-mua * l) / mua : W * l;
+      if (t != 0.0) orc_deposit(j, pix, t, j->adjoint ? theta + M_PI : theta);
+      j->st.segments++;
+      const double W_next = W * exp(-mua * l); /* W <- W exp(-mu_a s) (Sec. 3) */
+      j->st.absorbed_w += W - W_next;          /* weight lost, booked apart from t */
+      W = W_next;
+      x += l * sx;
+      z += l * sz;
+      if (collide) break;
+      tau -= mus * l;
+      if (dist_x <= dist_z) { /* ties: cross x first, z follows as a zero-length segment */
+        if (sx > 0.0) {
+          ++ix;
+          x = ix * dx;
+        } else {
+          x = ix * dx;
+          --ix;
+        }
+      } else {
+        if (sz > 0.0) {
+          ++iz;
+          z = iz * dx;
+        } else {
+          z = iz * dx;
+          --iz;
+        }
+      }
+      if (ix < 0 || ix >= nx || iz < 0 || iz >= nz) {
+        escaped = 1;
+        break;
+      }
+    }
+    if (escaped) {
+      j->st.escapes++;
+      j->st.escaped_w += W;
+      break;
+    }
+    /* ---- collision */
+    j->st.collisions++;
+    if (n_scatter >= r->max_scatter) {
+      j->st.scatter_limit++;
+      j->st.killed_w += W;
+      break;
+    }
+    theta = orc_wrap(theta + orc_hg_angle(m->g, orc_u01(b[1])));
+    ++n_scatter;
+    /* ---- threshold on |W| with Russian roulette */
+    if (fabs(W) < r->w_threshold * fabs(W0)) {
+      const double p = (double)r->roulette_p;
+      if (orc_u01(b[2]) < p) {
+        const double Wn = W / p;
+        j->st.rr_survive++;
+        j->st.rr_net_w += Wn - W;
+        W = Wn;
+      } else {
+        j->st.rr_kill++;
+        j->st.rr_net_w -= W;
+        break;
+      }
+    }
+  }
+}
+
+static void *orc_worker(void *arg) {
+  orc_job *j = (orc_job *)arg;
+  for (uint64_t p = j->p_begin; p < j->p_end; ++p) {
+    orc_packet(j, p);
+    if (j->sq) {
+      for (int64_t k = 0; k < j->n_touched; ++k) {
+        const int64_t pix = j->touched[k];
+        j->sq[pix] += j->pk[pix] * j->pk[pix];
+        j->pk[pix] = 0.0;
+      }
+      j->n_touched = 0;
+    }
+  }
+  return NULL;
+}
+
+static int orc_check(const orc_medium *m, const orc_run *r) {
+  if (!m || !r || !m->mua || !m->mus) return ORC_ERR_ARG;
+  if (m->nx <= 0 || m->nz <= 0 || !(m->dx > 0.0)) return ORC_ERR_ARG;
+  if (!(m->g > -1.0 && m->g < 1.0)) return ORC_ERR_ARG;
+  if (r->K < 0 || r->K > 256 || r->n_threads <= 0) return ORC_ERR_ARG;
+  if (!(r->roulette_p > 0.0f && r->roulette_p <= 1.0f)) return ORC_ERR_ARG;
+  const int64_t npix = (int64_t)m->nx * m->nz;
+  for (int64_t i = 0; i < npix; ++i)
+    if (!(m->mua[i] >= 0.0) || !(m->mus[i] >= 0.0)) return ORC_ERR_ARG;
+  return ORC_OK;
+}
+
+/*
+ * Runs packets [first_packet, first_packet + n_packets) and ADDS raw sums to
+ * tally ([2K+1][nz][nx], sums of t cos(n theta), t sin(n theta), no
+ * normalisation) and to sq ([nz][nx], sums over packets of the squared
+ * per-packet a_0 sum; may be NULL).  Normalisation is done by the caller
+ * (S / (N_p dx^2)).  Threads take equal contiguous packet ranges; their tallies
+ * are summed in thread order.
+ */
+static int orc_run_packets(const orc_medium *m, const orc_source *s, const orc_volsrc *vol,
+                           const orc_run *r, int adjoint, double *tally, double *sq, orc_stats *st) {
+  const int64_t npix = (int64_t)m->nx * m->nz;
+  const int64_t C = 2 * (int64_t)r->K + 1;
+  const int nt = r->n_threads;
+  orc_job *jobs = (orc_job *)calloc((size_t)nt, sizeof(orc_job));
+  pthread_t *th = (pthread_t *)calloc((size_t)nt, sizeof(pthread_t));
+  if (!jobs || !th) {
+    free(jobs);
+    free(th);
+    return ORC_ERR_NOMEM;
+  }
+  int rc = ORC_OK;
+  for (int k = 0; k < nt; ++k) {
+    orc_job *j = &jobs[k];
+    j->med = m;
+    j->src = s;
+    j->vol = vol;
+    j->run = r;
+    j->adjoint = adjoint;
+    j->p_begin = r->first_packet + r->n_packets * (uint64_t)k / (uint64_t)nt;
+    j->p_end = r->first_packet + r->n_packets * (uint64_t)(k + 1) / (uint64_t)nt;
+    j->tally = (double *)calloc((size_t)(C * npix), sizeof(double));
+    if (!j->tally) rc = ORC_ERR_NOMEM;
+    if (sq) {
+      j->sq = (double *)calloc((size_t)npix, sizeof(double));
+      j->pk = (double *)calloc((size_t)npix, sizeof(double));
+      j->touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)npix);
+      if (!j->sq || !j->pk || !j->touched) rc = ORC_ERR_NOMEM;
+    }
+  }
+  if (rc == ORC_OK) {
+    for (int k = 0; k < nt; ++k) pthread_create(&th[k], NULL, orc_worker, &jobs[k]);
+    for (int k = 0; k < nt; ++k) pthread_join(th[k], NULL);
+    memset(st, 0, sizeof(*st));
+    for (int k = 0; k < nt; ++k) {
+      orc_job *j = &jobs[k];
+      for (int64_t i = 0; i < C * npix; ++i) tally[i] += j->tally[i];
+      if (sq)
+        for (int64_t i = 0; i < npix; ++i) sq[i] += j->sq[i];
+      st->launched += j->st.launched;
+      st->flights += j->st.flights;
+      st->collisions += j->st.collisions;
+      st->segments += j->st.segments;
+      st->escapes += j->st.escapes;
+      st->rr_kill += j->st.rr_kill;
+      st->rr_survive += j->st.rr_survive;
+      st->scatter_limit += j->st.scatter_limit;
+      st->event_limit += j->st.event_limit;
+      st->launched_w += j->st.launched_w;
+      st->escaped_w += j->st.escaped_w;
+      st->rr_net_w += j->st.rr_net_w;
+      st->absorbed_w += j->st.absorbed_w;
+      st->killed_w += j->st.killed_w;
+    }
+  }
+  for (int k = 0; k < nt; ++k) {
+    free(jobs[k].tally);
+    free(jobs[k].sq);
+    free(jobs[k].pk);
+    free(jobs[k].touched);
+  }
+  free(jobs);
+  free(th);
+  return rc;
+}
+
+/* Forward run from a boundary / point source (Sec. 3).  Adds raw sums. */
+int orc_forward_raw(const orc_medium *m, const orc_source *s, const orc_run *r, double *tally,
+                    double *sq, orc_stats *st) {
+  int rc = orc_check(m, r);
+  if (rc) return rc;
+  if (!s || !tally || !st || s->kind < ORC_PENCIL || s->kind > ORC_ISO_POINT) return ORC_ERR_ARG;
+  return orc_run_packets(m, s, NULL, r, 0, tally, sq, st);
+}
+
+/*
+ * Adjoint run (Sec. 4, Sec. 6) from the signed volumetric source q ([nz][nx],
+ * per unit area and unit angle).  Adds raw sums; *source_strength receives
+ * S = 2 pi dx^2 qmax total / 2^32 (the strength that the sampled distribution
+ * represents), by which the caller scales.  Set adjoint = 0 to tally at theta
+ * (a plain forward run from the same volumetric source).
+ */
+int orc_volume_raw(const orc_medium *m, const float *q, const orc_run *r, int adjoint,
+                   double *tally, double *sq, orc_stats *st, double *source_strength) {
+  int rc = orc_check(m, r);
+  if (rc) return rc;
+  if (!q || !tally || !st || !source_strength) return ORC_ERR_ARG;
+  const int64_t npix = (int64_t)m->nx * m->nz;
+  orc_volsrc vs;
+  rc = orc_volsrc_build(&vs, q, npix);
+  if (rc) return rc;
+  *source_strength = 2.0 * M_PI * m->dx * m->dx * vs.qmax * (double)vs.total / 4294967296.0;
+  if (vs.total == 0) {
+    memset(st, 0, sizeof(*st));
+    free(vs.cdf);
+    return ORC_OK;
+  }
+  rc = orc_run_packets(m, NULL, &vs, r, adjoint ? 1 : 0, tally, sq, st);
+  free(vs.cdf);
+  return rc;
+}
+
+/* Pixel drawn for packet p by the volumetric source sampler (for tests). */
+int64_t orc_volume_pick(const float *q, int64_t npix, uint64_t seed, uint32_t stream_id, uint64_t p) {
+  orc_volsrc vs;
+  if (orc_volsrc_build(&vs, q, npix)) return -1;
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ stream_id};
+  const uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0u, 0u};
+  uint32_t b0[4];
+  orc_philox4x32_10(ctr, key, b0);
+  int64_t pix = vs.total ? orc_volsrc_pick(&vs, npix, b0[0], b0[1]) : -1;
+  free(vs.cdf);
+  return pix;
+}

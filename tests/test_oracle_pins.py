@@ -1,0 +1,313 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed form
+(Beer-Lambert, uncollided fluence, HG moments), exact bookkeeping, the adjoint
+transport equation, or an independent numerical construction (ray-pixel chords,
+quadrature).  The finite-difference gradient pins live in test_oracle_gradients.py.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+import oracle
+from oracle import RunParams
+
+
+# ----------------------------------------------------------------------------- RNG
+def test_philox_uniform_and_independent():
+    """Philox4x32-10 words are uniform, bit-balanced and uncorrelated across counters."""
+    key = (0x12345678, 0x9ABCDEF0)
+    words = np.array([oracle.philox4x32_10((p, 0, e, 0), key) for p in range(2048) for e in range(4)],
+                     dtype=np.uint64).reshape(2048, 4, 4)
+    u = oracle.u01(words).ravel()
+    # uniformity (KS) and bit balance of all 32 bits
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+    bits = np.array([(words.ravel() >> np.uint64(b)) & np.uint64(1) for b in range(32)], dtype=np.float64)
+    assert np.all(np.abs(bits.mean(axis=1) - 0.5) < 5 * 0.5 / math.sqrt(words.size))
+    # neighbouring packets / events are uncorrelated
+    up = oracle.u01(words[:, 0, 0])
+    for other in (oracle.u01(words[:, 1, 0]), oracle.u01(np.roll(words[:, 0, 0], 1)), oracle.u01(words[:, 0, 1])):
+        assert abs(np.corrcoef(up, other)[0, 1]) < 5 / math.sqrt(up.size)
+    # counter and key both matter
+    assert not np.array_equal(oracle.philox4x32_10((0, 0, 0, 0), (0, 0)), oracle.philox4x32_10((1, 0, 0, 0), (0, 0)))
+    assert not np.array_equal(oracle.philox4x32_10((0, 0, 0, 0), (0, 0)), oracle.philox4x32_10((0, 0, 0, 0), (1, 0)))
+
+
+def test_uniform_map_exact_in_fp32():
+    """u = ((x>>9)+1/2) 2^-23 is exactly representable in FP32 and lies strictly inside (0, 1)."""
+    x = np.array([0, 1, 511, 512, 2 ** 31, 2 ** 32 - 1, 0xDEADBEEF], dtype=np.uint64)
+    u = oracle.u01(x)
+    assert np.all(u > 0) and np.all(u < 1)
+    assert np.array_equal(u.astype(np.float32).astype(np.float64), u)
+
+
+# ------------------------------------------------------------------- HG (Eqs. 6, 7, 24)
+@pytest.mark.parametrize("g", [0.0, 0.5, 0.8, 0.9, -0.3])
+def test_hg_sampler_circular_moments(g):
+    """E[cos n theta_s] = g^n and E[sin n theta_s] = 0 for the sampler of Eq. 7.
+
+    These are the Fourier coefficients of the phase function (Eq. 24); the expectation over
+    U ~ U(0,1) is evaluated by the midpoint rule, which converges spectrally for this smooth
+    periodic integrand.
+    """
+    n_u = 1 << 15
+    u = (np.arange(n_u) + 0.5) / n_u
+    th = oracle.hg_angle(g, u)
+    for n in range(1, 9):
+        assert abs(np.mean(np.cos(n * th)) - g ** n) < 1e-9
+        assert abs(np.mean(np.sin(n * th))) < 1e-9
+
+
+@pytest.mark.parametrize("g", [0.0, 0.7, 0.9])
+def test_hg_sampler_distribution_matches_phase_function(g):
+    """The angles of Eq. 7 are distributed as the phase function of Eq. 6 (KS on the exact CDF)."""
+    n_u = 4000
+    u = (np.arange(n_u) + 0.5) / n_u
+    th = oracle.hg_angle(g, u)
+
+    def cdf(x):
+        return integrate.quad(lambda t: oracle.hg_phase(g, t)[0], -math.pi, x, limit=200)[0]
+
+    xs = np.linspace(-math.pi + 1e-3, math.pi - 1e-3, 41)
+    emp = np.array([np.mean(th <= x) for x in xs])
+    ref = np.array([cdf(x) for x in xs])
+    assert np.max(np.abs(emp - ref)) < 2.0 / n_u
+
+
+@pytest.mark.parametrize("g", [0.0, 0.6, 0.9])
+def test_hg_phase_normalised_and_fourier_series(g):
+    """Eq. 6 integrates to 1 and has the cosine series of Eq. 24 (coefficients g^l / pi)."""
+    th = np.linspace(-math.pi, math.pi, 4097)[:-1]
+    P = oracle.hg_phase(g, th)
+    w = 2 * math.pi / th.size
+    assert abs(P.sum() * w - 1.0) < 1e-10
+    for l in range(1, 6):
+        assert abs((P * np.cos(l * th)).sum() * w - g ** l) < 1e-10
+
+
+# --------------------------------------------------------------- Beer-Lambert (exact)
+def _chords(x0, z0, sx, sz, nx, nz, dx):
+    """Ray-pixel chord lengths by sorting all grid-line crossings (independent of the DDA)."""
+    W, D = nx * dx, nz * dx
+    ts = [0.0]
+    for k in range(nx + 1):
+        if sx != 0:
+            t = (k * dx - x0) / sx
+            if t > 0:
+                ts.append(t)
+    for k in range(nz + 1):
+        if sz != 0:
+            t = (k * dx - z0) / sz
+            if t > 0:
+                ts.append(t)
+    ts = np.unique(np.array(ts))
+    out = []
+    for a, b in zip(ts[:-1], ts[1:]):
+        m = 0.5 * (a + b)
+        xm, zm = x0 + m * sx, z0 + m * sz
+        if not (0 <= xm < W and 0 <= zm < D):
+            break
+        out.append((int(zm // dx), int(xm // dx), b - a))
+    return out
+
+
+@pytest.mark.parametrize("angle_deg", [0.0, 23.0, -61.0])
+def test_beer_lambert_closed_form(angle_deg):
+    """mu_s = 0: every packet follows one ray; a_0 is the attenuated track length per area.
+
+    a_0,i = exp(-sum_prev mu_a l) (1 - exp(-mu_a,i l_i)) / (mu_a,i A), a_n = a_0 cos(n theta),
+    b_n = a_0 sin(n theta), independent of N_p (Sec. 3 deposit with absorption weighting).
+    """
+    rng = np.random.default_rng(3)
+    nz, nx, dx = 9, 11, 0.3
+    mua = rng.uniform(0.05, 1.5, (nz, nx))
+    mua[4, 5] = 0.0  # the t = W l branch
+    mus = np.zeros((nz, nx))
+    th = math.radians(angle_deg)
+    sx, sz = math.sin(th), math.cos(th)
+    x0, z0 = 1.73, 0.0
+    K = 5
+    r = oracle.forward(mua, mus, dx, 0.5, dict(kind=oracle.PENCIL, x0=x0, z0=z0, dir_x=sx, dir_z=sz),
+                       RunParams(K=K, n_packets=7, n_threads=2))
+    expect = np.zeros((2 * K + 1, nz, nx))
+    W = 1.0
+    for iz, ix, l in _chords(x0, z0, sx, sz, nx, nz, dx):
+        m = mua[iz, ix]
+        t = W * (1 - math.exp(-m * l)) / m if m > 0 else W * l
+        W *= math.exp(-m * l)
+        expect[0, iz, ix] += t / (dx * dx)
+    for n in range(1, K + 1):
+        expect[2 * n - 1] = expect[0] * math.cos(n * th)
+        expect[2 * n] = expect[0] * math.sin(n * th)
+    assert np.max(np.abs(r.coeff - expect)) <= 1e-12 * np.max(expect[0])
+    assert r.stats["escapes"] == 7
+
+
+def test_pencil_unit_fluence_without_absorption():
+    """mu_a = mu_s = 0: a straight beam gives a_0 = 1/dx in every pixel of its column."""
+    nz, nx, dx = 6, 5, 0.2
+    z = np.zeros((nz, nx))
+    r = oracle.forward(z, z, dx, 0.0, dict(kind=oracle.PENCIL, x0=0.5, z0=0.0, dir_x=0.0, dir_z=1.0),
+                       RunParams(K=2, n_packets=3, n_threads=1))
+    col = np.zeros((nz, nx))
+    col[:, 2] = 1.0 / dx
+    assert np.allclose(r.coeff[0], col, rtol=1e-13, atol=1e-13)
+    assert np.allclose(r.coeff[1], col, rtol=1e-13, atol=1e-13)  # a_1 = a_0 cos 0
+    assert np.allclose(r.coeff[2], 0.0, atol=1e-13)              # b_1 = a_0 sin 0
+
+
+# ------------------------------------------------------------ energy bookkeeping (exact)
+def _hetero(nz, nx, seed):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.02, 0.6, (nz, nx)), rng.uniform(0.5, 8.0, (nz, nx))
+
+
+@pytest.mark.parametrize("mode", ["line", "adjoint"])
+def test_energy_conservation(mode):
+    """launched + roulette gain = absorbed + escaped + killed, and the absorbed weight equals
+    sum_i mu_a,i a_0,i A N_p / S (the tally of track weights times mu_a)."""
+    nz, nx, dx = 12, 10, 0.15
+    mua, mus = _hetero(nz, nx, 5)
+    run = RunParams(K=3, n_packets=20000, seed=9, w_threshold=0.95, roulette_p=0.5, max_scatter=3)
+    if mode == "line":
+        r = oracle.forward(mua, mus, dx, 0.7, dict(kind=oracle.LINE, x0=0.0, z0=0.0, x1=nx * dx, z1=0.0,
+                                                   dir_x=0.0, dir_z=1.0), run)
+    else:
+        q = np.random.default_rng(1).normal(size=(nz, nx)).astype(np.float32)
+        r = oracle.adjoint(mua, mus, dx, 0.7, q, run)
+    st = r.stats
+    assert st["rr_kill"] > 0 and st["rr_survive"] > 0 and st["scatter_limit"] > 0
+    lhs = st["launched_w"] + st["rr_net_w"]
+    rhs = st["absorbed_w"] + st["escaped_w"] + st["killed_w"]
+    assert abs(lhs - rhs) <= 1e-11 * run.n_packets
+    from_tally = float(np.sum(mua * r.coeff[0])) * dx * dx * run.n_packets / r.source_strength
+    assert abs(from_tally - st["absorbed_w"]) <= 1e-11 * run.n_packets
+
+
+def test_event_limit_ends_packets():
+    nz, nx, dx = 8, 8, 0.5
+    mua, mus = np.full((nz, nx), 0.001), np.full((nz, nx), 20.0)
+    r = oracle.forward(mua, mus, dx, 0.0, dict(kind=oracle.ISO_POINT, x0=2.0, z0=2.0),
+                       RunParams(K=1, n_packets=50, max_events=5, n_threads=1))
+    assert r.stats["event_limit"] == 50 and r.stats["flights"] == 250
+
+
+# --------------------------------------------------------- uncollided fluence (closed form)
+def _uncollided_pixel_means(nz, nx, dx, xs, zs, mut, sub=24):
+    """Pixel means of exp(-mu_t r) cos(n phi)/(2 pi r) (phi = atan2(x-xs, z-zs)), n = 0, 1 (a and b)."""
+    o = (np.arange(sub) + 0.5) / sub * dx
+    out = np.zeros((3, nz, nx))
+    for iz in range(nz):
+        for ix in range(nx):
+            X, Z = np.meshgrid(ix * dx + o, iz * dx + o)
+            r = np.hypot(X - xs, Z - zs)
+            phi = np.arctan2(X - xs, Z - zs)
+            f = np.exp(-mut * r) / (2 * math.pi * r)
+            out[0, iz, ix] = f.mean()
+            out[1, iz, ix] = (f * np.cos(phi)).mean()
+            out[2, iz, ix] = (f * np.sin(phi)).mean()
+    return out
+
+
+def test_uncollided_fluence_point_source():
+    """Isotropic point source, packets ended at their first collision: the tally is the
+    uncollided radiance exp(-(mu_a+mu_s) r)/(2 pi r) along the outward ray, so
+    a_0 = pixel mean of that, a_1 + i b_1 = pixel mean times exp(i phi)."""
+    nz, nx, dx = 14, 14, 0.1
+    mua, mus = 0.4, 2.0
+    xs, zs = 0.7, 0.7
+    r = oracle.forward(np.full((nz, nx), mua), np.full((nz, nx), mus), dx, 0.9,
+                       dict(kind=oracle.ISO_POINT, x0=xs, z0=zs),
+                       RunParams(K=1, n_packets=400000, seed=2, max_scatter=0), with_variance=True)
+    ref = _uncollided_pixel_means(nz, nx, dx, xs, zs, mua + mus)
+    far = np.ones((nz, nx), bool)
+    far[5:9, 5:9] = False  # the four pixels touching the source and their ring: singular pixel means
+    sig = np.sqrt(r.a0_var)
+    z0 = (r.coeff[0] - ref[0])[far] / sig[far]
+    assert np.max(np.abs(z0)) < 5.0
+    assert abs(np.mean(z0)) < 4.0 / math.sqrt(z0.size)
+    # harmonics: |a_n| <= a_0 per packet, so a_0's sigma bounds theirs
+    for c in (1, 2):
+        zc = (r.coeff[c] - ref[c])[far] / sig[far]
+        assert np.max(np.abs(zc)) < 5.0
+
+
+# ------------------------------------------------------------ reciprocity (Eqs. 13, 17)
+def test_reciprocity_case1_pixel_sources():
+    """Case 1 (Eqs. 14, 17): isotropic unit sources uniform over pixel s and pixel d give
+    Phi_s(d) = Phi_d(s) in a heterogeneous scattering medium."""
+    nz, nx, dx = 16, 16, 0.1
+    mua, mus = _hetero(nz, nx, 11)
+    g = 0.6
+    pairs = [((3, 4), (11, 12)), ((8, 2), (8, 13)), ((1, 7), (14, 7))]
+    for k, (s, d) in enumerate(pairs):
+        def unit(p):
+            q = np.zeros((nz, nx), np.float32)
+            q[p] = 1.0 / (2 * math.pi * dx * dx)
+            return q
+        run = RunParams(K=0, n_packets=200000, seed=100 + k)
+        fs = oracle.volume(mua, mus, dx, g, unit(s), run, adjoint=False, with_variance=True)
+        fd = oracle.volume(mua, mus, dx, g, unit(d), run, adjoint=True, with_variance=True)
+        assert abs(fs.source_strength - 1.0) < 1e-7  # q is stored in FP32
+        a, b = fs.coeff[0][d], fd.coeff[0][s]
+        sig = math.sqrt(fs.a0_var[d] + fd.a0_var[s])
+        assert abs(a - b) < 5 * sig, (s, d, a, b, sig)
+        assert a > 10 * sig
+
+
+def test_point_source_vs_volume_source_normalisation():
+    """A unit isotropic point source at the centre of pixel s and a unit volumetric adjoint
+    source in a far pixel d see the same fluence at each other's pixel (Eq. 17); this fixes the
+    volumetric strength S = 2 pi A sum|q*| against the forward normalisation."""
+    nz, nx, dx = 20, 20, 0.1
+    mua, mus = np.full((nz, nx), 0.3), np.full((nz, nx), 4.0)
+    s, d = (5, 5), (14, 13)
+    fwd = oracle.forward(mua, mus, dx, 0.5, dict(kind=oracle.ISO_POINT, x0=(s[1] + 0.5) * dx, z0=(s[0] + 0.5) * dx),
+                         RunParams(K=0, n_packets=300000, seed=7), with_variance=True)
+    q = np.zeros((nz, nx), np.float32)
+    q[d] = 1.0 / (2 * math.pi * dx * dx)
+    adj = oracle.adjoint(mua, mus, dx, 0.5, q, RunParams(K=0, n_packets=300000, seed=8), with_variance=True)
+    a, b = fwd.coeff[0][d], adj.coeff[0][s]
+    assert abs(a - b) < 5 * math.sqrt(fwd.a0_var[d] + adj.a0_var[s]) + 0.01 * a
+
+
+# ------------------------------------------------------- adjoint direction (Eq. 12)
+def test_adjoint_radiance_points_back_to_source():
+    """With mu_s = 0, Eq. 12 gives phi*(x, s) = int_0^inf q*(x + t s) e^{-mu_a t} dt: the adjoint
+    radiance below a source pixel looks UP (theta = pi), so a*_1 ~ -a*_0 there, whereas the
+    forward radiance of the same volumetric source points down (a_1 ~ +a_0)."""
+    nz, nx, dx = 40, 9, 0.1
+    mua, mus = np.full((nz, nx), 0.05), np.zeros((nz, nx))
+    q = np.zeros((nz, nx), np.float32)
+    q[1, 4] = 1.0
+    run = RunParams(K=2, n_packets=200000, seed=4)
+    adj = oracle.adjoint(mua, mus, dx, 0.0, q, run)
+    fwd = oracle.volume(mua, mus, dx, 0.0, q, run, adjoint=False)
+    for iz in (20, 30, 38):
+        a0, a1, b1 = adj.coeff[0, iz, 4], adj.coeff[1, iz, 4], adj.coeff[2, iz, 4]
+        assert a0 > 0 and a1 / a0 < -0.99 and abs(b1 / a0) < 0.05
+        f0, f1 = fwd.coeff[0, iz, 4], fwd.coeff[1, iz, 4]
+        assert f1 / f0 > 0.99
+        assert abs(a0 - f0) < 1e-12 * f0  # a_0 does not depend on the direction convention
+    # a_2 is even under theta -> theta + pi
+    assert np.allclose(adj.coeff[3], fwd.coeff[3], rtol=1e-12, atol=1e-15)
+    assert np.allclose(adj.coeff[1], -fwd.coeff[1], rtol=1e-12, atol=1e-15)
+
+
+# -------------------------------------------------------- volumetric source sampling
+def test_volume_sampler_follows_abs_q():
+    """Adjoint launch pixels are drawn with probability |q*_i| / sum |q*| (Sec. 6, reading A5)."""
+    rng = np.random.default_rng(0)
+    q = (rng.normal(size=(3, 4)) * np.array([1, 0, 2, 0.5])).astype(np.float32)
+    q[1, 1] = 0.0
+    n = 20000
+    picks = np.array([oracle.volume_pick(q, 5, 0, p) for p in range(n)])
+    assert np.all(np.abs(q.ravel()[picks]) > 0)
+    counts = np.bincount(picks, minlength=q.size).astype(float)
+    p = np.abs(q.ravel()).astype(np.float64)
+    p /= p.sum()
+    nz = p > 0
+    chi2 = np.sum((counts[nz] - n * p[nz]) ** 2 / (n * p[nz]))
+    assert stats.chi2.sf(chi2, nz.sum() - 1) > 1e-4
