@@ -1,0 +1,172 @@
+/*
+ * mcr.h -- C ABI of libmcr: GPU (sm_103a) forward and adjoint harmonic radiance Monte Carlo,
+ * after Hochuli, Powell, Arridge & Cox, "Quantitative photoacoustic tomography using forward
+ * and adjoint Monte Carlo models of radiance" (arXiv 1608.05238).
+ *
+ * All array arguments are DEVICE pointers owned by the caller unless a comment says "host".
+ * Maps are row-major [nz][nx] (x = column = lateral, z = row = depth, z = 0 the top edge;
+ * pixel (ix, iz) covers [ix dx, (ix+1) dx) x [iz dx, (iz+1) dx)).  Directions are angles theta
+ * from the +z axis, s = (sin theta, cos theta) = (s_x, s_z).  Coefficient arrays are
+ * channel-major [2K+1][nz][nx] FP32 with channel 0 = a_0, 2n-1 = a_n, 2n = b_n (Sec. 3.1,
+ * Eqs. 8-11), normalised so that phi(x, theta) = a_0/(2 pi) + (1/pi) sum (a_n cos n theta +
+ * b_n sin n theta) is the radiance and a_0 the fluence.  Units: mm and 1/mm.
+ *
+ * Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy default
+ * stream) unless a `stats` pointer is given, in which case the call synchronises that stream
+ * to fill it.  Every call returns MCR_OK (0) or a negative status; no C++ exception crosses the
+ * ABI.  Errors found on the device (negative or NaN mu, a packet that hit its event cap, a tally
+ * near overflow) are latched per device and returned by the next call that synchronises
+ * (a call with stats != NULL, or mc_check).
+ *
+ * The library keeps one grow-only workspace per device (fixed-point tallies, packed medium,
+ * source CDF, counters), allocated with cudaMalloc on first use and freed by
+ * mc_release_workspace().  Calls that share a device share that workspace: calls on different
+ * streams of one device must not overlap in time.
+ */
+#ifndef MCR_H
+#define MCR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MCR_OK 0
+#define MCR_ERR_ARG (-1)            /* bad argument (shape, pointer, range) */
+#define MCR_ERR_CUDA (-2)           /* a CUDA runtime call failed */
+#define MCR_ERR_NOMEM (-3)          /* workspace allocation failed */
+#define MCR_ERR_EVENT_LIMIT (-4)    /* a packet reached max_events flights and was ended */
+#define MCR_ERR_TALLY_OVERFLOW (-5) /* a fixed-point tally came within 2 bits of overflow */
+#define MCR_ERR_MEDIUM (-6)         /* the device medium holds a negative or non-finite mu */
+
+#define MCR_PENCIL 0    /* collimated beam from (x0, z0) along (dir_x, dir_z)            */
+#define MCR_LINE 1      /* collimated line source: start uniform on (x0,z0)-(x1,z1)       */
+#define MCR_ISO_POINT 2 /* isotropic point source at (x0, z0)                             */
+
+#define MCR_MAX_K 64
+
+/* Pixelised medium (Sec. 3, Eq. 5): piecewise-constant mu_a, mu_s per pixel, scalar HG g. */
+typedef struct {
+  int32_t nx, nz;   /* pixels along x (columns) and z (rows), each >= 1 */
+  float dx;         /* pixel side, mm, > 0 */
+  float g;          /* 2D Henyey-Greenstein anisotropy, -1 < g < 1 (Eq. 6) */
+  const float *mua; /* device [nz][nx] absorption coefficient, 1/mm, >= 0 */
+  const float *mus; /* device [nz][nx] scattering coefficient, 1/mm, >= 0 */
+} mcr_medium;
+
+/* Boundary or point source of a forward run (Sec. 3.2, Sec. 6).  Positions in mm; a point on
+ * the far edge of the domain belongs to the last pixel; a point outside the domain escapes. */
+typedef struct {
+  int32_t kind;          /* MCR_PENCIL | MCR_LINE | MCR_ISO_POINT */
+  float x0, z0, x1, z1;  /* pencil / point: (x0, z0); line: segment (x0,z0)-(x1,z1) */
+  float dir_x, dir_z;    /* launch direction (pencil, line); normalised by the library */
+  float power;           /* total source power S (coefficients scale linearly with it) */
+} mcr_source;
+
+/* Monte Carlo run parameters.  Random numbers: Philox4x32-10 with key (seed_lo,
+ * seed_hi ^ stream_id) and counter (packet_lo, packet_hi, event, 0); packet p of the run is
+ * packet id first_packet + p, so a run split into packet ranges tallies bit-identically. */
+typedef struct {
+  int32_t K;             /* harmonic order, 0 <= K <= MCR_MAX_K (2K+1 channels) */
+  uint32_t max_scatter;  /* packets end at collision max_scatter+1 (0xFFFFFFFF: unlimited) */
+  uint64_t n_packets;    /* packets N_p launched by this call (normalisation divisor) */
+  uint64_t first_packet; /* id of the first packet */
+  uint64_t seed;
+  uint32_t stream_id;
+  uint32_t max_events;   /* flights per packet before it is ended (watchdog, e.g. 1e7) */
+  float w_threshold;     /* Russian roulette once |W| < w_threshold |W0| (e.g. 1e-4) */
+  float roulette_p;      /* roulette survival probability p, 0 < p <= 1; survivors W <- W/p */
+} mcr_run;
+
+/* Run counters (host struct filled when a non-NULL pointer is passed; synchronises). */
+typedef struct {
+  uint64_t launched, flights, collisions, segments, escapes;
+  uint64_t rr_kill, rr_survive, scatter_limit, event_limit;
+  double launched_w;  /* sum of initial weights W0 (+-1) */
+  double escaped_w;   /* weight carried out of the domain */
+  double rr_net_w;    /* net weight added by roulette (survivor gain minus killed weight) */
+  double killed_w;    /* weight of packets ended by max_scatter or max_events */
+  double absorbed_w;  /* launched_w + rr_net_w - escaped_w - killed_w (bookkeeping) */
+} mcr_stats;
+
+/*
+ * mc_forward -- forward harmonic radiance MC (Sec. 3 and 3.1, Eqs. 7, 9-11).
+ * Launches run->n_packets packets from `src`, transports them with exponential free paths in
+ * mu_s, absorption weighting W <- W exp(-mu_a l) per pixel segment, 2D HG scattering (Eq. 7)
+ * and roulette below the weight threshold, and tallies each segment's track weight
+ * t = W (1 - exp(-mu_a l)) / mu_a into a_0, a_n = t cos(n theta), b_n = t sin(n theta) of its
+ * pixel.  coeff (device, [2K+1][nz][nx] FP32, overwritten) = power * sums / (N_p dx^2).
+ * stats (host, may be NULL).  Tallies are 64-bit fixed point (quantum 2^-32 mm): the result
+ * does not depend on scheduling and is bit-reproducible for a given run.
+ */
+int mc_forward(const mcr_medium *med, const mcr_source *src, const mcr_run *run, float *coeff,
+               mcr_stats *stats, void *stream);
+
+/*
+ * mc_adjoint -- adjoint harmonic radiance MC (Sec. 4, Eq. 12; source of Sec. 6).
+ * qstar (device [nz][nx] FP32, signed) is the isotropic adjoint source per unit area and unit
+ * angle.  Packets start in pixel i with probability |q*_i| / sum|q*| (|q*| quantised to 2^32
+ * levels of max|q*|), uniformly over the pixel, isotropically, with weight sign(q*_i); the run
+ * represents the source strength S = 2 pi dx^2 sum|q*|.  The tally is the adjoint radiance
+ * phi*(x, theta) = psi(x, theta + pi), psi being the forward radiance of the same source:
+ * coeff_adj channels a*_n, b*_n carry the factor (-1)^n.  All-zero q* gives all-zero output.
+ */
+int mc_adjoint(const mcr_medium *med, const float *qstar, const mcr_run *run, float *coeff_adj,
+               mcr_stats *stats, void *stream);
+
+/*
+ * mc_h_eps -- absorbed energy and error functional (Sec. 2, Eq. 2).
+ * H = mu_a a_0 (device out [nz][nx] FP32, Grueneisen parameter 1); if Hmeas != NULL also
+ * dL_dH = -dx^2 (H^meas - H) (device out [nz][nx] FP32, may be NULL) and
+ * eps = 1/2 dx^2 sum (H^meas - H)^2 (device out, one double, may be NULL), the sum reduced in
+ * FP64 in a fixed order (deterministic).
+ */
+int mc_h_eps(const mcr_medium *med, const float *coeff, const float *Hmeas, float *H, float *dL_dH,
+             double *eps, void *stream);
+
+/*
+ * mc_adjoint_source -- q*_i = -mu_a,i dL_dH_i / dx^2 (device out [nz][nx] FP32).  For the
+ * paper's eps (dL_dH = -dx^2 (H^meas - H)) this is q* = mu_a (H^meas - H) of Sec. 6.
+ */
+int mc_adjoint_source(const mcr_medium *med, const float *dL_dH, float *qstar, void *stream);
+
+/*
+ * mc_gradient -- functional gradients from forward and adjoint coefficients (Sec. 5).
+ * Per pixel, in FP64 with the sums over n in increasing n:
+ *   G_a = a_0 a_0^* / (2 pi) + (1/pi) sum_{n=1..K} (a_n a_n^* + b_n b_n^*)             (Eq. 22)
+ *   G_s = (1/pi) sum_{n=1..K} (a_n a_n^* + b_n b_n^*) (1 - g^n)                    (Eq. 28)
+ *   d_mua = dL_dH a_0 + dx^2 G_a,   d_mus = dx^2 G_s     (device out [nz][nx] FP64)
+ * i.e. the gradient of the pixel loss L with respect to each pixel's mu_a and mu_s.  With
+ * dL_dH = -dx^2 (H^meas - H) this is dx^2 times Eqs. 22 and 28.  d_mus may be NULL.
+ */
+int mc_gradient(const mcr_medium *med, int32_t K, const float *coeff, const float *coeff_adj,
+                const float *dL_dH, double *d_mua, double *d_mus, void *stream);
+
+/* Synchronises `stream` and returns (and clears) the device's latched error status. */
+int mc_check(void *stream);
+
+/*
+ * mc_last_run_info -- profiling query (the paper has no counterpart).  which = 0: the last
+ * mc_forward call on the current device; which = 1: the last mc_adjoint call.  Fills `stats`
+ * (host, may be NULL) with that call's counters and `transport_ms` (host, may be NULL) with the
+ * device time of its transport kernel launch(es), measured by CUDA events recorded on the
+ * call's stream around them.  Waits for that call to finish.  MCR_ERR_ARG if no such call ran.
+ */
+int mc_last_run_info(int32_t which, mcr_stats *stats, float *transport_ms);
+
+/* Frees the calling device's workspace (synchronises the device). */
+int mc_release_workspace(void);
+
+/* Static text for a status code. */
+const char *mc_status_string(int status);
+
+/* Library version string, e.g. "mcr 1.0 sm_103a". */
+const char *mc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCR_H */

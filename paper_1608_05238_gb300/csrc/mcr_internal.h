@@ -1,0 +1,111 @@
+// mcr_internal.h -- declarations shared by the translation units of libmcr (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mcr.h"
+
+namespace mcr {
+
+// Fixed-point quantum of the tallies: 2^-32 (weight x mm).
+constexpr float kFixScale = 4294967296.0f;
+constexpr double kFixInv = 1.0 / 4294967296.0;
+// Packets per transport launch; longer runs are split into chunks whose fixed-point sums are
+// flushed into an FP64 accumulator in chunk order (keeps |sum| far below 2^63).
+constexpr uint64_t kChunkPackets = 1ull << 26;
+
+// Source kinds seen by the transport kernel (MCR_* plus the volumetric adjoint source).
+constexpr int kVolume = 3;
+
+// Device counters of one run, accumulated per warp.
+struct DevStats {
+  unsigned long long launched, flights, collisions, segments, escapes;
+  unsigned long long rr_kill, rr_survive, scatter_limit, event_limit;
+  double launched_w, escaped_w, rr_net_w, killed_w;
+};
+
+// Error bits latched on the device.
+constexpr unsigned kFlagEventLimit = 1u;
+constexpr unsigned kFlagOverflow = 2u;
+constexpr unsigned kFlagMedium = 4u;
+
+struct TransportParams {
+  // medium
+  int nx, nz;
+  float dx;
+  float hg_c;  // (1 - g) / (1 + g)
+  const float2 *mu;  // packed (mu_a, mu_s) per pixel
+  // source
+  int kind;
+  float x0, z0, x1, z1, dir_x, dir_z;
+  const unsigned long long *cdf;  // volumetric: inclusive prefix of quantised |q|
+  const float *q;                 // volumetric: signed source (for the packet sign)
+  // run
+  int K, C, Cpad, row_stride;     // C = 2K+1 channels, Cpad = C rounded up to 4, smem row stride
+  unsigned long long first_packet, n_packets;
+  unsigned key0, key1;
+  unsigned max_scatter, max_events;
+  float w_threshold, rr_p, rr_inv_p;
+  // outputs / scratch
+  unsigned long long *tally;      // [npix][Cpad] fixed point
+  unsigned long long *work;       // packet counter
+  DevStats *stats;
+  const unsigned *flags;          // medium-invalid flag: transport does nothing if set
+};
+
+// Workspace of one device (grow-only).
+struct Workspace {
+  int device = -1;
+  unsigned long long *tally = nullptr;
+  size_t tally_bytes = 0;
+  double *acc = nullptr;  // FP64 chunk accumulator [C][npix]
+  size_t acc_bytes = 0;
+  float2 *mu = nullptr;
+  size_t mu_bytes = 0;
+  unsigned long long *cdf = nullptr;
+  size_t cdf_bytes = 0;
+  unsigned long long *block_sums = nullptr;
+  size_t block_sums_bytes = 0;
+  double *partials = nullptr;
+  size_t partials_bytes = 0;
+  // small block: packet counter, per-kind run counters (0 forward, 1 adjoint), flags
+  unsigned char *small = nullptr;
+  unsigned long long *work() const { return reinterpret_cast<unsigned long long *>(small); }
+  DevStats *stats(int slot) const { return reinterpret_cast<DevStats *>(small + 64 + 128 * slot); }
+  unsigned *qmax_bits() const { return reinterpret_cast<unsigned *>(small + 320); }
+  unsigned *flags() const { return reinterpret_cast<unsigned *>(small + 324); }
+  // events around the transport launches of the last forward (0) and adjoint (1) call
+  cudaEvent_t ev_start[2] = {nullptr, nullptr};
+  cudaEvent_t ev_stop[2] = {nullptr, nullptr};
+  bool ran[2] = {false, false};
+};
+
+constexpr size_t kSmallBytes = 512;
+static_assert(sizeof(DevStats) <= 128, "stats slot");
+
+// ---- launchers (each enqueues on `s` and returns the launch error) ----
+cudaError_t launch_pack_medium(const float *mua, const float *mus, float2 *mu, int64_t npix, unsigned *flags,
+                               cudaStream_t s);
+cudaError_t launch_transport(const TransportParams &p, cudaStream_t s);
+size_t transport_smem_bytes(int row_stride);
+cudaError_t launch_source_cdf(const float *q, int64_t npix, unsigned long long *cdf,
+                              unsigned long long *block_sums, size_t block_sums_cap, unsigned *qmax_bits,
+                              cudaStream_t s);
+// accumulate (chunked runs): acc[c][pix] += tally[pix][c] * 2^-32
+cudaError_t launch_accumulate(const unsigned long long *tally, int64_t npix, int C, int Cpad, double *acc,
+                              cudaStream_t s);
+// coeff[c][pix] = sums * scale, sign (-1)^n on channels 2n-1, 2n when `adjoint`.
+// scale = fixed_scale (forward) or 2 pi qmax total 2^-32 / N_p (volumetric: read on device).
+cudaError_t launch_finalize(const unsigned long long *tally, const double *acc, int64_t npix, int C, int Cpad,
+                            double fixed_scale, bool volumetric, const unsigned *qmax_bits,
+                            const unsigned long long *cdf_total, double n_packets, bool adjoint, float *coeff,
+                            unsigned *flags, cudaStream_t s);
+cudaError_t launch_h_eps(const float *mua, const float *a0, const float *Hmeas, int64_t npix, float area, float *H,
+                         float *dL_dH, double *partials, size_t partials_cap, double *eps, cudaStream_t s);
+cudaError_t launch_adjoint_source(const float *mua, const float *dL_dH, int64_t npix, float area, float *q,
+                                  cudaStream_t s);
+cudaError_t launch_gradient(const float *coeff, const float *coeff_adj, const float *dL_dH, int64_t npix, int K,
+                            double g, double area, double *d_mua, double *d_mus, cudaStream_t s);
+
+}  // namespace mcr

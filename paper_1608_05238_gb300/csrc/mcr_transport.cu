@@ -1,0 +1,403 @@
+// mcr_transport.cu -- the photon-packet transport kernel of the forward and adjoint harmonic
+// radiance Monte Carlo (Sec. 3, 3.1 and 4 of Hochuli et al., arXiv 1608.05238), for sm_103a.
+//
+// Design (one GPU, HBM/L2 resident tallies):
+//  * Persistent warps.  Each lane carries one packet; a lane whose packet ended takes the next
+//    packet id from a global counter (one atomic per warp per refill), so lanes stay busy
+//    until the run's packets are used up.  One loop iteration = one pixel segment per lane.
+//  * Counter-based Philox4x32-10 per packet: the random numbers of packet p depend only on
+//    (seed, stream_id, p, event), never on which warp ran it.
+//  * Pixel traversal keeps integer pixel indices authoritative and the position as an offset
+//    inside the pixel (exactly 0 or dx after an edge crossing), so FP32 positions do not drift.
+//  * Harmonic vectors h = (1, cos theta, sin theta, ..., cos K theta, sin K theta) are built
+//    once per free flight from (s_z + i s_x)^n (K complex products, no trigonometry) into a
+//    per-lane shared-memory row.
+//  * Deposits are warp-cooperative: for each pixel touched in this iteration, the lanes of the
+//    warp take one coefficient each, sum the contributions of every lane in that pixel (warp
+//    reduction via match_any) as 64-bit fixed-point integers, and issue one coalesced red.add
+//    per coefficient into the pixel-major tally [pix][Cpad].  Integer sums are exact, so the
+//    tally does not depend on scheduling.
+#include <math_constants.h>
+
+#include "mcr_internal.h"
+
+namespace mcr {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32->64 products and
+// xors, Weyl-incremented key.
+__device__ __forceinline__ uint4 philox4x32_10(unsigned long long pid, unsigned event, unsigned k0,
+                                               unsigned k1) {
+  unsigned c0 = (unsigned)pid, c1 = (unsigned)(pid >> 32), c2 = event, c3 = 0u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const unsigned lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const unsigned n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// Uniform in (0,1): ((x >> 9) + 1/2) 2^-23, exact in FP32.
+__device__ __forceinline__ float u01(unsigned x) { return fmaf((float)(x >> 9), 0x1p-23f, 0x1p-24f); }
+
+// Volumetric source: smallest i with cdf[i] > floor(r48 * total / 2^48).
+__device__ __forceinline__ int pick_pixel(const unsigned long long *__restrict__ cdf, int npix, unsigned w0,
+                                          unsigned w1) {
+  const unsigned long long total = cdf[npix - 1];
+  const unsigned long long r48 = ((unsigned long long)w0 << 16) | (unsigned long long)(w1 >> 16);
+  const unsigned long long target = __umul64hi(r48 << 16, total);
+  int lo = 0, hi = npix - 1;
+  while (lo < hi) {
+    const int mid = lo + ((hi - lo) >> 1);
+    if (__ldg(cdf + mid) > target)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ float clamp_dx(float v, float dx) { return fminf(fmaxf(v, 0.f), dx); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+template <int NP>
+__global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
+  extern __shared__ float smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  float *const rows = smem + (size_t)warp * 32 * p.row_stride;
+  float *const my = rows + lane * p.row_stride;
+  if (*p.flags & kFlagMedium) return;
+  if (p.kind == kVolume && p.cdf[p.nx * p.nz - 1] == 0ull) return;  // all-zero source: nothing to launch
+
+  const float dx = p.dx;
+  const int nx = p.nx, nz = p.nz, K = p.K, C = p.C;
+
+  bool alive = false, exhausted = false;
+  unsigned long long pid = 0;
+  float fx = 0.f, fz = 0.f, sx = 0.f, sz = 1.f, inv_ax = 0.f, inv_az = 0.f, W = 0.f, tau = 0.f;
+  int ix = 0, iz = 0;
+  unsigned flight = 0, nscat = 0, cu1 = 0, cu2 = 0;
+  unsigned n_launch = 0, n_flight = 0, n_coll = 0, n_seg = 0, n_esc = 0, n_rrk = 0, n_rrs = 0, n_scl = 0,
+           n_evl = 0;
+  double w_launch = 0.0, w_esc = 0.0, w_rr = 0.0, w_kill = 0.0;
+
+  // harmonic row of the current flight direction: h_n = (s_z + i s_x)^n
+  auto write_row = [&]() {
+    my[0] = 1.f;
+    float c = sz, s = sx;
+    if (K >= 1) {
+      my[1] = c;
+      my[2] = s;
+    }
+    for (int n = 2; n <= K; ++n) {
+      const float cn = fmaf(c, sz, -s * sx);
+      const float sn = fmaf(s, sz, c * sx);
+      c = cn;
+      s = sn;
+      my[2 * n - 1] = c;
+      my[2 * n] = s;
+    }
+  };
+  // start free flight number `flight` (event flight+1): tau = -ln U, keep U for scatter/roulette
+  auto begin_flight = [&]() {
+    const uint4 r = philox4x32_10(pid, flight + 1u, p.key0, p.key1);
+    tau = -logf(u01(r.x));
+    cu1 = r.y;
+    cu2 = r.z;
+    inv_ax = 1.f / fabsf(sx);
+    inv_az = 1.f / fabsf(sz);
+    ++n_flight;
+    write_row();
+  };
+
+  for (;;) {
+    // ---------------------------------------------------------------- refill / launch
+    const unsigned need = __ballot_sync(kFull, !alive && !exhausted);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(p.work, (unsigned long long)__popc(need));
+      base = __shfl_sync(kFull, base, leader);
+      if (!alive && !exhausted) {
+        const unsigned long long idx = base + __popc(need & ((1u << lane) - 1u));
+        if (idx >= p.n_packets) {
+          exhausted = true;
+        } else {
+          pid = p.first_packet + idx;
+          ++n_launch;
+          float W0 = 1.f;
+          bool inside = true;
+          if (p.kind == kVolume) {
+            const uint4 r0 = philox4x32_10(pid, 0u, p.key0, p.key1);
+            const uint4 r1 = philox4x32_10(pid, 1u, p.key0, p.key1);
+            const int pix = pick_pixel(p.cdf, nx * nz, r0.x, r0.y);
+            ix = pix % nx;
+            iz = pix / nx;
+            fx = u01(r1.x) * dx;
+            fz = u01(r1.y) * dx;
+            sincospif(2.f * u01(r0.z), &sx, &sz);
+            W0 = __ldg(p.q + pix) < 0.f ? -1.f : 1.f;
+          } else {
+            float x = p.x0, z = p.z0;
+            sx = p.dir_x;
+            sz = p.dir_z;
+            if (p.kind == MCR_LINE) {
+              const uint4 r0 = philox4x32_10(pid, 0u, p.key0, p.key1);
+              const float u = u01(r0.x);
+              x = fmaf(u, p.x1 - p.x0, p.x0);
+              z = fmaf(u, p.z1 - p.z0, p.z0);
+            } else if (p.kind == MCR_ISO_POINT) {
+              const uint4 r0 = philox4x32_10(pid, 0u, p.key0, p.key1);
+              sincospif(2.f * u01(r0.z), &sx, &sz);
+            }
+            inside = x >= 0.f && x <= nx * dx && z >= 0.f && z <= nz * dx;
+            if (inside) {
+              ix = min((int)floorf(x / dx), nx - 1);
+              iz = min((int)floorf(z / dx), nz - 1);
+              fx = clamp_dx(x - ix * dx, dx);
+              fz = clamp_dx(z - iz * dx, dx);
+            }
+          }
+          W = W0;
+          w_launch += W0;
+          nscat = 0;
+          flight = 0;
+          if (!inside) {
+            ++n_esc;
+            w_esc += W;
+          } else if (p.max_events == 0u) {
+            ++n_evl;
+            w_kill += W;
+          } else {
+            flight = 1;
+            begin_flight();
+            alive = true;
+          }
+        }
+      }
+    }
+    if (!__any_sync(kFull, alive)) break;
+    __syncwarp();
+
+    // ---------------------------------------------------------------- one pixel segment
+    int seg_pix = -1;
+    float seg_t = 0.f;
+    bool collided = false, escaped = false;
+    if (alive) {
+      const int pix = iz * nx + ix;
+      const float2 m = __ldg(p.mu + pix);  // (mu_a, mu_s)
+      float dist_x = CUDART_INF_F, dist_z = CUDART_INF_F;
+      if (sx != 0.f) dist_x = fmaxf((sx > 0.f ? dx - fx : fx) * inv_ax, 0.f);
+      if (sz != 0.f) dist_z = fmaxf((sz > 0.f ? dx - fz : fz) * inv_az, 0.f);
+      const float d_edge = fminf(dist_x, dist_z);
+      const float d_coll = tau / m.y;  // +inf when mu_s = 0
+      collided = d_coll < d_edge;
+      const float l = collided ? d_coll : d_edge;
+      // track weight of the segment: W (1 - e^{-mu_a l}) / mu_a, then W <- W e^{-mu_a l}
+      const float em1 = expm1f(-m.x * l);
+      const float t = m.x > 0.f ? (-W * em1) / m.x : W * l;
+      W = fmaf(W, em1, W);
+      ++n_seg;
+      if (t != 0.f) {
+        seg_pix = pix;
+        seg_t = t;
+      }
+      if (collided) {
+        fx = clamp_dx(fmaf(l, sx, fx), dx);
+        fz = clamp_dx(fmaf(l, sz, fz), dx);
+      } else {
+        tau = fmaxf(fmaf(-m.y, l, tau), 0.f);
+        if (dist_x <= dist_z) {  // ties: x first, z follows as a zero-length segment
+          if (sx > 0.f) {
+            ++ix;
+            fx = 0.f;
+          } else {
+            --ix;
+            fx = dx;
+          }
+          fz = clamp_dx(fmaf(l, sz, fz), dx);
+        } else {
+          if (sz > 0.f) {
+            ++iz;
+            fz = 0.f;
+          } else {
+            --iz;
+            fz = dx;
+          }
+          fx = clamp_dx(fmaf(l, sx, fx), dx);
+        }
+        escaped = (unsigned)ix >= (unsigned)nx || (unsigned)iz >= (unsigned)nz;
+      }
+    }
+
+    // ---------------------------------------------------------------- cooperative deposit
+    unsigned pend = __ballot_sync(kFull, seg_pix >= 0);
+    if (pend) {
+      const unsigned same = __match_any_sync(kFull, seg_pix);
+      while (pend) {
+        const int L = __ffs(pend) - 1;
+        const unsigned grp = __shfl_sync(kFull, same, L) & pend;
+        const int pix = __shfl_sync(kFull, seg_pix, L);
+        long long acc[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) acc[q] = 0;
+        unsigned g = grp;
+        while (g) {
+          const int M = __ffs(g) - 1;
+          g &= g - 1;
+          const float t = __shfl_sync(kFull, seg_t, M);
+          const float *hr = rows + M * p.row_stride;
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            const int j = q * 32 + lane;
+            if (j < C) acc[q] += __float2ll_rn(t * hr[j] * kFixScale);
+          }
+        }
+        unsigned long long *dst = p.tally + (size_t)pix * p.Cpad;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const int j = q * 32 + lane;
+          if (j < C && acc[q] != 0) atomicAdd(dst + j, (unsigned long long)acc[q]);
+        }
+        pend &= ~grp;
+      }
+    }
+    __syncwarp();
+
+    // ---------------------------------------------------------------- escape / collision
+    if (alive) {
+      if (escaped) {
+        ++n_esc;
+        w_esc += W;
+        alive = false;
+      } else if (collided) {
+        ++n_coll;
+        if (nscat >= p.max_scatter) {
+          ++n_scl;
+          w_kill += W;
+          alive = false;
+        } else {
+          // 2D HG angle theta_s = 2 atan(c tan(pi U)) (Eq. 7), applied as a rotation with
+          // cos theta_s = (cp^2 - c^2 sp^2)/(cp^2 + c^2 sp^2), sin theta_s = 2 c sp cp/(...),
+          // (sp, cp) = (sin pi U, cos pi U): the same angle without tan's pole at U = 1/2.
+          float sp, cp;
+          sincospif(u01(cu1), &sp, &cp);
+          const float a = cp * cp, b = p.hg_c * p.hg_c * sp * sp;
+          const float inv = 1.f / (a + b);
+          const float cs = (a - b) * inv, sn = 2.f * p.hg_c * sp * cp * inv;
+          const float nsx = fmaf(sx, cs, sz * sn), nsz = fmaf(sz, cs, -sx * sn);
+          const float rn = rsqrtf(fmaf(nsx, nsx, nsz * nsz));
+          sx = nsx * rn;
+          sz = nsz * rn;
+          ++nscat;
+          if (fabsf(W) < p.w_threshold) {  // |W0| = 1
+            if (u01(cu2) < p.rr_p) {
+              const float Wn = W * p.rr_inv_p;
+              w_rr += (double)Wn - (double)W;
+              W = Wn;
+              ++n_rrs;
+            } else {
+              w_rr -= W;
+              ++n_rrk;
+              alive = false;
+            }
+          }
+          if (alive) {
+            if (flight >= p.max_events) {
+              ++n_evl;
+              w_kill += W;
+              alive = false;
+            } else {
+              ++flight;
+              begin_flight();
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+
+  // ---------------------------------------------------------------- counters
+  const unsigned c_launch = __reduce_add_sync(kFull, n_launch), c_flight = __reduce_add_sync(kFull, n_flight),
+                 c_coll = __reduce_add_sync(kFull, n_coll), c_seg = __reduce_add_sync(kFull, n_seg),
+                 c_esc = __reduce_add_sync(kFull, n_esc), c_rrk = __reduce_add_sync(kFull, n_rrk),
+                 c_rrs = __reduce_add_sync(kFull, n_rrs), c_scl = __reduce_add_sync(kFull, n_scl),
+                 c_evl = __reduce_add_sync(kFull, n_evl);
+  w_launch = warp_sum(w_launch);
+  w_esc = warp_sum(w_esc);
+  w_rr = warp_sum(w_rr);
+  w_kill = warp_sum(w_kill);
+  if (lane == 0 && c_launch) {
+    DevStats *s = p.stats;
+    atomicAdd(&s->launched, (unsigned long long)c_launch);
+    atomicAdd(&s->flights, (unsigned long long)c_flight);
+    atomicAdd(&s->collisions, (unsigned long long)c_coll);
+    atomicAdd(&s->segments, (unsigned long long)c_seg);
+    atomicAdd(&s->escapes, (unsigned long long)c_esc);
+    if (c_rrk) atomicAdd(&s->rr_kill, (unsigned long long)c_rrk);
+    if (c_rrs) atomicAdd(&s->rr_survive, (unsigned long long)c_rrs);
+    if (c_scl) atomicAdd(&s->scatter_limit, (unsigned long long)c_scl);
+    if (c_evl) atomicAdd(&s->event_limit, (unsigned long long)c_evl);
+    atomicAdd(&s->launched_w, w_launch);
+    atomicAdd(&s->escaped_w, w_esc);
+    atomicAdd(&s->rr_net_w, w_rr);
+    atomicAdd(&s->killed_w, w_kill);
+  }
+}
+
+template <int NP>
+cudaError_t launch_np(const TransportParams &p, cudaStream_t s) {
+  const size_t smem = transport_smem_bytes(p.row_stride);
+  static int configured_dev[64];  // smem attribute set once per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaError_t e = cudaSuccess;
+  if (dev < 64 && configured_dev[dev] != (int)smem + 1) {
+    e = cudaFuncSetAttribute(k_transport<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured_dev[dev] = (int)smem + 1;
+  }
+  int sms = 0, per_sm = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport<NP>, 128, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  k_transport<NP><<<sms * per_sm, 128, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t transport_smem_bytes(int row_stride) { return (size_t)4 * 32 * row_stride * sizeof(float); }
+
+cudaError_t launch_transport(const TransportParams &p, cudaStream_t s) {
+  const int np = (p.C + 31) / 32;
+  switch (np) {
+    case 1: return launch_np<1>(p, s);
+    case 2: return launch_np<2>(p, s);
+    case 3: return launch_np<3>(p, s);
+    case 4: return launch_np<4>(p, s);
+    case 5: return launch_np<5>(p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace mcr

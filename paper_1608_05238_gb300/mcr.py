@@ -1,0 +1,283 @@
+"""Thin Python binding of libmcr (include/mcr.h): argument marshalling only.
+
+Every step of the path runs in the CUDA library; this module passes torch device pointers, the
+current CUDA stream and plain structs through ctypes, and raises :class:`McrError` on a negative
+status.  There is no CPU fallback: if ``libmcr.so`` is missing or no GPU is present the calls
+raise.  Names follow the paper (Hochuli et al., arXiv 1608.05238): ``mua``/``mus`` are mu_a and
+mu_s maps [nz, nx] in 1/mm, ``dx`` the pixel side in mm, ``g`` the 2D Henyey-Greenstein
+anisotropy, ``K`` the harmonic order; coefficient tensors are [2K+1, nz, nx] with channel 0 = a_0,
+2n-1 = a_n, 2n = b_n.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _build
+
+PENCIL, LINE, ISO_POINT = 0, 1, 2
+MAX_K = 64
+
+OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_EVENT_LIMIT, ERR_TALLY_OVERFLOW, ERR_MEDIUM = 0, -1, -2, -3, -4, -5, -6
+
+# every symbol declared in include/mcr.h
+EXPORTS = ("mc_forward", "mc_adjoint", "mc_h_eps", "mc_adjoint_source", "mc_gradient", "mc_check",
+           "mc_last_run_info", "mc_release_workspace", "mc_status_string", "mc_version")
+
+
+class McrError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+class _Medium(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("nz", C.c_int32), ("dx", C.c_float), ("g", C.c_float),
+                ("mua", C.c_void_p), ("mus", C.c_void_p)]
+
+
+class _Source(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("x0", C.c_float), ("z0", C.c_float), ("x1", C.c_float), ("z1", C.c_float),
+                ("dir_x", C.c_float), ("dir_z", C.c_float), ("power", C.c_float)]
+
+
+class _Run(C.Structure):
+    _fields_ = [("K", C.c_int32), ("max_scatter", C.c_uint32), ("n_packets", C.c_uint64),
+                ("first_packet", C.c_uint64), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
+                ("max_events", C.c_uint32), ("w_threshold", C.c_float), ("roulette_p", C.c_float)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("launched", "flights", "collisions", "segments", "escapes", "rr_kill",
+                                          "rr_survive", "scatter_limit", "event_limit")] + \
+               [(n, C.c_double) for n in ("launched_w", "escaped_w", "rr_net_w", "killed_w", "absorbed_w")]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> C.CDLL:
+    """Load libmcr.so (built by ``__graft_entry__.build()`` / ``_build.build()``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libmcr.so is not built ({_build.LIB}); run __graft_entry__.build() first")
+        lib = C.CDLL(_build.LIB)
+        vp = C.c_void_p
+        lib.mc_forward.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
+        lib.mc_adjoint.argtypes = [C.POINTER(_Medium), vp, C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
+        lib.mc_h_eps.argtypes = [C.POINTER(_Medium), vp, vp, vp, vp, vp, vp]
+        lib.mc_adjoint_source.argtypes = [C.POINTER(_Medium), vp, vp, vp]
+        lib.mc_gradient.argtypes = [C.POINTER(_Medium), C.c_int32, vp, vp, vp, vp, vp, vp]
+        lib.mc_check.argtypes = [vp]
+        lib.mc_last_run_info.argtypes = [C.c_int32, C.POINTER(_Stats), C.POINTER(C.c_float)]
+        lib.mc_release_workspace.argtypes = []
+        lib.mc_status_string.argtypes = [C.c_int]
+        lib.mc_status_string.restype = C.c_char_p
+        lib.mc_version.argtypes = []
+        lib.mc_version.restype = C.c_char_p
+        for name in ("mc_forward", "mc_adjoint", "mc_h_eps", "mc_adjoint_source", "mc_gradient", "mc_check",
+                     "mc_last_run_info", "mc_release_workspace"):
+            getattr(lib, name).restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def status_string(status: int) -> str:
+    return load().mc_status_string(int(status)).decode()
+
+
+def version() -> str:
+    return load().mc_version().decode()
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise McrError(rc, where)
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev_f32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    return t
+
+
+@dataclass
+class Medium:
+    """Pixelised medium (Sec. 3): mu_a, mu_s maps [nz, nx] (float32 CUDA), pixel side dx, HG g."""
+    mua: torch.Tensor
+    mus: torch.Tensor
+    dx: float
+    g: float
+
+    @property
+    def shape(self):
+        return tuple(self.mua.shape)
+
+    def c(self) -> _Medium:
+        _dev_f32(self.mua, "mua")
+        _dev_f32(self.mus, "mus")
+        if self.mua.shape != self.mus.shape or self.mua.dim() != 2:
+            raise ValueError("mua and mus must have the same [nz, nx] shape")
+        nz, nx = self.mua.shape
+        return _Medium(nx, nz, float(self.dx), float(self.g), self.mua.data_ptr(), self.mus.data_ptr())
+
+
+@dataclass
+class Source:
+    """Forward source: PENCIL / LINE / ISO_POINT (positions in mm, direction normalised by the library)."""
+    kind: int
+    x0: float = 0.0
+    z0: float = 0.0
+    x1: float = 0.0
+    z1: float = 0.0
+    dir_x: float = 0.0
+    dir_z: float = 1.0
+    power: float = 1.0
+
+    def c(self) -> _Source:
+        return _Source(int(self.kind), self.x0, self.z0, self.x1, self.z1, self.dir_x, self.dir_z, self.power)
+
+    def as_dict(self) -> dict:
+        return dict(kind=self.kind, x0=self.x0, z0=self.z0, x1=self.x1, z1=self.z1, dir_x=self.dir_x,
+                    dir_z=self.dir_z, power=self.power)
+
+
+@dataclass
+class Run:
+    """MC run parameters (mcr_run)."""
+    K: int
+    n_packets: int
+    seed: int = 0
+    stream_id: int = 0
+    first_packet: int = 0
+    max_scatter: int = 0xFFFFFFFF
+    max_events: int = 10_000_000
+    w_threshold: float = 1e-4
+    roulette_p: float = 0.1
+
+    def c(self) -> _Run:
+        return _Run(int(self.K), int(self.max_scatter), int(self.n_packets), int(self.first_packet),
+                    int(self.seed) & 0xFFFFFFFFFFFFFFFF, int(self.stream_id), int(self.max_events),
+                    float(self.w_threshold), float(self.roulette_p))
+
+
+def _stats_dict(st: _Stats) -> dict:
+    return {n: getattr(st, n) for n, _ in _Stats._fields_}
+
+
+def _coeff_out(med: Medium, K: int, out):
+    nz, nx = med.shape
+    if out is None:
+        return torch.empty((2 * K + 1, nz, nx), dtype=torch.float32, device=med.mua.device)
+    _dev_f32(out, "out")
+    if tuple(out.shape) != (2 * K + 1, nz, nx):
+        raise ValueError("out must be [2K+1, nz, nx]")
+    return out
+
+
+def forward(med: Medium, src: Source, run: Run, out=None, stats: bool = False, stream=None):
+    """Forward harmonic radiance MC (``mc_forward``); returns coeff [2K+1, nz, nx] (and stats dict)."""
+    lib = load()
+    coeff = _coeff_out(med, run.K, out)
+    st = _Stats() if stats else None
+    rc = lib.mc_forward(C.byref(med.c()), C.byref(src.c()), C.byref(run.c()), _ptr(coeff),
+                        C.byref(st) if st is not None else None, _stream(stream))
+    _check(rc, "mc_forward")
+    return (coeff, _stats_dict(st)) if stats else coeff
+
+
+def adjoint(med: Medium, qstar: torch.Tensor, run: Run, out=None, stats: bool = False, stream=None):
+    """Adjoint harmonic radiance MC from q* (``mc_adjoint``); returns coeff_adj (and stats dict)."""
+    lib = load()
+    _dev_f32(qstar, "qstar")
+    if tuple(qstar.shape) != med.shape:
+        raise ValueError("qstar must have the medium's shape")
+    coeff = _coeff_out(med, run.K, out)
+    st = _Stats() if stats else None
+    rc = lib.mc_adjoint(C.byref(med.c()), _ptr(qstar), C.byref(run.c()), _ptr(coeff),
+                        C.byref(st) if st is not None else None, _stream(stream))
+    _check(rc, "mc_adjoint")
+    return (coeff, _stats_dict(st)) if stats else coeff
+
+
+def h_eps(med: Medium, coeff: torch.Tensor, Hmeas: torch.Tensor | None = None, stream=None):
+    """H = mu_a a_0; with Hmeas also dL/dH = -dx^2 (Hmeas - H) and eps (``mc_h_eps``).
+
+    Returns H, or (H, dL_dH, eps) with eps a 0-d float64 CUDA tensor.
+    """
+    lib = load()
+    _dev_f32(coeff, "coeff")
+    H = torch.empty(med.shape, dtype=torch.float32, device=coeff.device)
+    if Hmeas is None:
+        _check(lib.mc_h_eps(C.byref(med.c()), _ptr(coeff), None, _ptr(H), None, None, _stream(stream)), "mc_h_eps")
+        return H
+    _dev_f32(Hmeas, "Hmeas")
+    v = torch.empty_like(H)
+    eps = torch.empty((), dtype=torch.float64, device=coeff.device)
+    _check(lib.mc_h_eps(C.byref(med.c()), _ptr(coeff), _ptr(Hmeas), _ptr(H), _ptr(v), _ptr(eps), _stream(stream)),
+           "mc_h_eps")
+    return H, v, eps
+
+
+def adjoint_source(med: Medium, dL_dH: torch.Tensor, stream=None) -> torch.Tensor:
+    """q* = -mu_a dL/dH / dx^2 (``mc_adjoint_source``)."""
+    lib = load()
+    _dev_f32(dL_dH, "dL_dH")
+    q = torch.empty(med.shape, dtype=torch.float32, device=dL_dH.device)
+    _check(lib.mc_adjoint_source(C.byref(med.c()), _ptr(dL_dH), _ptr(q), _stream(stream)), "mc_adjoint_source")
+    return q
+
+
+def gradient(med: Medium, coeff: torch.Tensor, coeff_adj: torch.Tensor, dL_dH: torch.Tensor, stream=None):
+    """(dL/dmu_a, dL/dmu_s) per pixel in float64 (``mc_gradient``, Eqs. 22 and 28 x dx^2)."""
+    lib = load()
+    for t, n in ((coeff, "coeff"), (coeff_adj, "coeff_adj"), (dL_dH, "dL_dH")):
+        _dev_f32(t, n)
+    K = (coeff.shape[0] - 1) // 2
+    if coeff.shape != coeff_adj.shape:
+        raise ValueError("coeff and coeff_adj must match")
+    d_mua = torch.empty(med.shape, dtype=torch.float64, device=coeff.device)
+    d_mus = torch.empty_like(d_mua)
+    _check(lib.mc_gradient(C.byref(med.c()), K, _ptr(coeff), _ptr(coeff_adj), _ptr(dL_dH), _ptr(d_mua), _ptr(d_mus),
+                           _stream(stream)), "mc_gradient")
+    return d_mua, d_mus
+
+
+def check(stream=None):
+    """Synchronise and raise any latched device error (``mc_check``)."""
+    _check(load().mc_check(_stream(stream)), "mc_check")
+
+
+def last_run_info(which: str = "forward"):
+    """(stats dict, transport kernel ms) of the last forward / adjoint call (``mc_last_run_info``)."""
+    st = _Stats()
+    ms = C.c_float(0.0)
+    _check(load().mc_last_run_info(0 if which == "forward" else 1, C.byref(st), C.byref(ms)), "mc_last_run_info")
+    return _stats_dict(st), float(ms.value)
+
+
+def release_workspace():
+    _check(load().mc_release_workspace(), "mc_release_workspace")

@@ -1,0 +1,137 @@
+"""Seeded synthetic inputs shaped like the paper's phantoms (no dataset exists for this method).
+
+This module holds input generators only -- pixel maps, source descriptors and run sizes -- and
+none of the method's arithmetic; the CUDA path and the oracle both draw their inputs from it.
+The paper's phantoms (Sec. 6.1, 6.2: background mu_a 0.01/mm, inclusions of 0.2/mm, mu_s 5 -> 15
+/mm, g = 0.9, collimated line sources) are under-specified, so the media below are synthetic
+stand-ins of the same kind: a homogeneous background with random circular inclusions, or a
+smooth lognormal random field.
+
+Workloads (sizes in pixels, dx in mm):
+  * ``pencil32``  32x32 of 0.25 mm, mu_a 0.01, mu_s 5, g 0.8, pencil beam at the top centre,
+                  K = 8, 1e5 packets, seed 0.
+  * ``grad256``   256x256 of 0.05 mm (12.8 mm), background mu_a 0.01 / mu_s 10, g 0.9,
+                  3 random circular inclusions (mu_a 0.02-0.2, mu_s 5-20), collimated line source
+                  on the top edge, K = 32, 1e7 packets forward + 1e7 adjoint, gradient.
+  * ``large1024`` 1024x1024 of 0.02 mm, same background, 8 inclusions (mu_s <= 20), K = 64,
+                  1e9 packets, four line sources (one per edge).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+PENCIL, LINE, ISO_POINT = 0, 1, 2
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    nz: int
+    dx: float
+    g: float
+    K: int
+    n_packets: int
+    mua: np.ndarray          # current estimate [nz, nx] float32
+    mus: np.ndarray
+    sources: list            # list of source dicts (kind, x0, z0, x1, z1, dir_x, dir_z, power)
+    mua_true: np.ndarray | None = None   # phantom that generates H^meas (gradient workloads)
+    mus_true: np.ndarray | None = None
+    seed: int = 0
+    meta: dict = field(default_factory=dict)
+
+
+def inclusion_phantom(n: int, dx: float, n_incl: int, seed: int, mua_bg=0.01, mus_bg=10.0,
+                      mua_range=(0.02, 0.2), mus_range=(5.0, 20.0), radius=(0.5, 1.5), margin=2.0):
+    """Homogeneous background with circular inclusions (later ones overwrite earlier ones).
+
+    Centres uniform in [margin, L - margin]^2 (L = n dx), radii uniform in ``radius`` (mm),
+    inclusion mu_a / mu_s uniform in the given ranges; numpy ``default_rng(seed)``.
+    """
+    rng = np.random.default_rng(seed)
+    L = n * dx
+    c = (np.arange(n) + 0.5) * dx
+    X, Z = np.meshgrid(c, c)
+    mua = np.full((n, n), mua_bg, np.float64)
+    mus = np.full((n, n), mus_bg, np.float64)
+    for _ in range(n_incl):
+        cx, cz = rng.uniform(margin, L - margin, 2)
+        r = rng.uniform(*radius)
+        a = rng.uniform(*mua_range)
+        s = rng.uniform(*mus_range)
+        m = (X - cx) ** 2 + (Z - cz) ** 2 <= r * r
+        mua[m] = a
+        mus[m] = s
+    return mua.astype(np.float32), mus.astype(np.float32)
+
+
+def lognormal_field(n: int, dx: float, mean: float, sigma: float, corr_mm: float, seed: int):
+    """mean * exp(sigma G - sigma^2/2), G a unit-variance Gaussian random field with squared-
+    exponential correlation of length corr_mm, made by FFT-filtering seeded white noise."""
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal((n, n))
+    k = np.fft.fftfreq(n, d=dx) * 2 * np.pi
+    KX, KZ = np.meshgrid(k, k)
+    filt = np.exp(-(KX ** 2 + KZ ** 2) * corr_mm ** 2 / 4.0)
+    G = np.real(np.fft.ifft2(np.fft.fft2(w) * filt))
+    G = (G - G.mean()) / (G.std() + 1e-30)
+    return (mean * np.exp(sigma * G - 0.5 * sigma * sigma)).astype(np.float32)
+
+
+def top_line_source(nx: int, dx: float) -> dict:
+    return dict(kind=LINE, x0=0.0, z0=0.0, x1=nx * dx, z1=0.0, dir_x=0.0, dir_z=1.0, power=1.0)
+
+
+def edge_line_sources(n: int, dx: float, per_edge: int = 1) -> list:
+    """``per_edge`` equal collimated line sources on each of the four edges, pointing inward."""
+    L = n * dx
+    out = []
+    for k in range(per_edge):
+        a, b = k * L / per_edge, (k + 1) * L / per_edge
+        out.append(dict(kind=LINE, x0=a, z0=0.0, x1=b, z1=0.0, dir_x=0.0, dir_z=1.0, power=1.0))   # top, +z
+        out.append(dict(kind=LINE, x0=a, z0=L, x1=b, z1=L, dir_x=0.0, dir_z=-1.0, power=1.0))     # bottom, -z
+        out.append(dict(kind=LINE, x0=0.0, z0=a, x1=0.0, z1=b, dir_x=1.0, dir_z=0.0, power=1.0))   # left, +x
+        out.append(dict(kind=LINE, x0=L, z0=a, x1=L, z1=b, dir_x=-1.0, dir_z=0.0, power=1.0))     # right, -x
+    return out
+
+
+def pencil32() -> Workload:
+    n, dx = 32, 0.25
+    mua = np.full((n, n), 0.01, np.float32)
+    mus = np.full((n, n), 5.0, np.float32)
+    src = dict(kind=PENCIL, x0=n * dx / 2, z0=0.0, dir_x=0.0, dir_z=1.0, power=1.0)
+    return Workload("pencil32", n, n, dx, 0.8, 8, 100_000, mua, mus, [src], seed=0)
+
+
+def grad256(n_packets: int = 10_000_000) -> Workload:
+    n, dx = 256, 0.05
+    mua_t, mus_t = inclusion_phantom(n, dx, 3, seed=1)
+    mua = np.full((n, n), 0.01, np.float32)   # starting estimate: the background
+    mus = np.full((n, n), 10.0, np.float32)
+    return Workload("grad256", n, n, dx, 0.9, 32, n_packets, mua, mus, [top_line_source(n, dx)],
+                    mua_true=mua_t, mus_true=mus_t, seed=0, meta=dict(hmeas_seed=1001))
+
+
+def large1024(n_packets: int = 1_000_000_000) -> Workload:
+    n, dx = 1024, 0.02
+    mua_t, mus_t = inclusion_phantom(n, dx, 8, seed=5, radius=(0.5, 2.5))
+    mua = np.full((n, n), 0.01, np.float32)
+    mus = np.full((n, n), 10.0, np.float32)
+    return Workload("large1024", n, n, dx, 0.9, 64, n_packets, mua, mus, edge_line_sources(n, dx),
+                    mua_true=mua_t, mus_true=mus_t, seed=0, meta=dict(hmeas_seed=1001))
+
+
+def small_hetero(nz: int, nx: int, dx: float, seed: int):
+    """Heterogeneous test medium: smooth background plus two rectangles (parity tests)."""
+    rng = np.random.default_rng(seed)
+    c_x = (np.arange(nx) + 0.5) * dx
+    c_z = (np.arange(nz) + 0.5) * dx
+    X, Z = np.meshgrid(c_x, c_z)
+    mua = 0.05 + 0.04 * np.sin(X * 2.1 + rng.uniform(0, 6)) * np.cos(Z * 1.3)
+    mus = 6.0 + 3.0 * np.cos(X * 1.7 - Z * 0.9 + rng.uniform(0, 6))
+    i0, j0 = nz // 4, nx // 5
+    mua[i0:i0 + nz // 3, j0:j0 + nx // 4] = 0.3
+    mus[nz // 2:nz // 2 + nz // 4, nx // 2:nx // 2 + nx // 3] = 15.0
+    return mua.astype(np.float32), mus.astype(np.float32)

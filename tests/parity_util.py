@@ -1,0 +1,42 @@
+"""Shared helpers of the GPU-vs-oracle parity tests (tolerances are stated here once).
+
+Parity is per seed on identical Philox streams: the CUDA path (FP32 arithmetic, 64-bit
+fixed-point tallies) and the FP64 oracle run the same packets.  Their difference is the FP32
+rounding of each packet's deposits and positions (continuous, ~1e-6 of a packet's contribution)
+plus the rare packet whose threshold/roulette or boundary decision flips under rounding.  Hence
+(reading of the stated 1e-4 tolerance):
+
+ (i)   per channel, sum_i |G - O| <= REL * sum_i A_i          (relative L1 over the field)
+ (ii)  per pixel with A_i >= 1e-3 max A:  |G - O| <= REL * A_i
+ (iii) elsewhere |G - O| <= 3 sigma_i + REL * A_i
+
+where A_i is the pixel's absolute tally (a_0 of the same packets with |W|; for forward runs
+a_0 itself, since |a_n|, |b_n| <= a_0 per packet) and sigma_i the oracle's standard error of a_0.
+"""
+import numpy as np
+
+REL = 1e-4
+
+
+def f32(v):
+    return float(np.float32(v))
+
+
+def assert_parity(G, O, A, sigma, rel=REL, label=""):
+    G = np.asarray(G, np.float64)
+    O = np.asarray(O, np.float64)
+    A = np.abs(np.asarray(A, np.float64))
+    assert G.shape == O.shape, (G.shape, O.shape)
+    d = np.abs(G - O)
+    tot = A.sum()
+    for c in range(G.shape[0]):
+        l1 = d[c].sum() / tot
+        assert l1 <= rel, f"{label} channel {c}: relative L1 {l1:.3e} > {rel}"
+    hi = A >= 1e-3 * A.max()
+    worst = float(np.max(d[:, hi] / A[hi])) if hi.any() else 0.0
+    assert worst <= rel, f"{label}: per-pixel relative error {worst:.3e} > {rel}"
+    lo = ~hi
+    if lo.any():
+        bound = 3 * sigma[lo] + rel * A[lo] + 1e-30
+        assert np.all(d[:, lo] <= bound), f"{label}: low-count pixels beyond 3 sigma"
+    return dict(max_rel=worst, l1=float(d.sum(axis=(1, 2)).max() / tot))

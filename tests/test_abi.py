@@ -1,0 +1,103 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports every symbol that
+include/mcr.h declares, and rejects bad arguments on the host before touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1608_05238_gb300 import _build, mcr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(mc_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return mcr.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_symbols()
+    for n in ("mc_forward", "mc_adjoint", "mc_gradient", "mc_h_eps", "mc_adjoint_source"):
+        assert n in names
+    assert set(names) == set(mcr.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in _declared_symbols():
+        assert hasattr(lib, n), n
+
+
+def test_status_strings_and_version(lib):
+    assert mcr.status_string(0) == "ok"
+    assert "argument" in mcr.status_string(mcr.ERR_ARG)
+    assert "sm_103a" in mcr.version()
+    assert mcr.status_string(12345) == "unknown status"
+
+
+def _medium(nx=4, nz=3, dx=0.1, g=0.5, mua=1, mus=1):
+    # non-null dummy pointers: only the host-side checks run before any CUDA call
+    return mcr._Medium(nx, nz, dx, g, mua, mus)
+
+
+@pytest.mark.parametrize("kw", [dict(nx=0), dict(nz=-1), dict(dx=0.0), dict(dx=float("nan")), dict(g=1.0),
+                                dict(g=-1.5), dict(mua=None), dict(mus=None)])
+def test_bad_medium_rejected_on_host(lib, kw):
+    m = _medium(**kw)
+    src = mcr._Source(mcr.PENCIL, 0.1, 0.0, 0, 0, 0.0, 1.0, 1.0)
+    run = mcr.Run(K=2, n_packets=10).c()
+    assert lib.mc_forward(C.byref(m), C.byref(src), C.byref(run), C.c_void_p(8), None, None) == mcr.ERR_ARG
+    assert lib.mc_gradient(C.byref(m), 2, C.c_void_p(8), C.c_void_p(8), C.c_void_p(8), C.c_void_p(8), None,
+                           None) == mcr.ERR_ARG
+
+
+@pytest.mark.parametrize("kw", [dict(K=-1), dict(K=mcr.MAX_K + 1), dict(roulette_p=0.0), dict(roulette_p=1.5),
+                                dict(w_threshold=-1.0), dict(first_packet=2 ** 64 - 5, n_packets=10)])
+def test_bad_run_rejected_on_host(lib, kw):
+    args = dict(K=2, n_packets=10)
+    args.update(kw)
+    run = mcr.Run(**args).c()
+    m = _medium()
+    src = mcr._Source(mcr.PENCIL, 0.1, 0.0, 0, 0, 0.0, 1.0, 1.0)
+    assert lib.mc_forward(C.byref(m), C.byref(src), C.byref(run), C.c_void_p(8), None, None) == mcr.ERR_ARG
+    assert lib.mc_adjoint(C.byref(m), C.c_void_p(8), C.byref(run), C.c_void_p(8), None, None) == mcr.ERR_ARG
+
+
+@pytest.mark.parametrize("src", [dict(kind=7), dict(kind=mcr.PENCIL, dir_x=0.0, dir_z=0.0),
+                                 dict(kind=mcr.LINE, x0=float("inf")), dict(kind=mcr.ISO_POINT, power=float("nan"))])
+def test_bad_source_rejected_on_host(lib, src):
+    s = mcr.Source(**src).c()
+    run = mcr.Run(K=1, n_packets=10).c()
+    assert lib.mc_forward(C.byref(_medium()), C.byref(s), C.byref(run), C.c_void_p(8), None, None) == mcr.ERR_ARG
+
+
+def test_null_outputs_rejected_on_host(lib):
+    run = mcr.Run(K=1, n_packets=10).c()
+    src = mcr._Source(mcr.PENCIL, 0.1, 0.0, 0, 0, 0.0, 1.0, 1.0)
+    m = _medium()
+    assert lib.mc_forward(C.byref(m), C.byref(src), C.byref(run), None, None, None) == mcr.ERR_ARG
+    assert lib.mc_forward(C.byref(m), None, C.byref(run), C.c_void_p(8), None, None) == mcr.ERR_ARG
+    assert lib.mc_adjoint(C.byref(m), None, C.byref(run), C.c_void_p(8), None, None) == mcr.ERR_ARG
+    assert lib.mc_h_eps(C.byref(m), None, None, None, None, None, None) == mcr.ERR_ARG
+    # eps requested without H^meas
+    assert lib.mc_h_eps(C.byref(m), C.c_void_p(8), None, None, None, C.c_void_p(8), None) == mcr.ERR_ARG
+    assert lib.mc_adjoint_source(C.byref(m), None, C.c_void_p(8), None) == mcr.ERR_ARG
+    assert lib.mc_gradient(C.byref(m), 1, C.c_void_p(8), C.c_void_p(8), C.c_void_p(8), None, None, None) == mcr.ERR_ARG
+
+
+def test_binding_refuses_cpu_tensors(lib):
+    import torch
+    med = mcr.Medium(torch.zeros(3, 4), torch.zeros(3, 4), 0.1, 0.5)
+    with pytest.raises(TypeError):
+        mcr.forward(med, mcr.Source(mcr.PENCIL, x0=0.2), mcr.Run(K=1, n_packets=10))

@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on identical streams.
+
+Sizes are ones the oracle finishes in seconds, spanning many warps' worth of packets and a
+ragged tail (packet counts that are not multiples of 32), on square and non-square grids, for
+every deposit width (K = 8, 16, 32, 64 -> 1, 2, 3, 5 warp passes per pixel).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import RunParams
+from oracle import functionals as F
+from paper_1608_05238_gb300 import _build, mcr, workloads
+from parity_util import assert_parity, f32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    _build.build()
+    mcr.load()
+    yield
+    torch.cuda.synchronize()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def _gpu_forward(mua, mus, dx, g, src, run, stats=False):
+    med = mcr.Medium(_dev(mua), _dev(mus), dx, g)
+    out = mcr.forward(med, mcr.Source(**src), run, stats=stats)
+    if stats:
+        c, st = out
+        return c.double().cpu().numpy(), st
+    return out.double().cpu().numpy()
+
+
+def _orc_run(run: mcr.Run) -> RunParams:
+    return RunParams(K=run.K, n_packets=run.n_packets, seed=run.seed, stream_id=run.stream_id,
+                     first_packet=run.first_packet, max_scatter=run.max_scatter, max_events=run.max_events,
+                     w_threshold=run.w_threshold, roulette_p=run.roulette_p)
+
+
+def _src32(src):
+    return {k: (f32(v) if isinstance(v, float) else v) for k, v in src.items()}
+
+
+def _forward_case(mua, mus, dx, g, src, run, label):
+    dx, g = f32(dx), f32(g)
+    src = _src32(src)
+    G, st = _gpu_forward(mua, mus, dx, g, src, run, stats=True)
+    O = oracle.forward(mua.astype(np.float64), mus.astype(np.float64), dx, g, src, _orc_run(run),
+                       with_variance=True)
+    info = assert_parity(G, O.coeff, O.coeff[0], np.sqrt(O.a0_var), label=label)
+    assert st["launched"] == O.stats["launched"] == run.n_packets
+    return G, O, st, info
+
+
+def test_forward_pencil32_config():
+    """The 32x32 pencil-beam workload in full: K = 8, 1e5 packets, seed 0."""
+    w = workloads.pencil32()
+    run = mcr.Run(K=w.K, n_packets=w.n_packets, seed=w.seed)
+    _forward_case(w.mua, w.mus, w.dx, w.g, w.sources[0], run, "pencil32")
+
+
+def test_forward_line_heterogeneous_K32_ragged():
+    mua, mus = workloads.small_hetero(48, 64, 0.1, seed=3)
+    src = dict(kind=mcr.LINE, x0=0.0, z0=0.0, x1=6.4, z1=0.0, dir_x=0.0, dir_z=1.0, power=1.0)
+    run = mcr.Run(K=32, n_packets=60_001, seed=7)
+    _forward_case(mua, mus, 0.1, 0.9, src, run, "line K32")
+
+
+def test_forward_iso_point_K64_oblique_grid():
+    mua, mus = workloads.small_hetero(30, 41, 0.07, seed=4)
+    src = dict(kind=mcr.ISO_POINT, x0=1.234, z0=0.987, power=2.5)
+    run = mcr.Run(K=64, n_packets=30_017, seed=11, stream_id=3)
+    _forward_case(mua, mus, 0.07, 0.75, src, run, "iso K64")
+
+
+def test_forward_oblique_pencil_K16_roulette():
+    """Oblique pencil, strong absorption and a high threshold so that roulette is exercised."""
+    mua, mus = workloads.small_hetero(33, 35, 0.1, seed=5)
+    mua = mua * 8
+    src = dict(kind=mcr.PENCIL, x0=1.3, z0=0.0, dir_x=0.5, dir_z=0.8, power=1.0)
+    run = mcr.Run(K=16, n_packets=40_000, seed=2, w_threshold=0.05, roulette_p=0.25)
+    G, O, st, _ = _forward_case(mua, mus, 0.1, 0.6, src, run, "pencil K16 roulette")
+    assert O.stats["rr_kill"] > 1000 and st["rr_kill"] > 1000
+    assert abs(st["rr_kill"] - O.stats["rr_kill"]) <= 0.002 * O.stats["rr_kill"] + 5
+
+
+def _adjoint_case(mua, mus, dx, g, q, run, label):
+    dx, g = f32(dx), f32(g)
+    med = mcr.Medium(_dev(mua), _dev(mus), dx, g)
+    G, st = mcr.adjoint(med, _dev(q), run, stats=True)
+    G = G.double().cpu().numpy()
+    O = oracle.adjoint(mua.astype(np.float64), mus.astype(np.float64), dx, g, q, _orc_run(run))
+    # absolute tally: the same packets with |W| (sampling uses |q*|, so the paths are identical)
+    Oabs = oracle.adjoint(mua.astype(np.float64), mus.astype(np.float64), dx, g, np.abs(q), _orc_run(run),
+                          with_variance=True)
+    info = assert_parity(G, O.coeff, Oabs.coeff[0], np.sqrt(Oabs.a0_var), label=label)
+    assert st["launched"] == run.n_packets
+    assert abs(st["launched_w"] - O.stats["launched_w"]) == 0
+    return G, O, st, info
+
+
+def test_adjoint_signed_source_K16():
+    mua, mus = workloads.small_hetero(40, 48, 0.08, seed=6)
+    rng = np.random.default_rng(3)
+    q = (rng.normal(size=mua.shape) * (rng.uniform(size=mua.shape) < 0.3)).astype(np.float32)
+    run = mcr.Run(K=16, n_packets=50_003, seed=21, stream_id=1)
+    _adjoint_case(mua, mus, 0.08, 0.8, q, run, "adjoint K16")
+
+
+def test_adjoint_single_pixel_source_K8():
+    mua, mus = workloads.small_hetero(24, 24, 0.1, seed=8)
+    q = np.zeros(mua.shape, np.float32)
+    q[5, 17] = -3.0
+    run = mcr.Run(K=8, n_packets=40_000, seed=5)
+    _adjoint_case(mua, mus, 0.1, 0.9, q, run, "adjoint point")
+
+
+def test_gradient_h_eps_and_adjoint_source_parity():
+    """mc_gradient / mc_h_eps / mc_adjoint_source vs the oracle functionals on the SAME inputs."""
+    rng = np.random.default_rng(9)
+    K, nz, nx, dx, g = 12, 37, 29, f32(0.05), f32(0.9)
+    c = rng.normal(size=(2 * K + 1, nz, nx)).astype(np.float32)
+    cs = rng.normal(size=(2 * K + 1, nz, nx)).astype(np.float32)
+    c[0] = np.abs(c[0])
+    mua = rng.uniform(0.01, 0.2, (nz, nx)).astype(np.float32)
+    mus = rng.uniform(5, 20, (nz, nx)).astype(np.float32)
+    Hm = rng.uniform(0, 0.5, (nz, nx)).astype(np.float32)
+    med = mcr.Medium(_dev(mua), _dev(mus), dx, g)
+    H, v, eps = mcr.h_eps(med, _dev(c), _dev(Hm))
+    H = H.cpu().numpy()
+    assert np.array_equal(H, (mua * c[0]).astype(np.float32))  # one FP32 product, exact
+    H64 = H.astype(np.float64)
+    assert abs(eps.item() - F.error_functional(Hm.astype(np.float64), H64, dx)) < 1e-12 * eps.item()
+    v = v.cpu().numpy()
+    assert np.allclose(v, F.dL_dH_eps(Hm, H64, dx), rtol=1e-6, atol=0)
+    q = mcr.adjoint_source(med, _dev(v)).cpu().numpy()
+    assert np.allclose(q, F.adjoint_source(mua, v, dx), rtol=1e-6, atol=0)
+    d_mua, d_mus = mcr.gradient(med, _dev(c), _dev(cs), _dev(v))
+    ra, rs = F.dL_dmu(c.astype(np.float64), cs.astype(np.float64), v.astype(np.float64), dx, g)
+    assert np.allclose(d_mua.cpu().numpy(), ra, rtol=1e-12, atol=1e-15 * np.abs(ra).max())
+    assert np.allclose(d_mus.cpu().numpy(), rs, rtol=1e-12, atol=1e-15 * np.abs(rs).max())
+
+
+def test_beer_lambert_closed_form_gpu():
+    """mu_s = 0: one ray per packet; the GPU tally equals the Beer-Lambert closed form."""
+    import test_oracle_pins as pins
+    rng = np.random.default_rng(3)
+    nz, nx, dx = 9, 11, f32(0.3)
+    mua = rng.uniform(0.05, 1.5, (nz, nx)).astype(np.float32)
+    mus = np.zeros((nz, nx), np.float32)
+    th = math.radians(23.0)
+    sx, sz = f32(math.sin(th)), f32(math.cos(th))
+    x0 = f32(1.73)
+    K = 5
+    G = _gpu_forward(mua, mus, dx, 0.5, dict(kind=mcr.PENCIL, x0=x0, z0=0.0, dir_x=sx, dir_z=sz),
+                     mcr.Run(K=K, n_packets=777))
+    nrm = math.hypot(sx, sz)
+    sx, sz = sx / nrm, sz / nrm
+    exp = np.zeros_like(G)
+    W = 1.0
+    for iz, ix, l in pins._chords(x0, 0.0, sx, sz, nx, nz, dx):
+        m = float(mua[iz, ix])
+        exp[0, iz, ix] += W * (1 - math.exp(-m * l)) / m / (dx * dx)
+        W *= math.exp(-m * l)
+    th = math.atan2(sx, sz)
+    for n in range(1, K + 1):
+        exp[2 * n - 1] = exp[0] * math.cos(n * th)
+        exp[2 * n] = exp[0] * math.sin(n * th)
+    assert np.max(np.abs(G - exp)) <= 2e-5 * np.max(exp[0])
+
+
+def test_energy_bookkeeping_gpu():
+    """absorbed weight from the tally (sum mu_a a_0 A N_p) equals launched + roulette - escaped - killed."""
+    mua, mus = workloads.small_hetero(40, 40, 0.1, seed=12)
+    src = dict(kind=mcr.LINE, x0=0.0, z0=0.0, x1=4.0, z1=0.0, dir_x=0.0, dir_z=1.0, power=1.0)
+    run = mcr.Run(K=4, n_packets=500_000, seed=3, w_threshold=0.02, roulette_p=0.3, max_scatter=200)
+    G, st = _gpu_forward(mua * 5, mus, 0.1, 0.8, src, run, stats=True)
+    absorbed_tally = float(np.sum((mua * 5).astype(np.float64) * G[0])) * f32(0.1) ** 2 * run.n_packets
+    assert st["rr_kill"] > 0 and st["scatter_limit"] > 0
+    assert abs(absorbed_tally - st["absorbed_w"]) <= 1e-5 * st["launched_w"]
+
+
+def test_bit_reproducible_and_packet_ranges_add_up():
+    mua, mus = workloads.small_hetero(32, 32, 0.1, seed=13)
+    src = dict(kind=mcr.LINE, x0=0.0, z0=0.0, x1=3.2, z1=0.0, dir_x=0.0, dir_z=1.0, power=1.0)
+    a = _gpu_forward(mua, mus, 0.1, 0.9, src, mcr.Run(K=8, n_packets=100_000, seed=4))
+    b = _gpu_forward(mua, mus, 0.1, 0.9, src, mcr.Run(K=8, n_packets=100_000, seed=4))
+    assert np.array_equal(a, b)
+    h1 = _gpu_forward(mua, mus, 0.1, 0.9, src, mcr.Run(K=8, n_packets=37_000, seed=4))
+    h2 = _gpu_forward(mua, mus, 0.1, 0.9, src, mcr.Run(K=8, n_packets=63_000, seed=4, first_packet=37_000))
+    comb = (h1 * 37_000 + h2 * 63_000) / 100_000
+    assert np.allclose(comb, a, rtol=2e-6, atol=2e-7 * np.abs(a).max())
+
+
+def test_edge_cases():
+    dev = torch.device("cuda")
+    # zero packets -> zeros; K = 0; a 1-pixel-wide grid
+    mua, mus = np.full((7, 1), 0.1, np.float32), np.full((7, 1), 2.0, np.float32)
+    src = dict(kind=mcr.PENCIL, x0=0.05, z0=0.0, dir_x=0.0, dir_z=1.0, power=1.0)
+    z = _gpu_forward(mua, mus, 0.1, 0.5, src, mcr.Run(K=0, n_packets=0))
+    assert z.shape == (1, 7, 1) and np.all(z == 0)
+    G = _gpu_forward(mua, mus, 0.1, 0.5, src, mcr.Run(K=3, n_packets=20_000, seed=1))
+    O = oracle.forward(mua.astype(np.float64), mus.astype(np.float64), f32(0.1), 0.5, _src32(src),
+                       RunParams(K=3, n_packets=20_000, seed=1), with_variance=True)
+    assert_parity(G, O.coeff, O.coeff[0], np.sqrt(O.a0_var), label="1-wide")
+    # all-zero adjoint source -> zeros
+    med = mcr.Medium(_dev(mua), _dev(mus), 0.1, 0.5)
+    za = mcr.adjoint(med, torch.zeros((7, 1), device=dev), mcr.Run(K=2, n_packets=1000))
+    assert torch.count_nonzero(za) == 0
+    # a source outside the domain escapes at once
+    Ge, st = _gpu_forward(mua, mus, 0.1, 0.5, dict(kind=mcr.PENCIL, x0=5.0, z0=0.0), mcr.Run(K=1, n_packets=64),
+                          stats=True)
+    assert st["escapes"] == 64 and np.all(Ge == 0)
+
+
+def test_device_errors_are_reported():
+    mua, mus = np.full((8, 8), 0.001, np.float32), np.full((8, 8), 50.0, np.float32)
+    src = dict(kind=mcr.ISO_POINT, x0=0.4, z0=0.4, power=1.0)
+    with pytest.raises(mcr.McrError) as e:
+        _gpu_forward(mua, mus, 0.1, 0.0, src, mcr.Run(K=1, n_packets=100, max_events=3), stats=True)
+    assert e.value.status == mcr.ERR_EVENT_LIMIT
+    bad = mua.copy()
+    bad[2, 3] = -1.0
+    med = mcr.Medium(_dev(bad), _dev(mus), 0.1, 0.0)
+    mcr.forward(med, mcr.Source(**src), mcr.Run(K=1, n_packets=100))
+    with pytest.raises(mcr.McrError) as e:
+        mcr.check()
+    assert e.value.status == mcr.ERR_MEDIUM
+    mcr.check()  # latched error is cleared once reported
+
+
+def test_chunked_run_matches_closed_form():
+    """More than 2^26 packets (two chunks with an FP64 flush): the mu_s = 0 tally is still exact."""
+    nz, nx, dx = 4, 3, f32(0.2)
+    mua = np.full((nz, nx), 0.5, np.float32)
+    mus = np.zeros((nz, nx), np.float32)
+    src = dict(kind=mcr.LINE, x0=0.0, z0=0.0, x1=f32(0.6), z1=0.0, dir_x=0.0, dir_z=1.0, power=1.0)
+    n = (1 << 26) + 12345
+    G = _gpu_forward(mua, mus, dx, 0.0, src, mcr.Run(K=1, n_packets=n, seed=3))
+    col = np.array([(1 - math.exp(-0.5 * dx)) / 0.5 * math.exp(-0.5 * dx * k) for k in range(nz)]) / (dx * dx)
+    frac = G[0] / col[:, None]  # each column receives ~1/3 of the packets
+    assert np.allclose(frac.sum(axis=1), 1.0, rtol=1e-5)
+    assert np.allclose(frac, 1 / 3, atol=5e-4)
