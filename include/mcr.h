@@ -98,8 +98,10 @@ typedef struct {
  * and roulette below the weight threshold, and tallies each segment's track weight
  * t = W (1 - exp(-mu_a l)) / mu_a into a_0, a_n = t cos(n theta), b_n = t sin(n theta) of its
  * pixel.  coeff (device, [2K+1][nz][nx] FP32, overwritten) = power * sums / (N_p dx^2).
- * stats (host, may be NULL).  Tallies are 64-bit fixed point (quantum 2^-32 mm): the result
- * does not depend on scheduling and is bit-reproducible for a given run.
+ * stats (host, may be NULL).  Tallies are 64-bit fixed-point sums of deposits rounded to a
+ * quantum 2^-q mm, q chosen per run from dx, w_threshold and roulette_p so that one deposit
+ * spans at most 2^30 quanta: the result does not depend on scheduling and is bit-reproducible
+ * for a given run.
  */
 int mc_forward(const mcr_medium *med, const mcr_source *src, const mcr_run *run, float *coeff,
                mcr_stats *stats, void *stream);

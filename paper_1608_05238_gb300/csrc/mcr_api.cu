@@ -57,7 +57,7 @@ int workspace(int64_t npix, int C, bool chunked, bool volumetric, Workspace **ou
         return MCR_ERR_CUDA;
   }
   if ((rc = grow((void **)&w.tally, &w.tally_bytes, (size_t)npix * Cpad * 8))) return rc;
-  if ((rc = grow((void **)&w.mu, &w.mu_bytes, (size_t)npix * sizeof(float2)))) return rc;
+  if ((rc = grow((void **)&w.mu, &w.mu_bytes, (size_t)npix * sizeof(float4)))) return rc;
   if ((rc = grow((void **)&w.partials, &w.partials_bytes, (size_t)4096 * sizeof(double)))) return rc;
   if (chunked && (rc = grow((void **)&w.acc, &w.acc_bytes, (size_t)npix * C * sizeof(double)))) return rc;
   if (volumetric) {
@@ -171,7 +171,10 @@ int run_mc(const mcr_medium *med, const mcr_source *src, const float *qstar, con
   p.K = run->K;
   p.C = C;
   p.Cpad = Cpad;
-  p.row_stride = Cpad | 1;
+  p.row_stride = Cpad + 2;  // = 2 mod 4 words: conflict-free 8-byte row stores
+  const int qexp = tally_exponent(med->dx, run->w_threshold, run->roulette_p);
+  p.qscale = ldexpf(1.f, qexp);
+  const double quantum = ldexp(1.0, -qexp);
   p.key0 = (unsigned)run->seed;
   p.key1 = (unsigned)(run->seed >> 32) ^ run->stream_id;
   p.max_scatter = run->max_scatter;
@@ -195,14 +198,14 @@ int run_mc(const mcr_medium *med, const mcr_source *src, const float *qstar, con
     p.first_packet = run->first_packet + done;
     p.n_packets = this_n;
     if (this_n) MCR_TRY_CUDA(launch_transport(p, s));
-    if (chunked) MCR_TRY_CUDA(launch_accumulate(w->tally, npix, C, Cpad, w->acc, s));
+    if (chunked) MCR_TRY_CUDA(launch_accumulate(w->tally, npix, C, Cpad, quantum, w->acc, s));
     done += this_n;
   } while (done < n);
   MCR_TRY_CUDA(cudaEventRecord(w->ev_stop[slot], s));
   w->ran[slot] = true;
   const double area = (double)med->dx * (double)med->dx;
   const double fixed_scale = (!volumetric && n) ? (double)src->power / ((double)n * area) : 0.0;
-  MCR_TRY_CUDA(launch_finalize(w->tally, chunked ? w->acc : nullptr, npix, C, Cpad, fixed_scale,
+  MCR_TRY_CUDA(launch_finalize(w->tally, chunked ? w->acc : nullptr, npix, C, Cpad, chunked ? 1.0 : quantum, fixed_scale,
                                volumetric && n > 0, w->qmax_bits(), volumetric ? w->cdf + (npix - 1) : nullptr,
                                (double)(n ? n : 1), volumetric, coeff, w->flags(), s));
   if (stats) {
@@ -242,7 +245,7 @@ int mc_h_eps(const mcr_medium *med, const float *coeff, const float *Hmeas, floa
   std::lock_guard<std::mutex> lock(g_mu);
   Workspace *w = nullptr;
   if ((rc = workspace(npix, 1, false, false, &w))) return rc;
-  MCR_TRY_CUDA(launch_h_eps(med->mua, coeff, Hmeas, npix, med->dx * med->dx, H, dL_dH, w->partials,
+  MCR_TRY_CUDA(launch_h_eps(med->mua, coeff, Hmeas, npix, (double)med->dx * (double)med->dx, H, dL_dH, w->partials,
                             w->partials_bytes / sizeof(double), eps, (cudaStream_t)stream));
   return MCR_OK;
 }
@@ -251,7 +254,7 @@ int mc_adjoint_source(const mcr_medium *med, const float *dL_dH, float *qstar, v
   int rc;
   if ((rc = check_medium(med))) return rc;
   if (!dL_dH || !qstar) return MCR_ERR_ARG;
-  MCR_TRY_CUDA(launch_adjoint_source(med->mua, dL_dH, (int64_t)med->nx * med->nz, med->dx * med->dx, qstar,
+  MCR_TRY_CUDA(launch_adjoint_source(med->mua, dL_dH, (int64_t)med->nx * med->nz, (double)med->dx * (double)med->dx, qstar,
                                      (cudaStream_t)stream));
   return MCR_OK;
 }
@@ -328,3 +331,19 @@ const char *mc_status_string(int status) {
 const char *mc_version(void) { return "mcr 1.0 sm_103a"; }
 
 }  // extern "C"
+
+namespace mcr {
+
+// q such that every deposit |t h| 2^q stays below 2^30 (< 2^31 with margin for |h| rounding):
+// t <= W l with l <= dx sqrt 2 inside one pixel, and |W| <= max(1, w_threshold / p) because the
+// weight only decreases except for roulette survivors, which are below the threshold before.
+int tally_exponent(float dx, float w_threshold, float roulette_p) {
+  const double wmax = fmax(1.0, (double)w_threshold / (double)roulette_p);
+  const double tmax = wmax * (double)dx * 1.41421356237309515 * 1.001;
+  int q = (int)floor(30.0 - log2(tmax));
+  if (q > 60) q = 60;
+  if (q < -60) q = -60;
+  return q;
+}
+
+}  // namespace mcr

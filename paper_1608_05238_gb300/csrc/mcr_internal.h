@@ -8,9 +8,10 @@
 
 namespace mcr {
 
-// Fixed-point quantum of the tallies: 2^-32 (weight x mm).
-constexpr float kFixScale = 4294967296.0f;
-constexpr double kFixInv = 1.0 / 4294967296.0;
+// Fixed-point tallies: each deposit t h (weight x mm) is stored as round(t h 2^q) in 64-bit sums.
+// The run picks q so that |t h| 2^q < 2^31 for every possible deposit (t <= W_max dx sqrt 2),
+// so one 32-bit conversion per coefficient suffices.
+int tally_exponent(float dx, float w_threshold, float roulette_p);
 // Packets per transport launch; longer runs are split into chunks whose fixed-point sums are
 // flushed into an FP64 accumulator in chunk order (keeps |sum| far below 2^63).
 constexpr uint64_t kChunkPackets = 1ull << 26;
@@ -35,7 +36,7 @@ struct TransportParams {
   int nx, nz;
   float dx;
   float hg_c;  // (1 - g) / (1 + g)
-  const float2 *mu;  // packed (mu_a, mu_s) per pixel
+  const float4 *mu;  // packed (mu_a, mu_s, 1/mu_a, 1/mu_s) per pixel
   // source
   int kind;
   float x0, z0, x1, z1, dir_x, dir_z;
@@ -43,6 +44,7 @@ struct TransportParams {
   const float *q;                 // volumetric: signed source (for the packet sign)
   // run
   int K, C, Cpad, row_stride;     // C = 2K+1 channels, Cpad = C rounded up to 4, smem row stride
+  float qscale;                   // 2^q, the fixed-point scale of the deposits
   unsigned long long first_packet, n_packets;
   unsigned key0, key1;
   unsigned max_scatter, max_events;
@@ -61,7 +63,7 @@ struct Workspace {
   size_t tally_bytes = 0;
   double *acc = nullptr;  // FP64 chunk accumulator [C][npix]
   size_t acc_bytes = 0;
-  float2 *mu = nullptr;
+  float4 *mu = nullptr;
   size_t mu_bytes = 0;
   unsigned long long *cdf = nullptr;
   size_t cdf_bytes = 0;
@@ -85,25 +87,26 @@ constexpr size_t kSmallBytes = 512;
 static_assert(sizeof(DevStats) <= 128, "stats slot");
 
 // ---- launchers (each enqueues on `s` and returns the launch error) ----
-cudaError_t launch_pack_medium(const float *mua, const float *mus, float2 *mu, int64_t npix, unsigned *flags,
+cudaError_t launch_pack_medium(const float *mua, const float *mus, float4 *mu, int64_t npix, unsigned *flags,
                                cudaStream_t s);
 cudaError_t launch_transport(const TransportParams &p, cudaStream_t s);
 size_t transport_smem_bytes(int row_stride);
 cudaError_t launch_source_cdf(const float *q, int64_t npix, unsigned long long *cdf,
                               unsigned long long *block_sums, size_t block_sums_cap, unsigned *qmax_bits,
                               cudaStream_t s);
-// accumulate (chunked runs): acc[c][pix] += tally[pix][c] * 2^-32
-cudaError_t launch_accumulate(const unsigned long long *tally, int64_t npix, int C, int Cpad, double *acc,
-                              cudaStream_t s);
-// coeff[c][pix] = sums * scale, sign (-1)^n on channels 2n-1, 2n when `adjoint`.
-// scale = fixed_scale (forward) or 2 pi qmax total 2^-32 / N_p (volumetric: read on device).
+// accumulate (chunked runs): acc[c][pix] += tally[pix][c] * quantum   (quantum = 2^-q)
+cudaError_t launch_accumulate(const unsigned long long *tally, int64_t npix, int C, int Cpad, double quantum,
+                              double *acc, cudaStream_t s);
+// coeff[c][pix] = sums * scale, sign (-1)^n on channels 2n-1, 2n when `adjoint`; the fixed-point
+// sums are multiplied by `quantum` (2^-q) first.  scale = fixed_scale (forward) or
+// 2 pi qmax total 2^-32 / N_p (volumetric: read on device).
 cudaError_t launch_finalize(const unsigned long long *tally, const double *acc, int64_t npix, int C, int Cpad,
-                            double fixed_scale, bool volumetric, const unsigned *qmax_bits,
+                            double quantum, double fixed_scale, bool volumetric, const unsigned *qmax_bits,
                             const unsigned long long *cdf_total, double n_packets, bool adjoint, float *coeff,
                             unsigned *flags, cudaStream_t s);
-cudaError_t launch_h_eps(const float *mua, const float *a0, const float *Hmeas, int64_t npix, float area, float *H,
+cudaError_t launch_h_eps(const float *mua, const float *a0, const float *Hmeas, int64_t npix, double area, float *H,
                          float *dL_dH, double *partials, size_t partials_cap, double *eps, cudaStream_t s);
-cudaError_t launch_adjoint_source(const float *mua, const float *dL_dH, int64_t npix, float area, float *q,
+cudaError_t launch_adjoint_source(const float *mua, const float *dL_dH, int64_t npix, double area, float *q,
                                   cudaStream_t s);
 cudaError_t launch_gradient(const float *coeff, const float *coeff_adj, const float *dL_dH, int64_t npix, int K,
                             double g, double area, double *d_mua, double *d_mus, cudaStream_t s);

@@ -11,13 +11,14 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__global__ void k_pack_medium(const float *__restrict__ mua, const float *__restrict__ mus, float2 *__restrict__ mu,
+// (mu_a, mu_s, 1/mu_a, 1/mu_s) per pixel, one 16-byte load per segment; 1/0 = +inf
+__global__ void k_pack_medium(const float *__restrict__ mua, const float *__restrict__ mus, float4 *__restrict__ mu,
                               int64_t npix, unsigned *flags) {
   bool bad = false;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
     const float a = mua[i], s = mus[i];
     bad |= !(a >= 0.f && a < CUDART_INF_F) || !(s >= 0.f && s < CUDART_INF_F);
-    mu[i] = make_float2(a, s);
+    mu[i] = make_float4(a, s, 1.f / a, 1.f / s);
   }
   if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagMedium);
 }
@@ -87,13 +88,13 @@ __global__ void k_cdf_add(unsigned long long *__restrict__ cdf, int64_t npix,
   if (i < npix) cdf[i] += block_sums[blockIdx.x];
 }
 
-// acc[c][pix] += tally[pix][c] 2^-32 ; the tally tile of 32 pixels is read contiguously.
+// acc[c][pix] += tally[pix][c] * quantum ; the tally tile of 32 pixels is read contiguously.
 __global__ void k_accumulate(const unsigned long long *__restrict__ tally, int64_t npix, int C, int Cpad,
-                             double *__restrict__ acc) {
+                             double quantum, double *__restrict__ acc) {
   const int64_t p0 = (int64_t)blockIdx.x * 32;
   for (int c = threadIdx.y; c < C; c += blockDim.y) {
     const int64_t pix = p0 + threadIdx.x;
-    if (pix < npix) acc[(int64_t)c * npix + pix] += (double)(long long)tally[pix * Cpad + c] * kFixInv;
+    if (pix < npix) acc[(int64_t)c * npix + pix] += (double)(long long)tally[pix * Cpad + c] * quantum;
   }
 }
 
@@ -101,16 +102,16 @@ __global__ void k_accumulate(const unsigned long long *__restrict__ tally, int64
 // One block = 32 pixels: the tile [32][Cpad] is staged through shared memory so that both the
 // read (contiguous rows) and the write (32 pixels per channel) are coalesced.
 __global__ void k_finalize(const unsigned long long *__restrict__ tally, const double *__restrict__ acc,
-                           int64_t npix, int C, int Cpad, double fixed_scale, int volumetric,
+                           int64_t npix, int C, int Cpad, double quantum, double fixed_scale, int volumetric,
                            const unsigned *qmax_bits, const unsigned long long *cdf_total, double n_packets,
                            int adjoint, float *__restrict__ coeff, unsigned *flags) {
   extern __shared__ long long tile[];  // [32][Cpad]
   const int64_t p0 = (int64_t)blockIdx.x * 32;
   const int npx = npix - p0 < 32 ? (int)(npix - p0) : 32;
   double scale = fixed_scale;
-  // volumetric: S / (N_p A) with S = 2 pi A qmax total 2^-32
-  if (volumetric) scale = 2.0 * CUDART_PI * (double)__uint_as_float(*qmax_bits) * (double)(*cdf_total) * kFixInv /
-                          n_packets;
+  // volumetric: S / (N_p A) with S = 2 pi A qmax total 2^-32 (the source CDF has 2^32 levels of qmax)
+  if (volumetric) scale = 2.0 * CUDART_PI * (double)__uint_as_float(*qmax_bits) * (double)(*cdf_total) *
+                          (1.0 / 4294967296.0) / n_packets;
   const int tid = threadIdx.y * 32 + threadIdx.x, nthr = blockDim.x * blockDim.y;
   bool near_overflow = false;
   if (!acc) {
@@ -131,7 +132,7 @@ __global__ void k_finalize(const unsigned long long *__restrict__ tally, const d
       if (acc)
         v = acc[(int64_t)c * npix + pix] * scale;
       else
-        v = (double)tile[threadIdx.x * Cpad + c] * kFixInv * scale;
+        v = (double)tile[threadIdx.x * Cpad + c] * quantum * scale;
       coeff[(int64_t)c * npix + pix] = (float)(sgn * v);
     }
   }
@@ -140,7 +141,7 @@ __global__ void k_finalize(const unsigned long long *__restrict__ tally, const d
 
 // H = mu_a a_0 ; r = H^meas - H ; dL/dH = -A r ; per-block FP64 partial sums of r^2.
 __global__ void k_h_eps(const float *__restrict__ mua, const float *__restrict__ a0, const float *__restrict__ Hmeas,
-                        int64_t npix, float area, float *__restrict__ H, float *__restrict__ dL_dH,
+                        int64_t npix, double area, float *__restrict__ H, float *__restrict__ dL_dH,
                         double *__restrict__ partials) {
   __shared__ double red[kThreads / 32];
   double acc = 0.0;
@@ -148,9 +149,9 @@ __global__ void k_h_eps(const float *__restrict__ mua, const float *__restrict__
     const float h = mua[i] * a0[i];
     if (H) H[i] = h;
     if (Hmeas) {
-      const float r = Hmeas[i] - h;
-      if (dL_dH) dL_dH[i] = -area * r;
-      acc += (double)r * (double)r;
+      const double r = (double)Hmeas[i] - (double)h;  // residual and its square in FP64
+      if (dL_dH) dL_dH[i] = (float)(-area * r);
+      acc += r * r;
     }
   }
   if (!partials) return;
@@ -173,9 +174,9 @@ __global__ void k_eps_final(const double *__restrict__ partials, int n, double h
 }
 
 __global__ void k_adjoint_source(const float *__restrict__ mua, const float *__restrict__ dL_dH, int64_t npix,
-                                 float inv_area, float *__restrict__ q) {
+                                 double area, float *__restrict__ q) {
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < npix; i += (int64_t)gridDim.x * kThreads)
-    q[i] = -mua[i] * dL_dH[i] * inv_area;
+    q[i] = (float)(-(double)mua[i] * (double)dL_dH[i] / area);
 }
 
 // Per pixel, FP64: G_a = a0 a0*/(2pi) + (1/pi) sum (a_n a_n* + b_n b_n*)      (Eq. 22)
@@ -210,7 +211,7 @@ int grid_for(int64_t n, int threads) {
 
 }  // namespace
 
-cudaError_t launch_pack_medium(const float *mua, const float *mus, float2 *mu, int64_t npix, unsigned *flags,
+cudaError_t launch_pack_medium(const float *mua, const float *mus, float4 *mu, int64_t npix, unsigned *flags,
                                cudaStream_t s) {
   k_pack_medium<<<grid_for(npix, kThreads), kThreads, 0, s>>>(mua, mus, mu, npix, flags);
   return cudaGetLastError();
@@ -229,37 +230,37 @@ cudaError_t launch_source_cdf(const float *q, int64_t npix, unsigned long long *
   return cudaGetLastError();
 }
 
-cudaError_t launch_accumulate(const unsigned long long *tally, int64_t npix, int C, int Cpad, double *acc,
-                              cudaStream_t s) {
+cudaError_t launch_accumulate(const unsigned long long *tally, int64_t npix, int C, int Cpad, double quantum,
+                              double *acc, cudaStream_t s) {
   const dim3 block(32, 8);
-  k_accumulate<<<(unsigned)((npix + 31) / 32), block, 0, s>>>(tally, npix, C, Cpad, acc);
+  k_accumulate<<<(unsigned)((npix + 31) / 32), block, 0, s>>>(tally, npix, C, Cpad, quantum, acc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const unsigned long long *tally, const double *acc, int64_t npix, int C, int Cpad,
-                            double fixed_scale, bool volumetric, const unsigned *qmax_bits,
+                            double quantum, double fixed_scale, bool volumetric, const unsigned *qmax_bits,
                             const unsigned long long *cdf_total, double n_packets, bool adjoint, float *coeff,
                             unsigned *flags, cudaStream_t s) {
   const dim3 block(32, 8);
   const size_t smem = acc ? 0 : (size_t)32 * Cpad * sizeof(long long);
-  k_finalize<<<(unsigned)((npix + 31) / 32), block, smem, s>>>(tally, acc, npix, C, Cpad, fixed_scale,
+  k_finalize<<<(unsigned)((npix + 31) / 32), block, smem, s>>>(tally, acc, npix, C, Cpad, quantum, fixed_scale,
                                                               volumetric ? 1 : 0, qmax_bits, cdf_total, n_packets,
                                                               adjoint ? 1 : 0, coeff, flags);
   return cudaGetLastError();
 }
 
-cudaError_t launch_h_eps(const float *mua, const float *a0, const float *Hmeas, int64_t npix, float area, float *H,
+cudaError_t launch_h_eps(const float *mua, const float *a0, const float *Hmeas, int64_t npix, double area, float *H,
                          float *dL_dH, double *partials, size_t partials_cap, double *eps, cudaStream_t s) {
   int grid = grid_for(npix, kThreads);
   if ((size_t)grid > partials_cap) grid = (int)partials_cap;
   k_h_eps<<<grid, kThreads, 0, s>>>(mua, a0, Hmeas, npix, area, H, dL_dH, (Hmeas && eps) ? partials : nullptr);
-  if (Hmeas && eps) k_eps_final<<<1, 1, 0, s>>>(partials, grid, 0.5 * (double)area, eps);
+  if (Hmeas && eps) k_eps_final<<<1, 1, 0, s>>>(partials, grid, 0.5 * area, eps);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_source(const float *mua, const float *dL_dH, int64_t npix, float area, float *q,
+cudaError_t launch_adjoint_source(const float *mua, const float *dL_dH, int64_t npix, double area, float *q,
                                   cudaStream_t s) {
-  k_adjoint_source<<<grid_for(npix, kThreads), kThreads, 0, s>>>(mua, dL_dH, npix, 1.f / area, q);
+  k_adjoint_source<<<grid_for(npix, kThreads), kThreads, 0, s>>>(mua, dL_dH, npix, area, q);
   return cudaGetLastError();
 }
 

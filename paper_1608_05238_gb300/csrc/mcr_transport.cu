@@ -97,21 +97,19 @@ __global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
            n_evl = 0;
   double w_launch = 0.0, w_esc = 0.0, w_rr = 0.0, w_kill = 0.0;
 
-  // harmonic row of the current flight direction: h_n = (s_z + i s_x)^n
+  // harmonic row of the current flight direction, h_n = (s_z + i s_x)^n, stored one slot to the
+  // right (my[1 + c] holds channel c) so that each (cos n theta, sin n theta) pair is one
+  // 8-byte aligned store; the row stride is 2 mod 4 words, so these stores are conflict-free.
   auto write_row = [&]() {
-    my[0] = 1.f;
+    my[1] = 1.f;
     float c = sz, s = sx;
-    if (K >= 1) {
-      my[1] = c;
-      my[2] = s;
-    }
-    for (int n = 2; n <= K; ++n) {
+    float2 *pairs = reinterpret_cast<float2 *>(my);
+    for (int n = 1; n <= K; ++n) {
+      pairs[n] = make_float2(c, s);
       const float cn = fmaf(c, sz, -s * sx);
       const float sn = fmaf(s, sz, c * sx);
       c = cn;
       s = sn;
-      my[2 * n - 1] = c;
-      my[2 * n] = s;
     }
   };
   // start free flight number `flight` (event flight+1): tau = -ln U, keep U for scatter/roulette
@@ -120,8 +118,8 @@ __global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
     tau = -logf(u01(r.x));
     cu1 = r.y;
     cu2 = r.z;
-    inv_ax = 1.f / fabsf(sx);
-    inv_az = 1.f / fabsf(sz);
+    inv_ax = __frcp_rn(fabsf(sx));
+    inv_az = __frcp_rn(fabsf(sz));
     ++n_flight;
     write_row();
   };
@@ -201,17 +199,17 @@ __global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
     bool collided = false, escaped = false;
     if (alive) {
       const int pix = iz * nx + ix;
-      const float2 m = __ldg(p.mu + pix);  // (mu_a, mu_s)
+      const float4 m = __ldg(p.mu + pix);  // (mu_a, mu_s, 1/mu_a, 1/mu_s)
       float dist_x = CUDART_INF_F, dist_z = CUDART_INF_F;
       if (sx != 0.f) dist_x = fmaxf((sx > 0.f ? dx - fx : fx) * inv_ax, 0.f);
       if (sz != 0.f) dist_z = fmaxf((sz > 0.f ? dx - fz : fz) * inv_az, 0.f);
       const float d_edge = fminf(dist_x, dist_z);
-      const float d_coll = tau / m.y;  // +inf when mu_s = 0
+      const float d_coll = tau * m.w;  // +inf when mu_s = 0 (tau > 0)
       collided = d_coll < d_edge;
       const float l = collided ? d_coll : d_edge;
       // track weight of the segment: W (1 - e^{-mu_a l}) / mu_a, then W <- W e^{-mu_a l}
       const float em1 = expm1f(-m.x * l);
-      const float t = m.x > 0.f ? (-W * em1) / m.x : W * l;
+      const float t = m.x > 0.f ? (-W * em1) * m.z : W * l;
       W = fmaf(W, em1, W);
       ++n_seg;
       if (t != 0.f) {
@@ -261,19 +259,21 @@ __global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
         while (g) {
           const int M = __ffs(g) - 1;
           g &= g - 1;
-          const float t = __shfl_sync(kFull, seg_t, M);
-          const float *hr = rows + M * p.row_stride;
+          // |t h 2^q| < 2^31 by the choice of q, so a 32-bit conversion suffices (the 64-bit one
+          // runs on the FP64 pipe, which is narrow on this part)
+          const float ts = __shfl_sync(kFull, seg_t, M) * p.qscale;
+          const float *hr = rows + M * p.row_stride + 1;
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
             const int j = q * 32 + lane;
-            if (j < C) acc[q] += __float2ll_rn(t * hr[j] * kFixScale);
+            if (j < C) acc[q] += (long long)__float2int_rn(ts * hr[j]);
           }
         }
         unsigned long long *dst = p.tally + (size_t)pix * p.Cpad;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
           const int j = q * 32 + lane;
-          if (j < C && acc[q] != 0) atomicAdd(dst + j, (unsigned long long)acc[q]);
+          if (j < C) atomicAdd(dst + j, (unsigned long long)acc[q]);
         }
         pend &= ~grp;
       }
