@@ -40,6 +40,7 @@ extern "C" {
 #define MCR_ERR_EVENT_LIMIT (-4)    /* a packet reached max_events flights and was ended */
 #define MCR_ERR_TALLY_OVERFLOW (-5) /* a fixed-point tally came within 2 bits of overflow */
 #define MCR_ERR_MEDIUM (-6)         /* the device medium holds a negative or non-finite mu */
+#define MCR_ERR_SCRATCH (-7)        /* problem too large for mc_forward_noalloc's fixed scratch */
 
 #define MCR_PENCIL 0    /* collimated beam from (x0, z0) along (dir_x, dir_z)            */
 #define MCR_LINE 1      /* collimated line source: start uniform on (x0,z0)-(x1,z1)       */
@@ -105,6 +106,30 @@ typedef struct {
  */
 int mc_forward(const mcr_medium *med, const mcr_source *src, const mcr_run *run, float *coeff,
                mcr_stats *stats, void *stream);
+
+/*
+ * mc_forward_noalloc -- mc_forward without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc where they run the forward
+ * model -- programs whose device memory is owned by another allocator or pool, loops that cannot
+ * afford the device synchronisation that cudaMalloc/cudaFree imply, or hosts that forbid
+ * allocation after start-up.  The caller passes the medium, the source and the output buffer
+ * as for mc_forward; the scratch the kernels need (packed medium, fixed-point tally, counters)
+ * lives in one 16 MiB array inside the library, which every GPU that loads libmcr holds until
+ * the process exits.
+ *   Limits: 512 + nx*nz*16 (rounded up to 256) + nx*nz*Cpad*8 bytes <= 16 MiB, with Cpad = 2K+1
+ *   rounded up to a multiple of 4 (e.g. 128x128 at K = 32, 256x256 at K = 8), and at most 2^26
+ *   packets per call (use first_packet to split larger runs); larger problems return
+ *   MCR_ERR_SCRATCH and launch nothing.
+ *   The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ *   with that device current) and caches it: make that first call before any stream capture.
+ *   All calls share the one array and each call clears what it needs; calls whose work overlaps
+ *   on the GPU (different streams, or different host threads) race on it and must be ordered
+ *   by the caller.  No run counters are returned and device-side medium checks are not
+ *   reported: a negative or non-finite mu gives an all-zero output.
+ * Same arguments, layout and results as mc_forward with stats = NULL.
+ */
+int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_run *run, float *coeff,
+                       void *stream);
 
 /*
  * mc_adjoint -- adjoint harmonic radiance MC (Sec. 4, Eq. 12; source of Sec. 6).

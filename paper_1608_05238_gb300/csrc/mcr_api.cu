@@ -324,6 +324,7 @@ const char *mc_status_string(int status) {
     case MCR_ERR_EVENT_LIMIT: return "a packet reached max_events flights and was ended";
     case MCR_ERR_TALLY_OVERFLOW: return "fixed-point tally near overflow";
     case MCR_ERR_MEDIUM: return "medium holds a negative or non-finite coefficient";
+    case MCR_ERR_SCRATCH: return "problem exceeds the fixed 16 MiB scratch of mc_forward_noalloc";
     default: return "unknown status";
   }
 }

@@ -1,0 +1,139 @@
+// mcr_noalloc.cu -- mc_forward_noalloc: the forward transport with its scratch memory (packed
+// medium, 64-bit fixed-point tally, counters) in a fixed-size array that is part of the loaded
+// library, so that the call performs no device allocation at all.
+//
+// Who needs this: callers that may not call cudaMalloc on the path where they run the forward
+// model -- code whose device memory is entirely owned by another allocator or memory pool (the
+// library's own grow-only workspace would compete with it), latency-critical loops where the
+// implicit device synchronisation of cudaMalloc/cudaFree is not acceptable, and hosts that
+// forbid allocation after start-up.  They pass their own input and output buffers; everything
+// else the kernels need lives in g_scratch below.
+#include <math.h>
+
+#include <mutex>
+
+#include "mcr_internal.h"
+
+namespace {
+
+// Every GPU that loads libmcr holds this array (16 MiB) until the process exits.
+constexpr size_t kScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// Layout inside g_scratch: [0, 512) counters and flags, then the packed medium, then the tally.
+constexpr size_t kOffWork = 0, kOffStats = 64, kOffFlags = 256, kSmall = 512;
+
+constexpr int kMaxDev = 64;
+std::mutex g_setup_mu;
+unsigned char *g_scratch_ptr[kMaxDev];  // device address of g_scratch, per device
+
+// Device address of g_scratch on the current device.  In host code `g_scratch` names a host-side
+// stand-in, not device memory, so the address is asked from the runtime once per device (with
+// that device current) and cached.
+int scratch_address(unsigned char **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return MCR_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  if (!g_scratch_ptr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return MCR_ERR_CUDA;
+    }
+    g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return MCR_OK;
+}
+
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" {
+
+int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_run *run, float *coeff,
+                       void *stream) {
+  using namespace mcr;
+  // argument checks (same rules as mc_forward)
+  if (!med || !med->mua || !med->mus || !src || !run || !coeff) return MCR_ERR_ARG;
+  if (med->nx <= 0 || med->nz <= 0 || !(med->dx > 0.f) || !isfinite(med->dx)) return MCR_ERR_ARG;
+  if (!(med->g > -1.f && med->g < 1.f)) return MCR_ERR_ARG;
+  if (run->K < 0 || run->K > MCR_MAX_K || !(run->roulette_p > 0.f && run->roulette_p <= 1.f)) return MCR_ERR_ARG;
+  if (!(run->w_threshold >= 0.f) || !isfinite(run->w_threshold)) return MCR_ERR_ARG;
+  if (run->first_packet + run->n_packets < run->first_packet) return MCR_ERR_ARG;
+  if (src->kind < MCR_PENCIL || src->kind > MCR_ISO_POINT) return MCR_ERR_ARG;
+  if (!isfinite(src->x0) || !isfinite(src->z0) || !isfinite(src->x1) || !isfinite(src->z1) || !isfinite(src->power))
+    return MCR_ERR_ARG;
+  float dirx = 0.f, dirz = 1.f;
+  if (src->kind != MCR_ISO_POINT) {
+    const double nrm = sqrt((double)src->dir_x * src->dir_x + (double)src->dir_z * src->dir_z);
+    if (!(nrm > 0.0) || !isfinite(nrm)) return MCR_ERR_ARG;
+    dirx = (float)(src->dir_x / nrm);
+    dirz = (float)(src->dir_z / nrm);
+  }
+  // size limits of the fixed scratch: one transport launch (no FP64 chunk accumulator)
+  if (run->n_packets > kChunkPackets) return MCR_ERR_SCRATCH;
+  const int64_t npix = (int64_t)med->nx * med->nz;
+  const int C = 2 * run->K + 1, Cpad = (C + 3) & ~3;
+  const size_t mu_bytes = round256((size_t)npix * sizeof(float4));
+  const size_t tally_bytes = (size_t)npix * Cpad * 8;
+  if (npix > ((int64_t)1 << 30) || kSmall + mu_bytes + tally_bytes > kScratchBytes) return MCR_ERR_SCRATCH;
+
+  unsigned char *base = nullptr;
+  int rc = scratch_address(&base);
+  if (rc) return rc;
+  unsigned long long *work = reinterpret_cast<unsigned long long *>(base + kOffWork);
+  DevStats *stats = reinterpret_cast<DevStats *>(base + kOffStats);
+  unsigned *flags = reinterpret_cast<unsigned *>(base + kOffFlags);
+  float4 *mu = reinterpret_cast<float4 *>(base + kSmall);
+  unsigned long long *tally = reinterpret_cast<unsigned long long *>(base + kSmall + mu_bytes);
+
+  cudaStream_t s = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: clear counters, flags and the tally
+  if (cudaMemsetAsync(base, 0, kSmall, s) != cudaSuccess) return MCR_ERR_CUDA;
+  if (cudaMemsetAsync(tally, 0, tally_bytes, s) != cudaSuccess) return MCR_ERR_CUDA;
+  if (launch_pack_medium(med->mua, med->mus, mu, npix, flags, s) != cudaSuccess) return MCR_ERR_CUDA;
+
+  TransportParams p{};
+  p.nx = med->nx;
+  p.nz = med->nz;
+  p.dx = med->dx;
+  p.hg_c = (1.f - med->g) / (1.f + med->g);
+  p.mu = mu;
+  p.kind = src->kind;
+  p.x0 = src->x0;
+  p.z0 = src->z0;
+  p.x1 = src->x1;
+  p.z1 = src->z1;
+  p.dir_x = dirx;
+  p.dir_z = dirz;
+  p.K = run->K;
+  p.C = C;
+  p.Cpad = Cpad;
+  p.row_stride = Cpad + 2;
+  const int qexp = tally_exponent(med->dx, run->w_threshold, run->roulette_p);
+  p.qscale = ldexpf(1.f, qexp);
+  p.first_packet = run->first_packet;
+  p.n_packets = run->n_packets;
+  p.key0 = (unsigned)run->seed;
+  p.key1 = (unsigned)(run->seed >> 32) ^ run->stream_id;
+  p.max_scatter = run->max_scatter;
+  p.max_events = run->max_events;
+  p.w_threshold = run->w_threshold;
+  p.rr_p = run->roulette_p;
+  p.rr_inv_p = 1.f / run->roulette_p;
+  p.tally = tally;
+  p.work = work;
+  p.stats = stats;
+  p.flags = flags;
+  if (run->n_packets && launch_transport(p, s) != cudaSuccess) return MCR_ERR_CUDA;
+  const double area = (double)med->dx * (double)med->dx;
+  const double fixed_scale = run->n_packets ? (double)src->power / ((double)run->n_packets * area) : 0.0;
+  if (launch_finalize(tally, nullptr, npix, C, Cpad, ldexp(1.0, -qexp), fixed_scale, false, nullptr, nullptr,
+                      (double)(run->n_packets ? run->n_packets : 1), false, coeff, flags, s) != cudaSuccess)
+    return MCR_ERR_CUDA;
+  return MCR_OK;
+}
+
+}  // extern "C"

@@ -25,8 +25,9 @@ MAX_K = 64
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_EVENT_LIMIT, ERR_TALLY_OVERFLOW, ERR_MEDIUM = 0, -1, -2, -3, -4, -5, -6
 
 # every symbol declared in include/mcr.h
-EXPORTS = ("mc_forward", "mc_adjoint", "mc_h_eps", "mc_adjoint_source", "mc_gradient", "mc_check",
-           "mc_last_run_info", "mc_release_workspace", "mc_status_string", "mc_version")
+EXPORTS = ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_h_eps", "mc_adjoint_source", "mc_gradient",
+           "mc_check", "mc_last_run_info", "mc_release_workspace", "mc_status_string", "mc_version")
+ERR_SCRATCH = -7
 
 
 class McrError(RuntimeError):
@@ -76,6 +77,7 @@ def load() -> C.CDLL:
         lib = C.CDLL(_build.LIB)
         vp = C.c_void_p
         lib.mc_forward.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
+        lib.mc_forward_noalloc.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run), vp, vp]
         lib.mc_adjoint.argtypes = [C.POINTER(_Medium), vp, C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
         lib.mc_h_eps.argtypes = [C.POINTER(_Medium), vp, vp, vp, vp, vp, vp]
         lib.mc_adjoint_source.argtypes = [C.POINTER(_Medium), vp, vp, vp]
@@ -87,8 +89,8 @@ def load() -> C.CDLL:
         lib.mc_status_string.restype = C.c_char_p
         lib.mc_version.argtypes = []
         lib.mc_version.restype = C.c_char_p
-        for name in ("mc_forward", "mc_adjoint", "mc_h_eps", "mc_adjoint_source", "mc_gradient", "mc_check",
-                     "mc_last_run_info", "mc_release_workspace"):
+        for name in ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_h_eps", "mc_adjoint_source",
+                     "mc_gradient", "mc_check", "mc_last_run_info", "mc_release_workspace"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
         return lib
