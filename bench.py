@@ -2,10 +2,11 @@
 
 Workload (``grad256``): 256 x 256 pixels of 0.05 mm, background mu_a 0.01 / mu_s 10 per mm,
 g = 0.9, three random circular inclusions in the phantom that makes H^meas, collimated line
-source on the top edge, K = 32 harmonics, 1e7 forward + 1e7 adjoint packets.  One step =
-mc_forward -> mc_h_eps (H, eps, dL/dH) -> mc_adjoint_source -> mc_adjoint -> mc_gradient, all
-CUDA kernels on one stream.  Metric: photons/s (forward + adjoint packets per second); the
-gradient evaluations per second are the same number divided by 2e7.
+source on the top edge, K = 32 harmonics, 1e7 forward + 1e7 adjoint packets.  One step is one
+gradient evaluation through the autograd.Function: H = HFromMu(mu_a, mu_s) (mc_forward, H),
+eps = EpsFromH(H, H^meas) (mc_eps), eps.backward() (mc_adjoint_source, mc_adjoint,
+mc_gradient_f32), all libmcr kernels on one stream.  Metric: photons/s (forward + adjoint packets
+per second); the gradient evaluations per second are the same number divided by 2e7.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun (N > 1) every rank runs an independent replica (its own seeds) and rank 0
@@ -29,7 +30,9 @@ if ROOT not in sys.path:
 
 METRIC = "photons/s fwd+adjoint harmonic MC; grad evals/s vs plain MC at stated error"
 UNIT = "photons/s"
-KERNELS_PER_STEP = 14  # pack, transport, finalize | h_eps x2 | adjoint source | pack, 4 cdf, transport, finalize | gradient
+# kernels of libmcr per step: forward (pack, transport, finalize, H) | eps (residual, reduction) |
+# backward (adjoint source | pack, 4 CDF, transport, finalize | gradient)
+KERNELS_PER_STEP = 15
 
 
 def _args():
@@ -41,6 +44,9 @@ def _args():
     ap.add_argument("--packets", type=int, default=10_000_000, help="packets per forward and per adjoint run")
     ap.add_argument("--cpu-sample", type=int, default=20_000, help="oracle packets (fwd and adj) for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="grad256", choices=["grad256", "batch64"],
+                    help="grad256: the gradient evaluation (default); batch64: 64 forward problems in one "
+                         "graph-captured batched launch")
     return ap.parse_args()
 
 
@@ -185,17 +191,22 @@ def _gpu(args):
     # H^meas: the phantom's absorbed energy from a separate 1e7-packet run (seed 1001), made once
     med_t = mcr.Medium(torch.from_numpy(w.mua_true).to(dev), torch.from_numpy(w.mus_true).to(dev), dx, g)
     Hmeas = mcr.h_eps(med_t, mcr.forward(med_t, src, mcr.Run(K=0, n_packets=n, seed=w.meta["hmeas_seed"])))
-    coeff = torch.empty((2 * w.K + 1, w.nz, w.nx), dtype=torch.float32, device=dev)
-    coeff_adj = torch.empty_like(coeff)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    def step(k, m=med, hm=Hmeas):
+    from paper_1608_05238_gb300.autograd import EpsFromH, HFromMu, MCSpec
+    leaf_a = mua.clone().requires_grad_(True)
+    leaf_s = mus.clone().requires_grad_(True)
+
+    def step(k, a=leaf_a, s=leaf_s, hm=Hmeas):
+        # one gradient evaluation through the autograd.Function: H(mu) -> eps -> backward
         base = 1_000_003 * rank + 7919 * k
-        mcr.forward(m, src, mcr.Run(K=w.K, n_packets=n, seed=base), out=coeff)
-        H, v, eps = mcr.h_eps(m, coeff, hm)
-        q = mcr.adjoint_source(m, v)
-        mcr.adjoint(m, q, mcr.Run(K=w.K, n_packets=n, seed=base, stream_id=1), out=coeff_adj)
-        return mcr.gradient(m, coeff, coeff_adj, v), eps
+        spec = MCSpec(dx=dx, g=g, sources=[src], K=w.K, n_packets=n, seed=base, adjoint_seed=base + 1)
+        a.grad = None
+        s.grad = None
+        H = HFromMu.apply(a, s, spec)
+        eps = EpsFromH.apply(H, hm, dx)
+        eps.backward()
+        return (a.grad, s.grad), eps
 
     for k in range(args.warmup):
         step(-1 - k)
@@ -236,21 +247,24 @@ def _gpu(args):
     h_mua = torch.from_numpy(w.mua).pin_memory()
     h_mus = torch.from_numpy(w.mus).pin_memory()
     h_hm = Hmeas.cpu().pin_memory()
-    d_mua, d_mus, d_hm = torch.empty_like(mua), torch.empty_like(mus), torch.empty_like(Hmeas)
-    out_a = torch.empty((w.nz, w.nx), dtype=torch.float64).pin_memory()
+    d_mua = torch.empty_like(mua).requires_grad_(True)
+    d_mus = torch.empty_like(mus).requires_grad_(True)
+    d_hm = torch.empty_like(Hmeas)
+    out_a = torch.empty((w.nz, w.nx), dtype=torch.float32).pin_memory()
     out_s = torch.empty_like(out_a)
     out_e = torch.empty((), dtype=torch.float64).pin_memory()
     h2d = 3 * 4 * w.nx * w.nz
-    d2h = 2 * 8 * w.nx * w.nz + 8
+    d2h = 2 * 4 * w.nx * w.nz + 8
     e2e_T = 0.0
     for k in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        d_mua.copy_(h_mua, non_blocking=True)
-        d_mus.copy_(h_mus, non_blocking=True)
-        d_hm.copy_(h_hm, non_blocking=True)
-        (ga, gs), eps = step(1000 + k, mcr.Medium(d_mua, d_mus, dx, g), d_hm)
+        with torch.no_grad():
+            d_mua.copy_(h_mua, non_blocking=True)
+            d_mus.copy_(h_mus, non_blocking=True)
+            d_hm.copy_(h_hm, non_blocking=True)
+        (ga, gs), eps = step(1000 + k, d_mua, d_mus, d_hm)
         out_a.copy_(ga, non_blocking=True)
         out_s.copy_(gs, non_blocking=True)
         out_e.copy_(eps, non_blocking=True)
@@ -301,8 +315,74 @@ def _gpu(args):
     return 0
 
 
+def _batch64(args):
+    """64 forward problems (16 line sources x 4 wavelengths, 128^2/256^2/512^2 grids, K = 16,
+    1e6 packets each) in one persistent batched launch, captured in a CUDA graph and replayed."""
+    import torch
+    from paper_1608_05238_gb300 import _build, batch, mcr, workloads
+    _build.build()
+    dev = torch.device("cuda", 0)
+    n = min(args.packets, 1_000_000)
+    specs = workloads.batch64(n)
+    K = 16
+    probs = []
+    for s in specs:
+        med = mcr.Medium(torch.from_numpy(s["mua"]).to(dev), torch.from_numpy(s["mus"]).to(dev),
+                         float(np.float32(s["dx"])), float(np.float32(s["g"])))
+        probs.append(mcr.Problem(med, s["n_packets"], seed=s["seed"], stream_id=s["stream_id"],
+                                 source=mcr.Source(**s["source"])))
+    common = mcr.Run(K=K, n_packets=0)
+    launch = batch.autotune(probs, common, reps=1)
+    runner = batch.BatchRunner(probs, common, launch=launch)
+    _, st = runner.run(stats=True)
+    runner.capture()
+    for _ in range(args.warmup):
+        runner.replay()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(0)
+    clocks.start()
+    T = 0.0
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        runner.replay()
+        b.record(stream)
+        b.synchronize()
+        T += a.elapsed_time(b) / 1e3
+    clk = clocks.stop()
+    mcr.check()
+    total = n * len(probs)
+    value = total * args.steps / T
+    C = 2 * K + 1
+    achieved = C * 8 * st["segments"] / (T / args.steps) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+i64", "data": "synthetic",
+           "config": {"workload": f"batch64: 64 forward problems (16 line sources x 4 wavelengths) on 128^2/256^2/"
+                                  f"512^2 grids of 12.8 mm, lognormal media, g 0.9, K={K}, {n:.0e} packets each, "
+                                  f"one graph-captured batched launch", "launch": list(launch),
+                      "tally_bytes": int(sum(p.medium.shape[0] * p.medium.shape[1] for p in probs) * 36 * 8),
+                      "l2": "tallies (2.1 GB) exceed L2"},
+           "clocks": clk, "gpu_launches": None,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                        "traffic": None, "kernel": "k_transport (whole graph timed)",
+                        "segments_per_launch": st["segments"], "bytes_per_segment": C * 8},
+           "cpu_baseline": None}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = _args()
+    if args.workload == "batch64" and args.impl != "reference":
+        return _batch64(args)
     if args.impl == "reference":
         return _reference(args)
     return _gpu(args)

@@ -50,7 +50,7 @@ extern "C" {
 
 /* Pixelised medium (Sec. 3, Eq. 5): piecewise-constant mu_a, mu_s per pixel, scalar HG g. */
 typedef struct {
-  int32_t nx, nz;   /* pixels along x (columns) and z (rows), each >= 1 */
+  int32_t nx, nz;   /* pixels along x (columns) and z (rows), each >= 1, nx*nz < 2^26 */
   float dx;         /* pixel side, mm, > 0 */
   float g;          /* 2D Henyey-Greenstein anisotropy, -1 < g < 1 (Eq. 6) */
   const float *mua; /* device [nz][nx] absorption coefficient, 1/mm, >= 0 */
@@ -143,6 +143,43 @@ int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_r
 int mc_adjoint(const mcr_medium *med, const float *qstar, const mcr_run *run, float *coeff_adj,
                mcr_stats *stats, void *stream);
 
+#define MCR_MAX_BATCH 64
+
+/* One problem of a batched launch: its own medium, source (forward) or q* (adjoint), packets,
+ * seed and output. */
+typedef struct {
+  mcr_medium medium;
+  mcr_source source;     /* forward source; ignored when qstar != NULL */
+  const float *qstar;    /* device [nz][nx] adjoint source (as mc_adjoint), or NULL (forward) */
+  uint64_t n_packets;    /* at most 2^26 per problem in a batch */
+  uint64_t first_packet;
+  uint64_t seed;
+  uint32_t stream_id;
+  float *coeff;          /* device out [2K+1][nz][nx], normalised as mc_forward / mc_adjoint */
+} mcr_problem;
+
+/* Launch shape of the persistent transport kernel; 0 fields take the defaults (128 threads per
+ * block, as many blocks per SM as fit). */
+typedef struct {
+  int32_t threads_per_block; /* multiple of 32, <= 256 */
+  int32_t blocks_per_sm;     /* cap on resident blocks per SM */
+} mcr_launch;
+
+/*
+ * mc_run_batch -- many forward and/or adjoint problems (uneven grids, different media, sources
+ * and packet counts; one harmonic order) in ONE persistent transport launch: warps draw packets
+ * from the concatenated packet ranges of all problems, so the launch stays full until the last
+ * problem is done (the batching pattern of the method's data-parallel structure, Sec. 3 and 4).
+ * `common` supplies K, max_scatter, max_events, w_threshold and roulette_p (its n_packets, seed,
+ * first_packet and stream_id are ignored).  Each problem's coefficients equal what mc_forward /
+ * mc_adjoint returns for it alone (same packets, bit-identical tallies).  No host
+ * synchronisation and, once the workspace has grown to the batch's size (make one call outside
+ * capture first), no allocation: the call can be captured in a CUDA graph.  `launch` may be
+ * NULL.  stats (host, may be NULL) sums the counters of all problems and synchronises.
+ */
+int mc_run_batch(const mcr_problem *problems, int32_t n_problems, const mcr_run *common, const mcr_launch *launch,
+                 mcr_stats *stats, void *stream);
+
 /*
  * mc_h_eps -- absorbed energy and error functional (Sec. 2, Eq. 2).
  * H = mu_a a_0 (device out [nz][nx] FP32, Grueneisen parameter 1); if Hmeas != NULL also
@@ -152,6 +189,15 @@ int mc_adjoint(const mcr_medium *med, const float *qstar, const mcr_run *run, fl
  */
 int mc_h_eps(const mcr_medium *med, const float *coeff, const float *Hmeas, float *H, float *dL_dH,
              double *eps, void *stream);
+
+/*
+ * mc_eps -- the error functional of Eq. 2 from a given absorbed-energy map: for npix pixels of
+ * area pixel_area, eps = 1/2 pixel_area sum (H^meas - H)^2 (device out, one double, FP64
+ * residuals, fixed-order reduction) and dL_dH = -pixel_area (H^meas - H) (device out FP32, may be
+ * NULL).  H, Hmeas: device FP32 [npix].
+ */
+int mc_eps(int64_t npix, double pixel_area, const float *H, const float *Hmeas, float *dL_dH, double *eps,
+           void *stream);
 
 /*
  * mc_adjoint_source -- q*_i = -mu_a,i dL_dH_i / dx^2 (device out [nz][nx] FP32).  For the
@@ -171,12 +217,18 @@ int mc_adjoint_source(const mcr_medium *med, const float *dL_dH, float *qstar, v
 int mc_gradient(const mcr_medium *med, int32_t K, const float *coeff, const float *coeff_adj,
                 const float *dL_dH, double *d_mua, double *d_mus, void *stream);
 
+/* mc_gradient_f32 -- mc_gradient with the same FP64 accumulation and FP32 outputs (rounded once),
+ * for callers whose parameters are FP32 (e.g. autograd leaves). */
+int mc_gradient_f32(const mcr_medium *med, int32_t K, const float *coeff, const float *coeff_adj,
+                    const float *dL_dH, float *d_mua, float *d_mus, void *stream);
+
 /* Synchronises `stream` and returns (and clears) the device's latched error status. */
 int mc_check(void *stream);
 
 /*
  * mc_last_run_info -- profiling query (the paper has no counterpart).  which = 0: the last
- * mc_forward call on the current device; which = 1: the last mc_adjoint call.  Fills `stats`
+ * mc_forward call on the current device; which = 1: the last mc_adjoint call; which = 2: the
+ * last mc_run_batch call that was not being captured into a graph.  Fills `stats`
  * (host, may be NULL) with that call's counters and `transport_ms` (host, may be NULL) with the
  * device time of its transport kernel launch(es), measured by CUDA events recorded on the
  * call's stream around them.  Waits for that call to finish.  MCR_ERR_ARG if no such call ran.

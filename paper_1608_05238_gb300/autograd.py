@@ -1,0 +1,123 @@
+"""Differentiable forward model: ``torch.autograd.Function`` wrappers over the CUDA library.
+
+``HFromMu.apply(mua, mus, spec)`` maps the absorption and scattering maps to the absorbed energy
+H = mu_a Phi (Sec. 2) with the forward harmonic radiance MC (Sec. 3).  Its backward is the
+adjoint method of Secs. 4-5: given v = dL/dH it launches the adjoint MC from
+q* = -mu_a v / dx^2 (Sec. 6's q* = mu_a (H^meas - H) when L is Eq. 2's eps) and combines forward
+and adjoint coefficients pixel by pixel into
+    dL/dmu_a = v a_0 + dx^2 [a_0 a_0*/(2 pi) + (1/pi) sum (a_n a_n* + b_n b_n*)]      (Eq. 22)
+    dL/dmu_s = dx^2 (1/pi) sum (a_n a_n* + b_n b_n*)(1 - g^n)                        (Eq. 28)
+with FP64 sums.  The forward coefficients are kept for the backward pass, or -- at large K or
+when they would exceed a memory budget -- recomputed from the same seeds, which reproduces them
+bit for bit (fixed-point tallies do not depend on scheduling).  The adjoint source is always
+built in the backward pass from the incoming gradient.
+
+``EpsFromH.apply(H, Hmeas, dx)`` is the error functional of Eq. 2 with dL/dH = -dx^2 (H^meas - H).
+Every arithmetic step runs in libmcr's kernels; autograd adds only its own bookkeeping (the seed
+gradient of the scalar loss and its product with dL/dH).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import torch
+
+from . import mcr
+
+
+@dataclass
+class MCSpec:
+    """What the forward model runs: geometry, illumination, harmonic order and packet budgets."""
+    dx: float
+    g: float
+    sources: list                     # mcr.Source list; their fluences add (one illumination)
+    K: int
+    n_packets: int                    # packets per forward source
+    n_adjoint: int | None = None      # adjoint packets (default: n_packets)
+    seed: int = 0
+    adjoint_seed: int | None = None   # default: seed
+    recompute: bool | None = None     # None: recompute when K > 32 or coeff > coeff_budget bytes
+    coeff_budget: int = 256 << 20
+    w_threshold: float = 1e-4
+    roulette_p: float = 0.1
+    max_events: int = 10_000_000
+
+    def forward_run(self, s: int) -> mcr.Run:
+        return mcr.Run(K=self.K, n_packets=self.n_packets, seed=self.seed, stream_id=2 * s,
+                       w_threshold=self.w_threshold, roulette_p=self.roulette_p, max_events=self.max_events)
+
+    def adjoint_run(self) -> mcr.Run:
+        return mcr.Run(K=self.K, n_packets=self.n_adjoint or self.n_packets,
+                       seed=self.seed if self.adjoint_seed is None else self.adjoint_seed, stream_id=1,
+                       w_threshold=self.w_threshold, roulette_p=self.roulette_p, max_events=self.max_events)
+
+    def should_recompute(self, nz: int, nx: int) -> bool:
+        if self.recompute is not None:
+            return bool(self.recompute)
+        return self.K > 32 or (2 * self.K + 1) * nz * nx * 4 > self.coeff_budget
+
+
+def forward_coefficients(med: mcr.Medium, spec: MCSpec) -> torch.Tensor:
+    """Forward coefficients of the whole illumination (sum over ``spec.sources``)."""
+    coeff = mcr.forward(med, spec.sources[0], spec.forward_run(0))
+    for s in range(1, len(spec.sources)):
+        coeff.add_(mcr.forward(med, spec.sources[s], spec.forward_run(s)))
+    return coeff
+
+
+class HFromMu(torch.autograd.Function):
+    """(mu_a, mu_s) -> H = mu_a Phi by forward MC; backward by adjoint MC (Secs. 3-6)."""
+
+    @staticmethod
+    def forward(ctx, mua: torch.Tensor, mus: torch.Tensor, spec: MCSpec):
+        mua_c = mua.detach().contiguous()
+        mus_c = mus.detach().contiguous()
+        med = mcr.Medium(mua_c, mus_c, spec.dx, spec.g)
+        coeff = forward_coefficients(med, spec)
+        H = mcr.h_eps(med, coeff)
+        recompute = spec.should_recompute(*mua_c.shape)
+        ctx.spec = spec
+        ctx.recompute = recompute
+        if recompute:
+            ctx.save_for_backward(mua_c, mus_c)
+        else:
+            ctx.save_for_backward(mua_c, mus_c, coeff)
+        return H
+
+    @staticmethod
+    def backward(ctx, grad_H: torch.Tensor):
+        spec: MCSpec = ctx.spec
+        saved = ctx.saved_tensors
+        mua_c, mus_c = saved[0], saved[1]
+        med = mcr.Medium(mua_c, mus_c, spec.dx, spec.g)
+        v = grad_H.detach().float().contiguous()
+        q = mcr.adjoint_source(med, v)
+        coeff_adj = mcr.adjoint(med, q, spec.adjoint_run())
+        coeff = forward_coefficients(med, spec) if ctx.recompute else saved[2]
+        d_mua, d_mus = mcr.gradient(med, coeff, coeff_adj, v, dtype=torch.float32)
+        return (d_mua if ctx.needs_input_grad[0] else None, d_mus if ctx.needs_input_grad[1] else None, None)
+
+
+class EpsFromH(torch.autograd.Function):
+    """eps = 1/2 dx^2 sum (H^meas - H)^2 (Eq. 2, FP64) with dL/dH = -dx^2 (H^meas - H)."""
+
+    @staticmethod
+    def forward(ctx, H: torch.Tensor, Hmeas: torch.Tensor, dx: float):
+        e, v = mcr.eps(H.detach().contiguous(), Hmeas.detach().contiguous(), dx)
+        ctx.save_for_backward(v)
+        return e
+
+    @staticmethod
+    def backward(ctx, grad_eps: torch.Tensor):
+        (v,) = ctx.saved_tensors
+        return v * grad_eps.to(v.dtype), None, None
+
+
+def absorbed_energy(mua: torch.Tensor, mus: torch.Tensor, spec: MCSpec) -> torch.Tensor:
+    """H(mu_a, mu_s), differentiable with respect to both maps."""
+    return HFromMu.apply(mua, mus, spec)
+
+
+def error_functional(H: torch.Tensor, Hmeas: torch.Tensor, dx: float) -> torch.Tensor:
+    """Eq. 2's eps(H), differentiable with respect to H."""
+    return EpsFromH.apply(H, Hmeas, dx)

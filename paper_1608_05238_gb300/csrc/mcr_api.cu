@@ -1,10 +1,11 @@
 // mcr_api.cu -- the C ABI of libmcr (declared in include/mcr.h): argument checks, the per-device
-// workspace, and the launch sequences of mc_forward / mc_adjoint / mc_h_eps /
-// mc_adjoint_source / mc_gradient.
+// workspace, and the launch sequences of mc_forward / mc_adjoint / mc_run_batch / mc_h_eps /
+// mc_eps / mc_adjoint_source / mc_gradient.
 #include <math.h>
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "mcr_internal.h"
 
@@ -16,13 +17,14 @@ constexpr int kMaxDevices = 64;
 Workspace g_ws[kMaxDevices];
 std::mutex g_mu;
 
-#define MCR_TRY_CUDA(expr)                  \
-  do {                                      \
-    cudaError_t e_ = (expr);                \
+#define MCR_TRY_CUDA(expr)                      \
+  do {                                          \
+    cudaError_t e_ = (expr);                    \
     if (e_ != cudaSuccess) return MCR_ERR_CUDA; \
   } while (0)
 
 int grow(void **ptr, size_t *cap, size_t need) {
+  if (need == 0) need = 256;
   if (*cap >= need && *ptr) return MCR_OK;
   if (*ptr) {
     cudaFree(*ptr);
@@ -38,13 +40,17 @@ int grow(void **ptr, size_t *cap, size_t need) {
   return MCR_OK;
 }
 
-// Workspace of the current device, grown to hold a problem of npix pixels and C channels.
-int workspace(int64_t npix, int C, bool chunked, bool volumetric, Workspace **out) {
+// Sizes the workspace of one launch needs (all problems together).
+struct Need {
+  size_t tally = 0, acc = 0, mu = 0, cdf = 0, block_sums = 0;
+};
+
+// Workspace of the current device, grown to `need`.
+int workspace(const Need &need, Workspace **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MCR_ERR_CUDA;
   Workspace &w = g_ws[dev];
   w.device = dev;
-  const int Cpad = (C + 3) & ~3;
   int rc;
   if (!w.small) {
     if (cudaMalloc(&w.small, kSmallBytes) != cudaSuccess) {
@@ -52,18 +58,16 @@ int workspace(int64_t npix, int C, bool chunked, bool volumetric, Workspace **ou
       return MCR_ERR_NOMEM;
     }
     if (cudaMemset(w.small, 0, kSmallBytes) != cudaSuccess) return MCR_ERR_CUDA;
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 3; ++k)
       if (cudaEventCreate(&w.ev_start[k]) != cudaSuccess || cudaEventCreate(&w.ev_stop[k]) != cudaSuccess)
         return MCR_ERR_CUDA;
   }
-  if ((rc = grow((void **)&w.tally, &w.tally_bytes, (size_t)npix * Cpad * 8))) return rc;
-  if ((rc = grow((void **)&w.mu, &w.mu_bytes, (size_t)npix * sizeof(float4)))) return rc;
   if ((rc = grow((void **)&w.partials, &w.partials_bytes, (size_t)4096 * sizeof(double)))) return rc;
-  if (chunked && (rc = grow((void **)&w.acc, &w.acc_bytes, (size_t)npix * C * sizeof(double)))) return rc;
-  if (volumetric) {
-    if ((rc = grow((void **)&w.cdf, &w.cdf_bytes, (size_t)npix * 8))) return rc;
-    if ((rc = grow((void **)&w.block_sums, &w.block_sums_bytes, (size_t)((npix + 255) / 256) * 8))) return rc;
-  }
+  if (need.tally && (rc = grow((void **)&w.tally, &w.tally_bytes, need.tally))) return rc;
+  if (need.mu && (rc = grow((void **)&w.mu, &w.mu_bytes, need.mu))) return rc;
+  if (need.acc && (rc = grow((void **)&w.acc, &w.acc_bytes, need.acc))) return rc;
+  if (need.cdf && (rc = grow((void **)&w.cdf, &w.cdf_bytes, need.cdf))) return rc;
+  if (need.block_sums && (rc = grow((void **)&w.block_sums, &w.block_sums_bytes, need.block_sums))) return rc;
   *out = &w;
   return MCR_OK;
 }
@@ -72,7 +76,8 @@ bool finite_f(float v) { return isfinite(v) != 0; }
 
 int check_medium(const mcr_medium *m) {
   if (!m || !m->mua || !m->mus) return MCR_ERR_ARG;
-  if (m->nx <= 0 || m->nz <= 0 || (int64_t)m->nx * m->nz > (int64_t)1 << 30) return MCR_ERR_ARG;
+  // the deposit key packs (pixel + 1) into 26 bits
+  if (m->nx <= 0 || m->nz <= 0 || (int64_t)m->nx * m->nz >= (int64_t)1 << 26) return MCR_ERR_ARG;
   if (!(m->dx > 0.f) || !finite_f(m->dx)) return MCR_ERR_ARG;
   if (!(m->g > -1.f && m->g < 1.f)) return MCR_ERR_ARG;
   return MCR_OK;
@@ -84,6 +89,23 @@ int check_run(const mcr_run *r) {
   if (!(r->roulette_p > 0.f && r->roulette_p <= 1.f)) return MCR_ERR_ARG;
   if (!(r->w_threshold >= 0.f) || !finite_f(r->w_threshold)) return MCR_ERR_ARG;
   if (r->first_packet + r->n_packets < r->first_packet) return MCR_ERR_ARG;  // id overflow
+  return MCR_OK;
+}
+
+// Normalised launch direction of a boundary source, or MCR_ERR_ARG.
+int check_source(const mcr_source *src, float *dirx, float *dirz) {
+  if (!src || src->kind < MCR_PENCIL || src->kind > MCR_ISO_POINT) return MCR_ERR_ARG;
+  if (!finite_f(src->x0) || !finite_f(src->z0) || !finite_f(src->x1) || !finite_f(src->z1) ||
+      !finite_f(src->power))
+    return MCR_ERR_ARG;
+  *dirx = 0.f;
+  *dirz = 1.f;
+  if (src->kind != MCR_ISO_POINT) {
+    const double nrm = sqrt((double)src->dir_x * src->dir_x + (double)src->dir_z * src->dir_z);
+    if (!(nrm > 0.0) || !isfinite(nrm)) return MCR_ERR_ARG;
+    *dirx = (float)(src->dir_x / nrm);
+    *dirz = (float)(src->dir_z / nrm);
+  }
   return MCR_OK;
 }
 
@@ -117,97 +139,139 @@ int take_flags(Workspace *w, cudaStream_t s) {
   return MCR_OK;
 }
 
-// The shared body of mc_forward and mc_adjoint.
-int run_mc(const mcr_medium *med, const mcr_source *src, const float *qstar, const mcr_run *run, float *coeff,
-           mcr_stats *stats, cudaStream_t s) {
-  int rc;
-  if ((rc = check_medium(med)) || (rc = check_run(run))) return rc;
-  if (!coeff) return MCR_ERR_ARG;
-  const bool volumetric = qstar != nullptr;
-  float dirx = 0.f, dirz = 1.f;
-  if (!volumetric) {
-    if (!src || src->kind < MCR_PENCIL || src->kind > MCR_ISO_POINT) return MCR_ERR_ARG;
-    if (!finite_f(src->x0) || !finite_f(src->z0) || !finite_f(src->x1) || !finite_f(src->z1) ||
-        !finite_f(src->power))
-      return MCR_ERR_ARG;
-    if (src->kind != MCR_ISO_POINT) {
-      const double nrm = sqrt((double)src->dir_x * src->dir_x + (double)src->dir_z * src->dir_z);
-      if (!(nrm > 0.0) || !isfinite(nrm)) return MCR_ERR_ARG;
-      dirx = (float)(src->dir_x / nrm);
-      dirz = (float)(src->dir_z / nrm);
+// One problem as the host sees it.
+struct HostProblem {
+  const mcr_medium *med;
+  const mcr_source *src;  // forward source, or null
+  const float *qstar;     // volumetric (adjoint) source, or null
+  uint64_t n_packets, first_packet, seed;
+  uint32_t stream_id;
+  float *coeff;
+  float dirx, dirz;
+};
+
+// Enqueues the whole sequence for `probs` on stream s: pack media, source CDFs, zero tallies,
+// transport launch(es), finalize per problem.  `slot` selects the run counters / events.
+int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const TransportLaunch &cfg, int slot,
+            mcr_stats *stats, cudaStream_t s) {
+  const int np = (int)probs.size();
+  const int C = 2 * common->K + 1, Cpad = (C + 3) & ~3;
+  // a single problem may exceed one launch's packet budget (chunks + FP64 flush); a batch may not
+  const bool chunked = np == 1 && probs[0].n_packets > kChunkPackets;
+  Need need;
+  std::vector<size_t> mu_off(np), tally_off(np), cdf_off(np), bs_off(np);
+  for (int i = 0; i < np; ++i) {
+    const int64_t npix = (int64_t)probs[i].med->nx * probs[i].med->nz;
+    mu_off[i] = need.mu / sizeof(float4);
+    need.mu += ((size_t)npix * sizeof(float4) + 255) & ~size_t(255);
+    tally_off[i] = need.tally / 8;
+    need.tally += ((size_t)npix * Cpad * 8 + 255) & ~size_t(255);
+    if (probs[i].qstar) {
+      cdf_off[i] = need.cdf / 8;
+      need.cdf += ((size_t)npix * 8 + 255) & ~size_t(255);
+      bs_off[i] = need.block_sums / 8;
+      need.block_sums += (size_t)((npix + 255) / 256) * 8;
     }
+    if (chunked) need.acc = (size_t)npix * C * sizeof(double);
   }
-  const int64_t npix = (int64_t)med->nx * med->nz;
-  const int C = 2 * run->K + 1, Cpad = (C + 3) & ~3;
-  const bool chunked = run->n_packets > kChunkPackets;
-  std::lock_guard<std::mutex> lock(g_mu);
   Workspace *w = nullptr;
-  if ((rc = workspace(npix, C, chunked, volumetric, &w))) return rc;
+  int rc;
+  if ((rc = workspace(need, &w))) return rc;
 
-  MCR_TRY_CUDA(launch_pack_medium(med->mua, med->mus, w->mu, npix, w->flags(), s));
-  const int slot = volumetric ? 1 : 0;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  MCR_TRY_CUDA(cudaStreamIsCapturing(s, &cap));
+  const bool timed = cap == cudaStreamCaptureStatusNone;
+
   MCR_TRY_CUDA(cudaMemsetAsync(w->stats(slot), 0, sizeof(DevStats), s));
-  if (volumetric)
-    MCR_TRY_CUDA(launch_source_cdf(qstar, npix, w->cdf, w->block_sums, w->block_sums_bytes / 8, w->qmax_bits(), s));
-  if (chunked) MCR_TRY_CUDA(cudaMemsetAsync(w->acc, 0, (size_t)npix * C * sizeof(double), s));
-
-  TransportParams p{};
-  p.nx = med->nx;
-  p.nz = med->nz;
-  p.dx = med->dx;
-  p.hg_c = (1.f - med->g) / (1.f + med->g);
-  p.mu = w->mu;
-  p.kind = volumetric ? kVolume : src->kind;
-  if (!volumetric) {
-    p.x0 = src->x0;
-    p.z0 = src->z0;
-    p.x1 = src->x1;
-    p.z1 = src->z1;
-  }
-  p.dir_x = dirx;
-  p.dir_z = dirz;
-  p.cdf = volumetric ? w->cdf : nullptr;
-  p.q = qstar;
-  p.K = run->K;
+  TransportParams p;
+  memset(&p, 0, sizeof(p));
+  p.n_problems = np;
+  p.K = common->K;
   p.C = C;
   p.Cpad = Cpad;
   p.row_stride = Cpad + 2;  // = 2 mod 4 words: conflict-free 8-byte row stores
-  const int qexp = tally_exponent(med->dx, run->w_threshold, run->roulette_p);
-  p.qscale = ldexpf(1.f, qexp);
-  const double quantum = ldexp(1.0, -qexp);
-  p.key0 = (unsigned)run->seed;
-  p.key1 = (unsigned)(run->seed >> 32) ^ run->stream_id;
-  p.max_scatter = run->max_scatter;
-  p.max_events = run->max_events;
-  p.w_threshold = run->w_threshold;
-  p.rr_p = run->roulette_p;
-  p.rr_inv_p = 1.f / run->roulette_p;
-  p.tally = w->tally;
+  p.max_scatter = common->max_scatter;
+  p.max_events = common->max_events;
+  p.w_threshold = common->w_threshold;
+  p.rr_p = common->roulette_p;
+  p.rr_inv_p = 1.f / common->roulette_p;
   p.work = w->work();
   p.stats = w->stats(slot);
   p.flags = w->flags();
-
-  // packets in chunks of at most kChunkPackets; n = 0 runs no transport and gives zeros
-  const uint64_t n = run->n_packets;
-  uint64_t done = 0;
-  MCR_TRY_CUDA(cudaEventRecord(w->ev_start[slot], s));
-  do {
-    const uint64_t this_n = n - done < kChunkPackets ? n - done : kChunkPackets;
-    MCR_TRY_CUDA(cudaMemsetAsync(w->tally, 0, (size_t)npix * Cpad * 8, s));
+  std::vector<int> qexp(np);
+  uint64_t end = 0;
+  for (int i = 0; i < np; ++i) {
+    const HostProblem &h = probs[i];
+    const int64_t npix = (int64_t)h.med->nx * h.med->nz;
+    float4 *mu = w->mu + mu_off[i];
+    MCR_TRY_CUDA(launch_pack_medium(h.med->mua, h.med->mus, mu, npix, w->flags(), s));
+    ProblemDesc &d = p.prob[i];
+    d.mu = mu;
+    d.tally = w->tally + tally_off[i];
+    d.nx = h.med->nx;
+    d.nz = h.med->nz;
+    d.dx = h.med->dx;
+    d.hg_c = (1.f - h.med->g) / (1.f + h.med->g);
+    qexp[i] = tally_exponent(h.med->dx, common->w_threshold, common->roulette_p);
+    d.qscale = ldexpf(1.f, qexp[i]);
+    d.key0 = (unsigned)h.seed;
+    d.key1 = (unsigned)(h.seed >> 32) ^ h.stream_id;
+    d.first_packet = h.first_packet;
+    if (h.qstar) {
+      d.kind = kVolume;
+      d.cdf = w->cdf + cdf_off[i];
+      d.q = h.qstar;
+      MCR_TRY_CUDA(launch_source_cdf(h.qstar, npix, w->cdf + cdf_off[i], w->block_sums + bs_off[i],
+                                     (size_t)((npix + 255) / 256), w->qmax_bits(i), s));
+    } else {
+      d.kind = h.src->kind;
+      d.x0 = h.src->x0;
+      d.z0 = h.src->z0;
+      d.x1 = h.src->x1;
+      d.z1 = h.src->z1;
+      d.dir_x = h.dirx;
+      d.dir_z = h.dirz;
+    }
+    end += chunked ? 0 : h.n_packets;
+    d.end = end;
+  }
+  MCR_TRY_CUDA(cudaMemsetAsync(w->tally, 0, need.tally, s));
+  if (chunked) MCR_TRY_CUDA(cudaMemsetAsync(w->acc, 0, need.acc, s));
+  if (timed) MCR_TRY_CUDA(cudaEventRecord(w->ev_start[slot], s));
+  if (!chunked) {
+    p.total_packets = end;
     MCR_TRY_CUDA(cudaMemsetAsync(w->work(), 0, 8, s));
-    p.first_packet = run->first_packet + done;
-    p.n_packets = this_n;
-    if (this_n) MCR_TRY_CUDA(launch_transport(p, s));
-    if (chunked) MCR_TRY_CUDA(launch_accumulate(w->tally, npix, C, Cpad, quantum, w->acc, s));
-    done += this_n;
-  } while (done < n);
-  MCR_TRY_CUDA(cudaEventRecord(w->ev_stop[slot], s));
-  w->ran[slot] = true;
-  const double area = (double)med->dx * (double)med->dx;
-  const double fixed_scale = (!volumetric && n) ? (double)src->power / ((double)n * area) : 0.0;
-  MCR_TRY_CUDA(launch_finalize(w->tally, chunked ? w->acc : nullptr, npix, C, Cpad, chunked ? 1.0 : quantum, fixed_scale,
-                               volumetric && n > 0, w->qmax_bits(), volumetric ? w->cdf + (npix - 1) : nullptr,
-                               (double)(n ? n : 1), volumetric, coeff, w->flags(), s));
+    if (end) MCR_TRY_CUDA(launch_transport(p, cfg, s));
+  } else {
+    const HostProblem &h = probs[0];
+    const int64_t npix = (int64_t)h.med->nx * h.med->nz;
+    for (uint64_t done = 0; done < h.n_packets;) {
+      const uint64_t this_n = h.n_packets - done < kChunkPackets ? h.n_packets - done : kChunkPackets;
+      if (done) MCR_TRY_CUDA(cudaMemsetAsync(w->tally, 0, need.tally, s));
+      MCR_TRY_CUDA(cudaMemsetAsync(w->work(), 0, 8, s));
+      p.prob[0].first_packet = h.first_packet + done;
+      p.prob[0].end = this_n;
+      p.total_packets = this_n;
+      MCR_TRY_CUDA(launch_transport(p, cfg, s));
+      MCR_TRY_CUDA(launch_accumulate(w->tally, npix, C, Cpad, ldexp(1.0, -qexp[0]), w->acc, s));
+      done += this_n;
+    }
+  }
+  if (timed) {
+    MCR_TRY_CUDA(cudaEventRecord(w->ev_stop[slot], s));
+    w->ran[slot] = true;
+  }
+  for (int i = 0; i < np; ++i) {
+    const HostProblem &h = probs[i];
+    const int64_t npix = (int64_t)h.med->nx * h.med->nz;
+    const double area = (double)h.med->dx * (double)h.med->dx;
+    const bool vol = h.qstar != nullptr;
+    const double fixed_scale = (!vol && h.n_packets) ? (double)h.src->power / ((double)h.n_packets * area) : 0.0;
+    MCR_TRY_CUDA(launch_finalize(w->tally + tally_off[i], chunked ? w->acc : nullptr, npix, C, Cpad,
+                                 chunked ? 1.0 : ldexp(1.0, -qexp[i]), fixed_scale, vol && h.n_packets > 0,
+                                 w->qmax_bits(i), vol ? w->cdf + cdf_off[i] + (npix - 1) : nullptr,
+                                 (double)(h.n_packets ? h.n_packets : 1), vol, h.coeff, w->flags(), s));
+  }
   if (stats) {
     DevStats d;
     MCR_TRY_CUDA(cudaMemcpyAsync(&d, w->stats(slot), sizeof(DevStats), cudaMemcpyDeviceToHost, s));
@@ -218,6 +282,18 @@ int run_mc(const mcr_medium *med, const mcr_source *src, const float *qstar, con
     return rc;
   }
   return MCR_OK;
+}
+
+// The shared body of mc_forward and mc_adjoint.
+int run_mc(const mcr_medium *med, const mcr_source *src, const float *qstar, const mcr_run *run, float *coeff,
+           mcr_stats *stats, cudaStream_t s) {
+  int rc;
+  if ((rc = check_medium(med)) || (rc = check_run(run))) return rc;
+  if (!coeff) return MCR_ERR_ARG;
+  HostProblem h{med, src, qstar, run->n_packets, run->first_packet, run->seed, run->stream_id, coeff, 0.f, 1.f};
+  if (!qstar && (rc = check_source(src, &h.dirx, &h.dirz))) return rc;
+  std::lock_guard<std::mutex> lock(g_mu);
+  return enqueue({h}, run, TransportLaunch{0, 0}, qstar ? 1 : 0, stats, s);
 }
 
 }  // namespace
@@ -236,6 +312,35 @@ int mc_adjoint(const mcr_medium *med, const float *qstar, const mcr_run *run, fl
   return run_mc(med, nullptr, qstar, run, coeff_adj, stats, (cudaStream_t)stream);
 }
 
+int mc_run_batch(const mcr_problem *problems, int32_t n_problems, const mcr_run *common, const mcr_launch *launch,
+                 mcr_stats *stats, void *stream) {
+  int rc;
+  if (!problems || n_problems < 1 || n_problems > MCR_MAX_BATCH) return MCR_ERR_ARG;
+  if ((rc = check_run(common))) return rc;
+  TransportLaunch cfg{0, 0};
+  if (launch) {
+    if (launch->threads_per_block < 0 || launch->threads_per_block > 256 || launch->threads_per_block % 32 ||
+        launch->blocks_per_sm < 0)
+      return MCR_ERR_ARG;
+    cfg = TransportLaunch{launch->threads_per_block, launch->blocks_per_sm};
+  }
+  std::vector<HostProblem> probs;
+  uint64_t total = 0;
+  for (int i = 0; i < n_problems; ++i) {
+    const mcr_problem &q = problems[i];
+    if ((rc = check_medium(&q.medium))) return rc;
+    if (!q.coeff || q.n_packets > kChunkPackets || q.first_packet + q.n_packets < q.first_packet) return MCR_ERR_ARG;
+    HostProblem h{&q.medium, q.qstar ? nullptr : &q.source, q.qstar, q.n_packets, q.first_packet, q.seed,
+                  q.stream_id, q.coeff, 0.f, 1.f};
+    if (!q.qstar && (rc = check_source(&q.source, &h.dirx, &h.dirz))) return rc;
+    total += q.n_packets;
+    probs.push_back(h);
+  }
+  (void)total;
+  std::lock_guard<std::mutex> lock(g_mu);
+  return enqueue(probs, common, cfg, 2, stats, (cudaStream_t)stream);
+}
+
 int mc_h_eps(const mcr_medium *med, const float *coeff, const float *Hmeas, float *H, float *dL_dH, double *eps,
              void *stream) {
   int rc;
@@ -244,8 +349,20 @@ int mc_h_eps(const mcr_medium *med, const float *coeff, const float *Hmeas, floa
   const int64_t npix = (int64_t)med->nx * med->nz;
   std::lock_guard<std::mutex> lock(g_mu);
   Workspace *w = nullptr;
-  if ((rc = workspace(npix, 1, false, false, &w))) return rc;
+  if ((rc = workspace(Need{}, &w))) return rc;
   MCR_TRY_CUDA(launch_h_eps(med->mua, coeff, Hmeas, npix, (double)med->dx * (double)med->dx, H, dL_dH, w->partials,
+                            w->partials_bytes / sizeof(double), eps, (cudaStream_t)stream));
+  return MCR_OK;
+}
+
+int mc_eps(int64_t npix, double pixel_area, const float *H, const float *Hmeas, float *dL_dH, double *eps,
+           void *stream) {
+  if (npix <= 0 || !(pixel_area > 0.0) || !isfinite(pixel_area) || !H || !Hmeas || !eps) return MCR_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  Workspace *w = nullptr;
+  int rc;
+  if ((rc = workspace(Need{}, &w))) return rc;
+  MCR_TRY_CUDA(launch_h_eps(nullptr, H, Hmeas, npix, pixel_area, nullptr, dL_dH, w->partials,
                             w->partials_bytes / sizeof(double), eps, (cudaStream_t)stream));
   return MCR_OK;
 }
@@ -254,8 +371,8 @@ int mc_adjoint_source(const mcr_medium *med, const float *dL_dH, float *qstar, v
   int rc;
   if ((rc = check_medium(med))) return rc;
   if (!dL_dH || !qstar) return MCR_ERR_ARG;
-  MCR_TRY_CUDA(launch_adjoint_source(med->mua, dL_dH, (int64_t)med->nx * med->nz, (double)med->dx * (double)med->dx, qstar,
-                                     (cudaStream_t)stream));
+  MCR_TRY_CUDA(launch_adjoint_source(med->mua, dL_dH, (int64_t)med->nx * med->nz,
+                                     (double)med->dx * (double)med->dx, qstar, (cudaStream_t)stream));
   return MCR_OK;
 }
 
@@ -266,6 +383,16 @@ int mc_gradient(const mcr_medium *med, int32_t K, const float *coeff, const floa
   if (K < 0 || K > MCR_MAX_K || !coeff || !coeff_adj || !dL_dH || !d_mua) return MCR_ERR_ARG;
   MCR_TRY_CUDA(launch_gradient(coeff, coeff_adj, dL_dH, (int64_t)med->nx * med->nz, K, (double)med->g,
                                (double)med->dx * (double)med->dx, d_mua, d_mus, (cudaStream_t)stream));
+  return MCR_OK;
+}
+
+int mc_gradient_f32(const mcr_medium *med, int32_t K, const float *coeff, const float *coeff_adj, const float *dL_dH,
+                    float *d_mua, float *d_mus, void *stream) {
+  int rc;
+  if ((rc = check_medium(med))) return rc;
+  if (K < 0 || K > MCR_MAX_K || !coeff || !coeff_adj || !dL_dH || !d_mua) return MCR_ERR_ARG;
+  MCR_TRY_CUDA(launch_gradient_f32(coeff, coeff_adj, dL_dH, (int64_t)med->nx * med->nz, K, (double)med->g,
+                                   (double)med->dx * (double)med->dx, d_mua, d_mus, (cudaStream_t)stream));
   return MCR_OK;
 }
 
@@ -283,7 +410,7 @@ int mc_check(void *stream) {
 
 int mc_last_run_info(int32_t which, mcr_stats *stats, float *transport_ms) {
   int dev = 0;
-  if (which < 0 || which > 1) return MCR_ERR_ARG;
+  if (which < 0 || which > 2) return MCR_ERR_ARG;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MCR_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
   Workspace &w = g_ws[dev];
@@ -307,7 +434,7 @@ int mc_release_workspace(void) {
   void *ptrs[] = {w.tally, w.acc, w.mu, w.cdf, w.block_sums, w.partials, w.small};
   for (void *p : ptrs)
     if (p) cudaFree(p);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < 3; ++k) {
     if (w.ev_start[k]) cudaEventDestroy(w.ev_start[k]);
     if (w.ev_stop[k]) cudaEventDestroy(w.ev_stop[k]);
   }

@@ -31,29 +31,42 @@ constexpr unsigned kFlagEventLimit = 1u;
 constexpr unsigned kFlagOverflow = 2u;
 constexpr unsigned kFlagMedium = 4u;
 
-struct TransportParams {
-  // medium
-  int nx, nz;
-  float dx;
-  float hg_c;  // (1 - g) / (1 + g)
-  const float4 *mu;  // packed (mu_a, mu_s, 1/mu_a, 1/mu_s) per pixel
-  // source
-  int kind;
-  float x0, z0, x1, z1, dir_x, dir_z;
+// Problems per transport launch (the table travels in kernel parameter space).
+constexpr int kMaxBatch = 64;
+
+// One problem of a transport launch: medium, source, tally and its packet range.
+struct ProblemDesc {
+  const float4 *mu;               // packed (mu_a, mu_s, 1/mu_a, 1/mu_s) per pixel
+  unsigned long long *tally;      // [npix][Cpad] fixed point
   const unsigned long long *cdf;  // volumetric: inclusive prefix of quantised |q|
   const float *q;                 // volumetric: signed source (for the packet sign)
-  // run
-  int K, C, Cpad, row_stride;     // C = 2K+1 channels, Cpad = C rounded up to 4, smem row stride
-  float qscale;                   // 2^q, the fixed-point scale of the deposits
-  unsigned long long first_packet, n_packets;
+  unsigned long long first_packet;  // packet id of the problem's first packet
+  unsigned long long end;           // exclusive end of its packets in the launch's packet space
+  int nx, nz;
+  float dx;
+  float hg_c;    // (1 - g) / (1 + g)
+  float qscale;  // 2^q, the fixed-point scale of the deposits
+  int kind;      // MCR_PENCIL | MCR_LINE | MCR_ISO_POINT | kVolume
+  float x0, z0, x1, z1, dir_x, dir_z;
   unsigned key0, key1;
+};
+
+struct TransportParams {
+  int n_problems;
+  int K, C, Cpad, row_stride;  // C = 2K+1 channels, Cpad = C rounded up to 4, smem row stride
   unsigned max_scatter, max_events;
   float w_threshold, rr_p, rr_inv_p;
-  // outputs / scratch
-  unsigned long long *tally;      // [npix][Cpad] fixed point
-  unsigned long long *work;       // packet counter
+  unsigned long long total_packets;  // = prob[n_problems-1].end
+  unsigned long long *work;          // packet counter
   DevStats *stats;
-  const unsigned *flags;          // medium-invalid flag: transport does nothing if set
+  const unsigned *flags;             // medium-invalid flag: transport does nothing if set
+  ProblemDesc prob[kMaxBatch];
+};
+
+// Launch shape of the persistent transport kernel (0 = default: 128 threads, full occupancy).
+struct TransportLaunch {
+  int threads_per_block;
+  int blocks_per_sm;
 };
 
 // Workspace of one device (grow-only).
@@ -71,26 +84,27 @@ struct Workspace {
   size_t block_sums_bytes = 0;
   double *partials = nullptr;
   size_t partials_bytes = 0;
-  // small block: packet counter, per-kind run counters (0 forward, 1 adjoint), flags
+  // small block: packet counter, run counters per call kind (0 forward, 1 adjoint, 2 batch),
+  // flags, and max|q*| bits per problem of a volumetric run
   unsigned char *small = nullptr;
   unsigned long long *work() const { return reinterpret_cast<unsigned long long *>(small); }
   DevStats *stats(int slot) const { return reinterpret_cast<DevStats *>(small + 64 + 128 * slot); }
-  unsigned *qmax_bits() const { return reinterpret_cast<unsigned *>(small + 320); }
-  unsigned *flags() const { return reinterpret_cast<unsigned *>(small + 324); }
-  // events around the transport launches of the last forward (0) and adjoint (1) call
-  cudaEvent_t ev_start[2] = {nullptr, nullptr};
-  cudaEvent_t ev_stop[2] = {nullptr, nullptr};
-  bool ran[2] = {false, false};
+  unsigned *flags() const { return reinterpret_cast<unsigned *>(small + 448); }
+  unsigned *qmax_bits(int problem = 0) const { return reinterpret_cast<unsigned *>(small + 512) + problem; }
+  // events around the transport launches of the last call of each kind
+  cudaEvent_t ev_start[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_stop[3] = {nullptr, nullptr, nullptr};
+  bool ran[3] = {false, false, false};
 };
 
-constexpr size_t kSmallBytes = 512;
+constexpr size_t kSmallBytes = 512 + 4 * kMaxBatch;
 static_assert(sizeof(DevStats) <= 128, "stats slot");
 
 // ---- launchers (each enqueues on `s` and returns the launch error) ----
 cudaError_t launch_pack_medium(const float *mua, const float *mus, float4 *mu, int64_t npix, unsigned *flags,
                                cudaStream_t s);
-cudaError_t launch_transport(const TransportParams &p, cudaStream_t s);
-size_t transport_smem_bytes(int row_stride);
+cudaError_t launch_transport(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s);
+size_t transport_smem_bytes(int row_stride, int threads);
 cudaError_t launch_source_cdf(const float *q, int64_t npix, unsigned long long *cdf,
                               unsigned long long *block_sums, size_t block_sums_cap, unsigned *qmax_bits,
                               cudaStream_t s);
@@ -110,5 +124,7 @@ cudaError_t launch_adjoint_source(const float *mua, const float *dL_dH, int64_t 
                                   cudaStream_t s);
 cudaError_t launch_gradient(const float *coeff, const float *coeff_adj, const float *dL_dH, int64_t npix, int K,
                             double g, double area, double *d_mua, double *d_mus, cudaStream_t s);
+cudaError_t launch_gradient_f32(const float *coeff, const float *coeff_adj, const float *dL_dH, int64_t npix, int K,
+                                double g, double area, float *d_mua, float *d_mus, cudaStream_t s);
 
 }  // namespace mcr

@@ -9,6 +9,7 @@
 // forbid allocation after start-up.  They pass their own input and output buffers; everything
 // else the kernels need lives in g_scratch below.
 #include <math.h>
+#include <string.h>
 
 #include <mutex>
 
@@ -95,39 +96,44 @@ int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_r
   if (cudaMemsetAsync(tally, 0, tally_bytes, s) != cudaSuccess) return MCR_ERR_CUDA;
   if (launch_pack_medium(med->mua, med->mus, mu, npix, flags, s) != cudaSuccess) return MCR_ERR_CUDA;
 
-  TransportParams p{};
-  p.nx = med->nx;
-  p.nz = med->nz;
-  p.dx = med->dx;
-  p.hg_c = (1.f - med->g) / (1.f + med->g);
-  p.mu = mu;
-  p.kind = src->kind;
-  p.x0 = src->x0;
-  p.z0 = src->z0;
-  p.x1 = src->x1;
-  p.z1 = src->z1;
-  p.dir_x = dirx;
-  p.dir_z = dirz;
+  // a transport launch with a one-problem table (the table lives in kernel parameter space)
+  TransportParams p;
+  memset(&p, 0, sizeof(p));
+  p.n_problems = 1;
   p.K = run->K;
   p.C = C;
   p.Cpad = Cpad;
   p.row_stride = Cpad + 2;
-  const int qexp = tally_exponent(med->dx, run->w_threshold, run->roulette_p);
-  p.qscale = ldexpf(1.f, qexp);
-  p.first_packet = run->first_packet;
-  p.n_packets = run->n_packets;
-  p.key0 = (unsigned)run->seed;
-  p.key1 = (unsigned)(run->seed >> 32) ^ run->stream_id;
   p.max_scatter = run->max_scatter;
   p.max_events = run->max_events;
   p.w_threshold = run->w_threshold;
   p.rr_p = run->roulette_p;
   p.rr_inv_p = 1.f / run->roulette_p;
-  p.tally = tally;
+  p.total_packets = run->n_packets;
   p.work = work;
   p.stats = stats;
   p.flags = flags;
-  if (run->n_packets && launch_transport(p, s) != cudaSuccess) return MCR_ERR_CUDA;
+  ProblemDesc &d = p.prob[0];
+  d.mu = mu;
+  d.tally = tally;
+  d.first_packet = run->first_packet;
+  d.end = run->n_packets;
+  d.nx = med->nx;
+  d.nz = med->nz;
+  d.dx = med->dx;
+  d.hg_c = (1.f - med->g) / (1.f + med->g);
+  const int qexp = tally_exponent(med->dx, run->w_threshold, run->roulette_p);
+  d.qscale = ldexpf(1.f, qexp);
+  d.kind = src->kind;
+  d.x0 = src->x0;
+  d.z0 = src->z0;
+  d.x1 = src->x1;
+  d.z1 = src->z1;
+  d.dir_x = dirx;
+  d.dir_z = dirz;
+  d.key0 = (unsigned)run->seed;
+  d.key1 = (unsigned)(run->seed >> 32) ^ run->stream_id;
+  if (run->n_packets && launch_transport(p, TransportLaunch{0, 0}, s) != cudaSuccess) return MCR_ERR_CUDA;
   const double area = (double)med->dx * (double)med->dx;
   const double fixed_scale = run->n_packets ? (double)src->power / ((double)run->n_packets * area) : 0.0;
   if (launch_finalize(tally, nullptr, npix, C, Cpad, ldexp(1.0, -qexp), fixed_scale, false, nullptr, nullptr,

@@ -139,14 +139,15 @@ __global__ void k_finalize(const unsigned long long *__restrict__ tally, const d
   if (__syncthreads_or(near_overflow) && tid == 0) atomicOr(flags, kFlagOverflow);
 }
 
-// H = mu_a a_0 ; r = H^meas - H ; dL/dH = -A r ; per-block FP64 partial sums of r^2.
+// H = mu_a a_0 (or H = a0 when mua is null) ; r = H^meas - H ; dL/dH = -A r ; per-block FP64
+// partial sums of r^2.
 __global__ void k_h_eps(const float *__restrict__ mua, const float *__restrict__ a0, const float *__restrict__ Hmeas,
                         int64_t npix, double area, float *__restrict__ H, float *__restrict__ dL_dH,
                         double *__restrict__ partials) {
   __shared__ double red[kThreads / 32];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < npix; i += (int64_t)gridDim.x * kThreads) {
-    const float h = mua[i] * a0[i];
+    const float h = mua ? mua[i] * a0[i] : a0[i];
     if (H) H[i] = h;
     if (Hmeas) {
       const double r = (double)Hmeas[i] - (double)h;  // residual and its square in FP64
@@ -181,9 +182,10 @@ __global__ void k_adjoint_source(const float *__restrict__ mua, const float *__r
 
 // Per pixel, FP64: G_a = a0 a0*/(2pi) + (1/pi) sum (a_n a_n* + b_n b_n*)      (Eq. 22)
 //                  G_s = (1/pi) sum (a_n a_n* + b_n b_n*)(1 - g^n)            (Eq. 28)
+template <typename OutT>
 __global__ void k_gradient(const float *__restrict__ F, const float *__restrict__ Fs, const float *__restrict__ v,
-                           int64_t npix, int K, double g, double area, double *__restrict__ d_mua,
-                           double *__restrict__ d_mus) {
+                           int64_t npix, int K, double g, double area, OutT *__restrict__ d_mua,
+                           OutT *__restrict__ d_mus) {
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < npix; i += (int64_t)gridDim.x * kThreads) {
     const double a0 = F[i];
     double Ga = a0 * (double)Fs[i] * (0.5 / CUDART_PI);
@@ -195,8 +197,8 @@ __global__ void k_gradient(const float *__restrict__ F, const float *__restrict_
       Ga += pr * (1.0 / CUDART_PI);
       Gs += pr * (1.0 - gn) * (1.0 / CUDART_PI);
     }
-    d_mua[i] = (double)v[i] * a0 + area * Ga;
-    if (d_mus) d_mus[i] = area * Gs;
+    d_mua[i] = (OutT)((double)v[i] * a0 + area * Ga);
+    if (d_mus) d_mus[i] = (OutT)(area * Gs);
   }
 }
 
@@ -266,7 +268,15 @@ cudaError_t launch_adjoint_source(const float *mua, const float *dL_dH, int64_t 
 
 cudaError_t launch_gradient(const float *coeff, const float *coeff_adj, const float *dL_dH, int64_t npix, int K,
                             double g, double area, double *d_mua, double *d_mus, cudaStream_t s) {
-  k_gradient<<<grid_for(npix, kThreads), kThreads, 0, s>>>(coeff, coeff_adj, dL_dH, npix, K, g, area, d_mua, d_mus);
+  k_gradient<double><<<grid_for(npix, kThreads), kThreads, 0, s>>>(coeff, coeff_adj, dL_dH, npix, K, g, area, d_mua,
+                                                                   d_mus);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gradient_f32(const float *coeff, const float *coeff_adj, const float *dL_dH, int64_t npix, int K,
+                                double g, double area, float *d_mua, float *d_mus, cudaStream_t s) {
+  k_gradient<float><<<grid_for(npix, kThreads), kThreads, 0, s>>>(coeff, coeff_adj, dL_dH, npix, K, g, area, d_mua,
+                                                                  d_mus);
   return cudaGetLastError();
 }
 

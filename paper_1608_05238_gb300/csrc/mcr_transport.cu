@@ -2,9 +2,14 @@
 // radiance Monte Carlo (Sec. 3, 3.1 and 4 of Hochuli et al., arXiv 1608.05238), for sm_103a.
 //
 // Design (one GPU, HBM/L2 resident tallies):
+//  * One launch runs a table of problems (up to kMaxBatch: grids of different sizes, media,
+//    sources, tallies; one harmonic order K).  The table travels in kernel parameter space, so
+//    the launch needs no device-side descriptor memory and can be captured in a CUDA graph.  A
+//    single mc_forward / mc_adjoint call is a table of one.
 //  * Persistent warps.  Each lane carries one packet; a lane whose packet ended takes the next
-//    packet id from a global counter (one atomic per warp per refill), so lanes stay busy
-//    until the run's packets are used up.  One loop iteration = one pixel segment per lane.
+//    packet index of the launch's packet space from a global counter (one atomic per warp per
+//    refill) and finds its problem by binary search over the table's prefix ends, so lanes stay
+//    busy until all problems' packets are used up.  One loop iteration = one pixel segment.
 //  * Counter-based Philox4x32-10 per packet: the random numbers of packet p depend only on
 //    (seed, stream_id, p, event), never on which warp ran it.
 //  * Pixel traversal keeps integer pixel indices authoritative and the position as an offset
@@ -12,11 +17,13 @@
 //  * Harmonic vectors h = (1, cos theta, sin theta, ..., cos K theta, sin K theta) are built
 //    once per free flight from (s_z + i s_x)^n (K complex products, no trigonometry) into a
 //    per-lane shared-memory row.
-//  * Deposits are warp-cooperative: for each pixel touched in this iteration, the lanes of the
-//    warp take one coefficient each, sum the contributions of every lane in that pixel (warp
-//    reduction via match_any) as 64-bit fixed-point integers, and issue one coalesced red.add
-//    per coefficient into the pixel-major tally [pix][Cpad].  Integer sums are exact, so the
-//    tally does not depend on scheduling.
+//  * Deposits are warp-cooperative: for each tally row touched in this iteration, the lanes of
+//    the warp take one coefficient each, sum the contributions of every lane in that row (warp
+//    reduction via match_any on the row address) as 64-bit fixed-point integers, and issue one
+//    coalesced red.add per coefficient into the pixel-major tally [pix][Cpad].  Integer sums are
+//    exact, so the tally does not depend on scheduling.  Deposits are rounded to 2^-q with q
+//    chosen per problem so that one deposit fits in int32: the conversion is a 32-bit one (the
+//    64-bit conversion runs on the FP64 pipe, which is narrow on this part).
 #include <math_constants.h>
 
 #include "mcr_internal.h"
@@ -50,9 +57,8 @@ __device__ __forceinline__ uint4 philox4x32_10(unsigned long long pid, unsigned 
 __device__ __forceinline__ float u01(unsigned x) { return fmaf((float)(x >> 9), 0x1p-23f, 0x1p-24f); }
 
 // Volumetric source: smallest i with cdf[i] > floor(r48 * total / 2^48).
-__device__ __forceinline__ int pick_pixel(const unsigned long long *__restrict__ cdf, int npix, unsigned w0,
-                                          unsigned w1) {
-  const unsigned long long total = cdf[npix - 1];
+__device__ __forceinline__ int pick_pixel(const unsigned long long *__restrict__ cdf, int npix,
+                                          unsigned long long total, unsigned w0, unsigned w1) {
   const unsigned long long r48 = ((unsigned long long)w0 << 16) | (unsigned long long)(w1 >> 16);
   const unsigned long long target = __umul64hi(r48 << 16, total);
   int lo = 0, hi = npix - 1;
@@ -75,21 +81,35 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-template <int NP>
-__global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
+template <int NP, bool BATCH>
+__global__ void __launch_bounds__(256) k_transport(const __grid_constant__ TransportParams p) {
   extern __shared__ float smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   float *const rows = smem + (size_t)warp * 32 * p.row_stride;
   float *const my = rows + lane * p.row_stride;
   if (*p.flags & kFlagMedium) return;
-  if (p.kind == kVolume && p.cdf[p.nx * p.nz - 1] == 0ull) return;  // all-zero source: nothing to launch
 
-  const float dx = p.dx;
-  const int nx = p.nx, nz = p.nz, K = p.K, C = p.C;
+  const int K = p.K, C = p.C;
 
   bool alive = false, exhausted = false;
   unsigned long long pid = 0;
+  // the lane's problem, cached at launch
+  const float4 *mu = nullptr;
+  int prob = 0;
+  int nx = 1, nz = 1;
+  float dx = 1.f, hg_c = 1.f, qscale = 1.f;
+  unsigned key0 = 0, key1 = 0;
+  // problem fields: per-lane registers in a batch, uniform kernel parameters for a single problem
+  auto NX = [&]() { return BATCH ? nx : p.prob[0].nx; };
+  auto NZ = [&]() { return BATCH ? nz : p.prob[0].nz; };
+  auto DX = [&]() { return BATCH ? dx : p.prob[0].dx; };
+  auto HGC = [&]() { return BATCH ? hg_c : p.prob[0].hg_c; };
+  auto QS = [&]() { return BATCH ? qscale : p.prob[0].qscale; };
+  auto KEY0 = [&]() { return BATCH ? key0 : p.prob[0].key0; };
+  auto KEY1 = [&]() { return BATCH ? key1 : p.prob[0].key1; };
+  auto MU = [&]() { return BATCH ? mu : p.prob[0].mu; };
+  // packet state
   float fx = 0.f, fz = 0.f, sx = 0.f, sz = 1.f, inv_ax = 0.f, inv_az = 0.f, W = 0.f, tau = 0.f;
   int ix = 0, iz = 0;
   unsigned flight = 0, nscat = 0, cu1 = 0, cu2 = 0;
@@ -114,7 +134,7 @@ __global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
   };
   // start free flight number `flight` (event flight+1): tau = -ln U, keep U for scatter/roulette
   auto begin_flight = [&]() {
-    const uint4 r = philox4x32_10(pid, flight + 1u, p.key0, p.key1);
+    const uint4 r = philox4x32_10(pid, flight + 1u, KEY0(), KEY1());
     tau = -logf(u01(r.x));
     cu1 = r.y;
     cu2 = r.z;
@@ -133,43 +153,75 @@ __global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
       if (lane == leader) base = atomicAdd(p.work, (unsigned long long)__popc(need));
       base = __shfl_sync(kFull, base, leader);
       if (!alive && !exhausted) {
-        const unsigned long long idx = base + __popc(need & ((1u << lane) - 1u));
-        if (idx >= p.n_packets) {
+        const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
+        if (g >= p.total_packets) {
           exhausted = true;
         } else {
-          pid = p.first_packet + idx;
+          // the problem owning launch packet g: smallest pi with prob[pi].end > g
+          int lo = 0;
+          if (BATCH) {
+            int hi = p.n_problems - 1;
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (p.prob[mid].end > g)
+                hi = mid;
+              else
+                lo = mid + 1;
+            }
+          }
+          const ProblemDesc &P = p.prob[lo];
+          const unsigned long long start = lo ? p.prob[lo - 1].end : 0ull;
+          pid = P.first_packet + (g - start);
+          if (BATCH) {
+            mu = P.mu;
+            prob = lo;
+            nx = P.nx;
+            nz = P.nz;
+            dx = P.dx;
+            hg_c = P.hg_c;
+            qscale = P.qscale;
+            key0 = P.key0;
+            key1 = P.key1;
+          }
           ++n_launch;
           float W0 = 1.f;
           bool inside = true;
-          if (p.kind == kVolume) {
-            const uint4 r0 = philox4x32_10(pid, 0u, p.key0, p.key1);
-            const uint4 r1 = philox4x32_10(pid, 1u, p.key0, p.key1);
-            const int pix = pick_pixel(p.cdf, nx * nz, r0.x, r0.y);
-            ix = pix % nx;
-            iz = pix / nx;
-            fx = u01(r1.x) * dx;
-            fz = u01(r1.y) * dx;
-            sincospif(2.f * u01(r0.z), &sx, &sz);
-            W0 = __ldg(p.q + pix) < 0.f ? -1.f : 1.f;
+          if (P.kind == kVolume) {
+            const int npix = NX() * NZ();
+            const unsigned long long total = __ldg(P.cdf + npix - 1);
+            if (total == 0ull) {  // all-zero source: nothing to launch
+              inside = false;
+              W0 = 0.f;
+            } else {
+              const uint4 r0 = philox4x32_10(pid, 0u, KEY0(), KEY1());
+              const uint4 r1 = philox4x32_10(pid, 1u, KEY0(), KEY1());
+              const int pix = pick_pixel(P.cdf, npix, total, r0.x, r0.y);
+              ix = pix % NX();
+              iz = pix / NX();
+              fx = u01(r1.x) * DX();
+              fz = u01(r1.y) * DX();
+              sincospif(2.f * u01(r0.z), &sx, &sz);
+              W0 = __ldg(P.q + pix) < 0.f ? -1.f : 1.f;
+            }
           } else {
-            float x = p.x0, z = p.z0;
-            sx = p.dir_x;
-            sz = p.dir_z;
-            if (p.kind == MCR_LINE) {
-              const uint4 r0 = philox4x32_10(pid, 0u, p.key0, p.key1);
+            float x = P.x0, z = P.z0;
+            sx = P.dir_x;
+            sz = P.dir_z;
+            if (P.kind == MCR_LINE) {
+              const uint4 r0 = philox4x32_10(pid, 0u, KEY0(), KEY1());
               const float u = u01(r0.x);
-              x = fmaf(u, p.x1 - p.x0, p.x0);
-              z = fmaf(u, p.z1 - p.z0, p.z0);
-            } else if (p.kind == MCR_ISO_POINT) {
-              const uint4 r0 = philox4x32_10(pid, 0u, p.key0, p.key1);
+              x = fmaf(u, P.x1 - P.x0, P.x0);
+              z = fmaf(u, P.z1 - P.z0, P.z0);
+            } else if (P.kind == MCR_ISO_POINT) {
+              const uint4 r0 = philox4x32_10(pid, 0u, KEY0(), KEY1());
               sincospif(2.f * u01(r0.z), &sx, &sz);
             }
-            inside = x >= 0.f && x <= nx * dx && z >= 0.f && z <= nz * dx;
+            inside = x >= 0.f && x <= NX() * DX() && z >= 0.f && z <= NZ() * DX();
             if (inside) {
-              ix = min((int)floorf(x / dx), nx - 1);
-              iz = min((int)floorf(z / dx), nz - 1);
-              fx = clamp_dx(x - ix * dx, dx);
-              fz = clamp_dx(z - iz * dx, dx);
+              ix = min((int)floorf(x / DX()), NX() - 1);
+              iz = min((int)floorf(z / DX()), NZ() - 1);
+              fx = clamp_dx(x - ix * DX(), DX());
+              fz = clamp_dx(z - iz * DX(), DX());
             }
           }
           W = W0;
@@ -194,15 +246,15 @@ __global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
     __syncwarp();
 
     // ---------------------------------------------------------------- one pixel segment
-    int seg_pix = -1;
-    float seg_t = 0.f;
+    unsigned seg_key = 0u;  // (pixel + 1) << 6 | problem of this lane's segment (0: none)
+    float seg_ts = 0.f;     // its track weight times 2^q
     bool collided = false, escaped = false;
     if (alive) {
-      const int pix = iz * nx + ix;
-      const float4 m = __ldg(p.mu + pix);  // (mu_a, mu_s, 1/mu_a, 1/mu_s)
+      const int pix = iz * NX() + ix;
+      const float4 m = __ldg(MU() + pix);  // (mu_a, mu_s, 1/mu_a, 1/mu_s)
       float dist_x = CUDART_INF_F, dist_z = CUDART_INF_F;
-      if (sx != 0.f) dist_x = fmaxf((sx > 0.f ? dx - fx : fx) * inv_ax, 0.f);
-      if (sz != 0.f) dist_z = fmaxf((sz > 0.f ? dx - fz : fz) * inv_az, 0.f);
+      if (sx != 0.f) dist_x = fmaxf((sx > 0.f ? DX() - fx : fx) * inv_ax, 0.f);
+      if (sz != 0.f) dist_z = fmaxf((sz > 0.f ? DX() - fz : fz) * inv_az, 0.f);
       const float d_edge = fminf(dist_x, dist_z);
       const float d_coll = tau * m.w;  // +inf when mu_s = 0 (tau > 0)
       collided = d_coll < d_edge;
@@ -213,12 +265,12 @@ __global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
       W = fmaf(W, em1, W);
       ++n_seg;
       if (t != 0.f) {
-        seg_pix = pix;
-        seg_t = t;
+        seg_key = ((unsigned)(pix + 1) << 6) | (unsigned)(BATCH ? prob : 0);
+        seg_ts = t * QS();
       }
       if (collided) {
-        fx = clamp_dx(fmaf(l, sx, fx), dx);
-        fz = clamp_dx(fmaf(l, sz, fz), dx);
+        fx = clamp_dx(fmaf(l, sx, fx), DX());
+        fz = clamp_dx(fmaf(l, sz, fz), DX());
       } else {
         tau = fmaxf(fmaf(-m.y, l, tau), 0.f);
         if (dist_x <= dist_z) {  // ties: x first, z follows as a zero-length segment
@@ -227,31 +279,32 @@ __global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
             fx = 0.f;
           } else {
             --ix;
-            fx = dx;
+            fx = DX();
           }
-          fz = clamp_dx(fmaf(l, sz, fz), dx);
+          fz = clamp_dx(fmaf(l, sz, fz), DX());
         } else {
           if (sz > 0.f) {
             ++iz;
             fz = 0.f;
           } else {
             --iz;
-            fz = dx;
+            fz = DX();
           }
-          fx = clamp_dx(fmaf(l, sx, fx), dx);
+          fx = clamp_dx(fmaf(l, sx, fx), DX());
         }
-        escaped = (unsigned)ix >= (unsigned)nx || (unsigned)iz >= (unsigned)nz;
+        escaped = (unsigned)ix >= (unsigned)NX() || (unsigned)iz >= (unsigned)NZ();
       }
     }
 
     // ---------------------------------------------------------------- cooperative deposit
-    unsigned pend = __ballot_sync(kFull, seg_pix >= 0);
+    unsigned pend = __ballot_sync(kFull, seg_key != 0u);
     if (pend) {
-      const unsigned same = __match_any_sync(kFull, seg_pix);
+      const unsigned same = __match_any_sync(kFull, seg_key);
       while (pend) {
         const int L = __ffs(pend) - 1;
         const unsigned grp = __shfl_sync(kFull, same, L) & pend;
-        const int pix = __shfl_sync(kFull, seg_pix, L);
+        const unsigned key = __shfl_sync(kFull, seg_key, L);
+        unsigned long long *dst = p.prob[key & 63u].tally + (size_t)((key >> 6) - 1u) * p.Cpad;
         long long acc[NP];
 #pragma unroll
         for (int q = 0; q < NP; ++q) acc[q] = 0;
@@ -259,9 +312,8 @@ __global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
         while (g) {
           const int M = __ffs(g) - 1;
           g &= g - 1;
-          // |t h 2^q| < 2^31 by the choice of q, so a 32-bit conversion suffices (the 64-bit one
-          // runs on the FP64 pipe, which is narrow on this part)
-          const float ts = __shfl_sync(kFull, seg_t, M) * p.qscale;
+          // |t h 2^q| < 2^31 by the choice of q, so a 32-bit conversion suffices
+          const float ts = __shfl_sync(kFull, seg_ts, M);
           const float *hr = rows + M * p.row_stride + 1;
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
@@ -269,7 +321,6 @@ __global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
             if (j < C) acc[q] += (long long)__float2int_rn(ts * hr[j]);
           }
         }
-        unsigned long long *dst = p.tally + (size_t)pix * p.Cpad;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
           const int j = q * 32 + lane;
@@ -298,9 +349,9 @@ __global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
           // (sp, cp) = (sin pi U, cos pi U): the same angle without tan's pole at U = 1/2.
           float sp, cp;
           sincospif(u01(cu1), &sp, &cp);
-          const float a = cp * cp, b = p.hg_c * p.hg_c * sp * sp;
+          const float a = cp * cp, b = HGC() * HGC() * sp * sp;
           const float inv = 1.f / (a + b);
-          const float cs = (a - b) * inv, sn = 2.f * p.hg_c * sp * cp * inv;
+          const float cs = (a - b) * inv, sn = 2.f * HGC() * sp * cp * inv;
           const float nsx = fmaf(sx, cs, sz * sn), nsz = fmaf(sz, cs, -sx * sn);
           const float rn = rsqrtf(fmaf(nsx, nsx, nsz * nsz));
           sx = nsx * rn;
@@ -362,40 +413,51 @@ __global__ void __launch_bounds__(128) k_transport(const TransportParams p) {
   }
 }
 
-template <int NP>
-cudaError_t launch_np(const TransportParams &p, cudaStream_t s) {
-  const size_t smem = transport_smem_bytes(p.row_stride);
-  static int configured_dev[64];  // smem attribute set once per device
+template <int NP, bool BATCH>
+cudaError_t launch_kernel(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s) {
+  const int threads = cfg.threads_per_block > 0 ? cfg.threads_per_block : 128;
+  if (threads % 32 || threads > 256) return cudaErrorInvalidValue;
+  const size_t smem = transport_smem_bytes(p.row_stride, threads);
+  static int configured[64];  // largest dynamic smem opted in, per device
   int dev = 0;
-  cudaGetDevice(&dev);
-  cudaError_t e = cudaSuccess;
-  if (dev < 64 && configured_dev[dev] != (int)smem + 1) {
-    e = cudaFuncSetAttribute(k_transport<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64 || configured[dev] < (int)smem) {
+    e = cudaFuncSetAttribute(k_transport<NP, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured_dev[dev] = (int)smem + 1;
+    if (dev < 64) configured[dev] = (int)smem;
   }
   int sms = 0, per_sm = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport<NP>, 128, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport<NP, BATCH>, threads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  k_transport<NP><<<sms * per_sm, 128, smem, s>>>(p);
+  if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < per_sm) per_sm = cfg.blocks_per_sm;
+  k_transport<NP, BATCH><<<sms * per_sm, threads, smem, s>>>(p);
   return cudaGetLastError();
+}
+
+// a table of one reads its problem as uniform parameters; larger tables cache it per lane
+template <int NP>
+cudaError_t launch_np(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s) {
+  return p.n_problems > 1 ? launch_kernel<NP, true>(p, cfg, s) : launch_kernel<NP, false>(p, cfg, s);
 }
 
 }  // namespace
 
-size_t transport_smem_bytes(int row_stride) { return (size_t)4 * 32 * row_stride * sizeof(float); }
+size_t transport_smem_bytes(int row_stride, int threads) {
+  return (size_t)threads * row_stride * sizeof(float);
+}
 
-cudaError_t launch_transport(const TransportParams &p, cudaStream_t s) {
+cudaError_t launch_transport(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s) {
   const int np = (p.C + 31) / 32;
   switch (np) {
-    case 1: return launch_np<1>(p, s);
-    case 2: return launch_np<2>(p, s);
-    case 3: return launch_np<3>(p, s);
-    case 4: return launch_np<4>(p, s);
-    case 5: return launch_np<5>(p, s);
+    case 1: return launch_np<1>(p, cfg, s);
+    case 2: return launch_np<2>(p, cfg, s);
+    case 3: return launch_np<3>(p, cfg, s);
+    case 4: return launch_np<4>(p, cfg, s);
+    case 5: return launch_np<5>(p, cfg, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -25,8 +25,10 @@ MAX_K = 64
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_EVENT_LIMIT, ERR_TALLY_OVERFLOW, ERR_MEDIUM = 0, -1, -2, -3, -4, -5, -6
 
 # every symbol declared in include/mcr.h
-EXPORTS = ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_h_eps", "mc_adjoint_source", "mc_gradient",
-           "mc_check", "mc_last_run_info", "mc_release_workspace", "mc_status_string", "mc_version")
+EXPORTS = ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_run_batch", "mc_h_eps", "mc_eps",
+           "mc_adjoint_source", "mc_gradient", "mc_gradient_f32", "mc_check", "mc_last_run_info",
+           "mc_release_workspace", "mc_status_string", "mc_version")
+MAX_BATCH = 64
 ERR_SCRATCH = -7
 
 
@@ -50,6 +52,15 @@ class _Run(C.Structure):
     _fields_ = [("K", C.c_int32), ("max_scatter", C.c_uint32), ("n_packets", C.c_uint64),
                 ("first_packet", C.c_uint64), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
                 ("max_events", C.c_uint32), ("w_threshold", C.c_float), ("roulette_p", C.c_float)]
+
+
+class _Problem(C.Structure):
+    _fields_ = [("medium", _Medium), ("source", _Source), ("qstar", C.c_void_p), ("n_packets", C.c_uint64),
+                ("first_packet", C.c_uint64), ("seed", C.c_uint64), ("stream_id", C.c_uint32), ("coeff", C.c_void_p)]
+
+
+class _Launch(C.Structure):
+    _fields_ = [("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -79,9 +90,13 @@ def load() -> C.CDLL:
         lib.mc_forward.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
         lib.mc_forward_noalloc.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run), vp, vp]
         lib.mc_adjoint.argtypes = [C.POINTER(_Medium), vp, C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
+        lib.mc_run_batch.argtypes = [C.POINTER(_Problem), C.c_int32, C.POINTER(_Run), C.POINTER(_Launch),
+                                     C.POINTER(_Stats), vp]
         lib.mc_h_eps.argtypes = [C.POINTER(_Medium), vp, vp, vp, vp, vp, vp]
         lib.mc_adjoint_source.argtypes = [C.POINTER(_Medium), vp, vp, vp]
         lib.mc_gradient.argtypes = [C.POINTER(_Medium), C.c_int32, vp, vp, vp, vp, vp, vp]
+        lib.mc_gradient_f32.argtypes = [C.POINTER(_Medium), C.c_int32, vp, vp, vp, vp, vp, vp]
+        lib.mc_eps.argtypes = [C.c_int64, C.c_double, vp, vp, vp, vp, vp]
         lib.mc_check.argtypes = [vp]
         lib.mc_last_run_info.argtypes = [C.c_int32, C.POINTER(_Stats), C.POINTER(C.c_float)]
         lib.mc_release_workspace.argtypes = []
@@ -89,8 +104,9 @@ def load() -> C.CDLL:
         lib.mc_status_string.restype = C.c_char_p
         lib.mc_version.argtypes = []
         lib.mc_version.restype = C.c_char_p
-        for name in ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_h_eps", "mc_adjoint_source",
-                     "mc_gradient", "mc_check", "mc_last_run_info", "mc_release_workspace"):
+        for name in ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_run_batch", "mc_h_eps", "mc_eps",
+                     "mc_adjoint_source", "mc_gradient", "mc_gradient_f32", "mc_check", "mc_last_run_info",
+                     "mc_release_workspace"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
         return lib
@@ -225,6 +241,57 @@ def adjoint(med: Medium, qstar: torch.Tensor, run: Run, out=None, stats: bool = 
     return (coeff, _stats_dict(st)) if stats else coeff
 
 
+@dataclass
+class Problem:
+    """One problem of a batched launch: a forward source (``source``) or an adjoint q* (``qstar``)."""
+    medium: Medium
+    n_packets: int
+    seed: int = 0
+    stream_id: int = 0
+    first_packet: int = 0
+    source: Source | None = None
+    qstar: torch.Tensor | None = None
+    out: torch.Tensor | None = None
+
+    def c(self, K: int) -> _Problem:
+        if (self.source is None) == (self.qstar is None):
+            raise ValueError("a problem has exactly one of source / qstar")
+        if self.out is None:
+            self.out = torch.empty((2 * K + 1,) + self.medium.shape, dtype=torch.float32,
+                                   device=self.medium.mua.device)
+        _dev_f32(self.out, "out")
+        if tuple(self.out.shape) != (2 * K + 1,) + self.medium.shape:
+            raise ValueError("out must be [2K+1, nz, nx]")
+        if self.qstar is not None:
+            _dev_f32(self.qstar, "qstar")
+            if tuple(self.qstar.shape) != self.medium.shape:
+                raise ValueError("qstar must have the medium's shape")
+        src = self.source.c() if self.source is not None else _Source()
+        return _Problem(self.medium.c(), src, self.qstar.data_ptr() if self.qstar is not None else None,
+                        int(self.n_packets), int(self.first_packet), int(self.seed) & 0xFFFFFFFFFFFFFFFF,
+                        int(self.stream_id), self.out.data_ptr())
+
+
+def run_batch(problems: list, common: Run, launch: tuple | None = None, stats: bool = False, stream=None):
+    """All ``problems`` in one persistent transport launch (``mc_run_batch``); returns their outputs.
+
+    ``common`` gives K and the termination parameters; ``launch`` = (threads_per_block,
+    blocks_per_sm) or None for the defaults.  The call can be captured in a CUDA graph once a
+    first call has grown the library's workspace to this batch's size.
+    """
+    lib = load()
+    if not 1 <= len(problems) <= MAX_BATCH:
+        raise ValueError(f"1..{MAX_BATCH} problems per batch")
+    arr = (_Problem * len(problems))(*[p.c(common.K) for p in problems])
+    ln = _Launch(*launch) if launch is not None else None
+    st = _Stats() if stats else None
+    rc = lib.mc_run_batch(arr, len(problems), C.byref(common.c()), C.byref(ln) if ln is not None else None,
+                          C.byref(st) if st is not None else None, _stream(stream))
+    _check(rc, "mc_run_batch")
+    outs = [p.out for p in problems]
+    return (outs, _stats_dict(st)) if stats else outs
+
+
 def h_eps(med: Medium, coeff: torch.Tensor, Hmeas: torch.Tensor | None = None, stream=None):
     """H = mu_a a_0; with Hmeas also dL/dH = -dx^2 (Hmeas - H) and eps (``mc_h_eps``).
 
@@ -253,19 +320,40 @@ def adjoint_source(med: Medium, dL_dH: torch.Tensor, stream=None) -> torch.Tenso
     return q
 
 
-def gradient(med: Medium, coeff: torch.Tensor, coeff_adj: torch.Tensor, dL_dH: torch.Tensor, stream=None):
-    """(dL/dmu_a, dL/dmu_s) per pixel in float64 (``mc_gradient``, Eqs. 22 and 28 x dx^2)."""
+def gradient(med: Medium, coeff: torch.Tensor, coeff_adj: torch.Tensor, dL_dH: torch.Tensor, stream=None,
+             dtype=torch.float64):
+    """(dL/dmu_a, dL/dmu_s) per pixel (``mc_gradient`` / ``mc_gradient_f32``, Eqs. 22 and 28 x dx^2).
+
+    The sums run in FP64 either way; ``dtype`` float32 rounds the results once on output.
+    """
     lib = load()
     for t, n in ((coeff, "coeff"), (coeff_adj, "coeff_adj"), (dL_dH, "dL_dH")):
         _dev_f32(t, n)
     K = (coeff.shape[0] - 1) // 2
     if coeff.shape != coeff_adj.shape:
         raise ValueError("coeff and coeff_adj must match")
-    d_mua = torch.empty(med.shape, dtype=torch.float64, device=coeff.device)
+    d_mua = torch.empty(med.shape, dtype=dtype, device=coeff.device)
     d_mus = torch.empty_like(d_mua)
-    _check(lib.mc_gradient(C.byref(med.c()), K, _ptr(coeff), _ptr(coeff_adj), _ptr(dL_dH), _ptr(d_mua), _ptr(d_mus),
-                           _stream(stream)), "mc_gradient")
+    fn, name = (lib.mc_gradient, "mc_gradient") if dtype == torch.float64 else (lib.mc_gradient_f32, "mc_gradient_f32")
+    if dtype not in (torch.float64, torch.float32):
+        raise TypeError("dtype must be float64 or float32")
+    _check(fn(C.byref(med.c()), K, _ptr(coeff), _ptr(coeff_adj), _ptr(dL_dH), _ptr(d_mua), _ptr(d_mus),
+              _stream(stream)), name)
     return d_mua, d_mus
+
+
+def eps(H: torch.Tensor, Hmeas: torch.Tensor, dx: float, stream=None):
+    """eps = 1/2 dx^2 sum (Hmeas - H)^2 (FP64) and dL/dH = -dx^2 (Hmeas - H) from a given H (``mc_eps``)."""
+    lib = load()
+    _dev_f32(H, "H")
+    _dev_f32(Hmeas, "Hmeas")
+    if H.shape != Hmeas.shape:
+        raise ValueError("H and Hmeas must match")
+    v = torch.empty_like(H)
+    e = torch.empty((), dtype=torch.float64, device=H.device)
+    d32 = C.c_float(dx).value  # the pixel side as the medium struct carries it (FP32)
+    _check(lib.mc_eps(H.numel(), d32 * d32, _ptr(H), _ptr(Hmeas), _ptr(v), _ptr(e), _stream(stream)), "mc_eps")
+    return e, v
 
 
 def check(stream=None):
@@ -274,10 +362,11 @@ def check(stream=None):
 
 
 def last_run_info(which: str = "forward"):
-    """(stats dict, transport kernel ms) of the last forward / adjoint call (``mc_last_run_info``)."""
+    """(stats dict, transport kernel ms) of the last forward / adjoint / batch call (``mc_last_run_info``)."""
     st = _Stats()
     ms = C.c_float(0.0)
-    _check(load().mc_last_run_info(0 if which == "forward" else 1, C.byref(st), C.byref(ms)), "mc_last_run_info")
+    code = {"forward": 0, "adjoint": 1, "batch": 2}[which]
+    _check(load().mc_last_run_info(code, C.byref(st), C.byref(ms)), "mc_last_run_info")
     return _stats_dict(st), float(ms.value)
 
 

@@ -123,6 +123,32 @@ def large1024(n_packets: int = 1_000_000_000) -> Workload:
                     mua_true=mua_t, mus_true=mus_t, seed=0, meta=dict(hmeas_seed=1001))
 
 
+def batch64(n_packets: int = 1_000_000, extent_mm: float = 12.8):
+    """64 forward problems: 16 collimated line sources (4 per edge, each a quarter of the edge,
+    pointing inward) x 4 wavelengths, on grids of 128^2 / 256^2 / 512^2 pixels taken round-robin
+    over the problems at a fixed extent.  mu_a and mu_s are lognormal Gaussian random fields
+    (sigma 0.5, correlation 1 mm, seed = problem index) around 0.01 and 10 /mm, scaled per
+    wavelength by (0.5, 1, 1.5, 2) and (1.2, 1.0, 0.9, 0.8); g = 0.9; K = 16.
+
+    Returns a list of dicts: nx, dx, mua, mus, g, source, n_packets, seed, stream_id.
+    """
+    sizes = (128, 256, 512)
+    a_scale = (0.5, 1.0, 1.5, 2.0)
+    s_scale = (1.2, 1.0, 0.9, 0.8)
+    out = []
+    for i in range(64):
+        n = sizes[i % 3]
+        dx = extent_mm / n
+        srcs = edge_line_sources(n, dx, per_edge=4)
+        src = srcs[(i // 4) % 16]
+        wl = i % 4
+        mua = lognormal_field(n, dx, 0.01, 0.5, 1.0, seed=i) * a_scale[wl]
+        mus = lognormal_field(n, dx, 10.0, 0.5, 1.0, seed=1000 + i) * s_scale[wl]
+        out.append(dict(nx=n, dx=dx, mua=mua.astype(np.float32), mus=mus.astype(np.float32), g=0.9,
+                        source=src, n_packets=n_packets, seed=0, stream_id=2 * i))
+    return out
+
+
 def small_hetero(nz: int, nx: int, dx: float, seed: int):
     """Heterogeneous test medium: smooth background plus two rectangles (parity tests)."""
     rng = np.random.default_rng(seed)

@@ -1,0 +1,121 @@
+"""Batched persistent launch (mc_run_batch), CUDA-graph replay and the autotuner."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import RunParams
+from paper_1608_05238_gb300 import _build, batch, mcr, workloads
+from parity_util import assert_parity, f32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    _build.build()
+    mcr.load()
+
+
+def _medium(nz, nx, dx, g, seed):
+    mua, mus = workloads.small_hetero(nz, nx, dx, seed=seed)
+    return mcr.Medium(torch.from_numpy(mua).cuda(), torch.from_numpy(mus).cuda(), f32(dx), f32(g)), mua, mus
+
+
+def _mixed_problems(K):
+    """Forward and adjoint problems on uneven grids with different sources and packet counts."""
+    probs, meta = [], []
+    shapes = [(40, 56, 0.1), (33, 33, 0.05), (64, 24, 0.08), (17, 90, 0.12), (50, 50, 0.07)]
+    for i, (nz, nx, dx) in enumerate(shapes):
+        med, mua, mus = _medium(nz, nx, dx, 0.6 + 0.05 * i, seed=30 + i)
+        n = 20_000 + 7_777 * i
+        if i % 2 == 0:
+            kinds = [mcr.Source(mcr.LINE, x0=0.0, z0=0.0, x1=f32(nx * dx), z1=0.0, dir_x=0.0, dir_z=1.0),
+                     mcr.Source(mcr.ISO_POINT, x0=f32(0.37 * nx * dx), z0=f32(0.61 * nz * dx), power=2.0),
+                     mcr.Source(mcr.PENCIL, x0=f32(0.5 * nx * dx), z0=0.0, dir_x=0.3, dir_z=0.9)]
+            p = mcr.Problem(med, n, seed=5 + i, stream_id=2 * i, source=kinds[(i // 2) % 3])
+        else:
+            q = np.random.default_rng(i).normal(size=(nz, nx)).astype(np.float32)
+            q[np.random.default_rng(i + 9).uniform(size=q.shape) < 0.5] = 0
+            p = mcr.Problem(med, n, seed=5 + i, stream_id=2 * i + 1, qstar=torch.from_numpy(q).cuda())
+        probs.append(p)
+        meta.append((mua, mus))
+    return probs, meta
+
+
+def test_batch_equals_separate_calls_bit_for_bit():
+    K = 16
+    common = mcr.Run(K=K, n_packets=0)
+    probs, _ = _mixed_problems(K)
+    outs, st = mcr.run_batch(probs, common, stats=True)
+    assert st["launched"] == sum(p.n_packets for p in probs)
+    for p, o in zip(probs, outs):
+        run = mcr.Run(K=K, n_packets=p.n_packets, seed=p.seed, stream_id=p.stream_id)
+        ref = mcr.forward(p.medium, p.source, run) if p.source is not None else mcr.adjoint(p.medium, p.qstar, run)
+        assert torch.equal(o, ref)
+
+
+def test_batch_problem_matches_oracle():
+    K = 16
+    common = mcr.Run(K=K, n_packets=0)
+    probs, meta = _mixed_problems(K)
+    outs = mcr.run_batch(probs, common)
+    for i in (0, 3):
+        p, (mua, mus) = probs[i], meta[i]
+        rp = RunParams(K=K, n_packets=p.n_packets, seed=p.seed, stream_id=p.stream_id)
+        args = (mua.astype(np.float64), mus.astype(np.float64), p.medium.dx, p.medium.g)
+        if p.source is not None:
+            O = oracle.forward(*args, p.source.as_dict(), rp, with_variance=True)
+            A, sig = O.coeff[0], np.sqrt(O.a0_var)
+        else:
+            q = p.qstar.cpu().numpy()
+            O = oracle.adjoint(*args, q, rp)
+            Oa = oracle.adjoint(*args, np.abs(q), rp, with_variance=True)
+            A, sig = Oa.coeff[0], np.sqrt(Oa.a0_var)
+        assert_parity(outs[i].double().cpu().numpy(), O.coeff, A, sig, label=f"batch problem {i}")
+
+
+def test_launch_shape_does_not_change_results_and_autotuner_picks_one():
+    K = 8
+    common = mcr.Run(K=K, n_packets=0)
+    probs, _ = _mixed_problems(K)
+    ref = [o.clone() for o in mcr.run_batch(probs, common)]
+    for shape in ((64, 0), (256, 1), (96, 3)):
+        outs = mcr.run_batch(probs, common, launch=shape)
+        assert all(torch.equal(a, b) for a, b in zip(outs, ref))
+    choice = batch.autotune(probs, common, reps=1)
+    assert choice in batch.DEFAULT_CANDIDATES
+
+
+def test_graph_replay_reproduces_eager_run():
+    K = 16
+    common = mcr.Run(K=K, n_packets=0)
+    probs, _ = _mixed_problems(K)
+    runner = batch.BatchRunner(probs, common)
+    eager = [o.clone() for o in runner.run()]
+    runner.capture()
+    for o in runner.outputs:
+        o.fill_(float("nan"))
+    runner.replay()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(runner.outputs, eager))
+    runner.recapture(seed=77)
+    runner.replay()
+    torch.cuda.synchronize()
+    assert not torch.equal(runner.outputs[0], eager[0])  # a new ensemble
+
+
+def test_batch_limits():
+    K = 4
+    common = mcr.Run(K=K, n_packets=0)
+    med, _, _ = _medium(8, 8, 0.1, 0.5, seed=1)
+    src = mcr.Source(mcr.PENCIL, x0=0.4)
+    with pytest.raises(ValueError):
+        mcr.run_batch([mcr.Problem(med, 10, source=src)] * 65, common)
+    with pytest.raises(mcr.McrError):
+        mcr.run_batch([mcr.Problem(med, (1 << 26) + 1, source=src)], common)
+    outs = mcr.run_batch([mcr.Problem(med, 0, source=src), mcr.Problem(med, 1000, source=src)], common)
+    assert torch.count_nonzero(outs[0]) == 0 and torch.count_nonzero(outs[1]) > 0
+    probs = [mcr.Problem(med, 100, seed=i, source=src) for i in range(64)]
+    outs = mcr.run_batch(probs, common)
+    assert all(torch.count_nonzero(o) > 0 for o in outs)
