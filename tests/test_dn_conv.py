@@ -1,0 +1,85 @@
+"""Tensor-core convolution (dn_conv) against a plain PyTorch CPU convolution of the same bf16 data."""
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as Fnn
+
+from paper_1608_05238_gb300 import _build, denoise_ops as ops
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    _build.build()
+    ops.lib()
+
+
+def _ref(x, w, cin, cout, taps, bias=None, relu=False, mask=None, mask_off=0):
+    """CPU fp64 reference: NHWC bf16 input / [n_pad][taps][cin_pad] weights -> NHWC fp64."""
+    xc = x.double().cpu()[..., :cin].permute(0, 3, 1, 2)
+    k = 3 if taps == 9 else 1
+    wc = w.double().cpu()[:cout, :, :cin].reshape(cout, k, k, cin).permute(0, 3, 1, 2)
+    y = Fnn.conv2d(xc, wc, padding=k // 2).permute(0, 2, 3, 1)
+    if bias is not None:
+        y = y + bias.double().cpu()
+    if relu:
+        y = y.clamp_min(0)
+    if mask is not None:
+        y = y * (mask.double().cpu()[..., mask_off:mask_off + cout] > 0)
+    return y
+
+
+def _case(B, H, W, cin, cout, taps, seed, cin_pad=None, n_pad=None):
+    g = torch.Generator().manual_seed(seed)
+    cin_pad = cin_pad or ((cin + 63) // 64) * 64
+    n_pad = n_pad or ((cout + 15) // 16) * 16
+    x = torch.zeros(B, H, W, cin_pad)
+    x[..., :cin] = torch.randn(B, H, W, cin, generator=g)
+    w = torch.zeros(n_pad, taps, cin_pad)
+    w[:cout, :, :cin] = torch.randn(cout, taps, cin, generator=g) / np.sqrt(taps * cin)
+    return x.bfloat16().cuda(), w.bfloat16().cuda(), cin_pad, n_pad
+
+
+@pytest.mark.parametrize("B,H,W,cin,cout,taps", [
+    (1, 4, 32, 64, 16, 1),     # one tile, plain GEMM
+    (2, 16, 32, 64, 32, 9),    # 3x3, several tiles of 4 rows
+    (1, 2, 256, 128, 64, 9),   # rows of 256 pixels: two tiles per row, two channel blocks
+    (1, 8, 64, 64, 256, 9),    # N = 256
+    (3, 8, 128, 33, 48, 9),    # padded input channels
+])
+def test_conv_fp32_output_matches_reference(B, H, W, cin, cout, taps):
+    x, w, cin_pad, n_pad = _case(B, H, W, cin, cout, taps, seed=B * 100 + H + W + cout)
+    out = torch.full((B, H, W, ((cout + 7) // 8) * 8), float("nan"), device="cuda")
+    ops.conv(x, w, cout, out, taps=taps)
+    ops.check()
+    ref = _ref(x, w, cin, cout, taps)
+    got = out[..., :cout].double().cpu()
+    assert torch.allclose(got, ref, rtol=1e-4, atol=1e-4 * ref.abs().max().item())
+
+
+def test_conv_bias_relu_bf16_slice_and_mask():
+    B, H, W, cin, cout = 2, 8, 64, 96, 40
+    x, w, cin_pad, n_pad = _case(B, H, W, cin, cout, 9, seed=7)
+    bias = torch.randn(cout).cuda()
+    out = torch.zeros(B, H, W, 128, dtype=torch.bfloat16, device="cuda")
+    ops.conv(x, w, cout, out, bias=bias, relu=True, out_off=64)
+    ref = _ref(x, w, cin, cout, 9, bias=bias, relu=True)
+    got = out[..., 64:64 + cout].double().cpu()
+    assert torch.allclose(got, ref, rtol=2 ** -7, atol=1e-3)
+    assert torch.count_nonzero(out[..., :64]) == 0 and torch.count_nonzero(out[..., 64 + cout:]) == 0
+    mask = torch.randn(B, H, W, 64).bfloat16().cuda()
+    out2 = torch.zeros(B, H, W, cout + (8 - cout % 8) % 8, device="cuda")
+    ops.conv(x, w, cout, out2, mask=mask, mask_off=8)
+    ops.check()
+    ref2 = _ref(x, w, cin, cout, 9, mask=mask, mask_off=8)
+    assert torch.allclose(out2[..., :cout].double().cpu(), ref2, rtol=1e-4, atol=1e-4 * ref2.abs().max().item())
+
+
+def test_conv_rejects_bad_shapes():
+    x, w, _, _ = _case(1, 4, 32, 64, 16, 9, seed=1)
+    out = torch.zeros(1, 4, 32, 16, device="cuda")
+    with pytest.raises(Exception):
+        ops.conv(x[:, :, :16].contiguous(), w, 16, out[:, :, :16].contiguous())  # W < 32
+    with pytest.raises(Exception):
+        ops.conv(x, w, 16, torch.zeros(1, 4, 32, 12, device="cuda"))  # out stride not a multiple of 8
