@@ -13,7 +13,7 @@
  * bf16 (taps = 9 for 3x3, 1 for 1x1), N_pad = output channels rounded up to 16; bias fp32 [C].
  * All pointers are device pointers; every call is asynchronous on `stream` and returns 0 or a
  * negative status (same codes as mcr.h).  Requirements of the convolutions: W a power of two,
- * 32 <= W, H*W a multiple of 128, N_pad <= 256.
+ * 16 <= W, H*W a multiple of 128, N_pad <= 256.
  */
 #ifndef MCR_DENOISE_H
 #define MCR_DENOISE_H
@@ -49,6 +49,61 @@ typedef struct {
  * shape requirements above are not met.
  */
 int dn_conv(const dn_conv_desc *d, void *stream);
+
+/*
+ * dn_wgrad -- weight gradient of a convolution on the tensor cores:
+ *   dw[n][tap][c] += sum_{b, pixel} dz[b, pixel][n] x[b, pixel + tap][c]     (FP32 accumulate)
+ * with the operands in pixel-contiguous ("transposed") layouts made by dn_to_ct: dzT
+ * [cout][B][H*W] and xT = three x-shifted copies [3][cin][B][H*W].  dw is fp32
+ * [cout][taps][cin] and is ADDED to (zero it first); partial sums of split reductions are added
+ * with atomics, so the last bits depend on scheduling.  Requires W >= 16 a power of two and
+ * H*W a multiple of 64; cout, cin <= 512.
+ */
+int dn_wgrad(int32_t B, int32_t H, int32_t W, int32_t taps, int32_t cout, int32_t cin, const void *dzT,
+             const void *xT, float *dw, void *stream);
+
+/* NHWC bf16 slice (data + channel stride + channel offset). */
+typedef struct {
+  void *data;
+  int32_t stride, off;
+} dn_slice;
+
+/* dst[c][b][p] = src[b][p][off + c] for c < C (bf16); shifted = 1 writes three copies
+ * (dst + k*C*B*HW) with x shifted by k - 1 and zeros outside the row. */
+int dn_to_ct(dn_slice src, int32_t B, int32_t H, int32_t W, int32_t C, int32_t shifted, void *dst, void *stream);
+/* 2x2 average pooling of an H x W slice into an (H/2) x (W/2) slice. */
+int dn_pool2(dn_slice src, int32_t B, int32_t H, int32_t W, int32_t C, dn_slice dst, void *stream);
+/* dz = (skip + pool2-backward(dp)) * (act > 0) on the H x W grid (skip may have data NULL). */
+int dn_pool2_bwd(dn_slice dp, dn_slice skip, dn_slice act, int32_t B, int32_t H, int32_t W, int32_t C, dn_slice dz,
+                 void *stream);
+/* nearest 2x up-sampling of an H x W slice into a 2H x 2W slice. */
+int dn_up2(dn_slice src, int32_t B, int32_t H, int32_t W, int32_t C, dn_slice dst, void *stream);
+/* dz (H x W) = 2x2 sums of du (2H x 2W) times (act > 0). */
+int dn_up2_bwd(dn_slice du, dn_slice act, int32_t B, int32_t H, int32_t W, int32_t C, dn_slice dz, void *stream);
+/* db[c] += sum over the B*H*W pixels of dz[., off + c]. */
+int dn_bias_grad(dn_slice dz, int64_t pixels, int32_t C, float *db, void *stream);
+/* Residual MSE over C channels of P pixels: y = x + out, loss = mean (y - t)^2 (FP64, fixed
+ * order), dout = 2 (y - t) / (P C) as bf16 NHWC (stride dstride).  out fp32 [P][ostride], x bf16
+ * [P][xstride], t fp32 [P][C]. */
+int dn_mse(const float *out, int32_t ostride, const void *x, int32_t xstride, const float *t, int64_t P, int32_t C,
+           void *dout, int32_t dstride, double *loss, void *stream);
+/* y = x + out over C channels (fp32 [P][C]). */
+int dn_residual(const float *out, int32_t ostride, const void *x, int32_t xstride, int64_t P, int32_t C, float *y,
+                void *stream);
+/* Adam step `step` (>= 1; 0 only refreshes the bf16 copies) on fp32 master weights [cout][taps][cin] with
+ * gradient g, which it then sets to zero (the next backward pass accumulates into it); writes wf bf16
+ * [n_pad][taps][cin_pad] and, if wd != NULL, the flipped input-gradient copy wd bf16
+ * [cin_npad][taps][cout_pad] (wd[c][taps-1-t][n] = w[n][t][c]). */
+int dn_adam(float *w, float *m, float *v, float *g, int32_t cout, int32_t taps, int32_t cin, float lr, float beta1,
+            float beta2, float eps, int32_t step, void *wf, int32_t cin_pad, void *wd, int32_t cout_pad, void *stream);
+int dn_adam_bias(float *b, float *m, float *v, float *g, int32_t n, float lr, float beta1, float beta2, float eps,
+                 int32_t step, void *stream);
+/* channel-major fp32 maps [B][C][HW] times scale[b] -> NHWC bf16 [B][HW][stride] (input) or NHWC
+ * fp32 [B][HW][C] (target); and back (output / scale). */
+int dn_pack_input(const float *src, const float *scale, int32_t B, int64_t HW, int32_t C, void *dst, int32_t stride,
+                  void *stream);
+int dn_pack_target(const float *src, const float *scale, int32_t B, int64_t HW, int32_t C, float *dst, void *stream);
+int dn_unpack_output(const float *src, const float *scale, int32_t B, int64_t HW, int32_t C, float *dst, void *stream);
 
 /* Device error word of the denoiser kernels (a bounded wait that gave up); read and clear.
  * Synchronises `stream`. */

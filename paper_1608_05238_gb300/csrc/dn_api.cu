@@ -57,8 +57,21 @@ unsigned *error_word() {
   return g_err[dev];
 }
 
+double *partials_buffer() {
+  static double *g_partials[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_partials[dev]) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, 4096 * sizeof(double)) != cudaSuccess) return nullptr;
+    g_partials[dev] = static_cast<double *>(p);
+  }
+  return g_partials[dev];
+}
+
 bool conv_shape_ok(int B, int H, int W) {
-  if (B <= 0 || H <= 0 || W < 32 || (W & (W - 1))) return false;
+  if (B <= 0 || H <= 0 || W < 16 || (W & (W - 1))) return false;
   if (((long long)H * W) % 128) return false;
   return true;
 }
@@ -126,6 +139,152 @@ int dn_conv(const dn_conv_desc *d, void *stream) {
   a.err = err;
   if (launch_conv_tc(tmX, tmW, a, (cudaStream_t)stream) != cudaSuccess) return MCR_ERR_CUDA;
   return MCR_OK;
+}
+
+int dn_wgrad(int32_t B, int32_t H, int32_t W, int32_t taps, int32_t cout, int32_t cin, const void *dzT,
+             const void *xT, float *dw, void *stream) {
+  if (!dzT || !xT || !dw || (taps != 9 && taps != 1)) return MCR_ERR_ARG;
+  if (B <= 0 || H <= 0 || W < 16 || (W & (W - 1)) || ((long long)H * W) % 64) return MCR_ERR_ARG;
+  if (cout < 1 || cin < 1 || cout > 512 || cin > 512) return MCR_ERR_ARG;
+  unsigned *err = error_word();
+  if (!err) return MCR_ERR_CUDA;
+  const uint64_t HW = (uint64_t)H * W;
+  CUtensorMap tmA, tmB[3];
+  {
+    const uint64_t dims[3] = {HW, (uint64_t)B, (uint64_t)cout};
+    const uint64_t strides[2] = {HW * 2, (uint64_t)B * HW * 2};
+    const uint32_t box[3] = {64, 1, 128};
+    if (encode_tiled(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(dzT), dims, strides, box,
+                     CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+      return MCR_ERR_CUDA;
+  }
+  const int N = cin > 128 ? 128 : ((cin + 15) / 16) * 16;
+  for (int k = 0; k < 3; ++k) {
+    const uint64_t dims[3] = {HW, (uint64_t)B, (uint64_t)cin};
+    const uint64_t strides[2] = {HW * 2, (uint64_t)B * HW * 2};
+    const uint32_t box[3] = {64, 1, (uint32_t)N};
+    void *base = static_cast<char *>(const_cast<void *>(xT)) + (size_t)k * cin * B * HW * 2;
+    if (encode_tiled(&tmB[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
+                     CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+      return MCR_ERR_CUDA;
+  }
+  WgradArgs a{};
+  a.B = B;
+  a.HW = (int)HW;
+  a.W = W;
+  a.taps = taps;
+  a.cout = cout;
+  a.cin = cin;
+  a.cin_pad = cin;
+  a.N = N;
+  a.m_tiles = (cout + 127) / 128;
+  a.n_tiles = (cin + N - 1) / N;
+  const long long kblocks = (long long)B * HW / 64;
+  long long splits = (2 * 152 + taps * a.m_tiles * a.n_tiles - 1) / (taps * a.m_tiles * a.n_tiles);
+  if (splits > kblocks) splits = kblocks;
+  if (splits < 1) splits = 1;
+  a.splits = (int)splits;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)N) cols <<= 1;
+  a.tmem_cols = cols;
+  a.dw = dw;
+  a.err = err;
+  if (launch_wgrad_tc(tmA, tmB, a, (cudaStream_t)stream) != cudaSuccess) return MCR_ERR_CUDA;
+  return MCR_OK;
+}
+
+#define DN_TRY(expr) return (expr) == cudaSuccess ? MCR_OK : MCR_ERR_CUDA
+
+static bool slice_ok(const dn_slice &s, int C) { return s.data && s.off >= 0 && s.off + C <= s.stride; }
+
+int dn_to_ct(dn_slice src, int32_t B, int32_t H, int32_t W, int32_t C, int32_t shifted, void *dst, void *stream) {
+  if (!slice_ok(src, C) || !dst || B <= 0 || H <= 0 || W <= 0 || C <= 0) return MCR_ERR_ARG;
+  DN_TRY(to_ct(static_cast<const __nv_bfloat16 *>(src.data), B, H * W, W, src.stride, src.off, C, shifted,
+               static_cast<__nv_bfloat16 *>(dst), (cudaStream_t)stream));
+}
+
+int dn_pool2(dn_slice src, int32_t B, int32_t H, int32_t W, int32_t C, dn_slice dst, void *stream) {
+  if (!slice_ok(src, C) || !slice_ok(dst, C) || B <= 0 || H < 2 || W < 2 || H % 2 || W % 2) return MCR_ERR_ARG;
+  DN_TRY(pool2(static_cast<const __nv_bfloat16 *>(src.data), B, H, W, src.stride, src.off, C,
+               static_cast<__nv_bfloat16 *>(dst.data), dst.stride, dst.off, (cudaStream_t)stream));
+}
+
+int dn_pool2_bwd(dn_slice dp, dn_slice skip, dn_slice act, int32_t B, int32_t H, int32_t W, int32_t C, dn_slice dz,
+                 void *stream) {
+  if (!slice_ok(dp, C) || !slice_ok(act, C) || !slice_ok(dz, C) || (skip.data && !slice_ok(skip, C))) return MCR_ERR_ARG;
+  if (B <= 0 || H < 2 || W < 2 || H % 2 || W % 2) return MCR_ERR_ARG;
+  DN_TRY(pool2_bwd(static_cast<const __nv_bfloat16 *>(dp.data), dp.stride, dp.off,
+                   static_cast<const __nv_bfloat16 *>(skip.data), skip.stride, skip.off,
+                   static_cast<const __nv_bfloat16 *>(act.data), act.stride, act.off, B, H, W, C,
+                   static_cast<__nv_bfloat16 *>(dz.data), dz.stride, dz.off, (cudaStream_t)stream));
+}
+
+int dn_up2(dn_slice src, int32_t B, int32_t H, int32_t W, int32_t C, dn_slice dst, void *stream) {
+  if (!slice_ok(src, C) || !slice_ok(dst, C) || B <= 0 || H <= 0 || W <= 0) return MCR_ERR_ARG;
+  DN_TRY(up2(static_cast<const __nv_bfloat16 *>(src.data), B, H, W, src.stride, src.off, C,
+             static_cast<__nv_bfloat16 *>(dst.data), dst.stride, dst.off, (cudaStream_t)stream));
+}
+
+int dn_up2_bwd(dn_slice du, dn_slice act, int32_t B, int32_t H, int32_t W, int32_t C, dn_slice dz, void *stream) {
+  if (!slice_ok(du, C) || !slice_ok(act, C) || !slice_ok(dz, C) || B <= 0 || H <= 0 || W <= 0) return MCR_ERR_ARG;
+  DN_TRY(up2_bwd(static_cast<const __nv_bfloat16 *>(du.data), du.stride, du.off,
+                 static_cast<const __nv_bfloat16 *>(act.data), act.stride, act.off, B, H, W, C,
+                 static_cast<__nv_bfloat16 *>(dz.data), dz.stride, dz.off, (cudaStream_t)stream));
+}
+
+int dn_bias_grad(dn_slice dz, int64_t pixels, int32_t C, float *db, void *stream) {
+  if (!slice_ok(dz, C) || !db || pixels <= 0) return MCR_ERR_ARG;
+  DN_TRY(bias_grad(static_cast<const __nv_bfloat16 *>(dz.data), pixels, dz.stride, dz.off, C, db,
+                   (cudaStream_t)stream));
+}
+
+int dn_mse(const float *out, int32_t ostride, const void *x, int32_t xstride, const float *t, int64_t P, int32_t C,
+           void *dout, int32_t dstride, double *loss, void *stream) {
+  if (!out || !x || !t || !dout || !loss || P <= 0 || C <= 0 || ostride < C || xstride < C || dstride < C)
+    return MCR_ERR_ARG;
+  double *partials = partials_buffer();
+  if (!partials) return MCR_ERR_CUDA;
+  DN_TRY(mse(out, ostride, static_cast<const __nv_bfloat16 *>(x), xstride, t, P, C, static_cast<__nv_bfloat16 *>(dout),
+             dstride, partials, 4096, loss, (cudaStream_t)stream));
+}
+
+int dn_residual(const float *out, int32_t ostride, const void *x, int32_t xstride, int64_t P, int32_t C, float *y,
+                void *stream) {
+  if (!out || !x || !y || P <= 0 || C <= 0 || ostride < C || xstride < C) return MCR_ERR_ARG;
+  DN_TRY(residual(out, ostride, static_cast<const __nv_bfloat16 *>(x), xstride, P, C, y, (cudaStream_t)stream));
+}
+
+int dn_adam(float *w, float *m, float *v, float *g, int32_t cout, int32_t taps, int32_t cin, float lr,
+            float beta1, float beta2, float eps, int32_t step, void *wf, int32_t cin_pad, void *wd, int32_t cout_pad,
+            void *stream) {
+  if (!w || !wf || cout <= 0 || cin <= 0 || cin_pad < cin || (taps != 9 && taps != 1)) return MCR_ERR_ARG;
+  if (step > 0 && (!m || !v || !g)) return MCR_ERR_ARG;
+  if (wd && cout_pad < cout) return MCR_ERR_ARG;
+  DN_TRY(adam(w, m, v, g, cout, taps, cin, lr, beta1, beta2, eps, step, static_cast<__nv_bfloat16 *>(wf), cin_pad,
+              static_cast<__nv_bfloat16 *>(wd), cout_pad, (cudaStream_t)stream));
+}
+
+int dn_adam_bias(float *b, float *m, float *v, float *g, int32_t n, float lr, float beta1, float beta2,
+                 float eps, int32_t step, void *stream) {
+  if (!b || !m || !v || !g || n <= 0) return MCR_ERR_ARG;
+  DN_TRY(adam_bias(b, m, v, g, n, lr, beta1, beta2, eps, step, (cudaStream_t)stream));
+}
+
+int dn_pack_input(const float *src, const float *scale, int32_t B, int64_t HW, int32_t C, void *dst, int32_t stride,
+                  void *stream) {
+  if (!src || !scale || !dst || B <= 0 || HW <= 0 || C <= 0 || stride < C) return MCR_ERR_ARG;
+  DN_TRY(pack_input(src, scale, B, HW, C, static_cast<__nv_bfloat16 *>(dst), stride, (cudaStream_t)stream));
+}
+
+int dn_pack_target(const float *src, const float *scale, int32_t B, int64_t HW, int32_t C, float *dst, void *stream) {
+  if (!src || !scale || !dst || B <= 0 || HW <= 0 || C <= 0) return MCR_ERR_ARG;
+  DN_TRY(pack_target(src, scale, B, HW, C, dst, (cudaStream_t)stream));
+}
+
+int dn_unpack_output(const float *src, const float *scale, int32_t B, int64_t HW, int32_t C, float *dst,
+                     void *stream) {
+  if (!src || !scale || !dst || B <= 0 || HW <= 0 || C <= 0) return MCR_ERR_ARG;
+  DN_TRY(unpack_output(src, scale, B, HW, C, dst, (cudaStream_t)stream));
 }
 
 int dn_check(void *stream) {

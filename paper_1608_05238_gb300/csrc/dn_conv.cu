@@ -154,7 +154,126 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
 }
 
+// k_wgrad_tc: weight gradient dW[n][tap][c] += sum_p dZ[p][n] X[p + tap][c] as a GEMM over pixels
+// with M = 128 output channels, N = `N` input channels, K = 64-pixel blocks.  Operands are
+// K-major (pixels contiguous): dZ^T [cout][B][HW] and three x-shifted copies
+// X^T_kx [cin][B][HW] (X^T_kx[c][b][y W + x] = X[b][y][x + kx - 1][c], zero outside the row).
+// The y shift of a tap is a TMA coordinate offset of (ky - 1) W pixels inside one image (zero
+// filled outside it), which keeps every box start 16-byte aligned.  Each CTA sums a contiguous
+// range of K blocks for one tap and one (M, N) tile and adds its partial tile to dW (FP32).
+__global__ void __launch_bounds__(128, 1)
+    k_wgrad_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
+               const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2, const WgradArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t bTileBytes = (uint32_t)a.N * kBlockK * 2;
+  uint8_t *tileA = smem;
+  uint8_t *tileB = smem + kStages * kATileBytes;
+  uint64_t *full = reinterpret_cast<uint64_t *>(tileB + kStages * bTileBytes);
+  uint64_t *empty = full + kStages;
+  uint64_t *done = empty + kStages;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int split = blockIdx.x, tap = blockIdx.y;
+  const int m_tile = blockIdx.z % a.m_tiles, n_tile = blockIdx.z / a.m_tiles;
+  const int ky = a.taps == 9 ? tap / 3 : 1, kx = a.taps == 9 ? tap % 3 : 1;
+  const CUtensorMap *tmB = kx == 0 ? &tmB0 : (kx == 1 ? &tmB1 : &tmB2);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    fence_barrier_init();
+    prefetch_tensormap(&tmA);
+    prefetch_tensormap(tmB);
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, a.tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // this CTA's K blocks: [k_begin, k_end) of B * HW / 64 blocks (image-major)
+  const int blocks_per_image = a.HW / kBlockK;
+  const int total = a.B * blocks_per_image;
+  const int k_begin = (int)((long long)total * split / a.splits);
+  const int k_end = (int)((long long)total * (split + 1) / a.splits);
+  const int nk = k_end - k_begin;
+  const int dy = (ky - 1) * a.W;
+
+  if (warp == 0 && lane == 0) {
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kStages, r = i / kStages;
+      if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1)) {
+        atomicOr(a.err, 8u);
+        break;
+      }
+      const int kb = k_begin + i;
+      const int b = kb / blocks_per_image, pix = (kb % blocks_per_image) * kBlockK;
+      mbar_arrive_expect_tx(&full[s], kATileBytes + bTileBytes);
+      tma_load_3d(tileA + s * kATileBytes, &tmA, &full[s], pix, b, m_tile * kBlockM);
+      tma_load_3d(tileB + s * bTileBytes, tmB, &full[s], pix + dy, b, n_tile * a.N);
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_bf16_f32(kBlockM, (uint32_t)a.N);
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kStages, r = i / kStages;
+      if (!mbar_wait(&full[s], r & 1)) {
+        atomicOr(a.err, 16u);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t aBase = smem_u32(tileA + s * kATileBytes), bBase = smem_u32(tileB + s * bTileBytes);
+#pragma unroll
+      for (int kk = 0; kk < kBlockK / 16; ++kk)
+        mma_bf16(tmem, sdesc_k128(aBase + kk * 32), sdesc_k128(bBase + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+
+  const bool have = nk > 0 && mbar_wait(done, 0);
+  if (nk > 0 && !have && tid == 0) atomicOr(a.err, 32u);
+  tc_fence_after();
+  const int m = m_tile * kBlockM + warp * 32 + lane;  // output channel of this thread's row
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  for (int c0 = 0; c0 < a.N; c0 += 16) {
+    uint32_t v[16];
+    tmem_ld16(trow + (uint32_t)c0, v);
+    tmem_ld_wait();
+    if (!have || m >= a.cout) continue;
+    float *o = a.dw + ((size_t)m * a.taps + tap) * a.cin_pad + n_tile * a.N + c0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int c = n_tile * a.N + c0 + j;
+      if (c < a.cin) atomicAdd(o + j, __uint_as_float(v[j]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
+}
+
 }  // namespace
+
+cudaError_t launch_wgrad_tc(const CUtensorMap &tmA, const CUtensorMap tmB[3], const WgradArgs &a, cudaStream_t s) {
+  const size_t smem = conv_smem_bytes(a.N);
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  const dim3 grid((unsigned)a.splits, (unsigned)a.taps, (unsigned)(a.m_tiles * a.n_tiles));
+  k_wgrad_tc<<<grid, 128, smem, s>>>(tmA, tmB[0], tmB[1], tmB[2], a);
+  return cudaGetLastError();
+}
 
 size_t conv_smem_bytes(int N) { return 1024 + kStages * (kATileBytes + (size_t)N * kBlockK * 2) + 256; }
 

@@ -29,6 +29,48 @@ struct ConvArgs {
 size_t conv_smem_bytes(int N);
 cudaError_t launch_conv_tc(const CUtensorMap &tmX, const CUtensorMap &tmW, const ConvArgs &a, cudaStream_t s);
 
+// Weight-gradient GEMM launch arguments (see k_wgrad_tc).
+struct WgradArgs {
+  int B, HW, W;      // images, pixels per image, row length (for the y shift)
+  int taps;          // 9 or 1
+  int cout, cin;     // real channel counts
+  int cin_pad;       // dW row length per tap
+  int N;             // input channels per CTA tile (multiple of 16, <= 256)
+  int m_tiles, n_tiles, splits;
+  uint32_t tmem_cols;
+  float *dw;         // fp32 [n_pad][taps][cin_pad], accumulated with atomics
+  unsigned *err;
+};
+cudaError_t launch_wgrad_tc(const CUtensorMap &tmA, const CUtensorMap tmB[3], const WgradArgs &a, cudaStream_t s);
+
+// memory-bound kernels (dn_ops.cu)
+cudaError_t to_ct(const __nv_bfloat16 *src, int B, int HW, int W, int stride, int off, int C, int shifted,
+                  __nv_bfloat16 *dst, cudaStream_t s);
+cudaError_t pool2(const __nv_bfloat16 *src, int B, int H, int W, int sstride, int soff, int C, __nv_bfloat16 *dst,
+                  int dstride, int doff, cudaStream_t s);
+cudaError_t pool2_bwd(const __nv_bfloat16 *dp, int pstride, int poff, const __nv_bfloat16 *skip, int kstride, int koff,
+                      const __nv_bfloat16 *act, int astride, int aoff, int B, int H, int W, int C, __nv_bfloat16 *dz,
+                      int zstride, int zoff, cudaStream_t s);
+cudaError_t up2(const __nv_bfloat16 *src, int B, int H, int W, int sstride, int soff, int C, __nv_bfloat16 *dst,
+                int dstride, int doff, cudaStream_t s);
+cudaError_t up2_bwd(const __nv_bfloat16 *du, int ustride, int uoff, const __nv_bfloat16 *act, int astride, int aoff,
+                    int B, int H, int W, int C, __nv_bfloat16 *dz, int zstride, int zoff, cudaStream_t s);
+cudaError_t bias_grad(const __nv_bfloat16 *dz, long long P, int stride, int off, int C, float *db, cudaStream_t s);
+cudaError_t mse(const float *out, int ostride, const __nv_bfloat16 *x, int xstride, const float *t, long long P, int C,
+                __nv_bfloat16 *dout, int dstride, double *partials, int partials_cap, double *loss, cudaStream_t s);
+cudaError_t residual(const float *out, int ostride, const __nv_bfloat16 *x, int xstride, long long P, int C, float *y,
+                     cudaStream_t s);
+cudaError_t adam(float *w, float *m, float *v, float *g, int cout, int taps, int cin, float lr, float b1,
+                 float b2, float eps, int step, __nv_bfloat16 *wf, int cin_pad, __nv_bfloat16 *wd, int cout_pad,
+                 cudaStream_t s);
+cudaError_t adam_bias(float *b, float *m, float *v, float *g, int n, float lr, float b1, float b2, float eps,
+                      int step, cudaStream_t s);
+cudaError_t pack_input(const float *src, const float *scale, int B, long long HW, int C, __nv_bfloat16 *dst, int stride,
+                       cudaStream_t s);
+cudaError_t pack_target(const float *src, const float *scale, int B, long long HW, int C, float *dst, cudaStream_t s);
+cudaError_t unpack_output(const float *src, const float *scale, int B, long long HW, int C, float *dst,
+                          cudaStream_t s);
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link needed).
 CUresult encode_tiled(CUtensorMap *map, CUtensorMapDataType dtype, uint32_t rank, void *base, const uint64_t *dims,
                       const uint64_t *strides_bytes, const uint32_t *box, CUtensorMapSwizzle swizzle);

@@ -22,19 +22,152 @@ class _ConvDesc(C.Structure):
                 ("out_off", C.c_int32)]
 
 
-EXPORTS = ("dn_conv", "dn_check")
+class _Slice(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("stride", C.c_int32), ("off", C.c_int32)]
+
+
+EXPORTS = ("dn_conv", "dn_wgrad", "dn_to_ct", "dn_pool2", "dn_pool2_bwd", "dn_up2", "dn_up2_bwd", "dn_bias_grad",
+           "dn_mse", "dn_residual", "dn_adam", "dn_adam_bias", "dn_pack_input", "dn_pack_target",
+           "dn_unpack_output", "dn_check")
 
 
 def lib():
     global _bound
     L = mcr.load()
     if not _bound:
-        L.dn_conv.argtypes = [C.POINTER(_ConvDesc), C.c_void_p]
-        L.dn_conv.restype = C.c_int
-        L.dn_check.argtypes = [C.c_void_p]
-        L.dn_check.restype = C.c_int
+        vp, i32, i64, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_float
+        S = _Slice
+        sig = {
+            "dn_conv": [C.POINTER(_ConvDesc), vp],
+            "dn_wgrad": [i32, i32, i32, i32, i32, i32, vp, vp, vp, vp],
+            "dn_to_ct": [S, i32, i32, i32, i32, i32, vp, vp],
+            "dn_pool2": [S, i32, i32, i32, i32, S, vp],
+            "dn_pool2_bwd": [S, S, S, i32, i32, i32, i32, S, vp],
+            "dn_up2": [S, i32, i32, i32, i32, S, vp],
+            "dn_up2_bwd": [S, S, i32, i32, i32, i32, S, vp],
+            "dn_bias_grad": [S, i64, i32, vp, vp],
+            "dn_mse": [vp, i32, vp, i32, vp, i64, i32, vp, i32, vp, vp],
+            "dn_residual": [vp, i32, vp, i32, i64, i32, vp, vp],
+            "dn_adam": [vp, vp, vp, vp, i32, i32, i32, f32, f32, f32, f32, i32, vp, i32, vp, i32, vp],
+            "dn_adam_bias": [vp, vp, vp, vp, i32, f32, f32, f32, f32, i32, vp],
+            "dn_pack_input": [vp, vp, i32, i64, i32, vp, i32, vp],
+            "dn_pack_target": [vp, vp, i32, i64, i32, vp, vp],
+            "dn_unpack_output": [vp, vp, i32, i64, i32, vp, vp],
+            "dn_check": [vp],
+        }
+        for name, args in sig.items():
+            getattr(L, name).argtypes = args
+            getattr(L, name).restype = C.c_int
         _bound = True
     return L
+
+
+def _call(name, *args):
+    rc = getattr(lib(), name)(*args)
+    if rc != 0:
+        raise mcr.McrError(rc, name)
+
+
+class Act:
+    """An NHWC bf16 activation slice: channels [off, off + C) of ``t`` ([B, H, W, stride])."""
+
+    def __init__(self, t: torch.Tensor, C: int, off: int = 0):
+        assert t.is_cuda and t.dtype == torch.bfloat16 and t.is_contiguous() and t.dim() == 4
+        assert 0 <= off and off + C <= t.shape[3]
+        self.t, self.C, self.off = t, C, off
+
+    @property
+    def B(self):
+        return self.t.shape[0]
+
+    @property
+    def H(self):
+        return self.t.shape[1]
+
+    @property
+    def W(self):
+        return self.t.shape[2]
+
+    def s(self) -> _Slice:
+        return _Slice(self.t.data_ptr(), self.t.shape[3], self.off)
+
+
+def _null_slice() -> _Slice:
+    return _Slice(None, 1, 0)
+
+
+def wgrad(dzT: torch.Tensor, xT: torch.Tensor, B, H, W, taps, cout, cin, dw: torch.Tensor, stream=None):
+    """dw [cout][taps][cin] += weight gradient from dz^T [cout][B][HW] and x^T copies [3][cin][B][HW]."""
+    assert dzT.dtype == torch.bfloat16 and xT.dtype == torch.bfloat16 and dw.dtype == torch.float32
+    assert dzT.numel() >= cout * B * H * W and xT.numel() >= 3 * cin * B * H * W and dw.numel() >= cout * taps * cin
+    _call("dn_wgrad", B, H, W, taps, cout, cin, _p(dzT), _p(xT), _p(dw), _stream(stream))
+
+
+def to_ct(src: Act, shifted: bool, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    n = (3 if shifted else 1) * src.C * src.B * src.H * src.W
+    if out is None:
+        out = torch.empty(n, dtype=torch.bfloat16, device=src.t.device)
+    assert out.numel() >= n and out.dtype == torch.bfloat16
+    _call("dn_to_ct", src.s(), src.B, src.H, src.W, src.C, 1 if shifted else 0, _p(out), _stream(stream))
+    return out
+
+
+def pool2(src: Act, dst: Act, stream=None):
+    _call("dn_pool2", src.s(), src.B, src.H, src.W, src.C, dst.s(), _stream(stream))
+
+
+def pool2_bwd(dp: Act, skip: Act | None, act: Act, dz: Act, stream=None):
+    _call("dn_pool2_bwd", dp.s(), skip.s() if skip is not None else _null_slice(), act.s(), act.B, act.H, act.W,
+          act.C, dz.s(), _stream(stream))
+
+
+def up2(src: Act, dst: Act, stream=None):
+    _call("dn_up2", src.s(), src.B, src.H, src.W, src.C, dst.s(), _stream(stream))
+
+
+def up2_bwd(du: Act, act: Act, dz: Act, stream=None):
+    _call("dn_up2_bwd", du.s(), act.s(), act.B, act.H, act.W, act.C, dz.s(), _stream(stream))
+
+
+def bias_grad(dz: Act, db: torch.Tensor, stream=None):
+    _call("dn_bias_grad", dz.s(), dz.B * dz.H * dz.W, dz.C, _p(db), _stream(stream))
+
+
+def mse(out: torch.Tensor, x: torch.Tensor, t: torch.Tensor, C: int, dout: torch.Tensor, loss: torch.Tensor,
+        stream=None):
+    P = out.shape[0] * out.shape[1] * out.shape[2]
+    _call("dn_mse", _p(out), out.shape[3], _p(x), x.shape[3], _p(t), P, C, _p(dout), dout.shape[3], _p(loss),
+          _stream(stream))
+
+
+def residual(out: torch.Tensor, x: torch.Tensor, C: int, y: torch.Tensor, stream=None):
+    P = out.shape[0] * out.shape[1] * out.shape[2]
+    _call("dn_residual", _p(out), out.shape[3], _p(x), x.shape[3], P, C, _p(y), _stream(stream))
+
+
+def adam(w, m, v, g, cout, taps, cin, lr, b1, b2, eps, step, wf, cin_pad, wd=None, cout_pad=0, stream=None):
+    _call("dn_adam", _p(w), _p(m), _p(v), _p(g), cout, taps, cin, lr, b1, b2, eps, step, _p(wf), cin_pad, _p(wd),
+          cout_pad, _stream(stream))
+
+
+def adam_bias(b, m, v, g, lr, b1, b2, eps, step, stream=None):
+    _call("dn_adam_bias", _p(b), _p(m), _p(v), _p(g), b.numel(), lr, b1, b2, eps, step, _stream(stream))
+
+
+def pack_input(src: torch.Tensor, scale: torch.Tensor, dst: torch.Tensor, stream=None):
+    B, Cc = src.shape[0], src.shape[1]
+    _call("dn_pack_input", _p(src), _p(scale), B, src.shape[2] * src.shape[3], Cc, _p(dst), dst.shape[3],
+          _stream(stream))
+
+
+def pack_target(src: torch.Tensor, scale: torch.Tensor, dst: torch.Tensor, stream=None):
+    B, Cc = src.shape[0], src.shape[1]
+    _call("dn_pack_target", _p(src), _p(scale), B, src.shape[2] * src.shape[3], Cc, _p(dst), _stream(stream))
+
+
+def unpack_output(src: torch.Tensor, scale: torch.Tensor, dst: torch.Tensor, stream=None):
+    B, Cc = dst.shape[0], dst.shape[1]
+    _call("dn_unpack_output", _p(src), _p(scale), B, dst.shape[2] * dst.shape[3], Cc, _p(dst), _stream(stream))
 
 
 def _p(t):

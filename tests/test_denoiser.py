@@ -1,0 +1,134 @@
+"""The tensor-core U-Net denoiser and its kernels against plain PyTorch CPU references."""
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as Fnn
+
+from oracle import denoiser_ref as ref
+from paper_1608_05238_gb300 import _build
+from paper_1608_05238_gb300 import denoise_ops as ops
+from paper_1608_05238_gb300.denoise_ops import Act
+from paper_1608_05238_gb300.denoiser import UNet, r64, sample_scale
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    _build.build()
+    ops.lib()
+
+
+def _nhwc(B, H, W, C, stride, seed, positive=False):
+    g = torch.Generator().manual_seed(seed)
+    t = torch.zeros(B, H, W, stride)
+    v = torch.randn(B, H, W, C, generator=g)
+    t[..., :C] = v.abs() if positive else v
+    return t.bfloat16().cuda()
+
+
+@pytest.mark.parametrize("B,H,W,cin,cout,taps", [(2, 16, 32, 64, 32, 9), (1, 32, 64, 96, 128, 9),
+                                                 (2, 16, 16, 33, 48, 1), (1, 8, 128, 200, 256, 9)])
+def test_wgrad_matches_autograd(B, H, W, cin, cout, taps):
+    x = _nhwc(B, H, W, cin, r64(cin), 1)
+    dz = _nhwc(B, H, W, cout, r64(cout), 2)
+    dw = torch.zeros(cout, taps, cin, device="cuda")
+    dzT = ops.to_ct(Act(dz, cout), False)
+    xT = ops.to_ct(Act(x, cin), True)
+    ops.wgrad(dzT, xT, B, H, W, taps, cout, cin, dw)
+    ops.check()
+    k = 3 if taps == 9 else 1
+    xc = x.double().cpu()[..., :cin].permute(0, 3, 1, 2)
+    w = torch.zeros(cout, cin, k, k, dtype=torch.float64, requires_grad=True)
+    y = Fnn.conv2d(xc, w, padding=k // 2)
+    y.backward(dz.double().cpu()[..., :cout].permute(0, 3, 1, 2))
+    ref_dw = w.grad.permute(0, 2, 3, 1).reshape(cout, taps, cin)
+    got = dw.double().cpu()
+    assert torch.allclose(got, ref_dw, rtol=1e-4, atol=1e-4 * ref_dw.abs().max().item())
+
+
+def test_layout_pool_upsample_and_backward_kernels():
+    B, H, W, C = 2, 16, 32, 40
+    x = _nhwc(B, H, W, C, 128, 3)
+    src = Act(x, C, 64 - 40 + 24)  # slice at offset 48
+    t = ops.to_ct(src, True)
+    xs = x.float().cpu()[..., 48:48 + C]
+    ct = xs.permute(3, 0, 1, 2).reshape(C, B, H * W)
+    plane = C * B * H * W
+    assert torch.equal(t[plane:2 * plane].float().cpu().view(C, B, H * W), ct)
+    left = torch.zeros_like(xs)
+    left[:, :, 1:] = xs[:, :, :-1]  # copy 0: x shifted by -1
+    assert torch.equal(t[:plane].float().cpu().view(C, B, H * W), left.permute(3, 0, 1, 2).reshape(C, B, H * W))
+    p = torch.zeros(B, H // 2, W // 2, 64, dtype=torch.bfloat16, device="cuda")
+    ops.pool2(src, Act(p, C))
+    rp = Fnn.avg_pool2d(xs.permute(0, 3, 1, 2), 2).permute(0, 2, 3, 1)
+    assert torch.allclose(p[..., :C].float().cpu(), rp, rtol=2 ** -8, atol=1e-2)
+    u = torch.zeros(B, H, W, 64, dtype=torch.bfloat16, device="cuda")
+    ops.up2(Act(p, C), Act(u, C, 8))
+    assert torch.equal(u[..., 8:8 + C].float().cpu(), Fnn.interpolate(p[..., :C].float().cpu().permute(0, 3, 1, 2),
+                                                                      scale_factor=2).permute(0, 2, 3, 1))
+    # backward kernels with masks
+    act = _nhwc(B, H // 2, W // 2, C, 64, 4)
+    du = _nhwc(B, H, W, C, 64, 5)
+    dz = torch.zeros(B, H // 2, W // 2, 64, dtype=torch.bfloat16, device="cuda")
+    ops.up2_bwd(Act(du, C), Act(act, C), Act(dz, C))
+    r = du.float().cpu()[..., :C].reshape(B, H // 2, 2, W // 2, 2, C).sum(dim=(2, 4)) * (act.float().cpu()[..., :C] > 0)
+    assert torch.allclose(dz[..., :C].float().cpu(), r, rtol=2 ** -7, atol=1e-2)
+    dp = _nhwc(B, H // 2, W // 2, C, 64, 6)
+    skip = _nhwc(B, H, W, C, 64, 7)
+    act2 = _nhwc(B, H, W, C, 64, 8)
+    dz2 = torch.zeros(B, H, W, 64, dtype=torch.bfloat16, device="cuda")
+    ops.pool2_bwd(Act(dp, C), Act(skip, C), Act(act2, C), Act(dz2, C))
+    r2 = (skip.float().cpu()[..., :C] + 0.25 * dp.float().cpu()[..., :C].repeat_interleave(2, 1).repeat_interleave(2, 2))
+    r2 = r2 * (act2.float().cpu()[..., :C] > 0)
+    assert torch.allclose(dz2[..., :C].float().cpu(), r2, rtol=2 ** -7, atol=1e-2)
+    db = torch.zeros(C, device="cuda")
+    ops.bias_grad(Act(skip, C), db)
+    assert torch.allclose(db.cpu(), skip.float().cpu()[..., :C].sum(dim=(0, 1, 2)), rtol=1e-4, atol=1e-3)
+
+
+def _data(B, H, W, C, seed):
+    g = torch.Generator().manual_seed(seed)
+    base = torch.rand(B, 1, H, W, generator=g) + 0.5
+    x = base * (1 + 0.3 * torch.randn(B, C, H, W, generator=g)) / torch.arange(1, C + 1).view(1, C, 1, 1)
+    t = base / torch.arange(1, C + 1).view(1, C, 1, 1)
+    return x.float(), t.float()
+
+
+def test_unet_forward_and_gradients_match_reference():
+    B, C, H, W = 2, 33, 128, 128
+    x, t = _data(B, H, W, C, 1)
+    net = UNet(in_ch=C, seed=3)
+    # perturb the output head so that every layer receives a gradient
+    net.layers["out"].w.normal_(0, 0.05)
+    net.layers["out"].refresh()
+    xs, ts = x.cuda(), t.cuda()
+    scale = sample_scale(xs)
+    net.load(xs, scale, ts)
+    net.forward()
+    loss = net.loss_and_grad_seed().item()
+    net.backward()
+    ops.check()
+    s = scale.cpu().view(B, 1, 1, 1)
+    rl, ry, rg = ref.loss_and_grads(net.state(), x * s, t * s, bf16=True)
+    assert abs(loss - rl) <= 2e-3 * rl
+    for name, lay in net.layers.items():
+        gw, gb = lay.gw.cpu(), lay.gb.cpu()
+        rw, rb = rg[name]
+        err = (gw - rw).norm() / rw.norm()
+        cos = torch.nn.functional.cosine_similarity(gw.flatten(), rw.flatten(), dim=0)
+        assert err < 5e-2 and cos > 0.998, (name, err.item(), cos.item())
+        assert (gb - rb).norm() / (rb.norm() + 1e-30) < 5e-2, name
+
+
+def test_unet_training_reduces_loss():
+    B, C, H, W = 2, 33, 128, 128
+    x, t = _data(B, H, W, C, 2)
+    net = UNet(in_ch=C, seed=4)
+    xs, ts = x.cuda(), t.cuda()
+    scale = sample_scale(xs)
+    losses = [net.train_step(xs, scale, ts, lr=1e-3).item() for _ in range(60)]
+    ops.check()
+    assert losses[-1] < 0.7 * losses[0], losses[::10]
+    pred = net.predict(xs, scale)
+    assert pred.shape == xs.shape and torch.isfinite(pred).all()
