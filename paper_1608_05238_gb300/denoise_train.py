@@ -1,0 +1,73 @@
+"""Training data from the method itself, training and evaluation of the harmonic-map denoiser.
+
+Pairs are (low-count, high-count) forward harmonic maps of the same random inclusion phantom,
+both produced by the batched forward MC (mc_run_batch) with independent packets; the high-count
+map is the training target and, on held-out phantoms, the judge of the denoiser's error.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import mcr, workloads
+from .denoiser import UNet, sample_scale
+
+
+def make_pairs(n_pairs: int, n: int = 256, dx: float = 0.05, K: int = 16, n_low: int = 100_000,
+               n_high: int = 10_000_000, seed0: int = 10_000, device="cuda"):
+    """(x, t): low- and high-count coefficient maps [n_pairs][2K+1][n][n] (fp32, device) of random
+    circular-inclusion phantoms (3 inclusions, g 0.9, collimated line source on the top edge)."""
+    C = 2 * K + 1
+    x = torch.empty(n_pairs, C, n, n, device=device)
+    t = torch.empty_like(x)
+    common = mcr.Run(K=K, n_packets=0)
+    src = mcr.Source(**workloads.top_line_source(n, dx))
+    dx32, g32 = float(np.float32(dx)), float(np.float32(0.9))
+    for start in range(0, n_pairs, 32):
+        probs = []
+        for i in range(start, min(n_pairs, start + 32)):
+            mua, mus = workloads.inclusion_phantom(n, dx, 3, seed=seed0 + i, margin=min(2.0, 0.15 * n * dx))
+            med = mcr.Medium(torch.from_numpy(mua).to(device), torch.from_numpy(mus).to(device), dx32, g32)
+            probs.append(mcr.Problem(med, n_low, seed=seed0 + i, stream_id=0, source=src, out=x[i]))
+            probs.append(mcr.Problem(med, n_high, seed=seed0 + i, stream_id=1, source=src, out=t[i]))
+        mcr.run_batch(probs, common)
+    mcr.check()
+    return x, t
+
+
+def train(net: UNet, x: torch.Tensor, t: torch.Tensor, steps: int, batch: int = 8, lr: float = 1e-3,
+          seed: int = 0, log_every: int = 0):
+    """Adam on random mini-batches of the pairs, cosine-decayed learning rate; returns the losses."""
+    g = torch.Generator().manual_seed(seed)
+    losses = []
+    for s in range(steps):
+        idx = torch.randint(0, x.shape[0], (batch,), generator=g).to(x.device)
+        xb, tb = x[idx].contiguous(), t[idx].contiguous()
+        lr_s = lr * 0.5 * (1 + np.cos(np.pi * s / max(1, steps)))
+        loss = net.train_step(xb, sample_scale(xb), tb, lr_s)
+        if log_every and (s % log_every == 0 or s == steps - 1):
+            losses.append((s, loss.item()))
+    return losses
+
+
+def relative_error(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    """Per-sample ||a - b|| / ||b|| over all channels and pixels."""
+    d = (a - b).flatten(1).norm(dim=1)
+    return d / b.flatten(1).norm(dim=1).clamp_min(1e-30)
+
+
+@torch.no_grad()
+def evaluate(net: UNet, x: torch.Tensor, t: torch.Tensor, batch: int = 8):
+    """Mean relative L2 error of the low-count input and of the denoised output against the
+    high-count target, overall and for the fluence channel a_0."""
+    err_in, err_out, e0_in, e0_out = [], [], [], []
+    for s in range(0, x.shape[0], batch):
+        xb, tb = x[s:s + batch].contiguous(), t[s:s + batch].contiguous()
+        y = net.predict(xb, sample_scale(xb)).clone()
+        err_in.append(relative_error(xb, tb))
+        err_out.append(relative_error(y, tb))
+        e0_in.append(relative_error(xb[:, :1], tb[:, :1]))
+        e0_out.append(relative_error(y[:, :1], tb[:, :1]))
+    cat = lambda v: torch.cat(v).mean().item()
+    return {"err_input": cat(err_in), "err_denoised": cat(err_out), "err_a0_input": cat(e0_in),
+            "err_a0_denoised": cat(e0_out)}
