@@ -42,11 +42,12 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--packets", type=int, default=10_000_000, help="packets per forward and per adjoint run")
-    ap.add_argument("--cpu-sample", type=int, default=20_000, help="oracle packets (fwd and adj) for cpu_baseline")
+    ap.add_argument("--cpu-sample", type=int, default=200_000, help="oracle packets (fwd and adj) for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="grad256", choices=["grad256", "batch64"],
+    ap.add_argument("--workload", default="grad256", choices=["grad256", "batch64", "denoise256", "conv"],
                     help="grad256: the gradient evaluation (default); batch64: 64 forward problems in one "
-                         "graph-captured batched launch")
+                         "graph-captured batched launch; denoise256: the learned denoiser; conv: one large "
+                         "tensor-core convolution (profiling case)")
     return ap.parse_args()
 
 
@@ -379,10 +380,128 @@ def _batch64(args):
     return 0
 
 
+def _unet_flops(net, B, H, W):
+    """(algorithmic, executed) FLOPs of one U-Net forward pass on B images (2 per multiply-add);
+    executed counts the channel padding the tensor-core tiles compute."""
+    from paper_1608_05238_gb300.denoiser import UNet
+    alg = exe = 0
+    for name, lay in net.layers.items():
+        P = B * (H >> UNet._level(name)) * (W >> UNet._level(name))
+        alg += 2 * P * lay.cout * lay.taps * lay.cin
+        exe += 2 * P * lay.n_pad * lay.taps * lay.cin_pad
+    return alg, exe
+
+
+def _denoise256(args):
+    """The learned denoiser on 256x256 maps with K = 16 (33 channels): MC pair generation with the
+    batched launch, training and inference with the tensor-core kernels, held-out error, and the
+    throughput of one large tensor-core convolution against the measured BF16 peak."""
+    import torch
+    from paper_1608_05238_gb300 import _build, denoise_ops as ops, denoise_train as dt
+    from paper_1608_05238_gb300.denoiser import UNet, sample_scale
+    _build.build()
+    K, n, dx = 16, 256, 0.05
+    n_train, n_test, n_low, n_high = 64, 8, 100_000, 10_000_000
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    a, b = ev()
+    a.record()
+    x, t = dt.make_pairs(n_train + n_test, n=n, dx=dx, K=K, n_low=n_low, n_high=n_high)
+    b.record()
+    b.synchronize()
+    gen_s = a.elapsed_time(b) / 1e3
+    net = UNet(in_ch=2 * K + 1, seed=0)
+    batch, steps = 8, max(50, args.steps * 100)
+    dt.train(net, x[:n_train], t[:n_train], steps=3, batch=batch)  # warm-up
+    a, b = ev()
+    a.record()
+    dt.train(net, x[:n_train], t[:n_train], steps=steps, batch=batch, lr=1e-3, seed=1)
+    b.record()
+    b.synchronize()
+    train_s = a.elapsed_time(b) / 1e3
+    ops.check()
+    res = dt.evaluate(net, x[n_train:], t[n_train:])
+    xb = x[:batch].contiguous()
+    sc = sample_scale(xb)
+    net.predict(xb, sc)
+    a, b = ev()
+    a.record()
+    for _ in range(10):
+        net.predict(xb, sc)
+    b.record()
+    b.synchronize()
+    infer_s = a.elapsed_time(b) / 1e3 / 10
+    alg, exe = _unet_flops(net, batch, n, n)
+    # one large convolution (8 x 256 x 256 pixels, 128 -> 128 channels, 3x3) timed alone
+    xc = torch.randn(8, 256, 256, 128, device="cuda").bfloat16()
+    wc = (torch.randn(128, 9, 128, device="cuda") * 0.03).bfloat16()
+    yc = torch.empty(8, 256, 256, 128, device="cuda", dtype=torch.bfloat16)
+    for _ in range(3):
+        ops.conv(xc, wc, 128, yc)
+    a, b = ev()
+    a.record()
+    for _ in range(20):
+        ops.conv(xc, wc, 128, yc)
+    b.record()
+    b.synchronize()
+    conv_s = a.elapsed_time(b) / 1e3 / 20
+    conv_tf = 2 * 8 * 256 * 256 * 128 * 9 * 128 / conv_s / 1e12
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    out = {"metric": "denoised 256x256 K=16 maps/s (inference)", "value": batch / infer_s, "unit": "maps/s",
+           "n_gpus": 1, "steps": steps, "warmup": 3, "ms_per_step": 1e3 * train_s / steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+           "config": {"workload": f"denoise256: U-Net 32-256 ch on 33-channel 256^2 maps; {n_train} training + "
+                                  f"{n_test} held-out MC pairs, inputs {n_low:.0e} packets, targets {n_high:.0e} "
+                                  f"packets; batch {batch}",
+                      "pair_generation_photons_per_s": (n_train + n_test) * (n_low + n_high) / gen_s,
+                      "train_samples_per_s": steps * batch / train_s,
+                      "train_tflops_executed": 3 * exe * steps / train_s / 1e12,
+                      "infer_tflops_executed": exe / infer_s / 1e12,
+                      "unet_forward_gflop_alg": alg / batch / 1e9, "unet_forward_gflop_executed": exe / batch / 1e9,
+                      "heldout": res},
+           "roofline": {"bound": "tensor", "achieved": conv_tf, "peak": peak, "unit": "TFLOP/s", "frac": conv_tf / peak,
+                        "traffic": None, "kernel": "k_conv_tc (8x256x256, 128->128, 3x3)",
+                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"},
+           "cpu_baseline": None}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def _conv_only(args):
+    """One 3x3 convolution, 8 x 256 x 256 pixels, 128 -> 128 channels, on the tensor cores."""
+    import torch
+    from paper_1608_05238_gb300 import _build, denoise_ops as ops
+    _build.build()
+    xc = torch.randn(8, 256, 256, 128, device="cuda").bfloat16()
+    wc = (torch.randn(128, 9, 128, device="cuda") * 0.03).bfloat16()
+    yc = torch.empty(8, 256, 256, 128, device="cuda", dtype=torch.bfloat16)
+    for _ in range(args.warmup):
+        ops.conv(xc, wc, 128, yc)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        ops.conv(xc, wc, 128, yc)
+    b.record()
+    b.synchronize()
+    ops.check()
+    s = a.elapsed_time(b) / 1e3 / args.steps
+    print(json.dumps({"metric": "conv TFLOP/s", "value": 2 * 8 * 256 * 256 * 128 * 9 * 128 / s / 1e12,
+                      "unit": "TFLOP/s", "ms_per_step": 1e3 * s}), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.workload == "batch64" and args.impl != "reference":
         return _batch64(args)
+    if args.workload == "denoise256" and args.impl != "reference":
+        return _denoise256(args)
+    if args.workload == "conv" and args.impl != "reference":
+        return _conv_only(args)
     if args.impl == "reference":
         return _reference(args)
     return _gpu(args)
