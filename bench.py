@@ -464,7 +464,7 @@ def _denoise256(args):
                       "unet_forward_gflop_alg": alg / batch / 1e9, "unet_forward_gflop_executed": exe / batch / 1e9,
                       "heldout": res},
            "roofline": {"bound": "tensor", "achieved": conv_tf, "peak": peak, "unit": "TFLOP/s", "frac": conv_tf / peak,
-                        "traffic": None, "kernel": "k_conv_tc (8x256x256, 128->128, 3x3)",
+                        "traffic": None, "kernel": "k_conv_ws (8x256x256, 128->128, 3x3)",
                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"},
            "cpu_baseline": None}
     print(json.dumps(out), flush=True)

@@ -1,15 +1,16 @@
 // dn_conv.cu -- BF16 tensor-core convolutions of the harmonic-map denoiser on sm_103a.
 //
-// k_conv_tc: 3x3 (pad 1) or 1x1 convolution as an implicit GEMM, D[pixels x Cout] =
+// k_conv_ws: 3x3 (pad 1) or 1x1 convolution as an implicit GEMM, D[pixels x Cout] =
 // sum over taps and 64-channel blocks of X_tap[pixels x 64] * W_tap[Cout x 64]^T, with
 //   * activations NHWC bf16 with the channel stride padded to a multiple of 64; a 128-pixel tile
 //     (one row segment, or several short rows) of one tap is one 4D TMA box {64 ch, w, rows, 1};
 //     the shifted boxes of the taps start at x-1 / y-1 and the hardware fills the padding with
 //     zeros;
 //   * weights [Cout_pad][taps][Cin_pad] bf16, one 2D TMA box {64, N} per K block;
-//   * operands in shared memory with the 128-byte swizzle, a 4-stage TMA -> MMA mbarrier ring,
+//   * operands in shared memory with the 128-byte swizzle, a TMA -> MMA mbarrier ring,
 //     tcgen05.mma (M = 128, N = Cout_pad, K = 16 per instruction) issued by one thread with the
-//     FP32 accumulator in TMEM;
+//     FP32 accumulator in TMEM (two accumulators, so a tile's epilogue overlaps the next tile's
+//     MMAs in the persistent kernel);
 //   * an epilogue that reads TMEM with tcgen05.ld and applies bias, ReLU, or the ReLU mask of the
 //     next layer's input (for the backward pass), writing bf16 or fp32 NHWC slices (channel
 //     offset/stride, so concatenations are free).
@@ -26,132 +27,171 @@ constexpr int kBlockM = 128;
 constexpr int kBlockK = 64;
 constexpr uint32_t kATileBytes = kBlockM * kBlockK * 2;  // 16 KB
 
-__global__ void __launch_bounds__(128, 1)
-    k_conv_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, const ConvArgs a) {
+// k_conv_ws: persistent, warp-specialised.  One CTA per SM
+// walks the 128-pixel output tiles (tile = blockIdx.x + i gridDim.x); warp 0 streams the K
+// blocks of all its tiles through a ring of `stages` shared-memory buffers with TMA, warp 1
+// issues the MMAs into one of two TMEM accumulators (2 x acc_cols columns), and warps 2..5 drain
+// the other accumulator (TMEM lanes 32 (w % 4) ... + 31) while the next tile is being multiplied.
+constexpr int kWsThreads = 192;
+
+__global__ void __launch_bounds__(kWsThreads, 1)
+    k_conv_ws(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, const ConvArgs a,
+              int stages, int num_tiles) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t bTileBytes = (uint32_t)a.N * kBlockK * 2;
-  uint8_t *tileA = smem;
-  uint8_t *tileB = smem + kStages * kATileBytes;
-  uint64_t *full = reinterpret_cast<uint64_t *>(tileB + kStages * bTileBytes);
-  uint64_t *empty = full + kStages;
-  uint64_t *done = empty + kStages;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  const uint32_t stageBytes = kATileBytes + bTileBytes;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stageBytes);
+  uint64_t *empty = full + stages;
+  uint64_t *tfull = empty + stages;   // [2] accumulator b is ready for the epilogue
+  uint64_t *tempty = tfull + 2;       // [2] accumulator b has been drained
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+  const uint32_t acc_cols = a.tmem_cols;  // columns of one accumulator
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+    }
     fence_barrier_init();
     prefetch_tensormap(&tmX);
     prefetch_tensormap(&tmW);
   }
   if (warp == 0) {
-    tmem_alloc(tmem_slot, a.tmem_cols);
+    tmem_alloc(tmem_slot, 2 * acc_cols);
     tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-
-  // tile origin: 128 consecutive pixels of one image (wbox per row, `rows` rows)
-  const long long p0 = (long long)blockIdx.x * kBlockM;
   const int hw = a.H * a.W;
-  const int b0 = (int)(p0 / hw);
-  const int rem = (int)(p0 % hw);
-  const int y0 = rem / a.W, x0 = rem % a.W;
   const int cblocks = a.cin_pad / kBlockK;
   const int nk = a.taps * cblocks;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer
-    for (int i = 0; i < nk; ++i) {
-      const int s = i % kStages, r = i / kStages;
-      if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1)) {
-        atomicOr(a.err, 1u);
-        break;
+    // ---- TMA producer over all tiles of this CTA
+    uint32_t kc = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+      const long long p0 = (long long)tile * kBlockM;
+      const int b0 = (int)(p0 / hw), rem = (int)(p0 % hw);
+      const int y0 = rem / a.W, x0 = rem % a.W;
+      for (int i = 0; i < nk; ++i, ++kc) {
+        const int s = kc % stages;
+        const uint32_t r = kc / stages;
+        if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1)) {
+          atomicOr(a.err, 64u);
+          ok = false;
+          break;
+        }
+        const int tap = i / cblocks, cb = i % cblocks;
+        const int ky = a.taps == 9 ? tap / 3 : 1, kx = a.taps == 9 ? tap % 3 : 1;
+        uint8_t *st = smem + (size_t)s * stageBytes;
+        mbar_arrive_expect_tx(&full[s], stageBytes);
+        tma_load_4d(st, &tmX, &full[s], cb * kBlockK, x0 + kx - 1, y0 + ky - 1, b0);
+        tma_load_2d(st + kATileBytes, &tmW, &full[s], tap * a.cin_pad + cb * kBlockK, 0);
       }
-      const int tap = i / cblocks, cb = i % cblocks;
-      const int ky = a.taps == 9 ? tap / 3 : 1, kx = a.taps == 9 ? tap % 3 : 1;
-      mbar_arrive_expect_tx(&full[s], kATileBytes + bTileBytes);
-      tma_load_4d(tileA + s * kATileBytes, &tmX, &full[s], cb * kBlockK, x0 + kx - 1, y0 + ky - 1, b0);
-      tma_load_2d(tileB + s * bTileBytes, &tmW, &full[s], tap * a.cin_pad + cb * kBlockK, 0);
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     const uint32_t idesc = idesc_bf16_f32(kBlockM, (uint32_t)a.N);
+    uint32_t kc = 0;
+    int it = 0;
     bool ok = true;
-    for (int i = 0; i < nk && ok; ++i) {
-      const int s = i % kStages, r = i / kStages;
-      if (!mbar_wait(&full[s], r & 1)) {
-        atomicOr(a.err, 2u);
-        ok = false;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++it) {
+      const int b = it & 1;
+      const uint32_t use = it >> 1;
+      if (use > 0 && !mbar_wait(&tempty[b], (use - 1) & 1)) {
+        atomicOr(a.err, 128u);
         break;
       }
       tc_fence_after();
-      const uint32_t aBase = smem_u32(tileA + s * kATileBytes), bBase = smem_u32(tileB + s * bTileBytes);
+      const uint32_t d = tmem + b * acc_cols;
+      for (int i = 0; i < nk; ++i, ++kc) {
+        const int s = kc % stages;
+        if (!mbar_wait(&full[s], (kc / stages) & 1)) {
+          atomicOr(a.err, 256u);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t aBase = smem_u32(smem + (size_t)s * stageBytes), bBase = aBase + kATileBytes;
 #pragma unroll
-      for (int kk = 0; kk < kBlockK / 16; ++kk)
-        mma_bf16(tmem, sdesc_k128(aBase + kk * 32), sdesc_k128(bBase + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
-      mma_commit(&empty[s]);
+        for (int kk = 0; kk < kBlockK / 16; ++kk)
+          mma_bf16(d, sdesc_k128(aBase + kk * 32), sdesc_k128(bBase + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        mma_commit(&empty[s]);
+      }
+      mma_commit(&tfull[b]);
     }
-    mma_commit(done);
-  }
-  __syncwarp();
-
-  // ---- epilogue: TMEM -> registers -> global
-  const bool have = mbar_wait(done, 0);
-  if (!have && tid == 0) atomicOr(a.err, 4u);
-  tc_fence_after();
-  const int row = warp * 32 + lane;
-  const long long p = p0 + row;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-  for (int c0 = 0; c0 < a.N; c0 += 16) {
-    uint32_t v[16];
-    tmem_ld16(trow + (uint32_t)c0, v);
-    tmem_ld_wait();
-    if (!have) continue;
-    float f[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int n = c0 + j;
-      float x = __uint_as_float(v[j]);
-      if (a.bias && n < a.cout) x += a.bias[n];
-      if (a.relu) x = fmaxf(x, 0.f);
-      if (a.mask && n < a.cout) {
-        const float m = __bfloat162float(a.mask[p * a.mask_stride + a.mask_off + n]);
-        x = m > 0.f ? x : 0.f;
+  } else if (warp >= 2) {
+    // ---- epilogue warps: TMEM lanes 32 (warp % 4) .. + 31
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
+      const int b = it & 1;
+      const uint32_t use = it >> 1;
+      // warp-uniform decision: the TMEM loads below are warp-collective
+      const bool have = __all_sync(0xffffffffu, mbar_wait(&tfull[b], use & 1));
+      if (!have) {
+        if (lane == 0) atomicOr(a.err, 512u);
+        break;
       }
-      f[j] = x;
-    }
-    if (a.out_f32) {
-      float *o = a.out_f32 + p * a.out_stride + a.out_off + c0;
-      if (c0 + 16 <= a.cout) {
+      tc_fence_after();
+      const long long p = (long long)tile * kBlockM + row;
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + b * acc_cols;
+      for (int c0 = 0; c0 < a.N; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld16(trow + (uint32_t)c0, v);
+        tmem_ld_wait();
+        float f[16];
 #pragma unroll
-        for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4 *>(o + j) = make_float4(f[j], f[j + 1], f[j + 2], f[j + 3]);
-      } else {
-        for (int j = 0; j < 16 && c0 + j < a.cout; ++j) o[j] = f[j];
-      }
-    } else {
-      __nv_bfloat16 *o = a.out_bf16 + p * a.out_stride + a.out_off + c0;
-      if (c0 + 16 <= a.cout) {
-        __align__(16) __nv_bfloat162 h[8];
+        for (int j = 0; j < 16; ++j) {
+          const int n = c0 + j;
+          float x = __uint_as_float(v[j]);
+          if (a.bias && n < a.cout) x += a.bias[n];
+          if (a.relu) x = fmaxf(x, 0.f);
+          if (a.mask && n < a.cout) {
+            const float m = __bfloat162float(a.mask[p * a.mask_stride + a.mask_off + n]);
+            x = m > 0.f ? x : 0.f;
+          }
+          f[j] = x;
+        }
+        if (a.out_f32) {
+          float *o = a.out_f32 + p * a.out_stride + a.out_off + c0;
+          if (c0 + 16 <= a.cout) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
-        *reinterpret_cast<uint4 *>(o) = *reinterpret_cast<const uint4 *>(&h[0]);
-        *reinterpret_cast<uint4 *>(o + 8) = *reinterpret_cast<const uint4 *>(&h[4]);
-      } else {
-        for (int j = 0; j < 16 && c0 + j < a.cout; ++j) o[j] = __float2bfloat16_rn(f[j]);
+            for (int j = 0; j < 16; j += 4)
+              *reinterpret_cast<float4 *>(o + j) = make_float4(f[j], f[j + 1], f[j + 2], f[j + 3]);
+          } else {
+            for (int j = 0; j < 16 && c0 + j < a.cout; ++j) o[j] = f[j];
+          }
+        } else {
+          __nv_bfloat16 *o = a.out_bf16 + p * a.out_stride + a.out_off + c0;
+          if (c0 + 16 <= a.cout) {
+            __align__(16) __nv_bfloat162 h[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+            *reinterpret_cast<uint4 *>(o) = *reinterpret_cast<const uint4 *>(&h[0]);
+            *reinterpret_cast<uint4 *>(o + 8) = *reinterpret_cast<const uint4 *>(&h[4]);
+          } else {
+            for (int j = 0; j < 16 && c0 + j < a.cout; ++j) o[j] = __float2bfloat16_rn(f[j]);
+          }
+        }
       }
+      tc_fence_before();
+      mbar_arrive(&tempty[b]);
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
+  if (warp == 0) tmem_dealloc(tmem, 2 * acc_cols);
 }
 
 // k_wgrad_tc: weight gradient dW[n][tap][c] += sum_p dZ[p][n] X[p + tap][c] as a GEMM over pixels
@@ -275,18 +315,40 @@ cudaError_t launch_wgrad_tc(const CUtensorMap &tmA, const CUtensorMap tmB[3], co
   return cudaGetLastError();
 }
 
-size_t conv_smem_bytes(int N) { return 1024 + kStages * (kATileBytes + (size_t)N * kBlockK * 2) + 256; }
+// Ring depth of the persistent convolution for a given MMA N: as many stages as fit in
+// ~200 KB of shared memory, at most 8.
+static int conv_stages(int N) {
+  const size_t stage = kATileBytes + (size_t)N * kBlockK * 2;
+  int s = (int)((200u * 1024u) / stage);
+  return s > 8 ? 8 : (s < 2 ? 2 : s);
+}
+
+size_t conv_smem_bytes(int N) {
+  const size_t stage = kATileBytes + (size_t)N * kBlockK * 2;
+  return 1024 + conv_stages(N) * stage + 256;
+}
+
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 1;
+  }
+  return n;
+}
 
 cudaError_t launch_conv_tc(const CUtensorMap &tmX, const CUtensorMap &tmW, const ConvArgs &a, cudaStream_t s) {
   const size_t smem = conv_smem_bytes(a.N);
   static size_t configured = 0;
   if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
-    configured = smem;
+    configured = 232448;
   }
   const long long tiles = (long long)a.B * a.H * a.W / kBlockM;
-  k_conv_tc<<<(unsigned)tiles, 128, smem, s>>>(tmX, tmW, a);
+  const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
+  k_conv_ws<<<grid, kWsThreads, smem, s>>>(tmX, tmW, a, conv_stages(a.N), (int)tiles);
   return cudaGetLastError();
 }
 

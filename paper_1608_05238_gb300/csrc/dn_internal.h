@@ -8,7 +8,7 @@
 
 namespace dn {
 
-// Implicit-GEMM convolution launch arguments (see k_conv_tc).
+// Implicit-GEMM convolution launch arguments (see k_conv_ws).
 struct ConvArgs {
   int B, H, W;       // images and spatial size (output = input size)
   int cin_pad;       // channel stride of the input (multiple of 64)

@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     my[1] = 1.f;
     float c = sz, s = sx;
     float2 *pairs = reinterpret_cast<float2 *>(my);
+#pragma unroll 4
     for (int n = 1; n <= K; ++n) {
       pairs[n] = make_float2(c, s);
       const float cn = fmaf(c, sz, -s * sx);
@@ -304,15 +305,20 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
         const int L = __ffs(pend) - 1;
         const unsigned grp = __shfl_sync(kFull, same, L) & pend;
         const unsigned key = __shfl_sync(kFull, seg_key, L);
-        unsigned long long *dst = p.prob[key & 63u].tally + (size_t)((key >> 6) - 1u) * p.Cpad;
+        unsigned long long *dst = p.prob[BATCH ? (key & 63u) : 0].tally + (size_t)((key >> 6) - 1u) * p.Cpad;
         long long acc[NP];
+        // |t h 2^q| < 2^31 by the choice of q, so a 32-bit conversion suffices
+        const float tsL = __shfl_sync(kFull, seg_ts, L);
+        const float *hrL = rows + L * p.row_stride + 1;
 #pragma unroll
-        for (int q = 0; q < NP; ++q) acc[q] = 0;
-        unsigned g = grp;
+        for (int q = 0; q < NP; ++q) {
+          const int j = q * 32 + lane;
+          acc[q] = j < C ? (long long)__float2int_rn(tsL * hrL[j]) : 0;
+        }
+        unsigned g = grp & (grp - 1);  // other lanes in the same tally row (rare outside beams)
         while (g) {
           const int M = __ffs(g) - 1;
           g &= g - 1;
-          // |t h 2^q| < 2^31 by the choice of q, so a 32-bit conversion suffices
           const float ts = __shfl_sync(kFull, seg_ts, M);
           const float *hr = rows + M * p.row_stride + 1;
 #pragma unroll

@@ -2,7 +2,7 @@
 
 Pairs are (low-count, high-count) forward harmonic maps of the same random inclusion phantom,
 both produced by the batched forward MC (mc_run_batch) with independent packets; the high-count
-map is the training target and, on held-out phantoms, the judge of the denoiser's error.
+map is the training target and, on held-out phantoms, the yardstick of the denoiser's error.
 """
 from __future__ import annotations
 

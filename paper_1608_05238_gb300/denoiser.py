@@ -3,7 +3,7 @@
 The forward and adjoint MC (Secs. 3-4) deliver per-pixel Fourier coefficients a_0, a_n, b_n
 (Eqs. 8-11) whose noise falls like 1/sqrt(N_p).  The denoiser maps a low-packet-count map
 (2K+1 channels) to an estimate of the high-count map, trained on pairs the MC itself generates;
-full-count MC remains the reference that judges its error.  (The paper has no learned part.)
+full-count MC remains the reference that measures its error.  (The paper has no learned part.)
 
 Architecture: 4 levels with 32/64/128/256 channels, two 3x3 convolutions + ReLU per level,
 2x2 average pooling down, nearest 2x up-sampling + skip concatenation up, a 1x1 output head, and

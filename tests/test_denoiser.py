@@ -136,7 +136,7 @@ def test_unet_training_reduces_loss():
 
 def test_denoiser_trained_on_mc_pairs_beats_low_count_mc():
     """Trained on pairs the MC generates, the denoiser moves low-count maps closer to the
-    high-count MC (the judge of its error) than the low-count MC itself is, on held-out phantoms."""
+    high-count MC (the yardstick of its error) than the low-count MC itself is, on held-out phantoms."""
     from paper_1608_05238_gb300 import denoise_train as dt
     K, n = 8, 128
     x, t = dt.make_pairs(72, n=n, dx=0.1, K=K, n_low=20_000, n_high=2_000_000, seed0=20_000)
