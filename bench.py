@@ -420,6 +420,9 @@ def _denoise256(args):
     train_s = a.elapsed_time(b) / 1e3
     ops.check()
     res = dt.evaluate(net, x[n_train:], t[n_train:])
+    # equal-error comparison: plain MC at growing packet counts on the held-out phantoms
+    curve = dt.plain_mc_error_curve(t[n_train:], [n_low, 2 * n_low, 4 * n_low, 8 * n_low], n=n, dx=dx, K=K,
+                                    first=n_train)
     xb = x[:batch].contiguous()
     sc = sample_scale(xb)
     net.predict(xb, sc)
@@ -431,6 +434,14 @@ def _denoise256(args):
     b.synchronize()
     infer_s = a.elapsed_time(b) / 1e3 / 10
     alg, exe = _unet_flops(net, batch, n, n)
+    ms_per_packet = np.polyfit([c[0] for c in curve], [c[3] for c in curve], 1)[0]
+    ms_denoised = curve[0][3] + 1e3 * infer_s / batch  # n_low-packet MC map + its share of a batch inference
+    equal = {}
+    for which, key in ((1, "all_channels"), (2, "fluence_a0")):
+        m_eq = dt.packets_at_error(curve, res["err_denoised" if which == 1 else "err_a0_denoised"], which)
+        ms_plain = curve[0][3] + ms_per_packet * (m_eq - n_low)
+        equal[key] = {"plain_mc_packets_at_denoised_error": m_eq, "plain_mc_ms_per_map": ms_plain,
+                      "denoised_ms_per_map": ms_denoised, "speedup_at_equal_error": ms_plain / ms_denoised}
     # one large convolution (8 x 256 x 256 pixels, 128 -> 128 channels, 3x3) timed alone
     xc = torch.randn(8, 256, 256, 128, device="cuda").bfloat16()
     wc = (torch.randn(128, 9, 128, device="cuda") * 0.03).bfloat16()
@@ -462,7 +473,10 @@ def _denoise256(args):
                       "train_tflops_executed": 3 * exe * steps / train_s / 1e12,
                       "infer_tflops_executed": exe / infer_s / 1e12,
                       "unet_forward_gflop_alg": alg / batch / 1e9, "unet_forward_gflop_executed": exe / batch / 1e9,
-                      "heldout": res},
+                      "heldout": res,
+                      "plain_mc_curve": [{"packets": c[0], "err": c[1], "err_a0": c[2], "ms_per_map": c[3]}
+                                         for c in curve],
+                      "equal_error": equal},
            "roofline": {"bound": "tensor", "achieved": conv_tf, "peak": peak, "unit": "TFLOP/s", "frac": conv_tf / peak,
                         "traffic": None, "kernel": "k_conv_ws (8x256x256, 128->128, 3x3)",
                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"},

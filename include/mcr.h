@@ -79,6 +79,8 @@ typedef struct {
   uint32_t max_events;   /* flights per packet before it is ended (watchdog, e.g. 1e7) */
   float w_threshold;     /* Russian roulette once |W| < w_threshold |W0| (e.g. 1e-4) */
   float roulette_p;      /* roulette survival probability p, 0 < p <= 1; survivors W <- W/p */
+  uint32_t accumulate;   /* 0: write coeff; 1: add this run's coefficients to coeff (the fluences of
+                            several sources of one illumination sum, Eq. 5 is linear in q) */
 } mcr_run;
 
 /* Run counters (host struct filled when a non-NULL pointer is passed; synchronises). */
@@ -159,10 +161,16 @@ typedef struct {
 } mcr_problem;
 
 /* Launch shape of the persistent transport kernel; 0 fields take the defaults (128 threads per
- * block, as many blocks per SM as fit). */
+ * block, as many blocks per SM as fit; collision merge where the second harmonic row per lane
+ * costs no resident warps, or, with 96-thread blocks, where the tallies exceed 256 MB and their
+ * reductions go to HBM).  A shape whose shared memory does not fit fails with MCR_ERR_CUDA.
+ * The collision merge deposits a segment that ends in a surviving collision together with the
+ * packet's next segment (same pixel) in one row reduction; the tally is bit-identical either way,
+ * only the speed and the shared memory per block (one or two harmonic rows per lane) differ. */
 typedef struct {
   int32_t threads_per_block; /* multiple of 32, <= 256 */
   int32_t blocks_per_sm;     /* cap on resident blocks per SM */
+  int32_t merge_collisions;  /* 0 default, 1 off, 2 on */
 } mcr_launch;
 
 /*

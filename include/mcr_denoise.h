@@ -98,6 +98,10 @@ int dn_adam(float *w, float *m, float *v, float *g, int32_t cout, int32_t taps, 
             float beta2, float eps, int32_t step, void *wf, int32_t cin_pad, void *wd, int32_t cout_pad, void *stream);
 int dn_adam_bias(float *b, float *m, float *v, float *g, int32_t n, float lr, float beta1, float beta2, float eps,
                  int32_t step, void *stream);
+/* Per-sample input scale of channel-major fp32 maps [B][C][HW] (device): scale[b] = 1 / mean of
+ * channel 0 (the fluence a_0) over the HW pixels of sample b, clamped below at 1e-30; FP64 sum in
+ * a fixed order.  scale: device out [B] fp32. */
+int dn_sample_scale(const float *src, int32_t B, int64_t HW, int32_t C, float *scale, void *stream);
 /* channel-major fp32 maps [B][C][HW] times scale[b] -> NHWC bf16 [B][HW][stride] (input) or NHWC
  * fp32 [B][HW][C] (target); and back (output / scale). */
 int dn_pack_input(const float *src, const float *scale, int32_t B, int64_t HW, int32_t C, void *dst, int32_t stride,

@@ -18,7 +18,7 @@ gradient of the scalar loss and its product with dL/dH).
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 
 import torch
 
@@ -58,10 +58,11 @@ class MCSpec:
 
 
 def forward_coefficients(med: mcr.Medium, spec: MCSpec) -> torch.Tensor:
-    """Forward coefficients of the whole illumination (sum over ``spec.sources``)."""
+    """Forward coefficients of the whole illumination (sum over ``spec.sources``, added by the
+    library's finalize kernel: the RTE is linear in the source)."""
     coeff = mcr.forward(med, spec.sources[0], spec.forward_run(0))
     for s in range(1, len(spec.sources)):
-        coeff.add_(mcr.forward(med, spec.sources[s], spec.forward_run(s)))
+        mcr.forward(med, spec.sources[s], replace(spec.forward_run(s), accumulate=True), out=coeff)
     return coeff
 
 

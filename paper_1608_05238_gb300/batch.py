@@ -9,9 +9,10 @@ adds:
   graph captured once (the packing, CDF, transport and finalize launches of the whole batch
   become one graph launch).  A graph replays the same packets (its seeds are baked in); build a
   new runner, or call ``recapture(seed)``, for a fresh ensemble.
-* ``autotune`` -- times the candidate launch shapes (threads per block, resident blocks per SM)
-  on the actual batch with CUDA events and keeps the fastest, cached per device, K and batch
-  size.  Results do not depend on the shape (fixed-point tallies), only the time does.
+* ``autotune`` -- times the candidate launch shapes (threads per block, resident blocks per SM,
+  collision merge default/off/on) on the actual batch with CUDA events and keeps the fastest,
+  cached per device, K and batch size.  Results do not depend on the shape (fixed-point
+  tallies), only the time does.
 """
 from __future__ import annotations
 
@@ -23,7 +24,7 @@ import torch
 
 from . import mcr
 
-DEFAULT_CANDIDATES = ((128, 0), (256, 0), (64, 0), (128, 4), (256, 2))
+DEFAULT_CANDIDATES = ((128, 0, 0), (128, 0, 1), (256, 0, 1), (64, 0, 2), (128, 4, 1), (256, 2, 0))
 _cache: dict = {}
 
 
@@ -36,7 +37,8 @@ def _key(problems, common: mcr.Run):
 
 def autotune(problems: list, common: mcr.Run, candidates=DEFAULT_CANDIDATES, reps: int = 2,
              cache_path: str | None = None) -> tuple:
-    """Fastest (threads_per_block, blocks_per_sm) for this batch, measured with CUDA events."""
+    """Fastest (threads_per_block, blocks_per_sm, merge_collisions) for this batch, measured
+    with CUDA events."""
     key = _key(problems, common)
     if key in _cache:
         return _cache[key]
@@ -50,17 +52,21 @@ def autotune(problems: list, common: mcr.Run, candidates=DEFAULT_CANDIDATES, rep
             pass
     stream = torch.cuda.current_stream()
     timings = {}
-    mcr.run_batch(problems, common, launch=candidates[0])  # warm-up, grows the workspace
+    mcr.run_batch(problems, common)  # warm-up, grows the workspace
     for cand in candidates:
         best = float("inf")
         for _ in range(reps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            mcr.run_batch(problems, common, launch=cand)
+            try:
+                mcr.run_batch(problems, common, launch=cand)
+            except mcr.McrError:  # shape does not fit this K (shared memory): skip it
+                break
             b.record(stream)
             b.synchronize()
             best = min(best, a.elapsed_time(b))
-        timings[cand] = best
+        if best < float("inf"):
+            timings[cand] = best
     choice = min(timings, key=timings.get)
     _cache[key] = choice
     if cache_path:
@@ -70,7 +76,7 @@ def autotune(problems: list, common: mcr.Run, candidates=DEFAULT_CANDIDATES, rep
                 stored = json.load(open(cache_path))
             except (OSError, ValueError):
                 stored = {}
-        stored[key] = {"launch": list(choice), "ms": {f"{t}x{b}": ms for (t, b), ms in timings.items()}}
+        stored[key] = {"launch": list(choice), "ms": {"x".join(map(str, c)): ms for c, ms in timings.items()}}
         with open(cache_path, "w") as f:
             json.dump(stored, f, indent=1)
     return choice

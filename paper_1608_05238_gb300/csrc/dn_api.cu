@@ -276,6 +276,11 @@ int dn_pack_input(const float *src, const float *scale, int32_t B, int64_t HW, i
   DN_TRY(pack_input(src, scale, B, HW, C, static_cast<__nv_bfloat16 *>(dst), stride, (cudaStream_t)stream));
 }
 
+int dn_sample_scale(const float *src, int32_t B, int64_t HW, int32_t C, float *scale, void *stream) {
+  if (!src || !scale || B <= 0 || HW <= 0 || C <= 0) return MCR_ERR_ARG;
+  DN_TRY(sample_scale(src, B, HW, C, scale, (cudaStream_t)stream));
+}
+
 int dn_pack_target(const float *src, const float *scale, int32_t B, int64_t HW, int32_t C, float *dst, void *stream) {
   if (!src || !scale || !dst || B <= 0 || HW <= 0 || C <= 0) return MCR_ERR_ARG;
   DN_TRY(pack_target(src, scale, B, HW, C, dst, (cudaStream_t)stream));

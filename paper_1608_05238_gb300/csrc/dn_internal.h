@@ -67,6 +67,7 @@ cudaError_t adam_bias(float *b, float *m, float *v, float *g, int n, float lr, f
                       int step, cudaStream_t s);
 cudaError_t pack_input(const float *src, const float *scale, int B, long long HW, int C, __nv_bfloat16 *dst, int stride,
                        cudaStream_t s);
+cudaError_t sample_scale(const float *src, int B, long long HW, int C, float *scale, cudaStream_t s);
 cudaError_t pack_target(const float *src, const float *scale, int B, long long HW, int C, float *dst, cudaStream_t s);
 cudaError_t unpack_output(const float *src, const float *scale, int B, long long HW, int C, float *dst,
                           cudaStream_t s);

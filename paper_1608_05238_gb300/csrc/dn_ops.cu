@@ -250,6 +250,25 @@ __global__ void k_pack_input(const float *__restrict__ src, const float *__restr
   }
 }
 
+// per-sample input scale 1 / mean(channel 0) of channel-major fp32 maps [B][C][HW] (the fluence
+// a_0 of a harmonic map), one block per sample, FP64 sum in a fixed order
+__global__ void k_sample_scale(const float *__restrict__ src, int C, long long HW, float *__restrict__ scale) {
+  __shared__ double red[kT / 32];
+  const float *x = src + (size_t)blockIdx.x * C * HW;
+  double acc = 0.0;
+  for (long long i = threadIdx.x; i < HW; i += kT) acc += x[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kT / 32; ++k) s += red[k];
+    const double m = s / (double)HW;
+    scale[blockIdx.x] = (float)(1.0 / (m > 1e-30 ? m : 1e-30));
+  }
+}
+
 // channel-major fp32 [B][C][HW] * scale[b] -> NHWC fp32 [B][HW][C]   (training targets)
 __global__ void k_pack_target(const float *__restrict__ src, const float *__restrict__ scale, int B, long long HW,
                               int C, float *__restrict__ dst) {
@@ -346,6 +365,10 @@ cudaError_t adam_bias(float *b, float *m, float *v, float *g, int n, float lr, f
 cudaError_t pack_input(const float *src, const float *scale, int B, long long HW, int C, __nv_bfloat16 *dst, int stride,
                        cudaStream_t s) {
   k_pack_input<<<blocks_for((long long)B * HW * C), kT, 0, s>>>(src, scale, B, HW, C, dst, stride);
+  return cudaGetLastError();
+}
+cudaError_t sample_scale(const float *src, int B, long long HW, int C, float *scale, cudaStream_t s) {
+  k_sample_scale<<<B, kT, 0, s>>>(src, C, HW, scale);
   return cudaGetLastError();
 }
 cudaError_t pack_target(const float *src, const float *scale, int B, long long HW, int C, float *dst, cudaStream_t s) {

@@ -89,6 +89,7 @@ int check_run(const mcr_run *r) {
   if (!(r->roulette_p > 0.f && r->roulette_p <= 1.f)) return MCR_ERR_ARG;
   if (!(r->w_threshold >= 0.f) || !finite_f(r->w_threshold)) return MCR_ERR_ARG;
   if (r->first_packet + r->n_packets < r->first_packet) return MCR_ERR_ARG;  // id overflow
+  if (r->accumulate > 1u) return MCR_ERR_ARG;
   return MCR_OK;
 }
 
@@ -270,7 +271,8 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
     MCR_TRY_CUDA(launch_finalize(w->tally + tally_off[i], chunked ? w->acc : nullptr, npix, C, Cpad,
                                  chunked ? 1.0 : ldexp(1.0, -qexp[i]), fixed_scale, vol && h.n_packets > 0,
                                  w->qmax_bits(i), vol ? w->cdf + cdf_off[i] + (npix - 1) : nullptr,
-                                 (double)(h.n_packets ? h.n_packets : 1), vol, h.coeff, w->flags(), s));
+                                 (double)(h.n_packets ? h.n_packets : 1), vol, common->accumulate != 0, h.coeff,
+                                 w->flags(), s));
   }
   if (stats) {
     DevStats d;
@@ -293,7 +295,7 @@ int run_mc(const mcr_medium *med, const mcr_source *src, const float *qstar, con
   HostProblem h{med, src, qstar, run->n_packets, run->first_packet, run->seed, run->stream_id, coeff, 0.f, 1.f};
   if (!qstar && (rc = check_source(src, &h.dirx, &h.dirz))) return rc;
   std::lock_guard<std::mutex> lock(g_mu);
-  return enqueue({h}, run, TransportLaunch{0, 0}, qstar ? 1 : 0, stats, s);
+  return enqueue({h}, run, TransportLaunch{0, 0, 0}, qstar ? 1 : 0, stats, s);
 }
 
 }  // namespace
@@ -317,12 +319,12 @@ int mc_run_batch(const mcr_problem *problems, int32_t n_problems, const mcr_run 
   int rc;
   if (!problems || n_problems < 1 || n_problems > MCR_MAX_BATCH) return MCR_ERR_ARG;
   if ((rc = check_run(common))) return rc;
-  TransportLaunch cfg{0, 0};
+  TransportLaunch cfg{0, 0, 0};
   if (launch) {
     if (launch->threads_per_block < 0 || launch->threads_per_block > 256 || launch->threads_per_block % 32 ||
-        launch->blocks_per_sm < 0)
+        launch->blocks_per_sm < 0 || launch->merge_collisions < 0 || launch->merge_collisions > 2)
       return MCR_ERR_ARG;
-    cfg = TransportLaunch{launch->threads_per_block, launch->blocks_per_sm};
+    cfg = TransportLaunch{launch->threads_per_block, launch->blocks_per_sm, launch->merge_collisions};
   }
   std::vector<HostProblem> probs;
   uint64_t total = 0;

@@ -67,6 +67,7 @@ struct TransportParams {
 struct TransportLaunch {
   int threads_per_block;
   int blocks_per_sm;
+  int merge;  // collision merge: 0 library default, 1 off, 2 on
 };
 
 // Workspace of one device (grow-only).
@@ -104,7 +105,7 @@ static_assert(sizeof(DevStats) <= 128, "stats slot");
 cudaError_t launch_pack_medium(const float *mua, const float *mus, float4 *mu, int64_t npix, unsigned *flags,
                                cudaStream_t s);
 cudaError_t launch_transport(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s);
-size_t transport_smem_bytes(int row_stride, int threads);
+size_t transport_smem_bytes(int row_stride, int threads, bool merge);
 cudaError_t launch_source_cdf(const float *q, int64_t npix, unsigned long long *cdf,
                               unsigned long long *block_sums, size_t block_sums_cap, unsigned *qmax_bits,
                               cudaStream_t s);
@@ -116,8 +117,8 @@ cudaError_t launch_accumulate(const unsigned long long *tally, int64_t npix, int
 // 2 pi qmax total 2^-32 / N_p (volumetric: read on device).
 cudaError_t launch_finalize(const unsigned long long *tally, const double *acc, int64_t npix, int C, int Cpad,
                             double quantum, double fixed_scale, bool volumetric, const unsigned *qmax_bits,
-                            const unsigned long long *cdf_total, double n_packets, bool adjoint, float *coeff,
-                            unsigned *flags, cudaStream_t s);
+                            const unsigned long long *cdf_total, double n_packets, bool adjoint, bool accumulate,
+                            float *coeff, unsigned *flags, cudaStream_t s);
 cudaError_t launch_h_eps(const float *mua, const float *a0, const float *Hmeas, int64_t npix, double area, float *H,
                          float *dL_dH, double *partials, size_t partials_cap, double *eps, cudaStream_t s);
 cudaError_t launch_adjoint_source(const float *mua, const float *dL_dH, int64_t npix, double area, float *q,

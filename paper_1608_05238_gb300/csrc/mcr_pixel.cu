@@ -104,7 +104,7 @@ __global__ void k_accumulate(const unsigned long long *__restrict__ tally, int64
 __global__ void k_finalize(const unsigned long long *__restrict__ tally, const double *__restrict__ acc,
                            int64_t npix, int C, int Cpad, double quantum, double fixed_scale, int volumetric,
                            const unsigned *qmax_bits, const unsigned long long *cdf_total, double n_packets,
-                           int adjoint, float *__restrict__ coeff, unsigned *flags) {
+                           int adjoint, int accumulate, float *__restrict__ coeff, unsigned *flags) {
   extern __shared__ long long tile[];  // [32][Cpad]
   const int64_t p0 = (int64_t)blockIdx.x * 32;
   const int npx = npix - p0 < 32 ? (int)(npix - p0) : 32;
@@ -133,7 +133,8 @@ __global__ void k_finalize(const unsigned long long *__restrict__ tally, const d
         v = acc[(int64_t)c * npix + pix] * scale;
       else
         v = (double)tile[threadIdx.x * Cpad + c] * quantum * scale;
-      coeff[(int64_t)c * npix + pix] = (float)(sgn * v);
+      float *o = coeff + (int64_t)c * npix + pix;
+      *o = accumulate ? *o + (float)(sgn * v) : (float)(sgn * v);
     }
   }
   if (__syncthreads_or(near_overflow) && tid == 0) atomicOr(flags, kFlagOverflow);
@@ -241,13 +242,13 @@ cudaError_t launch_accumulate(const unsigned long long *tally, int64_t npix, int
 
 cudaError_t launch_finalize(const unsigned long long *tally, const double *acc, int64_t npix, int C, int Cpad,
                             double quantum, double fixed_scale, bool volumetric, const unsigned *qmax_bits,
-                            const unsigned long long *cdf_total, double n_packets, bool adjoint, float *coeff,
-                            unsigned *flags, cudaStream_t s) {
+                            const unsigned long long *cdf_total, double n_packets, bool adjoint, bool accumulate,
+                            float *coeff, unsigned *flags, cudaStream_t s) {
   const dim3 block(32, 8);
   const size_t smem = acc ? 0 : (size_t)32 * Cpad * sizeof(long long);
   k_finalize<<<(unsigned)((npix + 31) / 32), block, smem, s>>>(tally, acc, npix, C, Cpad, quantum, fixed_scale,
                                                               volumetric ? 1 : 0, qmax_bits, cdf_total, n_packets,
-                                                              adjoint ? 1 : 0, coeff, flags);
+                                                              adjoint ? 1 : 0, accumulate ? 1 : 0, coeff, flags);
   return cudaGetLastError();
 }
 

@@ -21,7 +21,13 @@
 //    the warp take one coefficient each, sum the contributions of every lane in that row (warp
 //    reduction via match_any on the row address) as 64-bit fixed-point integers, and issue one
 //    coalesced red.add per coefficient into the pixel-major tally [pix][Cpad].  Integer sums are
-//    exact, so the tally does not depend on scheduling.  Deposits are rounded to 2^-q with q
+//    exact, so the tally does not depend on scheduling.
+//  * Collision merge (MERGE): a segment that ends in a collision the packet survives is not
+//    deposited at once; it rides along with the next segment, which starts in the same pixel,
+//    and both are added into one row reduction.  Each lane keeps two harmonic rows (the previous
+//    flight's and the current one), and every term is still rounded on its own, so the integer
+//    tally is identical to the unmerged one while the L2 sees one row reduction fewer per such
+//    collision.  Deposits are rounded to 2^-q with q
 //    chosen per problem so that one deposit fits in int32: the conversion is a 32-bit one (the
 //    64-bit conversion runs on the FP64 pipe, which is narrow on this part).
 #include <math_constants.h>
@@ -32,6 +38,8 @@ namespace mcr {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kRowsPerStep = 2;  // independent single-lane rows deposited per step
+constexpr double kL2SpillBytes = 256.0 * 1024 * 1024;  // tallies beyond this live in HBM
 
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32->64 products and
 // xors, Weyl-incremented key.
@@ -81,16 +89,20 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-template <int NP, bool BATCH>
+template <int NP, bool BATCH, bool MERGE>
 __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ TransportParams p) {
   extern __shared__ float smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  float *const rows = smem + (size_t)warp * 32 * p.row_stride;
-  float *const my = rows + lane * p.row_stride;
+  // harmonic rows of this warp: row r of lane l at rows + (r * 32 + l) * row_stride (r < 2 with MERGE)
+  float *const rows = smem + (size_t)warp * (MERGE ? 64 : 32) * p.row_stride;
   if (*p.flags & kFlagMedium) return;
 
   const int K = p.K, C = p.C;
+  // Coefficients [0, Cw) are deposited warp-cooperatively (32 per instruction); a short remainder
+  // [Cw, C) of at most 4 (the last b_K when 2K+1 = 32 m + 1) is deposited by each lane into its
+  // own row, all lanes in one instruction, instead of one nearly empty instruction per row.
+  const int Cw = (C & 31) <= 4 ? (C & ~31) : C;
 
   bool alive = false, exhausted = false;
   unsigned long long pid = 0;
@@ -113,6 +125,9 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
   float fx = 0.f, fz = 0.f, sx = 0.f, sz = 1.f, inv_ax = 0.f, inv_az = 0.f, W = 0.f, tau = 0.f;
   int ix = 0, iz = 0;
   unsigned flight = 0, nscat = 0, cu1 = 0, cu2 = 0;
+  int rb = 0;             // row of the current flight's harmonics
+  int carry_rb = 0;       // row of the deferred segment's harmonics
+  float carry = 0.f;      // deferred track weight (times 2^q) of a collision segment, 0: none
   unsigned n_launch = 0, n_flight = 0, n_coll = 0, n_seg = 0, n_esc = 0, n_rrk = 0, n_rrs = 0, n_scl = 0,
            n_evl = 0;
   double w_launch = 0.0, w_esc = 0.0, w_rr = 0.0, w_kill = 0.0;
@@ -121,6 +136,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
   // right (my[1 + c] holds channel c) so that each (cos n theta, sin n theta) pair is one
   // 8-byte aligned store; the row stride is 2 mod 4 words, so these stores are conflict-free.
   auto write_row = [&]() {
+    float *const my = rows + (rb * 32 + lane) * p.row_stride;
     my[1] = 1.f;
     float c = sz, s = sx;
     float2 *pairs = reinterpret_cast<float2 *>(my);
@@ -142,6 +158,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     inv_ax = __frcp_rn(fabsf(sx));
     inv_az = __frcp_rn(fabsf(sz));
     ++n_flight;
+    if (MERGE) rb ^= 1;  // keep the previous flight's row for a deferred segment
     write_row();
   };
 
@@ -249,6 +266,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     // ---------------------------------------------------------------- one pixel segment
     unsigned seg_key = 0u;  // (pixel + 1) << 6 | problem of this lane's segment (0: none)
     float seg_ts = 0.f;     // its track weight times 2^q
+    float dep_carry = 0.f;  // a deferred segment deposited with this one (same pixel)
     bool collided = false, escaped = false;
     if (alive) {
       const int pix = iz * NX() + ix;
@@ -265,9 +283,24 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
       const float t = m.x > 0.f ? (-W * em1) * m.z : W * l;
       W = fmaf(W, em1, W);
       ++n_seg;
-      if (t != 0.f) {
+      if (MERGE) {
+        dep_carry = carry;
+        carry = 0.f;
+      }
+      if (t != 0.f || dep_carry != 0.f) {
         seg_key = ((unsigned)(pix + 1) << 6) | (unsigned)(BATCH ? prob : 0);
         seg_ts = t * QS();
+      }
+      if (MERGE && collided && dep_carry == 0.f && t != 0.f) {
+        // defer if the packet survives this collision (the same tests as below): its next
+        // segment starts in this pixel
+        const bool dies = nscat >= p.max_scatter ||
+                          (fabsf(W) < p.w_threshold && !(u01(cu2) < p.rr_p)) || flight >= p.max_events;
+        if (!dies) {
+          carry = seg_ts;
+          carry_rb = rb;
+          seg_key = 0u;
+        }
       }
       if (collided) {
         fx = clamp_dx(fmaf(l, sx, fx), DX());
@@ -301,6 +334,36 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     unsigned pend = __ballot_sync(kFull, seg_key != 0u);
     if (pend) {
       const unsigned same = __match_any_sync(kFull, seg_key);
+      // Rows of a single lane without a carried segment (nearly all of them away from the source)
+      // go kRowsPerStep at a time: their shuffles, loads, conversions and reductions are
+      // independent, so they overlap instead of running as one dependent chain per row.
+      unsigned easy = pend & __ballot_sync(kFull, seg_key != 0u && same == (1u << lane) && !(MERGE && dep_carry != 0.f));
+      pend &= ~easy;
+      while (easy) {
+        bool on[kRowsPerStep];
+        float ts[kRowsPerStep];
+        unsigned long long *dst[kRowsPerStep];
+        const float *hr[kRowsPerStep];
+#pragma unroll
+        for (int r = 0; r < kRowsPerStep; ++r) {
+          on[r] = easy != 0u;  // warp-uniform
+          const int L = on[r] ? __ffs(easy) - 1 : 0;
+          easy &= easy - 1u;
+          const unsigned key = on[r] ? __shfl_sync(kFull, seg_key, L) : 64u;
+          ts[r] = __shfl_sync(kFull, seg_ts, L);
+          dst[r] = p.prob[BATCH ? (key & 63u) : 0].tally + (size_t)((key >> 6) - 1u) * p.Cpad;
+          hr[r] = rows + ((MERGE ? __shfl_sync(kFull, rb, L) * 32 : 0) + L) * p.row_stride + 1;
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const int j = q * 32 + lane;
+          if (j < Cw) {
+#pragma unroll
+            for (int r = 0; r < kRowsPerStep; ++r)
+              if (on[r]) atomicAdd(dst[r] + j, (unsigned long long)(long long)__float2int_rn(ts[r] * hr[r][j]));
+          }
+        }
+      }
       while (pend) {
         const int L = __ffs(pend) - 1;
         const unsigned grp = __shfl_sync(kFull, same, L) & pend;
@@ -309,30 +372,62 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
         long long acc[NP];
         // |t h 2^q| < 2^31 by the choice of q, so a 32-bit conversion suffices
         const float tsL = __shfl_sync(kFull, seg_ts, L);
-        const float *hrL = rows + L * p.row_stride + 1;
+        const float *hrL = rows + ((MERGE ? __shfl_sync(kFull, rb, L) * 32 : 0) + L) * p.row_stride + 1;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
           const int j = q * 32 + lane;
-          acc[q] = j < C ? (long long)__float2int_rn(tsL * hrL[j]) : 0;
+          acc[q] = j < Cw ? (long long)__float2int_rn(tsL * hrL[j]) : 0;
+        }
+        if (MERGE) {
+          const float cL = __shfl_sync(kFull, dep_carry, L);
+          if (cL != 0.f) {
+            const float *hc = rows + (__shfl_sync(kFull, carry_rb, L) * 32 + L) * p.row_stride + 1;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+              const int j = q * 32 + lane;
+              if (j < Cw) acc[q] += (long long)__float2int_rn(cL * hc[j]);
+            }
+          }
         }
         unsigned g = grp & (grp - 1);  // other lanes in the same tally row (rare outside beams)
         while (g) {
           const int M = __ffs(g) - 1;
           g &= g - 1;
           const float ts = __shfl_sync(kFull, seg_ts, M);
-          const float *hr = rows + M * p.row_stride + 1;
+          const float *hr = rows + ((MERGE ? __shfl_sync(kFull, rb, M) * 32 : 0) + M) * p.row_stride + 1;
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
             const int j = q * 32 + lane;
-            if (j < C) acc[q] += (long long)__float2int_rn(ts * hr[j]);
+            if (j < Cw) acc[q] += (long long)__float2int_rn(ts * hr[j]);
+          }
+          if (MERGE) {
+            const float cM = __shfl_sync(kFull, dep_carry, M);
+            if (cM != 0.f) {
+              const float *hc = rows + (__shfl_sync(kFull, carry_rb, M) * 32 + M) * p.row_stride + 1;
+#pragma unroll
+              for (int q = 0; q < NP; ++q) {
+                const int j = q * 32 + lane;
+                if (j < Cw) acc[q] += (long long)__float2int_rn(cM * hc[j]);
+              }
+            }
           }
         }
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
           const int j = q * 32 + lane;
-          if (j < C) atomicAdd(dst + j, (unsigned long long)acc[q]);
+          if (j < Cw) atomicAdd(dst + j, (unsigned long long)acc[q]);
         }
         pend &= ~grp;
+      }
+      if (Cw < C && seg_key != 0u) {  // the per-lane remainder
+        unsigned long long *own = p.prob[BATCH ? (seg_key & 63u) : 0].tally + (size_t)((seg_key >> 6) - 1u) * p.Cpad;
+        const float *h = rows + ((MERGE ? rb * 32 : 0) + lane) * p.row_stride + 1;
+        const float *hc = rows + ((MERGE ? carry_rb * 32 : 0) + lane) * p.row_stride + 1;
+        for (int j = Cw; j < C; ++j) {
+          long long v = (long long)__float2int_rn(seg_ts * h[j]);
+          if (MERGE && dep_carry != 0.f) v += (long long)__float2int_rn(dep_carry * hc[j]);
+          atomicAdd(own + j, (unsigned long long)v);
+        }
       }
     }
     __syncwarp();
@@ -419,45 +514,88 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
   }
 }
 
-template <int NP, bool BATCH>
-cudaError_t launch_kernel(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s) {
-  const int threads = cfg.threads_per_block > 0 ? cfg.threads_per_block : 128;
-  if (threads % 32 || threads > 256) return cudaErrorInvalidValue;
-  const size_t smem = transport_smem_bytes(p.row_stride, threads);
+// Opts the kernel into `smem` bytes of dynamic shared memory (once per device) and returns how
+// many blocks of `threads` fit on one SM.
+template <int NP, bool BATCH, bool MERGE>
+cudaError_t blocks_per_sm(int threads, size_t smem, int *per_sm) {
   static int configured[64];  // largest dynamic smem opted in, per device
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  if (smem > 232448) {  // more than a block may have: does not fit
+    *per_sm = 0;
+    return cudaSuccess;
+  }
   if (dev >= 64 || configured[dev] < (int)smem) {
-    e = cudaFuncSetAttribute(k_transport<NP, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_transport<NP, BATCH, MERGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (dev < 64) configured[dev] = (int)smem;
   }
-  int sms = 0, per_sm = 0;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_transport<NP, BATCH, MERGE>, threads, smem);
+}
+
+template <int NP, bool BATCH, bool MERGE>
+cudaError_t launch_kernel(const TransportParams &p, int threads, int cap, cudaStream_t s) {
+  if (threads % 32 || threads > 256 || threads <= 0) return cudaErrorInvalidValue;
+  const size_t smem = transport_smem_bytes(p.row_stride, threads, MERGE);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport<NP, BATCH>, threads, smem);
+  e = blocks_per_sm<NP, BATCH, MERGE>(threads, smem, &per_sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < per_sm) per_sm = cfg.blocks_per_sm;
-  k_transport<NP, BATCH><<<sms * per_sm, threads, smem, s>>>(p);
+  if (cap > 0 && cap < per_sm) per_sm = cap;
+  k_transport<NP, BATCH, MERGE><<<sms * per_sm, threads, smem, s>>>(p);
   return cudaGetLastError();
+}
+
+// Default deposit mode: merge collisions when the second harmonic row per lane costs no resident
+// warps; otherwise only when the tallies are far larger than L2 (their reductions then go to
+// HBM and are the cost that matters), with 96-thread blocks.
+template <int NP, bool BATCH>
+cudaError_t launch_b(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s) {
+  int threads = cfg.threads_per_block > 0 ? cfg.threads_per_block : 128;
+  bool merge = cfg.merge == 2;
+  if (cfg.merge == 0) {
+    int plain = 0, merged = 0;
+    cudaError_t e = blocks_per_sm<NP, BATCH, false>(threads, transport_smem_bytes(p.row_stride, threads, false), &plain);
+    if (e != cudaSuccess) return e;
+    e = blocks_per_sm<NP, BATCH, true>(threads, transport_smem_bytes(p.row_stride, threads, true), &merged);
+    if (e != cudaSuccess) return e;
+    merge = merged >= plain;
+    if (!merge && cfg.threads_per_block == 0) {
+      double tally = 0.0;
+      for (int i = 0; i < p.n_problems; ++i) tally += (double)p.prob[i].nx * p.prob[i].nz * p.Cpad * 8.0;
+      if (tally > kL2SpillBytes) {
+        merge = true;
+        threads = 96;
+      }
+    }
+  }
+  return merge ? launch_kernel<NP, BATCH, true>(p, threads, cfg.blocks_per_sm, s)
+               : launch_kernel<NP, BATCH, false>(p, threads, cfg.blocks_per_sm, s);
 }
 
 // a table of one reads its problem as uniform parameters; larger tables cache it per lane
 template <int NP>
 cudaError_t launch_np(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s) {
-  return p.n_problems > 1 ? launch_kernel<NP, true>(p, cfg, s) : launch_kernel<NP, false>(p, cfg, s);
+  return p.n_problems > 1 ? launch_b<NP, true>(p, cfg, s) : launch_b<NP, false>(p, cfg, s);
 }
 
 }  // namespace
 
-size_t transport_smem_bytes(int row_stride, int threads) {
-  return (size_t)threads * row_stride * sizeof(float);
+size_t transport_smem_bytes(int row_stride, int threads, bool merge) {
+  return (size_t)threads * row_stride * sizeof(float) * (merge ? 2 : 1);
 }
 
+
+
 cudaError_t launch_transport(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s) {
-  const int np = (p.C + 31) / 32;
+  // chunks of 32 coefficients deposited cooperatively (a remainder of <= 4 goes per lane)
+  const int cw = (p.C & 31) <= 4 ? (p.C & ~31) : p.C;
+  const int np = cw > 32 ? (cw + 31) / 32 : 1;
   switch (np) {
     case 1: return launch_np<1>(p, cfg, s);
     case 2: return launch_np<2>(p, cfg, s);

@@ -27,7 +27,7 @@ class _Slice(C.Structure):
 
 
 EXPORTS = ("dn_conv", "dn_wgrad", "dn_to_ct", "dn_pool2", "dn_pool2_bwd", "dn_up2", "dn_up2_bwd", "dn_bias_grad",
-           "dn_mse", "dn_residual", "dn_adam", "dn_adam_bias", "dn_pack_input", "dn_pack_target",
+           "dn_mse", "dn_residual", "dn_adam", "dn_adam_bias", "dn_pack_input", "dn_sample_scale", "dn_pack_target",
            "dn_unpack_output", "dn_check")
 
 
@@ -51,6 +51,7 @@ def lib():
             "dn_adam": [vp, vp, vp, vp, i32, i32, i32, f32, f32, f32, f32, i32, vp, i32, vp, i32, vp],
             "dn_adam_bias": [vp, vp, vp, vp, i32, f32, f32, f32, f32, i32, vp],
             "dn_pack_input": [vp, vp, i32, i64, i32, vp, i32, vp],
+            "dn_sample_scale": [vp, i32, i64, i32, vp, vp],
             "dn_pack_target": [vp, vp, i32, i64, i32, vp, vp],
             "dn_unpack_output": [vp, vp, i32, i64, i32, vp, vp],
             "dn_check": [vp],
@@ -157,6 +158,12 @@ def adam_bias(b, m, v, g, lr, b1, b2, eps, step, stream=None):
 def pack_input(src: torch.Tensor, scale: torch.Tensor, dst: torch.Tensor, stream=None):
     B, Cc = src.shape[0], src.shape[1]
     _call("dn_pack_input", _p(src), _p(scale), B, src.shape[2] * src.shape[3], Cc, _p(dst), dst.shape[3],
+          _stream(stream))
+
+
+def sample_scale(src: torch.Tensor, scale: torch.Tensor, stream=None):
+    """scale[b] = 1 / mean of channel 0 of the channel-major fp32 maps src [B][C][H][W]."""
+    _call("dn_sample_scale", _p(src), src.shape[0], src.shape[2] * src.shape[3], src.shape[1], _p(scale),
           _stream(stream))
 
 

@@ -71,3 +71,45 @@ def evaluate(net: UNet, x: torch.Tensor, t: torch.Tensor, batch: int = 8):
     cat = lambda v: torch.cat(v).mean().item()
     return {"err_input": cat(err_in), "err_denoised": cat(err_out), "err_a0_input": cat(e0_in),
             "err_a0_denoised": cat(e0_out)}
+
+
+def plain_mc_error_curve(t: torch.Tensor, counts, n: int = 256, dx: float = 0.05, K: int = 16,
+                         seed0: int = 10_000, first: int = 0):
+    """Error of plain (not denoised) MC against the high-count targets ``t`` of the phantoms
+    ``seed0 + first + i`` as a function of the packet count, with the MC time per map.
+
+    Returns [(packets, mean relative L2 error, mean fluence-channel error, ms per map)], the maps
+    drawn with fresh packets (stream 2) so that they share none with the inputs or targets.
+    """
+    C = 2 * K + 1
+    common = mcr.Run(K=K, n_packets=0)
+    src = mcr.Source(**workloads.top_line_source(n, dx))
+    dx32, g32 = float(np.float32(dx)), float(np.float32(0.9))
+    meds = []
+    for i in range(t.shape[0]):
+        mua, mus = workloads.inclusion_phantom(n, dx, 3, seed=seed0 + first + i, margin=min(2.0, 0.15 * n * dx))
+        meds.append(mcr.Medium(torch.from_numpy(mua).to(t.device), torch.from_numpy(mus).to(t.device), dx32, g32))
+    out = torch.empty(t.shape[0], C, n, n, device=t.device)
+    curve = []
+    for m in counts:
+        probs = [mcr.Problem(md, int(m), seed=seed0 + first + i, stream_id=2, source=src, out=out[i])
+                 for i, md in enumerate(meds)]
+        mcr.run_batch(probs, common)  # warm-up (workspace size)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        mcr.run_batch(probs, common)
+        b.record()
+        b.synchronize()
+        curve.append((int(m), relative_error(out, t).mean().item(), relative_error(out[:, :1], t[:, :1]).mean().item(),
+                      a.elapsed_time(b) / t.shape[0]))
+    mcr.check()
+    return curve
+
+
+def packets_at_error(curve, err: float, which: int = 1) -> float:
+    """Packet count at which plain MC reaches ``err`` (log-log interpolation of the curve; the
+    error of plain MC falls as a power of the packet count).  ``which`` 1: all channels, 2: a_0."""
+    m = np.log([c[0] for c in curve])
+    e = np.log([c[which] for c in curve])
+    slope, icpt = np.polyfit(m, e, 1)
+    return float(np.exp((np.log(err) - icpt) / slope))

@@ -293,5 +293,7 @@ class UNet:
 
 def sample_scale(x: torch.Tensor) -> torch.Tensor:
     """Per-sample scale 1 / mean(a_0) (channel 0) so that inputs have unit mean fluence."""
-    m = x[:, 0].mean(dim=(1, 2))
-    return (1.0 / torch.clamp(m, min=1e-30)).float().contiguous()
+    x = x.contiguous()
+    scale = torch.empty(x.shape[0], device=x.device, dtype=torch.float32)
+    ops.sample_scale(x, scale)
+    return scale

@@ -51,7 +51,8 @@ class _Source(C.Structure):
 class _Run(C.Structure):
     _fields_ = [("K", C.c_int32), ("max_scatter", C.c_uint32), ("n_packets", C.c_uint64),
                 ("first_packet", C.c_uint64), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
-                ("max_events", C.c_uint32), ("w_threshold", C.c_float), ("roulette_p", C.c_float)]
+                ("max_events", C.c_uint32), ("w_threshold", C.c_float), ("roulette_p", C.c_float),
+                ("accumulate", C.c_uint32)]
 
 
 class _Problem(C.Structure):
@@ -60,7 +61,7 @@ class _Problem(C.Structure):
 
 
 class _Launch(C.Structure):
-    _fields_ = [("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32)]
+    _fields_ = [("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("merge_collisions", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -195,11 +196,12 @@ class Run:
     max_events: int = 10_000_000
     w_threshold: float = 1e-4
     roulette_p: float = 0.1
+    accumulate: bool = False  # add into ``out`` instead of overwriting it
 
     def c(self) -> _Run:
         return _Run(int(self.K), int(self.max_scatter), int(self.n_packets), int(self.first_packet),
                     int(self.seed) & 0xFFFFFFFFFFFFFFFF, int(self.stream_id), int(self.max_events),
-                    float(self.w_threshold), float(self.roulette_p))
+                    float(self.w_threshold), float(self.roulette_p), 1 if self.accumulate else 0)
 
 
 def _stats_dict(st: _Stats) -> dict:
@@ -276,7 +278,8 @@ def run_batch(problems: list, common: Run, launch: tuple | None = None, stats: b
     """All ``problems`` in one persistent transport launch (``mc_run_batch``); returns their outputs.
 
     ``common`` gives K and the termination parameters; ``launch`` = (threads_per_block,
-    blocks_per_sm) or None for the defaults.  The call can be captured in a CUDA graph once a
+    blocks_per_sm[, merge_collisions]) or None for the defaults (0 in a field: its default;
+    merge_collisions 1 off, 2 on).  The call can be captured in a CUDA graph once a
     first call has grown the library's workspace to this batch's size.
     """
     lib = load()

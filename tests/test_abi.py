@@ -6,7 +6,7 @@ import re
 
 import pytest
 
-from paper_1608_05238_gb300 import _build, mcr
+from paper_1608_05238_gb300 import _build, denoise_ops, mcr
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -17,7 +17,7 @@ def _declared_symbols():
         if f.endswith(".h"):
             text = open(os.path.join(ROOT, "include", f)).read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(mc_\w+)\s*\(", text, flags=re.M))
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*((?:mc|dn)_\w+)\s*\(", text, flags=re.M))
     return sorted(names)
 
 
@@ -29,9 +29,9 @@ def lib():
 
 def test_header_declares_the_boundary():
     names = _declared_symbols()
-    for n in ("mc_forward", "mc_adjoint", "mc_gradient", "mc_h_eps", "mc_adjoint_source"):
+    for n in ("mc_forward", "mc_adjoint", "mc_gradient", "mc_h_eps", "mc_adjoint_source", "dn_conv", "dn_wgrad"):
         assert n in names
-    assert set(names) == set(mcr.EXPORTS)
+    assert set(names) == set(mcr.EXPORTS) | set(denoise_ops.EXPORTS)
 
 
 def test_library_exports_every_declared_symbol(lib):

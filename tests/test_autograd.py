@@ -102,3 +102,30 @@ def test_mua_gradient_matches_crn_finite_differences_on_gpu():
         e[idx] = h
         fd[idx] = (eps(mua + e) - eps(mua - e)) / (2 * h)
     assert np.max(np.abs(ga - fd)) < 5e-3 * np.max(np.abs(fd))
+
+
+def test_two_source_illumination_accumulates_in_the_library():
+    """Several sources of one illumination: the library adds each run's coefficients into the
+    same output (accumulate), equal to the FP32 sum of separate runs, and the autograd forward
+    uses it."""
+    from paper_1608_05238_gb300.autograd import forward_coefficients
+    nz, nx, dx = 24, 20, 0.1
+    mua, mus = workloads.small_hetero(nz, nx, dx, seed=8)
+    med = mcr.Medium(torch.from_numpy(mua).cuda(), torch.from_numpy(mus).cuda(), f32(dx), f32(0.8))
+    top = mcr.Source(kind=mcr.LINE, x0=0.0, z0=0.0, x1=f32(nx * dx), z1=0.0, dir_x=0.0, dir_z=1.0)
+    left = mcr.Source(kind=mcr.LINE, x0=0.0, z0=0.0, x1=0.0, z1=f32(nz * dx), dir_x=1.0, dir_z=0.0, power=0.5)
+    spec = MCSpec(dx=f32(dx), g=f32(0.8), sources=[top, left], K=4, n_packets=50_000, seed=3)
+    a = mcr.forward(med, top, spec.forward_run(0))
+    b = mcr.forward(med, left, spec.forward_run(1))
+    both = forward_coefficients(med, spec)
+    assert torch.equal(both, a + b)
+    # the no-allocation entry point accumulates the same way
+    import ctypes as C
+    from dataclasses import replace
+    c = a.clone()
+    run = replace(spec.forward_run(1), accumulate=True)
+    rc = mcr.load().mc_forward_noalloc(C.byref(med.c()), C.byref(left.c()), C.byref(run.c()),
+                                       C.c_void_p(c.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert torch.equal(c, both)

@@ -80,11 +80,30 @@ def test_launch_shape_does_not_change_results_and_autotuner_picks_one():
     common = mcr.Run(K=K, n_packets=0)
     probs, _ = _mixed_problems(K)
     ref = [o.clone() for o in mcr.run_batch(probs, common)]
-    for shape in ((64, 0), (256, 1), (96, 3)):
+    for shape in ((64, 0), (256, 1, 1), (96, 3, 2), (128, 0, 1), (128, 0, 2)):
         outs = mcr.run_batch(probs, common, launch=shape)
         assert all(torch.equal(a, b) for a, b in zip(outs, ref))
     choice = batch.autotune(probs, common, reps=1)
     assert choice in batch.DEFAULT_CANDIDATES
+
+
+@pytest.mark.parametrize("K", [8, 32, 64])
+def test_collision_merge_is_bit_identical(K):
+    """Depositing a surviving collision's segment together with the packet's next one changes
+    only the number of L2 reductions, not the integer tally: also with roulette, the scatter cap
+    and the event cap cutting packets off right at a collision."""
+    med, _, _ = _medium(48, 40, 0.06, 0.8, seed=77)
+    src = mcr.Source(mcr.LINE, x0=0.0, z0=0.0, x1=f32(40 * 0.06), z1=0.0, dir_x=0.0, dir_z=1.0)
+    q = torch.from_numpy(np.random.default_rng(3).normal(size=(48, 40)).astype(np.float32)).cuda()
+    for run in (mcr.Run(K=K, n_packets=0),
+                mcr.Run(K=K, n_packets=0, w_threshold=0.6, roulette_p=0.5, max_scatter=40, max_events=25)):
+        probs = [mcr.Problem(med, 30_000, seed=11, stream_id=0, source=src),
+                 mcr.Problem(med, 30_000, seed=11, stream_id=1, qstar=q)]
+        for pr in probs:
+            outs = [mcr.run_batch([pr], run, launch=(128, 0, m))[0].clone() for m in (1, 2)]
+            assert torch.equal(outs[0], outs[1])
+        both = [[o.clone() for o in mcr.run_batch(probs, run, launch=(128, 0, m))] for m in (1, 2)]
+        assert all(torch.equal(a, b) for a, b in zip(*both))
 
 
 def test_graph_replay_reproduces_eager_run():

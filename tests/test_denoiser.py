@@ -87,6 +87,15 @@ def test_layout_pool_upsample_and_backward_kernels():
     assert torch.allclose(db.cpu(), skip.float().cpu()[..., :C].sum(dim=(0, 1, 2)), rtol=1e-4, atol=1e-3)
 
 
+def test_sample_scale_is_inverse_mean_fluence():
+    g = torch.Generator().manual_seed(5)
+    x = torch.rand(3, 5, 64, 32, generator=g) * torch.tensor([1.0, 1e-3, 7.0]).view(3, 1, 1, 1)
+    x[2, 0] = 0.0  # an all-dark sample: clamped at 1e-30
+    got = sample_scale(x.cuda()).cpu().double()
+    m = x[:, 0].double().mean(dim=(1, 2)).clamp_min(1e-30)
+    assert torch.allclose(got, (1.0 / m).float().double(), rtol=1e-6, atol=0)
+
+
 def _data(B, H, W, C, seed):
     g = torch.Generator().manual_seed(seed)
     base = torch.rand(B, 1, H, W, generator=g) + 0.5

@@ -234,6 +234,69 @@ def test_uncollided_fluence_point_source():
         assert np.max(np.abs(zc)) < 5.0
 
 
+def _ring_sums(field, R, edges):
+    return np.array([field[(R >= lo) & (R < hi)].sum() for lo, hi in zip(edges[:-1], edges[1:])])
+
+
+def test_diffusion_far_field_fluence_and_flux():
+    """Deep in a scattering medium (mu_a << mu_s') the oracle's a_0 follows the 2D diffusion
+    Green's function Phi = K_0(kappa r)/(2 pi D), D = 1/(2(mu_a + mu_s(1-g))), kappa^2 = mu_a/D,
+    and its first harmonics follow Fick's law: with Eq. 8, phi = a_0/(2 pi) + (a_1 cos + b_1 sin)/pi,
+    so (b_1, a_1) = J = kappa K_1(kappa r)/(2 pi) r_hat (radial, no tangential part).  A 5 %
+    budget covers diffusion theory's own error at mu_a/mu_s' = 0.04 and r >= 3/mu_s'."""
+    from scipy.special import k0, k1
+    n, dx = 60, 0.2
+    mua, mus, g = 0.2, 10.0, 0.5
+    xs = zs = n * dx / 2
+    r = oracle.forward(np.full((n, n), mua), np.full((n, n), mus), dx, g, dict(kind=oracle.ISO_POINT, x0=xs, z0=zs),
+                       RunParams(K=2, n_packets=20000, seed=3), with_variance=True)
+    D = 1 / (2 * (mua + mus * (1 - g)))
+    kappa = math.sqrt(mua / D)
+    sub = 8
+    o = (np.arange(sub) + 0.5) / sub * dx
+    phi, flux = np.zeros((n, n)), np.zeros((n, n))
+    for iz in range(n):
+        for ix in range(n):
+            X, Z = np.meshgrid(ix * dx + o, iz * dx + o)
+            rr = np.hypot(X - xs, Z - zs)
+            phi[iz, ix] = (k0(kappa * rr) / (2 * math.pi * D)).mean()
+            flux[iz, ix] = (kappa * k1(kappa * rr) / (2 * math.pi)).mean()
+    c = (np.arange(n) + 0.5) * dx
+    X, Z = np.meshgrid(c, c)
+    R = np.hypot(X - xs, Z - zs)
+    edges = np.arange(0.6, 3.01, 0.4)
+    ratio = _ring_sums(r.coeff[0], R, edges) / _ring_sums(phi, R, edges)
+    assert np.all(np.abs(ratio - 1) < 0.05), ratio
+    jr = (r.coeff[2] * (X - xs) + r.coeff[1] * (Z - zs)) / R
+    jt = (r.coeff[2] * (Z - zs) - r.coeff[1] * (X - xs)) / R
+    jr_ring = _ring_sums(jr, R, edges)
+    assert np.all(np.abs(jr_ring / _ring_sums(flux, R, edges) - 1) < 0.05)
+    assert np.all(np.abs(_ring_sums(jt, R, edges) / jr_ring) < 0.05)
+
+
+def test_mirror_symmetry_of_harmonics():
+    """A medium and a source symmetric under x -> L - x give mirror-symmetric radiance: theta ->
+    -theta, so a_n(x) = a_n(L - x) and b_n(x) = -b_n(L - x) (statistically; |a_n|, |b_n| <= a_0
+    per deposit, so a_0's standard error bounds theirs)."""
+    nz, nx, dx = 24, 31, 0.1  # odd width: the pencil runs down the middle of column 15
+    mua, mus = _hetero(nz, nx, 21)
+    mua = 0.5 * (mua + mua[:, ::-1])
+    mus = 0.5 * (mus + mus[:, ::-1])
+    r = oracle.forward(mua, mus, dx, 0.7, dict(kind=oracle.PENCIL, x0=nx * dx / 2, z0=0.0, dir_x=0.0, dir_z=1.0),
+                       RunParams(K=3, n_packets=100000, seed=9), with_variance=True)
+    sig = np.sqrt(r.a0_var + r.a0_var[:, ::-1])
+    use = r.coeff[0] > 0.02 * r.coeff[0].max()
+    zs_ = []
+    for c in range(7):
+        sign = 1.0 if c == 0 or c % 2 == 1 else -1.0  # channel 2n-1 = a_n (even), 2n = b_n (odd)
+        d = (r.coeff[c] - sign * r.coeff[c][:, ::-1])[use] / sig[use]
+        assert np.max(np.abs(d)) < 6.0, c
+        zs_.append(d)
+    assert abs(np.mean(np.concatenate(zs_))) < 0.1
+    # b_n themselves are far from zero off the axis: the test is not vacuous
+    assert np.abs(r.coeff[2][use]).max() > 20 * sig[use].max()
+
+
 # ------------------------------------------------------------ reciprocity (Eqs. 13, 17)
 def test_reciprocity_case1_pixel_sources():
     """Case 1 (Eqs. 14, 17): isotropic unit sources uniform over pixel s and pixel d give
