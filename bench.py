@@ -41,14 +41,25 @@ def _args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--packets", type=int, default=10_000_000, help="packets per forward and per adjoint run")
+    ap.add_argument("--packets", type=int, default=None,
+                    help="packets per forward and per adjoint run (default 1e7 for grad256, 2e7 for large1024)")
     ap.add_argument("--cpu-sample", type=int, default=200_000, help="oracle packets (fwd and adj) for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="grad256", choices=["grad256", "batch64", "denoise256", "conv"],
-                    help="grad256: the gradient evaluation (default); batch64: 64 forward problems in one "
-                         "graph-captured batched launch; denoise256: the learned denoiser; conv: one large "
-                         "tensor-core convolution (profiling case)")
-    return ap.parse_args()
+    ap.add_argument("--workload", default="grad256",
+                    choices=["grad256", "large1024", "batch64", "denoise256", "conv"],
+                    help="grad256: the gradient evaluation (default); large1024: the same on 1024^2 px at "
+                         "K = 64 with four edge sources; batch64: 64 forward problems in one graph-captured "
+                         "batched launch; denoise256: the learned denoiser; conv: one large tensor-core "
+                         "convolution (profiling case)")
+    args = ap.parse_args()
+    if args.packets is None:
+        args.packets = 20_000_000 if args.workload == "large1024" else 10_000_000
+    return args
+
+
+def _grad_workload(name, n):
+    from paper_1608_05238_gb300 import workloads
+    return workloads.large1024(n) if name == "large1024" else workloads.grad256(n)
 
 
 def _dist():
@@ -59,9 +70,13 @@ def _dist():
 
 
 def _workload_config(w, n):
-    return {"workload": f"grad256: {w.nx}x{w.nz} px of {w.dx} mm, 3 circular inclusions, g {w.g}, K={w.K}, "
-                        f"line source on the top edge, {n:.0e} forward + {n:.0e} adjoint packets, gradient",
-            "K": w.K, "pixels": [w.nz, w.nx], "dx_mm": w.dx, "packets_fwd": n, "packets_adj": n}
+    if w.name == "large1024":
+        desc = (f"large1024: {w.nx}x{w.nz} px of {w.dx} mm, 8 circular inclusions, g {w.g}, K={w.K}, "
+                f"4 line sources (one per edge, {n // 4:.1e} packets each) + {n:.0e} adjoint packets, gradient")
+    else:
+        desc = (f"grad256: {w.nx}x{w.nz} px of {w.dx} mm, 3 circular inclusions, g {w.g}, K={w.K}, "
+                f"line source on the top edge, {n:.0e} forward + {n:.0e} adjoint packets, gradient")
+    return {"workload": desc, "K": w.K, "pixels": [w.nz, w.nx], "dx_mm": w.dx, "packets_fwd": n, "packets_adj": n}
 
 
 # ------------------------------------------------------------------------------- clocks
@@ -113,16 +128,24 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------- oracle leg
 def cpu_oracle_rate(w, Hmeas_np, n_sample: int, seed: int = 0):
-    """The FP64 oracle, as it stands, on a bounded sample of the same workload (host cores)."""
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload (host cores).
+    The oracle keeps one FP64 tally per thread (1 GB at 1024^2, K = 64), so the large grid runs
+    on 2 threads to bound host memory."""
     import oracle
     from oracle import RunParams
     from oracle import functionals as F
     dx, g = float(np.float32(w.dx)), float(np.float32(w.g))
     mua, mus = w.mua.astype(np.float64), w.mus.astype(np.float64)
     cores = os.cpu_count() or 1
+    if w.nx * w.nz * (2 * w.K + 1) * 8 > (256 << 20):
+        cores = min(cores, 2)
     t0 = time.perf_counter()
-    fw = oracle.forward(mua, mus, dx, g, w.sources[0], RunParams(K=w.K, n_packets=n_sample, seed=seed,
+    per = max(1, n_sample // len(w.sources))
+    fw = oracle.forward(mua, mus, dx, g, w.sources[0], RunParams(K=w.K, n_packets=per, seed=seed,
                                                                   n_threads=cores))
+    for s in range(1, len(w.sources)):  # one illumination: the sources' fluences add
+        fw.coeff += oracle.forward(mua, mus, dx, g, w.sources[s], RunParams(K=w.K, n_packets=per, seed=seed,
+                                                                             stream_id=2 * s, n_threads=cores)).coeff
     H = F.absorbed_energy(mua, fw.coeff)
     v = F.dL_dH_eps(Hmeas_np, H, dx)
     q = F.adjoint_source(mua, v, dx).astype(np.float32)
@@ -137,16 +160,18 @@ def _reference(args):
     rank, world, _ = _dist()
     if rank != 0:
         return 0
-    from paper_1608_05238_gb300 import workloads
-    w = workloads.grad256(args.packets)
+    w = _grad_workload(args.workload, args.packets)
     # H^meas for the oracle leg: the phantom's absorbed energy from an oracle run (bounded sample)
     import oracle
     from oracle import RunParams
     from oracle import functionals as F
     dx, g = float(np.float32(w.dx)), float(np.float32(w.g))
-    n = max(1000, args.cpu_sample // 10)
+    n = max(1000, args.cpu_sample // (10 if w.name == "grad256" else 200))
     hm = oracle.forward(w.mua_true.astype(np.float64), w.mus_true.astype(np.float64), dx, g, w.sources[0],
                         RunParams(K=0, n_packets=n, seed=1001))
+    for s in range(1, len(w.sources)):
+        hm.coeff += oracle.forward(w.mua_true.astype(np.float64), w.mus_true.astype(np.float64), dx, g,
+                                   w.sources[s], RunParams(K=0, n_packets=n, seed=1001, stream_id=2 * s)).coeff
     Hmeas = F.absorbed_energy(w.mua_true.astype(np.float64), hm.coeff)
     for k in range(args.warmup):
         cpu_oracle_rate(w, Hmeas, n, seed=10 * k)
@@ -156,12 +181,12 @@ def _reference(args):
         times.append(dt)
     T = float(np.sum(times))
     value = 2 * n * args.steps / T
-    sample = f"{n} forward + {n} adjoint packets per step of the grad256 workload (full 256x256 grid, K={w.K})"
+    sample = f"{n} forward + {n} adjoint packets per step of the {w.name} workload (full {w.nx}x{w.nz} grid, K={w.K})"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": _workload_config(w, args.packets),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -178,30 +203,32 @@ def _gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    from paper_1608_05238_gb300 import _build, mcr, workloads
+    from paper_1608_05238_gb300 import _build, mcr
+    from paper_1608_05238_gb300.autograd import EpsFromH, HFromMu, MCSpec, forward_coefficients
     _build.build()
-    w = workloads.grad256(args.packets)
+    w = _grad_workload(args.workload, args.packets)
     n = args.packets
     dx, g = float(np.float32(w.dx)), float(np.float32(w.g))
     stream = torch.cuda.current_stream()
 
     mua = torch.from_numpy(w.mua).to(dev)
     mus = torch.from_numpy(w.mus).to(dev)
-    med = mcr.Medium(mua, mus, dx, g)
-    src = mcr.Source(**w.sources[0])
-    # H^meas: the phantom's absorbed energy from a separate 1e7-packet run (seed 1001), made once
+    srcs = [mcr.Source(**s) for s in w.sources]
+    per_src = n // len(srcs)  # one illumination: the forward packets split over its sources
+    # H^meas: the phantom's absorbed energy from a separate run (seed 1001), made once
     med_t = mcr.Medium(torch.from_numpy(w.mua_true).to(dev), torch.from_numpy(w.mus_true).to(dev), dx, g)
-    Hmeas = mcr.h_eps(med_t, mcr.forward(med_t, src, mcr.Run(K=0, n_packets=n, seed=w.meta["hmeas_seed"])))
+    Hmeas = mcr.h_eps(med_t, forward_coefficients(med_t, MCSpec(dx=dx, g=g, sources=srcs, K=0, n_packets=per_src,
+                                                                 seed=w.meta["hmeas_seed"])))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    from paper_1608_05238_gb300.autograd import EpsFromH, HFromMu, MCSpec
     leaf_a = mua.clone().requires_grad_(True)
     leaf_s = mus.clone().requires_grad_(True)
 
     def step(k, a=leaf_a, s=leaf_s, hm=Hmeas):
         # one gradient evaluation through the autograd.Function: H(mu) -> eps -> backward
         base = 1_000_003 * rank + 7919 * k
-        spec = MCSpec(dx=dx, g=g, sources=[src], K=w.K, n_packets=n, seed=base, adjoint_seed=base + 1)
+        spec = MCSpec(dx=dx, g=g, sources=srcs, K=w.K, n_packets=per_src, n_adjoint=n, seed=base,
+                      adjoint_seed=base + 1)
         a.grad = None
         s.grad = None
         H = HFromMu.apply(a, s, spec)
@@ -242,7 +269,8 @@ def _gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         T = float(t.item())
         dist.barrier()
-    value = 2 * n * args.steps * world / T
+    n_fwd = per_src * len(srcs)
+    value = (n_fwd + n) * args.steps * world / T
 
     # end to end through the public API: pinned host inputs -> device, result -> host, each step
     h_mua = torch.from_numpy(w.mua).pin_memory()
@@ -271,7 +299,7 @@ def _gpu(args):
         out_e.copy_(eps, non_blocking=True)
         torch.cuda.synchronize()
         e2e_T += time.perf_counter() - t0
-    e2e_val = 2 * n * args.steps / e2e_T
+    e2e_val = (n_fwd + n) * args.steps / e2e_T
 
     # roofline of the dominant kernel (the transport): algorithmic bytes = (2K+1) fixed-point
     # read-modify-writes of 8 B per pixel segment; achieved = bytes / event-timed kernel duration
@@ -294,21 +322,23 @@ def _gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         hm_np = Hmeas.double().cpu().numpy()
-        rate, cores, dt = cpu_oracle_rate(w, hm_np, args.cpu_sample)
+        sample = args.cpu_sample if w.name == "grad256" else max(4, args.cpu_sample // 20)
+        rate, cores, dt = cpu_oracle_rate(w, hm_np, sample)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_sample} forward + {args.cpu_sample} adjoint packets of grad256 "
+               "sample": f"{sample} forward + {sample} adjoint packets of {w.name} "
                          f"(full grid, K={w.K}), {dt:.1f} s"}
 
     if rank == 0:
         cfg = _workload_config(w, n)
-        cfg.update({"l2": "flushed between timed steps (256 MB write)", "grad_evals_per_s": value / (2 * n),
+        cfg.update({"l2": "flushed between timed steps (256 MB write)", "grad_evals_per_s": value / (n_fwd + n),
                     "parallelism": f"replicas{world}" if world > 1 else "single"})
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64 (FP64 gradient)", "data": "synthetic",
                "config": cfg, "clocks": clk,
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-               "gpu_launches": KERNELS_PER_STEP * args.steps, "roofline": roofline, "cpu_baseline": cpu}
+               "gpu_launches": (KERNELS_PER_STEP + 3 * (len(srcs) - 1)) * args.steps, "roofline": roofline,
+               "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
