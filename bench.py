@@ -69,6 +69,27 @@ def _dist():
     return rank, world, local
 
 
+def replica_seed(rank: int, k: int) -> int:
+    """Seed of gradient evaluation k on rank ``rank``: each replica draws its own packets."""
+    return 1_000_003 * rank + 7919 * k
+
+
+def max_over_ranks(T: float, device=None) -> float:
+    """The slowest rank's time (every rank calls this; any torch.distributed backend)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return T
+    t = torch.tensor([T], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_step: float, steps: int, world: int, T: float) -> float:
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return units_per_step * steps * world / T
+
+
 def _workload_config(w, n):
     if w.name == "large1024":
         desc = (f"large1024: {w.nx}x{w.nz} px of {w.dx} mm, 8 circular inclusions, g {w.g}, K={w.K}, "
@@ -226,7 +247,7 @@ def _gpu(args):
 
     def step(k, a=leaf_a, s=leaf_s, hm=Hmeas):
         # one gradient evaluation through the autograd.Function: H(mu) -> eps -> backward
-        base = 1_000_003 * rank + 7919 * k
+        base = replica_seed(rank, k)
         spec = MCSpec(dx=dx, g=g, sources=srcs, K=w.K, n_packets=per_src, n_adjoint=n, seed=base,
                       adjoint_seed=base + 1)
         a.grad = None
@@ -262,15 +283,12 @@ def _gpu(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     mcr.check()
-    T = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    T = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, dev)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([T], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        T = float(t.item())
         dist.barrier()
     n_fwd = per_src * len(srcs)
-    value = (n_fwd + n) * args.steps * world / T
+    value = job_throughput(n_fwd + n, args.steps, world, T)
 
     # end to end through the public API: pinned host inputs -> device, result -> host, each step
     h_mua = torch.from_numpy(w.mua).pin_memory()
@@ -299,7 +317,7 @@ def _gpu(args):
         out_e.copy_(eps, non_blocking=True)
         torch.cuda.synchronize()
         e2e_T += time.perf_counter() - t0
-    e2e_val = (n_fwd + n) * args.steps / e2e_T
+    e2e_val = job_throughput(n_fwd + n, args.steps, world, max_over_ranks(e2e_T, dev))
 
     # roofline of the dominant kernel (the transport): algorithmic bytes = (2K+1) fixed-point
     # read-modify-writes of 8 B per pixel segment; achieved = bytes / event-timed kernel duration
@@ -431,7 +449,7 @@ def _denoise256(args):
     from paper_1608_05238_gb300.denoiser import UNet, sample_scale
     _build.build()
     K, n, dx = 16, 256, 0.05
-    n_train, n_test, n_low, n_high = 64, 8, 100_000, 10_000_000
+    n_train, n_test, n_low, n_high = 128, 8, 100_000, 10_000_000
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     a, b = ev()
     a.record()
@@ -440,7 +458,7 @@ def _denoise256(args):
     b.synchronize()
     gen_s = a.elapsed_time(b) / 1e3
     net = UNet(in_ch=2 * K + 1, seed=0)
-    batch, steps = 8, max(50, args.steps * 100)
+    batch, steps = 8, max(50, args.steps * 300)
     dt.train(net, x[:n_train], t[:n_train], steps=3, batch=batch)  # warm-up
     a, b = ev()
     a.record()

@@ -28,19 +28,23 @@ constexpr int kBlockK = 64;
 constexpr uint32_t kATileBytes = kBlockM * kBlockK * 2;  // 16 KB
 
 // k_conv_ws: persistent, warp-specialised.  One CTA per SM
-// walks the 128-pixel output tiles (tile = blockIdx.x + i gridDim.x); warp 0 streams the K
-// blocks of all its tiles through a ring of `stages` shared-memory buffers with TMA, warp 1
-// issues the MMAs into one of two TMEM accumulators (2 x acc_cols columns), and warps 2..5 drain
-// the other accumulator (TMEM lanes 32 (w % 4) ... + 31) while the next tile is being multiplied.
+// walks the output tiles (tile = blockIdx.x + i gridDim.x); warp 0 streams the K blocks of all
+// its tiles through a ring of `stages` shared-memory buffers with TMA, warp 1 issues the MMAs
+// into one of two TMEM accumulators (2 x acc_cols columns), and warps 2..5 drain the other
+// accumulator (TMEM lanes 32 (w % 4) ... + 31) while the next tile is being multiplied.
+// SUB = 2 (N <= 128): a tile is 2 x 128 pixels whose two A tiles share one weight tile per
+// stage (two MMAs per K step into the two halves of the accumulator, acc_cols / 2 >= N columns
+// apart), which halves the weight bytes each output pixel pulls through L2.
 constexpr int kWsThreads = 192;
 
+template <int SUB>
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_conv_ws(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, const ConvArgs a,
               int stages, int num_tiles) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t bTileBytes = (uint32_t)a.N * kBlockK * 2;
-  const uint32_t stageBytes = kATileBytes + bTileBytes;
+  const uint32_t stageBytes = SUB * kATileBytes + bTileBytes;
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stageBytes);
   uint64_t *empty = full + stages;
   uint64_t *tfull = empty + stages;   // [2] accumulator b is ready for the epilogue
@@ -79,9 +83,15 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     uint32_t kc = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-      const long long p0 = (long long)tile * kBlockM;
-      const int b0 = (int)(p0 / hw), rem = (int)(p0 % hw);
-      const int y0 = rem / a.W, x0 = rem % a.W;
+      int b0[SUB], y0[SUB], x0[SUB];
+#pragma unroll
+      for (int u = 0; u < SUB; ++u) {
+        const long long p0 = ((long long)tile * SUB + u) * kBlockM;
+        b0[u] = (int)(p0 / hw);
+        const int rem = (int)(p0 % hw);
+        y0[u] = rem / a.W;
+        x0[u] = rem % a.W;
+      }
       for (int i = 0; i < nk; ++i, ++kc) {
         const int s = kc % stages;
         const uint32_t r = kc / stages;
@@ -94,8 +104,10 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         const int ky = a.taps == 9 ? tap / 3 : 1, kx = a.taps == 9 ? tap % 3 : 1;
         uint8_t *st = smem + (size_t)s * stageBytes;
         mbar_arrive_expect_tx(&full[s], stageBytes);
-        tma_load_4d(st, &tmX, &full[s], cb * kBlockK, x0 + kx - 1, y0 + ky - 1, b0);
-        tma_load_2d(st + kATileBytes, &tmW, &full[s], tap * a.cin_pad + cb * kBlockK, 0);
+#pragma unroll
+        for (int u = 0; u < SUB; ++u)
+          tma_load_4d(st + u * kATileBytes, &tmX, &full[s], cb * kBlockK, x0[u] + kx - 1, y0[u] + ky - 1, b0[u]);
+        tma_load_2d(st + SUB * kATileBytes, &tmW, &full[s], tap * a.cin_pad + cb * kBlockK, 0);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -121,10 +133,15 @@ __global__ void __launch_bounds__(kWsThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t aBase = smem_u32(smem + (size_t)s * stageBytes), bBase = aBase + kATileBytes;
+        const uint32_t aBase = smem_u32(smem + (size_t)s * stageBytes), bBase = aBase + SUB * kATileBytes;
 #pragma unroll
-        for (int kk = 0; kk < kBlockK / 16; ++kk)
-          mma_bf16(d, sdesc_k128(aBase + kk * 32), sdesc_k128(bBase + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < kBlockK / 16; ++kk) {
+          const uint64_t bdesc = sdesc_k128(bBase + kk * 32);
+#pragma unroll
+          for (int u = 0; u < SUB; ++u)
+            mma_bf16(d + u * (acc_cols / 2), sdesc_k128(aBase + u * kATileBytes + kk * 32), bdesc, idesc,
+                     (i > 0 || kk > 0) ? 1u : 0u);
+        }
         mma_commit(&empty[s]);
       }
       mma_commit(&tfull[b]);
@@ -144,8 +161,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         break;
       }
       tc_fence_after();
-      const long long p = (long long)tile * kBlockM + row;
-      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + b * acc_cols;
+      for (int u = 0; u < SUB; ++u) {
+      const long long p = ((long long)tile * SUB + u) * kBlockM + row;
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + b * acc_cols + u * (acc_cols / 2);
       for (int c0 = 0; c0 < a.N; c0 += 16) {
         uint32_t v[16];
         tmem_ld16(trow + (uint32_t)c0, v);
@@ -184,6 +202,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             for (int j = 0; j < 16 && c0 + j < a.cout; ++j) o[j] = __float2bfloat16_rn(f[j]);
           }
         }
+      }
       }
       tc_fence_before();
       mbar_arrive(&tempty[b]);
@@ -303,7 +322,7 @@ __global__ void __launch_bounds__(128, 1)
 }  // namespace
 
 cudaError_t launch_wgrad_tc(const CUtensorMap &tmA, const CUtensorMap tmB[3], const WgradArgs &a, cudaStream_t s) {
-  const size_t smem = conv_smem_bytes(a.N);
+  const size_t smem = 1024 + kStages * (kATileBytes + (size_t)a.N * kBlockK * 2) + 256;
   static size_t configured = 0;
   if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -315,17 +334,16 @@ cudaError_t launch_wgrad_tc(const CUtensorMap &tmA, const CUtensorMap tmB[3], co
   return cudaGetLastError();
 }
 
-// Ring depth of the persistent convolution for a given MMA N: as many stages as fit in
-// ~200 KB of shared memory, at most 8.
-static int conv_stages(int N) {
-  const size_t stage = kATileBytes + (size_t)N * kBlockK * 2;
+// Ring depth of the persistent convolution: as many stages as fit in ~200 KB of shared memory,
+// at most 8.
+static int conv_stages(int N, int sub) {
+  const size_t stage = sub * kATileBytes + (size_t)N * kBlockK * 2;
   int s = (int)((200u * 1024u) / stage);
   return s > 8 ? 8 : (s < 2 ? 2 : s);
 }
 
-size_t conv_smem_bytes(int N) {
-  const size_t stage = kATileBytes + (size_t)N * kBlockK * 2;
-  return 1024 + conv_stages(N) * stage + 256;
+static size_t conv_smem(int N, int sub) {
+  return 1024 + conv_stages(N, sub) * (sub * kATileBytes + (size_t)N * kBlockK * 2) + 256;
 }
 
 static int sm_count() {
@@ -338,18 +356,29 @@ static int sm_count() {
   return n;
 }
 
-cudaError_t launch_conv_tc(const CUtensorMap &tmX, const CUtensorMap &tmW, const ConvArgs &a, cudaStream_t s) {
-  const size_t smem = conv_smem_bytes(a.N);
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+template <int SUB>
+static cudaError_t launch_ws(const CUtensorMap &tmX, const CUtensorMap &tmW, ConvArgs a, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv_ws<SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
-    configured = 232448;
+    configured = true;
   }
-  const long long tiles = (long long)a.B * a.H * a.W / kBlockM;
+  uint32_t cols = 32;  // one accumulator: SUB x N columns, a power of two
+  while (cols < (uint32_t)(SUB * a.N)) cols <<= 1;
+  a.tmem_cols = cols;
+  const long long tiles = (long long)a.B * a.H * a.W / (kBlockM * SUB);
   const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
-  k_conv_ws<<<grid, kWsThreads, smem, s>>>(tmX, tmW, a, conv_stages(a.N), (int)tiles);
+  k_conv_ws<SUB><<<grid, kWsThreads, conv_smem(a.N, SUB), s>>>(tmX, tmW, a, conv_stages(a.N, SUB), (int)tiles);
   return cudaGetLastError();
+}
+
+cudaError_t launch_conv_tc(const CUtensorMap &tmX, const CUtensorMap &tmW, const ConvArgs &a, cudaStream_t s) {
+  const long long P = (long long)a.B * a.H * a.W;
+  // two 128-pixel tiles per weight stage when two accumulators of N columns, double-buffered,
+  // fit in the 512 TMEM columns and the pixels split into 256-pixel tiles
+  if (a.N <= 128 && P % (2 * kBlockM) == 0) return launch_ws<2>(tmX, tmW, a, s);
+  return launch_ws<1>(tmX, tmW, a, s);
 }
 
 }  // namespace dn

@@ -26,7 +26,6 @@ struct ConvArgs {
   unsigned *err;            // device error word (bounded waits that gave up)
 };
 
-size_t conv_smem_bytes(int N);
 cudaError_t launch_conv_tc(const CUtensorMap &tmX, const CUtensorMap &tmW, const ConvArgs &a, cudaStream_t s);
 
 // Weight-gradient GEMM launch arguments (see k_wgrad_tc).

@@ -47,6 +47,8 @@ def _case(B, H, W, cin, cout, taps, seed, cin_pad=None, n_pad=None):
     (1, 2, 256, 128, 64, 9),   # rows of 256 pixels: two tiles per row, two channel blocks
     (1, 8, 64, 64, 256, 9),    # N = 256
     (3, 8, 128, 33, 48, 9),    # padded input channels
+    (1, 12, 32, 64, 128, 9),   # three 128-pixel tiles: no 256-pixel pairing
+    (2, 4, 32, 64, 96, 9),     # a 256-pixel pair spanning two images
 ])
 def test_conv_fp32_output_matches_reference(B, H, W, cin, cout, taps):
     x, w, cin_pad, n_pad = _case(B, H, W, cin, cout, taps, seed=B * 100 + H + W + cout)
