@@ -526,7 +526,7 @@ def _denoise256(args):
                                          for c in curve],
                       "equal_error": equal},
            "roofline": {"bound": "tensor", "achieved": conv_tf, "peak": peak, "unit": "TFLOP/s", "frac": conv_tf / peak,
-                        "traffic": None, "kernel": "k_conv_ws (8x256x256, 128->128, 3x3)",
+                        "traffic": None, "kernel": "k_conv_ws<2> (8x256x256, 128->128, 3x3, paired 256-pixel tiles)",
                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"},
            "cpu_baseline": None}
     print(json.dumps(out), flush=True)

@@ -38,6 +38,7 @@ namespace mcr {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kRowsPerStep = 2;  // independent single-lane rows deposited per step
 constexpr double kL2SpillBytes = 256.0 * 1024 * 1024;  // tallies beyond this live in HBM
 
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32->64 products and
@@ -91,7 +92,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 template <int NP, bool BATCH, bool MERGE>
-__global__ void __launch_bounds__(256, 3) k_transport(const __grid_constant__ TransportParams p) {
+__global__ void __launch_bounds__(256) k_transport(const __grid_constant__ TransportParams p) {
   extern __shared__ float smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -336,23 +337,32 @@ __global__ void __launch_bounds__(256, 3) k_transport(const __grid_constant__ Tr
     if (pend) {
       const unsigned same = __match_any_sync(kFull, seg_key);
       // Rows of a single lane without a carried segment (nearly all of them away from the source)
-      // are deposited in one fully unrolled pass over the 32 lanes: the lane index is a
-      // compile-time constant in each block, the blocks are independent (their shuffles, loads,
-      // conversions and reductions overlap), and no bit-scan loop walks the row mask.
-      const unsigned easy = pend & __ballot_sync(kFull, seg_key != 0u && same == (1u << lane) &&
-                                                           !(MERGE && dep_carry != 0.f));
+      // go kRowsPerStep at a time: their shuffles, loads, conversions and reductions are
+      // independent, so they overlap instead of running as one dependent chain per row.
+      unsigned easy = pend & __ballot_sync(kFull, seg_key != 0u && same == (1u << lane) && !(MERGE && dep_carry != 0.f));
       pend &= ~easy;
+      while (easy) {
+        bool on[kRowsPerStep];
+        float ts[kRowsPerStep];
+        unsigned long long *dst[kRowsPerStep];
+        const float *hr[kRowsPerStep];
 #pragma unroll
-      for (int L = 0; L < 32; ++L) {
-        const unsigned key = __shfl_sync(kFull, seg_key, L);
-        const float ts = __shfl_sync(kFull, seg_ts, L);
-        if (easy & (1u << L)) {  // warp-uniform
-          unsigned long long *dst = p.prob[BATCH ? (key & 63u) : 0].tally + (size_t)((key >> 6) - 1u) * p.Cpad;
-          const float *hr = rows + ((MERGE ? __shfl_sync(kFull, rb, L) * 32 : 0) + L) * p.row_stride + 1;
+        for (int r = 0; r < kRowsPerStep; ++r) {
+          on[r] = easy != 0u;  // warp-uniform
+          const int L = on[r] ? __ffs(easy) - 1 : 0;
+          easy &= easy - 1u;
+          const unsigned key = on[r] ? __shfl_sync(kFull, seg_key, L) : 64u;
+          ts[r] = __shfl_sync(kFull, seg_ts, L);
+          dst[r] = p.prob[BATCH ? (key & 63u) : 0].tally + (size_t)((key >> 6) - 1u) * p.Cpad;
+          hr[r] = rows + ((MERGE ? __shfl_sync(kFull, rb, L) * 32 : 0) + L) * p.row_stride + 1;
+        }
 #pragma unroll
-          for (int q = 0; q < NP; ++q) {
-            const int j = q * 32 + lane;
-            if (j < Cw) atomicAdd(dst + j, (unsigned long long)(long long)__float2int_rn(ts * hr[j]));
+        for (int q = 0; q < NP; ++q) {
+          const int j = q * 32 + lane;
+          if (j < Cw) {
+#pragma unroll
+            for (int r = 0; r < kRowsPerStep; ++r)
+              if (on[r]) atomicAdd(dst[r] + j, (unsigned long long)(long long)__float2int_rn(ts[r] * hr[r][j]));
           }
         }
       }
