@@ -33,6 +33,10 @@ UNIT = "photons/s"
 # kernels of libmcr per step: forward (pack, transport, finalize, H) | eps (residual, reduction) |
 # backward (adjoint source | pack, 4 CDF, transport, finalize | gradient)
 KERNELS_PER_STEP = 15
+# DRAM bytes (read + write) per K = 32 transport launch of the grad256 gradient evaluation, from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark's forward
+# (36.95 MB) and adjoint (38.27 MB) launches at full size: the tally footprint, read once.
+TRANSPORT_DRAM_BYTES = {"grad256": 37_609_088}
 
 
 def _args():
@@ -333,7 +337,7 @@ def _gpu(args):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
-                "traffic": None, "kernel": "k_transport", "launch_ms": avg_ms, "launches_timed": launches,
+                "traffic": TRANSPORT_DRAM_BYTES.get(w.name), "kernel": "k_transport", "launch_ms": avg_ms, "launches_timed": launches,
                 "segments_per_launch": avg_segs, "bytes_per_segment": C * 8,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
 

@@ -56,7 +56,7 @@ def _eps_and_grad(mua, mus, Hmeas, spec, want_a, want_s):
     s = mus.clone().requires_grad_(want_s)
     eps = EpsFromH.apply(HFromMu.apply(a, s, spec), Hmeas, spec.dx)
     eps.backward()
-    return float(eps), (a.grad if want_a else None), (s.grad if want_s else None)
+    return float(eps.detach()), (a.grad if want_a else None), (s.grad if want_s else None)
 
 
 def _eps(mua, mus, Hmeas, spec):

@@ -1,5 +1,6 @@
 """The reconstruction driver (Sec. 6) on the GPU: mu_a-only gradient descent with backtracking on a
-small inclusion phantom lowers eps and the mean relative error of mu_a at every accepted step."""
+small inclusion phantom, started from a uniform guess twice the background, lowers eps at every
+accepted step and the mean relative error of mu_a over the domain."""
 import numpy as np
 import pytest
 import torch
@@ -29,13 +30,13 @@ def test_mua_reconstruction_reduces_eps_and_error():
     hspec = MCSpec(dx=f32(dx), g=g, sources=[src], K=0, n_packets=4_000_000, seed=99)
     Hmeas = mcr.h_eps(mcr.Medium(mua_true, mus, f32(dx), g), forward_coefficients(
         mcr.Medium(mua_true, mus, f32(dx), g), hspec))
-    spec = MCSpec(dx=f32(dx), g=g, sources=[src], K=8, n_packets=1_000_000)
-    mua0 = torch.full_like(mua_true, 0.01)
-    res = invert(mua0, mus, Hmeas, spec, unknowns=("mua",), iters=6, mua_true=mua_true)
+    spec = MCSpec(dx=f32(dx), g=g, sources=[src], K=8, n_packets=2_000_000)
+    mua0 = torch.full_like(mua_true, 0.02)  # background 0.01: 100 % error there
+    res = invert(mua0, mus, Hmeas, spec, unknowns=("mua",), iters=10, mua_true=mua_true)
     assert len(res.history) >= 3
     e0 = mean_relative_error(mua0, mua_true)
     eps = [h.eps for h in res.history]
     errs = [h.rel_err_mua for h in res.history]
     assert all(b < a for a, b in zip(eps, eps[1:])), eps
-    assert errs[-1] < 0.8 * e0, (e0, errs)
+    assert errs[-1] < 0.6 * e0, (e0, errs)
     assert torch.all(res.mua > 0) and torch.equal(res.mus, mus)
