@@ -171,6 +171,11 @@ typedef struct {
   int32_t threads_per_block; /* multiple of 32, <= 256 */
   int32_t blocks_per_sm;     /* cap on resident blocks per SM */
   int32_t merge_collisions;  /* 0 default, 1 off, 2 on */
+  int32_t shared_tally;      /* 0 default (global), 1 global, 2 each block deposits into its own
+                                shared-memory copy of the tally and adds it to the global one at
+                                the end -- applies to a batch of one problem with 2K+1 <= 36
+                                whose tally (pixels x Cpad x 8 B) fits beside the harmonic rows
+                                (e.g. 32x32 at K = 8); otherwise the global tally is used */
 } mcr_launch;
 
 /*

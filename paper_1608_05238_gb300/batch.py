@@ -10,7 +10,7 @@ adds:
   become one graph launch).  A graph replays the same packets (its seeds are baked in); build a
   new runner, or call ``recapture(seed)``, for a fresh ensemble.
 * ``autotune`` -- times the candidate launch shapes (threads per block, resident blocks per SM,
-  collision merge default/off/on) on the actual batch with CUDA events and keeps the fastest,
+  collision merge default/off/on, shared-memory tally for a small single problem) on the actual batch with CUDA events and keeps the fastest,
   cached per device, K and batch size.  Results do not depend on the shape (fixed-point
   tallies), only the time does.
 """
@@ -24,7 +24,8 @@ import torch
 
 from . import mcr
 
-DEFAULT_CANDIDATES = ((128, 0, 0), (128, 0, 1), (256, 0, 1), (64, 0, 2), (128, 4, 1), (256, 2, 0))
+DEFAULT_CANDIDATES = ((128, 0, 0), (128, 0, 1), (256, 0, 1), (64, 0, 2), (128, 4, 1), (256, 2, 0), (256, 0, 0, 2),
+                      (128, 0, 2, 2))
 _cache: dict = {}
 
 
@@ -37,8 +38,8 @@ def _key(problems, common: mcr.Run):
 
 def autotune(problems: list, common: mcr.Run, candidates=DEFAULT_CANDIDATES, reps: int = 2,
              cache_path: str | None = None) -> tuple:
-    """Fastest (threads_per_block, blocks_per_sm, merge_collisions) for this batch, measured
-    with CUDA events."""
+    """Fastest (threads_per_block, blocks_per_sm, merge_collisions[, shared_tally]) for this
+    batch, measured with CUDA events."""
     key = _key(problems, common)
     if key in _cache:
         return _cache[key]

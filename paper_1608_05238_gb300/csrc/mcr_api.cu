@@ -295,7 +295,7 @@ int run_mc(const mcr_medium *med, const mcr_source *src, const float *qstar, con
   HostProblem h{med, src, qstar, run->n_packets, run->first_packet, run->seed, run->stream_id, coeff, 0.f, 1.f};
   if (!qstar && (rc = check_source(src, &h.dirx, &h.dirz))) return rc;
   std::lock_guard<std::mutex> lock(g_mu);
-  return enqueue({h}, run, TransportLaunch{0, 0, 0}, qstar ? 1 : 0, stats, s);
+  return enqueue({h}, run, TransportLaunch{0, 0, 0, 0}, qstar ? 1 : 0, stats, s);
 }
 
 }  // namespace
@@ -319,12 +319,14 @@ int mc_run_batch(const mcr_problem *problems, int32_t n_problems, const mcr_run 
   int rc;
   if (!problems || n_problems < 1 || n_problems > MCR_MAX_BATCH) return MCR_ERR_ARG;
   if ((rc = check_run(common))) return rc;
-  TransportLaunch cfg{0, 0, 0};
+  TransportLaunch cfg{0, 0, 0, 0};
   if (launch) {
     if (launch->threads_per_block < 0 || launch->threads_per_block > 256 || launch->threads_per_block % 32 ||
-        launch->blocks_per_sm < 0 || launch->merge_collisions < 0 || launch->merge_collisions > 2)
+        launch->blocks_per_sm < 0 || launch->merge_collisions < 0 || launch->merge_collisions > 2 ||
+        launch->shared_tally < 0 || launch->shared_tally > 2)
       return MCR_ERR_ARG;
-    cfg = TransportLaunch{launch->threads_per_block, launch->blocks_per_sm, launch->merge_collisions};
+    cfg = TransportLaunch{launch->threads_per_block, launch->blocks_per_sm, launch->merge_collisions,
+                          launch->shared_tally};
   }
   std::vector<HostProblem> probs;
   uint64_t total = 0;

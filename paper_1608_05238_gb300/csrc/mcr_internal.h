@@ -67,7 +67,8 @@ struct TransportParams {
 struct TransportLaunch {
   int threads_per_block;
   int blocks_per_sm;
-  int merge;  // collision merge: 0 library default, 1 off, 2 on
+  int merge;         // collision merge: 0 library default, 1 off, 2 on
+  int shared_tally;  // 0 default (global), 1 global, 2 per-block shared-memory copy where it applies
 };
 
 // Workspace of one device (grow-only).

@@ -133,7 +133,7 @@ int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_r
   d.dir_z = dirz;
   d.key0 = (unsigned)run->seed;
   d.key1 = (unsigned)(run->seed >> 32) ^ run->stream_id;
-  if (run->n_packets && launch_transport(p, TransportLaunch{0, 0, 0}, s) != cudaSuccess) return MCR_ERR_CUDA;
+  if (run->n_packets && launch_transport(p, TransportLaunch{0, 0, 0, 0}, s) != cudaSuccess) return MCR_ERR_CUDA;
   const double area = (double)med->dx * (double)med->dx;
   const double fixed_scale = run->n_packets ? (double)src->power / ((double)run->n_packets * area) : 0.0;
   if (launch_finalize(tally, nullptr, npix, C, Cpad, ldexp(1.0, -qexp), fixed_scale, false, nullptr, nullptr,

@@ -91,14 +91,27 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-template <int NP, bool BATCH, bool MERGE>
+template <int NP, bool BATCH, bool MERGE, bool STALLY>
 __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ TransportParams p) {
   extern __shared__ float smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   // harmonic rows of this warp: row r of lane l at rows + (r * 32 + l) * row_stride (r < 2 with MERGE)
   float *const rows = smem + (size_t)warp * (MERGE ? 64 : 32) * p.row_stride;
+  // STALLY (one small problem): the block deposits into its own shared-memory copy of the tally,
+  // placed after all warps' rows, and adds it to the global tally once at the end
+  unsigned long long *const stally =
+      reinterpret_cast<unsigned long long *>(smem + (size_t)blockDim.x * (MERGE ? 2 : 1) * p.row_stride);
   if (*p.flags & kFlagMedium) return;
+  if (STALLY) {
+    const size_t nw = (size_t)p.prob[0].nx * p.prob[0].nz * p.Cpad;
+    for (size_t i = threadIdx.x; i < nw; i += blockDim.x) stally[i] = 0ull;
+    __syncthreads();
+  }
+  // base of the tally row of a segment key ((pixel + 1) << 6 | problem)
+  auto tally_row = [&](unsigned key) -> unsigned long long * {
+    return (STALLY ? stally : p.prob[BATCH ? (key & 63u) : 0].tally) + (size_t)((key >> 6) - 1u) * p.Cpad;
+  };
 
   const int K = p.K, C = p.C;
   // Coefficients [0, Cw) are deposited warp-cooperatively (32 per instruction); a short remainder
@@ -353,7 +366,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
           easy &= easy - 1u;
           const unsigned key = on[r] ? __shfl_sync(kFull, seg_key, L) : 64u;
           ts[r] = __shfl_sync(kFull, seg_ts, L);
-          dst[r] = p.prob[BATCH ? (key & 63u) : 0].tally + (size_t)((key >> 6) - 1u) * p.Cpad;
+          dst[r] = tally_row(key);
           hr[r] = rows + ((MERGE ? __shfl_sync(kFull, rb, L) * 32 : 0) + L) * p.row_stride + 1;
         }
 #pragma unroll
@@ -370,7 +383,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
         const int L = __ffs(pend) - 1;
         const unsigned grp = __shfl_sync(kFull, same, L) & pend;
         const unsigned key = __shfl_sync(kFull, seg_key, L);
-        unsigned long long *dst = p.prob[BATCH ? (key & 63u) : 0].tally + (size_t)((key >> 6) - 1u) * p.Cpad;
+        unsigned long long *dst = tally_row(key);
         long long acc[NP];
         // |t h 2^q| < 2^31 by the choice of q, so a 32-bit conversion suffices
         const float tsL = __shfl_sync(kFull, seg_ts, L);
@@ -422,7 +435,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
         pend &= ~grp;
       }
       if (Cw < C && seg_key != 0u) {  // the per-lane remainder
-        unsigned long long *own = p.prob[BATCH ? (seg_key & 63u) : 0].tally + (size_t)((seg_key >> 6) - 1u) * p.Cpad;
+        unsigned long long *own = tally_row(seg_key);
         const float *h = rows + ((MERGE ? rb * 32 : 0) + lane) * p.row_stride + 1;
         const float *hc = rows + ((MERGE ? carry_rb * 32 : 0) + lane) * p.row_stride + 1;
         for (int j = Cw; j < C; ++j) {
@@ -514,11 +527,24 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     atomicAdd(&s->rr_net_w, w_rr);
     atomicAdd(&s->killed_w, w_kill);
   }
+  if (STALLY) {  // the block's tally into the global one: coalesced, zero words skipped
+    __syncthreads();
+    const size_t nw = (size_t)p.prob[0].nx * p.prob[0].nz * p.Cpad;
+    unsigned long long *g = p.prob[0].tally;
+    for (size_t i = threadIdx.x; i < nw; i += blockDim.x) {
+      const unsigned long long v = stally[i];
+      if (v) atomicAdd(g + i, v);
+    }
+  }
+}
+
+size_t shared_tally_bytes(const TransportParams &p) {
+  return (size_t)p.prob[0].nx * p.prob[0].nz * p.Cpad * sizeof(unsigned long long);
 }
 
 // Opts the kernel into `smem` bytes of dynamic shared memory (once per device) and returns how
 // many blocks of `threads` fit on one SM.
-template <int NP, bool BATCH, bool MERGE>
+template <int NP, bool BATCH, bool MERGE, bool STALLY = false>
 cudaError_t blocks_per_sm(int threads, size_t smem, int *per_sm) {
   static int configured[64];  // largest dynamic smem opted in, per device
   int dev = 0;
@@ -529,27 +555,27 @@ cudaError_t blocks_per_sm(int threads, size_t smem, int *per_sm) {
     return cudaSuccess;
   }
   if (dev >= 64 || configured[dev] < (int)smem) {
-    e = cudaFuncSetAttribute(k_transport<NP, BATCH, MERGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_transport<NP, BATCH, MERGE, STALLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (dev < 64) configured[dev] = (int)smem;
   }
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_transport<NP, BATCH, MERGE>, threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_transport<NP, BATCH, MERGE, STALLY>, threads, smem);
 }
 
-template <int NP, bool BATCH, bool MERGE>
+template <int NP, bool BATCH, bool MERGE, bool STALLY = false>
 cudaError_t launch_kernel(const TransportParams &p, int threads, int cap, cudaStream_t s) {
   if (threads % 32 || threads > 256 || threads <= 0) return cudaErrorInvalidValue;
-  const size_t smem = transport_smem_bytes(p.row_stride, threads, MERGE);
+  const size_t smem = transport_smem_bytes(p.row_stride, threads, MERGE) + (STALLY ? shared_tally_bytes(p) : 0);
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = blocks_per_sm<NP, BATCH, MERGE>(threads, smem, &per_sm);
+  e = blocks_per_sm<NP, BATCH, MERGE, STALLY>(threads, smem, &per_sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (cap > 0 && cap < per_sm) per_sm = cap;
-  k_transport<NP, BATCH, MERGE><<<sms * per_sm, threads, smem, s>>>(p);
+  k_transport<NP, BATCH, MERGE, STALLY><<<sms * per_sm, threads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -574,6 +600,19 @@ cudaError_t launch_b(const TransportParams &p, const TransportLaunch &cfg, cudaS
         merge = true;
         threads = 96;
       }
+    }
+  }
+  if constexpr (NP == 1 && !BATCH) {
+    // per-block shared-memory tally when asked for and it fits beside the harmonic rows
+    if (cfg.shared_tally == 2) {
+      int per_sm = 0;
+      const size_t smem = transport_smem_bytes(p.row_stride, threads, merge) + shared_tally_bytes(p);
+      cudaError_t e = merge ? blocks_per_sm<1, false, true, true>(threads, smem, &per_sm)
+                            : blocks_per_sm<1, false, false, true>(threads, smem, &per_sm);
+      if (e != cudaSuccess) return e;
+      if (per_sm >= 1)
+        return merge ? launch_kernel<1, false, true, true>(p, threads, cfg.blocks_per_sm, s)
+                     : launch_kernel<1, false, false, true>(p, threads, cfg.blocks_per_sm, s);
     }
   }
   return merge ? launch_kernel<NP, BATCH, true>(p, threads, cfg.blocks_per_sm, s)

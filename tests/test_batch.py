@@ -138,3 +138,23 @@ def test_batch_limits():
     probs = [mcr.Problem(med, 100, seed=i, source=src) for i in range(64)]
     outs = mcr.run_batch(probs, common)
     assert all(torch.count_nonzero(o) > 0 for o in outs)
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_shared_memory_tally_is_bit_identical(adjoint):
+    """A per-block shared-memory copy of a small tally (32x32, K = 8) adds up to the same integer
+    tally as the global one; a tally too large for shared memory falls back to the global one."""
+    K = 8
+    run = mcr.Run(K=K, n_packets=0, w_threshold=0.05, roulette_p=0.3)
+    for n in (32, 80):
+        med, _, _ = _medium(n, n, 0.25, 0.8, seed=91)
+        if adjoint:
+            q = torch.from_numpy(np.random.default_rng(5).normal(size=(n, n)).astype(np.float32)).cuda()
+            prob = mcr.Problem(med, 300_000, seed=4, stream_id=1, qstar=q)
+        else:
+            src = mcr.Source(mcr.PENCIL, x0=f32(n * 0.25 / 2 + 0.1), z0=0.0, dir_x=0.0, dir_z=1.0)
+            prob = mcr.Problem(med, 300_000, seed=4, stream_id=0, source=src)
+        ref = mcr.run_batch([prob], run, launch=(128, 0, 1, 1))[0].clone()
+        for shape in ((128, 0, 1, 2), (256, 0, 2, 2), (64, 0, 0, 2)):
+            got = mcr.run_batch([prob], run, launch=shape)[0]
+            assert torch.equal(got, ref), (n, shape)
