@@ -49,12 +49,13 @@ def _args():
                     help="packets per forward and per adjoint run (default 1e7 for grad256, 2e7 for large1024)")
     ap.add_argument("--cpu-sample", type=int, default=200_000, help="oracle packets (fwd and adj) for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-gd", action="store_true", help="invert256: no fluence preconditioning")
     ap.add_argument("--workload", default="grad256",
-                    choices=["grad256", "large1024", "batch64", "denoise256", "conv"],
+                    choices=["grad256", "large1024", "batch64", "denoise256", "conv", "invert256"],
                     help="grad256: the gradient evaluation (default); large1024: the same on 1024^2 px at "
                          "K = 64 with four edge sources; batch64: 64 forward problems in one graph-captured "
                          "batched launch; denoise256: the learned denoiser; conv: one large tensor-core "
-                         "convolution (profiling case)")
+                         "convolution (profiling case); invert256: mu_a reconstruction on the grad256 phantom")
     args = ap.parse_args()
     if args.packets is None:
         args.packets = 20_000_000 if args.workload == "large1024" else 10_000_000
@@ -560,8 +561,66 @@ def _conv_only(args):
     return 0
 
 
+def _invert256(args):
+    """mu_a reconstruction (Sec. 6.1: mu_s known) on the 256x256 inclusion phantom from a
+    homogeneous start: (fluence-preconditioned, unless --plain-gd) gradient descent with the
+    backtracking line search of inversion.py, one
+    forward + one adjoint run per iteration plus the line search's forward runs, K = 10 (the
+    paper's harmonic count for its inversions).  Reports the mean relative mu_a error after each
+    accepted step and the wall time to reach it."""
+    import torch
+    from paper_1608_05238_gb300 import _build, mcr, workloads
+    from paper_1608_05238_gb300.autograd import MCSpec, forward_coefficients
+    from paper_1608_05238_gb300.inversion import invert, mean_relative_error
+    _build.build()
+    n_pk = args.packets
+    w = workloads.grad256(n_pk)
+    dx, g = float(np.float32(w.dx)), float(np.float32(w.g))
+    dev = torch.device("cuda")
+    mua_t = torch.from_numpy(w.mua_true).to(dev)
+    mus_t = torch.from_numpy(w.mus_true).to(dev)
+    srcs = [mcr.Source(**s) for s in w.sources]
+    med_t = mcr.Medium(mua_t, mus_t, dx, g)
+    Hmeas = mcr.h_eps(med_t, forward_coefficients(med_t, MCSpec(dx=dx, g=g, sources=srcs, K=0, n_packets=10 * n_pk,
+                                                                 seed=w.meta["hmeas_seed"])))
+    spec = MCSpec(dx=dx, g=g, sources=srcs, K=10, n_packets=n_pk)
+    mua0 = torch.from_numpy(w.mua).to(dev)
+    invert(mua0, mus_t, Hmeas, replace_spec(spec, n_packets=max(1000, n_pk // 100)), iters=1)  # warm-up
+    torch.cuda.synchronize()
+    iters = max(args.steps, 1) * 4
+    t0 = time.perf_counter()
+    res = invert(mua0, mus_t, Hmeas, spec, unknowns=("mua",), iters=iters, tol=1e-9, mua_true=mua_t,
+                 precondition=not args.plain_gd)
+    torch.cuda.synchronize()
+    T = time.perf_counter() - t0
+    e0 = mean_relative_error(mua0, mua_t)
+    hist = [{"it": h.it, "eps": h.eps, "rel_err_mua": h.rel_err_mua, "seconds": h.seconds, "trials": h.trials}
+            for h in res.history]
+    runs = sum(2 + h.trials for h in res.history)
+    out = {"metric": "mu_a reconstruction: mean relative error after the timed iterations", "value":
+           res.history[-1].rel_err_mua if res.history else e0, "unit": "relative error", "n_gpus": 1,
+           "steps": len(res.history), "warmup": 1, "ms_per_step": 1e3 * T / max(1, len(res.history)),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64 (FP64 gradient)",
+           "data": "synthetic",
+           "config": {"workload": f"invert256: grad256 phantom (256x256 px of {w.dx} mm, 3 inclusions, g {w.g}), "
+                                  f"mu_s known, homogeneous mu_a start, K=10, {n_pk:.0e} packets per MC run, "
+                                  + ("plain gradient descent" if args.plain_gd else "fluence-preconditioned descent"),
+                      "initial_rel_err_mua": e0, "seconds": T, "mc_runs": runs,
+                      "photons_per_s": runs * n_pk / T, "history": hist},
+           "cpu_baseline": None}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def replace_spec(spec, **kw):
+    from dataclasses import replace
+    return replace(spec, **kw)
+
+
 def main():
     args = _args()
+    if args.workload == "invert256" and args.impl != "reference":
+        return _invert256(args)
     if args.workload == "batch64" and args.impl != "reference":
         return _batch64(args)
     if args.workload == "denoise256" and args.impl != "reference":

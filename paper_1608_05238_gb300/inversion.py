@@ -12,7 +12,12 @@ sufficiently (Eq. 30) and a stop once the relative decrease of eps falls below a
   by ``nu`` until eps(mu - alpha g) <= eps(mu) - c1 alpha |g|^2; its trial forward runs reuse
   the iteration's seed (common random numbers), so a trial is compared with the same packets'
   estimate of eps at mu and MC noise does not decide the comparison;
-* mu stays positive (mu_a >= mu_floor, mu_s >= mu_floor).
+* mu stays positive (mu_a >= mu_floor, mu_s >= mu_floor);
+* optionally (``precondition=True``, mu_a only; not in the paper) the mu_a step is scaled per
+  pixel by 1 / (dx^2 Phi_i^2), the curvature of the local part of eps, dx^2 (H^meas - mu_a Phi)^2 / 2,
+  in mu_a_i: the descent direction is then (H^meas - H)_i / Phi_i plus the scaled non-local part,
+  so pixels deep in the medium move as fast as those near the source.  The line search then uses
+  the directional derivative g.d instead of |g|^2.
 
 The step update itself (mu - alpha g, clamp) is a handful of torch elementwise operations: the
 driver is plumbing around the MC gradient, which is where the time goes.
@@ -54,9 +59,10 @@ def mean_relative_error(est: torch.Tensor, true: torch.Tensor) -> float:
 def _eps_and_grad(mua, mus, Hmeas, spec, want_a, want_s):
     a = mua.clone().requires_grad_(want_a)
     s = mus.clone().requires_grad_(want_s)
-    eps = EpsFromH.apply(HFromMu.apply(a, s, spec), Hmeas, spec.dx)
+    H = HFromMu.apply(a, s, spec)
+    eps = EpsFromH.apply(H, Hmeas, spec.dx)
     eps.backward()
-    return float(eps.detach()), (a.grad if want_a else None), (s.grad if want_s else None)
+    return float(eps.detach()), (a.grad if want_a else None), (s.grad if want_s else None), H.detach()
 
 
 def _eps(mua, mus, Hmeas, spec):
@@ -67,11 +73,11 @@ def _eps(mua, mus, Hmeas, spec):
 def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MCSpec, unknowns=("mua",),
            iters: int = 20, tol: float = 1e-5, step0: float | None = None, nu: float = 0.2, grow: float = 2.0,
            c1: float = 1e-4, max_trials: int = 12, mu_floor: float = 1e-6, mua_true=None, mus_true=None,
-           seed0: int = 1) -> InversionResult:
+           seed0: int = 1, precondition: bool = False) -> InversionResult:
     """Reconstruct ``unknowns`` (a subset of ("mua", "mus")) from H^meas; the others stay fixed.
 
     ``step0`` defaults to the step that changes the unknowns by 10 % of their norm on the first
-    iteration.  Returns the estimates and one ``Iteration`` record per accepted step.
+    iteration (1, a full fixed-point-like step, with ``precondition``).  Returns the estimates and one ``Iteration`` record per accepted step.
     """
     want_a, want_s = "mua" in unknowns, "mus" in unknowns
     mua, mus = mua0.detach().clone(), mus0.detach().clone()
@@ -80,22 +86,30 @@ def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MC
     t0 = time.perf_counter()
     for it in range(iters):
         s_it = replace(spec, seed=seed0 + 1009 * it, adjoint_seed=seed0 + 1009 * it + 1)
-        eps, ga, gs = _eps_and_grad(mua, mus, Hmeas, s_it, want_a, want_s)
-        g2 = sum(float((g.double() ** 2).sum()) for g in (ga, gs) if g is not None)
-        if g2 == 0.0:
+        eps, ga, gs, H = _eps_and_grad(mua, mus, Hmeas, s_it, want_a, want_s)
+        da = None
+        if want_a:
+            da = -ga
+            if precondition:  # 1 / (dx^2 Phi^2), Phi = H / mu_a = a_0
+                phi = H / mua
+                da = da / (float(spec.dx) ** 2 * phi * phi).clamp_min(1e-30)
+        ds = -gs if want_s else None
+        slope = -sum(float((g.double() * d.double()).sum()) for g, d in ((ga, da), (gs, ds)) if g is not None)
+        if slope <= 0.0:
             res.converged = True
             break
         if alpha is None:
             norm_mu = sum(float((m.double() ** 2).sum()) for m, w in ((mua, want_a), (mus, want_s)) if w) ** 0.5
-            alpha = 0.1 * norm_mu / g2 ** 0.5
+            norm_d = sum(float((d.double() ** 2).sum()) for d in (da, ds) if d is not None) ** 0.5
+            alpha = (1.0 if precondition else 0.1 * norm_mu / norm_d)
         else:
-            alpha *= grow
+            alpha = min(alpha * grow, 1.0) if precondition else alpha * grow
         accepted = False
         for trial in range(1, max_trials + 1):
-            na = (mua - alpha * ga).clamp_min(mu_floor) if want_a else mua
-            ns = (mus - alpha * gs).clamp_min(mu_floor) if want_s else mus
+            na = (mua + alpha * da).clamp_min(mu_floor) if want_a else mua
+            ns = (mus + alpha * ds).clamp_min(mu_floor) if want_s else mus
             e_new = _eps(na, ns, Hmeas, s_it)
-            if e_new <= eps - c1 * alpha * g2:
+            if e_new <= eps - c1 * alpha * slope:
                 accepted = True
                 break
             alpha *= nu
