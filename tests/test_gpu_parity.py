@@ -253,3 +253,22 @@ def test_chunked_run_matches_closed_form():
     frac = G[0] / col[:, None]  # each column receives ~1/3 of the packets
     assert np.allclose(frac.sum(axis=1), 1.0, rtol=1e-5)
     assert np.allclose(frac, 1 / 3, atol=5e-4)
+
+
+@pytest.mark.parametrize("K,g", [(1, 0.0), (15, -0.9), (17, 0.99), (31, 0.5), (33, 0.3), (48, 0.8)])
+def test_forward_every_deposit_split_and_extreme_anisotropy(K, g):
+    """Every way the 2K+1 coefficients split between warp-wide chunks and the per-lane remainder
+    (K = 17 and 33 leave three coefficients per lane, K = 15 and 31 fill partial chunks, K = 48
+    one per lane), with isotropic, strongly backward and strongly forward scattering."""
+    mua, mus = workloads.small_hetero(29, 37, 0.08, seed=40 + K)
+    src = dict(kind=mcr.LINE, x0=0.0, z0=0.0, x1=2.96, z1=0.0, dir_x=0.2, dir_z=0.9, power=1.0)
+    run = mcr.Run(K=K, n_packets=40_003, seed=K)
+    _forward_case(mua, mus, 0.08, g, src, run, f"K{K} g{g}")
+
+
+@pytest.mark.parametrize("K", [17, 33])
+def test_adjoint_with_per_lane_remainder(K):
+    mua, mus = workloads.small_hetero(26, 31, 0.1, seed=60 + K)
+    q = np.random.default_rng(K).normal(size=(26, 31)).astype(np.float32)
+    run = mcr.Run(K=K, n_packets=40_009, seed=K + 1, stream_id=1)
+    _adjoint_case(mua, mus, 0.1, 0.7, q, run, f"adjoint K{K}")
