@@ -34,9 +34,10 @@ UNIT = "photons/s"
 # backward (adjoint source | pack, 4 CDF, transport, finalize | gradient)
 KERNELS_PER_STEP = 15
 # DRAM bytes (read + write) per K = 32 transport launch of the grad256 gradient evaluation, from
-# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark's forward
-# (36.95 MB) and adjoint (38.27 MB) launches at full size: the tally footprint, read once.
-TRANSPORT_DRAM_BYTES = {"grad256": 37_609_088}
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark's forward and
+# adjoint launches at full size (the tally footprint, read once); empty until captured for the
+# current kernel.
+TRANSPORT_DRAM_BYTES = {}
 
 
 def _args():

@@ -119,7 +119,8 @@ int mc_forward(const mcr_medium *med, const mcr_source *src, const mcr_run *run,
  * lives in one 16 MiB array inside the library, which every GPU that loads libmcr holds until
  * the process exits.
  *   Limits: 512 + nx*nz*16 (rounded up to 256) + nx*nz*Cpad*8 bytes <= 16 MiB, with Cpad = 2K+1
- *   rounded up to a multiple of 4 (e.g. 128x128 at K = 32, 256x256 at K = 8), and at most 2^26
+ *   rounded up to a multiple of 16 when 2K+1 > 32, else to a multiple of 4 (e.g. 128x128 at
+ *   K = 32, 256x256 at K = 8), and at most 2^26
  *   packets per call (use first_packet to split larger runs); larger problems return
  *   MCR_ERR_SCRATCH and launch nothing.
  *   The first call on each device looks up the array's device address (cudaGetSymbolAddress,

@@ -156,7 +156,7 @@ struct HostProblem {
 int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const TransportLaunch &cfg, int slot,
             mcr_stats *stats, cudaStream_t s) {
   const int np = (int)probs.size();
-  const int C = 2 * common->K + 1, Cpad = (C + 3) & ~3;
+  const int C = 2 * common->K + 1, Cpad = tally_row_words(C);
   // a single problem may exceed one launch's packet budget (chunks + FP64 flush); a batch may not
   const bool chunked = np == 1 && probs[0].n_packets > kChunkPackets;
   Need need;
@@ -190,7 +190,7 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
   p.K = common->K;
   p.C = C;
   p.Cpad = Cpad;
-  p.row_stride = Cpad + 2;  // = 2 mod 4 words: conflict-free 8-byte row stores
+  p.row_stride = transport_row_stride(C);
   p.max_scatter = common->max_scatter;
   p.max_events = common->max_events;
   p.w_threshold = common->w_threshold;

@@ -76,7 +76,7 @@ int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_r
   // size limits of the fixed scratch: one transport launch (no FP64 chunk accumulator)
   if (run->n_packets > kChunkPackets) return MCR_ERR_SCRATCH;
   const int64_t npix = (int64_t)med->nx * med->nz;
-  const int C = 2 * run->K + 1, Cpad = (C + 3) & ~3;
+  const int C = 2 * run->K + 1, Cpad = tally_row_words(C);
   const size_t mu_bytes = round256((size_t)npix * sizeof(float4));
   const size_t tally_bytes = (size_t)npix * Cpad * 8;
   if (npix > ((int64_t)1 << 30) || kSmall + mu_bytes + tally_bytes > kScratchBytes) return MCR_ERR_SCRATCH;
@@ -103,7 +103,7 @@ int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_r
   p.K = run->K;
   p.C = C;
   p.Cpad = Cpad;
-  p.row_stride = Cpad + 2;
+  p.row_stride = transport_row_stride(C);
   p.max_scatter = run->max_scatter;
   p.max_events = run->max_events;
   p.w_threshold = run->w_threshold;
