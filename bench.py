@@ -34,10 +34,9 @@ UNIT = "photons/s"
 # backward (adjoint source | pack, 4 CDF, transport, finalize | gradient)
 KERNELS_PER_STEP = 15
 # DRAM bytes (read + write) per K = 32 transport launch of the grad256 gradient evaluation, from
-# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark's forward and
-# adjoint launches at full size (the tally footprint, read once); empty until captured for the
-# current kernel.
-TRANSPORT_DRAM_BYTES = {}
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark's forward
+# (40.91 MB) and adjoint (41.56 MB) launches at full size: the tally footprint, read once.
+TRANSPORT_DRAM_BYTES = {"grad256": 41_236_096}
 
 
 def _args():
