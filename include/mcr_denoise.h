@@ -68,6 +68,18 @@ typedef struct {
   int32_t stride, off;
 } dn_slice;
 
+/*
+ * dn_wgrad_nhwc -- weight gradient of a convolution on the tensor cores,
+ *   dw[n][tap][c] += sum_{b, pixel} dz[b, pixel][n] x[b, pixel + tap][c]     (FP32 accumulate)
+ * read directly from NHWC bf16 slices (no transposed copies): dz [B][H][W] channels
+ * [off, off + cout) of rows of `stride`, x likewise with cin channels.  Both operands enter the tensor cores MN-major (channels contiguous); the tap's
+ * shift is a TMA coordinate with zero fill at the image border.  Slice offsets and strides must
+ * be multiples of 8 channels (16-byte aligned rows).  Same dw layout, accumulation and limits as
+ * dn_wgrad.
+ */
+int dn_wgrad_nhwc(dn_slice dz, dn_slice x, int32_t B, int32_t H, int32_t W, int32_t taps, int32_t cout, int32_t cin,
+                  float *dw, void *stream);
+
 /* dst[c][b][p] = src[b][p][off + c] for c < C (bf16); shifted = 1 writes three copies
  * (dst + k*C*B*HW) with x shifted by k - 1 and zeros outside the row. */
 int dn_to_ct(dn_slice src, int32_t B, int32_t H, int32_t W, int32_t C, int32_t shifted, void *dst, void *stream);

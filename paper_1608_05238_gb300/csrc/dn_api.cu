@@ -197,6 +197,61 @@ int dn_wgrad(int32_t B, int32_t H, int32_t W, int32_t taps, int32_t cout, int32_
 
 static bool slice_ok(const dn_slice &s, int C) { return s.data && s.off >= 0 && s.off + C <= s.stride; }
 
+int dn_wgrad_nhwc(dn_slice dz, dn_slice x, int32_t B, int32_t H, int32_t W, int32_t taps, int32_t cout, int32_t cin,
+                  float *dw, void *stream) {
+  if (!slice_ok(dz, cout) || !slice_ok(x, cin) || !dw || (taps != 9 && taps != 1)) return MCR_ERR_ARG;
+  if (B <= 0 || H <= 0 || W < 16 || (W & (W - 1)) || ((long long)H * W) % 64) return MCR_ERR_ARG;
+  if (cout < 1 || cin < 1 || cout > 512 || cin > 512) return MCR_ERR_ARG;
+  // TMA: 16-byte aligned slice bases and row strides
+  if (dz.off % 8 || dz.stride % 8 || x.off % 8 || x.stride % 8) return MCR_ERR_ARG;
+  unsigned *err = error_word();
+  if (!err) return MCR_ERR_CUDA;
+  const uint64_t HW = (uint64_t)H * W;
+  CUtensorMap tmA, tmB;
+  {
+    const uint64_t dims[2] = {(uint64_t)cout, (uint64_t)B * HW};
+    const uint64_t strides[1] = {(uint64_t)dz.stride * 2};
+    const uint32_t box[2] = {64, 64};
+    void *base = static_cast<char *>(dz.data) + (size_t)dz.off * 2;
+    if (encode_tiled(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box,
+                     CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+      return MCR_ERR_CUDA;
+  }
+  {
+    const int wbox = W < 64 ? W : 64;
+    const uint64_t dims[4] = {(uint64_t)cin, (uint64_t)W, (uint64_t)H, (uint64_t)B};
+    const uint64_t strides[3] = {(uint64_t)x.stride * 2, (uint64_t)W * x.stride * 2, HW * x.stride * 2};
+    const uint32_t box[4] = {64, (uint32_t)wbox, (uint32_t)(64 / wbox), 1};
+    void *base = static_cast<char *>(x.data) + (size_t)x.off * 2;
+    if (encode_tiled(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box,
+                     CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+      return MCR_ERR_CUDA;
+  }
+  WgradArgs a{};
+  a.B = B;
+  a.HW = (int)HW;
+  a.W = W;
+  a.taps = taps;
+  a.cout = cout;
+  a.cin = cin;
+  a.cin_pad = cin;
+  a.N = cin > 64 ? 128 : 64;  // whole 64-channel boxes
+  a.m_tiles = (cout + 127) / 128;
+  a.n_tiles = (cin + a.N - 1) / a.N;
+  const long long kblocks = (long long)B * HW / 64;
+  long long splits = (2 * 152 + taps * a.m_tiles * a.n_tiles - 1) / (taps * a.m_tiles * a.n_tiles);
+  if (splits > kblocks) splits = kblocks;
+  if (splits < 1) splits = 1;
+  a.splits = (int)splits;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)a.N) cols <<= 1;
+  a.tmem_cols = cols;
+  a.dw = dw;
+  a.err = err;
+  if (launch_wgrad_mn(tmA, tmB, a, (cudaStream_t)stream) != cudaSuccess) return MCR_ERR_CUDA;
+  return MCR_OK;
+}
+
 int dn_to_ct(dn_slice src, int32_t B, int32_t H, int32_t W, int32_t C, int32_t shifted, void *dst, void *stream) {
   if (!slice_ok(src, C) || !dst || B <= 0 || H <= 0 || W <= 0 || C <= 0) return MCR_ERR_ARG;
   DN_TRY(to_ct(static_cast<const __nv_bfloat16 *>(src.data), B, H * W, W, src.stride, src.off, C, shifted,

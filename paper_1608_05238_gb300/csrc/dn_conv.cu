@@ -319,6 +319,117 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
 }
 
+// k_wgrad_mn: the same weight gradient read straight from the NHWC activations, with both
+// operands MN-major (channels contiguous, pixels = K rows): A = dZ [pixels][cout] in 2D boxes of
+// 64 channels x 64 pixels, B = X [b][y][x][cin] in 4D boxes of 64 channels x a 64-pixel block,
+// the tap's shift applied as TMA coordinates (x + kx - 1, y + ky - 1) with hardware zero fill at
+// the image border -- no transposed or shifted copies.  A 128-byte-swizzled MN-major operand of
+// M (or N) = 64 j channels is j boxes 8 KB apart (leading byte offset 8 KB), 8-pixel groups
+// 1 KB apart (stride byte offset), and each K = 16 step advances 16 pixel rows (2 KB).
+constexpr int kWgMnSlack = 32768;  // unused shared memory after the ring
+
+__global__ void __launch_bounds__(128, 1)
+    k_wgrad_mn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const WgradArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t bTileBytes = (uint32_t)a.N * kBlockK * 2;  // N channels x 64 pixels
+  uint8_t *tileA = smem;
+  uint8_t *tileB = smem + kStages * kATileBytes;
+  uint64_t *full = reinterpret_cast<uint64_t *>(tileB + kStages * bTileBytes);
+  uint64_t *empty = full + kStages;
+  uint64_t *done = empty + kStages;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int split = blockIdx.x, tap = blockIdx.y;
+  const int m_tile = blockIdx.z % a.m_tiles, n_tile = blockIdx.z / a.m_tiles;
+  const int ky = a.taps == 9 ? tap / 3 : 1, kx = a.taps == 9 ? tap % 3 : 1;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    fence_barrier_init();
+    prefetch_tensormap(&tmA);
+    prefetch_tensormap(&tmB);
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, a.tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int blocks_per_image = a.HW / kBlockK;
+  const int total = a.B * blocks_per_image;
+  const int k_begin = (int)((long long)total * split / a.splits);
+  const int k_end = (int)((long long)total * (split + 1) / a.splits);
+  const int nk = k_end - k_begin;
+  const int nb = a.N / 64;  // B boxes per stage
+
+  if (warp == 0 && lane == 0) {
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kStages, r = i / kStages;
+      if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1)) {
+        atomicOr(a.err, 8u);
+        break;
+      }
+      const int kb = k_begin + i;
+      const int b = kb / blocks_per_image, p = (kb % blocks_per_image) * kBlockK;  // first pixel in image b
+      const int y0 = p / a.W, x0 = p % a.W;
+      mbar_arrive_expect_tx(&full[s], kATileBytes + bTileBytes);
+      uint8_t *sa = tileA + s * kATileBytes, *sb = tileB + s * bTileBytes;
+      const int pg = b * a.HW + p;  // pixel index in the flattened dZ
+      tma_load_2d(sa, &tmA, &full[s], m_tile * kBlockM, pg);
+      tma_load_2d(sa + 8192, &tmA, &full[s], m_tile * kBlockM + 64, pg);
+      for (int j = 0; j < nb; ++j)
+        tma_load_4d(sb + j * 8192, &tmB, &full[s], n_tile * a.N + 64 * j, x0 + kx - 1, y0 + ky - 1, b);
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_bf16_f32(kBlockM, (uint32_t)a.N) | (1u << 15) | (1u << 16);  // A, B MN-major
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kStages, r = i / kStages;
+      if (!mbar_wait(&full[s], r & 1)) {
+        atomicOr(a.err, 16u);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t aBase = smem_u32(tileA + s * kATileBytes), bBase = smem_u32(tileB + s * bTileBytes);
+#pragma unroll
+      for (int kk = 0; kk < kBlockK / 16; ++kk)
+        mma_bf16(tmem, sdesc_mn128(aBase + kk * 2048), sdesc_mn128(bBase + kk * 2048), idesc,
+                 (i > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+
+  const bool have = nk > 0 && __all_sync(0xffffffffu, mbar_wait(done, 0));
+  if (nk > 0 && !have && tid == 0) atomicOr(a.err, 32u);
+  tc_fence_after();
+  const int m = m_tile * kBlockM + warp * 32 + lane;  // output channel of this thread's row
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  for (int c0 = 0; c0 < a.N; c0 += 16) {
+    uint32_t v[16];
+    tmem_ld16(trow + (uint32_t)c0, v);
+    tmem_ld_wait();
+    if (!have || m >= a.cout) continue;
+    float *o = a.dw + ((size_t)m * a.taps + tap) * a.cin_pad + n_tile * a.N + c0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int c = n_tile * a.N + c0 + j;
+      if (c < a.cin) atomicAdd(o + j, __uint_as_float(v[j]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
+}
+
 }  // namespace
 
 cudaError_t launch_wgrad_tc(const CUtensorMap &tmA, const CUtensorMap tmB[3], const WgradArgs &a, cudaStream_t s) {
@@ -379,6 +490,19 @@ cudaError_t launch_conv_tc(const CUtensorMap &tmX, const CUtensorMap &tmW, const
   // fit in the 512 TMEM columns and the pixels split into 256-pixel tiles
   if (a.N <= 128 && P % (2 * kBlockM) == 0) return launch_ws<2>(tmX, tmW, a, s);
   return launch_ws<1>(tmX, tmW, a, s);
+}
+
+cudaError_t launch_wgrad_mn(const CUtensorMap &tmA, const CUtensorMap &tmB, const WgradArgs &a, cudaStream_t s) {
+  const size_t smem = 1024 + kStages * (kATileBytes + (size_t)a.N * kBlockK * 2) + 256 + kWgMnSlack;
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_mn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  const dim3 grid((unsigned)a.splits, (unsigned)a.taps, (unsigned)(a.m_tiles * a.n_tiles));
+  k_wgrad_mn<<<grid, 128, smem, s>>>(tmA, tmB, a);
+  return cudaGetLastError();
 }
 
 }  // namespace dn

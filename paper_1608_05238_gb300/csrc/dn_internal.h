@@ -41,6 +41,7 @@ struct WgradArgs {
   unsigned *err;
 };
 cudaError_t launch_wgrad_tc(const CUtensorMap &tmA, const CUtensorMap tmB[3], const WgradArgs &a, cudaStream_t s);
+cudaError_t launch_wgrad_mn(const CUtensorMap &tmA, const CUtensorMap &tmB, const WgradArgs &a, cudaStream_t s);
 
 // memory-bound kernels (dn_ops.cu)
 cudaError_t to_ct(const __nv_bfloat16 *src, int B, int HW, int W, int stride, int off, int C, int shifted,

@@ -55,82 +55,59 @@ __global__ void k_to_ct(const __nv_bfloat16 *__restrict__ src, int B, int HW, in
   }
 }
 
-// 2x2 average pooling: dst[b][y][x] = mean of src[b][2y..2y+1][2x..2x+1]
-__global__ void k_pool2(const __nv_bfloat16 *__restrict__ src, int B, int H, int W, int sstride, int soff, int C,
+// The pooling / up-sampling kernels below use one thread per (pixel, channel) with a 3D grid:
+// x = blockIdx.x * 8 + threadIdx.y is the pixel column, blockIdx.y the pixel row over all images
+// (row R of image b is b * rows + y, so the 2x2 neighbourhoods follow from R by shifts), and
+// c = blockIdx.z * 32 + threadIdx.x the channel: a warp touches 32 consecutive channels of one
+// pixel and no thread divides.
+
+// 2x2 average pooling: dst[R][x] = mean of src[2R..2R+1][2x..2x+1] (dst Wo = W/2 columns)
+__global__ void k_pool2(const __nv_bfloat16 *__restrict__ src, int W, int sstride, int soff, int C,
                         __nv_bfloat16 *__restrict__ dst, int dstride, int doff) {
-  const int Ho = H / 2, Wo = W / 2;
-  const long long n = (long long)B * Ho * Wo * C;
-  for (long long i = blockIdx.x * (long long)kT + threadIdx.x; i < n; i += (long long)gridDim.x * kT) {
-    const int c = (int)(i % C);
-    long long q = i / C;
-    const int x = (int)(q % Wo);
-    q /= Wo;
-    const int y = (int)(q % Ho);
-    const int b = (int)(q / Ho);
-    const size_t s00 = (((size_t)b * H + 2 * y) * W + 2 * x) * sstride + soff + c;
-    const float v = 0.25f * (bf(src[s00]) + bf(src[s00 + sstride]) + bf(src[s00 + (size_t)W * sstride]) +
-                             bf(src[s00 + (size_t)W * sstride + sstride]));
-    dst[(((size_t)b * Ho + y) * Wo + x) * dstride + doff + c] = __float2bfloat16_rn(v);
-  }
+  const int x = blockIdx.x * 8 + threadIdx.y, R = blockIdx.y, c = blockIdx.z * 32 + threadIdx.x;
+  const int Wo = W >> 1;
+  if (x >= Wo || c >= C) return;
+  const size_t s00 = ((size_t)(2 * R) * W + 2 * x) * sstride + soff + c;
+  const float v = 0.25f * (bf(src[s00]) + bf(src[s00 + sstride]) + bf(src[s00 + (size_t)W * sstride]) +
+                           bf(src[s00 + (size_t)W * sstride + sstride]));
+  dst[((size_t)R * Wo + x) * dstride + doff + c] = __float2bfloat16_rn(v);
 }
 
 // backward of pool2 plus an optional skip gradient, times the ReLU mask of the pooled tensor:
-// dz[b][y][x] = (skip[b][y][x] + dp[b][y/2][x/2] / 4) * (y_act[b][y][x] > 0)
+// dz[R][x] = (skip[R][x] + dp[R/2][x/2] / 4) * (act[R][x] > 0) on the full-resolution grid
 __global__ void k_pool2_bwd(const __nv_bfloat16 *__restrict__ dp, int pstride, int poff,
                             const __nv_bfloat16 *__restrict__ skip, int kstride, int koff,
-                            const __nv_bfloat16 *__restrict__ act, int astride, int aoff, int B, int H, int W, int C,
+                            const __nv_bfloat16 *__restrict__ act, int astride, int aoff, int W, int C,
                             __nv_bfloat16 *__restrict__ dz, int zstride, int zoff) {
-  const long long n = (long long)B * H * W * C;
-  for (long long i = blockIdx.x * (long long)kT + threadIdx.x; i < n; i += (long long)gridDim.x * kT) {
-    const int c = (int)(i % C);
-    long long q = i / C;
-    const int x = (int)(q % W);
-    q /= W;
-    const int y = (int)(q % H);
-    const int b = (int)(q / H);
-    const size_t pix = ((size_t)b * H + y) * W + x;
-    float g = 0.25f * bf(dp[(((size_t)b * (H / 2) + y / 2) * (W / 2) + x / 2) * pstride + poff + c]);
-    if (skip) g += bf(skip[pix * kstride + koff + c]);
-    if (!(bf(act[pix * astride + aoff + c]) > 0.f)) g = 0.f;
-    dz[pix * zstride + zoff + c] = __float2bfloat16_rn(g);
-  }
+  const int x = blockIdx.x * 8 + threadIdx.y, R = blockIdx.y, c = blockIdx.z * 32 + threadIdx.x;
+  if (x >= W || c >= C) return;
+  const size_t pix = (size_t)R * W + x;
+  float g = 0.25f * bf(dp[((size_t)(R >> 1) * (W >> 1) + (x >> 1)) * pstride + poff + c]);
+  if (skip) g += bf(skip[pix * kstride + koff + c]);
+  if (!(bf(act[pix * astride + aoff + c]) > 0.f)) g = 0.f;
+  dz[pix * zstride + zoff + c] = __float2bfloat16_rn(g);
 }
 
-// nearest 2x up-sampling: dst[b][y][x] = src[b][y/2][x/2]   (src is H x W, dst 2H x 2W)
-__global__ void k_up2(const __nv_bfloat16 *__restrict__ src, int B, int H, int W, int sstride, int soff, int C,
+// nearest 2x up-sampling: dst[R][x] = src[R/2][x/2]   (src W columns, dst 2W)
+__global__ void k_up2(const __nv_bfloat16 *__restrict__ src, int W, int sstride, int soff, int C,
                       __nv_bfloat16 *__restrict__ dst, int dstride, int doff) {
-  const long long n = (long long)B * 4 * H * W * C;
-  for (long long i = blockIdx.x * (long long)kT + threadIdx.x; i < n; i += (long long)gridDim.x * kT) {
-    const int c = (int)(i % C);
-    long long q = i / C;
-    const int x = (int)(q % (2 * W));
-    q /= 2 * W;
-    const int y = (int)(q % (2 * H));
-    const int b = (int)(q / (2 * H));
-    dst[(((size_t)b * 2 * H + y) * 2 * W + x) * dstride + doff + c] =
-        src[(((size_t)b * H + y / 2) * W + x / 2) * sstride + soff + c];
-  }
+  const int x = blockIdx.x * 8 + threadIdx.y, R = blockIdx.y, c = blockIdx.z * 32 + threadIdx.x;
+  if (x >= 2 * W || c >= C) return;
+  dst[((size_t)R * 2 * W + x) * dstride + doff + c] = src[((size_t)(R >> 1) * W + (x >> 1)) * sstride + soff + c];
 }
 
-// backward of up2 times the ReLU mask of its input: dz[b][y][x] = sum_2x2 du * (act > 0)
+// backward of up2 times the ReLU mask of its input: dz[R][x] = sum_2x2 du * (act > 0)  (dz W columns)
 __global__ void k_up2_bwd(const __nv_bfloat16 *__restrict__ du, int ustride, int uoff,
-                          const __nv_bfloat16 *__restrict__ act, int astride, int aoff, int B, int H, int W, int C,
+                          const __nv_bfloat16 *__restrict__ act, int astride, int aoff, int W, int C,
                           __nv_bfloat16 *__restrict__ dz, int zstride, int zoff) {
-  const long long n = (long long)B * H * W * C;
-  for (long long i = blockIdx.x * (long long)kT + threadIdx.x; i < n; i += (long long)gridDim.x * kT) {
-    const int c = (int)(i % C);
-    long long q = i / C;
-    const int x = (int)(q % W);
-    q /= W;
-    const int y = (int)(q % H);
-    const int b = (int)(q / H);
-    const size_t u00 = (((size_t)b * 2 * H + 2 * y) * 2 * W + 2 * x) * ustride + uoff + c;
-    float g = bf(du[u00]) + bf(du[u00 + ustride]) + bf(du[u00 + (size_t)2 * W * ustride]) +
-              bf(du[u00 + (size_t)2 * W * ustride + ustride]);
-    const size_t pix = ((size_t)b * H + y) * W + x;
-    if (!(bf(act[pix * astride + aoff + c]) > 0.f)) g = 0.f;
-    dz[pix * zstride + zoff + c] = __float2bfloat16_rn(g);
-  }
+  const int x = blockIdx.x * 8 + threadIdx.y, R = blockIdx.y, c = blockIdx.z * 32 + threadIdx.x;
+  if (x >= W || c >= C) return;
+  const size_t u00 = ((size_t)(2 * R) * 2 * W + 2 * x) * ustride + uoff + c;
+  float g = bf(du[u00]) + bf(du[u00 + ustride]) + bf(du[u00 + (size_t)2 * W * ustride]) +
+            bf(du[u00 + (size_t)2 * W * ustride + ustride]);
+  const size_t pix = (size_t)R * W + x;
+  if (!(bf(act[pix * astride + aoff + c]) > 0.f)) g = 0.f;
+  dz[pix * zstride + zoff + c] = __float2bfloat16_rn(g);
 }
 
 // db[c] += sum over pixels of dz[p][c]
@@ -153,45 +130,52 @@ __global__ void k_bias_grad(const __nv_bfloat16 *__restrict__ dz, long long P, i
 
 // residual MSE: y = x + out over C channels; loss partials (FP64) and dout = 2 (y - t) / count
 // written as bf16 NHWC (stride dstride) for the next convolution's input gradient.
+// One thread per (pixel, channel): threadIdx.x over channels, the rest over pixels (grid-stride),
+// the difference in FP32, each thread's sum of squares in FP64 (fixed order).
 __global__ void k_mse(const float *__restrict__ out, int ostride, const __nv_bfloat16 *__restrict__ x, int xstride,
-                      const float *__restrict__ t, long long P, int C, double inv_count,
+                      const float *__restrict__ t, long long P, int C, float two_over_count,
                       __nv_bfloat16 *__restrict__ dout, int dstride, double *__restrict__ partials) {
   __shared__ double red[kT / 32];
   double acc = 0.0;
-  const long long n = P * C;
-  for (long long i = blockIdx.x * (long long)kT + threadIdx.x; i < n; i += (long long)gridDim.x * kT) {
-    const long long p = i / C;
-    const int c = (int)(i % C);
-    const float y = bf(x[p * xstride + c]) + out[p * ostride + c];
-    const double d = (double)y - (double)t[i];
-    acc += d * d;
-    dout[p * dstride + c] = __float2bfloat16_rn((float)(2.0 * d * inv_count));
-  }
+  const int c = threadIdx.x + 32 * blockIdx.y;
+  if (c < C)
+    for (long long p = blockIdx.x * 8ll + threadIdx.y; p < P; p += gridDim.x * 8ll) {
+      const float d = bf(x[p * xstride + c]) + out[p * ostride + c] - t[p * C + c];
+      acc += (double)(d * d);
+      dout[p * dstride + c] = __float2bfloat16_rn(d * two_over_count);
+    }
+  const int tid = threadIdx.y * 32 + threadIdx.x;
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  if ((tid & 31) == 0) red[tid >> 5] = acc;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double s = 0.0;
     for (int w = 0; w < kT / 32; ++w) s += red[w];
-    partials[blockIdx.x] = s;
+    partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
 }
 
+// One block: strided per-thread sums, then a fixed-order tree (deterministic).
 __global__ void k_sum_partials(const double *__restrict__ partials, int n, double scale, double *out) {
+  __shared__ double red[kT];
   double s = 0.0;
-  for (int i = 0; i < n; ++i) s += partials[i];
-  *out = s * scale;
+  for (int i = threadIdx.x; i < n; i += kT) s += partials[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = kT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0] * scale;
 }
 
 // prediction y = x + out (fp32 [P][C] from [P][ostride]); used at inference
 __global__ void k_residual(const float *__restrict__ out, int ostride, const __nv_bfloat16 *__restrict__ x,
                            int xstride, long long P, int C, float *__restrict__ y) {
-  const long long n = P * C;
-  for (long long i = blockIdx.x * (long long)kT + threadIdx.x; i < n; i += (long long)gridDim.x * kT) {
-    const long long p = i / C;
-    const int c = (int)(i % C);
-    y[i] = bf(x[p * xstride + c]) + out[p * ostride + c];
-  }
+  const int c = threadIdx.x + 32 * blockIdx.y;
+  if (c >= C) return;
+  for (long long p = blockIdx.x * 8ll + threadIdx.y; p < P; p += gridDim.x * 8ll)
+    y[p * C + c] = bf(x[p * xstride + c]) + out[p * ostride + c];
 }
 
 // Adam on the FP32 master weights [cout][taps][cin] and bias; writes the forward BF16 copy
@@ -237,16 +221,24 @@ __global__ void k_adam_bias(float *__restrict__ b, float *__restrict__ m, float 
   b[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+// Layout changes between channel-major [B][C][HW] maps (the MC's output) and pixel-major NHWC
+// rows go through a 32 x 32 shared-memory tile (grid: pixel blocks x channel blocks x images),
+// so both the reads and the writes are coalesced.
+
 // channel-major fp32 coefficient maps [B][C][HW] * scale[b] -> NHWC bf16 [B][HW][stride]
-__global__ void k_pack_input(const float *__restrict__ src, const float *__restrict__ scale, int B, long long HW,
-                             int C, __nv_bfloat16 *__restrict__ dst, int stride) {
-  const long long n = (long long)B * HW * C;
-  for (long long i = blockIdx.x * (long long)kT + threadIdx.x; i < n; i += (long long)gridDim.x * kT) {
-    const int c = (int)(i % C);
-    const long long q = i / C;
-    const long long p = q % HW;
-    const int b = (int)(q / HW);
-    dst[((size_t)b * HW + p) * stride + c] = __float2bfloat16_rn(src[((size_t)b * C + c) * HW + p] * scale[b]);
+__global__ void k_pack_input(const float *__restrict__ src, const float *__restrict__ scale, int HW, int C,
+                             __nv_bfloat16 *__restrict__ dst, int stride) {
+  __shared__ float tile[32][33];
+  const int p0 = blockIdx.x * 32, c0 = blockIdx.y * 32, b = blockIdx.z;
+  const float sc = scale[b];
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int c = c0 + r, p = p0 + threadIdx.x;
+    tile[r][threadIdx.x] = (c < C && p < HW) ? src[((size_t)b * C + c) * HW + p] * sc : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int p = p0 + r, c = c0 + threadIdx.x;
+    if (p < HW && c < C) dst[((size_t)b * HW + p) * stride + c] = __float2bfloat16_rn(tile[threadIdx.x][r]);
   }
 }
 
@@ -270,28 +262,36 @@ __global__ void k_sample_scale(const float *__restrict__ src, int C, long long H
 }
 
 // channel-major fp32 [B][C][HW] * scale[b] -> NHWC fp32 [B][HW][C]   (training targets)
-__global__ void k_pack_target(const float *__restrict__ src, const float *__restrict__ scale, int B, long long HW,
-                              int C, float *__restrict__ dst) {
-  const long long n = (long long)B * HW * C;
-  for (long long i = blockIdx.x * (long long)kT + threadIdx.x; i < n; i += (long long)gridDim.x * kT) {
-    const int c = (int)(i % C);
-    const long long q = i / C;
-    const long long p = q % HW;
-    const int b = (int)(q / HW);
-    dst[i] = src[((size_t)b * C + c) * HW + p] * scale[b];
+__global__ void k_pack_target(const float *__restrict__ src, const float *__restrict__ scale, int HW, int C,
+                              float *__restrict__ dst) {
+  __shared__ float tile[32][33];
+  const int p0 = blockIdx.x * 32, c0 = blockIdx.y * 32, b = blockIdx.z;
+  const float sc = scale[b];
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int c = c0 + r, p = p0 + threadIdx.x;
+    tile[r][threadIdx.x] = (c < C && p < HW) ? src[((size_t)b * C + c) * HW + p] * sc : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int p = p0 + r, c = c0 + threadIdx.x;
+    if (p < HW && c < C) dst[((size_t)b * HW + p) * C + c] = tile[threadIdx.x][r];
   }
 }
 
 // NHWC fp32 [B][HW][C] / scale[b] -> channel-major fp32 [B][C][HW]
-__global__ void k_unpack_output(const float *__restrict__ src, const float *__restrict__ scale, int B, long long HW,
-                                int C, float *__restrict__ dst) {
-  const long long n = (long long)B * HW * C;
-  for (long long i = blockIdx.x * (long long)kT + threadIdx.x; i < n; i += (long long)gridDim.x * kT) {
-    const int c = (int)(i % C);
-    const long long q = i / C;
-    const long long p = q % HW;
-    const int b = (int)(q / HW);
-    dst[((size_t)b * C + c) * HW + p] = src[i] / scale[b];
+__global__ void k_unpack_output(const float *__restrict__ src, const float *__restrict__ scale, int HW, int C,
+                                float *__restrict__ dst) {
+  __shared__ float tile[32][33];
+  const int p0 = blockIdx.x * 32, c0 = blockIdx.y * 32, b = blockIdx.z;
+  const float sc = scale[b];
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int p = p0 + r, c = c0 + threadIdx.x;
+    tile[r][threadIdx.x] = (p < HW && c < C) ? src[((size_t)b * HW + p) * C + c] / sc : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int c = c0 + r, p = p0 + threadIdx.x;
+    if (c < C && p < HW) dst[((size_t)b * C + c) * HW + p] = tile[threadIdx.x][r];
   }
 }
 
@@ -303,27 +303,34 @@ cudaError_t to_ct(const __nv_bfloat16 *src, int B, int HW, int W, int stride, in
   k_to_ct<<<grid, block, 0, s>>>(src, B, HW, W, stride, off, C, shifted, dst);
   return cudaGetLastError();
 }
+static dim3 pix_grid(int cols, int rows, int C) { return dim3((cols + 7) / 8, rows, (C + 31) / 32); }
+static bool pix_grid_ok(int rows, int C) { return rows >= 1 && rows <= 65535 && (C + 31) / 32 <= 65535; }
+
 cudaError_t pool2(const __nv_bfloat16 *src, int B, int H, int W, int sstride, int soff, int C, __nv_bfloat16 *dst,
                   int dstride, int doff, cudaStream_t s) {
-  k_pool2<<<blocks_for((long long)B * H * W * C / 4), kT, 0, s>>>(src, B, H, W, sstride, soff, C, dst, dstride, doff);
+  if (!pix_grid_ok(B * (H / 2), C)) return cudaErrorInvalidConfiguration;
+  k_pool2<<<pix_grid(W / 2, B * (H / 2), C), dim3(32, 8), 0, s>>>(src, W, sstride, soff, C, dst, dstride, doff);
   return cudaGetLastError();
 }
 cudaError_t pool2_bwd(const __nv_bfloat16 *dp, int pstride, int poff, const __nv_bfloat16 *skip, int kstride, int koff,
                       const __nv_bfloat16 *act, int astride, int aoff, int B, int H, int W, int C, __nv_bfloat16 *dz,
                       int zstride, int zoff, cudaStream_t s) {
-  k_pool2_bwd<<<blocks_for((long long)B * H * W * C), kT, 0, s>>>(dp, pstride, poff, skip, kstride, koff, act, astride,
-                                                                   aoff, B, H, W, C, dz, zstride, zoff);
+  if (!pix_grid_ok(B * H, C)) return cudaErrorInvalidConfiguration;
+  k_pool2_bwd<<<pix_grid(W, B * H, C), dim3(32, 8), 0, s>>>(dp, pstride, poff, skip, kstride, koff, act, astride, aoff,
+                                                             W, C, dz, zstride, zoff);
   return cudaGetLastError();
 }
 cudaError_t up2(const __nv_bfloat16 *src, int B, int H, int W, int sstride, int soff, int C, __nv_bfloat16 *dst,
                 int dstride, int doff, cudaStream_t s) {
-  k_up2<<<blocks_for((long long)B * 4 * H * W * C), kT, 0, s>>>(src, B, H, W, sstride, soff, C, dst, dstride, doff);
+  if (!pix_grid_ok(B * 2 * H, C)) return cudaErrorInvalidConfiguration;
+  k_up2<<<pix_grid(2 * W, B * 2 * H, C), dim3(32, 8), 0, s>>>(src, W, sstride, soff, C, dst, dstride, doff);
   return cudaGetLastError();
 }
 cudaError_t up2_bwd(const __nv_bfloat16 *du, int ustride, int uoff, const __nv_bfloat16 *act, int astride, int aoff,
                     int B, int H, int W, int C, __nv_bfloat16 *dz, int zstride, int zoff, cudaStream_t s) {
-  k_up2_bwd<<<blocks_for((long long)B * H * W * C), kT, 0, s>>>(du, ustride, uoff, act, astride, aoff, B, H, W, C, dz,
-                                                                 zstride, zoff);
+  if (!pix_grid_ok(B * H, C)) return cudaErrorInvalidConfiguration;
+  k_up2_bwd<<<pix_grid(W, B * H, C), dim3(32, 8), 0, s>>>(du, ustride, uoff, act, astride, aoff, W, C, dz, zstride,
+                                                           zoff);
   return cudaGetLastError();
 }
 cudaError_t bias_grad(const __nv_bfloat16 *dz, long long P, int stride, int off, int C, float *db, cudaStream_t s) {
@@ -335,16 +342,21 @@ cudaError_t bias_grad(const __nv_bfloat16 *dz, long long P, int stride, int off,
 }
 cudaError_t mse(const float *out, int ostride, const __nv_bfloat16 *x, int xstride, const float *t, long long P, int C,
                 __nv_bfloat16 *dout, int dstride, double *partials, int partials_cap, double *loss, cudaStream_t s) {
-  int grid = blocks_for(P * C);
-  if (grid > partials_cap) grid = partials_cap;
+  const int cy = (C + 31) / 32;
+  if (cy > partials_cap) return cudaErrorInvalidValue;
+  long long gx = (P + 8 * 16 - 1) / (8 * 16);  // ~16 pixels per thread
+  if (gx > partials_cap / cy) gx = partials_cap / cy;
   const double inv = 1.0 / ((double)P * C);
-  k_mse<<<grid, kT, 0, s>>>(out, ostride, x, xstride, t, P, C, inv, dout, dstride, partials);
-  k_sum_partials<<<1, 1, 0, s>>>(partials, grid, inv, loss);
+  k_mse<<<dim3((unsigned)gx, cy), dim3(32, 8), 0, s>>>(out, ostride, x, xstride, t, P, C, (float)(2.0 * inv), dout,
+                                                        dstride, partials);
+  k_sum_partials<<<1, kT, 0, s>>>(partials, (int)gx * cy, inv, loss);
   return cudaGetLastError();
 }
 cudaError_t residual(const float *out, int ostride, const __nv_bfloat16 *x, int xstride, long long P, int C, float *y,
                      cudaStream_t s) {
-  k_residual<<<blocks_for(P * C), kT, 0, s>>>(out, ostride, x, xstride, P, C, y);
+  long long gx = (P + 8 * 16 - 1) / (8 * 16);
+  if (gx > 65535) gx = 65535;
+  k_residual<<<dim3((unsigned)gx, (C + 31) / 32), dim3(32, 8), 0, s>>>(out, ostride, x, xstride, P, C, y);
   return cudaGetLastError();
 }
 cudaError_t adam(float *w, float *m, float *v, float *g, int cout, int taps, int cin, float lr, float b1,
@@ -364,7 +376,9 @@ cudaError_t adam_bias(float *b, float *m, float *v, float *g, int n, float lr, f
 }
 cudaError_t pack_input(const float *src, const float *scale, int B, long long HW, int C, __nv_bfloat16 *dst, int stride,
                        cudaStream_t s) {
-  k_pack_input<<<blocks_for((long long)B * HW * C), kT, 0, s>>>(src, scale, B, HW, C, dst, stride);
+  if (HW > 0x7fffffffll - 31 || B > 65535) return cudaErrorInvalidValue;
+  k_pack_input<<<dim3((unsigned)((HW + 31) / 32), (C + 31) / 32, B), dim3(32, 8), 0, s>>>(src, scale, (int)HW, C, dst,
+                                                                                         stride);
   return cudaGetLastError();
 }
 cudaError_t sample_scale(const float *src, int B, long long HW, int C, float *scale, cudaStream_t s) {
@@ -372,12 +386,15 @@ cudaError_t sample_scale(const float *src, int B, long long HW, int C, float *sc
   return cudaGetLastError();
 }
 cudaError_t pack_target(const float *src, const float *scale, int B, long long HW, int C, float *dst, cudaStream_t s) {
-  k_pack_target<<<blocks_for((long long)B * HW * C), kT, 0, s>>>(src, scale, B, HW, C, dst);
+  if (HW > 0x7fffffffll - 31 || B > 65535) return cudaErrorInvalidValue;
+  k_pack_target<<<dim3((unsigned)((HW + 31) / 32), (C + 31) / 32, B), dim3(32, 8), 0, s>>>(src, scale, (int)HW, C, dst);
   return cudaGetLastError();
 }
 cudaError_t unpack_output(const float *src, const float *scale, int B, long long HW, int C, float *dst,
                           cudaStream_t s) {
-  k_unpack_output<<<blocks_for((long long)B * HW * C), kT, 0, s>>>(src, scale, B, HW, C, dst);
+  if (HW > 0x7fffffffll - 31 || B > 65535) return cudaErrorInvalidValue;
+  k_unpack_output<<<dim3((unsigned)((HW + 31) / 32), (C + 31) / 32, B), dim3(32, 8), 0, s>>>(src, scale, (int)HW, C,
+                                                                                            dst);
   return cudaGetLastError();
 }
 

@@ -119,6 +119,20 @@ __device__ __forceinline__ uint64_t sdesc_k128(uint32_t smem_addr) {
   return d;
 }
 
+// Shared-memory descriptor of an MN-major operand (the M or N index contiguous) stored with the
+// 128-byte swizzle: each 128-byte row holds 64 consecutive M (N) elements of one K index, 8-row
+// atoms along K are 1024 B apart (stride byte offset) and consecutive 64-element groups along M
+// (N) are 8192 B apart (leading byte offset: boxes of 64 K rows); tile base 1024-byte aligned.
+__device__ __forceinline__ uint64_t sdesc_mn128(uint32_t smem_addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(8192u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
 // Instruction descriptor of tcgen05.mma kind::f16 with BF16 A and B (both K-major), FP32 D:
 // D format [4,6) = 1 (F32), A format [7,10) = 1 (BF16), B format [10,13) = 1 (BF16),
 // N >> 3 at [17,23), M >> 4 at [24,29).

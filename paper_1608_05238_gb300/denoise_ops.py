@@ -26,7 +26,7 @@ class _Slice(C.Structure):
     _fields_ = [("data", C.c_void_p), ("stride", C.c_int32), ("off", C.c_int32)]
 
 
-EXPORTS = ("dn_conv", "dn_wgrad", "dn_to_ct", "dn_pool2", "dn_pool2_bwd", "dn_up2", "dn_up2_bwd", "dn_bias_grad",
+EXPORTS = ("dn_conv", "dn_wgrad", "dn_wgrad_nhwc", "dn_to_ct", "dn_pool2", "dn_pool2_bwd", "dn_up2", "dn_up2_bwd", "dn_bias_grad",
            "dn_mse", "dn_residual", "dn_adam", "dn_adam_bias", "dn_pack_input", "dn_sample_scale", "dn_pack_target",
            "dn_unpack_output", "dn_check")
 
@@ -40,6 +40,7 @@ def lib():
         sig = {
             "dn_conv": [C.POINTER(_ConvDesc), vp],
             "dn_wgrad": [i32, i32, i32, i32, i32, i32, vp, vp, vp, vp],
+            "dn_wgrad_nhwc": [S, S, i32, i32, i32, i32, i32, i32, vp, vp],
             "dn_to_ct": [S, i32, i32, i32, i32, i32, vp, vp],
             "dn_pool2": [S, i32, i32, i32, i32, S, vp],
             "dn_pool2_bwd": [S, S, S, i32, i32, i32, i32, S, vp],
@@ -102,6 +103,11 @@ def wgrad(dzT: torch.Tensor, xT: torch.Tensor, B, H, W, taps, cout, cin, dw: tor
     assert dzT.dtype == torch.bfloat16 and xT.dtype == torch.bfloat16 and dw.dtype == torch.float32
     assert dzT.numel() >= cout * B * H * W and xT.numel() >= 3 * cin * B * H * W and dw.numel() >= cout * taps * cin
     _call("dn_wgrad", B, H, W, taps, cout, cin, _p(dzT), _p(xT), _p(dw), _stream(stream))
+
+
+def wgrad_nhwc(dz: Act, x: Act, taps: int, dw: torch.Tensor, stream=None):
+    """dw[n][tap][c] += sum over pixels of dz[p][n] x[p + tap][c], read from the NHWC slices."""
+    _call("dn_wgrad_nhwc", dz.s(), x.s(), x.B, x.H, x.W, taps, dz.C, x.C, _p(dw), _stream(stream))
 
 
 def to_ct(src: Act, shifted: bool, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -153,8 +153,6 @@ class UNet:
         g["dp0"], g["dp1"], g["dp2"] = torch.zeros_like(a["p0"]), torch.zeros_like(a["p1"]), torch.zeros_like(a["p2"])
         self.g = g
         P = B * H * W
-        self.s_dzT = torch.zeros(max(self.in_ch, c[0]) * P + 4096, dtype=torch.bfloat16, device=dev)
-        self.s_xT = torch.zeros(3 * (c[1] + c[0]) * P + 4096, dtype=torch.bfloat16, device=dev)
         self.target = torch.zeros(B, H, W, self.in_ch, device=dev)
         self.loss = torch.zeros((), dtype=torch.float64, device=dev)
         self.pred = torch.zeros(B, self.in_ch, H, W, device=dev)
@@ -202,10 +200,8 @@ class UNet:
         return a["out"]
 
     def _wgrad(self, lay: Conv, dz: torch.Tensor, x: Act):
-        B, H, W = dz.shape[:3]
-        dzT = ops.to_ct(Act(dz, lay.cout), False, out=self.s_dzT)
-        xT = ops.to_ct(x, True, out=self.s_xT)
-        ops.wgrad(dzT, xT, B, H, W, lay.taps, lay.cout, lay.cin, lay.gw)
+        # straight from the NHWC activations (MN-major operands, no transposed copies)
+        ops.wgrad_nhwc(Act(dz, lay.cout), x, lay.taps, lay.gw)
         ops.bias_grad(Act(dz, lay.cout), lay.gb)
 
     def backward(self):

@@ -47,6 +47,27 @@ def test_wgrad_matches_autograd(B, H, W, cin, cout, taps):
     assert torch.allclose(got, ref_dw, rtol=1e-4, atol=1e-4 * ref_dw.abs().max().item())
 
 
+@pytest.mark.parametrize("B,H,W,cin,cout,taps,xoff,zoff", [(2, 16, 32, 64, 32, 9, 0, 0), (1, 32, 64, 96, 128, 9, 64, 0),
+                                                            (2, 16, 16, 33, 48, 1, 0, 64), (1, 8, 128, 200, 256, 9, 0, 0),
+                                                            (3, 4, 16, 40, 33, 9, 24, 8), (1, 64, 256, 32, 32, 9, 32, 0)])
+def test_wgrad_nhwc_matches_autograd(B, H, W, cin, cout, taps, xoff, zoff):
+    """The weight gradient read straight from NHWC slices (MN-major operands, tap shifts as TMA
+    coordinates) equals FP64 autograd of the convolution, also for slices at channel offsets."""
+    x = _nhwc(B, H, W, cin + xoff, r64(cin + xoff), 11)
+    dz = _nhwc(B, H, W, cout + zoff, r64(cout + zoff), 12)
+    dw = torch.zeros(cout, taps, cin, device="cuda")
+    ops.wgrad_nhwc(Act(dz, cout, zoff), Act(x, cin, xoff), taps, dw)
+    ops.check()
+    k = 3 if taps == 9 else 1
+    xc = x.double().cpu()[..., xoff:xoff + cin].permute(0, 3, 1, 2)
+    w = torch.zeros(cout, cin, k, k, dtype=torch.float64, requires_grad=True)
+    y = Fnn.conv2d(xc, w, padding=k // 2)
+    y.backward(dz.double().cpu()[..., zoff:zoff + cout].permute(0, 3, 1, 2))
+    ref_dw = w.grad.permute(0, 2, 3, 1).reshape(cout, taps, cin)
+    got = dw.double().cpu()
+    assert torch.allclose(got, ref_dw, rtol=1e-4, atol=1e-4 * ref_dw.abs().max().item())
+
+
 def test_layout_pool_upsample_and_backward_kernels():
     B, H, W, C = 2, 16, 32, 40
     x = _nhwc(B, H, W, C, 128, 3)
