@@ -49,6 +49,8 @@ def _case(B, H, W, cin, cout, taps, seed, cin_pad=None, n_pad=None):
     (3, 8, 128, 33, 48, 9),    # padded input channels
     (1, 12, 32, 64, 128, 9),   # three 128-pixel tiles: no 256-pixel pairing
     (2, 4, 32, 64, 96, 9),     # a 256-pixel pair spanning two images
+    (2, 5, 128, 64, 32, 9),    # odd image height, 256-pixel pairs over rows of 128
+    (1, 3, 512, 192, 16, 9),   # rows of 512 pixels, three channel blocks, N = 16
 ])
 def test_conv_fp32_output_matches_reference(B, H, W, cin, cout, taps):
     x, w, cin_pad, n_pad = _case(B, H, W, cin, cout, taps, seed=B * 100 + H + W + cout)
@@ -76,6 +78,24 @@ def test_conv_bias_relu_bf16_slice_and_mask():
     ops.check()
     ref2 = _ref(x, w, cin, cout, 9, mask=mask, mask_off=8)
     assert torch.allclose(out2[..., :cout].double().cpu(), ref2, rtol=1e-4, atol=1e-4 * ref2.abs().max().item())
+
+
+def test_wide_row_conv_bias_relu_slice_and_mask():
+    """Paired 256-pixel tiles of 256-pixel rows (N <= 64) through every epilogue option."""
+    B, H, W, cin, cout = 2, 6, 256, 72, 40
+    x, w, cin_pad, n_pad = _case(B, H, W, cin, cout, 9, seed=17)
+    bias = torch.randn(cout).cuda()
+    out = torch.zeros(B, H, W, 128, dtype=torch.bfloat16, device="cuda")
+    ops.conv(x, w, cout, out, bias=bias, relu=True, out_off=64)
+    ref = _ref(x, w, cin, cout, 9, bias=bias, relu=True)
+    assert torch.allclose(out[..., 64:64 + cout].double().cpu(), ref, rtol=2 ** -7, atol=1e-3)
+    assert torch.count_nonzero(out[..., :64]) == 0 and torch.count_nonzero(out[..., 64 + cout:]) == 0
+    mask = torch.randn(B, H, W, 64).bfloat16().cuda()
+    out2 = torch.zeros(B, H, W, 40, device="cuda")
+    ops.conv(x, w, cout, out2, mask=mask, mask_off=16)
+    ops.check()
+    ref2 = _ref(x, w, cin, cout, 9, mask=mask, mask_off=16)
+    assert torch.allclose(out2.double().cpu(), ref2, rtol=1e-4, atol=1e-4 * ref2.abs().max().item())
 
 
 def test_conv_rejects_bad_shapes():
