@@ -235,7 +235,7 @@ int dn_wgrad_nhwc(dn_slice dz, dn_slice x, int32_t B, int32_t H, int32_t W, int3
   a.cout = cout;
   a.cin = cin;
   a.cin_pad = cin;
-  a.N = cin > 64 ? 128 : 64;  // whole 64-channel boxes
+  a.N = cin > 128 ? 128 : ((cin + 15) / 16) * 16;  // MMA N; B arrives in whole 64-channel boxes
   a.m_tiles = (cout + 127) / 128;
   a.n_tiles = (cin + a.N - 1) / a.N;
   const long long kblocks = (long long)B * HW / 64;

@@ -332,7 +332,8 @@ __global__ void __launch_bounds__(128, 1)
     k_wgrad_mn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const WgradArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t bTileBytes = (uint32_t)a.N * kBlockK * 2;  // N channels x 64 pixels
+  const int nb = (a.N + 63) / 64;  // 64-channel B boxes per stage (the MMA uses the first N)
+  const uint32_t bTileBytes = (uint32_t)nb * 8192u;
   uint8_t *tileA = smem;
   uint8_t *tileB = smem + kStages * kATileBytes;
   uint64_t *full = reinterpret_cast<uint64_t *>(tileB + kStages * bTileBytes);
@@ -368,7 +369,6 @@ __global__ void __launch_bounds__(128, 1)
   const int k_begin = (int)((long long)total * split / a.splits);
   const int k_end = (int)((long long)total * (split + 1) / a.splits);
   const int nk = k_end - k_begin;
-  const int nb = a.N / 64;  // B boxes per stage
 
   if (warp == 0 && lane == 0) {
     for (int i = 0; i < nk; ++i) {
@@ -493,7 +493,7 @@ cudaError_t launch_conv_tc(const CUtensorMap &tmX, const CUtensorMap &tmW, const
 }
 
 cudaError_t launch_wgrad_mn(const CUtensorMap &tmA, const CUtensorMap &tmB, const WgradArgs &a, cudaStream_t s) {
-  const size_t smem = 1024 + kStages * (kATileBytes + (size_t)a.N * kBlockK * 2) + 256 + kWgMnSlack;
+  const size_t smem = 1024 + kStages * (kATileBytes + (size_t)((a.N + 63) / 64) * 8192) + 256 + kWgMnSlack;
   static size_t configured = 0;
   if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(k_wgrad_mn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
