@@ -49,6 +49,7 @@ def _args():
                     help="packets per forward and per adjoint run (default 1e7 for grad256, 2e7 for large1024)")
     ap.add_argument("--cpu-sample", type=int, default=200_000, help="oracle packets (fwd and adj) for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-grad-error", action="store_true", help="skip the gradient-error measurement")
     ap.add_argument("--plain-gd", action="store_true", help="invert256: no fluence preconditioning")
     ap.add_argument("--workload", default="grad256",
                     choices=["grad256", "large1024", "batch64", "denoise256", "conv", "invert256"],
@@ -250,10 +251,10 @@ def _gpu(args):
     leaf_a = mua.clone().requires_grad_(True)
     leaf_s = mus.clone().requires_grad_(True)
 
-    def step(k, a=leaf_a, s=leaf_s, hm=Hmeas):
+    def step(k, a=leaf_a, s=leaf_s, hm=Hmeas, scale=1):
         # one gradient evaluation through the autograd.Function: H(mu) -> eps -> backward
         base = replica_seed(rank, k)
-        spec = MCSpec(dx=dx, g=g, sources=srcs, K=w.K, n_packets=per_src, n_adjoint=n, seed=base,
+        spec = MCSpec(dx=dx, g=g, sources=srcs, K=w.K, n_packets=scale * per_src, n_adjoint=scale * n, seed=base,
                       adjoint_seed=base + 1)
         a.grad = None
         s.grad = None
@@ -324,6 +325,20 @@ def _gpu(args):
         e2e_T += time.perf_counter() - t0
     e2e_val = job_throughput(n_fwd + n, args.steps, world, max_over_ranks(e2e_T, dev))
 
+    # the error the rate is quoted at: relative L2 error of one gradient evaluation at this
+    # packet count against one with 10x the packets (independent seeds); the reference's own
+    # noise is 1/sqrt(10) of it, so the error proper is the measured one / sqrt(1.1)
+    grad_err = None
+    if rank == 0 and w.name == "grad256" and not args.no_grad_error:
+        (ga, gs), _ = step(3000)
+        ga, gs = ga.double().clone(), gs.double().clone()
+        (ra, rs), _ = step(3001, scale=10)
+        ra, rs = ra.double(), rs.double()
+        ea = float((ga - ra).norm() / ra.norm()) / 1.1 ** 0.5
+        es = float((gs - rs).norm() / rs.norm()) / 1.1 ** 0.5
+        grad_err = {"d_eps_d_mua": ea, "d_eps_d_mus": es,
+                    "how": "relative L2 error vs a 10x-packet evaluation, corrected for its noise"}
+
     # roofline of the dominant kernel (the transport): algorithmic bytes = (2K+1) fixed-point
     # read-modify-writes of 8 B per pixel segment; achieved = bytes / event-timed kernel duration
     C = 2 * w.K + 1
@@ -354,6 +369,7 @@ def _gpu(args):
     if rank == 0:
         cfg = _workload_config(w, n)
         cfg.update({"l2": "flushed between timed steps (256 MB write)", "grad_evals_per_s": value / (n_fwd + n),
+                    "gradient_error_at_this_packet_count": grad_err,
                     "parallelism": f"replicas{world}" if world > 1 else "single"})
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
