@@ -239,7 +239,7 @@ int dn_wgrad_nhwc(dn_slice dz, dn_slice x, int32_t B, int32_t H, int32_t W, int3
   a.m_tiles = (cout + 127) / 128;
   a.n_tiles = (cin + a.N - 1) / a.N;
   const long long kblocks = (long long)B * HW / 64;
-  long long splits = (2 * 152 + taps * a.m_tiles * a.n_tiles - 1) / (taps * a.m_tiles * a.n_tiles);
+  long long splits = (2 * 152) / (taps * a.m_tiles * a.n_tiles);  // one wave of two blocks per SM
   if (splits > kblocks) splits = kblocks;
   if (splits < 1) splits = 1;
   a.splits = (int)splits;

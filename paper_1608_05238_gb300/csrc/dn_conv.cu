@@ -326,19 +326,23 @@ __global__ void __launch_bounds__(128, 1)
 // the image border -- no transposed or shifted copies.  A 128-byte-swizzled MN-major operand of
 // M (or N) = 64 j channels is j boxes 8 KB apart (leading byte offset 8 KB), 8-pixel groups
 // 1 KB apart (stride byte offset), and each K = 16 step advances 16 pixel rows (2 KB).
-constexpr int kWgMnSlack = 32768;  // unused shared memory after the ring
+// Ring depth: 4 stages of 24 KB (N <= 64) or 3 of 32 KB, so that two blocks fit on an SM (an
+// 8-deep ring at one block per SM was 20 % slower on 32 -> 32 channels at 8 x 256^2); the host
+// sizes the split count for one wave of two blocks per SM.
+static int wgrad_mn_stages(int N) { return N <= 64 ? 4 : 3; }
 
 __global__ void __launch_bounds__(128, 1)
-    k_wgrad_mn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const WgradArgs a) {
+    k_wgrad_mn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const WgradArgs a,
+               int stages) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int nb = (a.N + 63) / 64;  // 64-channel B boxes per stage (the MMA uses the first N)
   const uint32_t bTileBytes = (uint32_t)nb * 8192u;
   uint8_t *tileA = smem;
-  uint8_t *tileB = smem + kStages * kATileBytes;
-  uint64_t *full = reinterpret_cast<uint64_t *>(tileB + kStages * bTileBytes);
-  uint64_t *empty = full + kStages;
-  uint64_t *done = empty + kStages;
+  uint8_t *tileB = smem + stages * kATileBytes;
+  uint64_t *full = reinterpret_cast<uint64_t *>(tileB + stages * bTileBytes);
+  uint64_t *empty = full + stages;
+  uint64_t *done = empty + stages;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -346,7 +350,7 @@ __global__ void __launch_bounds__(128, 1)
   const int m_tile = blockIdx.z % a.m_tiles, n_tile = blockIdx.z / a.m_tiles;
   const int ky = a.taps == 9 ? tap / 3 : 1, kx = a.taps == 9 ? tap % 3 : 1;
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -372,7 +376,7 @@ __global__ void __launch_bounds__(128, 1)
 
   if (warp == 0 && lane == 0) {
     for (int i = 0; i < nk; ++i) {
-      const int s = i % kStages, r = i / kStages;
+      const int s = i % stages, r = i / stages;
       if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1)) {
         atomicOr(a.err, 8u);
         break;
@@ -391,7 +395,7 @@ __global__ void __launch_bounds__(128, 1)
   } else if (warp == 1 && lane == 0) {
     const uint32_t idesc = idesc_bf16_f32(kBlockM, (uint32_t)a.N) | (1u << 15) | (1u << 16);  // A, B MN-major
     for (int i = 0; i < nk; ++i) {
-      const int s = i % kStages, r = i / kStages;
+      const int s = i % stages, r = i / stages;
       if (!mbar_wait(&full[s], r & 1)) {
         atomicOr(a.err, 16u);
         break;
@@ -493,7 +497,8 @@ cudaError_t launch_conv_tc(const CUtensorMap &tmX, const CUtensorMap &tmW, const
 }
 
 cudaError_t launch_wgrad_mn(const CUtensorMap &tmA, const CUtensorMap &tmB, const WgradArgs &a, cudaStream_t s) {
-  const size_t smem = 1024 + kStages * (kATileBytes + (size_t)((a.N + 63) / 64) * 8192) + 256 + kWgMnSlack;
+  const int st = wgrad_mn_stages(a.N);
+  const size_t smem = 1024 + st * (kATileBytes + (size_t)((a.N + 63) / 64) * 8192) + 256;
   static size_t configured = 0;
   if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(k_wgrad_mn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -501,7 +506,7 @@ cudaError_t launch_wgrad_mn(const CUtensorMap &tmA, const CUtensorMap &tmB, cons
     configured = smem;
   }
   const dim3 grid((unsigned)a.splits, (unsigned)a.taps, (unsigned)(a.m_tiles * a.n_tiles));
-  k_wgrad_mn<<<grid, 128, smem, s>>>(tmA, tmB, a);
+  k_wgrad_mn<<<grid, 128, smem, s>>>(tmA, tmB, a, st);
   return cudaGetLastError();
 }
 
