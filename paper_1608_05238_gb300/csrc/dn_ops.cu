@@ -110,6 +110,94 @@ __global__ void k_up2_bwd(const __nv_bfloat16 *__restrict__ du, int ustride, int
   dz[pix * zstride + zoff + c] = __float2bfloat16_rn(g);
 }
 
+// 16-byte variants of the four kernels above (8 channels per thread, threadIdx.x over the C/8
+// channel groups of a pixel, threadIdx.y over pixels of the row), used when every channel count,
+// stride and offset is a multiple of 8; a warp then moves whole 128-byte pixel rows.
+union BF8 {
+  uint4 u;
+  __nv_bfloat162 h[4];
+};
+__device__ __forceinline__ uint4 ld8(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint4 *>(p); }
+__device__ __forceinline__ void st8(__nv_bfloat16 *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
+
+__global__ void k_up2_v8(const __nv_bfloat16 *__restrict__ src, int W, int sstride, int soff, int G,
+                         __nv_bfloat16 *__restrict__ dst, int dstride, int doff) {
+  const int g = threadIdx.x, x = blockIdx.x * blockDim.y + threadIdx.y, R = blockIdx.y;
+  if (g >= G || x >= 2 * W) return;
+  st8(dst + ((size_t)R * 2 * W + x) * dstride + doff + 8 * g,
+      ld8(src + ((size_t)(R >> 1) * W + (x >> 1)) * sstride + soff + 8 * g));
+}
+
+__global__ void k_pool2_v8(const __nv_bfloat16 *__restrict__ src, int W, int sstride, int soff, int G,
+                           __nv_bfloat16 *__restrict__ dst, int dstride, int doff) {
+  const int g = threadIdx.x, x = blockIdx.x * blockDim.y + threadIdx.y, R = blockIdx.y;
+  const int Wo = W >> 1;
+  if (g >= G || x >= Wo) return;
+  const size_t s00 = ((size_t)(2 * R) * W + 2 * x) * sstride + soff + 8 * g;
+  BF8 a, b, c, d, o;
+  a.u = ld8(src + s00);
+  b.u = ld8(src + s00 + sstride);
+  c.u = ld8(src + s00 + (size_t)W * sstride);
+  d.u = ld8(src + s00 + (size_t)W * sstride + sstride);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 fa = __bfloat1622float2(a.h[k]), fb = __bfloat1622float2(b.h[k]), fc = __bfloat1622float2(c.h[k]),
+                 fd = __bfloat1622float2(d.h[k]);
+    o.h[k] = __floats2bfloat162_rn(0.25f * (fa.x + fb.x + fc.x + fd.x), 0.25f * (fa.y + fb.y + fc.y + fd.y));
+  }
+  st8(dst + ((size_t)R * Wo + x) * dstride + doff + 8 * g, o.u);
+}
+
+__global__ void k_pool2_bwd_v8(const __nv_bfloat16 *__restrict__ dp, int pstride, int poff,
+                               const __nv_bfloat16 *__restrict__ skip, int kstride, int koff,
+                               const __nv_bfloat16 *__restrict__ act, int astride, int aoff, int W, int G,
+                               __nv_bfloat16 *__restrict__ dz, int zstride, int zoff) {
+  const int g = threadIdx.x, x = blockIdx.x * blockDim.y + threadIdx.y, R = blockIdx.y;
+  if (g >= G || x >= W) return;
+  const size_t pix = (size_t)R * W + x;
+  BF8 p, k, a, o;
+  p.u = ld8(dp + ((size_t)(R >> 1) * (W >> 1) + (x >> 1)) * pstride + poff + 8 * g);
+  a.u = ld8(act + pix * astride + aoff + 8 * g);
+  if (skip) k.u = ld8(skip + pix * kstride + koff + 8 * g);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float2 v = __bfloat1622float2(p.h[j]);
+    v.x *= 0.25f;
+    v.y *= 0.25f;
+    if (skip) {
+      const float2 w = __bfloat1622float2(k.h[j]);
+      v.x += w.x;
+      v.y += w.y;
+    }
+    const float2 m = __bfloat1622float2(a.h[j]);
+    o.h[j] = __floats2bfloat162_rn(m.x > 0.f ? v.x : 0.f, m.y > 0.f ? v.y : 0.f);
+  }
+  st8(dz + pix * zstride + zoff + 8 * g, o.u);
+}
+
+__global__ void k_up2_bwd_v8(const __nv_bfloat16 *__restrict__ du, int ustride, int uoff,
+                             const __nv_bfloat16 *__restrict__ act, int astride, int aoff, int W, int G,
+                             __nv_bfloat16 *__restrict__ dz, int zstride, int zoff) {
+  const int g = threadIdx.x, x = blockIdx.x * blockDim.y + threadIdx.y, R = blockIdx.y;
+  if (g >= G || x >= W) return;
+  const size_t u00 = ((size_t)(2 * R) * 2 * W + 2 * x) * ustride + uoff + 8 * g;
+  BF8 a, b, c, d, m, o;
+  a.u = ld8(du + u00);
+  b.u = ld8(du + u00 + ustride);
+  c.u = ld8(du + u00 + (size_t)2 * W * ustride);
+  d.u = ld8(du + u00 + (size_t)2 * W * ustride + ustride);
+  const size_t pix = (size_t)R * W + x;
+  m.u = ld8(act + pix * astride + aoff + 8 * g);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 fa = __bfloat1622float2(a.h[k]), fb = __bfloat1622float2(b.h[k]), fc = __bfloat1622float2(c.h[k]),
+                 fd = __bfloat1622float2(d.h[k]), fm = __bfloat1622float2(m.h[k]);
+    o.h[k] = __floats2bfloat162_rn(fm.x > 0.f ? fa.x + fb.x + fc.x + fd.x : 0.f,
+                                   fm.y > 0.f ? fa.y + fb.y + fc.y + fd.y : 0.f);
+  }
+  st8(dz + pix * zstride + zoff + 8 * g, o.u);
+}
+
 // db[c] += sum over pixels of dz[p][c]
 __global__ void k_bias_grad(const __nv_bfloat16 *__restrict__ dz, long long P, int stride, int off, int C,
                             float *__restrict__ db) {
@@ -305,10 +393,22 @@ cudaError_t to_ct(const __nv_bfloat16 *src, int B, int HW, int W, int stride, in
 }
 static dim3 pix_grid(int cols, int rows, int C) { return dim3((cols + 7) / 8, rows, (C + 31) / 32); }
 static bool pix_grid_ok(int rows, int C) { return rows >= 1 && rows <= 65535 && (C + 31) / 32 <= 65535; }
+static bool al8(int a, int b, int c, int d) { return a % 8 == 0 && b % 8 == 0 && c % 8 == 0 && d % 8 == 0; }
+// block and grid of the 16-byte kernels: C/8 channel groups x enough pixels for ~256 threads
+static dim3 v8_block(int G) {
+  int py = 256 / G;
+  return dim3(G, py < 1 ? 1 : (py > 64 ? 64 : py));
+}
+static dim3 v8_grid(int cols, int rows, dim3 blk) { return dim3((cols + blk.y - 1) / blk.y, rows); }
 
 cudaError_t pool2(const __nv_bfloat16 *src, int B, int H, int W, int sstride, int soff, int C, __nv_bfloat16 *dst,
                   int dstride, int doff, cudaStream_t s) {
   if (!pix_grid_ok(B * (H / 2), C)) return cudaErrorInvalidConfiguration;
+  if (al8(C, sstride, soff, dstride) && doff % 8 == 0 && C / 8 <= 256) {
+    const dim3 blk = v8_block(C / 8);
+    k_pool2_v8<<<v8_grid(W / 2, B * (H / 2), blk), blk, 0, s>>>(src, W, sstride, soff, C / 8, dst, dstride, doff);
+    return cudaGetLastError();
+  }
   k_pool2<<<pix_grid(W / 2, B * (H / 2), C), dim3(32, 8), 0, s>>>(src, W, sstride, soff, C, dst, dstride, doff);
   return cudaGetLastError();
 }
@@ -316,6 +416,13 @@ cudaError_t pool2_bwd(const __nv_bfloat16 *dp, int pstride, int poff, const __nv
                       const __nv_bfloat16 *act, int astride, int aoff, int B, int H, int W, int C, __nv_bfloat16 *dz,
                       int zstride, int zoff, cudaStream_t s) {
   if (!pix_grid_ok(B * H, C)) return cudaErrorInvalidConfiguration;
+  if (al8(C, pstride, poff, astride) && al8(aoff, zstride, zoff, 0) && (!skip || al8(kstride, koff, 0, 0)) &&
+      C / 8 <= 256) {
+    const dim3 blk = v8_block(C / 8);
+    k_pool2_bwd_v8<<<v8_grid(W, B * H, blk), blk, 0, s>>>(dp, pstride, poff, skip, kstride, koff, act, astride, aoff,
+                                                          W, C / 8, dz, zstride, zoff);
+    return cudaGetLastError();
+  }
   k_pool2_bwd<<<pix_grid(W, B * H, C), dim3(32, 8), 0, s>>>(dp, pstride, poff, skip, kstride, koff, act, astride, aoff,
                                                              W, C, dz, zstride, zoff);
   return cudaGetLastError();
@@ -323,12 +430,23 @@ cudaError_t pool2_bwd(const __nv_bfloat16 *dp, int pstride, int poff, const __nv
 cudaError_t up2(const __nv_bfloat16 *src, int B, int H, int W, int sstride, int soff, int C, __nv_bfloat16 *dst,
                 int dstride, int doff, cudaStream_t s) {
   if (!pix_grid_ok(B * 2 * H, C)) return cudaErrorInvalidConfiguration;
+  if (al8(C, sstride, soff, dstride) && doff % 8 == 0 && C / 8 <= 256) {
+    const dim3 blk = v8_block(C / 8);
+    k_up2_v8<<<v8_grid(2 * W, B * 2 * H, blk), blk, 0, s>>>(src, W, sstride, soff, C / 8, dst, dstride, doff);
+    return cudaGetLastError();
+  }
   k_up2<<<pix_grid(2 * W, B * 2 * H, C), dim3(32, 8), 0, s>>>(src, W, sstride, soff, C, dst, dstride, doff);
   return cudaGetLastError();
 }
 cudaError_t up2_bwd(const __nv_bfloat16 *du, int ustride, int uoff, const __nv_bfloat16 *act, int astride, int aoff,
                     int B, int H, int W, int C, __nv_bfloat16 *dz, int zstride, int zoff, cudaStream_t s) {
   if (!pix_grid_ok(B * H, C)) return cudaErrorInvalidConfiguration;
+  if (al8(C, ustride, uoff, astride) && al8(aoff, zstride, zoff, 0) && C / 8 <= 256) {
+    const dim3 blk = v8_block(C / 8);
+    k_up2_bwd_v8<<<v8_grid(W, B * H, blk), blk, 0, s>>>(du, ustride, uoff, act, astride, aoff, W, C / 8, dz, zstride,
+                                                        zoff);
+    return cudaGetLastError();
+  }
   k_up2_bwd<<<pix_grid(W, B * H, C), dim3(32, 8), 0, s>>>(du, ustride, uoff, act, astride, aoff, W, C, dz, zstride,
                                                            zoff);
   return cudaGetLastError();

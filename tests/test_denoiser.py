@@ -68,10 +68,11 @@ def test_wgrad_nhwc_matches_autograd(B, H, W, cin, cout, taps, xoff, zoff):
     assert torch.allclose(got, ref_dw, rtol=1e-4, atol=1e-4 * ref_dw.abs().max().item())
 
 
-def test_layout_pool_upsample_and_backward_kernels():
-    B, H, W, C = 2, 16, 32, 40
-    x = _nhwc(B, H, W, C, 128, 3)
-    src = Act(x, C, 64 - 40 + 24)  # slice at offset 48
+@pytest.mark.parametrize("C", [40, 33])  # 16-byte vector path (C, strides, offsets multiples of 8) / scalar path
+def test_layout_pool_upsample_and_backward_kernels(C):
+    B, H, W = 2, 16, 32
+    x = _nhwc(B, H, W, C + 48, 128, 3)
+    src = Act(x, C, 48)  # a slice at channel offset 48 of rows of 128
     t = ops.to_ct(src, True)
     xs = x.float().cpu()[..., 48:48 + C]
     ct = xs.permute(3, 0, 1, 2).reshape(C, B, H * W)
