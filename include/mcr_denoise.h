@@ -120,6 +120,11 @@ int dn_pack_input(const float *src, const float *scale, int32_t B, int64_t HW, i
                   void *stream);
 int dn_pack_target(const float *src, const float *scale, int32_t B, int64_t HW, int32_t C, float *dst, void *stream);
 int dn_unpack_output(const float *src, const float *scale, int32_t B, int64_t HW, int32_t C, float *dst, void *stream);
+/* The prediction in one pass: dst channel-major fp32 [B][C][HW] = (x + out) / scale[b], with out
+ * fp32 NHWC [B*HW][ostride] (the network's output) and x bf16 NHWC [B*HW][xstride] (its scaled
+ * input); = dn_residual followed by dn_unpack_output without the intermediate buffer. */
+int dn_predict_output(const float *out, int32_t ostride, const void *x, int32_t xstride, const float *scale,
+                      int32_t B, int64_t HW, int32_t C, float *dst, void *stream);
 
 /* Device error word of the denoiser kernels (a bounded wait that gave up); read and clear.
  * Synchronises `stream`. */

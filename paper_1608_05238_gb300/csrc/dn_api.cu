@@ -341,6 +341,13 @@ int dn_pack_target(const float *src, const float *scale, int32_t B, int64_t HW, 
   DN_TRY(pack_target(src, scale, B, HW, C, dst, (cudaStream_t)stream));
 }
 
+int dn_predict_output(const float *out, int32_t ostride, const void *x, int32_t xstride, const float *scale,
+                      int32_t B, int64_t HW, int32_t C, float *dst, void *stream) {
+  if (!out || !x || !scale || !dst || B <= 0 || HW <= 0 || C <= 0 || ostride < C || xstride < C) return MCR_ERR_ARG;
+  DN_TRY(predict_output(out, ostride, static_cast<const __nv_bfloat16 *>(x), xstride, scale, B, HW, C, dst,
+                        (cudaStream_t)stream));
+}
+
 int dn_unpack_output(const float *src, const float *scale, int32_t B, int64_t HW, int32_t C, float *dst,
                      void *stream) {
   if (!src || !scale || !dst || B <= 0 || HW <= 0 || C <= 0) return MCR_ERR_ARG;

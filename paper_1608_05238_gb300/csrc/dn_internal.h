@@ -69,6 +69,8 @@ cudaError_t pack_input(const float *src, const float *scale, int B, long long HW
                        cudaStream_t s);
 cudaError_t sample_scale(const float *src, int B, long long HW, int C, float *scale, cudaStream_t s);
 cudaError_t pack_target(const float *src, const float *scale, int B, long long HW, int C, float *dst, cudaStream_t s);
+cudaError_t predict_output(const float *out, int ostride, const __nv_bfloat16 *x, int xstride, const float *scale,
+                           int B, long long HW, int C, float *dst, cudaStream_t s);
 cudaError_t unpack_output(const float *src, const float *scale, int B, long long HW, int C, float *dst,
                           cudaStream_t s);
 

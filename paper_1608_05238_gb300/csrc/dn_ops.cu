@@ -366,6 +366,29 @@ __global__ void k_pack_target(const float *__restrict__ src, const float *__rest
   }
 }
 
+// prediction straight to channel-major maps: dst[b][c][p] = (x[b,p][c] + out[b,p][c]) / scale[b]
+// (the residual output and the un-scaling in one pass through a 32 x 32 tile)
+__global__ void k_predict_output(const float *__restrict__ out, int ostride, const __nv_bfloat16 *__restrict__ x,
+                                 int xstride, const float *__restrict__ scale, int HW, int C, float *__restrict__ dst) {
+  __shared__ float tile[32][33];
+  const int p0 = blockIdx.x * 32, c0 = blockIdx.y * 32, b = blockIdx.z;
+  const float inv = 1.f / scale[b];
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int p = p0 + r, c = c0 + threadIdx.x;
+    float v = 0.f;
+    if (p < HW && c < C) {
+      const size_t q = (size_t)b * HW + p;
+      v = (bf(x[q * xstride + c]) + out[q * ostride + c]) * inv;
+    }
+    tile[r][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int c = c0 + r, p = p0 + threadIdx.x;
+    if (c < C && p < HW) dst[((size_t)b * C + c) * HW + p] = tile[threadIdx.x][r];
+  }
+}
+
 // NHWC fp32 [B][HW][C] / scale[b] -> channel-major fp32 [B][C][HW]
 __global__ void k_unpack_output(const float *__restrict__ src, const float *__restrict__ scale, int HW, int C,
                                 float *__restrict__ dst) {
@@ -506,6 +529,13 @@ cudaError_t sample_scale(const float *src, int B, long long HW, int C, float *sc
 cudaError_t pack_target(const float *src, const float *scale, int B, long long HW, int C, float *dst, cudaStream_t s) {
   if (HW > 0x7fffffffll - 31 || B > 65535) return cudaErrorInvalidValue;
   k_pack_target<<<dim3((unsigned)((HW + 31) / 32), (C + 31) / 32, B), dim3(32, 8), 0, s>>>(src, scale, (int)HW, C, dst);
+  return cudaGetLastError();
+}
+cudaError_t predict_output(const float *out, int ostride, const __nv_bfloat16 *x, int xstride, const float *scale,
+                           int B, long long HW, int C, float *dst, cudaStream_t s) {
+  if (HW > 0x7fffffffll - 31 || B > 65535) return cudaErrorInvalidValue;
+  k_predict_output<<<dim3((unsigned)((HW + 31) / 32), (C + 31) / 32, B), dim3(32, 8), 0, s>>>(out, ostride, x, xstride,
+                                                                                             scale, (int)HW, C, dst);
   return cudaGetLastError();
 }
 cudaError_t unpack_output(const float *src, const float *scale, int B, long long HW, int C, float *dst,

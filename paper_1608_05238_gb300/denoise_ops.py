@@ -27,7 +27,7 @@ class _Slice(C.Structure):
 
 
 EXPORTS = ("dn_conv", "dn_wgrad", "dn_wgrad_nhwc", "dn_to_ct", "dn_pool2", "dn_pool2_bwd", "dn_up2", "dn_up2_bwd", "dn_bias_grad",
-           "dn_mse", "dn_residual", "dn_adam", "dn_adam_bias", "dn_pack_input", "dn_sample_scale", "dn_pack_target",
+           "dn_mse", "dn_residual", "dn_adam", "dn_adam_bias", "dn_pack_input", "dn_sample_scale", "dn_pack_target", "dn_predict_output",
            "dn_unpack_output", "dn_check")
 
 
@@ -55,6 +55,7 @@ def lib():
             "dn_sample_scale": [vp, i32, i64, i32, vp, vp],
             "dn_pack_target": [vp, vp, i32, i64, i32, vp, vp],
             "dn_unpack_output": [vp, vp, i32, i64, i32, vp, vp],
+            "dn_predict_output": [vp, i32, vp, i32, vp, i32, i64, i32, vp, vp],
             "dn_check": [vp],
         }
         for name, args in sig.items():
@@ -170,6 +171,13 @@ def pack_input(src: torch.Tensor, scale: torch.Tensor, dst: torch.Tensor, stream
 def sample_scale(src: torch.Tensor, scale: torch.Tensor, stream=None):
     """scale[b] = 1 / mean of channel 0 of the channel-major fp32 maps src [B][C][H][W]."""
     _call("dn_sample_scale", _p(src), src.shape[0], src.shape[2] * src.shape[3], src.shape[1], _p(scale),
+          _stream(stream))
+
+
+def predict_output(out: torch.Tensor, x: torch.Tensor, C: int, scale: torch.Tensor, dst: torch.Tensor, stream=None):
+    """dst [B][C][H][W] = (x[..., :C] + out[..., :C]) / scale[b] from the NHWC network output and input."""
+    B, H, W = x.shape[:3]
+    _call("dn_predict_output", _p(out), out.shape[3], _p(x), x.shape[3], _p(scale), B, H * W, C, _p(dst),
           _stream(stream))
 
 

@@ -270,10 +270,7 @@ class UNet:
         """Denoised channel-major maps [B][in_ch][H][W] (unscaled)."""
         self.load(x, scale)
         out = self.forward()
-        B, H, W = self._shape
-        y = torch.empty(B, H, W, self.in_ch, device=self.device)
-        ops.residual(out, self.a["x0"], self.in_ch, y)
-        ops.unpack_output(y, scale, self.pred)
+        ops.predict_output(out, self.a["x0"], self.in_ch, scale, self.pred)
         return self.pred
 
     # ------------------------------------------------------------------ state

@@ -118,6 +118,21 @@ def test_sample_scale_is_inverse_mean_fluence():
     assert torch.allclose(got, (1.0 / m).float().double(), rtol=1e-6, atol=0)
 
 
+def test_predict_output_is_residual_then_unpack():
+    B, H, W, C = 2, 16, 32, 33
+    g = torch.Generator().manual_seed(9)
+    x = _nhwc(B, H, W, C, 64, 21)
+    out = torch.randn(B, H, W, 40, generator=g).cuda()
+    scale = (torch.rand(B, generator=g) + 0.5).cuda()
+    y = torch.empty(B, H, W, C, device="cuda")
+    ops.residual(out, x, C, y)
+    ref = torch.empty(B, C, H, W, device="cuda")
+    ops.unpack_output(y, scale, ref)
+    got = torch.empty(B, C, H, W, device="cuda")
+    ops.predict_output(out, x, C, scale, got)
+    assert torch.allclose(got, ref, rtol=2e-7, atol=0)
+
+
 def _data(B, H, W, C, seed):
     g = torch.Generator().manual_seed(seed)
     base = torch.rand(B, 1, H, W, generator=g) + 0.5
