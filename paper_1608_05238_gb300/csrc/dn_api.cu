@@ -137,6 +137,18 @@ int dn_conv(const dn_conv_desc *d, void *stream) {
   a.out_stride = d->out_stride;
   a.out_off = d->out_off;
   a.err = err;
+  if (conv_halo_applies(a)) {  // few output channels: one haloed input box per channel block
+    CUtensorMap tmH;
+    const uint64_t dims[4] = {(uint64_t)d->cin_pad, (uint64_t)d->W, (uint64_t)d->H, (uint64_t)d->B};
+    const uint64_t strides[3] = {(uint64_t)d->cin_pad * 2, (uint64_t)d->W * d->cin_pad * 2,
+                                 (uint64_t)d->H * d->W * d->cin_pad * 2};
+    const uint32_t box[4] = {64, 130, 3, 1};
+    if (encode_tiled(&tmH, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(d->x), dims, strides, box,
+                     CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+      return MCR_ERR_CUDA;
+    if (launch_conv_halo(tmH, tmW, a, (cudaStream_t)stream) != cudaSuccess) return MCR_ERR_CUDA;
+    return MCR_OK;
+  }
   if (launch_conv_tc(tmX, tmW, a, (cudaStream_t)stream) != cudaSuccess) return MCR_ERR_CUDA;
   return MCR_OK;
 }

@@ -213,6 +213,179 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   if (warp == 0) tmem_dealloc(tmem, 2 * acc_cols);
 }
 
+// Epilogue of one output pixel p (this thread's TMEM lane, row address trow): N accumulator
+// columns through bias / ReLU / the next layer's ReLU mask into the bf16 or fp32 output slice.
+__device__ __forceinline__ void drain_row(const ConvArgs &a, long long p, uint32_t trow) {
+  for (int c0 = 0; c0 < a.N; c0 += 16) {
+    uint32_t v[16];
+    tmem_ld16(trow + (uint32_t)c0, v);
+    tmem_ld_wait();
+    float f[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int n = c0 + j;
+      float x = __uint_as_float(v[j]);
+      if (a.bias && n < a.cout) x += a.bias[n];
+      if (a.relu) x = fmaxf(x, 0.f);
+      if (a.mask && n < a.cout) {
+        const float m = __bfloat162float(a.mask[p * a.mask_stride + a.mask_off + n]);
+        x = m > 0.f ? x : 0.f;
+      }
+      f[j] = x;
+    }
+    if (a.out_f32) {
+      float *o = a.out_f32 + p * a.out_stride + a.out_off + c0;
+      if (c0 + 16 <= a.cout) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4 *>(o + j) = make_float4(f[j], f[j + 1], f[j + 2], f[j + 3]);
+      } else {
+        for (int j = 0; j < 16 && c0 + j < a.cout; ++j) o[j] = f[j];
+      }
+    } else {
+      __nv_bfloat16 *o = a.out_bf16 + p * a.out_stride + a.out_off + c0;
+      if (c0 + 16 <= a.cout) {
+        __align__(16) __nv_bfloat162 h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+        *reinterpret_cast<uint4 *>(o) = *reinterpret_cast<const uint4 *>(&h[0]);
+        *reinterpret_cast<uint4 *>(o + 8) = *reinterpret_cast<const uint4 *>(&h[4]);
+      } else {
+        for (int j = 0; j < 16 && c0 + j < a.cout; ++j) o[j] = __float2bfloat16_rn(f[j]);
+      }
+    }
+  }
+}
+
+// k_conv_halo: 3x3 convolution with few output channels (N <= 32) whose 128-pixel tiles lie in
+// one image row (W a multiple of 128).  A stage holds, for one 64-channel block, the haloed input
+// -- rows y-1..y+1 x columns x0-1..x0+128, one 4D TMA box {64, 130, 3, 1} with zero fill -- and
+// the weights of all nine taps; the nine taps read the haloed tile at row offsets ky 130 + kx (the
+// descriptor starts at that row, base-offset field 0: the 128-byte swizzle follows the address
+// bits of the 1024-byte-aligned tile).  Per stage that is 36 MMAs for one barrier round trip and
+// ~1.9x fewer L2 -> SM bytes per FLOP than one input box per tap, which is what bounds these
+// convolutions.  Same warp roles and double TMEM accumulator as k_conv_ws.
+constexpr uint32_t kHaloBytes = 3 * 130 * 128;  // 49,920 B written by the input box
+constexpr uint32_t kHaloStride = (kHaloBytes + 1023) & ~1023u;
+
+__global__ void __launch_bounds__(kWsThreads, 1)
+    k_conv_halo(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmW, const ConvArgs a,
+                int stages, int num_tiles) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t bTileBytes = (uint32_t)a.N * kBlockK * 2;
+  const uint32_t stageBytes = kHaloStride + 9 * bTileBytes;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stageBytes);
+  uint64_t *empty = full + stages;
+  uint64_t *tfull = empty + stages;
+  uint64_t *tempty = tfull + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+  const uint32_t acc_cols = a.tmem_cols;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int i = 0; i < stages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 128);
+    }
+    fence_barrier_init();
+    prefetch_tensormap(&tmH);
+    prefetch_tensormap(&tmW);
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, 2 * acc_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int hw = a.H * a.W;
+  const int cblocks = a.cin_pad / kBlockK;
+
+  if (warp == 0 && lane == 0) {
+    uint32_t kc = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+      const long long p0 = (long long)tile * kBlockM;
+      const int b0 = (int)(p0 / hw), rem = (int)(p0 % hw);
+      const int y0 = rem / a.W, x0 = rem % a.W;
+      for (int cb = 0; cb < cblocks; ++cb, ++kc) {
+        const int st = kc % stages;
+        const uint32_t r = kc / stages;
+        if (r > 0 && !mbar_wait(&empty[st], (r - 1) & 1)) {
+          atomicOr(a.err, 1024u);
+          ok = false;
+          break;
+        }
+        uint8_t *base = smem + (size_t)st * stageBytes;
+        mbar_arrive_expect_tx(&full[st], kHaloBytes + 9 * bTileBytes);
+        tma_load_4d(base, &tmH, &full[st], cb * kBlockK, x0 - 1, y0 - 1, b0);
+        for (int tap = 0; tap < 9; ++tap)
+          tma_load_2d(base + kHaloStride + tap * bTileBytes, &tmW, &full[st], tap * a.cin_pad + cb * kBlockK, 0);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_bf16_f32(kBlockM, (uint32_t)a.N);
+    uint32_t kc = 0;
+    int it = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++it) {
+      const int b = it & 1;
+      const uint32_t use = it >> 1;
+      if (use > 0 && !mbar_wait(&tempty[b], (use - 1) & 1)) {
+        atomicOr(a.err, 2048u);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tmem + b * acc_cols;
+      for (int cb = 0; cb < cblocks; ++cb, ++kc) {
+        const int st = kc % stages;
+        if (!mbar_wait(&full[st], (kc / stages) & 1)) {
+          atomicOr(a.err, 2048u);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t aBase = smem_u32(smem + (size_t)st * stageBytes), bBase = aBase + kHaloStride;
+        for (int tap = 0; tap < 9; ++tap) {
+          const uint32_t arow = aBase + (uint32_t)((tap / 3) * 130 + tap % 3) * 128u;
+#pragma unroll
+          for (int kk = 0; kk < kBlockK / 16; ++kk)
+            mma_bf16(d, sdesc_k128(arow + kk * 32), sdesc_k128(bBase + tap * bTileBytes + kk * 32), idesc,
+                     (cb > 0 || tap > 0 || kk > 0) ? 1u : 0u);
+        }
+        mma_commit(&empty[st]);
+      }
+      mma_commit(&tfull[b]);
+    }
+  } else if (warp >= 2) {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
+      const int b = it & 1;
+      const uint32_t use = it >> 1;
+      const bool have = __all_sync(0xffffffffu, mbar_wait(&tfull[b], use & 1));
+      if (!have) {
+        if (lane == 0) atomicOr(a.err, 4096u);
+        break;
+      }
+      tc_fence_after();
+      drain_row(a, (long long)tile * kBlockM + row, tmem + ((uint32_t)(q * 32) << 16) + b * acc_cols);
+      tc_fence_before();
+      mbar_arrive(&tempty[b]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 2 * acc_cols);
+}
+
 // k_wgrad_tc: weight gradient dW[n][tap][c] += sum_p dZ[p][n] X[p + tap][c] as a GEMM over pixels
 // with M = 128 output channels, N = `N` input channels, K = 64-pixel blocks.  Operands are
 // K-major (pixels contiguous): dZ^T [cout][B][HW] and three x-shifted copies
@@ -507,6 +680,34 @@ cudaError_t launch_wgrad_mn(const CUtensorMap &tmA, const CUtensorMap &tmB, cons
   }
   const dim3 grid((unsigned)a.splits, (unsigned)a.taps, (unsigned)(a.m_tiles * a.n_tiles));
   k_wgrad_mn<<<grid, 128, smem, s>>>(tmA, tmB, a, st);
+  return cudaGetLastError();
+}
+
+static int halo_stages(int N) {
+  const size_t stage = kHaloStride + 9 * (size_t)N * kBlockK * 2;
+  const int st = (int)((200u * 1024u) / stage);
+  return st > 4 ? 4 : st;
+}
+
+bool conv_halo_applies(const ConvArgs &a) {
+  return a.taps == 9 && a.W % kBlockM == 0 && a.N <= 32 && halo_stages(a.N) >= 2;
+}
+
+cudaError_t launch_conv_halo(const CUtensorMap &tmH, const CUtensorMap &tmW, ConvArgs a, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  uint32_t cols = 32;
+  while (cols < (uint32_t)a.N) cols <<= 1;
+  a.tmem_cols = cols;
+  const int st = halo_stages(a.N);
+  const size_t smem = 1024 + (size_t)st * (kHaloStride + 9 * (size_t)a.N * kBlockK * 2) + 512;
+  const long long tiles = (long long)a.B * a.H * a.W / kBlockM;
+  const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
+  k_conv_halo<<<grid, kWsThreads, smem, s>>>(tmH, tmW, a, st, (int)tiles);
   return cudaGetLastError();
 }
 

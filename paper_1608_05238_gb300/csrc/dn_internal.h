@@ -27,6 +27,10 @@ struct ConvArgs {
 };
 
 cudaError_t launch_conv_tc(const CUtensorMap &tmX, const CUtensorMap &tmW, const ConvArgs &a, cudaStream_t s);
+// 3x3 convolution with N <= 32 on rows of whole 128-pixel tiles: one haloed input box {64, 130, 3, 1}
+// and all nine taps' weights per channel block
+bool conv_halo_applies(const ConvArgs &a);
+cudaError_t launch_conv_halo(const CUtensorMap &tmH, const CUtensorMap &tmW, ConvArgs a, cudaStream_t s);
 
 // Weight-gradient GEMM launch arguments (see k_wgrad_tc).
 struct WgradArgs {

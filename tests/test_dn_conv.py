@@ -98,6 +98,25 @@ def test_wide_row_conv_bias_relu_slice_and_mask():
     assert torch.allclose(out2.double().cpu(), ref2, rtol=1e-4, atol=1e-4 * ref2.abs().max().item())
 
 
+def test_haloed_conv_epilogue_options():
+    """Few output channels (N <= 32) on rows of 256 pixels take the haloed kernel: bias, ReLU,
+    bf16 slice output and the ReLU-mask path against the reference."""
+    B, H, W, cin, cout = 2, 6, 256, 72, 30
+    x, w, cin_pad, n_pad = _case(B, H, W, cin, cout, 9, seed=19)
+    bias = torch.randn(cout).cuda()
+    out = torch.zeros(B, H, W, 128, dtype=torch.bfloat16, device="cuda")
+    ops.conv(x, w, cout, out, bias=bias, relu=True, out_off=64)
+    ref = _ref(x, w, cin, cout, 9, bias=bias, relu=True)
+    assert torch.allclose(out[..., 64:64 + cout].double().cpu(), ref, rtol=2 ** -7, atol=1e-3)
+    assert torch.count_nonzero(out[..., :64]) == 0 and torch.count_nonzero(out[..., 64 + cout:]) == 0
+    mask = torch.randn(B, H, W, 64).bfloat16().cuda()
+    out2 = torch.zeros(B, H, W, 32, device="cuda")
+    ops.conv(x, w, cout, out2, mask=mask, mask_off=16)
+    ops.check()
+    ref2 = _ref(x, w, cin, cout, 9, mask=mask, mask_off=16)
+    assert torch.allclose(out2[..., :cout].double().cpu(), ref2, rtol=1e-4, atol=1e-4 * ref2.abs().max().item())
+
+
 def test_conv_rejects_bad_shapes():
     x, w, _, _ = _case(1, 4, 32, 64, 16, 9, seed=1)
     out = torch.zeros(1, 4, 32, 16, device="cuda")
