@@ -52,11 +52,12 @@ def _args():
     ap.add_argument("--no-grad-error", action="store_true", help="skip the gradient-error measurement")
     ap.add_argument("--plain-gd", action="store_true", help="invert256: no fluence preconditioning")
     ap.add_argument("--workload", default="grad256",
-                    choices=["grad256", "large1024", "batch64", "denoise256", "conv", "invert256"],
+                    choices=["grad256", "large1024", "batch64", "denoise256", "conv", "invert256", "unet256"],
                     help="grad256: the gradient evaluation (default); large1024: the same on 1024^2 px at "
                          "K = 64 with four edge sources; batch64: 64 forward problems in one graph-captured "
                          "batched launch; denoise256: the learned denoiser; conv: one large tensor-core "
-                         "convolution (profiling case); invert256: mu_a reconstruction on the grad256 phantom")
+                         "convolution (profiling case); invert256: mu_a reconstruction on the grad256 phantom; "
+                         "unet256: U-Net training step and inference on synthetic maps (profiling case)")
     args = ap.parse_args()
     if args.packets is None:
         args.packets = 20_000_000 if args.workload == "large1024" else 10_000_000
@@ -577,6 +578,50 @@ def _conv_only(args):
     return 0
 
 
+def _unet256(args):
+    """U-Net training step and inference on 8 synthetic 33-channel 256x256 maps (no MC pairs): the
+    tensor-core convolutions, weight gradients and memory-bound layers of the denoiser alone
+    (profiling case for its launch list)."""
+    import torch
+    from paper_1608_05238_gb300 import _build, denoise_ops as ops
+    from paper_1608_05238_gb300.denoiser import UNet, sample_scale
+    _build.build()
+    B, C, H, W = 8, 33, 256, 256
+    g = torch.Generator().manual_seed(0)
+    x = (torch.rand(B, C, H, W, generator=g) + 0.5).cuda()
+    t = (0.9 * x + 0.05).contiguous()
+    net = UNet(in_ch=C, seed=0)
+    sc = sample_scale(x)
+    for _ in range(args.warmup):
+        net.train_step(x, sc, t, 1e-4)
+        net.predict(x, sc)
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    (a, b), (c, d) = ev(), ev()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(args.steps):
+        net.train_step(x, sc, t, 1e-4)
+    b.record()
+    c.record()
+    for _ in range(args.steps):
+        net.predict(x, sc)
+    d.record()
+    d.synchronize()
+    ops.check()
+    train_ms, infer_ms = a.elapsed_time(b) / args.steps, c.elapsed_time(d) / args.steps
+    alg, exe = _unet_flops(net, B, H, W)
+    print(json.dumps({"metric": "U-Net training samples/s", "value": B / train_ms * 1e3, "unit": "samples/s",
+                      "ms_per_step": train_ms, "steps": args.steps, "warmup": args.warmup,
+                      "higher_is_better": True, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+                      "config": {"workload": "unet256: U-Net 32-256 ch, batch 8 of 33-channel 256^2 maps",
+                                 "infer_ms": infer_ms, "infer_maps_per_s": B / infer_ms * 1e3,
+                                 "train_tflops_executed": 3 * exe / train_ms / 1e9,
+                                 "infer_tflops_executed": exe / infer_ms / 1e9,
+                                 "unet_forward_gflop_alg": alg / B / 1e9, "unet_forward_gflop_executed": exe / B / 1e9}}),
+          flush=True)
+    return 0
+
+
 def _invert256(args):
     """mu_a reconstruction (Sec. 6.1: mu_s known) on the 256x256 inclusion phantom from a
     homogeneous start: (fluence-preconditioned, unless --plain-gd) gradient descent with the
@@ -643,6 +688,8 @@ def main():
         return _denoise256(args)
     if args.workload == "conv" and args.impl != "reference":
         return _conv_only(args)
+    if args.workload == "unet256" and args.impl != "reference":
+        return _unet256(args)
     if args.impl == "reference":
         return _reference(args)
     return _gpu(args)

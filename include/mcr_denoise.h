@@ -50,6 +50,34 @@ typedef struct {
  */
 int dn_conv(const dn_conv_desc *d, void *stream);
 
+/* Fused output head of the denoiser (its residual output; Sec. 3.1 defines the maps it predicts). */
+enum { DN_HEAD_PREDICT = 1, DN_HEAD_LOSS = 2 };
+typedef struct {
+  int32_t mode;             /* DN_HEAD_PREDICT or DN_HEAD_LOSS */
+  const void *res;          /* x0: bf16 NHWC [B][H][W][res_stride], channels [0, cout); stride multiple of 8,
+                               16-byte aligned */
+  int32_t res_stride;
+  const float *scale;       /* fp32 [B] per-sample input scale */
+  float *pred;              /* DN_HEAD_PREDICT: fp32 [B][cout][H][W] */
+  const float *target;      /* DN_HEAD_LOSS: fp32 [B][cout][H][W], unscaled */
+  void *dout;               /* DN_HEAD_LOSS: bf16 NHWC, channel stride dout_stride (multiple of 8), 16-byte aligned */
+  int32_t dout_stride;
+  double *loss;             /* DN_HEAD_LOSS: device FP64 scalar */
+} dn_head_desc;
+
+/*
+ * dn_conv_head -- the 1x1 output convolution d (taps 1, bias allowed; relu, mask and out are not
+ * used) with the residual head in its epilogue, so that no NHWC fp32 output is written or re-read:
+ *   y = x0 + conv(x, w) + bias  (per pixel, channels < cout)
+ *   DN_HEAD_PREDICT: pred[b][c][p] = y / scale[b]              (channel-major maps)
+ *   DN_HEAD_LOSS:    r = y - scale[b] target[b][c][p];  dout = bf16(2 r / (B H W cout));
+ *                    loss = sum r^2 / (B H W cout), FP64, from per-warp partial sums in a fixed order
+ * Bit-identical to dn_conv + dn_predict_output (prediction) and, for dout, to dn_conv + dn_pack_target
+ * + dn_mse (loss; the loss itself differs only in the order of its FP64 sum).  Uses the library's
+ * reduction scratch: calls on one device must not overlap.  MCR_ERR_ARG on a bad shape or pointer.
+ */
+int dn_conv_head(const dn_conv_desc *d, const dn_head_desc *h, void *stream);
+
 /*
  * dn_wgrad -- weight gradient of a convolution on the tensor cores:
  *   dw[n][tap][c] += sum_{b, pixel} dz[b, pixel][n] x[b, pixel + tap][c]     (FP32 accumulate)

@@ -14,6 +14,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+constexpr int kPartialsCap = 4096;  // doubles in the per-device scratch of the loss reductions
+
 std::mutex g_mu;
 EncodeTiledFn g_encode = nullptr;
 unsigned *g_err[64];  // device error word per device
@@ -64,7 +66,7 @@ double *partials_buffer() {
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_partials[dev]) {
     void *p = nullptr;
-    if (cudaMalloc(&p, 4096 * sizeof(double)) != cudaSuccess) return nullptr;
+    if (cudaMalloc(&p, kPartialsCap * sizeof(double)) != cudaSuccess) return nullptr;
     g_partials[dev] = static_cast<double *>(p);
   }
   return g_partials[dev];
@@ -82,20 +84,21 @@ using namespace dn;
 
 extern "C" {
 
-int dn_conv(const dn_conv_desc *d, void *stream) {
-  if (!d || !d->x || !d->w || !d->out) return MCR_ERR_ARG;
+}  // extern "C"
+
+// Shape checks, tensor maps and epilogue arguments shared by dn_conv and dn_conv_head.
+static int conv_setup(const dn_conv_desc *d, CUtensorMap &tmX, CUtensorMap &tmW, ConvArgs &a) {
+  if (!d->x || !d->w) return MCR_ERR_ARG;
   if (!conv_shape_ok(d->B, d->H, d->W)) return MCR_ERR_ARG;
   if (d->cin_pad < 64 || d->cin_pad % 64) return MCR_ERR_ARG;
   if (d->taps != 9 && d->taps != 1) return MCR_ERR_ARG;
   if (d->n_pad < 16 || d->n_pad > 256 || d->n_pad % 16 || d->cout < 1 || d->cout > d->n_pad) return MCR_ERR_ARG;
-  if (d->out_stride % 8 || d->out_off % 8 || d->out_off + d->cout > d->out_stride) return MCR_ERR_ARG;
   if (d->mask && (d->mask_off + d->cout > d->mask_stride)) return MCR_ERR_ARG;
   unsigned *err = error_word();
   if (!err) return MCR_ERR_CUDA;
 
   const int wbox = d->W < 128 ? d->W : 128;
   const int rows = 128 / wbox;
-  CUtensorMap tmX, tmW;
   {
     const uint64_t dims[4] = {(uint64_t)d->cin_pad, (uint64_t)d->W, (uint64_t)d->H, (uint64_t)d->B};
     const uint64_t strides[3] = {(uint64_t)d->cin_pad * 2, (uint64_t)d->W * d->cin_pad * 2,
@@ -114,7 +117,6 @@ int dn_conv(const dn_conv_desc *d, void *stream) {
                      CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
       return MCR_ERR_CUDA;
   }
-  ConvArgs a{};
   a.B = d->B;
   a.H = d->H;
   a.W = d->W;
@@ -130,13 +132,27 @@ int dn_conv(const dn_conv_desc *d, void *stream) {
   a.mask = static_cast<const __nv_bfloat16 *>(d->mask);
   a.mask_stride = d->mask_stride;
   a.mask_off = d->mask_off;
+  a.mask_vec = d->mask && d->mask_stride % 8 == 0 && d->mask_off % 8 == 0 &&
+               (reinterpret_cast<uintptr_t>(d->mask) & 15) == 0;
+  a.err = err;
+  return MCR_OK;
+}
+
+extern "C" {
+
+int dn_conv(const dn_conv_desc *d, void *stream) {
+  if (!d || !d->out) return MCR_ERR_ARG;
+  if (d->out_stride % 8 || d->out_off % 8 || d->out_off + d->cout > d->out_stride) return MCR_ERR_ARG;
+  CUtensorMap tmX, tmW;
+  ConvArgs a{};
+  const int rc = conv_setup(d, tmX, tmW, a);
+  if (rc != MCR_OK) return rc;
   if (d->out_f32)
     a.out_f32 = static_cast<float *>(d->out);
   else
     a.out_bf16 = static_cast<__nv_bfloat16 *>(d->out);
   a.out_stride = d->out_stride;
   a.out_off = d->out_off;
-  a.err = err;
   if (conv_halo_applies(a)) {  // few output channels: one haloed input box per channel block
     CUtensorMap tmH;
     const uint64_t dims[4] = {(uint64_t)d->cin_pad, (uint64_t)d->W, (uint64_t)d->H, (uint64_t)d->B};
@@ -150,6 +166,45 @@ int dn_conv(const dn_conv_desc *d, void *stream) {
     return MCR_OK;
   }
   if (launch_conv_tc(tmX, tmW, a, (cudaStream_t)stream) != cudaSuccess) return MCR_ERR_CUDA;
+  return MCR_OK;
+}
+
+int dn_conv_head(const dn_conv_desc *d, const dn_head_desc *h, void *stream) {
+  if (!d || !h || d->taps != 1 || d->relu || d->mask) return MCR_ERR_ARG;
+  if (h->mode != DN_HEAD_PREDICT && h->mode != DN_HEAD_LOSS) return MCR_ERR_ARG;
+  const auto al16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  if (!h->res || !h->scale || h->res_stride < d->cout || h->res_stride % 8 || !al16(h->res)) return MCR_ERR_ARG;
+  if (h->mode == DN_HEAD_PREDICT && !h->pred) return MCR_ERR_ARG;
+  if (h->mode == DN_HEAD_LOSS &&
+      (!h->target || !h->dout || !h->loss || h->dout_stride < d->cout || h->dout_stride % 8 || !al16(h->dout)))
+    return MCR_ERR_ARG;
+  CUtensorMap tmX, tmW;
+  ConvArgs a{};
+  const int rc = conv_setup(d, tmX, tmW, a);
+  if (rc != MCR_OK) return rc;
+  double *partials = partials_buffer();
+  if (!partials) return MCR_ERR_CUDA;
+  int dev = 0, sms = 0;  // the loss head writes <= 8 partial sums per block, at most one block per SM
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return MCR_ERR_CUDA;
+  if (8 * sms > kPartialsCap) return MCR_ERR_ARG;
+  const long long P = (long long)d->B * d->H * d->W;
+  const double inv = 1.0 / ((double)P * d->cout);
+  a.head = h->mode;
+  a.res = static_cast<const __nv_bfloat16 *>(h->res);
+  a.res_stride = h->res_stride;
+  a.scale = h->scale;
+  a.HW = d->H * d->W;
+  a.pred = h->pred;
+  a.target = h->target;
+  a.dout = static_cast<__nv_bfloat16 *>(h->dout);
+  a.dout_stride = h->dout_stride;
+  a.two_over_count = (float)(2.0 * inv);
+  a.partials = partials;
+  int n_partials = 0;
+  if (launch_conv_tc(tmX, tmW, a, (cudaStream_t)stream, &n_partials) != cudaSuccess) return MCR_ERR_CUDA;
+  if (h->mode == DN_HEAD_LOSS && sum_partials(partials, n_partials, inv, h->loss, (cudaStream_t)stream) != cudaSuccess)
+    return MCR_ERR_CUDA;
   return MCR_OK;
 }
 
@@ -312,7 +367,7 @@ int dn_mse(const float *out, int32_t ostride, const void *x, int32_t xstride, co
   double *partials = partials_buffer();
   if (!partials) return MCR_ERR_CUDA;
   DN_TRY(mse(out, ostride, static_cast<const __nv_bfloat16 *>(x), xstride, t, P, C, static_cast<__nv_bfloat16 *>(dout),
-             dstride, partials, 4096, loss, (cudaStream_t)stream));
+             dstride, partials, kPartialsCap, loss, (cudaStream_t)stream));
 }
 
 int dn_residual(const float *out, int32_t ostride, const void *x, int32_t xstride, int64_t P, int32_t C, float *y,

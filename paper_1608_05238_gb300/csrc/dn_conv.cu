@@ -27,6 +27,288 @@ constexpr int kBlockM = 128;
 constexpr int kBlockK = 64;
 constexpr uint32_t kATileBytes = kBlockM * kBlockK * 2;  // 16 KB
 
+// 16 floats of one row as bf16: two 16-byte stores when all 16 lie below `valid` (16-byte
+// aligned rows), else element stores of the first `valid`.
+__device__ __forceinline__ void store_bf16x16(__nv_bfloat16 *o, int valid, const float *f) {
+  if (valid >= 16) {
+    __align__(16) __nv_bfloat162 h[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+    *reinterpret_cast<uint4 *>(o) = *reinterpret_cast<const uint4 *>(&h[0]);
+    *reinterpret_cast<uint4 *>(o + 8) = *reinterpret_cast<const uint4 *>(&h[4]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < valid) o[j] = __float2bfloat16_rn(f[j]);
+  }
+}
+
+// 16 bf16 values of one row as floats: two 16-byte loads when the row is 16-byte aligned and all
+// 16 lie below `valid`, else element loads of the first `valid` (the rest read as 0).
+__device__ __forceinline__ void load_bf16x16(const __nv_bfloat16 *p, bool vec, int valid, float *f) {
+  if (vec && valid >= 16) {
+    const uint4 u0 = __ldg(reinterpret_cast<const uint4 *>(p));
+    const uint4 u1 = __ldg(reinterpret_cast<const uint4 *>(p + 8));
+    const __nv_bfloat162 *h0 = reinterpret_cast<const __nv_bfloat162 *>(&u0);
+    const __nv_bfloat162 *h1 = reinterpret_cast<const __nv_bfloat162 *>(&u1);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 a = __bfloat1622float2(h0[j]), b = __bfloat1622float2(h1[j]);
+      f[2 * j] = a.x;
+      f[2 * j + 1] = a.y;
+      f[8 + 2 * j] = b.x;
+      f[8 + 2 * j + 1] = b.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) f[j] = j < valid ? __bfloat162float(p[j]) : 0.f;
+  }
+}
+
+// Fused output head on 16 output channels c0.. of pixel p (image bi, pixel pi of it), f = the
+// layer's output (accumulator + bias).  Prediction: pred[bi][c][pi] = (x0 + f) / scale; loss:
+// r = x0 + f - scale * target[bi][c][pi], dout = bf16(2 r / count), returns the sum of r^2.  The
+// channel-major reads and writes are coalesced: the lanes of a warp hold consecutive pixels.
+__device__ __forceinline__ double head_chunk(const ConvArgs &a, long long p, long long bi, long long pi, float hs,
+                                             int c0, int valid, const float *f) {
+  float xv[16];
+  load_bf16x16(a.res + p * a.res_stride + c0, true, valid, xv);
+  if (a.head == 1) {
+    float *o = a.pred + (bi * a.cout + c0) * a.HW + pi;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < valid) o[(long long)j * a.HW] = (xv[j] + f[j]) * hs;
+    return 0.0;
+  }
+  const float *t = a.target + (bi * a.cout + c0) * a.HW + pi;
+  float g[16];
+  double ss = 0.0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    g[j] = 0.f;
+    if (j < valid) {
+      // the scaled target rounded on its own, as a stored scaled copy would be
+      const float r = xv[j] + f[j] - __fmul_rn(t[(long long)j * a.HW], hs);
+      ss += (double)__fmul_rn(r, r);
+      g[j] = r * a.two_over_count;
+    }
+  }
+  __nv_bfloat16 *o = a.dout + p * a.dout_stride + c0;
+  if (valid >= 16) {
+    __align__(16) __nv_bfloat162 h[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(g[2 * j], g[2 * j + 1]);
+    *reinterpret_cast<uint4 *>(o) = *reinterpret_cast<const uint4 *>(&h[0]);
+    *reinterpret_cast<uint4 *>(o + 8) = *reinterpret_cast<const uint4 *>(&h[4]);
+  } else {
+    for (int j = 0; j < valid; ++j) o[j] = __float2bfloat16_rn(g[j]);
+  }
+  return ss;
+}
+
+// 16 bf16 of one row as raw 16-byte words (two loads when 16-byte aligned and all 16 lie below
+// `valid`, else element loads of the first `valid`, the rest 0), converted after the TMEM wait so
+// that the global loads of a row are all in flight while its accumulator is read.
+union Raw16 {
+  uint4 u[2];
+  __nv_bfloat16 h[16];
+};
+__device__ __forceinline__ void load_raw16(const __nv_bfloat16 *p, bool vec, int valid, Raw16 &r) {
+  if (vec && valid >= 16) {
+    r.u[0] = __ldg(reinterpret_cast<const uint4 *>(p));
+    r.u[1] = __ldg(reinterpret_cast<const uint4 *>(p + 8));
+  } else {
+    r.u[0] = make_uint4(0u, 0u, 0u, 0u);
+    r.u[1] = r.u[0];
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < valid) r.h[j] = p[j];
+  }
+}
+__device__ __forceinline__ void unpack16(const Raw16 &r, float *f) {
+  const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(r.u);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float2 v = __bfloat1622float2(h[j]);
+    f[2 * j] = v.x;
+    f[2 * j + 1] = v.y;
+  }
+}
+
+// Epilogue of 16 NCH columns c0b.. of one row: every global load (the ReLU mask, or the head's
+// residual input and target) is issued first, then the TMEM loads and one wait, then the
+// arithmetic and stores -- one memory latency per 16 NCH columns instead of one per 16.  HEAD:
+// the fused output head (a.head != 0), else the plain epilogue.
+template <int NCH, bool HEAD>
+__device__ __forceinline__ double drain_row_t(const ConvArgs &a, long long p, uint32_t trow, int c0b) {
+  long long bi = 0, pi = 0;
+  float hs = 0.f;
+  if (HEAD) {
+    bi = p / a.HW;
+    pi = p - bi * a.HW;
+    hs = a.head == 1 ? 1.f / __ldg(a.scale + bi) : __ldg(a.scale + bi);
+  }
+  Raw16 raw[NCH];  // mask rows, or the head's residual input rows
+  float tv[HEAD ? NCH : 1][16];
+#pragma unroll
+  for (int k = 0; k < NCH; ++k) {
+    const int c0 = c0b + 16 * k, valid = a.cout - c0;
+    if (HEAD) {
+      load_raw16(a.res + p * a.res_stride + c0, true, valid, raw[k]);
+      if (a.head == 2) {
+        const float *t = a.target + (bi * a.cout + c0) * a.HW + pi;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) tv[HEAD ? k : 0][j] = j < valid ? __ldg(t + (long long)j * a.HW) : 0.f;
+      }
+    } else if (a.mask) {
+      load_raw16(a.mask + p * a.mask_stride + a.mask_off + c0, a.mask_vec != 0, valid, raw[k]);
+    }
+  }
+  uint32_t v[NCH][16];
+#pragma unroll
+  for (int k = 0; k < NCH; ++k) {
+    // only the accumulator's own N columns (N is a multiple of 16; warp-uniform test)
+    if (c0b + 16 * k < a.N) tmem_ld16(trow + (uint32_t)(c0b + 16 * k), v[k]);
+    else
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[k][j] = 0u;
+  }
+  tmem_ld_wait();
+  double ss = 0.0;
+#pragma unroll
+  for (int k = 0; k < NCH; ++k) {
+    const int c0 = c0b + 16 * k, valid = a.cout - c0;
+    if (valid <= 0) break;
+    float f[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      float x = __uint_as_float(v[k][j]);
+      if (a.bias && j < valid) x += __ldg(a.bias + c0 + j);
+      if (a.relu) x = fmaxf(x, 0.f);
+      f[j] = x;
+    }
+    if (HEAD) {
+      float xv[16];
+      unpack16(raw[k], xv);
+      if (a.head == 1) {
+        float *o = a.pred + (bi * a.cout + c0) * a.HW + pi;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (j < valid) o[(long long)j * a.HW] = (xv[j] + f[j]) * hs;
+      } else {
+        float g[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          g[j] = 0.f;
+          if (j < valid) {
+            // the scaled target rounded on its own, as a stored scaled copy would be
+            const float r = xv[j] + f[j] - __fmul_rn(tv[HEAD ? k : 0][j], hs);
+            ss += (double)__fmul_rn(r, r);
+            g[j] = r * a.two_over_count;
+          }
+        }
+        store_bf16x16(a.dout + p * a.dout_stride + c0, valid, g);
+      }
+      continue;
+    }
+    if (a.mask) {
+      float mk[16];
+      unpack16(raw[k], mk);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (j < valid) f[j] = mk[j] > 0.f ? f[j] : 0.f;
+    }
+    if (a.out_f32) {
+      float *o = a.out_f32 + p * a.out_stride + a.out_off + c0;
+      if (valid >= 16) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4 *>(o + j) = make_float4(f[j], f[j + 1], f[j + 2], f[j + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (j < valid) o[j] = f[j];
+      }
+    } else {
+      store_bf16x16(a.out_bf16 + p * a.out_stride + a.out_off + c0, valid, f);
+    }
+  }
+  return ss;
+}
+
+// Epilogue of one output pixel p (this thread's TMEM lane, row address trow): N accumulator
+// columns through bias / ReLU / the next layer's ReLU mask into the bf16 or fp32 output slice,
+// or through the fused output head.  Returns the head's sum of squared residuals (else 0).
+__device__ __forceinline__ double drain_row_any(const ConvArgs &a, long long p, uint32_t trow) {
+  double ss = 0.0;
+  long long bi = 0, pi = 0;
+  float hs = 0.f;
+  if (a.head) {
+    bi = p / a.HW;
+    pi = p - bi * a.HW;
+    hs = a.head == 1 ? 1.f / a.scale[bi] : a.scale[bi];
+  }
+  for (int c0 = 0; c0 < a.N; c0 += 16) {
+    uint32_t v[16];
+    tmem_ld16(trow + (uint32_t)c0, v);
+    tmem_ld_wait();
+    const int valid = a.cout - c0;
+    float mk[16];
+    if (a.mask) load_bf16x16(a.mask + p * a.mask_stride + a.mask_off + c0, a.mask_vec != 0, valid, mk);
+    float f[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int n = c0 + j;
+      float x = __uint_as_float(v[j]);
+      if (a.bias && n < a.cout) x += a.bias[n];
+      if (a.relu) x = fmaxf(x, 0.f);
+      if (a.mask && n < a.cout) x = mk[j] > 0.f ? x : 0.f;
+      f[j] = x;
+    }
+    if (a.head) {
+      if (valid > 0) ss += head_chunk(a, p, bi, pi, hs, c0, valid, f);
+      continue;
+    }
+    if (a.out_f32) {
+      float *o = a.out_f32 + p * a.out_stride + a.out_off + c0;
+      if (c0 + 16 <= a.cout) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4 *>(o + j) = make_float4(f[j], f[j + 1], f[j + 2], f[j + 3]);
+      } else {
+        for (int j = 0; j < 16 && c0 + j < a.cout; ++j) o[j] = f[j];
+      }
+    } else {
+      __nv_bfloat16 *o = a.out_bf16 + p * a.out_stride + a.out_off + c0;
+      if (c0 + 16 <= a.cout) {
+        __align__(16) __nv_bfloat162 h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+        *reinterpret_cast<uint4 *>(o) = *reinterpret_cast<const uint4 *>(&h[0]);
+        *reinterpret_cast<uint4 *>(o + 8) = *reinterpret_cast<const uint4 *>(&h[4]);
+      } else {
+        for (int j = 0; j < 16 && c0 + j < a.cout; ++j) o[j] = __float2bfloat16_rn(f[j]);
+      }
+    }
+  }
+  return ss;
+}
+
+template <bool HEAD>
+__device__ __forceinline__ double drain_row(const ConvArgs &a, long long p, uint32_t trow) {
+  if (HEAD) return a.N == 48 ? drain_row_t<3, true>(a, p, trow, 0) : drain_row_any(a, p, trow);
+  for (int c0 = 0; c0 < a.N; c0 += 32) drain_row_t<2, false>(a, p, trow, c0);
+  return 0.0;
+}
+
+// one sum of squared residuals per epilogue warp (fused loss head), in a fixed order
+__device__ __forceinline__ void head_partial(const ConvArgs &a, double ss, int e, int epi_warps, int lane) {
+  if (a.head != 2) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (lane == 0) a.partials[blockIdx.x * epi_warps + e] = ss;
+}
+
 // k_conv_ws: persistent, warp-specialised.  One CTA per SM
 // walks the output tiles (tile = blockIdx.x + i gridDim.x); warp 0 streams the K blocks of all
 // its tiles through a ring of `stages` shared-memory buffers with TMA, warp 1 issues the MMAs
@@ -34,11 +316,14 @@ constexpr uint32_t kATileBytes = kBlockM * kBlockK * 2;  // 16 KB
 // accumulator (TMEM lanes 32 (w % 4) ... + 31) while the next tile is being multiplied.
 // SUB = 2 (N <= 128): a tile is 2 x 128 pixels whose two A tiles share one weight tile per
 // stage (two MMAs per K step into the two halves of the accumulator, acc_cols / 2 >= N columns
-// apart), which halves the weight bytes each output pixel pulls through L2.
+// apart), which halves the weight bytes each output pixel pulls through L2; warps 2..9 drain
+// it, warps 2..5 the first half and 6..9 the second (each warp its TMEM lane quarter w % 4).
 constexpr int kWsThreads = 192;
-
 template <int SUB>
-__global__ void __launch_bounds__(kWsThreads, 1)
+constexpr int ws_threads() { return 64 + 128 * SUB; }
+
+template <int SUB, bool HEAD>
+__global__ void __launch_bounds__(ws_threads<SUB>(), 1)
     k_conv_ws(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, const ConvArgs a,
               int stages, int num_tiles) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -60,7 +345,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], 128 * SUB);
     }
     fence_barrier_init();
     prefetch_tensormap(&tmX);
@@ -147,10 +432,11 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       mma_commit(&tfull[b]);
     }
   } else if (warp >= 2) {
-    // ---- epilogue warps: TMEM lanes 32 (warp % 4) .. + 31
-    const int q = warp & 3;
+    // ---- epilogue warps: TMEM lanes 32 (warp % 4) .. + 31 of sub-tile (warp - 2) / 4
+    const int e = warp - 2, q = warp & 3, u = e >> 2;
     const int row = q * 32 + lane;
     int it = 0;
+    double ss = 0.0;
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
       const int b = it & 1;
       const uint32_t use = it >> 1;
@@ -161,100 +447,16 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         break;
       }
       tc_fence_after();
-      for (int u = 0; u < SUB; ++u) {
-      const long long p = ((long long)tile * SUB + u) * kBlockM + row;
-      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + b * acc_cols + u * (acc_cols / 2);
-      for (int c0 = 0; c0 < a.N; c0 += 16) {
-        uint32_t v[16];
-        tmem_ld16(trow + (uint32_t)c0, v);
-        tmem_ld_wait();
-        float f[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = c0 + j;
-          float x = __uint_as_float(v[j]);
-          if (a.bias && n < a.cout) x += a.bias[n];
-          if (a.relu) x = fmaxf(x, 0.f);
-          if (a.mask && n < a.cout) {
-            const float m = __bfloat162float(a.mask[p * a.mask_stride + a.mask_off + n]);
-            x = m > 0.f ? x : 0.f;
-          }
-          f[j] = x;
-        }
-        if (a.out_f32) {
-          float *o = a.out_f32 + p * a.out_stride + a.out_off + c0;
-          if (c0 + 16 <= a.cout) {
-#pragma unroll
-            for (int j = 0; j < 16; j += 4)
-              *reinterpret_cast<float4 *>(o + j) = make_float4(f[j], f[j + 1], f[j + 2], f[j + 3]);
-          } else {
-            for (int j = 0; j < 16 && c0 + j < a.cout; ++j) o[j] = f[j];
-          }
-        } else {
-          __nv_bfloat16 *o = a.out_bf16 + p * a.out_stride + a.out_off + c0;
-          if (c0 + 16 <= a.cout) {
-            __align__(16) __nv_bfloat162 h[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
-            *reinterpret_cast<uint4 *>(o) = *reinterpret_cast<const uint4 *>(&h[0]);
-            *reinterpret_cast<uint4 *>(o + 8) = *reinterpret_cast<const uint4 *>(&h[4]);
-          } else {
-            for (int j = 0; j < 16 && c0 + j < a.cout; ++j) o[j] = __float2bfloat16_rn(f[j]);
-          }
-        }
-      }
-      }
+      ss += drain_row<HEAD>(a, ((long long)tile * SUB + u) * kBlockM + row,
+                      tmem + ((uint32_t)(q * 32) << 16) + b * acc_cols + u * (acc_cols / 2));
       tc_fence_before();
       mbar_arrive(&tempty[b]);
     }
+    head_partial(a, ss, e, 4 * SUB, lane);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 2 * acc_cols);
-}
-
-// Epilogue of one output pixel p (this thread's TMEM lane, row address trow): N accumulator
-// columns through bias / ReLU / the next layer's ReLU mask into the bf16 or fp32 output slice.
-__device__ __forceinline__ void drain_row(const ConvArgs &a, long long p, uint32_t trow) {
-  for (int c0 = 0; c0 < a.N; c0 += 16) {
-    uint32_t v[16];
-    tmem_ld16(trow + (uint32_t)c0, v);
-    tmem_ld_wait();
-    float f[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int n = c0 + j;
-      float x = __uint_as_float(v[j]);
-      if (a.bias && n < a.cout) x += a.bias[n];
-      if (a.relu) x = fmaxf(x, 0.f);
-      if (a.mask && n < a.cout) {
-        const float m = __bfloat162float(a.mask[p * a.mask_stride + a.mask_off + n]);
-        x = m > 0.f ? x : 0.f;
-      }
-      f[j] = x;
-    }
-    if (a.out_f32) {
-      float *o = a.out_f32 + p * a.out_stride + a.out_off + c0;
-      if (c0 + 16 <= a.cout) {
-#pragma unroll
-        for (int j = 0; j < 16; j += 4)
-          *reinterpret_cast<float4 *>(o + j) = make_float4(f[j], f[j + 1], f[j + 2], f[j + 3]);
-      } else {
-        for (int j = 0; j < 16 && c0 + j < a.cout; ++j) o[j] = f[j];
-      }
-    } else {
-      __nv_bfloat16 *o = a.out_bf16 + p * a.out_stride + a.out_off + c0;
-      if (c0 + 16 <= a.cout) {
-        __align__(16) __nv_bfloat162 h[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
-        *reinterpret_cast<uint4 *>(o) = *reinterpret_cast<const uint4 *>(&h[0]);
-        *reinterpret_cast<uint4 *>(o + 8) = *reinterpret_cast<const uint4 *>(&h[4]);
-      } else {
-        for (int j = 0; j < 16 && c0 + j < a.cout; ++j) o[j] = __float2bfloat16_rn(f[j]);
-      }
-    }
-  }
 }
 
 // k_conv_halo: 3x3 convolution with few output channels (N <= 32) whose 128-pixel tiles lie in
@@ -376,7 +578,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         break;
       }
       tc_fence_after();
-      drain_row(a, (long long)tile * kBlockM + row, tmem + ((uint32_t)(q * 32) << 16) + b * acc_cols);
+      drain_row<false>(a, (long long)tile * kBlockM + row, tmem + ((uint32_t)(q * 32) << 16) + b * acc_cols);
       tc_fence_before();
       mbar_arrive(&tempty[b]);
     }
@@ -644,11 +846,12 @@ static int sm_count() {
   return n;
 }
 
-template <int SUB>
-static cudaError_t launch_ws(const CUtensorMap &tmX, const CUtensorMap &tmW, ConvArgs a, cudaStream_t s) {
+template <int SUB, bool HEAD>
+static cudaError_t launch_ws(const CUtensorMap &tmX, const CUtensorMap &tmW, ConvArgs a, cudaStream_t s,
+                             int *partials_out) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_ws<SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_ws<SUB, HEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -657,16 +860,20 @@ static cudaError_t launch_ws(const CUtensorMap &tmX, const CUtensorMap &tmW, Con
   a.tmem_cols = cols;
   const long long tiles = (long long)a.B * a.H * a.W / (kBlockM * SUB);
   const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
-  k_conv_ws<SUB><<<grid, kWsThreads, conv_smem(a.N, SUB), s>>>(tmX, tmW, a, conv_stages(a.N, SUB), (int)tiles);
+  if (partials_out) *partials_out = grid * 4 * SUB;
+  k_conv_ws<SUB, HEAD><<<grid, ws_threads<SUB>(), conv_smem(a.N, SUB), s>>>(tmX, tmW, a, conv_stages(a.N, SUB),
+                                                                            (int)tiles);
   return cudaGetLastError();
 }
 
-cudaError_t launch_conv_tc(const CUtensorMap &tmX, const CUtensorMap &tmW, const ConvArgs &a, cudaStream_t s) {
+cudaError_t launch_conv_tc(const CUtensorMap &tmX, const CUtensorMap &tmW, const ConvArgs &a, cudaStream_t s,
+                           int *partials_out) {
   const long long P = (long long)a.B * a.H * a.W;
   // two 128-pixel tiles per weight stage when two accumulators of N columns, double-buffered,
   // fit in the 512 TMEM columns and the pixels split into 256-pixel tiles
-  if (a.N <= 128 && P % (2 * kBlockM) == 0) return launch_ws<2>(tmX, tmW, a, s);
-  return launch_ws<1>(tmX, tmW, a, s);
+  const bool pair = a.N <= 128 && P % (2 * kBlockM) == 0;
+  if (a.head) return pair ? launch_ws<2, true>(tmX, tmW, a, s, partials_out) : launch_ws<1, true>(tmX, tmW, a, s, partials_out);
+  return pair ? launch_ws<2, false>(tmX, tmW, a, s, partials_out) : launch_ws<1, false>(tmX, tmW, a, s, partials_out);
 }
 
 cudaError_t launch_wgrad_mn(const CUtensorMap &tmA, const CUtensorMap &tmB, const WgradArgs &a, cudaStream_t s) {

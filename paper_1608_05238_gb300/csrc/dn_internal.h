@@ -24,9 +24,24 @@ struct ConvArgs {
   float *out_f32;
   int out_stride, out_off;  // channel stride and offset of the output slice
   unsigned *err;            // device error word (bounded waits that gave up)
+  int mask_vec;             // mask rows 16-byte aligned (stride and offset multiples of 8): vector loads
+  // fused output head of a 1x1 output layer (k_conv_ws only; out_bf16 / out_f32 unused when set)
+  int head;                   // 0 none, 1 prediction, 2 residual MSE loss and its gradient
+  const __nv_bfloat16 *res;   // residual input x0: NHWC bf16, channel stride res_stride (multiple of 8)
+  int res_stride;
+  const float *scale;         // [B] per-sample input scale
+  int HW;                     // pixels per image
+  float *pred;                // head 1: [B][cout][HW] = (x0 + out) / scale
+  const float *target;        // head 2: [B][cout][HW], unscaled
+  __nv_bfloat16 *dout;        // head 2: NHWC bf16 2 (x0 + out - scale target) / count, stride dout_stride
+  int dout_stride;
+  float two_over_count;
+  double *partials;           // head 2: one sum of squares per (block, epilogue warp)
 };
 
-cudaError_t launch_conv_tc(const CUtensorMap &tmX, const CUtensorMap &tmW, const ConvArgs &a, cudaStream_t s);
+// partials_out (optional): the number of partial sums the fused loss head writes (one per epilogue warp)
+cudaError_t launch_conv_tc(const CUtensorMap &tmX, const CUtensorMap &tmW, const ConvArgs &a, cudaStream_t s,
+                           int *partials_out = nullptr);
 // 3x3 convolution with N <= 32 on rows of whole 128-pixel tiles: one haloed input box {64, 130, 3, 1}
 // and all nine taps' weights per channel block
 bool conv_halo_applies(const ConvArgs &a);
@@ -60,6 +75,8 @@ cudaError_t up2(const __nv_bfloat16 *src, int B, int H, int W, int sstride, int 
 cudaError_t up2_bwd(const __nv_bfloat16 *du, int ustride, int uoff, const __nv_bfloat16 *act, int astride, int aoff,
                     int B, int H, int W, int C, __nv_bfloat16 *dz, int zstride, int zoff, cudaStream_t s);
 cudaError_t bias_grad(const __nv_bfloat16 *dz, long long P, int stride, int off, int C, float *db, cudaStream_t s);
+// loss = scale * (sum of partials[0..n)) in one block, fixed order
+cudaError_t sum_partials(const double *partials, int n, double scale, double *loss, cudaStream_t s);
 cudaError_t mse(const float *out, int ostride, const __nv_bfloat16 *x, int xstride, const float *t, long long P, int C,
                 __nv_bfloat16 *dout, int dstride, double *partials, int partials_cap, double *loss, cudaStream_t s);
 cudaError_t residual(const float *out, int ostride, const __nv_bfloat16 *x, int xstride, long long P, int C, float *y,

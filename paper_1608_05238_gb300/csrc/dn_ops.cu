@@ -216,6 +216,37 @@ __global__ void k_bias_grad(const __nv_bfloat16 *__restrict__ dz, long long P, i
   }
 }
 
+// db[c] += sum over pixels of dz[p][off + c] with 16-byte loads: G = C / 8 threads cover one
+// pixel row (8 channels each), 256 / G rows per pass of the block; per-thread FP32 sums, a
+// fixed-order sum over the block's rows in shared memory, one atomic add per channel and block.
+__global__ void __launch_bounds__(256) k_bias_grad_v8(const __nv_bfloat16 *__restrict__ dz, long long P, int stride,
+                                                      int off, int G, float *__restrict__ db) {
+  __shared__ float red[256 * 8];
+  const int R = 256 / G, t = threadIdx.x, g = t % G, r = t / G, C = 8 * G;
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (r < R) {
+#pragma unroll 4
+    for (long long p = (long long)blockIdx.x * R + r; p < P; p += (long long)gridDim.x * R) {
+      const uint4 u = __ldg(reinterpret_cast<const uint4 *>(dz + p * stride + off) + g);
+      const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 f = __bfloat1622float2(h[j]);
+        acc[2 * j] += f.x;
+        acc[2 * j + 1] += f.y;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) red[r * C + 8 * g + j] = acc[j];
+  }
+  __syncthreads();
+  for (int c = t; c < C; c += 256) {
+    float sum = 0.f;
+    for (int k = 0; k < R; ++k) sum += red[k * C + c];
+    atomicAdd(db + c, sum);
+  }
+}
+
 // residual MSE: y = x + out over C channels; loss partials (FP64) and dout = 2 (y - t) / count
 // written as bf16 NHWC (stride dstride) for the next convolution's input gradient.
 // One thread per (pixel, channel): threadIdx.x over channels, the rest over pixels (grid-stride),
@@ -295,6 +326,41 @@ __global__ void k_adam(float *__restrict__ w, float *__restrict__ m, float *__re
   }
 }
 
+// The same update when the transposed copy wd is wanted, through a 32 x 32 (cout x cin) tile of
+// one tap: the update and wf are written along cin, wd along cout (both coalesced).
+__global__ void k_adam_t(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                         float *__restrict__ g, int cout, int taps, int cin, float lr, float b1, float b2,
+                         float eps, float c1, float c2, __nv_bfloat16 *__restrict__ wf, int cin_pad,
+                         __nv_bfloat16 *__restrict__ wd, int cout_pad, int step) {
+  __shared__ __nv_bfloat16 tile[32][34];
+  const int c0 = blockIdx.x * 32, o0 = blockIdx.y * 32, t = blockIdx.z;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int o = o0 + r, c = c0 + threadIdx.x;
+    if (o < cout && c < cin) {
+      const size_t i = ((size_t)o * taps + t) * cin + c;
+      float wi = w[i];
+      if (step > 0) {
+        const float gi = g[i];
+        g[i] = 0.f;
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        wi -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        w[i] = wi;
+      }
+      const __nv_bfloat16 h = __float2bfloat16_rn(wi);
+      wf[((size_t)o * taps + t) * cin_pad + c] = h;
+      tile[r][threadIdx.x] = h;
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int c = c0 + r, o = o0 + threadIdx.x;
+    if (o < cout && c < cin) wd[((size_t)c * taps + (taps - 1 - t)) * cout_pad + o] = tile[threadIdx.x][r];
+  }
+}
+
 __global__ void k_adam_bias(float *__restrict__ b, float *__restrict__ m, float *__restrict__ v,
                             float *__restrict__ g, int n, float lr, float b1, float b2, float eps, float c1,
                             float c2) {
@@ -327,6 +393,40 @@ __global__ void k_pack_input(const float *__restrict__ src, const float *__restr
   for (int r = threadIdx.y; r < 32; r += 8) {
     const int p = p0 + r, c = c0 + threadIdx.x;
     if (p < HW && c < C) dst[((size_t)b * HW + p) * stride + c] = __float2bfloat16_rn(tile[threadIdx.x][r]);
+  }
+}
+
+// The same with 64 pixels x 64 channels per block and 16-byte stores (8 channels per thread, 8
+// threads per 128-byte row segment); channels >= C are not written.  Requires HW % 64 == 0 and a
+// 16-byte aligned dst with stride % 8 == 0.
+__global__ void __launch_bounds__(256) k_pack_input_v8(const float *__restrict__ src, const float *__restrict__ scale,
+                                                       int HW, int C, __nv_bfloat16 *__restrict__ dst, int stride) {
+  __shared__ float tile[64][65];
+  const int p0 = blockIdx.x * 64, c0 = blockIdx.y * 64, b = blockIdx.z, t = threadIdx.x;
+  const float sc = scale[b];
+  {
+    const int pp = 2 * (t & 31);
+    for (int r = t >> 5; r < 64; r += 8) {
+      const int c = c0 + r;
+      float2 v = make_float2(0.f, 0.f);
+      if (c < C) v = __ldg(reinterpret_cast<const float2 *>(src + ((size_t)b * C + c) * HW + p0 + pp));
+      tile[r][pp] = v.x * sc;
+      tile[r][pp + 1] = v.y * sc;
+    }
+  }
+  __syncthreads();
+  for (int k = t; k < 64 * 8; k += 256) {
+    const int px = k >> 3, g = k & 7, cg = c0 + 8 * g;
+    if (cg >= C) continue;
+    __nv_bfloat16 *o = dst + ((size_t)b * HW + p0 + px) * stride + cg;
+    if (cg + 8 <= C) {
+      __align__(16) __nv_bfloat162 h[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(tile[8 * g + 2 * j][px], tile[8 * g + 2 * j + 1][px]);
+      *reinterpret_cast<uint4 *>(o) = *reinterpret_cast<const uint4 *>(h);
+    } else {
+      for (int j = 0; cg + j < C; ++j) o[j] = __float2bfloat16_rn(tile[8 * g + j][px]);
+    }
   }
 }
 
@@ -475,6 +575,13 @@ cudaError_t up2_bwd(const __nv_bfloat16 *du, int ustride, int uoff, const __nv_b
   return cudaGetLastError();
 }
 cudaError_t bias_grad(const __nv_bfloat16 *dz, long long P, int stride, int off, int C, float *db, cudaStream_t s) {
+  if (al8(C, stride, off, 0) && C / 8 <= 256 && (reinterpret_cast<uintptr_t>(dz) & 15) == 0) {
+    const int G = C / 8, R = 256 / G;
+    long long gx = (P + 4LL * R - 1) / (4LL * R);  // at least ~4 rows per thread
+    if (gx > 152 * 8) gx = 152 * 8;
+    k_bias_grad_v8<<<(unsigned)gx, 256, 0, s>>>(dz, P, stride, off, G, db);
+    return cudaGetLastError();
+  }
   long long gx = (P + 8 * 64 - 1) / (8 * 64);
   if (gx > 256) gx = 256;
   const dim3 grid((unsigned)gx, (C + 31) / 32), block(32, 8);
@@ -493,6 +600,10 @@ cudaError_t mse(const float *out, int ostride, const __nv_bfloat16 *x, int xstri
   k_sum_partials<<<1, kT, 0, s>>>(partials, (int)gx * cy, inv, loss);
   return cudaGetLastError();
 }
+cudaError_t sum_partials(const double *partials, int n, double scale, double *loss, cudaStream_t s) {
+  k_sum_partials<<<1, kT, 0, s>>>(partials, n, scale, loss);
+  return cudaGetLastError();
+}
 cudaError_t residual(const float *out, int ostride, const __nv_bfloat16 *x, int xstride, long long P, int C, float *y,
                      cudaStream_t s) {
   long long gx = (P + 8 * 16 - 1) / (8 * 16);
@@ -504,6 +615,12 @@ cudaError_t adam(float *w, float *m, float *v, float *g, int cout, int taps, int
                  float b2, float eps, int step, __nv_bfloat16 *wf, int cin_pad, __nv_bfloat16 *wd, int cout_pad,
                  cudaStream_t s) {
   const float c1 = step > 0 ? 1.f - powf(b1, (float)step) : 1.f, c2 = step > 0 ? 1.f - powf(b2, (float)step) : 1.f;
+  if (wd) {
+    k_adam_t<<<dim3((cin + 31) / 32, (cout + 31) / 32, taps), dim3(32, 8), 0, s>>>(w, m, v, g, cout, taps, cin, lr, b1,
+                                                                                  b2, eps, c1, c2, wf, cin_pad, wd,
+                                                                                  cout_pad, step);
+    return cudaGetLastError();
+  }
   k_adam<<<blocks_for((long long)cout * taps * cin), kT, 0, s>>>(w, m, v, g, cout, taps, cin, lr, b1, b2, eps, c1, c2,
                                                                   wf, cin_pad, wd, cout_pad, step);
   return cudaGetLastError();
@@ -518,6 +635,11 @@ cudaError_t adam_bias(float *b, float *m, float *v, float *g, int n, float lr, f
 cudaError_t pack_input(const float *src, const float *scale, int B, long long HW, int C, __nv_bfloat16 *dst, int stride,
                        cudaStream_t s) {
   if (HW > 0x7fffffffll - 31 || B > 65535) return cudaErrorInvalidValue;
+  if (HW % 64 == 0 && stride % 8 == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0 &&
+      (reinterpret_cast<uintptr_t>(src) & 7) == 0) {
+    k_pack_input_v8<<<dim3((unsigned)(HW / 64), (C + 63) / 64, B), 256, 0, s>>>(src, scale, (int)HW, C, dst, stride);
+    return cudaGetLastError();
+  }
   k_pack_input<<<dim3((unsigned)((HW + 31) / 32), (C + 31) / 32, B), dim3(32, 8), 0, s>>>(src, scale, (int)HW, C, dst,
                                                                                          stride);
   return cudaGetLastError();

@@ -22,11 +22,20 @@ class _ConvDesc(C.Structure):
                 ("out_off", C.c_int32)]
 
 
+class _HeadDesc(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("res", C.c_void_p), ("res_stride", C.c_int32), ("scale", C.c_void_p),
+                ("pred", C.c_void_p), ("target", C.c_void_p), ("dout", C.c_void_p), ("dout_stride", C.c_int32),
+                ("loss", C.c_void_p)]
+
+
+HEAD_PREDICT, HEAD_LOSS = 1, 2
+
+
 class _Slice(C.Structure):
     _fields_ = [("data", C.c_void_p), ("stride", C.c_int32), ("off", C.c_int32)]
 
 
-EXPORTS = ("dn_conv", "dn_wgrad", "dn_wgrad_nhwc", "dn_to_ct", "dn_pool2", "dn_pool2_bwd", "dn_up2", "dn_up2_bwd", "dn_bias_grad",
+EXPORTS = ("dn_conv", "dn_conv_head", "dn_wgrad", "dn_wgrad_nhwc", "dn_to_ct", "dn_pool2", "dn_pool2_bwd", "dn_up2", "dn_up2_bwd", "dn_bias_grad",
            "dn_mse", "dn_residual", "dn_adam", "dn_adam_bias", "dn_pack_input", "dn_sample_scale", "dn_pack_target", "dn_predict_output",
            "dn_unpack_output", "dn_check")
 
@@ -39,6 +48,7 @@ def lib():
         S = _Slice
         sig = {
             "dn_conv": [C.POINTER(_ConvDesc), vp],
+            "dn_conv_head": [C.POINTER(_ConvDesc), C.POINTER(_HeadDesc), vp],
             "dn_wgrad": [i32, i32, i32, i32, i32, i32, vp, vp, vp, vp],
             "dn_wgrad_nhwc": [S, S, i32, i32, i32, i32, i32, i32, vp, vp],
             "dn_to_ct": [S, i32, i32, i32, i32, i32, vp, vp],
@@ -224,6 +234,42 @@ def conv(x: torch.Tensor, w: torch.Tensor, cout: int, out: torch.Tensor, *, taps
     if rc != 0:
         raise mcr.McrError(rc, "dn_conv")
     return out
+
+
+def conv_head(x: torch.Tensor, w: torch.Tensor, cout: int, bias, res: torch.Tensor, scale: torch.Tensor, *,
+              pred: torch.Tensor | None = None, target: torch.Tensor | None = None, dout: torch.Tensor | None = None,
+              loss: torch.Tensor | None = None, stream=None):
+    """The 1x1 output layer with the residual head fused into its epilogue (``dn_conv_head``).
+
+    With ``pred`` ([B][cout][H][W] fp32): pred = (res + conv(x, w) + bias) / scale.  With ``target``
+    ([B][cout][H][W] fp32, unscaled), ``dout`` (bf16 NHWC) and ``loss`` (FP64 scalar): the residual MSE
+    against scale * target and its gradient seed.
+    """
+    assert x.is_cuda and x.dtype == torch.bfloat16 and x.is_contiguous() and x.dim() == 4
+    assert w.is_cuda and w.dtype == torch.bfloat16 and w.is_contiguous() and w.shape[1] == 1
+    assert res.is_cuda and res.dtype == torch.bfloat16 and res.is_contiguous() and res.shape[:3] == x.shape[:3]
+    assert scale.is_cuda and scale.dtype == torch.float32 and scale.numel() == x.shape[0]
+    B, H, W, cin_pad = x.shape
+    assert w.shape[2] == cin_pad
+    if bias is not None:
+        assert bias.is_cuda and bias.dtype == torch.float32 and bias.is_contiguous()
+    if pred is not None:
+        assert pred.is_cuda and pred.dtype == torch.float32 and pred.is_contiguous()
+        assert tuple(pred.shape) == (B, cout, H, W)
+        h = _HeadDesc(HEAD_PREDICT, res.data_ptr(), res.shape[3], scale.data_ptr(), pred.data_ptr(), None, None, 0, None)
+    else:
+        assert target is not None and dout is not None and loss is not None
+        assert target.is_cuda and target.dtype == torch.float32 and target.is_contiguous()
+        assert tuple(target.shape) == (B, cout, H, W)
+        assert dout.is_cuda and dout.dtype == torch.bfloat16 and dout.is_contiguous() and dout.shape[:3] == x.shape[:3]
+        assert loss.is_cuda and loss.dtype == torch.float64
+        h = _HeadDesc(HEAD_LOSS, res.data_ptr(), res.shape[3], scale.data_ptr(), None, target.data_ptr(),
+                      dout.data_ptr(), dout.shape[3], loss.data_ptr())
+    d = _ConvDesc(B, H, W, cin_pad, x.data_ptr(), 1, cout, w.shape[0], w.data_ptr(),
+                  bias.data_ptr() if bias is not None else None, 0, None, 0, 0, None, 0, 0, 0)
+    rc = lib().dn_conv_head(C.byref(d), C.byref(h), _stream(stream))
+    if rc != 0:
+        raise mcr.McrError(rc, "dn_conv_head")
 
 
 def check(stream=None):

@@ -174,6 +174,14 @@ class UNet:
             ops.pack_target(target.contiguous(), scale, self.target)
 
     def forward(self):
+        """The network on the loaded input; returns the NHWC fp32 output of the 1x1 head."""
+        self._trunk()
+        a, o = self.a, self.layers["out"]
+        ops.conv(a["d0b"], o.wf, o.cout, a["out"], taps=1, bias=o.b, relu=False)
+        return a["out"]
+
+    def _trunk(self):
+        """Every layer but the 1x1 output head (its input is a["d0b"])."""
         a, L, c = self.a, self.layers, self.ch
         L["e0a"].forward(a["x0"], Act(a["e0a"], c[0]))
         L["e0b"].forward(a["e0a"], Act(a["cat0"], c[0], c[1]))
@@ -195,9 +203,6 @@ class UNet:
         ops.up2(Act(a["d1b"], c[1]), Act(a["cat0"], c[1], 0))
         L["d0a"].forward(a["cat0"], Act(a["d0a"], c[0]))
         L["d0b"].forward(a["d0a"], Act(a["d0b"], c[0]))
-        o = L["out"]
-        ops.conv(a["d0b"], o.wf, o.cout, a["out"], taps=1, bias=o.b, relu=False)
-        return a["out"]
 
     def _wgrad(self, lay: Conv, dz: torch.Tensor, x: Act):
         # straight from the NHWC activations (MN-major operands, no transposed copies)
@@ -259,18 +264,24 @@ class UNet:
             lay.step(lr, self.t)
 
     def train_step(self, x, scale, target, lr):
-        self.load(x, scale, target)
-        self.forward()
-        loss = self.loss_and_grad_seed()
+        """One Adam step on the residual MSE against scale * target; returns the loss (device FP64).
+        The head's epilogue computes the loss and its gradient seed from the channel-major target
+        (no packed target copy, no fp32 network output)."""
+        self.load(x, scale)
+        self._trunk()
+        o = self.layers["out"]
+        ops.conv_head(self.a["d0b"], o.wf, o.cout, o.b, self.a["x0"], scale, target=target.contiguous(),
+                      dout=self.g["out"], loss=self.loss)
         self.backward()
         self.step(lr)
-        return loss
+        return self.loss
 
     def predict(self, x: torch.Tensor, scale: torch.Tensor) -> torch.Tensor:
-        """Denoised channel-major maps [B][in_ch][H][W] (unscaled)."""
+        """Denoised channel-major maps [B][in_ch][H][W] (unscaled), written by the head's epilogue."""
         self.load(x, scale)
-        out = self.forward()
-        ops.predict_output(out, self.a["x0"], self.in_ch, scale, self.pred)
+        self._trunk()
+        o = self.layers["out"]
+        ops.conv_head(self.a["d0b"], o.wf, o.cout, o.b, self.a["x0"], scale, pred=self.pred)
         return self.pred
 
     # ------------------------------------------------------------------ state

@@ -109,6 +109,65 @@ def test_layout_pool_upsample_and_backward_kernels(C):
     assert torch.allclose(db.cpu(), skip.float().cpu()[..., :C].sum(dim=(0, 1, 2)), rtol=1e-4, atol=1e-3)
 
 
+@pytest.mark.parametrize("C,stride,off", [(32, 64, 0), (64, 192, 128), (256, 256, 0), (24, 64, 40), (33, 64, 0)])
+def test_bias_grad_sums_every_pixel_of_the_slice(C, stride, off):
+    B, H, W = 2, 64, 128
+    dz = _nhwc(B, H, W, stride, stride, 30 + C)
+    db = torch.full((C,), 0.5, device="cuda")
+    ops.bias_grad(Act(dz, C, off), db)
+    ops.check()
+    ref = dz.double().cpu()[..., off:off + C].sum(dim=(0, 1, 2)) + 0.5
+    assert torch.allclose(db.cpu().double(), ref, rtol=1e-5, atol=2e-3)
+
+
+@pytest.mark.parametrize("B,C,H,W", [(3, 33, 32, 64), (2, 64, 16, 16), (2, 70, 8, 24), (2, 5, 6, 10)])
+def test_pack_input_writes_scaled_bf16_rows(B, C, H, W):
+    """NHWC bf16 rows of x * scale[b] (round to nearest even), channels >= C untouched."""
+    g = torch.Generator().manual_seed(C)
+    x = torch.rand(B, C, H, W, generator=g) * 3
+    scale = torch.rand(B, generator=g) + 0.5
+    dst = torch.full((B, H, W, r64(C)), 7.0, dtype=torch.bfloat16, device="cuda")
+    ops.pack_input(x.cuda(), scale.cuda(), dst)
+    ops.check()
+    ref = (x * scale.view(B, 1, 1, 1)).permute(0, 2, 3, 1).bfloat16()
+    assert torch.equal(dst[..., :C].cpu(), ref)
+    assert bool((dst[..., C:].float() == 7.0).all())
+
+
+@pytest.mark.parametrize("cout,taps,cin", [(32, 9, 33), (128, 9, 96), (33, 1, 32), (70, 9, 45)])
+def test_adam_step_and_weight_copies(cout, taps, cin):
+    """One Adam step (bias-corrected, step 5) on the FP32 master weights, their BF16 forward copy and
+    the transposed, tap-flipped copy of the input-gradient pass: the tiled kernel (with the copy)
+    and the flat one (without) update identically, and both follow the formula in FP32."""
+    g = torch.Generator().manual_seed(cout * 100 + cin)
+    shp = (cout, taps, cin)
+    w0, m0 = torch.randn(*shp, generator=g), 0.01 * torch.randn(*shp, generator=g)
+    v0, g0 = 1e-3 * torch.rand(*shp, generator=g), torch.randn(*shp, generator=g)
+    cin_pad, cout_pad = r64(cin), r64(cout)
+    lr, b1, b2, eps, step = 1e-3, 0.9, 0.999, 1e-8, 5
+    outs = []
+    for with_wd in (False, True):
+        w, m, v, gr = (t.clone().cuda() for t in (w0, m0, v0, g0))
+        wf = torch.zeros((cout + 15) // 16 * 16, taps, cin_pad, dtype=torch.bfloat16, device="cuda")
+        wd = torch.zeros(cin, taps, cout_pad, dtype=torch.bfloat16, device="cuda") if with_wd else None
+        ops.adam(w, m, v, gr, cout, taps, cin, lr, b1, b2, eps, step, wf, cin_pad, wd, cout_pad if with_wd else 0)
+        outs.append((w, m, v, gr, wf, wd))
+    ops.check()
+    (w1, m1, v1, g1, wf1, _), (w2, m2, v2, g2, wf2, wd2) = outs
+    for a, b in ((w1, w2), (m1, m2), (v1, v2), (wf1, wf2)):
+        assert torch.equal(a, b)
+    assert not g1.any() and not g2.any()  # the gradient is consumed
+    assert torch.equal(wd2.permute(2, 1, 0).flip(1)[:cout].cpu(), wf2[:cout, :, :cin].cpu())
+    assert torch.equal(wf2[:cout, :, :cin].cpu(), w2.cpu().bfloat16())
+    f = lambda z: torch.tensor(z, dtype=torch.float32)  # the kernel's FP32 hyper-parameters
+    one, B1, B2 = f(1.0), f(b1), f(b2)
+    mi = B1 * m0 + (one - B1) * g0
+    vi = B2 * v0 + (one - B2) * g0 * g0
+    ref = w0 - f(lr) * (mi / (one - B1 ** step)) / (torch.sqrt(vi / (one - B2 ** step)) + f(eps))
+    assert torch.allclose(w2.cpu(), ref, rtol=1e-6, atol=1e-7)
+    assert torch.allclose(m2.cpu(), mi, rtol=1e-6, atol=1e-8) and torch.allclose(v2.cpu(), vi, rtol=1e-6, atol=0)
+
+
 def test_sample_scale_is_inverse_mean_fluence():
     g = torch.Generator().manual_seed(5)
     x = torch.rand(3, 5, 64, 32, generator=g) * torch.tensor([1.0, 1e-3, 7.0]).view(3, 1, 1, 1)
@@ -131,6 +190,51 @@ def test_predict_output_is_residual_then_unpack():
     got = torch.empty(B, C, H, W, device="cuda")
     ops.predict_output(out, x, C, scale, got)
     assert torch.allclose(got, ref, rtol=2e-7, atol=0)
+
+
+def _head_inputs(B, H, W, cout, seed):
+    g = torch.Generator().manual_seed(seed)
+    n_pad = (cout + 15) // 16 * 16
+    x = _nhwc(B, H, W, 32, 64, seed)                  # the head's input (d0b activations)
+    x0 = _nhwc(B, H, W, cout, 64, seed + 1, positive=True)  # the packed network input
+    w = torch.zeros(n_pad, 1, 64)
+    w[:cout, 0, :32] = 0.1 * torch.randn(cout, 32, generator=g)
+    bias = (0.01 * torch.randn(cout, generator=g)).cuda()
+    scale = (torch.rand(B, generator=g) + 0.5).cuda()
+    t = (torch.rand(B, cout, H, W, generator=g) + 0.5).cuda()
+    return x, w.bfloat16().cuda(), bias, x0, scale, t
+
+
+@pytest.mark.parametrize("B,H,W,cout", [(2, 16, 128, 33), (3, 16, 32, 20), (1, 8, 256, 48)])
+def test_fused_head_is_bit_identical_to_conv_then_output_kernels(B, H, W, cout):
+    """dn_conv_head against dn_conv (fp32 NHWC output) followed by dn_predict_output, and by
+    dn_pack_target + dn_mse: the prediction and the gradient seed are bit-identical, the loss equal
+    up to the order of its FP64 sum."""
+    x, w, bias, x0, scale, t = _head_inputs(B, H, W, cout, 40 + cout)
+    out = torch.zeros(B, H, W, (cout + 7) // 8 * 8, device="cuda")
+    ops.conv(x, w, cout, out, taps=1, bias=bias)
+    ref_pred = torch.empty(B, cout, H, W, device="cuda")
+    ops.predict_output(out, x0, cout, scale, ref_pred)
+    pred = torch.full((B, cout, H, W), float("nan"), device="cuda")
+    ops.conv_head(x, w, cout, bias, x0, scale, pred=pred)
+    ops.check()
+    assert torch.equal(pred, ref_pred)
+
+    tpk = torch.zeros(B, H, W, cout, device="cuda")
+    ops.pack_target(t, scale, tpk)
+    ref_dout = torch.zeros(B, H, W, 64, dtype=torch.bfloat16, device="cuda")
+    ref_loss = torch.zeros((), dtype=torch.float64, device="cuda")
+    ops.mse(out, x0, tpk, cout, ref_dout, ref_loss)
+    dout = torch.zeros_like(ref_dout)
+    loss = torch.zeros_like(ref_loss)
+    ops.conv_head(x, w, cout, bias, x0, scale, target=t, dout=dout, loss=loss)
+    ops.check()
+    assert torch.equal(dout, ref_dout)
+    assert abs(loss.item() - ref_loss.item()) <= 1e-12 * ref_loss.item()
+    # and against the definition in FP64 on the CPU
+    y = x0[..., :cout].double().cpu() + out[..., :cout].double().cpu()
+    r = y - (t.cpu().permute(0, 2, 3, 1).double() * scale.cpu().double().view(B, 1, 1, 1))
+    assert abs(loss.item() - (r ** 2).mean().item()) <= 1e-5 * loss.item()
 
 
 def _data(B, H, W, C, seed):
