@@ -302,6 +302,28 @@ int dn_wgrad_nhwc(dn_slice dz, dn_slice x, int32_t B, int32_t H, int32_t W, int3
   a.cout = cout;
   a.cin = cin;
   a.cin_pad = cin;
+  a.dw = dw;
+  a.err = err;
+  if (wgrad_halo_applies(taps, cout, W)) {  // few output channels: all nine taps from one haloed box
+    CUtensorMap tmH;
+    const uint64_t dims[4] = {(uint64_t)cin, (uint64_t)W, (uint64_t)H, (uint64_t)B};
+    const uint64_t strides[3] = {(uint64_t)x.stride * 2, (uint64_t)W * x.stride * 2, HW * x.stride * 2};
+    const uint32_t box[4] = {64, 66, 3, 1};
+    void *base = static_cast<char *>(x.data) + (size_t)x.off * 2;
+    if (encode_tiled(&tmH, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box,
+                     CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+      return MCR_ERR_CUDA;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return MCR_ERR_CUDA;
+    const long long segs = (long long)B * HW / 64;
+    long long splits = sms / ((cin + 63) / 64);  // one block per SM, one wave
+    if (splits > segs) splits = segs;
+    if (splits < 1) splits = 1;
+    a.splits = (int)splits;
+    if (launch_wgrad_halo(tmA, tmH, a, (cudaStream_t)stream) != cudaSuccess) return MCR_ERR_CUDA;
+    return MCR_OK;
+  }
   a.N = cin > 128 ? 128 : ((cin + 15) / 16) * 16;  // MMA N; B arrives in whole 64-channel boxes
   a.m_tiles = (cout + 127) / 128;
   a.n_tiles = (cin + a.N - 1) / a.N;
@@ -313,8 +335,6 @@ int dn_wgrad_nhwc(dn_slice dz, dn_slice x, int32_t B, int32_t H, int32_t W, int3
   uint32_t cols = 32;
   while (cols < (uint32_t)a.N) cols <<= 1;
   a.tmem_cols = cols;
-  a.dw = dw;
-  a.err = err;
   if (launch_wgrad_mn(tmA, tmB, a, (cudaStream_t)stream) != cudaSuccess) return MCR_ERR_CUDA;
   return MCR_OK;
 }

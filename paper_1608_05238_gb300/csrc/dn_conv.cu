@@ -809,6 +809,127 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
 }
 
+// k_wgrad_halo: weight gradient of a 3x3 layer with cout <= 64 on rows of whole 64-pixel
+// segments, all nine taps from one haloed input box per segment:
+//   D[(tap, c)][o] = sum_p X[p + d_tap][c] dZ[p][o],
+// M = 128 = two taps x 64 input channels (of channel block blockIdx.y), N = 64 (cout, zero
+// filled), K = 64-pixel row segments in 16-pixel steps.  A stage holds the haloed box of X
+// (channels of the block, columns x0-1 .. x0+64, rows y-1 .. y+1; zero fill outside the image)
+// and the dZ box {64 channels, 64 pixels}.  Tap (ky, kx)'s window starts ky 66 + kx pixel rows
+// into the box; an MMA's second 64-channel M group is the next tap's window (leading byte offset =
+// the distance of the two windows; for tap 8 a dummy window one row further, whose rows are
+// discarded).  Five accumulators of 64 columns (taps 0-1, 2-3, 4-5, 6-7, 8) stay in TMEM for
+// the CTA's contiguous range of segments; the epilogue adds them into dw with one atomic per
+// element (consecutive lanes = consecutive input channels).  Per segment the CTA reads 25 KB of
+// X and 8 KB of dZ instead of 9 x (8 + 8) KB for nine separate shifted GEMMs.
+constexpr uint32_t kWhBytes = 3 * 66 * 128;                          // 25,344 B written by the box
+constexpr uint32_t kWhStride = (kWhBytes + 1023) & ~1023u;           // 25,600 B
+constexpr uint32_t kWhStage = kWhStride + 8192;                      // + dZ box
+constexpr int kWhStages = 4;
+
+__global__ void __launch_bounds__(128, 1)
+    k_wgrad_halo(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtensorMap tmH, const WgradArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kWhStages * kWhStage);
+  uint64_t *empty = full + kWhStages;
+  uint64_t *done = empty + kWhStages;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int split = blockIdx.x, cb = blockIdx.y;
+  if (tid == 0) {
+    for (int s = 0; s < kWhStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    fence_barrier_init();
+    prefetch_tensormap(&tmZ);
+    prefetch_tensormap(&tmH);
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int segs_per_image = a.HW / 64, segs_per_row = a.W / 64;
+  const int total = a.B * segs_per_image;
+  const int k_begin = (int)((long long)total * split / a.splits);
+  const int k_end = (int)((long long)total * (split + 1) / a.splits);
+  const int nk = k_end - k_begin;
+
+  if (warp == 0 && lane == 0) {
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kWhStages, r = i / kWhStages;
+      if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1)) {
+        atomicOr(a.err, 8192u);
+        break;
+      }
+      const int kb = k_begin + i;
+      const int b = kb / segs_per_image, sg = kb % segs_per_image;
+      const int y0 = sg / segs_per_row, x0 = (sg % segs_per_row) * 64;
+      uint8_t *st = smem + (size_t)s * kWhStage;
+      mbar_arrive_expect_tx(&full[s], kWhBytes + 8192u);
+      tma_load_4d(st, &tmH, &full[s], cb * 64, x0 - 1, y0 - 1, b);
+      tma_load_2d(st + kWhStride, &tmZ, &full[s], 0, b * a.HW + sg * 64);
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_bf16_f32(kBlockM, 64) | (1u << 15) | (1u << 16);  // A, B MN-major
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kWhStages, r = i / kWhStages;
+      if (!mbar_wait(&full[s], r & 1)) {
+        atomicOr(a.err, 16384u);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t hBase = smem_u32(smem + (size_t)s * kWhStage), zBase = hBase + kWhStride;
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint64_t bdesc = sdesc_mn128(zBase + ks * 2048);
+#pragma unroll
+        for (int mt = 0; mt < 5; ++mt) {
+          const int t0 = 2 * mt;
+          const uint32_t r0 = (uint32_t)((t0 / 3) * 66 + t0 % 3);
+          const uint32_t r1 = t0 < 8 ? (uint32_t)(((t0 + 1) / 3) * 66 + (t0 + 1) % 3) : r0 + 1;
+          mma_bf16(tmem + mt * 64, sdesc_mn128_lbo(hBase + (r0 + 16 * ks) * 128, (r1 - r0) * 128), bdesc, idesc,
+                   (i > 0 || ks > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+
+  const bool have = nk > 0 && __all_sync(0xffffffffu, mbar_wait(done, 0));
+  if (nk > 0 && !have && tid == 0) atomicOr(a.err, 32768u);
+  tc_fence_after();
+  const int mrow = warp * 32 + lane;  // M row of this thread: tap offset mrow / 64, channel mrow % 64
+  const int c = cb * 64 + (mrow & 63);
+  for (int mt = 0; mt < 5; ++mt) {
+    const int tap = 2 * mt + (mrow >> 6);
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + mt * 64;
+    for (int c0 = 0; c0 < a.cout; c0 += 16) {
+      uint32_t v[16];
+      tmem_ld16(trow + (uint32_t)c0, v);
+      tmem_ld_wait();
+      if (!have || tap > 8 || c >= a.cin) continue;
+      float *o = a.dw + (size_t)tap * a.cin_pad + c;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (c0 + j < a.cout) atomicAdd(o + (size_t)(c0 + j) * 9 * a.cin_pad, __uint_as_float(v[j]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
 }  // namespace
 
 cudaError_t launch_wgrad_tc(const CUtensorMap &tmA, const CUtensorMap tmB[3], const WgradArgs &a, cudaStream_t s) {
@@ -915,6 +1036,21 @@ cudaError_t launch_conv_halo(const CUtensorMap &tmH, const CUtensorMap &tmW, Con
   const long long tiles = (long long)a.B * a.H * a.W / kBlockM;
   const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
   k_conv_halo<<<grid, kWsThreads, smem, s>>>(tmH, tmW, a, st, (int)tiles);
+  return cudaGetLastError();
+}
+
+bool wgrad_halo_applies(int taps, int cout, int W) { return taps == 9 && cout <= 64 && W % 64 == 0; }
+
+cudaError_t launch_wgrad_halo(const CUtensorMap &tmZ, const CUtensorMap &tmH, const WgradArgs &a, cudaStream_t s) {
+  const size_t smem = 1024 + kWhStages * (size_t)kWhStage + 256;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int cblocks = (a.cin + 63) / 64;
+  k_wgrad_halo<<<dim3((unsigned)a.splits, (unsigned)cblocks), 128, smem, s>>>(tmZ, tmH, a);
   return cudaGetLastError();
 }
 

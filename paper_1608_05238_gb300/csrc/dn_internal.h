@@ -61,6 +61,10 @@ struct WgradArgs {
 };
 cudaError_t launch_wgrad_tc(const CUtensorMap &tmA, const CUtensorMap tmB[3], const WgradArgs &a, cudaStream_t s);
 cudaError_t launch_wgrad_mn(const CUtensorMap &tmA, const CUtensorMap &tmB, const WgradArgs &a, cudaStream_t s);
+// 3x3 weight gradient with cout <= 64 on rows of 64-pixel segments: one haloed X box {64, 66, 3, 1}
+// per segment serves all nine taps (grid: splits x 64-channel blocks of cin; one block per SM)
+bool wgrad_halo_applies(int taps, int cout, int W);
+cudaError_t launch_wgrad_halo(const CUtensorMap &tmZ, const CUtensorMap &tmH, const WgradArgs &a, cudaStream_t s);
 
 // memory-bound kernels (dn_ops.cu)
 cudaError_t to_ct(const __nv_bfloat16 *src, int B, int HW, int W, int stride, int off, int C, int shifted,

@@ -133,6 +133,19 @@ __device__ __forceinline__ uint64_t sdesc_mn128(uint32_t smem_addr) {
   return d;
 }
 
+// The same with a chosen distance (bytes, multiple of 16) between the 64-element groups along M:
+// two such groups may be any two 128-byte-row windows of one swizzled buffer (the swizzle
+// follows the address bits, so a window may start at any row).
+__device__ __forceinline__ uint64_t sdesc_mn128_lbo(uint32_t smem_addr, uint32_t lbo_bytes) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
 // Instruction descriptor of tcgen05.mma kind::f16 with BF16 A and B (both K-major), FP32 D:
 // D format [4,6) = 1 (F32), A format [7,10) = 1 (BF16), B format [10,13) = 1 (BF16),
 // N >> 3 at [17,23), M >> 4 at [24,29).

@@ -49,7 +49,10 @@ def test_wgrad_matches_autograd(B, H, W, cin, cout, taps):
 
 @pytest.mark.parametrize("B,H,W,cin,cout,taps,xoff,zoff", [(2, 16, 32, 64, 32, 9, 0, 0), (1, 32, 64, 96, 128, 9, 64, 0),
                                                             (2, 16, 16, 33, 48, 1, 0, 64), (1, 8, 128, 200, 256, 9, 0, 0),
-                                                            (3, 4, 16, 40, 33, 9, 24, 8), (1, 64, 256, 32, 32, 9, 32, 0)])
+                                                            (3, 4, 16, 40, 33, 9, 24, 8), (1, 64, 256, 32, 32, 9, 32, 0),
+                                                            # haloed nine-tap kernel (cout <= 64, W % 64 == 0)
+                                                            (2, 8, 64, 33, 32, 9, 0, 0), (1, 16, 128, 96, 64, 9, 0, 0),
+                                                            (2, 4, 128, 192, 33, 9, 8, 0), (1, 3, 64, 64, 16, 9, 0, 64)])
 def test_wgrad_nhwc_matches_autograd(B, H, W, cin, cout, taps, xoff, zoff):
     """The weight gradient read straight from NHWC slices (MN-major operands, tap shifts as TMA
     coordinates) equals FP64 autograd of the convolution, also for slices at channel offsets."""
