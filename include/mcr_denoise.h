@@ -71,9 +71,10 @@ typedef struct {
  *   y = x0 + conv(x, w) + bias  (per pixel, channels < cout)
  *   DN_HEAD_PREDICT: pred[b][c][p] = y / scale[b]              (channel-major maps)
  *   DN_HEAD_LOSS:    r = y - scale[b] target[b][c][p];  dout = bf16(2 r / (B H W cout));
- *                    loss = sum r^2 / (B H W cout), FP64, from per-warp partial sums in a fixed order
+ *                    loss = sum r^2 / (B H W cout): FP32 sums over 16 channels of a pixel, FP64 across
+ *                    them and over per-warp partial sums in a fixed order (deterministic)
  * Bit-identical to dn_conv + dn_predict_output (prediction) and, for dout, to dn_conv + dn_pack_target
- * + dn_mse (loss; the loss itself differs only in the order of its FP64 sum).  Uses the library's
+ * + dn_mse (whose loss sums every square in FP64: the two losses agree to ~1e-6 relative).  Uses the library's
  * reduction scratch: calls on one device must not overlap.  MCR_ERR_ARG on a bad shape or pointer.
  */
 int dn_conv_head(const dn_conv_desc *d, const dn_head_desc *h, void *stream);
@@ -138,6 +139,20 @@ int dn_adam(float *w, float *m, float *v, float *g, int32_t cout, int32_t taps, 
             float beta2, float eps, int32_t step, void *wf, int32_t cin_pad, void *wd, int32_t cout_pad, void *stream);
 int dn_adam_bias(float *b, float *m, float *v, float *g, int32_t n, float lr, float beta1, float beta2, float eps,
                  int32_t step, void *stream);
+/* Every layer's dn_adam (and, where b != NULL, dn_adam_bias) step in one launch: the same
+ * arithmetic and outputs as the per-layer calls.  layers: host array of n <= 32 descriptors (read
+ * during the call only); all pointers device memory. */
+typedef struct {
+  float *w, *m, *v, *g;     /* fp32 [cout][taps][cin]: master weights, moments, gradient (zeroed) */
+  void *wf;                 /* bf16 [>= cout][taps][cin_pad] forward copy */
+  int32_t cin_pad;
+  void *wd;                 /* bf16 flipped input-gradient copy [cin][taps][cout_pad], or NULL */
+  int32_t cout_pad;
+  int32_t cout, taps, cin;
+  float *b, *mb, *vb, *gb;  /* fp32 [cout] bias, its moments and gradient (zeroed), or b = NULL */
+} dn_adam_layer;
+int dn_adam_multi(const dn_adam_layer *layers, int32_t n, float lr, float beta1, float beta2, float eps, int32_t step,
+                  void *stream);
 /* Per-sample input scale of channel-major fp32 maps [B][C][HW] (device): scale[b] = 1 / mean of
  * channel 0 (the fluence a_0) over the HW pixels of sample b, clamped below at 1e-30; FP64 sum in
  * a fixed order.  scale: device out [B] fp32. */

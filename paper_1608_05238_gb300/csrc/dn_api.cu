@@ -406,6 +406,41 @@ int dn_adam(float *w, float *m, float *v, float *g, int32_t cout, int32_t taps, 
               static_cast<__nv_bfloat16 *>(wd), cout_pad, (cudaStream_t)stream));
 }
 
+int dn_adam_multi(const dn_adam_layer *layers, int32_t n, float lr, float beta1, float beta2, float eps, int32_t step,
+                  void *stream) {
+  if (!layers || n < 1 || n > kMaxAdamLayers) return MCR_ERR_ARG;
+  AdamTable T{};
+  T.n = n;
+  long long blocks = 0;
+  for (int l = 0; l < n; ++l) {
+    const dn_adam_layer &d = layers[l];
+    if (!d.w || !d.wf || d.cout <= 0 || d.cin <= 0 || d.cin_pad < d.cin || (d.taps != 9 && d.taps != 1)) return MCR_ERR_ARG;
+    if (step > 0 && (!d.m || !d.v || !d.g)) return MCR_ERR_ARG;
+    if (d.wd && d.cout_pad < d.cout) return MCR_ERR_ARG;
+    if (d.b && step > 0 && (!d.mb || !d.vb || !d.gb)) return MCR_ERR_ARG;
+    AdamLayer &L = T.L[l];
+    L.w = d.w;
+    L.m = d.m;
+    L.v = d.v;
+    L.g = d.g;
+    L.wf = static_cast<__nv_bfloat16 *>(d.wf);
+    L.wd = static_cast<__nv_bfloat16 *>(d.wd);
+    L.b = d.b;
+    L.mb = d.mb;
+    L.vb = d.vb;
+    L.gb = d.gb;
+    L.cout = d.cout;
+    L.taps = d.taps;
+    L.cin = d.cin;
+    L.cin_pad = d.cin_pad;
+    L.cout_pad = d.cout_pad;
+    L.tile0 = (int)blocks;
+    blocks += (long long)d.taps * ((d.cout + 31) / 32) * ((d.cin + 31) / 32);
+  }
+  if (blocks > 0x7fffffffll) return MCR_ERR_ARG;
+  DN_TRY(adam_multi(T, lr, beta1, beta2, eps, step, (int)blocks, (cudaStream_t)stream));
+}
+
 int dn_adam_bias(float *b, float *m, float *v, float *g, int32_t n, float lr, float beta1, float beta2,
                  float eps, int32_t step, void *stream) {
   if (!b || !m || !v || !g || n <= 0) return MCR_ERR_ARG;

@@ -81,18 +81,18 @@ __device__ __forceinline__ double head_chunk(const ConvArgs &a, long long p, lon
     return 0.0;
   }
   const float *t = a.target + (bi * a.cout + c0) * a.HW + pi;
-  float g[16];
-  double ss = 0.0;
+  float g[16], sq = 0.f;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     g[j] = 0.f;
     if (j < valid) {
       // the scaled target rounded on its own, as a stored scaled copy would be
       const float r = xv[j] + f[j] - __fmul_rn(t[(long long)j * a.HW], hs);
-      ss += (double)__fmul_rn(r, r);
+      sq = __fmaf_rn(r, r, sq);
       g[j] = r * a.two_over_count;
     }
   }
+  const double ss = (double)sq;  // FP32 within 16 channels, FP64 across them
   __nv_bfloat16 *o = a.dout + p * a.dout_stride + c0;
   if (valid >= 16) {
     __align__(16) __nv_bfloat162 h[8];
@@ -196,17 +196,18 @@ __device__ __forceinline__ double drain_row_t(const ConvArgs &a, long long p, ui
         for (int j = 0; j < 16; ++j)
           if (j < valid) o[(long long)j * a.HW] = (xv[j] + f[j]) * hs;
       } else {
-        float g[16];
+        float g[16], sq = 0.f;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           g[j] = 0.f;
           if (j < valid) {
             // the scaled target rounded on its own, as a stored scaled copy would be
             const float r = xv[j] + f[j] - __fmul_rn(tv[HEAD ? k : 0][j], hs);
-            ss += (double)__fmul_rn(r, r);
+            sq = __fmaf_rn(r, r, sq);
             g[j] = r * a.two_over_count;
           }
         }
+        ss += (double)sq;  // FP32 within 16 channels, FP64 across them (FP64 is a slow pipe here)
         store_bf16x16(a.dout + p * a.dout_stride + c0, valid, g);
       }
       continue;

@@ -79,6 +79,21 @@ cudaError_t up2(const __nv_bfloat16 *src, int B, int H, int W, int sstride, int 
 cudaError_t up2_bwd(const __nv_bfloat16 *du, int ustride, int uoff, const __nv_bfloat16 *act, int astride, int aoff,
                     int B, int H, int W, int C, __nv_bfloat16 *dz, int zstride, int zoff, cudaStream_t s);
 cudaError_t bias_grad(const __nv_bfloat16 *dz, long long P, int stride, int off, int C, float *db, cudaStream_t s);
+// One layer of a multi-tensor Adam step (k_adam_multi): tile0 = its first block.
+struct AdamLayer {
+  float *w, *m, *v, *g;
+  __nv_bfloat16 *wf, *wd;
+  float *b, *mb, *vb, *gb;
+  int cout, taps, cin, cin_pad, cout_pad;
+  int tile0;
+};
+constexpr int kMaxAdamLayers = 32;
+struct AdamTable {
+  AdamLayer L[kMaxAdamLayers];
+  int n;
+};
+cudaError_t adam_multi(const AdamTable &T, float lr, float b1, float b2, float eps, int step, int blocks,
+                       cudaStream_t s);
 // loss = scale * (sum of partials[0..n)) in one block, fixed order
 cudaError_t sum_partials(const double *partials, int n, double scale, double *loss, cudaStream_t s);
 cudaError_t mse(const float *out, int ostride, const __nv_bfloat16 *x, int xstride, const float *t, long long P, int C,

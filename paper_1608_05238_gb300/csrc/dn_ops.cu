@@ -216,13 +216,14 @@ __global__ void k_bias_grad(const __nv_bfloat16 *__restrict__ dz, long long P, i
   }
 }
 
-// db[c] += sum over pixels of dz[p][off + c] with 16-byte loads: G = C / 8 threads cover one
-// pixel row (8 channels each), 256 / G rows per pass of the block; per-thread FP32 sums, a
+// db[c] += sum over pixels of dz[p][off + c] (c < C) with 16-byte loads: G = ceil(C / 8) threads
+// cover one pixel row (8 channels each; the row holds at least 8 G channels from off, those past
+// C are read and dropped), 256 / G rows per pass of the block; per-thread FP32 sums, a
 // fixed-order sum over the block's rows in shared memory, one atomic add per channel and block.
 __global__ void __launch_bounds__(256) k_bias_grad_v8(const __nv_bfloat16 *__restrict__ dz, long long P, int stride,
-                                                      int off, int G, float *__restrict__ db) {
+                                                      int off, int G, int C, float *__restrict__ db) {
   __shared__ float red[256 * 8];
-  const int R = 256 / G, t = threadIdx.x, g = t % G, r = t / G, C = 8 * G;
+  const int R = 256 / G, t = threadIdx.x, g = t % G, r = t / G, CG = 8 * G;
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (r < R) {
 #pragma unroll 4
@@ -237,12 +238,12 @@ __global__ void __launch_bounds__(256) k_bias_grad_v8(const __nv_bfloat16 *__res
       }
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) red[r * C + 8 * g + j] = acc[j];
+    for (int j = 0; j < 8; ++j) red[r * CG + 8 * g + j] = acc[j];
   }
   __syncthreads();
   for (int c = t; c < C; c += 256) {
     float sum = 0.f;
-    for (int k = 0; k < R; ++k) sum += red[k * C + c];
+    for (int k = 0; k < R; ++k) sum += red[k * CG + c];
     atomicAdd(db + c, sum);
   }
 }
@@ -300,23 +301,31 @@ __global__ void k_residual(const float *__restrict__ out, int ostride, const __n
 // Adam on the FP32 master weights [cout][taps][cin] and bias; writes the forward BF16 copy
 // wf [n_pad][taps][cin_pad] and the input-gradient copy wd [cin_npad][taps][cout_pad] with the
 // taps flipped (wd[c][8 - t][n] = w[n][t][c] for 3x3).
+// One Adam step on element i (bias-corrected moments; c1 = 1 - b1^t, c2 = 1 - b2^t); the
+// gradient is consumed (set to zero).  Returns the new weight.
+__device__ __forceinline__ float adam_elem(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                                           float *__restrict__ g, size_t i, float lr, float b1, float b2, float eps,
+                                           float c1, float c2) {
+  // explicit roundings, so that every kernel that inlines this computes the same bits
+  const float gi = g[i];
+  g[i] = 0.f;  // the gradient is consumed: the next backward pass accumulates from zero
+  const float mi = __fmaf_rn(b1, m[i], __fmul_rn(1.f - b1, gi));
+  const float vi = __fmaf_rn(b2, v[i], __fmul_rn(__fmul_rn(1.f - b2, gi), gi));
+  m[i] = mi;
+  v[i] = vi;
+  const float step = __fdiv_rn(__fmul_rn(lr, __fdiv_rn(mi, c1)), __fadd_rn(__fsqrt_rn(__fdiv_rn(vi, c2)), eps));
+  const float wi = __fsub_rn(w[i], step);
+  w[i] = wi;
+  return wi;
+}
+
 __global__ void k_adam(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
                        float *__restrict__ g, int cout, int taps, int cin, float lr, float b1, float b2,
                        float eps, float c1, float c2, __nv_bfloat16 *__restrict__ wf, int cin_pad,
                        __nv_bfloat16 *__restrict__ wd, int cout_pad, int step) {
   const long long n = (long long)cout * taps * cin;
   for (long long i = blockIdx.x * (long long)kT + threadIdx.x; i < n; i += (long long)gridDim.x * kT) {
-    float wi = w[i];
-    if (step > 0) {
-      const float gi = g[i];
-      g[i] = 0.f;  // the gradient is consumed: the next backward pass accumulates from zero
-      const float mi = b1 * m[i] + (1.f - b1) * gi;
-      const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-      m[i] = mi;
-      v[i] = vi;
-      wi -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-      w[i] = wi;
-    }
+    const float wi = step > 0 ? adam_elem(w, m, v, g, (size_t)i, lr, b1, b2, eps, c1, c2) : w[i];
     const int c = (int)(i % cin);
     const int t = (int)((i / cin) % taps);
     const int o = (int)(i / ((long long)cin * taps));
@@ -338,17 +347,7 @@ __global__ void k_adam_t(float *__restrict__ w, float *__restrict__ m, float *__
     const int o = o0 + r, c = c0 + threadIdx.x;
     if (o < cout && c < cin) {
       const size_t i = ((size_t)o * taps + t) * cin + c;
-      float wi = w[i];
-      if (step > 0) {
-        const float gi = g[i];
-        g[i] = 0.f;
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        wi -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-        w[i] = wi;
-      }
+      const float wi = step > 0 ? adam_elem(w, m, v, g, i, lr, b1, b2, eps, c1, c2) : w[i];
       const __nv_bfloat16 h = __float2bfloat16_rn(wi);
       wf[((size_t)o * taps + t) * cin_pad + c] = h;
       tile[r][threadIdx.x] = h;
@@ -365,14 +364,40 @@ __global__ void k_adam_bias(float *__restrict__ b, float *__restrict__ m, float 
                             float *__restrict__ g, int n, float lr, float b1, float b2, float eps, float c1,
                             float c2) {
   const int i = blockIdx.x * kT + threadIdx.x;
-  if (i >= n) return;
-  const float gi = g[i];
-  g[i] = 0.f;
-  const float mi = b1 * m[i] + (1.f - b1) * gi;
-  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-  m[i] = mi;
-  v[i] = vi;
-  b[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  if (i < n) adam_elem(b, m, v, g, (size_t)i, lr, b1, b2, eps, c1, c2);
+}
+
+// All layers' Adam steps in one launch: block -> (layer, 32 x 32 (cout x cin) tile of one tap) by
+// the table's first-block indices; the tile body is k_adam_t's (wd optional) and block 0 of a
+// layer also steps its bias.  Same arithmetic as the per-layer kernels.
+__global__ void k_adam_multi(const __grid_constant__ AdamTable T, float lr, float b1, float b2, float eps, float c1,
+                             float c2, int step) {
+  __shared__ __nv_bfloat16 tile[32][34];
+  int l = 0;
+  while (l + 1 < T.n && (int)blockIdx.x >= T.L[l + 1].tile0) ++l;
+  const AdamLayer &L = T.L[l];
+  const int local = (int)blockIdx.x - L.tile0;
+  const int ct = (L.cin + 31) / 32, ot = (L.cout + 31) / 32;
+  const int c0 = (local % ct) * 32, o0 = ((local / ct) % ot) * 32, t = local / (ct * ot);
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int o = o0 + r, c = c0 + threadIdx.x;
+    if (o < L.cout && c < L.cin) {
+      const size_t i = ((size_t)o * L.taps + t) * L.cin + c;
+      const float wi = step > 0 ? adam_elem(L.w, L.m, L.v, L.g, i, lr, b1, b2, eps, c1, c2) : L.w[i];
+      const __nv_bfloat16 h = __float2bfloat16_rn(wi);
+      L.wf[((size_t)o * L.taps + t) * L.cin_pad + c] = h;
+      tile[r][threadIdx.x] = h;
+    }
+  }
+  if (local == 0 && L.b && step > 0)
+    for (int i = tid; i < L.cout; i += 256) adam_elem(L.b, L.mb, L.vb, L.gb, (size_t)i, lr, b1, b2, eps, c1, c2);
+  if (!L.wd) return;  // uniform over the block
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int c = c0 + r, o = o0 + threadIdx.x;
+    if (o < L.cout && c < L.cin) L.wd[((size_t)c * L.taps + (L.taps - 1 - t)) * L.cout_pad + o] = tile[threadIdx.x][r];
+  }
 }
 
 // Layout changes between channel-major [B][C][HW] maps (the MC's output) and pixel-major NHWC
@@ -575,11 +600,12 @@ cudaError_t up2_bwd(const __nv_bfloat16 *du, int ustride, int uoff, const __nv_b
   return cudaGetLastError();
 }
 cudaError_t bias_grad(const __nv_bfloat16 *dz, long long P, int stride, int off, int C, float *db, cudaStream_t s) {
-  if (al8(C, stride, off, 0) && C / 8 <= 256 && (reinterpret_cast<uintptr_t>(dz) & 15) == 0) {
-    const int G = C / 8, R = 256 / G;
+  const int G = (C + 7) / 8;
+  if (al8(stride, off, 0, 0) && G <= 256 && off + 8 * G <= stride && (reinterpret_cast<uintptr_t>(dz) & 15) == 0) {
+    const int R = 256 / G;
     long long gx = (P + 4LL * R - 1) / (4LL * R);  // at least ~4 rows per thread
     if (gx > 152 * 8) gx = 152 * 8;
-    k_bias_grad_v8<<<(unsigned)gx, 256, 0, s>>>(dz, P, stride, off, G, db);
+    k_bias_grad_v8<<<(unsigned)gx, 256, 0, s>>>(dz, P, stride, off, G, C, db);
     return cudaGetLastError();
   }
   long long gx = (P + 8 * 64 - 1) / (8 * 64);
@@ -623,6 +649,12 @@ cudaError_t adam(float *w, float *m, float *v, float *g, int cout, int taps, int
   }
   k_adam<<<blocks_for((long long)cout * taps * cin), kT, 0, s>>>(w, m, v, g, cout, taps, cin, lr, b1, b2, eps, c1, c2,
                                                                   wf, cin_pad, wd, cout_pad, step);
+  return cudaGetLastError();
+}
+cudaError_t adam_multi(const AdamTable &T, float lr, float b1, float b2, float eps, int step, int blocks,
+                       cudaStream_t s) {
+  const float c1 = step > 0 ? 1.f - powf(b1, (float)step) : 1.f, c2 = step > 0 ? 1.f - powf(b2, (float)step) : 1.f;
+  k_adam_multi<<<blocks, dim3(32, 8), 0, s>>>(T, lr, b1, b2, eps, c1, c2, step);
   return cudaGetLastError();
 }
 cudaError_t adam_bias(float *b, float *m, float *v, float *g, int n, float lr, float b1, float b2, float eps,

@@ -31,12 +31,19 @@ class _HeadDesc(C.Structure):
 HEAD_PREDICT, HEAD_LOSS = 1, 2
 
 
+class _AdamLayer(C.Structure):
+    _fields_ = [("w", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p), ("g", C.c_void_p), ("wf", C.c_void_p),
+                ("cin_pad", C.c_int32), ("wd", C.c_void_p), ("cout_pad", C.c_int32), ("cout", C.c_int32),
+                ("taps", C.c_int32), ("cin", C.c_int32), ("b", C.c_void_p), ("mb", C.c_void_p), ("vb", C.c_void_p),
+                ("gb", C.c_void_p)]
+
+
 class _Slice(C.Structure):
     _fields_ = [("data", C.c_void_p), ("stride", C.c_int32), ("off", C.c_int32)]
 
 
 EXPORTS = ("dn_conv", "dn_conv_head", "dn_wgrad", "dn_wgrad_nhwc", "dn_to_ct", "dn_pool2", "dn_pool2_bwd", "dn_up2", "dn_up2_bwd", "dn_bias_grad",
-           "dn_mse", "dn_residual", "dn_adam", "dn_adam_bias", "dn_pack_input", "dn_sample_scale", "dn_pack_target", "dn_predict_output",
+           "dn_mse", "dn_residual", "dn_adam", "dn_adam_bias", "dn_adam_multi", "dn_pack_input", "dn_sample_scale", "dn_pack_target", "dn_predict_output",
            "dn_unpack_output", "dn_check")
 
 
@@ -61,6 +68,7 @@ def lib():
             "dn_residual": [vp, i32, vp, i32, i64, i32, vp, vp],
             "dn_adam": [vp, vp, vp, vp, i32, i32, i32, f32, f32, f32, f32, i32, vp, i32, vp, i32, vp],
             "dn_adam_bias": [vp, vp, vp, vp, i32, f32, f32, f32, f32, i32, vp],
+            "dn_adam_multi": [C.POINTER(_AdamLayer), i32, f32, f32, f32, f32, i32, vp],
             "dn_pack_input": [vp, vp, i32, i64, i32, vp, i32, vp],
             "dn_sample_scale": [vp, i32, i64, i32, vp, vp],
             "dn_pack_target": [vp, vp, i32, i64, i32, vp, vp],
@@ -170,6 +178,23 @@ def adam(w, m, v, g, cout, taps, cin, lr, b1, b2, eps, step, wf, cin_pad, wd=Non
 
 def adam_bias(b, m, v, g, lr, b1, b2, eps, step, stream=None):
     _call("dn_adam_bias", _p(b), _p(m), _p(v), _p(g), b.numel(), lr, b1, b2, eps, step, _stream(stream))
+
+
+def adam_table(layers):
+    """Descriptors of dn_adam_multi from tuples (w, m, v, g, wf, cin_pad, wd, cout_pad, cout, taps, cin,
+    b, mb, vb, gb) of tensors / ints (wd, b may be None).  The tensors must outlive the table."""
+    arr = (_AdamLayer * len(layers))()
+    for i, (w, m, v, g, wf, cin_pad, wd, cout_pad, cout, taps, cin, b, mb, vb, gb) in enumerate(layers):
+        arr[i] = _AdamLayer(w.data_ptr(), m.data_ptr(), v.data_ptr(), g.data_ptr(), wf.data_ptr(), cin_pad,
+                            None if wd is None else wd.data_ptr(), cout_pad, cout, taps, cin,
+                            None if b is None else b.data_ptr(), None if mb is None else mb.data_ptr(),
+                            None if vb is None else vb.data_ptr(), None if gb is None else gb.data_ptr())
+    return arr
+
+
+def adam_multi(table, lr, b1, b2, eps, step, stream=None):
+    """Every layer of ``table`` (``adam_table``) stepped in one launch (``dn_adam_multi``)."""
+    _call("dn_adam_multi", table, len(table), lr, b1, b2, eps, step, _stream(stream))
 
 
 def pack_input(src: torch.Tensor, scale: torch.Tensor, dst: torch.Tensor, stream=None):

@@ -62,6 +62,11 @@ class Conv:
                  self.cin_pad, self.wd, self.dz_stride)
         ops.adam_bias(self.b, self.mb, self.vb, self.gb, lr, b1, b2, eps, t)
 
+    def adam_entry(self):
+        """This layer's descriptor for the multi-tensor Adam step (``ops.adam_table``)."""
+        return (self.w, self.m, self.v, self.gw, self.wf, self.cin_pad, self.wd, self.dz_stride, self.cout, self.taps,
+                self.cin, self.b, self.mb, self.vb, self.gb)
+
     def forward(self, x: torch.Tensor, out: Act, f32: bool = False):
         assert x.shape[3] == self.cin_pad, (self.name, x.shape, self.cin_pad)
         ops.conv(x, self.wf, self.cout, out.t, taps=self.taps, bias=self.b, relu=self.relu, out_off=out.off)
@@ -109,6 +114,7 @@ class UNet:
                 return self.ch[spec]
             return self.ch[int(spec[0])] + self.ch[int(spec[1])]
 
+        self._adam = None  # multi-tensor Adam descriptors, built on the first step
         self.layers = {}
         for name, src, dst, ci, co, taps, relu in LAYERS:
             std = 1e-3 if name == "out" else None
@@ -259,9 +265,11 @@ class UNet:
         return self.loss
 
     def step(self, lr: float):
+        """One Adam step of every layer (weights, biases, bf16 copies) in one launch."""
         self.t += 1
-        for lay in self.layers.values():
-            lay.step(lr, self.t)
+        if self._adam is None:
+            self._adam = ops.adam_table([lay.adam_entry() for lay in self.layers.values()])
+        ops.adam_multi(self._adam, lr, 0.9, 0.999, 1e-8, self.t)
 
     def train_step(self, x, scale, target, lr):
         """One Adam step on the residual MSE against scale * target; returns the loss (device FP64).

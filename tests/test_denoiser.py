@@ -112,7 +112,8 @@ def test_layout_pool_upsample_and_backward_kernels(C):
     assert torch.allclose(db.cpu(), skip.float().cpu()[..., :C].sum(dim=(0, 1, 2)), rtol=1e-4, atol=1e-3)
 
 
-@pytest.mark.parametrize("C,stride,off", [(32, 64, 0), (64, 192, 128), (256, 256, 0), (24, 64, 40), (33, 64, 0)])
+@pytest.mark.parametrize("C,stride,off", [(32, 64, 0), (64, 192, 128), (256, 256, 0), (24, 64, 40), (33, 64, 0),
+                                          (36, 40, 0), (5, 64, 58)])
 def test_bias_grad_sums_every_pixel_of_the_slice(C, stride, off):
     B, H, W = 2, 64, 128
     dz = _nhwc(B, H, W, stride, stride, 30 + C)
@@ -171,6 +172,40 @@ def test_adam_step_and_weight_copies(cout, taps, cin):
     assert torch.allclose(m2.cpu(), mi, rtol=1e-6, atol=1e-8) and torch.allclose(v2.cpu(), vi, rtol=1e-6, atol=0)
 
 
+def test_multi_tensor_adam_equals_per_layer_steps():
+    """dn_adam_multi over several layers (3x3 and 1x1, with and without the transposed copy and the
+    bias) leaves every buffer bit-identical to per-layer dn_adam + dn_adam_bias."""
+    g = torch.Generator().manual_seed(17)
+    shapes = [(32, 9, 33, True, True), (256, 9, 256, True, True), (33, 1, 32, True, False), (70, 9, 45, False, True)]
+
+    def make():
+        g.manual_seed(17)
+        out = []
+        for cout, taps, cin, bias, with_wd in shapes:
+            t = lambda *sh, s=1.0: (s * torch.randn(*sh, generator=g)).cuda()
+            w, m, v, gr = t(cout, taps, cin), t(cout, taps, cin, s=0.01), t(cout, taps, cin, s=0.03).abs(), t(cout, taps, cin)
+            wf = torch.zeros((cout + 15) // 16 * 16, taps, r64(cin), dtype=torch.bfloat16, device="cuda")
+            wd = torch.zeros(cin, taps, r64(cout), dtype=torch.bfloat16, device="cuda") if with_wd else None
+            b = (t(cout), t(cout, s=0.01), t(cout, s=0.03).abs(), t(cout)) if bias else (None,) * 4
+            out.append([w, m, v, gr, wf, r64(cin), wd, r64(cout) if with_wd else 0, cout, taps, cin, *b])
+        return out
+
+    lr, b1, b2, eps, step = 2e-3, 0.9, 0.999, 1e-8, 3
+    ref = make()
+    for w, m, v, gr, wf, cin_pad, wd, cout_pad, cout, taps, cin, b, mb, vb, gb in ref:
+        ops.adam(w, m, v, gr, cout, taps, cin, lr, b1, b2, eps, step, wf, cin_pad, wd, cout_pad)
+        if b is not None:
+            ops.adam_bias(b, mb, vb, gb, lr, b1, b2, eps, step)
+    got = make()
+    table = ops.adam_table([tuple(e) for e in got])
+    ops.adam_multi(table, lr, b1, b2, eps, step)
+    ops.check()
+    for r, q in zip(ref, got):
+        for x, y in zip(r, q):
+            if isinstance(x, torch.Tensor):
+                assert torch.equal(x, y)
+
+
 def test_sample_scale_is_inverse_mean_fluence():
     g = torch.Generator().manual_seed(5)
     x = torch.rand(3, 5, 64, 32, generator=g) * torch.tensor([1.0, 1e-3, 7.0]).view(3, 1, 1, 1)
@@ -212,7 +247,7 @@ def _head_inputs(B, H, W, cout, seed):
 def test_fused_head_is_bit_identical_to_conv_then_output_kernels(B, H, W, cout):
     """dn_conv_head against dn_conv (fp32 NHWC output) followed by dn_predict_output, and by
     dn_pack_target + dn_mse: the prediction and the gradient seed are bit-identical, the loss equal
-    up to the order of its FP64 sum."""
+    up to the FP32 partial sums over 16 channels the fused head takes before its FP64 sum."""
     x, w, bias, x0, scale, t = _head_inputs(B, H, W, cout, 40 + cout)
     out = torch.zeros(B, H, W, (cout + 7) // 8 * 8, device="cuda")
     ops.conv(x, w, cout, out, taps=1, bias=bias)
@@ -233,7 +268,8 @@ def test_fused_head_is_bit_identical_to_conv_then_output_kernels(B, H, W, cout):
     ops.conv_head(x, w, cout, bias, x0, scale, target=t, dout=dout, loss=loss)
     ops.check()
     assert torch.equal(dout, ref_dout)
-    assert abs(loss.item() - ref_loss.item()) <= 1e-12 * ref_loss.item()
+    # FP32 partial sums over 16 channels (then FP64) against FP64 throughout: a few FP32 ulps
+    assert abs(loss.item() - ref_loss.item()) <= 1e-6 * ref_loss.item()
     # and against the definition in FP64 on the CPU
     y = x0[..., :cout].double().cpu() + out[..., :cout].double().cpu()
     r = y - (t.cpu().permute(0, 2, 3, 1).double() * scale.cpu().double().view(B, 1, 1, 1))
