@@ -51,6 +51,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad-error", action="store_true", help="skip the gradient-error measurement")
     ap.add_argument("--plain-gd", action="store_true", help="invert256: no fluence preconditioning")
+    ap.add_argument("--conv", default="128,128", help="conv: input,output channels of the timed 3x3 layer")
     ap.add_argument("--workload", default="grad256",
                     choices=["grad256", "large1024", "batch64", "denoise256", "conv", "invert256", "unet256"],
                     help="grad256: the gradient evaluation (default); large1024: the same on 1024^2 px at "
@@ -556,25 +557,41 @@ def _denoise256(args):
 
 
 def _conv_only(args):
-    """One 3x3 convolution, 8 x 256 x 256 pixels, 128 -> 128 channels, on the tensor cores."""
+    """One 3x3 convolution and its weight gradient on 8 x 256 x 256 pixels (--conv CIN,COUT;
+    default 128 -> 128 channels) on the tensor cores: the profiling case of the denoiser's
+    convolution kernels."""
     import torch
     from paper_1608_05238_gb300 import _build, denoise_ops as ops
+    from paper_1608_05238_gb300.denoise_ops import Act
     _build.build()
-    xc = torch.randn(8, 256, 256, 128, device="cuda").bfloat16()
-    wc = (torch.randn(128, 9, 128, device="cuda") * 0.03).bfloat16()
-    yc = torch.empty(8, 256, 256, 128, device="cuda", dtype=torch.bfloat16)
+    cin, cout = (int(v) for v in args.conv.split(","))
+    r64 = lambda c: (c + 63) // 64 * 64
+    B, H, W = 8, 256, 256
+    xc = torch.randn(B, H, W, r64(cin), device="cuda").bfloat16()
+    wc = (torch.randn((cout + 15) // 16 * 16, 9, r64(cin), device="cuda") * 0.03).bfloat16()
+    yc = torch.empty(B, H, W, r64(cout), device="cuda", dtype=torch.bfloat16)
+    dw = torch.zeros(cout, 9, cin, device="cuda")
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     for _ in range(args.warmup):
-        ops.conv(xc, wc, 128, yc)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ops.conv(xc, wc, cout, yc)
+        ops.wgrad_nhwc(Act(yc, cout), Act(xc, cin), 9, dw)
+    (a, b), (c, d) = ev(), ev()
     a.record()
     for _ in range(args.steps):
-        ops.conv(xc, wc, 128, yc)
+        ops.conv(xc, wc, cout, yc)
     b.record()
-    b.synchronize()
+    c.record()
+    for _ in range(args.steps):
+        ops.wgrad_nhwc(Act(yc, cout), Act(xc, cin), 9, dw)
+    d.record()
+    d.synchronize()
     ops.check()
-    s = a.elapsed_time(b) / 1e3 / args.steps
-    print(json.dumps({"metric": "conv TFLOP/s", "value": 2 * 8 * 256 * 256 * 128 * 9 * 128 / s / 1e12,
-                      "unit": "TFLOP/s", "ms_per_step": 1e3 * s}), flush=True)
+    s_conv, s_wg = a.elapsed_time(b) / 1e3 / args.steps, c.elapsed_time(d) / 1e3 / args.steps
+    flop = 2 * B * H * W * cout * 9 * cin
+    print(json.dumps({"metric": "conv TFLOP/s", "value": flop / s_conv / 1e12, "unit": "TFLOP/s",
+                      "ms_per_step": 1e3 * s_conv, "config": {"workload": f"conv 8x256x256, {cin} -> {cout}, 3x3",
+                                                              "wgrad_ms": 1e3 * s_wg,
+                                                              "wgrad_tflops": flop / s_wg / 1e12}}), flush=True)
     return 0
 
 

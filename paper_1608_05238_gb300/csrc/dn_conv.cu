@@ -461,13 +461,15 @@ __global__ void __launch_bounds__(ws_threads<SUB>(), 1)
 }
 
 // k_conv_halo: 3x3 convolution with few output channels (N <= 32) whose 128-pixel tiles lie in
-// one image row (W a multiple of 128).  A stage holds, for one 64-channel block, the haloed input
-// -- rows y-1..y+1 x columns x0-1..x0+128, one 4D TMA box {64, 130, 3, 1} with zero fill -- and
-// the weights of all nine taps; the nine taps read the haloed tile at row offsets ky 130 + kx (the
+// one image row (W a multiple of 128).  The weights of all taps and channel blocks (9 x cblocks
+// tiles of N x 64, <= 74 KB) are loaded once per CTA and stay resident; a ring stage holds, for
+// one 64-channel block, the haloed input -- rows y-1..y+1 x columns x0-1..x0+128, one 4D TMA box
+// {64, 130, 3, 1} with zero fill -- and the nine taps read it at row offsets ky 130 + kx (the
 // descriptor starts at that row, base-offset field 0: the 128-byte swizzle follows the address
 // bits of the 1024-byte-aligned tile).  Per stage that is 36 MMAs for one barrier round trip and
-// ~1.9x fewer L2 -> SM bytes per FLOP than one input box per tap, which is what bounds these
-// convolutions.  Same warp roles and double TMEM accumulator as k_conv_ws.
+// 50 KB through L2 per 128 pixels and channel block (a box per tap plus its weights would be
+// 9 x (16 + N/8) KB), which is what bounds these convolutions.  Same warp roles and double TMEM
+// accumulator as k_conv_ws.
 constexpr uint32_t kHaloBytes = 3 * 130 * 128;  // 49,920 B written by the input box
 constexpr uint32_t kHaloStride = (kHaloBytes + 1023) & ~1023u;
 
@@ -476,13 +478,16 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                 int stages, int num_tiles) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t bTileBytes = (uint32_t)a.N * kBlockK * 2;
-  const uint32_t stageBytes = kHaloStride + 9 * bTileBytes;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stageBytes);
+  const int cblocks = a.cin_pad / kBlockK;
+  const uint32_t bTileBytes = (uint32_t)a.N * kBlockK * 2;      // one tap's weights, one channel block
+  const uint32_t wBytes = (uint32_t)cblocks * 9u * bTileBytes;  // resident weights [cb][tap]
+  uint8_t *ring = smem + wBytes;
+  uint64_t *full = reinterpret_cast<uint64_t *>(ring + (size_t)stages * kHaloStride);
   uint64_t *empty = full + stages;
   uint64_t *tfull = empty + stages;
   uint64_t *tempty = tfull + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+  uint64_t *wfull = tempty + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wfull + 1);
   const uint32_t acc_cols = a.tmem_cols;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -495,6 +500,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], 128);
     }
+    mbar_init(wfull, 1);
     fence_barrier_init();
     prefetch_tensormap(&tmH);
     prefetch_tensormap(&tmW);
@@ -508,9 +514,13 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int hw = a.H * a.W;
-  const int cblocks = a.cin_pad / kBlockK;
 
   if (warp == 0 && lane == 0) {
+    // the weights once, then the haloed input boxes of all tiles of this CTA
+    mbar_arrive_expect_tx(wfull, wBytes);
+    for (int cb = 0; cb < cblocks; ++cb)
+      for (int tap = 0; tap < 9; ++tap)
+        tma_load_2d(smem + (cb * 9 + tap) * bTileBytes, &tmW, wfull, tap * a.cin_pad + cb * kBlockK, 0);
     uint32_t kc = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
@@ -525,18 +535,17 @@ __global__ void __launch_bounds__(kWsThreads, 1)
           ok = false;
           break;
         }
-        uint8_t *base = smem + (size_t)st * stageBytes;
-        mbar_arrive_expect_tx(&full[st], kHaloBytes + 9 * bTileBytes);
-        tma_load_4d(base, &tmH, &full[st], cb * kBlockK, x0 - 1, y0 - 1, b0);
-        for (int tap = 0; tap < 9; ++tap)
-          tma_load_2d(base + kHaloStride + tap * bTileBytes, &tmW, &full[st], tap * a.cin_pad + cb * kBlockK, 0);
+        mbar_arrive_expect_tx(&full[st], kHaloBytes);
+        tma_load_4d(ring + (size_t)st * kHaloStride, &tmH, &full[st], cb * kBlockK, x0 - 1, y0 - 1, b0);
       }
     }
   } else if (warp == 1 && lane == 0) {
     const uint32_t idesc = idesc_bf16_f32(kBlockM, (uint32_t)a.N);
+    const uint32_t wBase = smem_u32(smem);
+    bool ok = mbar_wait(wfull, 0);
+    if (!ok) atomicOr(a.err, 2048u);
     uint32_t kc = 0;
     int it = 0;
-    bool ok = true;
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++it) {
       const int b = it & 1;
       const uint32_t use = it >> 1;
@@ -554,7 +563,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t aBase = smem_u32(smem + (size_t)st * stageBytes), bBase = aBase + kHaloStride;
+        const uint32_t aBase = smem_u32(ring + (size_t)st * kHaloStride);
+        const uint32_t bBase = wBase + (uint32_t)cb * 9u * bTileBytes;
         for (int tap = 0; tap < 9; ++tap) {
           const uint32_t arow = aBase + (uint32_t)((tap / 3) * 130 + tap % 3) * 128u;
 #pragma unroll
@@ -1012,14 +1022,15 @@ cudaError_t launch_wgrad_mn(const CUtensorMap &tmA, const CUtensorMap &tmB, cons
   return cudaGetLastError();
 }
 
-static int halo_stages(int N) {
-  const size_t stage = kHaloStride + 9 * (size_t)N * kBlockK * 2;
-  const int st = (int)((200u * 1024u) / stage);
-  return st > 4 ? 4 : st;
+// ring depth of k_conv_halo beside its resident weights (cblocks x 9 x N x 128 B), at most 4
+static int halo_stages(int N, int cblocks) {
+  const long long avail = 232448 - 1024 - 512 - (long long)cblocks * 9 * N * kBlockK * 2;
+  const long long st = avail / (long long)kHaloStride;
+  return st > 4 ? 4 : (st < 0 ? 0 : (int)st);
 }
 
 bool conv_halo_applies(const ConvArgs &a) {
-  return a.taps == 9 && a.W % kBlockM == 0 && a.N <= 32 && halo_stages(a.N) >= 2;
+  return a.taps == 9 && a.W % kBlockM == 0 && a.N <= 32 && halo_stages(a.N, a.cin_pad / kBlockK) >= 2;
 }
 
 cudaError_t launch_conv_halo(const CUtensorMap &tmH, const CUtensorMap &tmW, ConvArgs a, cudaStream_t s) {
@@ -1032,8 +1043,9 @@ cudaError_t launch_conv_halo(const CUtensorMap &tmH, const CUtensorMap &tmW, Con
   uint32_t cols = 32;
   while (cols < (uint32_t)a.N) cols <<= 1;
   a.tmem_cols = cols;
-  const int st = halo_stages(a.N);
-  const size_t smem = 1024 + (size_t)st * (kHaloStride + 9 * (size_t)a.N * kBlockK * 2) + 512;
+  const int cblocks = a.cin_pad / kBlockK;
+  const int st = halo_stages(a.N, cblocks);
+  const size_t smem = 1024 + (size_t)cblocks * 9 * a.N * kBlockK * 2 + (size_t)st * kHaloStride + 512;
   const long long tiles = (long long)a.B * a.H * a.W / kBlockM;
   const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
   k_conv_halo<<<grid, kWsThreads, smem, s>>>(tmH, tmW, a, st, (int)tiles);

@@ -301,19 +301,20 @@ __global__ void k_residual(const float *__restrict__ out, int ostride, const __n
 // Adam on the FP32 master weights [cout][taps][cin] and bias; writes the forward BF16 copy
 // wf [n_pad][taps][cin_pad] and the input-gradient copy wd [cin_npad][taps][cout_pad] with the
 // taps flipped (wd[c][8 - t][n] = w[n][t][c] for 3x3).
-// One Adam step on element i (bias-corrected moments; c1 = 1 - b1^t, c2 = 1 - b2^t); the
-// gradient is consumed (set to zero).  Returns the new weight.
+// One Adam step on element i with bias-corrected moments (ic1 = 1 / (1 - b1^t), ic2 = 1 /
+// (1 - b2^t)); the gradient is consumed (set to zero).  Returns the new weight.  Explicit
+// roundings, so that every kernel that inlines this computes the same bits; the final quotient
+// is the fast division (2 ulp: far below what an optimizer step needs).
 __device__ __forceinline__ float adam_elem(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
                                            float *__restrict__ g, size_t i, float lr, float b1, float b2, float eps,
-                                           float c1, float c2) {
-  // explicit roundings, so that every kernel that inlines this computes the same bits
+                                           float ic1, float ic2) {
   const float gi = g[i];
   g[i] = 0.f;  // the gradient is consumed: the next backward pass accumulates from zero
   const float mi = __fmaf_rn(b1, m[i], __fmul_rn(1.f - b1, gi));
   const float vi = __fmaf_rn(b2, v[i], __fmul_rn(__fmul_rn(1.f - b2, gi), gi));
   m[i] = mi;
   v[i] = vi;
-  const float step = __fdiv_rn(__fmul_rn(lr, __fdiv_rn(mi, c1)), __fadd_rn(__fsqrt_rn(__fdiv_rn(vi, c2)), eps));
+  const float step = __fdividef(__fmul_rn(lr, __fmul_rn(mi, ic1)), __fadd_rn(__fsqrt_rn(__fmul_rn(vi, ic2)), eps));
   const float wi = __fsub_rn(w[i], step);
   w[i] = wi;
   return wi;
@@ -321,11 +322,11 @@ __device__ __forceinline__ float adam_elem(float *__restrict__ w, float *__restr
 
 __global__ void k_adam(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
                        float *__restrict__ g, int cout, int taps, int cin, float lr, float b1, float b2,
-                       float eps, float c1, float c2, __nv_bfloat16 *__restrict__ wf, int cin_pad,
+                       float eps, float ic1, float ic2, __nv_bfloat16 *__restrict__ wf, int cin_pad,
                        __nv_bfloat16 *__restrict__ wd, int cout_pad, int step) {
   const long long n = (long long)cout * taps * cin;
   for (long long i = blockIdx.x * (long long)kT + threadIdx.x; i < n; i += (long long)gridDim.x * kT) {
-    const float wi = step > 0 ? adam_elem(w, m, v, g, (size_t)i, lr, b1, b2, eps, c1, c2) : w[i];
+    const float wi = step > 0 ? adam_elem(w, m, v, g, (size_t)i, lr, b1, b2, eps, ic1, ic2) : w[i];
     const int c = (int)(i % cin);
     const int t = (int)((i / cin) % taps);
     const int o = (int)(i / ((long long)cin * taps));
@@ -339,7 +340,7 @@ __global__ void k_adam(float *__restrict__ w, float *__restrict__ m, float *__re
 // one tap: the update and wf are written along cin, wd along cout (both coalesced).
 __global__ void k_adam_t(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
                          float *__restrict__ g, int cout, int taps, int cin, float lr, float b1, float b2,
-                         float eps, float c1, float c2, __nv_bfloat16 *__restrict__ wf, int cin_pad,
+                         float eps, float ic1, float ic2, __nv_bfloat16 *__restrict__ wf, int cin_pad,
                          __nv_bfloat16 *__restrict__ wd, int cout_pad, int step) {
   __shared__ __nv_bfloat16 tile[32][34];
   const int c0 = blockIdx.x * 32, o0 = blockIdx.y * 32, t = blockIdx.z;
@@ -347,7 +348,7 @@ __global__ void k_adam_t(float *__restrict__ w, float *__restrict__ m, float *__
     const int o = o0 + r, c = c0 + threadIdx.x;
     if (o < cout && c < cin) {
       const size_t i = ((size_t)o * taps + t) * cin + c;
-      const float wi = step > 0 ? adam_elem(w, m, v, g, i, lr, b1, b2, eps, c1, c2) : w[i];
+      const float wi = step > 0 ? adam_elem(w, m, v, g, i, lr, b1, b2, eps, ic1, ic2) : w[i];
       const __nv_bfloat16 h = __float2bfloat16_rn(wi);
       wf[((size_t)o * taps + t) * cin_pad + c] = h;
       tile[r][threadIdx.x] = h;
@@ -361,17 +362,17 @@ __global__ void k_adam_t(float *__restrict__ w, float *__restrict__ m, float *__
 }
 
 __global__ void k_adam_bias(float *__restrict__ b, float *__restrict__ m, float *__restrict__ v,
-                            float *__restrict__ g, int n, float lr, float b1, float b2, float eps, float c1,
-                            float c2) {
+                            float *__restrict__ g, int n, float lr, float b1, float b2, float eps, float ic1,
+                            float ic2) {
   const int i = blockIdx.x * kT + threadIdx.x;
-  if (i < n) adam_elem(b, m, v, g, (size_t)i, lr, b1, b2, eps, c1, c2);
+  if (i < n) adam_elem(b, m, v, g, (size_t)i, lr, b1, b2, eps, ic1, ic2);
 }
 
 // All layers' Adam steps in one launch: block -> (layer, 32 x 32 (cout x cin) tile of one tap) by
 // the table's first-block indices; the tile body is k_adam_t's (wd optional) and block 0 of a
 // layer also steps its bias.  Same arithmetic as the per-layer kernels.
-__global__ void k_adam_multi(const __grid_constant__ AdamTable T, float lr, float b1, float b2, float eps, float c1,
-                             float c2, int step) {
+__global__ void k_adam_multi(const __grid_constant__ AdamTable T, float lr, float b1, float b2, float eps, float ic1,
+                             float ic2, int step) {
   __shared__ __nv_bfloat16 tile[32][34];
   int l = 0;
   while (l + 1 < T.n && (int)blockIdx.x >= T.L[l + 1].tile0) ++l;
@@ -384,14 +385,14 @@ __global__ void k_adam_multi(const __grid_constant__ AdamTable T, float lr, floa
     const int o = o0 + r, c = c0 + threadIdx.x;
     if (o < L.cout && c < L.cin) {
       const size_t i = ((size_t)o * L.taps + t) * L.cin + c;
-      const float wi = step > 0 ? adam_elem(L.w, L.m, L.v, L.g, i, lr, b1, b2, eps, c1, c2) : L.w[i];
+      const float wi = step > 0 ? adam_elem(L.w, L.m, L.v, L.g, i, lr, b1, b2, eps, ic1, ic2) : L.w[i];
       const __nv_bfloat16 h = __float2bfloat16_rn(wi);
       L.wf[((size_t)o * L.taps + t) * L.cin_pad + c] = h;
       tile[r][threadIdx.x] = h;
     }
   }
   if (local == 0 && L.b && step > 0)
-    for (int i = tid; i < L.cout; i += 256) adam_elem(L.b, L.mb, L.vb, L.gb, (size_t)i, lr, b1, b2, eps, c1, c2);
+    for (int i = tid; i < L.cout; i += 256) adam_elem(L.b, L.mb, L.vb, L.gb, (size_t)i, lr, b1, b2, eps, ic1, ic2);
   if (!L.wd) return;  // uniform over the block
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += 8) {
@@ -640,28 +641,28 @@ cudaError_t residual(const float *out, int ostride, const __nv_bfloat16 *x, int 
 cudaError_t adam(float *w, float *m, float *v, float *g, int cout, int taps, int cin, float lr, float b1,
                  float b2, float eps, int step, __nv_bfloat16 *wf, int cin_pad, __nv_bfloat16 *wd, int cout_pad,
                  cudaStream_t s) {
-  const float c1 = step > 0 ? 1.f - powf(b1, (float)step) : 1.f, c2 = step > 0 ? 1.f - powf(b2, (float)step) : 1.f;
+  const float ic1 = step > 0 ? 1.f / (1.f - powf(b1, (float)step)) : 1.f, ic2 = step > 0 ? 1.f / (1.f - powf(b2, (float)step)) : 1.f;
   if (wd) {
     k_adam_t<<<dim3((cin + 31) / 32, (cout + 31) / 32, taps), dim3(32, 8), 0, s>>>(w, m, v, g, cout, taps, cin, lr, b1,
-                                                                                  b2, eps, c1, c2, wf, cin_pad, wd,
+                                                                                  b2, eps, ic1, ic2, wf, cin_pad, wd,
                                                                                   cout_pad, step);
     return cudaGetLastError();
   }
-  k_adam<<<blocks_for((long long)cout * taps * cin), kT, 0, s>>>(w, m, v, g, cout, taps, cin, lr, b1, b2, eps, c1, c2,
+  k_adam<<<blocks_for((long long)cout * taps * cin), kT, 0, s>>>(w, m, v, g, cout, taps, cin, lr, b1, b2, eps, ic1, ic2,
                                                                   wf, cin_pad, wd, cout_pad, step);
   return cudaGetLastError();
 }
 cudaError_t adam_multi(const AdamTable &T, float lr, float b1, float b2, float eps, int step, int blocks,
                        cudaStream_t s) {
-  const float c1 = step > 0 ? 1.f - powf(b1, (float)step) : 1.f, c2 = step > 0 ? 1.f - powf(b2, (float)step) : 1.f;
-  k_adam_multi<<<blocks, dim3(32, 8), 0, s>>>(T, lr, b1, b2, eps, c1, c2, step);
+  const float ic1 = step > 0 ? 1.f / (1.f - powf(b1, (float)step)) : 1.f, ic2 = step > 0 ? 1.f / (1.f - powf(b2, (float)step)) : 1.f;
+  k_adam_multi<<<blocks, dim3(32, 8), 0, s>>>(T, lr, b1, b2, eps, ic1, ic2, step);
   return cudaGetLastError();
 }
 cudaError_t adam_bias(float *b, float *m, float *v, float *g, int n, float lr, float b1, float b2, float eps,
                       int step, cudaStream_t s) {
   if (step <= 0) return cudaSuccess;
-  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
-  k_adam_bias<<<(n + kT - 1) / kT, kT, 0, s>>>(b, m, v, g, n, lr, b1, b2, eps, c1, c2);
+  const float ic1 = 1.f / (1.f - powf(b1, (float)step)), ic2 = 1.f / (1.f - powf(b2, (float)step));
+  k_adam_bias<<<(n + kT - 1) / kT, kT, 0, s>>>(b, m, v, g, n, lr, b1, b2, eps, ic1, ic2);
   return cudaGetLastError();
 }
 cudaError_t pack_input(const float *src, const float *scale, int B, long long HW, int C, __nv_bfloat16 *dst, int stride,
