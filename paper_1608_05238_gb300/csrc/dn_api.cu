@@ -329,7 +329,7 @@ int dn_wgrad_nhwc(dn_slice dz, dn_slice x, int32_t B, int32_t H, int32_t W, int3
   a.n_tiles = (cin + a.N - 1) / a.N;
   const long long kblocks = (long long)B * HW / 64;
   long long splits = (2 * 152) / (taps * a.m_tiles * a.n_tiles);  // one wave of two blocks per SM
-  if (splits > kblocks) splits = kblocks;
+  if (splits > kblocks / 16) splits = kblocks / 16;  // >= 16 K blocks per CTA: its atomic epilogue stays small
   if (splits < 1) splits = 1;
   a.splits = (int)splits;
   uint32_t cols = 32;

@@ -694,10 +694,16 @@ __global__ void __launch_bounds__(128, 1)
     tmem_ld_wait();
     if (!have || m >= a.cout) continue;
     float *o = a.dw + ((size_t)m * a.taps + tap) * a.cin_pad + n_tile * a.N + c0;
+    const int cb = n_tile * a.N + c0;
+    if (a.cin_pad % 4 == 0 && cb + 16 <= a.cin) {  // 16-byte aligned: four 4-wide reductions
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int c = n_tile * a.N + c0 + j;
-      if (c < a.cin) atomicAdd(o + j, __uint_as_float(v[j]));
+      for (int j = 0; j < 16; j += 4)
+        red_add_v4(o + j, __uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
+                   __uint_as_float(v[j + 3]));
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (cb + j < a.cin) atomicAdd(o + j, __uint_as_float(v[j]));
     }
   }
   tc_fence_before();
@@ -809,10 +815,16 @@ __global__ void __launch_bounds__(128, 1)
     tmem_ld_wait();
     if (!have || m >= a.cout) continue;
     float *o = a.dw + ((size_t)m * a.taps + tap) * a.cin_pad + n_tile * a.N + c0;
+    const int cb = n_tile * a.N + c0;
+    if (a.cin_pad % 4 == 0 && cb + 16 <= a.cin) {  // 16-byte aligned: four 4-wide reductions
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int c = n_tile * a.N + c0 + j;
-      if (c < a.cin) atomicAdd(o + j, __uint_as_float(v[j]));
+      for (int j = 0; j < 16; j += 4)
+        red_add_v4(o + j, __uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
+                   __uint_as_float(v[j + 3]));
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (cb + j < a.cin) atomicAdd(o + j, __uint_as_float(v[j]));
     }
   }
   tc_fence_before();
