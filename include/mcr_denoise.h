@@ -108,6 +108,11 @@ typedef struct {
  */
 int dn_wgrad_nhwc(dn_slice dz, dn_slice x, int32_t B, int32_t H, int32_t W, int32_t taps, int32_t cout, int32_t cin,
                   float *dw, void *stream);
+/* dn_wgrad_nhwc plus, if db != NULL, the bias gradient db[n] += sum_{b, pixel} dz[b, pixel][n]
+ * (FP32).  For 3x3 layers with cout <= 64 and W a multiple of 64 the tensor cores produce it in
+ * the same pass (a block of ones as one more MMA operand), otherwise a reduction kernel follows. */
+int dn_wgrad_bias_nhwc(dn_slice dz, dn_slice x, int32_t B, int32_t H, int32_t W, int32_t taps, int32_t cout,
+                       int32_t cin, float *dw, float *db, void *stream);
 
 /* dst[c][b][p] = src[b][p][off + c] for c < C (bf16); shifted = 1 writes three copies
  * (dst + k*C*B*HW) with x shifted by k - 1 and zeros outside the row. */

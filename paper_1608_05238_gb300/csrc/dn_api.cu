@@ -266,6 +266,11 @@ static bool slice_ok(const dn_slice &s, int C) { return s.data && s.off >= 0 && 
 
 int dn_wgrad_nhwc(dn_slice dz, dn_slice x, int32_t B, int32_t H, int32_t W, int32_t taps, int32_t cout, int32_t cin,
                   float *dw, void *stream) {
+  return dn_wgrad_bias_nhwc(dz, x, B, H, W, taps, cout, cin, dw, nullptr, stream);
+}
+
+int dn_wgrad_bias_nhwc(dn_slice dz, dn_slice x, int32_t B, int32_t H, int32_t W, int32_t taps, int32_t cout,
+                       int32_t cin, float *dw, float *db, void *stream) {
   if (!slice_ok(dz, cout) || !slice_ok(x, cin) || !dw || (taps != 9 && taps != 1)) return MCR_ERR_ARG;
   if (B <= 0 || H <= 0 || W < 16 || (W & (W - 1)) || ((long long)H * W) % 64) return MCR_ERR_ARG;
   if (cout < 1 || cin < 1 || cout > 512 || cin > 512) return MCR_ERR_ARG;
@@ -305,6 +310,7 @@ int dn_wgrad_nhwc(dn_slice dz, dn_slice x, int32_t B, int32_t H, int32_t W, int3
   a.dw = dw;
   a.err = err;
   if (wgrad_halo_applies(taps, cout, W)) {  // few output channels: all nine taps from one haloed box
+    a.db = db;                              // its bias gradient comes with it
     CUtensorMap tmH;
     const uint64_t dims[4] = {(uint64_t)cin, (uint64_t)W, (uint64_t)H, (uint64_t)B};
     const uint64_t strides[3] = {(uint64_t)x.stride * 2, (uint64_t)W * x.stride * 2, HW * x.stride * 2};
@@ -336,6 +342,9 @@ int dn_wgrad_nhwc(dn_slice dz, dn_slice x, int32_t B, int32_t H, int32_t W, int3
   while (cols < (uint32_t)a.N) cols <<= 1;
   a.tmem_cols = cols;
   if (launch_wgrad_mn(tmA, tmB, a, (cudaStream_t)stream) != cudaSuccess) return MCR_ERR_CUDA;
+  if (db && bias_grad(static_cast<const __nv_bfloat16 *>(dz.data), (long long)B * HW, dz.stride, dz.off, cout, db,
+                      (cudaStream_t)stream) != cudaSuccess)
+    return MCR_ERR_CUDA;
   return MCR_OK;
 }
 

@@ -840,27 +840,34 @@ __global__ void __launch_bounds__(128, 1)
 // (channels of the block, columns x0-1 .. x0+64, rows y-1 .. y+1; zero fill outside the image)
 // and the dZ box {64 channels, 64 pixels}.  Tap (ky, kx)'s window starts ky 66 + kx pixel rows
 // into the box; an MMA's second 64-channel M group is the next tap's window (leading byte offset =
-// the distance of the two windows; for tap 8 a dummy window one row further, whose rows are
-// discarded).  Five accumulators of 64 columns (taps 0-1, 2-3, 4-5, 6-7, 8) stay in TMEM for
-// the CTA's contiguous range of segments; the epilogue adds them into dw with one atomic per
-// element (consecutive lanes = consecutive input channels).  Per segment the CTA reads 25 KB of
+// the distance of the two windows).  Tap 8's partner is a 16-row block of ones in shared memory,
+// so those 64 accumulator rows hold sum_p dZ[p][o]: the bias gradient comes free with the
+// weight gradient.  Five accumulators of 64 columns (taps 0-1, 2-3, 4-5, 6-7, 8 + ones) stay in
+// TMEM for the CTA's contiguous range of segments; the epilogue adds them into dw with one atomic
+// per element (consecutive lanes = consecutive input channels) and, on channel block 0, the
+// ones row into db.  Per segment the CTA reads 25 KB of
 // X and 8 KB of dZ instead of 9 x (8 + 8) KB for nine separate shifted GEMMs.
 constexpr uint32_t kWhBytes = 3 * 66 * 128;                          // 25,344 B written by the box
 constexpr uint32_t kWhStride = (kWhBytes + 1023) & ~1023u;           // 25,600 B
 constexpr uint32_t kWhStage = kWhStride + 8192;                      // + dZ box
 constexpr int kWhStages = 4;
+constexpr uint32_t kWhOnes = 2048;  // 16 rows x 64 bf16 ones (tap 8's partner M group)
 
 __global__ void __launch_bounds__(128, 1)
     k_wgrad_halo(const __grid_constant__ CUtensorMap tmZ, const __grid_constant__ CUtensorMap tmH, const WgradArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kWhStages * kWhStage);
+  uint8_t *ones = smem + kWhStages * kWhStage;
+  uint64_t *full = reinterpret_cast<uint64_t *>(ones + kWhOnes);
   uint64_t *empty = full + kWhStages;
   uint64_t *done = empty + kWhStages;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int split = blockIdx.x, cb = blockIdx.y;
+  for (int i = tid; i < (int)(kWhOnes / 4); i += blockDim.x)
+    reinterpret_cast<uint32_t *>(ones)[i] = 0x3F803F80u;  // bf16 1.0 pairs (any swizzle of it is the same)
+  fence_proxy_async_smem();
   if (tid == 0) {
     for (int s = 0; s < kWhStages; ++s) {
       mbar_init(&full[s], 1);
@@ -903,6 +910,7 @@ __global__ void __launch_bounds__(128, 1)
     }
   } else if (warp == 1 && lane == 0) {
     const uint32_t idesc = idesc_bf16_f32(kBlockM, 64) | (1u << 15) | (1u << 16);  // A, B MN-major
+    const uint32_t onesBase = smem_u32(ones);
     for (int i = 0; i < nk; ++i) {
       const int s = i % kWhStages, r = i / kWhStages;
       if (!mbar_wait(&full[s], r & 1)) {
@@ -918,9 +926,10 @@ __global__ void __launch_bounds__(128, 1)
         for (int mt = 0; mt < 5; ++mt) {
           const int t0 = 2 * mt;
           const uint32_t r0 = (uint32_t)((t0 / 3) * 66 + t0 % 3);
-          const uint32_t r1 = t0 < 8 ? (uint32_t)(((t0 + 1) / 3) * 66 + (t0 + 1) % 3) : r0 + 1;
-          mma_bf16(tmem + mt * 64, sdesc_mn128_lbo(hBase + (r0 + 16 * ks) * 128, (r1 - r0) * 128), bdesc, idesc,
-                   (i > 0 || ks > 0) ? 1u : 0u);
+          const uint32_t a0 = hBase + (r0 + 16 * ks) * 128;
+          // partner group: the next tap's window, or for tap 8 the ones block (above every stage)
+          const uint32_t lbo = t0 < 8 ? (uint32_t)(((t0 + 1) / 3) * 66 + (t0 + 1) % 3 - r0) * 128 : onesBase - a0;
+          mma_bf16(tmem + mt * 64, sdesc_mn128_lbo(a0, lbo), bdesc, idesc, (i > 0 || ks > 0) ? 1u : 0u);
         }
       }
       mma_commit(&empty[s]);
@@ -941,6 +950,11 @@ __global__ void __launch_bounds__(128, 1)
       uint32_t v[16];
       tmem_ld16(trow + (uint32_t)c0, v);
       tmem_ld_wait();
+      if (have && tap == 9 && mrow == 64 && cb == 0 && a.db) {  // the ones row: sum_p dZ[p][o]
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j < a.cout) atomicAdd(a.db + c0 + j, __uint_as_float(v[j]));
+      }
       if (!have || tap > 8 || c >= a.cin) continue;
       float *o = a.dw + (size_t)tap * a.cin_pad + c;
 #pragma unroll
@@ -1067,7 +1081,7 @@ cudaError_t launch_conv_halo(const CUtensorMap &tmH, const CUtensorMap &tmW, Con
 bool wgrad_halo_applies(int taps, int cout, int W) { return taps == 9 && cout <= 64 && W % 64 == 0; }
 
 cudaError_t launch_wgrad_halo(const CUtensorMap &tmZ, const CUtensorMap &tmH, const WgradArgs &a, cudaStream_t s) {
-  const size_t smem = 1024 + kWhStages * (size_t)kWhStage + 256;
+  const size_t smem = 1024 + kWhStages * (size_t)kWhStage + kWhOnes + 256;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_wgrad_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -58,6 +58,7 @@ struct WgradArgs {
   uint32_t tmem_cols;
   float *dw;         // fp32 [n_pad][taps][cin_pad], accumulated with atomics
   unsigned *err;
+  float *db;         // k_wgrad_halo: if set, db[o] += sum_p dZ[p][o] (the bias gradient), else unused
 };
 cudaError_t launch_wgrad_tc(const CUtensorMap &tmA, const CUtensorMap tmB[3], const WgradArgs &a, cudaStream_t s);
 cudaError_t launch_wgrad_mn(const CUtensorMap &tmA, const CUtensorMap &tmB, const WgradArgs &a, cudaStream_t s);

@@ -301,21 +301,28 @@ __global__ void k_residual(const float *__restrict__ out, int ostride, const __n
 // Adam on the FP32 master weights [cout][taps][cin] and bias; writes the forward BF16 copy
 // wf [n_pad][taps][cin_pad] and the input-gradient copy wd [cin_npad][taps][cout_pad] with the
 // taps flipped (wd[c][8 - t][n] = w[n][t][c] for 3x3).
-// One Adam step on element i with bias-corrected moments (ic1 = 1 / (1 - b1^t), ic2 = 1 /
-// (1 - b2^t)); the gradient is consumed (set to zero).  Returns the new weight.  Explicit
-// roundings, so that every kernel that inlines this computes the same bits; the final quotient
-// is the fast division (2 ulp: far below what an optimizer step needs).
+// One Adam step with bias-corrected moments (ic1 = 1 / (1 - b1^t), ic2 = 1 / (1 - b2^t)) on
+// registers.  Explicit roundings, so that every kernel that inlines this computes the same bits;
+// the final quotient is the fast division (2 ulp: far below what an optimizer step needs).
+__device__ __forceinline__ void adam_math(float &w, float &m, float &v, float g, float lr, float b1, float b2, float eps,
+                                          float ic1, float ic2) {
+  m = __fmaf_rn(b1, m, __fmul_rn(1.f - b1, g));
+  v = __fmaf_rn(b2, v, __fmul_rn(__fmul_rn(1.f - b2, g), g));
+  const float step = __fdividef(__fmul_rn(lr, __fmul_rn(m, ic1)), __fadd_rn(__fsqrt_rn(__fmul_rn(v, ic2)), eps));
+  w = __fsub_rn(w, step);
+}
+
+// The same on element i of the arrays; the gradient is consumed (set to zero: the next backward
+// pass accumulates from zero).  Returns the new weight.
 __device__ __forceinline__ float adam_elem(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
                                            float *__restrict__ g, size_t i, float lr, float b1, float b2, float eps,
                                            float ic1, float ic2) {
+  float wi = w[i], mi = m[i], vi = v[i];
   const float gi = g[i];
-  g[i] = 0.f;  // the gradient is consumed: the next backward pass accumulates from zero
-  const float mi = __fmaf_rn(b1, m[i], __fmul_rn(1.f - b1, gi));
-  const float vi = __fmaf_rn(b2, v[i], __fmul_rn(__fmul_rn(1.f - b2, gi), gi));
+  adam_math(wi, mi, vi, gi, lr, b1, b2, eps, ic1, ic2);
+  g[i] = 0.f;
   m[i] = mi;
   v[i] = vi;
-  const float step = __fdividef(__fmul_rn(lr, __fmul_rn(mi, ic1)), __fadd_rn(__fsqrt_rn(__fmul_rn(vi, ic2)), eps));
-  const float wi = __fsub_rn(w[i], step);
   w[i] = wi;
   return wi;
 }
@@ -376,20 +383,41 @@ __global__ void k_adam_multi(const __grid_constant__ AdamTable T, float lr, floa
   __shared__ __nv_bfloat16 tile[32][34];
   int l = 0;
   while (l + 1 < T.n && (int)blockIdx.x >= T.L[l + 1].tile0) ++l;
-  const AdamLayer &L = T.L[l];
+  const AdamLayer L = T.L[l];  // a register copy: the stores below cannot be assumed to miss the table
   const int local = (int)blockIdx.x - L.tile0;
   const int ct = (L.cin + 31) / 32, ot = (L.cout + 31) / 32;
   const int c0 = (local % ct) * 32, o0 = ((local / ct) % ot) * 32, t = local / (ct * ot);
   const int tid = threadIdx.y * 32 + threadIdx.x;
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int o = o0 + r, c = c0 + threadIdx.x;
-    if (o < L.cout && c < L.cin) {
-      const size_t i = ((size_t)o * L.taps + t) * L.cin + c;
-      const float wi = step > 0 ? adam_elem(L.w, L.m, L.v, L.g, i, lr, b1, b2, eps, ic1, ic2) : L.w[i];
-      const __nv_bfloat16 h = __float2bfloat16_rn(wi);
-      L.wf[((size_t)o * L.taps + t) * L.cin_pad + c] = h;
-      tile[r][threadIdx.x] = h;
+  // the tile's four rows of this thread: all loads first (memory-level parallelism), then the updates
+  float wv[4], mv[4], vv[4], gv[4];
+  size_t ix[4];
+  bool in[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int o = o0 + threadIdx.y + 8 * k, c = c0 + threadIdx.x;
+    in[k] = o < L.cout && c < L.cin;
+    ix[k] = ((size_t)o * L.taps + t) * L.cin + c;
+    wv[k] = in[k] ? L.w[ix[k]] : 0.f;
+    if (step > 0 && in[k]) {
+      mv[k] = L.m[ix[k]];
+      vv[k] = L.v[ix[k]];
+      gv[k] = L.g[ix[k]];
     }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!in[k]) continue;
+    const int r = threadIdx.y + 8 * k, o = o0 + r, c = c0 + threadIdx.x;
+    if (step > 0) {
+      adam_math(wv[k], mv[k], vv[k], gv[k], lr, b1, b2, eps, ic1, ic2);
+      L.g[ix[k]] = 0.f;
+      L.m[ix[k]] = mv[k];
+      L.v[ix[k]] = vv[k];
+      L.w[ix[k]] = wv[k];
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(wv[k]);
+    L.wf[((size_t)o * L.taps + t) * L.cin_pad + c] = h;
+    tile[r][threadIdx.x] = h;
   }
   if (local == 0 && L.b && step > 0)
     for (int i = tid; i < L.cout; i += 256) adam_elem(L.b, L.mb, L.vb, L.gb, (size_t)i, lr, b1, b2, eps, ic1, ic2);

@@ -186,6 +186,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Make this thread's generic-proxy shared-memory writes visible to the async proxy (tensor-core
+// operand reads, TMA).
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // ---------------------------------------------------------------- reductions
 // p[0..3] += (a, b, c, d) in one 16-byte global reduction (p 16-byte aligned).
 __device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d) {

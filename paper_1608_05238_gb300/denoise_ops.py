@@ -42,7 +42,7 @@ class _Slice(C.Structure):
     _fields_ = [("data", C.c_void_p), ("stride", C.c_int32), ("off", C.c_int32)]
 
 
-EXPORTS = ("dn_conv", "dn_conv_head", "dn_wgrad", "dn_wgrad_nhwc", "dn_to_ct", "dn_pool2", "dn_pool2_bwd", "dn_up2", "dn_up2_bwd", "dn_bias_grad",
+EXPORTS = ("dn_conv", "dn_conv_head", "dn_wgrad", "dn_wgrad_nhwc", "dn_wgrad_bias_nhwc", "dn_to_ct", "dn_pool2", "dn_pool2_bwd", "dn_up2", "dn_up2_bwd", "dn_bias_grad",
            "dn_mse", "dn_residual", "dn_adam", "dn_adam_bias", "dn_adam_multi", "dn_pack_input", "dn_sample_scale", "dn_pack_target", "dn_predict_output",
            "dn_unpack_output", "dn_check")
 
@@ -58,6 +58,7 @@ def lib():
             "dn_conv_head": [C.POINTER(_ConvDesc), C.POINTER(_HeadDesc), vp],
             "dn_wgrad": [i32, i32, i32, i32, i32, i32, vp, vp, vp, vp],
             "dn_wgrad_nhwc": [S, S, i32, i32, i32, i32, i32, i32, vp, vp],
+            "dn_wgrad_bias_nhwc": [S, S, i32, i32, i32, i32, i32, i32, vp, vp, vp],
             "dn_to_ct": [S, i32, i32, i32, i32, i32, vp, vp],
             "dn_pool2": [S, i32, i32, i32, i32, S, vp],
             "dn_pool2_bwd": [S, S, S, i32, i32, i32, i32, S, vp],
@@ -124,9 +125,14 @@ def wgrad(dzT: torch.Tensor, xT: torch.Tensor, B, H, W, taps, cout, cin, dw: tor
     _call("dn_wgrad", B, H, W, taps, cout, cin, _p(dzT), _p(xT), _p(dw), _stream(stream))
 
 
-def wgrad_nhwc(dz: Act, x: Act, taps: int, dw: torch.Tensor, stream=None):
-    """dw[n][tap][c] += sum over pixels of dz[p][n] x[p + tap][c], read from the NHWC slices."""
-    _call("dn_wgrad_nhwc", dz.s(), x.s(), x.B, x.H, x.W, taps, dz.C, x.C, _p(dw), _stream(stream))
+def wgrad_nhwc(dz: Act, x: Act, taps: int, dw: torch.Tensor, db: torch.Tensor | None = None, stream=None):
+    """dw[n][tap][c] += sum over pixels of dz[p][n] x[p + tap][c], read from the NHWC slices; with
+    ``db`` also the bias gradient db[n] += sum over pixels of dz[p][n] (``dn_wgrad_bias_nhwc``)."""
+    if db is None:
+        _call("dn_wgrad_nhwc", dz.s(), x.s(), x.B, x.H, x.W, taps, dz.C, x.C, _p(dw), _stream(stream))
+    else:
+        assert db.is_cuda and db.dtype == torch.float32 and db.numel() >= dz.C
+        _call("dn_wgrad_bias_nhwc", dz.s(), x.s(), x.B, x.H, x.W, taps, dz.C, x.C, _p(dw), _p(db), _stream(stream))
 
 
 def to_ct(src: Act, shifted: bool, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -212,8 +212,7 @@ class UNet:
 
     def _wgrad(self, lay: Conv, dz: torch.Tensor, x: Act):
         # straight from the NHWC activations (MN-major operands, no transposed copies)
-        ops.wgrad_nhwc(Act(dz, lay.cout), x, lay.taps, lay.gw)
-        ops.bias_grad(Act(dz, lay.cout), lay.gb)
+        ops.wgrad_nhwc(Act(dz, lay.cout), x, lay.taps, lay.gw, db=lay.gb)  # + the bias gradient
 
     def backward(self):
         """Gradients of the loss computed by the last ``loss()`` into every layer's gw, gb."""

@@ -55,12 +55,16 @@ def test_wgrad_matches_autograd(B, H, W, cin, cout, taps):
                                                             (2, 4, 128, 192, 33, 9, 8, 0), (1, 3, 64, 64, 16, 9, 0, 64)])
 def test_wgrad_nhwc_matches_autograd(B, H, W, cin, cout, taps, xoff, zoff):
     """The weight gradient read straight from NHWC slices (MN-major operands, tap shifts as TMA
-    coordinates) equals FP64 autograd of the convolution, also for slices at channel offsets."""
+    coordinates) equals FP64 autograd of the convolution, also for slices at channel offsets; the
+    bias gradient that comes with it is the pixel sum of dz."""
     x = _nhwc(B, H, W, cin + xoff, r64(cin + xoff), 11)
     dz = _nhwc(B, H, W, cout + zoff, r64(cout + zoff), 12)
     dw = torch.zeros(cout, taps, cin, device="cuda")
-    ops.wgrad_nhwc(Act(dz, cout, zoff), Act(x, cin, xoff), taps, dw)
+    db = torch.full((cout,), 0.25, device="cuda")
+    ops.wgrad_nhwc(Act(dz, cout, zoff), Act(x, cin, xoff), taps, dw, db=db)
     ops.check()
+    ref_db = dz.double().cpu()[..., zoff:zoff + cout].sum(dim=(0, 1, 2)) + 0.25
+    assert torch.allclose(db.cpu().double(), ref_db, rtol=1e-5, atol=1e-3), (db.cpu()[:4], ref_db[:4])
     k = 3 if taps == 9 else 1
     xc = x.double().cpu()[..., xoff:xoff + cin].permute(0, 3, 1, 2)
     w = torch.zeros(cout, cin, k, k, dtype=torch.float64, requires_grad=True)
