@@ -50,6 +50,7 @@ def _args():
     ap.add_argument("--cpu-sample", type=int, default=200_000, help="oracle packets (fwd and adj) for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad-error", action="store_true", help="skip the gradient-error measurement")
+    ap.add_argument("--no-red-probe", action="store_true", help="skip the tally-reduction ceiling measurement")
     ap.add_argument("--plain-gd", action="store_true", help="invert256: no fluence preconditioning")
     ap.add_argument("--conv", default="128,128", help="conv: input,output channels of the timed 3x3 layer")
     ap.add_argument("--workload", default="grad256",
@@ -223,6 +224,30 @@ def _reference(args):
 
 
 # ------------------------------------------------------------------------------- GPU leg
+def l2_reduction_peak(rows, n_coeff, blocks=152 * 8, threads=256, iters=20000, reps=3):
+    """Measured ceiling of the tally reductions (mc_reduction_probe): warps adding 1 to the first
+    n_coeff 64-bit words of pseudo-random rows of a tally of this workload's shape, in the
+    deposit's coalesced pattern, with no transport work.  Returns the best payload rate of
+    ``reps`` event-timed runs (GB/s of 8-byte reductions) and checks the tally's total."""
+    import torch
+    from paper_1608_05238_gb300 import mcr
+    row_words = (n_coeff + 15) // 16 * 16 if n_coeff > 32 else (n_coeff + 3) // 4 * 4
+    tally = torch.zeros(rows, row_words, dtype=torch.int64, device="cuda")
+    mcr.reduction_probe(tally, n_coeff, 100, blocks, threads)  # warm-up
+    best = 0.0
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        mcr.reduction_probe(tally, n_coeff, iters, blocks, threads)
+        b.record()
+        b.synchronize()
+        best = max(best, blocks * threads // 32 * iters * n_coeff * 8 / (a.elapsed_time(b) * 1e-3) / 1e9)
+    warps = blocks * threads // 32
+    assert int(tally.sum()) == warps * n_coeff * (100 + reps * iters), "reduction probe lost updates"
+    return {"value": best, "unit": "GB/s", "how": f"mc_reduction_probe: {warps} warps x {iters} random rows of "
+            f"{rows} x {row_words} int64, {n_coeff} coalesced 8-byte reductions per row, best of {reps}"}
+
+
 def _gpu(args):
     import torch
     rank, world, local = _dist()
@@ -358,6 +383,9 @@ def _gpu(args):
                 "traffic": TRANSPORT_DRAM_BYTES.get(w.name), "kernel": "k_transport", "launch_ms": avg_ms, "launches_timed": launches,
                 "segments_per_launch": avg_segs, "bytes_per_segment": C * 8,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+    if not args.no_red_probe:
+        red = l2_reduction_peak(w.nx * w.nz, C)
+        roofline["l2_reduction_peak"] = dict(red, frac=achieved_gbs / red["value"])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -249,6 +249,19 @@ int mc_check(void *stream);
  */
 int mc_last_run_info(int32_t which, mcr_stats *stats, float *transport_ms);
 
+/*
+ * mc_reduction_probe -- measurement kernel (the paper has no counterpart): the ceiling of the
+ * deposit step of Sec. 3.1 (Eqs. 9-11), one 64-bit reduction per coefficient per pixel segment.
+ * blocks x threads threads (threads a multiple of 32, <= 1024) run `iters` iterations per warp;
+ * each picks a pseudo-random row of `tally` (device, rows x row_words uint64, 8-byte aligned,
+ * caller-owned) and adds 1 to its words [0, C) in 32-lane coalesced chunks, as the transport's
+ * warp-cooperative deposit does.  Afterwards the words of the tally sum to (blocks threads / 32)
+ * iters C more than before.  Asynchronous on `stream`; time it with events around the call.
+ * The payload rate is 8 C (blocks threads / 32) iters bytes per duration.
+ */
+int mc_reduction_probe(void *tally, int64_t rows, int32_t row_words, int32_t C, int64_t iters, int32_t blocks,
+                       int32_t threads, void *stream);
+
 /* Frees the calling device's workspace (synchronises the device). */
 int mc_release_workspace(void);
 

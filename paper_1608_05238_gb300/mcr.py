@@ -27,7 +27,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_EVENT_LIMIT, ERR_TALLY_OVERFLOW, ERR_MEDIU
 # every symbol declared in include/mcr.h
 EXPORTS = ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_run_batch", "mc_h_eps", "mc_eps",
            "mc_adjoint_source", "mc_gradient", "mc_gradient_f32", "mc_check", "mc_last_run_info",
-           "mc_release_workspace", "mc_status_string", "mc_version")
+           "mc_release_workspace", "mc_status_string", "mc_version", "mc_reduction_probe")
 MAX_BATCH = 64
 ERR_SCRATCH = -7
 
@@ -100,6 +100,7 @@ def load() -> C.CDLL:
         lib.mc_gradient_f32.argtypes = [C.POINTER(_Medium), C.c_int32, vp, vp, vp, vp, vp, vp]
         lib.mc_eps.argtypes = [C.c_int64, C.c_double, vp, vp, vp, vp, vp]
         lib.mc_check.argtypes = [vp]
+        lib.mc_reduction_probe.argtypes = [vp, C.c_int64, C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32, vp]
         lib.mc_last_run_info.argtypes = [C.c_int32, C.POINTER(_Stats), C.POINTER(C.c_float)]
         lib.mc_release_workspace.argtypes = []
         lib.mc_status_string.argtypes = [C.c_int]
@@ -377,3 +378,15 @@ def last_run_info(which: str = "forward"):
 
 def release_workspace():
     _check(load().mc_release_workspace(), "mc_release_workspace")
+
+
+def reduction_probe(tally: torch.Tensor, n_coeff: int, iters: int, blocks: int, threads: int = 256, stream=None):
+    """``mc_reduction_probe``: (blocks x threads / 32) warps each add 1 to the first n_coeff words of
+    ``iters`` pseudo-random rows of ``tally`` (int64 [rows, row_words], device) in the deposit's
+    32-lane coalesced pattern -- the ceiling of the tally reductions, timed by the caller."""
+    assert tally.is_cuda and tally.dtype == torch.int64 and tally.dim() == 2 and tally.is_contiguous()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = load().mc_reduction_probe(C.c_void_p(tally.data_ptr()), tally.shape[0], tally.shape[1], n_coeff, iters,
+                                   blocks, threads, C.c_void_p(s.cuda_stream))
+    if rc != 0:
+        raise McrError(rc, "mc_reduction_probe")
