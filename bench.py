@@ -173,6 +173,7 @@ def cpu_oracle_rate(w, Hmeas_np, n_sample: int, seed: int = 0):
     per = max(1, n_sample // len(w.sources))
     fw = oracle.forward(mua, mus, dx, g, w.sources[0], RunParams(K=w.K, n_packets=per, seed=seed,
                                                                   n_threads=cores))
+    fw_stats = dict(fw.stats)  # the first source's packets (per-photon work)
     for s in range(1, len(w.sources)):  # one illumination: the sources' fluences add
         fw.coeff += oracle.forward(mua, mus, dx, g, w.sources[s], RunParams(K=w.K, n_packets=per, seed=seed,
                                                                              stream_id=2 * s, n_threads=cores)).coeff
@@ -183,7 +184,10 @@ def cpu_oracle_rate(w, Hmeas_np, n_sample: int, seed: int = 0):
                                                        n_threads=cores))
     F.dL_dmu(fw.coeff, ad.coeff, v, dx, g)
     dt = time.perf_counter() - t0
-    return 2 * n_sample / dt, cores, dt
+    fs, as_ = fw_stats, ad.stats
+    work = {"forward": {"segments": fs["segments"] / fs["launched"], "collisions": fs["collisions"] / fs["launched"]},
+            "adjoint": {"segments": as_["segments"] / as_["launched"], "collisions": as_["collisions"] / as_["launched"]}}
+    return 2 * n_sample / dt, cores, dt, work
 
 
 def _reference(args):
@@ -207,7 +211,7 @@ def _reference(args):
         cpu_oracle_rate(w, Hmeas, n, seed=10 * k)
     times = []
     for k in range(args.steps):
-        rate, cores, dt = cpu_oracle_rate(w, Hmeas, n, seed=100 + 10 * k)
+        rate, cores, dt, _ = cpu_oracle_rate(w, Hmeas, n, seed=100 + 10 * k)
         times.append(dt)
     T = float(np.sum(times))
     value = 2 * n * args.steps / T
@@ -303,6 +307,7 @@ def _gpu(args):
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     tr_ms, segs = [], []
+    work = {"forward": [0, 0, 0], "adjoint": [0, 0, 0]}  # launched, segments, collisions
     for k in range(args.steps):
         flush.zero_()  # L2 flush between timed steps (outside the timed events)
         ev[k][0].record(stream)
@@ -313,6 +318,8 @@ def _gpu(args):
             st, ms = mcr.last_run_info(which)
             tr_ms.append(ms)
             segs.append(st["segments"])
+            for i, key in enumerate(("launched", "segments", "collisions")):
+                work[which][i] += st[key]
     torch.cuda.synchronize()
     clk = clocks.stop()
     mcr.check()
@@ -391,13 +398,15 @@ def _gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         hm_np = Hmeas.double().cpu().numpy()
         sample = args.cpu_sample if w.name == "grad256" else max(4, args.cpu_sample // 20)
-        rate, cores, dt = cpu_oracle_rate(w, hm_np, sample)
+        rate, cores, dt, owork = cpu_oracle_rate(w, hm_np, sample)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{sample} forward + {sample} adjoint packets of {w.name} "
-                         f"(full grid, K={w.K}), {dt:.1f} s"}
+                         f"(full grid, K={w.K}), {dt:.1f} s", "work_per_photon": owork}
 
     if rank == 0:
         cfg = _workload_config(w, n)
+        cfg["work_per_photon"] = {k: {"segments": v[1] / v[0], "collisions": v[2] / v[0]} for k, v in work.items()
+                                  if v[0] > 0}
         cfg.update({"l2": "flushed between timed steps (256 MB write)", "grad_evals_per_s": value / (n_fwd + n),
                     "gradient_error_at_this_packet_count": grad_err,
                     "parallelism": f"replicas{world}" if world > 1 else "single"})
