@@ -53,16 +53,21 @@ def _args():
     ap.add_argument("--no-red-probe", action="store_true", help="skip the tally-reduction ceiling measurement")
     ap.add_argument("--plain-gd", action="store_true", help="invert256: no fluence preconditioning")
     ap.add_argument("--conv", default="128,128", help="conv: input,output channels of the timed 3x3 layer")
+    ap.add_argument("--unknown", default="mua", choices=["mua", "mus"], help="invert_rect: the reconstructed map")
+    ap.add_argument("--iters", type=int, default=None, help="invert_rect: iteration cap (default 20 mua, 40 mus)")
     ap.add_argument("--workload", default="grad256",
-                    choices=["grad256", "large1024", "batch64", "denoise256", "conv", "invert256", "unet256"],
+                    choices=["grad256", "large1024", "batch64", "denoise256", "conv", "invert256", "unet256", "invert_rect"],
                     help="grad256: the gradient evaluation (default); large1024: the same on 1024^2 px at "
                          "K = 64 with four edge sources; batch64: 64 forward problems in one graph-captured "
                          "batched launch; denoise256: the learned denoiser; conv: one large tensor-core "
                          "convolution (profiling case); invert256: mu_a reconstruction on the grad256 phantom; "
-                         "unet256: U-Net training step and inference on synthetic maps (profiling case)")
+                         "unet256: U-Net training step and inference on synthetic maps (profiling case); invert_rect: "
+                         "the Sec. 6 reconstructions on the rectangular-inclusion domain (--unknown mua|mus)")
     args = ap.parse_args()
     if args.packets is None:
         args.packets = 20_000_000 if args.workload == "large1024" else 10_000_000
+    if args.iters is None:
+        args.iters = 20 if args.unknown == "mua" else 40
     return args
 
 
@@ -727,6 +732,73 @@ def _invert256(args):
     return 0
 
 
+def _invert_rect(args):
+    """The reconstructions of Sec. 6 on its rectangular-inclusion domain (workloads.rect_phantom):
+    --unknown mua: mu_a only (mu_s known), gradient descent with the Hager-Zhang line search and
+    the Eq. 29 stop at 1e-9 (Sec. 6.1); --unknown mus: mu_s only (mu_a known), backtracking with
+    the sufficient-decrease constant 0.2 of Eq. 30, steps kept in [1e5, 1e9] and a 1e-5 stop
+    (Sec. 6.2).  K = 10, --packets
+    per MC run (the paper used 1e8), H^meas from 1e8 packets with seed 1001, homogeneous
+    background start.  Reports the mean relative error after every accepted step."""
+    import torch
+    from paper_1608_05238_gb300 import _build, mcr, workloads
+    from paper_1608_05238_gb300.autograd import MCSpec, forward_coefficients
+    from paper_1608_05238_gb300.inversion import invert, mean_relative_error
+    _build.build()
+    n_pk = args.packets
+    mua_t, mus_t, g, srcs = workloads.rect_phantom()
+    dx = float(np.float32(0.05))
+    g = float(np.float32(g))
+    dev = torch.device("cuda")
+    mua_t, mus_t = torch.from_numpy(mua_t).to(dev), torch.from_numpy(mus_t).to(dev)
+    sources = [mcr.Source(**s) for s in srcs]
+    med_t = mcr.Medium(mua_t, mus_t, dx, g)
+    Hmeas = mcr.h_eps(med_t, forward_coefficients(med_t, MCSpec(dx=dx, g=g, sources=sources, K=0,
+                                                                 n_packets=100_000_000, seed=1001)))
+    spec = MCSpec(dx=dx, g=g, sources=sources, K=10, n_packets=n_pk)
+    if args.unknown == "mua":
+        start = torch.full_like(mua_t, 0.01)
+        kw = dict(unknowns=("mua",), tol=1e-9, line_search="hager_zhang", mua_true=mua_t)
+        x0, fixed = start, mus_t
+        run = lambda iters: invert(x0, fixed, Hmeas, spec, iters=iters, **kw)
+        err0 = mean_relative_error(start, mua_t)
+    else:
+        start = torch.full_like(mus_t, 5.0)
+        kw = dict(unknowns=("mus",), tol=1e-5, line_search="backtracking", armijo=0.2, shrink=0.5,
+                  step_bounds=(1e5, 1e9), mus_true=mus_t)
+        run = lambda iters: invert(mua_t, start, Hmeas, spec, iters=iters, **kw)
+        err0 = mean_relative_error(start, mus_t)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = run(args.iters)
+    torch.cuda.synchronize()
+    T = time.perf_counter() - t0
+    key = "rel_err_mua" if args.unknown == "mua" else "rel_err_mus"
+    hist = [{"it": h.it, "eps": h.eps, "step": h.step, "mc_evals": h.trials, key: getattr(h, key),
+             "seconds": h.seconds} for h in res.history]
+    final = getattr(res.history[-1], key) if res.history else err0
+    # inside the reconstructed map's inclusion: its mean value and mean relative error
+    est, true = (res.mua, mua_t) if args.unknown == "mua" else (res.mus, mus_t)
+    incl = true > true.min()
+    inclusion = {"true": float(true[incl].mean()), "start": float(start[incl].mean()),
+                 "estimate_mean": float(est[incl].mean()),
+                 "rel_err_start": mean_relative_error(start[incl], true[incl]),
+                 "rel_err": mean_relative_error(est[incl], true[incl])}
+    out = {"metric": f"{args.unknown} reconstruction (Sec. 6): mean relative error", "value": final,
+           "unit": "relative error", "n_gpus": 1, "steps": len(res.history), "warmup": 0,
+           "ms_per_step": 1e3 * T / max(1, len(res.history)), "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+i64 (FP64 gradient)", "data": "synthetic",
+           "config": {"workload": f"invert_rect: 80x80 px of 0.05 mm, rectangular inclusions (mu_a 0.01/0.2, "
+                                  f"mu_s 5/15), g 0.9, line sources on z=0 and x=4 mm, K=10, {n_pk:.0e} packets "
+                                  f"per MC run, " + ("Hager-Zhang GD, tol 1e-9" if args.unknown == "mua"
+                                                     else "backtracking GD (Eq. 30 nu 0.2), tol 1e-5"),
+                      "initial_rel_err": err0, "inclusion": inclusion, "converged": res.converged, "seconds": T,
+                      "history": hist},
+           "cpu_baseline": None}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def replace_spec(spec, **kw):
     from dataclasses import replace
     return replace(spec, **kw)
@@ -744,6 +816,8 @@ def main():
         return _conv_only(args)
     if args.workload == "unet256" and args.impl != "reference":
         return _unet256(args)
+    if args.workload == "invert_rect" and args.impl != "reference":
+        return _invert_rect(args)
     if args.impl == "reference":
         return _reference(args)
     return _gpu(args)

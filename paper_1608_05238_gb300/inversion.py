@@ -8,10 +8,18 @@ sufficiently (Eq. 30) and a stop once the relative decrease of eps falls below a
 
 * the gradient comes from ``eps.backward()`` through ``HFromMu`` / ``EpsFromH`` (forward MC,
   adjoint MC, FP64 gradient combine, all in the CUDA library);
-* the line search is backtracking: start from the previous accepted step times ``grow``, shrink
-  by ``nu`` until eps(mu - alpha g) <= eps(mu) - c1 alpha |g|^2; its trial forward runs reuse
+* the default line search is backtracking: start from the previous accepted step times ``grow``,
+  shrink until eps(mu - alpha g) <= eps(mu) - armijo alpha |g|^2; its trial forward runs reuse
   the iteration's seed (common random numbers), so a trial is compared with the same packets'
   estimate of eps at mu and MC noise does not decide the comparison;
+* or (``line_search="hager_zhang"``, the paper's choice for mu_a) the Hager-Zhang line search:
+  a bracketing phase, secant steps and bisection until a trial step meets the Wolfe or the
+  approximate Wolfe conditions; every trial is a full gradient evaluation (forward + adjoint MC)
+  on the iteration's seeds;
+* ``armijo`` is the sufficient-decrease constant of Eq. 30 (the paper's nu = 0.2 for its mu_s
+  reconstruction), ``shrink`` the backtracking factor (not stated in the paper; 0.2 by default)
+  and ``step_bounds`` the range the backtracking step is kept in (the paper's [1e5, 1e9] for mu_s
+  in its units); the stop is Eq. 29, |eps_i - eps_(i-1)| / |eps_i| < tol;
 * mu stays positive (mu_a >= mu_floor, mu_s >= mu_floor);
 * optionally (``precondition=True``, mu_a only; not in the paper) the mu_a step is scaled per
   pixel by 1 / (dx^2 Phi_i^2), the curvature of the local part of eps, dx^2 (H^meas - mu_a Phi)^2 / 2,
@@ -70,19 +78,142 @@ def _eps(mua, mus, Hmeas, spec):
         return float(EpsFromH.apply(HFromMu.apply(mua, mus, spec), Hmeas, spec.dx))
 
 
+@dataclass
+class HZParams:
+    """Constants of the Hager-Zhang line search (their published defaults): Wolfe constants delta
+    and sigma, the approximate-Wolfe tolerance epsilon |phi(0)|, the bisection point theta, the
+    required interval shrink gamma, the bracket growth rho, and an evaluation budget."""
+    delta: float = 0.1
+    sigma: float = 0.9
+    epsilon: float = 1e-6
+    theta: float = 0.5
+    gamma: float = 0.66
+    rho: float = 5.0
+    max_evals: int = 10
+
+
+class _Accept(Exception):
+    pass
+
+
+class _OutOfEvals(Exception):
+    pass
+
+
+def _secant(a, ga, b, gb):
+    return (a * gb - b * ga) / (gb - ga) if gb != ga else 0.5 * (a + b)
+
+
+def hager_zhang(phi, f0: float, g0: float, c: float, p: HZParams = HZParams()):
+    """Hager-Zhang line search on phi(alpha) -> (value, slope) from phi(0) = f0, phi'(0) = g0 < 0
+    and the initial trial step c > 0.  Returns (alpha, phi(alpha), phi'(alpha), evaluations) for
+    the first evaluated step that meets the Wolfe conditions
+        phi(a) - f0 <= delta a g0   and   phi'(a) >= sigma g0
+    or the approximate Wolfe conditions
+        (2 delta - 1) g0 >= phi'(a) >= sigma g0   and   phi(a) <= f0 + epsilon |f0|;
+    when the budget runs out first, the evaluated step with the lowest value among those with a
+    sufficient decrease, else alpha = None."""
+    eps_k = p.epsilon * abs(f0)
+    vals = {0.0: (f0, g0)}
+    n = [0]
+
+    def ev(a):
+        if a in vals:
+            return vals[a]
+        if n[0] >= p.max_evals:
+            raise _OutOfEvals
+        f, g = phi(a)
+        n[0] += 1
+        vals[a] = (f, g)
+        wolfe = f - f0 <= p.delta * a * g0 and g >= p.sigma * g0
+        approx = (2 * p.delta - 1) * g0 >= g >= p.sigma * g0 and f <= f0 + eps_k
+        if wolfe or approx:
+            raise _Accept(a)
+        return f, g
+
+    def bisect(a, b):  # a: slope < 0, value <= f0 + eps_k; b: slope < 0, value above it
+        for _ in range(64):
+            d = (1 - p.theta) * a + p.theta * b
+            fd, gd = ev(d)
+            if gd >= 0:
+                return a, d
+            if fd <= f0 + eps_k:
+                a = d
+            else:
+                b = d
+        return a, b
+
+    def update(a, b, c):
+        if not a < c < b:
+            return a, b
+        fc, gc = ev(c)
+        if gc >= 0:
+            return a, c
+        if fc <= f0 + eps_k:
+            return c, b
+        return bisect(a, c)
+
+    def secant2(a, b):
+        c = _secant(a, vals[a][1], b, vals[b][1])
+        A, B = update(a, b, c)
+        if c == B:
+            return update(A, B, _secant(b, vals[b][1], B, vals[B][1]))
+        if c == A:
+            return update(A, B, _secant(a, vals[a][1], A, vals[A][1]))
+        return A, B
+
+    def bracket(c):
+        good = 0.0  # the largest trial so far with a negative slope and a value <= f0 + eps_k
+        for _ in range(64):
+            fc, gc = ev(c)
+            if gc >= 0:
+                return good, c
+            if fc > f0 + eps_k:
+                return bisect(0.0, c)
+            good, c = c, c * p.rho
+        return good, c
+
+    try:
+        a, b = bracket(c)
+        for _ in range(64):
+            A, B = secant2(a, b)
+            if B - A > p.gamma * (b - a):
+                A, B = update(A, B, 0.5 * (A + B))
+            if B - A <= 1e-12 * max(B, 1e-300):
+                break
+            a, b = A, B
+    except _Accept as e:
+        alpha = e.args[0]
+        return alpha, vals[alpha][0], vals[alpha][1], n[0]
+    except _OutOfEvals:
+        pass
+    good = [(f, a) for a, (f, g) in vals.items() if a > 0 and f <= f0 + p.delta * a * g0]
+    if good:
+        f, a = min(good)
+        return a, f, vals[a][1], n[0]
+    return None, f0, g0, n[0]
+
+
 def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MCSpec, unknowns=("mua",),
-           iters: int = 20, tol: float = 1e-5, step0: float | None = None, nu: float = 0.2, grow: float = 2.0,
-           c1: float = 1e-4, max_trials: int = 12, mu_floor: float = 1e-6, mua_true=None, mus_true=None,
+           iters: int = 20, tol: float = 1e-5, line_search: str = "backtracking", step0: float | None = None,
+           shrink: float = 0.2, grow: float = 2.0, armijo: float = 1e-4, step_bounds: tuple | None = None,
+           max_trials: int = 12, hz: HZParams | None = None, mu_floor: float = 1e-6, mua_true=None, mus_true=None,
            seed0: int = 1, precondition: bool = False) -> InversionResult:
     """Reconstruct ``unknowns`` (a subset of ("mua", "mus")) from H^meas; the others stay fixed.
 
     ``step0`` defaults to the step that changes the unknowns by 10 % of their norm on the first
-    iteration (1, a full fixed-point-like step, with ``precondition``).  Returns the estimates and one ``Iteration`` record per accepted step.
+    iteration (1, a full fixed-point-like step, with ``precondition``; for the Hager-Zhang search
+    its first trial is 0.01 max|mu| / max|d|).  Returns the estimates and one ``Iteration``
+    record per accepted step (``trials`` = MC evaluations of the line search).
     """
+    if line_search not in ("backtracking", "hager_zhang"):
+        raise ValueError(f"line_search must be 'backtracking' or 'hager_zhang', not {line_search!r}")
     want_a, want_s = "mua" in unknowns, "mus" in unknowns
     mua, mus = mua0.detach().clone(), mus0.detach().clone()
     res = InversionResult(mua, mus)
     alpha = step0
+    lo, hi = step_bounds if step_bounds is not None else (0.0, float("inf"))
+    hzp = hz or HZParams()
     t0 = time.perf_counter()
     for it in range(iters):
         s_it = replace(spec, seed=seed0 + 1009 * it, adjoint_seed=seed0 + 1009 * it + 1)
@@ -98,24 +229,53 @@ def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MC
         if slope <= 0.0:
             res.converged = True
             break
-        if alpha is None:
-            norm_mu = sum(float((m.double() ** 2).sum()) for m, w in ((mua, want_a), (mus, want_s)) if w) ** 0.5
-            norm_d = sum(float((d.double() ** 2).sum()) for d in (da, ds) if d is not None) ** 0.5
-            alpha = (1.0 if precondition else 0.1 * norm_mu / norm_d)
-        else:
-            alpha = min(alpha * grow, 1.0) if precondition else alpha * grow
-        accepted = False
-        for trial in range(1, max_trials + 1):
-            na = (mua + alpha * da).clamp_min(mu_floor) if want_a else mua
-            ns = (mus + alpha * ds).clamp_min(mu_floor) if want_s else mus
-            e_new = _eps(na, ns, Hmeas, s_it)
-            if e_new <= eps - c1 * alpha * slope:
-                accepted = True
+
+        def step_to(a):
+            na = (mua + a * da).clamp_min(mu_floor) if want_a else mua
+            ns = (mus + a * ds).clamp_min(mu_floor) if want_s else mus
+            return na, ns
+
+        if line_search == "hager_zhang":
+            if alpha is None:
+                amax = max(float(m.abs().max()) for m, w in ((mua, want_a), (mus, want_s)) if w)
+                dmax = max(float(d.abs().max()) for d in (da, ds) if d is not None)
+                c = 0.01 * amax / dmax
+            else:
+                c = 2.0 * alpha
+
+            def phi_fn(a):
+                na, ns = step_to(a)
+                e, ga2, gs2, _ = _eps_and_grad(na, ns, Hmeas, s_it, want_a, want_s)
+                return e, sum(float((g.double() * d.double()).sum()) for g, d in ((ga2, da), (gs2, ds))
+                              if g is not None)
+
+            a_acc, e_new, _, trial = hager_zhang(phi_fn, eps, -slope, c, hzp)
+            if a_acc is None:
+                res.converged = True  # no step with a sufficient decrease within the budget
                 break
-            alpha *= nu
-        if not accepted:
-            res.converged = True  # no sufficient decrease at the smallest trial step
-            break
+            alpha = a_acc
+            na, ns = step_to(alpha)
+        else:
+            if alpha is None:
+                norm_mu = sum(float((m.double() ** 2).sum()) for m, w in ((mua, want_a), (mus, want_s)) if w) ** 0.5
+                norm_d = sum(float((d.double() ** 2).sum()) for d in (da, ds) if d is not None) ** 0.5
+                alpha = (1.0 if precondition else 0.1 * norm_mu / norm_d)
+            else:
+                alpha = min(alpha * grow, 1.0) if precondition else alpha * grow
+            alpha = min(max(alpha, lo), hi)
+            accepted = False
+            for trial in range(1, max_trials + 1):
+                na, ns = step_to(alpha)
+                e_new = _eps(na, ns, Hmeas, s_it)
+                if e_new <= eps - armijo * alpha * slope:  # Eq. 30
+                    accepted = True
+                    break
+                if alpha * shrink < lo:
+                    break
+                alpha *= shrink
+            if not accepted:
+                res.converged = True  # no sufficient decrease down to the smallest allowed step
+                break
         mua, mus = na, ns
         torch.cuda.synchronize()
         rec = Iteration(it, e_new, alpha, trial, time.perf_counter() - t0)
@@ -124,7 +284,7 @@ def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MC
         if mus_true is not None:
             rec.rel_err_mus = mean_relative_error(mus, mus_true)
         res.history.append(rec)
-        if eps - e_new <= tol * eps:  # relative decrease below tol (same packets on both sides)
+        if abs(e_new - eps) <= tol * abs(e_new):  # Eq. 29 (both values from the same packets)
             res.converged = True
             break
     res.mua, res.mus = mua, mus

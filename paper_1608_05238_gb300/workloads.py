@@ -97,6 +97,27 @@ def edge_line_sources(n: int, dx: float, per_edge: int = 1) -> list:
     return out
 
 
+def rect_phantom(n: int = 80, dx: float = 0.05):
+    """The test domain of the reconstructions of Sec. 6: 4 mm x 4 mm (n = 80 pixels of 0.05 mm),
+    background mu_a 0.01 and mu_s 5 /mm with a rectangular mu_a inclusion of 0.2 /mm and a
+    rectangular mu_s inclusion of 15 /mm, g 0.9, lit by two equal collimated line sources on
+    adjacent edges: z = 0 (pointing +z) and x = 4 mm (pointing -x).  The inclusions' positions
+    are not given in the text (the figures are not available): the mu_a rectangle spans
+    x in [1, 2] mm, z in [1, 2] mm (the paper's mu_a profile is taken at x = 1.5 mm), the mu_s
+    rectangle x in [2, 3] mm, z in [1.5, 2.5] mm (its profile at x = 2.5 mm).
+    Returns (mua, mus, g, sources)."""
+    L = n * dx
+    c = (np.arange(n) + 0.5) * dx
+    X, Z = np.meshgrid(c, c)  # [iz][ix]
+    mua = np.full((n, n), 0.01, np.float32)
+    mus = np.full((n, n), 5.0, np.float32)
+    mua[(X >= 1.0) & (X <= 2.0) & (Z >= 1.0) & (Z <= 2.0)] = 0.2
+    mus[(X >= 2.0) & (X <= 3.0) & (Z >= 1.5) & (Z <= 2.5)] = 15.0
+    srcs = [dict(kind=LINE, x0=0.0, z0=0.0, x1=L, z1=0.0, dir_x=0.0, dir_z=1.0, power=1.0),
+            dict(kind=LINE, x0=L, z0=0.0, x1=L, z1=L, dir_x=-1.0, dir_z=0.0, power=1.0)]
+    return mua, mus, 0.9, srcs
+
+
 def pencil32() -> Workload:
     n, dx = 32, 0.25
     mua = np.full((n, n), 0.01, np.float32)

@@ -61,3 +61,46 @@ def test_preconditioned_mua_reconstruction_converges_fast():
     e0 = mean_relative_error(mua0, mua_true)
     errs = [h.rel_err_mua for h in res.history]
     assert errs[-1] < 0.15 * e0, (e0, errs)
+
+
+def _rect_setup(n_meas, K, n_packets):
+    mua_t, mus_t, g, srcs = workloads.rect_phantom()
+    dx, g = f32(0.05), f32(g)
+    dev = torch.device("cuda")
+    mua_t, mus_t = torch.from_numpy(mua_t).to(dev), torch.from_numpy(mus_t).to(dev)
+    sources = [mcr.Source(**s) for s in srcs]
+    med = mcr.Medium(mua_t, mus_t, dx, g)
+    Hmeas = mcr.h_eps(med, forward_coefficients(med, MCSpec(dx=dx, g=g, sources=sources, K=0, n_packets=n_meas,
+                                                            seed=1001)))
+    return mua_t, mus_t, Hmeas, MCSpec(dx=dx, g=g, sources=sources, K=K, n_packets=n_packets)
+
+
+def test_hager_zhang_mua_reconstruction_of_the_rectangular_inclusion():
+    """Sec. 6.1's setting (rectangular inclusions, two adjacent line sources, mu_s known, start at
+    the background): gradient descent with the Hager-Zhang line search brings the mean relative
+    mu_a error below half its start within eight iterations and eps down by two orders."""
+    mua_t, mus_t, Hmeas, spec = _rect_setup(20_000_000, 8, 2_000_000)
+    mua0 = torch.full_like(mua_t, 0.01)
+    res = invert(mua0, mus_t, Hmeas, spec, unknowns=("mua",), iters=8, tol=1e-9, line_search="hager_zhang",
+                 mua_true=mua_t)
+    e0 = mean_relative_error(mua0, mua_t)
+    errs = [h.rel_err_mua for h in res.history]
+    assert len(res.history) == 8, res.history
+    assert res.history[-1].eps < 1e-2 * res.history[0].eps, [h.eps for h in res.history]
+    assert errs[-1] < 0.5 * e0, (e0, errs)
+    assert all(h.trials >= 1 for h in res.history) and torch.equal(res.mus, mus_t)
+
+
+def test_backtracking_mus_reconstruction_lowers_eps_within_step_bounds():
+    """Sec. 6.2's mu_s-only setting: backtracking with the Eq. 30 constant 0.2 and steps kept in
+    [1e5, 1e9] lowers eps at every accepted step and moves mu_s inside the inclusion up from the
+    background towards its true value."""
+    mua_t, mus_t, Hmeas, spec = _rect_setup(20_000_000, 8, 2_000_000)
+    mus0 = torch.full_like(mus_t, 5.0)
+    res = invert(mua_t, mus0, Hmeas, spec, unknowns=("mus",), iters=8, tol=1e-5, line_search="backtracking",
+                 armijo=0.2, shrink=0.5, step_bounds=(1e5, 1e9), mus_true=mus_t)
+    assert len(res.history) >= 4
+    assert all(1e5 <= h.step <= 1e9 for h in res.history)
+    assert res.history[-1].eps < 0.5 * res.history[0].eps, [h.eps for h in res.history]
+    incl = mus_t > 10
+    assert float(res.mus[incl].mean()) > 5.5 and torch.equal(res.mua, mua_t)
