@@ -28,7 +28,8 @@ _LIB = os.path.join(_HERE, "libmcr_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PENCIL, LINE, ISO_POINT = 0, 1, 2
+PENCIL, LINE, ISO_POINT, ANGULAR_POINT = 0, 1, 2, 3
+MAX_ANG = 8
 
 
 def build(force: bool = False) -> str:
@@ -49,7 +50,8 @@ class _Medium(C.Structure):
 
 class _Source(C.Structure):
     _fields_ = [("kind", C.c_int32), ("x0", C.c_double), ("z0", C.c_double), ("x1", C.c_double),
-                ("z1", C.c_double), ("dir_x", C.c_double), ("dir_z", C.c_double), ("power", C.c_double)]
+                ("z1", C.c_double), ("dir_x", C.c_double), ("dir_z", C.c_double), ("power", C.c_double),
+                ("n_ang", C.c_int32), ("ang_c", C.c_double * MAX_ANG), ("ang_s", C.c_double * MAX_ANG)]
 
 
 class _Run(C.Structure):
@@ -146,16 +148,25 @@ def _finish(raw, sq, n_packets, S, dx, st) -> Result:
 
 
 def forward(mua, mus, dx, g, source: dict, run: RunParams, with_variance: bool = False) -> Result:
-    """Forward harmonic radiance MC (Sec. 3, 3.1) from a pencil, line or isotropic point source.
+    """Forward harmonic radiance MC (Sec. 3, 3.1) from a pencil, line, isotropic or angular point source.
 
-    ``source``: dict(kind=PENCIL|LINE|ISO_POINT, x0, z0, x1, z1, dir_x, dir_z, power=1).
+    ``source``: dict(kind=PENCIL|LINE|ISO_POINT|ANGULAR_POINT, x0, z0, x1, z1, dir_x, dir_z, power=1,
+    ang_c=[c_1..], ang_s=[s_1..]); an angular point source launches directions theta (from +z)
+    with density (1 + sum_n c_n cos n theta + s_n sin n theta) / (2 pi) -- a detector's angular
+    sensitivity as a source (Sec. 4.1).
     Returns coefficients a_0, a_n, b_n (Eqs. 9-11) normalised by power / (N_p dx^2).
     """
     lib = _load()
     m, keep = _medium(mua, mus, dx, g)
+    ac, as_ = list(source.get("ang_c", ())), list(source.get("ang_s", ()))
+    n_ang = max(len(ac), len(as_))
+    if n_ang > MAX_ANG:
+        raise ValueError(f"at most {MAX_ANG} angular harmonics")
+    ac, as_ = ac + [0.0] * (MAX_ANG - len(ac)), as_ + [0.0] * (MAX_ANG - len(as_))
     s = _Source(int(source["kind"]), float(source.get("x0", 0.0)), float(source.get("z0", 0.0)),
                 float(source.get("x1", 0.0)), float(source.get("z1", 0.0)), float(source.get("dir_x", 0.0)),
-                float(source.get("dir_z", 1.0)), float(source.get("power", 1.0)))
+                float(source.get("dir_z", 1.0)), float(source.get("power", 1.0)), n_ang,
+                (C.c_double * MAX_ANG)(*map(float, ac)), (C.c_double * MAX_ANG)(*map(float, as_)))
     nz, nx = keep[0].shape
     Cc = 2 * run.K + 1
     raw = np.zeros((Cc, nz, nx), dtype=np.float64)

@@ -68,7 +68,9 @@
 #define ORC_PENCIL 0
 #define ORC_LINE 1
 #define ORC_ISO_POINT 2
-#define ORC_VOLUME 3 /* internal: volumetric isotropic source (adjoint) */
+#define ORC_ANGULAR_POINT 3 /* point source with an angular density (a detector's, Sec. 4.1) */
+#define ORC_VOLUME 100      /* internal: volumetric isotropic source (adjoint) */
+#define ORC_MAX_ANG 8
 
 #define ORC_OK 0
 #define ORC_ERR_ARG -1
@@ -87,6 +89,10 @@ typedef struct {
   double x0, z0, x1, z1; /* mm */
   double dir_x, dir_z;   /* unit direction for pencil / line */
   double power;          /* total source power */
+  /* angular point: p(theta) = (1 + sum_n ang_c[n-1] cos n theta + ang_s[n-1] sin n theta) / (2 pi),
+   * theta from +z, n = 1 .. n_ang */
+  int32_t n_ang;
+  double ang_c[ORC_MAX_ANG], ang_s[ORC_MAX_ANG];
 } orc_source;
 
 typedef struct {
@@ -149,6 +155,26 @@ static double orc_wrap(double th) {
   while (th > M_PI) th -= 2.0 * M_PI;
   while (th <= -M_PI) th += 2.0 * M_PI;
   return th;
+}
+
+/* Direction angle of an angular point source: the theta in [0, 2 pi) with F(theta) = u, where
+ * F(theta) = theta / (2 pi) + (1 / 2 pi) sum_n [c_n sin(n theta) + s_n (1 - cos(n theta))] / n is
+ * the integral of its density from 0 (non-decreasing for a density >= 0), by bisection to the
+ * last FP64 bits. */
+static double orc_angle_sample(const orc_source *s, double u) {
+  double lo = 0.0, hi = 2.0 * M_PI;
+  for (int it = 0; it < 64; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    double F = mid;
+    for (int n = 1; n <= s->n_ang; ++n)
+      F += (s->ang_c[n - 1] * sin(n * mid) + s->ang_s[n - 1] * (1.0 - cos(n * mid))) / n;
+    F /= 2.0 * M_PI;
+    if (F < u)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return 0.5 * (lo + hi);
 }
 
 /* --------------------------------------------- volumetric source sampling */
@@ -260,6 +286,11 @@ static void orc_packet(orc_job *j, uint64_t p) {
       x = s->x0;
       z = s->z0;
       theta = orc_wrap(2.0 * M_PI * orc_u01(b0[2]));
+      break;
+    case ORC_ANGULAR_POINT:
+      x = s->x0;
+      z = s->z0;
+      theta = orc_wrap(orc_angle_sample(s, orc_u01(b0[2])));
       break;
     default: { /* ORC_VOLUME */
       const int64_t pix = orc_volsrc_pick(j->vol, npix, b0[0], b0[1]);
@@ -487,7 +518,8 @@ int orc_forward_raw(const orc_medium *m, const orc_source *s, const orc_run *r, 
                     double *sq, orc_stats *st) {
   int rc = orc_check(m, r);
   if (rc) return rc;
-  if (!s || !tally || !st || s->kind < ORC_PENCIL || s->kind > ORC_ISO_POINT) return ORC_ERR_ARG;
+  if (!s || !tally || !st || s->kind < ORC_PENCIL || s->kind > ORC_ANGULAR_POINT) return ORC_ERR_ARG;
+  if (s->kind == ORC_ANGULAR_POINT && (s->n_ang < 0 || s->n_ang > ORC_MAX_ANG)) return ORC_ERR_ARG;
   return orc_run_packets(m, s, NULL, r, 0, tally, sq, st);
 }
 

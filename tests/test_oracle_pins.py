@@ -374,3 +374,71 @@ def test_volume_sampler_follows_abs_q():
     nz = p > 0
     chi2 = np.sum((counts[nz] - n * p[nz]) ** 2 / (n * p[nz]))
     assert stats.chi2.sf(chi2, nz.sum() - 1) > 1e-4
+
+
+# ------------------------------------------------------------ angular point sources (Sec. 4.1)
+ANG_DENSITIES = [
+    ([0.0, 0.0, 0.0, -1.0], []),      # sin^2(2 theta) / pi, the detector of Sec. 4.1
+    ([], [1.0]),                      # (1 + sin theta) / (2 pi): odd under theta -> theta + pi
+    ([0.3, 0.0, 0.2], [0.0, -0.4]),   # a mixture of cos and sin terms
+]
+
+
+def _ang(v, n):
+    return v[n - 1] if n <= len(v) else 0.0
+
+
+@pytest.mark.parametrize("ac,as_", ANG_DENSITIES)
+def test_angular_point_source_launch_moments(ac, as_):
+    """Launch directions follow p(theta) = (1 + sum_n c_n cos n theta + s_n sin n theta) / (2 pi):
+    with absorption so strong that every packet leaves all its weight in the source pixel, that
+    pixel's a_n / a_0 and b_n / a_0 are the sample means of cos n theta and sin n theta, whose
+    expectations are c_n / 2 and s_n / 2."""
+    n, dx, K, N = 5, 1.0, 6, 200000
+    mua, mus = np.full((n, n), 1000.0), np.zeros((n, n))
+    src = dict(kind=oracle.ANGULAR_POINT, x0=2.5, z0=2.5, ang_c=ac, ang_s=as_)
+    r = oracle.forward(mua, mus, dx, 0.0, src, RunParams(K=K, n_packets=N, seed=21))
+    a0 = r.coeff[0][2, 2]
+    sig = 0.75 / math.sqrt(N)
+    for m in range(1, K + 1):
+        assert abs(r.coeff[2 * m - 1][2, 2] / a0 - _ang(ac, m) / 2) < 5 * sig, (m, r.coeff[2 * m - 1][2, 2] / a0)
+        assert abs(r.coeff[2 * m][2, 2] / a0 - _ang(as_, m) / 2) < 5 * sig, (m, r.coeff[2 * m][2, 2] / a0)
+
+
+def test_reciprocity_case2_angular_detectors():
+    """Case 2 (Eqs. 15, 18): a unit isotropic point source at r_s and a unit point detector at r_d
+    with angular sensitivity p(theta).  The detected signal  int phi(r_d, s) p(s) ds  is
+    (a_0 + sum_n c_n a_n + s_n b_n)(r_d) / (2 pi); by reciprocity it equals Phi*(r_s) / (2 pi), and
+    with the adjoint radiance read as phi*(r, s) = psi(r, -s) (reading A3) Phi*(r_s) is the fluence
+    at r_s of a forward run from r_d with density p(theta + pi), coefficients (-1)^n c_n, (-1)^n s_n.
+    The detector of Sec. 4.1 is even and cannot tell the flip; (1 + sin theta) / (2 pi) is odd and
+    the identity fails without it."""
+    nz = nx = 24
+    dx, g, K = 0.25, 0.5, 4
+    mua, mus = _hetero(nz, nx, 17)
+    mua, mus = mua * 0.2, mus * 0.5
+    ps, pd = (12, 12), (12, 18)  # (iz, ix): the detector 1.5 mm from the source along +x
+
+    def centre(p):
+        return dict(x0=(p[1] + 0.5) * dx, z0=(p[0] + 0.5) * dx)
+
+    def flipped(v):
+        return [(-1) ** n * x for n, x in enumerate(v, start=1)]
+
+    for ac, as_ in ANG_DENSITIES[:2]:
+        det, rec, unflipped = [], [], []
+        for k in range(6):
+            f = oracle.forward(mua, mus, dx, g, dict(kind=oracle.ISO_POINT, **centre(ps)),
+                               RunParams(K=K, n_packets=60000, seed=50 + k))
+            det.append(f.coeff[0][pd] + sum(_ang(ac, n) * f.coeff[2 * n - 1][pd] + _ang(as_, n) * f.coeff[2 * n][pd]
+                                            for n in range(1, K + 1)))
+            run = RunParams(K=0, n_packets=60000, seed=70 + k)
+            rec.append(oracle.forward(mua, mus, dx, g, dict(kind=oracle.ANGULAR_POINT, **centre(pd), ang_c=flipped(ac),
+                                                            ang_s=flipped(as_)), run).coeff[0][ps])
+            unflipped.append(oracle.forward(mua, mus, dx, g, dict(kind=oracle.ANGULAR_POINT, **centre(pd), ang_c=ac,
+                                                                  ang_s=as_), run).coeff[0][ps])
+        det, rec, unflipped = map(np.array, (det, rec, unflipped))
+        se = math.sqrt(det.var(ddof=1) / 6 + rec.var(ddof=1) / 6)
+        assert abs(det.mean() - rec.mean()) < 4 * se + 0.01 * det.mean(), (ac, as_, det.mean(), rec.mean(), se)
+        if as_:  # the odd detector: the missing flip is detected
+            assert abs(det.mean() - unflipped.mean()) > 6 * se + 0.05 * det.mean(), (det.mean(), unflipped.mean(), se)
