@@ -45,6 +45,9 @@ extern "C" {
 #define MCR_PENCIL 0    /* collimated beam from (x0, z0) along (dir_x, dir_z)            */
 #define MCR_LINE 1      /* collimated line source: start uniform on (x0,z0)-(x1,z1)       */
 #define MCR_ISO_POINT 2 /* isotropic point source at (x0, z0)                             */
+#define MCR_ANGULAR_POINT 3 /* point source at (x0, z0) with an angular density (below): a    *
+                             * detector of Sec. 4.1 as the source of an adjoint computation   */
+#define MCR_MAX_ANG 8   /* angular harmonics of an MCR_ANGULAR_POINT density               */
 
 #define MCR_MAX_K 64
 
@@ -60,10 +63,16 @@ typedef struct {
 /* Boundary or point source of a forward run (Sec. 3.2, Sec. 6).  Positions in mm; a point on
  * the far edge of the domain belongs to the last pixel; a point outside the domain escapes. */
 typedef struct {
-  int32_t kind;          /* MCR_PENCIL | MCR_LINE | MCR_ISO_POINT */
+  int32_t kind;          /* MCR_PENCIL | MCR_LINE | MCR_ISO_POINT | MCR_ANGULAR_POINT */
   float x0, z0, x1, z1;  /* pencil / point: (x0, z0); line: segment (x0,z0)-(x1,z1) */
   float dir_x, dir_z;    /* launch direction (pencil, line); normalised by the library */
   float power;           /* total source power S (coefficients scale linearly with it) */
+  /* MCR_ANGULAR_POINT: launch angles theta (from +z, theta = atan2(dir_x, dir_z)) with density
+   * p(theta) = (1 + sum_{n=1..n_ang} ang_c[n-1] cos n theta + ang_s[n-1] sin n theta) / (2 pi),
+   * which must be >= 0 (MCR_ERR_ARG otherwise); 0 <= n_ang <= MCR_MAX_ANG.  Ignored by the
+   * other kinds. */
+  int32_t n_ang;
+  float ang_c[MCR_MAX_ANG], ang_s[MCR_MAX_ANG];
 } mcr_source;
 
 /* Monte Carlo run parameters.  Random numbers: Philox4x32-10 with key (seed_lo,

@@ -95,13 +95,14 @@ int check_run(const mcr_run *r) {
 
 // Normalised launch direction of a boundary source, or MCR_ERR_ARG.
 int check_source(const mcr_source *src, float *dirx, float *dirz) {
-  if (!src || src->kind < MCR_PENCIL || src->kind > MCR_ISO_POINT) return MCR_ERR_ARG;
+  if (!src || src->kind < MCR_PENCIL || src->kind > MCR_ANGULAR_POINT) return MCR_ERR_ARG;
+  if (src->kind == MCR_ANGULAR_POINT && !angular_density_ok(*src)) return MCR_ERR_ARG;
   if (!finite_f(src->x0) || !finite_f(src->z0) || !finite_f(src->x1) || !finite_f(src->z1) ||
       !finite_f(src->power))
     return MCR_ERR_ARG;
   *dirx = 0.f;
   *dirz = 1.f;
-  if (src->kind != MCR_ISO_POINT) {
+  if (src->kind == MCR_PENCIL || src->kind == MCR_LINE) {
     const double nrm = sqrt((double)src->dir_x * src->dir_x + (double)src->dir_z * src->dir_z);
     if (!(nrm > 0.0) || !isfinite(nrm)) return MCR_ERR_ARG;
     *dirx = (float)(src->dir_x / nrm);
@@ -232,6 +233,7 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
       d.z1 = h.src->z1;
       d.dir_x = h.dirx;
       d.dir_z = h.dirz;
+      set_angular(d, *h.src);
     }
     end += chunked ? 0 : h.n_packets;
     d.end = end;
@@ -476,6 +478,19 @@ int tally_exponent(float dx, float w_threshold, float roulette_p) {
   if (q > 60) q = 60;
   if (q < -60) q = -60;
   return q;
+}
+
+bool angular_density_ok(const mcr_source &src) {
+  if (src.n_ang < 0 || src.n_ang > MCR_MAX_ANG) return false;
+  for (int n = 0; n < src.n_ang; ++n)
+    if (!isfinite(src.ang_c[n]) || !isfinite(src.ang_s[n])) return false;
+  for (int i = 0; i < 4096; ++i) {  // 2 pi p(theta) = 1 + sum_n c_n cos n theta + s_n sin n theta
+    const double th = 2.0 * 3.14159265358979323846 * i / 4096.0;
+    double v = 1.0;
+    for (int n = 1; n <= src.n_ang; ++n) v += src.ang_c[n - 1] * cos(n * th) + src.ang_s[n - 1] * sin(n * th);
+    if (v < -1e-6) return false;
+  }
+  return true;
 }
 
 }  // namespace mcr

@@ -17,7 +17,9 @@ int tally_exponent(float dx, float w_threshold, float roulette_p);
 constexpr uint64_t kChunkPackets = 1ull << 26;
 
 // Source kinds seen by the transport kernel (MCR_* plus the volumetric adjoint source).
-constexpr int kVolume = 3;
+constexpr int kVolume = 100;  // not a public MCR_* source kind
+static_assert(kVolume != MCR_PENCIL && kVolume != MCR_LINE && kVolume != MCR_ISO_POINT && kVolume != MCR_ANGULAR_POINT,
+              "the internal volumetric kind must differ from every public source kind");
 
 // Device counters of one run, accumulated per warp.
 struct DevStats {
@@ -46,8 +48,10 @@ struct ProblemDesc {
   float dx;
   float hg_c;    // (1 - g) / (1 + g)
   float qscale;  // 2^q, the fixed-point scale of the deposits
-  int kind;      // MCR_PENCIL | MCR_LINE | MCR_ISO_POINT | kVolume
+  int kind;      // MCR_PENCIL | MCR_LINE | MCR_ISO_POINT | MCR_ANGULAR_POINT | kVolume
   float x0, z0, x1, z1, dir_x, dir_z;
+  int n_ang;     // MCR_ANGULAR_POINT: harmonics of the launch-angle density
+  float ang_c[MCR_MAX_ANG], ang_s[MCR_MAX_ANG];
   unsigned key0, key1;
 };
 
@@ -111,6 +115,18 @@ size_t transport_smem_bytes(int row_stride, int threads, bool merge);
 // 8-byte words per pixel in the fixed-point tally: 2K+1 rounded up to 16 (rows of whole 128-byte
 // lines, so each warp-wide 256-byte reduction touches exactly two lines: 7 % faster at K = 32)
 // when 2K+1 > 32, else up to 4 (a pixel's block starts on a 32-byte sector).
+// The launch-angle density of an MCR_ANGULAR_POINT source into a problem descriptor.
+inline void set_angular(ProblemDesc &d, const mcr_source &src) {
+  d.n_ang = src.kind == MCR_ANGULAR_POINT ? src.n_ang : 0;
+  for (int n = 0; n < MCR_MAX_ANG; ++n) {
+    d.ang_c[n] = n < d.n_ang ? src.ang_c[n] : 0.f;
+    d.ang_s[n] = n < d.n_ang ? src.ang_s[n] : 0.f;
+  }
+}
+// Validation of an MCR_ANGULAR_POINT density: 0 <= n_ang <= MCR_MAX_ANG, finite coefficients,
+// p(theta) >= 0 on a 4096-point grid (tolerance 1e-6 / 2 pi).  Returns false when invalid.
+bool angular_density_ok(const mcr_source &src);
+
 inline int tally_row_words(int C) { return C > 32 ? (C + 15) & ~15 : (C + 3) & ~3; }
 
 // Words per harmonic row in shared memory: channel c at word 1 + c (so the (cos, sin) pairs are

@@ -63,11 +63,12 @@ int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_r
   if (run->K < 0 || run->K > MCR_MAX_K || !(run->roulette_p > 0.f && run->roulette_p <= 1.f)) return MCR_ERR_ARG;
   if (!(run->w_threshold >= 0.f) || !isfinite(run->w_threshold)) return MCR_ERR_ARG;
   if (run->first_packet + run->n_packets < run->first_packet) return MCR_ERR_ARG;
-  if (src->kind < MCR_PENCIL || src->kind > MCR_ISO_POINT) return MCR_ERR_ARG;
+  if (src->kind < MCR_PENCIL || src->kind > MCR_ANGULAR_POINT) return MCR_ERR_ARG;
+  if (src->kind == MCR_ANGULAR_POINT && !angular_density_ok(*src)) return MCR_ERR_ARG;
   if (!isfinite(src->x0) || !isfinite(src->z0) || !isfinite(src->x1) || !isfinite(src->z1) || !isfinite(src->power))
     return MCR_ERR_ARG;
   float dirx = 0.f, dirz = 1.f;
-  if (src->kind != MCR_ISO_POINT) {
+  if (src->kind == MCR_PENCIL || src->kind == MCR_LINE) {
     const double nrm = sqrt((double)src->dir_x * src->dir_x + (double)src->dir_z * src->dir_z);
     if (!(nrm > 0.0) || !isfinite(nrm)) return MCR_ERR_ARG;
     dirx = (float)(src->dir_x / nrm);
@@ -131,6 +132,7 @@ int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_r
   d.z1 = src->z1;
   d.dir_x = dirx;
   d.dir_z = dirz;
+  set_angular(d, *src);
   d.key0 = (unsigned)run->seed;
   d.key1 = (unsigned)(run->seed >> 32) ^ run->stream_id;
   if (run->n_packets && launch_transport(p, TransportLaunch{0, 0, 0, 0}, s) != cudaSuccess) return MCR_ERR_CUDA;

@@ -91,6 +91,31 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Launch angle (from +z) of an MCR_ANGULAR_POINT source: the theta in [0, 2 pi) at which the
+// integral of its density from 0,
+//   F(theta) = (theta + sum_n [c_n sin n theta + s_n (1 - cos n theta)] / n) / (2 pi),
+// reaches u; 24 bisection steps resolve theta to the FP32 spacing of [0, 2 pi).  Runs once per
+// packet, at launch.
+__device__ __forceinline__ float launch_angle(const ProblemDesc &P, float u) {
+  const float two_pi = 6.28318530717958648f;
+  float lo = 0.f, hi = two_pi;
+  const float target = u * two_pi;
+  for (int it = 0; it < 24; ++it) {
+    const float mid = 0.5f * (lo + hi);
+    float F = mid;
+    for (int n = 1; n <= P.n_ang; ++n) {
+      float sn, cn;
+      sincosf(n * mid, &sn, &cn);
+      F += (P.ang_c[n - 1] * sn + P.ang_s[n - 1] * (1.f - cn)) / n;
+    }
+    if (F < target)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return 0.5f * (lo + hi);
+}
+
 template <int NP, bool BATCH, bool MERGE, bool STALLY>
 __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ TransportParams p) {
   extern __shared__ float smem[];
@@ -248,6 +273,9 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
             } else if (P.kind == MCR_ISO_POINT) {
               const uint4 r0 = philox4x32_10(pid, 0u, KEY0(), KEY1());
               sincospif(2.f * u01(r0.z), &sx, &sz);
+            } else if (P.kind == MCR_ANGULAR_POINT) {
+              const uint4 r0 = philox4x32_10(pid, 0u, KEY0(), KEY1());
+              sincosf(launch_angle(P, u01(r0.z)), &sx, &sz);
             }
             inside = x >= 0.f && x <= NX() * DX() && z >= 0.f && z <= NZ() * DX();
             if (inside) {

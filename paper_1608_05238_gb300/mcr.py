@@ -19,7 +19,7 @@ import torch
 
 from . import _build
 
-PENCIL, LINE, ISO_POINT = 0, 1, 2
+PENCIL, LINE, ISO_POINT, ANGULAR_POINT = 0, 1, 2, 3
 MAX_K = 64
 
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_EVENT_LIMIT, ERR_TALLY_OVERFLOW, ERR_MEDIUM = 0, -1, -2, -3, -4, -5, -6
@@ -43,9 +43,13 @@ class _Medium(C.Structure):
                 ("mua", C.c_void_p), ("mus", C.c_void_p)]
 
 
+MAX_ANG = 8
+
+
 class _Source(C.Structure):
     _fields_ = [("kind", C.c_int32), ("x0", C.c_float), ("z0", C.c_float), ("x1", C.c_float), ("z1", C.c_float),
-                ("dir_x", C.c_float), ("dir_z", C.c_float), ("power", C.c_float)]
+                ("dir_x", C.c_float), ("dir_z", C.c_float), ("power", C.c_float), ("n_ang", C.c_int32),
+                ("ang_c", C.c_float * MAX_ANG), ("ang_s", C.c_float * MAX_ANG)]
 
 
 class _Run(C.Structure):
@@ -168,7 +172,9 @@ class Medium:
 
 @dataclass
 class Source:
-    """Forward source: PENCIL / LINE / ISO_POINT (positions in mm, direction normalised by the library)."""
+    """Forward source: PENCIL / LINE / ISO_POINT / ANGULAR_POINT (positions in mm, direction normalised
+    by the library).  ANGULAR_POINT launches angles theta (from +z) with density
+    (1 + sum_n ang_c[n-1] cos n theta + ang_s[n-1] sin n theta) / (2 pi), n <= 8."""
     kind: int
     x0: float = 0.0
     z0: float = 0.0
@@ -177,13 +183,21 @@ class Source:
     dir_x: float = 0.0
     dir_z: float = 1.0
     power: float = 1.0
+    ang_c: tuple = ()
+    ang_s: tuple = ()
 
     def c(self) -> _Source:
-        return _Source(int(self.kind), self.x0, self.z0, self.x1, self.z1, self.dir_x, self.dir_z, self.power)
+        ac, as_ = list(self.ang_c), list(self.ang_s)
+        n = max(len(ac), len(as_))
+        if n > MAX_ANG:
+            raise ValueError(f"at most {MAX_ANG} angular harmonics")
+        ac, as_ = ac + [0.0] * (MAX_ANG - len(ac)), as_ + [0.0] * (MAX_ANG - len(as_))
+        return _Source(int(self.kind), self.x0, self.z0, self.x1, self.z1, self.dir_x, self.dir_z, self.power, n,
+                       (C.c_float * MAX_ANG)(*ac), (C.c_float * MAX_ANG)(*as_))
 
     def as_dict(self) -> dict:
         return dict(kind=self.kind, x0=self.x0, z0=self.z0, x1=self.x1, z1=self.z1, dir_x=self.dir_x,
-                    dir_z=self.dir_z, power=self.power)
+                    dir_z=self.dir_z, power=self.power, ang_c=list(self.ang_c), ang_s=list(self.ang_s))
 
 
 @dataclass

@@ -22,7 +22,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-PENCIL, LINE, ISO_POINT = 0, 1, 2
+PENCIL, LINE, ISO_POINT, ANGULAR_POINT = 0, 1, 2, 3
 
 
 @dataclass

@@ -82,6 +82,60 @@ def test_forward_iso_point_K64_oblique_grid():
     _forward_case(mua, mus, 0.07, 0.75, src, run, "iso K64")
 
 
+@pytest.mark.parametrize("ac,as_", [([0.0, 0.0, 0.0, -1.0], []), ([0.3, -0.2], [0.25, 0.0, 0.125])])
+def test_forward_angular_point_source_K16(ac, as_):
+    """A point source with an angular density (the form of a Sec. 4.1 detector) against the oracle:
+    the launch angle is the FP32 bisection root of the density's integral on the GPU and the FP64
+    one in the oracle, so the streams agree to the FP32 resolution of the angle."""
+    mua, mus = workloads.small_hetero(36, 44, 0.08, seed=6)
+    src = dict(kind=mcr.ANGULAR_POINT, x0=1.77, z0=1.31, ang_c=ac, ang_s=as_, power=1.5)
+    run = mcr.Run(K=16, n_packets=50_003, seed=13, stream_id=5)
+    _forward_case(mua, mus, 0.08, 0.8, src, run, "angular point K16")
+
+
+def test_angular_point_launch_moments_and_rejected_density():
+    """Launch directions on the GPU follow the density: with every packet absorbed in the source
+    pixel, that pixel's a_n / a_0, b_n / a_0 are the means of cos n theta, sin n theta, whose
+    expectations are c_n / 2, s_n / 2.  A density with negative values is refused."""
+    n, dx, K, N = 5, 1.0, 6, 1_000_000
+    mua, mus = np.full((n, n), 1000.0, np.float32), np.zeros((n, n), np.float32)
+    ac, as_ = [0.3, 0.0, 0.2], [0.0, -0.4]
+    c = _gpu_forward(mua, mus, dx, 0.0, dict(kind=mcr.ANGULAR_POINT, x0=2.5, z0=2.5, ang_c=ac, ang_s=as_),
+                     mcr.Run(K=K, n_packets=N, seed=3))
+    a0 = c[0][2, 2]
+    sig = 0.75 / math.sqrt(N)
+    for m in range(1, K + 1):
+        cm = ac[m - 1] if m <= len(ac) else 0.0
+        sm = as_[m - 1] if m <= len(as_) else 0.0
+        assert abs(c[2 * m - 1][2, 2] / a0 - cm / 2) < 5 * sig, m
+        assert abs(c[2 * m][2, 2] / a0 - sm / 2) < 5 * sig, m
+    with pytest.raises(mcr.McrError):
+        _gpu_forward(mua, mus, dx, 0.0, dict(kind=mcr.ANGULAR_POINT, x0=2.5, z0=2.5, ang_c=[2.0]),
+                     mcr.Run(K=1, n_packets=10, seed=3))
+
+
+def test_reciprocity_case2_odd_detector_gpu():
+    """Case 2 (Eqs. 15, 18) on the GPU at 16 x the oracle pin's packets: the detected signal of an
+    odd angular detector at r_d from an isotropic source at r_s equals the fluence at r_s of a run
+    from r_d with the detector's density turned by pi (the adjoint's theta + pi reading)."""
+    nz = nx = 48
+    dx, g, K = 0.125, 0.5, 2
+    mua, mus = workloads.small_hetero(nz, nx, dx, seed=9)
+    ps, pd = (24, 24), (24, 36)
+    centre = lambda p: dict(x0=(p[1] + 0.5) * dx, z0=(p[0] + 0.5) * dx)
+    det, rec = [], []
+    for k in range(4):
+        f = _gpu_forward(mua, mus, dx, g, dict(kind=mcr.ISO_POINT, **centre(ps)), mcr.Run(K=K, n_packets=1_000_000,
+                                                                                         seed=40 + k))
+        det.append(f[0][pd] + f[2][pd])  # (1 + sin theta) / (2 pi): a_0 + b_1
+        a = _gpu_forward(mua, mus, dx, g, dict(kind=mcr.ANGULAR_POINT, **centre(pd), ang_s=[-1.0]),
+                         mcr.Run(K=0, n_packets=1_000_000, seed=60 + k))
+        rec.append(a[0][ps])
+    det, rec = np.array(det), np.array(rec)
+    se = math.sqrt(det.var(ddof=1) / 4 + rec.var(ddof=1) / 4)
+    assert abs(det.mean() - rec.mean()) < 4 * se + 0.01 * det.mean(), (det.mean(), rec.mean(), se)
+
+
 def test_forward_oblique_pencil_K16_roulette():
     """Oblique pencil, strong absorption and a high threshold so that roulette is exercised.
 
