@@ -58,7 +58,7 @@ class _Run(C.Structure):
     _fields_ = [("K", C.c_int32), ("n_threads", C.c_int32), ("n_packets", C.c_uint64),
                 ("first_packet", C.c_uint64), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
                 ("max_scatter", C.c_uint32), ("max_events", C.c_uint32), ("w_threshold", C.c_double),
-                ("roulette_p", C.c_float)]
+                ("roulette_p", C.c_float), ("sectors", C.c_uint32)]
 
 
 class _Stats(C.Structure):
@@ -104,6 +104,7 @@ class RunParams:
     w_threshold: float = 1e-4
     roulette_p: float = 0.1
     n_threads: int = 0
+    sectors: int = 0   # > 0: discrete-ordinates tally in that many equal sectors instead of harmonics
 
 
 @dataclass
@@ -127,14 +128,16 @@ def _run(p: RunParams):
     nt = p.n_threads or (os.cpu_count() or 1)
     nt = max(1, min(nt, max(1, p.n_packets)))
     return _Run(p.K, nt, p.n_packets, p.first_packet, p.seed, p.stream_id, p.max_scatter, p.max_events,
-                p.w_threshold, p.roulette_p)
+                p.w_threshold, p.roulette_p, p.sectors)
 
 
 def _stats_dict(st: _Stats) -> dict:
     return {n: getattr(st, n) for n, _ in _Stats._fields_}
 
 
-def _finish(raw, sq, n_packets, S, dx, st) -> Result:
+def _finish(raw, sq, n_packets, S, dx, st, sectors=0) -> Result:
+    """Normalised coefficients: harmonics a_0, a_n, b_n, or with ``sectors`` > 0 the angular
+    integrals of the radiance over each sector (they sum to a_0)."""
     A = dx * dx
     norm = S / (n_packets * A) if n_packets > 0 else 0.0
     coeff = raw * norm
@@ -142,7 +145,7 @@ def _finish(raw, sq, n_packets, S, dx, st) -> Result:
     if sq is not None and n_packets > 1:
         # a0 = (S/A) mean_p X_p with X_p the per-packet track-weight sum in the pixel;
         # its variance is (S/A)^2 Var(X) / N_p with the unbiased Var(X).
-        mean = raw[0] / n_packets
+        mean = (raw.sum(axis=0) if sectors else raw[0]) / n_packets
         var = np.maximum(sq / n_packets - mean * mean, 0.0) / (n_packets - 1) * (S / A) ** 2
     return Result(coeff, var, _stats_dict(st), S)
 
@@ -168,7 +171,7 @@ def forward(mua, mus, dx, g, source: dict, run: RunParams, with_variance: bool =
                 float(source.get("dir_z", 1.0)), float(source.get("power", 1.0)), n_ang,
                 (C.c_double * MAX_ANG)(*map(float, ac)), (C.c_double * MAX_ANG)(*map(float, as_)))
     nz, nx = keep[0].shape
-    Cc = 2 * run.K + 1
+    Cc = run.sectors or 2 * run.K + 1
     raw = np.zeros((Cc, nz, nx), dtype=np.float64)
     sq = np.zeros((nz, nx), dtype=np.float64) if with_variance else None
     st = _Stats()
@@ -177,7 +180,7 @@ def forward(mua, mus, dx, g, source: dict, run: RunParams, with_variance: bool =
                              sq.ctypes.data_as(C.POINTER(C.c_double)) if sq is not None else None, C.byref(st))
     if rc != 0:
         raise ValueError(f"oracle forward: status {rc}")
-    return _finish(raw, sq, run.n_packets, s.power, dx, st)
+    return _finish(raw, sq, run.n_packets, s.power, dx, st, run.sectors)
 
 
 def volume(mua, mus, dx, g, q, run: RunParams, adjoint: bool = True, with_variance: bool = False) -> Result:
@@ -192,7 +195,7 @@ def volume(mua, mus, dx, g, q, run: RunParams, adjoint: bool = True, with_varian
     q = np.ascontiguousarray(q, dtype=np.float32)
     nz, nx = keep[0].shape
     assert q.shape == (nz, nx)
-    Cc = 2 * run.K + 1
+    Cc = run.sectors or 2 * run.K + 1
     raw = np.zeros((Cc, nz, nx), dtype=np.float64)
     sq = np.zeros((nz, nx), dtype=np.float64) if with_variance else None
     st = _Stats()
@@ -203,7 +206,7 @@ def volume(mua, mus, dx, g, q, run: RunParams, adjoint: bool = True, with_varian
                             C.byref(st), C.byref(S))
     if rc != 0:
         raise ValueError(f"oracle volume: status {rc}")
-    return _finish(raw, sq, run.n_packets, S.value, dx, st)
+    return _finish(raw, sq, run.n_packets, S.value, dx, st, run.sectors)
 
 
 def adjoint(mua, mus, dx, g, qstar, run: RunParams, with_variance: bool = False) -> Result:

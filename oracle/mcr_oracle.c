@@ -106,6 +106,10 @@ typedef struct {
   uint32_t max_events;  /* flights per packet before it is ended */
   double w_threshold;   /* roulette when |W| < w_threshold |W0| */
   float roulette_p;     /* survival probability (FP32 so both paths compare alike) */
+  /* discrete ordinates (Sec. 3.1's alternative to the harmonics): > 0 tallies t into
+   * `sectors` equal angular sectors [m dth, (m+1) dth), dth = 2 pi / sectors, of theta in
+   * [0, 2 pi) instead of the 2K+1 harmonics; 0: harmonics */
+  uint32_t sectors;
 } orc_run;
 
 typedef struct {
@@ -241,6 +245,19 @@ static void orc_deposit(orc_job *j, int64_t pix, double t, double theta_tally) {
   const int K = j->run->K;
   const int64_t npix = (int64_t)j->med->nx * j->med->nz;
   double *T = j->tally;
+  if (j->run->sectors) { /* discrete ordinates: the sector holding theta */
+    const uint32_t M = j->run->sectors;
+    double th = fmod(theta_tally, 2.0 * M_PI);
+    if (th < 0.0) th += 2.0 * M_PI;
+    uint32_t sct = (uint32_t)(th * (M / (2.0 * M_PI)));
+    if (sct >= M) sct = M - 1;
+    T[(int64_t)sct * npix + pix] += t;
+    if (j->sq) {
+      if (j->pk[pix] == 0.0) j->touched[j->n_touched++] = pix;
+      j->pk[pix] += t;
+    }
+    return;
+  }
   T[pix] += t; /* a_0: Eq. 9 */
   for (int n = 1; n <= K; ++n) {
     T[(int64_t)(2 * n - 1) * npix + pix] += t * cos(n * theta_tally); /* a_n: Eq. 10 */
@@ -430,7 +447,7 @@ static int orc_check(const orc_medium *m, const orc_run *r) {
   if (!m || !r || !m->mua || !m->mus) return ORC_ERR_ARG;
   if (m->nx <= 0 || m->nz <= 0 || !(m->dx > 0.0)) return ORC_ERR_ARG;
   if (!(m->g > -1.0 && m->g < 1.0)) return ORC_ERR_ARG;
-  if (r->K < 0 || r->K > 256 || r->n_threads <= 0) return ORC_ERR_ARG;
+  if (r->K < 0 || r->K > 256 || r->n_threads <= 0 || r->sectors > 4096) return ORC_ERR_ARG;
   if (!(r->roulette_p > 0.0f && r->roulette_p <= 1.0f)) return ORC_ERR_ARG;
   const int64_t npix = (int64_t)m->nx * m->nz;
   for (int64_t i = 0; i < npix; ++i)
@@ -441,7 +458,7 @@ static int orc_check(const orc_medium *m, const orc_run *r) {
 /*
  * Runs packets [first_packet, first_packet + n_packets) and ADDS raw sums to
  * tally ([2K+1][nz][nx], sums of t cos(n theta), t sin(n theta), no
- * normalisation) and to sq ([nz][nx], sums over packets of the squared
+ * normalisation; with sectors > 0, [sectors][nz][nx] sums of t per sector) and to sq ([nz][nx], sums over packets of the squared
  * per-packet a_0 sum; may be NULL).  Normalisation is done by the caller
  * (S / (N_p dx^2)).  Threads take equal contiguous packet ranges; their tallies
  * are summed in thread order.
@@ -449,7 +466,7 @@ static int orc_check(const orc_medium *m, const orc_run *r) {
 static int orc_run_packets(const orc_medium *m, const orc_source *s, const orc_volsrc *vol,
                            const orc_run *r, int adjoint, double *tally, double *sq, orc_stats *st) {
   const int64_t npix = (int64_t)m->nx * m->nz;
-  const int64_t C = 2 * (int64_t)r->K + 1;
+  const int64_t C = r->sectors ? (int64_t)r->sectors : 2 * (int64_t)r->K + 1;
   const int nt = r->n_threads;
   orc_job *jobs = (orc_job *)calloc((size_t)nt, sizeof(orc_job));
   pthread_t *th = (pthread_t *)calloc((size_t)nt, sizeof(pthread_t));

@@ -442,3 +442,61 @@ def test_reciprocity_case2_angular_detectors():
         assert abs(det.mean() - rec.mean()) < 4 * se + 0.01 * det.mean(), (ac, as_, det.mean(), rec.mean(), se)
         if as_:  # the odd detector: the missing flip is detected
             assert abs(det.mean() - unflipped.mean()) > 6 * se + 0.05 * det.mean(), (det.mean(), unflipped.mean(), se)
+
+
+# ------------------------------------------------------------ discrete ordinates (Sec. 3.1)
+def _sector_case():
+    nz = nx = 20
+    dx, g = 0.2, 0.7
+    mua, mus = _hetero(nz, nx, 23)
+    src = dict(kind=oracle.ISO_POINT, x0=2.1, z0=1.9)
+    return mua * 0.3, mus, dx, g, src
+
+
+def test_sectors_partition_the_fluence_deposits():
+    """The discrete-ordinates tally (the alternative Sec. 3.1 sets aside) splits every deposit of
+    Eq. 9 into exactly one sector: on the same packets the sectors sum to a_0 (FP64 rounding)."""
+    mua, mus, dx, g, src = _sector_case()
+    h = oracle.forward(mua, mus, dx, g, src, RunParams(K=0, n_packets=20000, seed=5))
+    for M in (1, 6, 32):
+        s = oracle.forward(mua, mus, dx, g, src, RunParams(K=0, n_packets=20000, seed=5, sectors=M))
+        assert s.coeff.shape[0] == M
+        assert np.allclose(s.coeff.sum(axis=0), h.coeff[0], rtol=1e-12, atol=1e-15)
+
+
+def test_sectors_equal_the_harmonic_series_integrated_over_each_sector():
+    """On the same packets the sector integrals of the radiance equal the integrals over each
+    sector of its Fourier series (Eq. 8) with coefficients of Eqs. 9-11 up to K = 64; what is
+    left is the series' truncation near the sector edges, small where the field is diffuse."""
+    mua, mus, dx, g, src = _sector_case()
+    K, M, N = 64, 8, 40000
+    h = oracle.forward(mua, mus, dx, g, src, RunParams(K=K, n_packets=N, seed=8))
+    s = oracle.forward(mua, mus, dx, g, src, RunParams(K=0, n_packets=N, seed=8, sectors=M))
+    dth = 2 * math.pi / M
+    region = (slice(12, 20), slice(12, 20))  # away from the source: a diffuse field
+    for m in range(M):
+        t1, t2 = m * dth, (m + 1) * dth
+        series = h.coeff[0] * dth / (2 * math.pi)
+        for n in range(1, K + 1):
+            series = series + (h.coeff[2 * n - 1] * (math.sin(n * t2) - math.sin(n * t1))
+                               - h.coeff[2 * n] * (math.cos(n * t2) - math.cos(n * t1))) / (n * math.pi)
+        a, b = s.coeff[m][region].sum(), series[region].sum()
+        assert abs(a - b) < 0.01 * abs(a), (m, a, b)
+
+
+def test_sector_estimates_converge_slower_than_the_fluence():
+    """Sec. 3.1: the per-sector radiance estimate has a larger relative spread than the fluence
+    estimate from the same packets, and the gap grows with the number of sectors."""
+    mua, mus, dx, g, src = _sector_case()
+    pix = (14, 15)
+
+    def rel_sd(M):
+        vals = []
+        for k in range(8):
+            r = oracle.forward(mua, mus, dx, g, src, RunParams(K=0, n_packets=4000, seed=300 + k, sectors=M))
+            vals.append(r.coeff[0][pix] if M == 0 else r.coeff[:, pix[0], pix[1]])
+        v = np.array(vals)
+        return float(np.mean(v.std(axis=0, ddof=1) / np.abs(v.mean(axis=0))))
+
+    r0, r4, r16 = rel_sd(0), rel_sd(4), rel_sd(16)
+    assert r0 < r4 < r16, (r0, r4, r16)
