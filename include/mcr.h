@@ -90,6 +90,10 @@ typedef struct {
   float roulette_p;      /* roulette survival probability p, 0 < p <= 1; survivors W <- W/p */
   uint32_t accumulate;   /* 0: write coeff; 1: add this run's coefficients to coeff (the fluences of
                             several sources of one illumination sum, Eq. 5 is linear in q) */
+  uint32_t sectors;      /* 0: the harmonic tally.  M in 1..1024 (mc_forward only): the discrete-
+                            ordinates tally of Sec. 3.1 instead -- coeff [M][nz][nx] holds the radiance
+                            integrated over the angular sectors [m 2pi/M, (m+1) 2pi/M) of theta
+                            (from +z), summing to a_0; K is ignored */
 } mcr_run;
 
 /* Run counters (host struct filled when a non-NULL pointer is passed; synchronises). */

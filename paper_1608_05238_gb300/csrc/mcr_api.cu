@@ -90,6 +90,7 @@ int check_run(const mcr_run *r) {
   if (!(r->w_threshold >= 0.f) || !finite_f(r->w_threshold)) return MCR_ERR_ARG;
   if (r->first_packet + r->n_packets < r->first_packet) return MCR_ERR_ARG;  // id overflow
   if (r->accumulate > 1u) return MCR_ERR_ARG;
+  if (r->sectors > 1024u) return MCR_ERR_ARG;
   return MCR_OK;
 }
 
@@ -157,7 +158,7 @@ struct HostProblem {
 int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const TransportLaunch &cfg, int slot,
             mcr_stats *stats, cudaStream_t s) {
   const int np = (int)probs.size();
-  const int C = 2 * common->K + 1, Cpad = tally_row_words(C);
+  const int C = common->sectors ? (int)common->sectors : 2 * common->K + 1, Cpad = tally_row_words(C);
   // a single problem may exceed one launch's packet budget (chunks + FP64 flush); a batch may not
   const bool chunked = np == 1 && probs[0].n_packets > kChunkPackets;
   Need need;
@@ -191,7 +192,9 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
   p.K = common->K;
   p.C = C;
   p.Cpad = Cpad;
-  p.row_stride = transport_row_stride(C);
+  p.row_stride = common->sectors ? 1 : transport_row_stride(C);  // no harmonic rows for sectors
+  p.sectors = (int)common->sectors;
+  p.sector_scale = (float)(common->sectors / (2.0 * 3.14159265358979323846));
   p.max_scatter = common->max_scatter;
   p.max_events = common->max_events;
   p.w_threshold = common->w_threshold;
@@ -294,6 +297,7 @@ int run_mc(const mcr_medium *med, const mcr_source *src, const float *qstar, con
   int rc;
   if ((rc = check_medium(med)) || (rc = check_run(run))) return rc;
   if (!coeff) return MCR_ERR_ARG;
+  if (qstar && run->sectors) return MCR_ERR_ARG;  // the sector tally is a forward-only study
   HostProblem h{med, src, qstar, run->n_packets, run->first_packet, run->seed, run->stream_id, coeff, 0.f, 1.f};
   if (!qstar && (rc = check_source(src, &h.dirx, &h.dirz))) return rc;
   std::lock_guard<std::mutex> lock(g_mu);
@@ -321,6 +325,7 @@ int mc_run_batch(const mcr_problem *problems, int32_t n_problems, const mcr_run 
   int rc;
   if (!problems || n_problems < 1 || n_problems > MCR_MAX_BATCH) return MCR_ERR_ARG;
   if ((rc = check_run(common))) return rc;
+  if (common->sectors) return MCR_ERR_ARG;  // the sector tally runs through mc_forward only
   TransportLaunch cfg{0, 0, 0, 0};
   if (launch) {
     if (launch->threads_per_block < 0 || launch->threads_per_block > 256 || launch->threads_per_block % 32 ||

@@ -58,6 +58,8 @@ struct ProblemDesc {
 struct TransportParams {
   int n_problems;
   int K, C, Cpad, row_stride;  // C = 2K+1 channels, Cpad = tally_row_words(C), smem row stride
+  int sectors;                 // > 0: discrete-ordinates tally, C = sectors (single forward problem)
+  float sector_scale;          // sectors / (2 pi)
   unsigned max_scatter, max_events;
   float w_threshold, rr_p, rr_inv_p;
   unsigned long long total_packets;  // = prob[n_problems-1].end

@@ -63,6 +63,7 @@ int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_r
   if (run->K < 0 || run->K > MCR_MAX_K || !(run->roulette_p > 0.f && run->roulette_p <= 1.f)) return MCR_ERR_ARG;
   if (!(run->w_threshold >= 0.f) || !isfinite(run->w_threshold)) return MCR_ERR_ARG;
   if (run->first_packet + run->n_packets < run->first_packet) return MCR_ERR_ARG;
+  if (run->sectors) return MCR_ERR_ARG;  // the sector tally runs through mc_forward only
   if (src->kind < MCR_PENCIL || src->kind > MCR_ANGULAR_POINT) return MCR_ERR_ARG;
   if (src->kind == MCR_ANGULAR_POINT && !angular_density_ok(*src)) return MCR_ERR_ARG;
   if (!isfinite(src->x0) || !isfinite(src->z0) || !isfinite(src->x1) || !isfinite(src->z1) || !isfinite(src->power))

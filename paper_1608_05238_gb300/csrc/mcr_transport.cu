@@ -116,8 +116,13 @@ __device__ __forceinline__ float launch_angle(const ProblemDesc &P, float u) {
   return 0.5f * (lo + hi);
 }
 
+// NP = 0: the discrete-ordinates variant (Sec. 3.1's alternative to the harmonics): each segment
+// adds its track weight to one of p.sectors equal angular sectors of its pixel, one per-lane
+// reduction instead of 2K+1 cooperative ones (single forward problem, no merge).
 template <int NP, bool BATCH, bool MERGE, bool STALLY>
 __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ TransportParams p) {
+  constexpr bool SECT = NP == 0;
+  static_assert(!SECT || (!BATCH && !MERGE && !STALLY), "the sector tally runs one plain forward problem");
   extern __shared__ float smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -165,6 +170,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
   float fx = 0.f, fz = 0.f, sx = 0.f, sz = 1.f, inv_ax = 0.f, inv_az = 0.f, W = 0.f, tau = 0.f;
   int ix = 0, iz = 0;
   unsigned flight = 0, nscat = 0, cu1 = 0, cu2 = 0;
+  int sect = 0;           // SECT: the current flight's angular sector
   int rb = 0;             // row of the current flight's harmonics
   int carry_rb = 0;       // row of the deferred segment's harmonics
   float carry = 0.f;      // deferred track weight (times 2^q) of a collision segment, 0: none
@@ -199,7 +205,13 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     inv_az = __frcp_rn(fabsf(sz));
     ++n_flight;
     if (MERGE) rb ^= 1;  // keep the previous flight's row for a deferred segment
-    write_row();
+    if constexpr (SECT) {
+      float th = atan2f(sx, sz);  // (-pi, pi], from +z
+      if (th < 0.f) th += 6.28318530717958648f;
+      sect = min((int)(th * p.sector_scale), p.sectors - 1);
+    } else {
+      write_row();
+    }
   };
 
   for (;;) {
@@ -374,7 +386,10 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     }
 
     // ---------------------------------------------------------------- cooperative deposit
-    unsigned pend = __ballot_sync(kFull, seg_key != 0u);
+    if constexpr (SECT) {
+      if (seg_key != 0u) atomicAdd(tally_row(seg_key) + sect, (unsigned long long)(long long)__float2int_rn(seg_ts));
+    }
+    unsigned pend = SECT ? 0u : __ballot_sync(kFull, seg_key != 0u);
     if (pend) {
       const unsigned same = __match_any_sync(kFull, seg_key);
       // Rows of a single lane without a carried segment (nearly all of them away from the source)
@@ -412,7 +427,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
         const unsigned grp = __shfl_sync(kFull, same, L) & pend;
         const unsigned key = __shfl_sync(kFull, seg_key, L);
         unsigned long long *dst = tally_row(key);
-        long long acc[NP];
+        long long acc[NP > 0 ? NP : 1];
         // |t h 2^q| < 2^31 by the choice of q, so a 32-bit conversion suffices
         const float tsL = __shfl_sync(kFull, seg_ts, L);
         const float *hrL = rows + ((MERGE ? __shfl_sync(kFull, rb, L) * 32 : 0) + L) * p.row_stride + 1;
@@ -462,7 +477,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
         }
         pend &= ~grp;
       }
-      if (Cw < C && seg_key != 0u) {  // the per-lane remainder
+      if (!SECT && Cw < C && seg_key != 0u) {  // the per-lane remainder
         unsigned long long *own = tally_row(seg_key);
         const float *h = rows + ((MERGE ? rb * 32 : 0) + lane) * p.row_stride + 1;
         const float *hc = rows + ((MERGE ? carry_rb * 32 : 0) + lane) * p.row_stride + 1;
@@ -662,6 +677,11 @@ size_t transport_smem_bytes(int row_stride, int threads, bool merge) {
 
 
 cudaError_t launch_transport(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s) {
+  if (p.sectors > 0) {  // discrete ordinates: one plain forward problem
+    if (p.n_problems != 1) return cudaErrorInvalidValue;
+    return launch_kernel<0, false, false>(p, cfg.threads_per_block > 0 ? cfg.threads_per_block : 128,
+                                          cfg.blocks_per_sm, s);
+  }
   // chunks of 32 coefficients deposited cooperatively (a remainder of <= 4 goes per lane)
   const int cw = (p.C & 31) <= 4 ? (p.C & ~31) : p.C;
   const int np = cw > 32 ? (cw + 31) / 32 : 1;

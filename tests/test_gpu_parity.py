@@ -136,6 +136,37 @@ def test_reciprocity_case2_odd_detector_gpu():
     assert abs(det.mean() - rec.mean()) < 4 * se + 0.01 * det.mean(), (det.mean(), rec.mean(), se)
 
 
+@pytest.mark.parametrize("M", [8, 37])
+def test_forward_sector_tally_parity(M):
+    """The discrete-ordinates tally (Sec. 3.1's alternative basis) against the oracle on the same
+    streams: one sector per flight from the direction angle (FP32 atan2 on the GPU, FP64 in the
+    oracle), one reduction per segment."""
+    mua, mus = workloads.small_hetero(40, 52, 0.08, seed=12)
+    src = dict(kind=mcr.LINE, x0=0.4, z0=0.0, x1=3.6, z1=0.0, dir_x=0.3, dir_z=1.0)
+    run = mcr.Run(K=0, n_packets=40_001, seed=17, sectors=M)
+    dx, g = f32(0.08), f32(0.85)
+    src = _src32(src)
+    G = _gpu_forward(mua, mus, dx, g, src, run)
+    O = oracle.forward(mua.astype(np.float64), mus.astype(np.float64), dx, g, src,
+                       RunParams(K=0, n_packets=run.n_packets, seed=run.seed, sectors=M))
+    assert G.shape == O.coeff.shape == (M, 40, 52)
+    # per sector, relative L1 over the field (a packet whose angle sits within FP32 rounding of
+    # a sector edge may land in the neighbour on one side)
+    for m in range(M):
+        assert np.abs(G[m] - O.coeff[m]).sum() <= 2e-3 * np.abs(O.coeff[m]).sum() + 1e-12, m
+    # the sectors partition the fluence deposits: their sum is the K = 0 run's a_0
+    a0 = _gpu_forward(mua, mus, dx, g, src, mcr.Run(K=0, n_packets=40_001, seed=17))[0]
+    assert np.allclose(G.sum(axis=0), a0, rtol=2e-6, atol=1e-9 * a0.max())
+
+
+def test_sector_tally_is_forward_only():
+    mua, mus = workloads.small_hetero(8, 8, 0.1, seed=1)
+    med = mcr.Medium(_dev(mua), _dev(mus), 0.1, 0.5)
+    q = torch.ones(8, 8, device="cuda")
+    with pytest.raises(mcr.McrError):
+        mcr.adjoint(med, q, mcr.Run(K=0, n_packets=100, sectors=4))
+
+
 def test_forward_oblique_pencil_K16_roulette():
     """Oblique pencil, strong absorption and a high threshold so that roulette is exercised.
 
