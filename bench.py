@@ -56,13 +56,15 @@ def _args():
     ap.add_argument("--unknown", default="mua", choices=["mua", "mus"], help="invert_rect: the reconstructed map")
     ap.add_argument("--iters", type=int, default=None, help="invert_rect: iteration cap (default 20 mua, 40 mus)")
     ap.add_argument("--workload", default="grad256",
-                    choices=["grad256", "large1024", "batch64", "denoise256", "conv", "invert256", "unet256", "invert_rect"],
+                    choices=["grad256", "large1024", "batch64", "denoise256", "conv", "invert256", "unet256", "invert_rect",
+                             "sectors"],
                     help="grad256: the gradient evaluation (default); large1024: the same on 1024^2 px at "
                          "K = 64 with four edge sources; batch64: 64 forward problems in one graph-captured "
                          "batched launch; denoise256: the learned denoiser; conv: one large tensor-core "
                          "convolution (profiling case); invert256: mu_a reconstruction on the grad256 phantom; "
                          "unet256: U-Net training step and inference on synthetic maps (profiling case); invert_rect: "
-                         "the Sec. 6 reconstructions on the rectangular-inclusion domain (--unknown mua|mus)")
+                         "the Sec. 6 reconstructions on the rectangular-inclusion domain (--unknown mua|mus); sectors: "
+                         "harmonic vs discrete-ordinates tally (Sec. 3.1)")
     args = ap.parse_args()
     if args.packets is None:
         args.packets = 20_000_000 if args.workload == "large1024" else 10_000_000
@@ -732,6 +734,50 @@ def _invert256(args):
     return 0
 
 
+def _sectors(args):
+    """Sec. 3.1's trade-off, measured: the forward transport of the 256^2 workload with the harmonic
+    tally at K = 8, 16, 32 against the discrete-ordinates tally at M = 16, 32, 64 sectors -- tally
+    words per pixel, transport rate, and the relative spread over seeds of one angular channel
+    against that of the fluence at the same packet count."""
+    import torch
+    from paper_1608_05238_gb300 import _build, mcr, workloads
+    _build.build()
+    w = workloads.grad256(args.packets)
+    dx, g = float(np.float32(w.dx)), float(np.float32(w.g))
+    med = mcr.Medium(torch.from_numpy(w.mua).cuda(), torch.from_numpy(w.mus).cuda(), dx, g)
+    src = mcr.Source(**w.sources[0])
+    rows = []
+    pix = (64, 128)  # 3.2 mm under the middle of the source line
+    for label, K, M in [("harmonics", 8, 0), ("harmonics", 16, 0), ("harmonics", 32, 0), ("sectors", 0, 16),
+                        ("sectors", 0, 32), ("sectors", 0, 64)]:
+        mcr.forward(med, src, mcr.Run(K=K, n_packets=args.packets // 10, seed=1, sectors=M))  # warm-up
+        torch.cuda.synchronize()
+        t = []
+        for k in range(args.steps):
+            c, st = mcr.forward(med, src, mcr.Run(K=K, n_packets=args.packets, seed=2 + k, sectors=M), stats=True)
+            t.append(mcr.last_run_info("forward")[1])
+        seg_rate = st["segments"] / (float(np.mean(t)) * 1e-3)
+        # spread over 8 seeds of a^(1e6 packets): channel 0 (fluence) for harmonics, sector 0 for M
+        vals = np.array([mcr.forward(med, src, mcr.Run(K=K, n_packets=1_000_000, seed=100 + k, sectors=M))
+                         [:, pix[0], pix[1]].double().cpu().numpy() for k in range(8)])
+        rel = vals.std(axis=0, ddof=1) / np.abs(vals.mean(axis=0))
+        C = M if M else 2 * K + 1
+        words = (C + 15) // 16 * 16 if C > 32 else (C + 3) // 4 * 4
+        rows.append({"tally": label, "K": K, "sectors": M, "channels": C, "tally_words_per_pixel": words,
+                     "transport_ms": float(np.mean(t)), "segments_per_s": seg_rate,
+                     "photons_per_s": args.packets / (float(np.mean(t)) * 1e-3),
+                     "rel_spread_fluence_or_first_sector": float(rel[0])})
+    out = {"metric": "forward transport photons/s, harmonic vs discrete-ordinates tally", "value":
+           rows[-1]["photons_per_s"], "unit": "photons/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+           "ms_per_step": rows[-1]["transport_ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic",
+           "config": {"workload": f"sectors: grad256 medium and line source, forward, {args.packets:.0e} packets; "
+                                  f"spread over 8 seeds of 1e6 packets at pixel {pix}", "rows": rows},
+           "cpu_baseline": None}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def _invert_rect(args):
     """The reconstructions of Sec. 6 on its rectangular-inclusion domain (workloads.rect_phantom):
     --unknown mua: mu_a only (mu_s known), gradient descent with the Hager-Zhang line search and
@@ -818,6 +864,8 @@ def main():
         return _unet256(args)
     if args.workload == "invert_rect" and args.impl != "reference":
         return _invert_rect(args)
+    if args.workload == "sectors" and args.impl != "reference":
+        return _sectors(args)
     if args.impl == "reference":
         return _reference(args)
     return _gpu(args)
