@@ -40,6 +40,9 @@ typedef struct {
   void *out;                /* NHWC output slice */
   int32_t out_f32;          /* 1: fp32 output, 0: bf16 output */
   int32_t out_stride, out_off;
+  int32_t cin;              /* input channels in use (<= cin_pad; 0: all cin_pad): the weights of
+                               channels [cin, cin_pad) must be zero.  With cin <= 32 a 3x3 layer of
+                               <= 32 outputs reads only the first 32 channels (half the work) */
 } dn_conv_desc;
 
 /*

@@ -94,6 +94,7 @@ static int conv_setup(const dn_conv_desc *d, CUtensorMap &tmX, CUtensorMap &tmW,
   if (d->taps != 9 && d->taps != 1) return MCR_ERR_ARG;
   if (d->n_pad < 16 || d->n_pad > 256 || d->n_pad % 16 || d->cout < 1 || d->cout > d->n_pad) return MCR_ERR_ARG;
   if (d->mask && (d->mask_off + d->cout > d->mask_stride)) return MCR_ERR_ARG;
+  if (d->cin < 0 || d->cin > d->cin_pad) return MCR_ERR_ARG;
   unsigned *err = error_word();
   if (!err) return MCR_ERR_CUDA;
 
@@ -154,15 +155,27 @@ int dn_conv(const dn_conv_desc *d, void *stream) {
   a.out_stride = d->out_stride;
   a.out_off = d->out_off;
   if (conv_halo_applies(a)) {  // few output channels: one haloed input box per channel block
-    CUtensorMap tmH;
+    // an input with <= 32 channels of data: 32-channel rows (64-byte swizzle), half the MMAs
+    const int kb = (d->cin > 0 && d->cin <= 32) ? 32 : 64;
+    const CUtensorMapSwizzle sw = kb == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
+    CUtensorMap tmH, tmWk;
     const uint64_t dims[4] = {(uint64_t)d->cin_pad, (uint64_t)d->W, (uint64_t)d->H, (uint64_t)d->B};
     const uint64_t strides[3] = {(uint64_t)d->cin_pad * 2, (uint64_t)d->W * d->cin_pad * 2,
                                  (uint64_t)d->H * d->W * d->cin_pad * 2};
-    const uint32_t box[4] = {64, 130, 3, 1};
-    if (encode_tiled(&tmH, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(d->x), dims, strides, box,
-                     CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+    const uint32_t box[4] = {(uint32_t)kb, 130, 3, 1};
+    if (encode_tiled(&tmH, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(d->x), dims, strides, box, sw) !=
+        CUDA_SUCCESS)
       return MCR_ERR_CUDA;
-    if (launch_conv_halo(tmH, tmW, a, (cudaStream_t)stream) != cudaSuccess) return MCR_ERR_CUDA;
+    if (kb == 32) {  // weight boxes of 32 channels of each tap
+      const uint64_t K = (uint64_t)d->taps * d->cin_pad;
+      const uint64_t wdims[2] = {K, (uint64_t)d->n_pad};
+      const uint64_t wstrides[1] = {K * 2};
+      const uint32_t wbox[2] = {32, (uint32_t)d->n_pad};
+      if (encode_tiled(&tmWk, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(d->w), wdims, wstrides, wbox,
+                       CU_TENSOR_MAP_SWIZZLE_64B) != CUDA_SUCCESS)
+        return MCR_ERR_CUDA;
+    }
+    if (launch_conv_halo(tmH, kb == 32 ? tmWk : tmW, a, (cudaStream_t)stream, kb) != cudaSuccess) return MCR_ERR_CUDA;
     return MCR_OK;
   }
   if (launch_conv_tc(tmX, tmW, a, (cudaStream_t)stream) != cudaSuccess) return MCR_ERR_CUDA;

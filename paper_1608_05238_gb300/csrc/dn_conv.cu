@@ -470,16 +470,25 @@ __global__ void __launch_bounds__(ws_threads<SUB>(), 1)
 // 50 KB through L2 per 128 pixels and channel block (a box per tap plus its weights would be
 // 9 x (16 + N/8) KB), which is what bounds these convolutions.  Same warp roles and double TMEM
 // accumulator as k_conv_ws.
-constexpr uint32_t kHaloBytes = 3 * 130 * 128;  // 49,920 B written by the input box
-constexpr uint32_t kHaloStride = (kHaloBytes + 1023) & ~1023u;
+// KB = 32: layers whose input has at most 32 real channels (in a 64-channel row) read only those
+// 32: 64-byte rows with the 64-byte swizzle, half the MMAs and operand bytes of KB = 64.
+template <int KB>
+__host__ __device__ constexpr uint32_t halo_bytes() { return 3u * 130u * KB * 2u; }  // written by the input box
+template <int KB>
+__host__ __device__ constexpr uint32_t halo_stride() { return (halo_bytes<KB>() + 1023u) & ~1023u; }
+template <int KB>
+__device__ __forceinline__ uint64_t sdesc_kb(uint32_t addr) { return KB == 64 ? sdesc_k128(addr) : sdesc_k64(addr); }
 
+template <int KB>
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_conv_halo(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmW, const ConvArgs a,
                 int stages, int num_tiles) {
+  static_assert(KB == 64 || KB == 32, "channel block of 64 (128-byte rows) or 32 (64-byte rows)");
+  constexpr uint32_t kHaloBytes = halo_bytes<KB>(), kHaloStride = halo_stride<KB>();
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int cblocks = a.cin_pad / kBlockK;
-  const uint32_t bTileBytes = (uint32_t)a.N * kBlockK * 2;      // one tap's weights, one channel block
+  const int cblocks = KB == 64 ? a.cin_pad / 64 : 1;
+  const uint32_t bTileBytes = (uint32_t)a.N * KB * 2;      // one tap's weights, one channel block
   const uint32_t wBytes = (uint32_t)cblocks * 9u * bTileBytes;  // resident weights [cb][tap]
   uint8_t *ring = smem + wBytes;
   uint64_t *full = reinterpret_cast<uint64_t *>(ring + (size_t)stages * kHaloStride);
@@ -520,7 +529,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     mbar_arrive_expect_tx(wfull, wBytes);
     for (int cb = 0; cb < cblocks; ++cb)
       for (int tap = 0; tap < 9; ++tap)
-        tma_load_2d(smem + (cb * 9 + tap) * bTileBytes, &tmW, wfull, tap * a.cin_pad + cb * kBlockK, 0);
+        tma_load_2d(smem + (cb * 9 + tap) * bTileBytes, &tmW, wfull, tap * a.cin_pad + cb * KB, 0);
     uint32_t kc = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
@@ -536,7 +545,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
           break;
         }
         mbar_arrive_expect_tx(&full[st], kHaloBytes);
-        tma_load_4d(ring + (size_t)st * kHaloStride, &tmH, &full[st], cb * kBlockK, x0 - 1, y0 - 1, b0);
+        tma_load_4d(ring + (size_t)st * kHaloStride, &tmH, &full[st], cb * KB, x0 - 1, y0 - 1, b0);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -566,10 +575,10 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         const uint32_t aBase = smem_u32(ring + (size_t)st * kHaloStride);
         const uint32_t bBase = wBase + (uint32_t)cb * 9u * bTileBytes;
         for (int tap = 0; tap < 9; ++tap) {
-          const uint32_t arow = aBase + (uint32_t)((tap / 3) * 130 + tap % 3) * 128u;
+          const uint32_t arow = aBase + (uint32_t)((tap / 3) * 130 + tap % 3) * (KB * 2u);
 #pragma unroll
-          for (int kk = 0; kk < kBlockK / 16; ++kk)
-            mma_bf16(d, sdesc_k128(arow + kk * 32), sdesc_k128(bBase + tap * bTileBytes + kk * 32), idesc,
+          for (int kk = 0; kk < KB / 16; ++kk)
+            mma_bf16(d, sdesc_kb<KB>(arow + kk * 32), sdesc_kb<KB>(bBase + tap * bTileBytes + kk * 32), idesc,
                      (cb > 0 || tap > 0 || kk > 0) ? 1u : 0u);
         }
         mma_commit(&empty[st]);
@@ -1048,34 +1057,41 @@ cudaError_t launch_wgrad_mn(const CUtensorMap &tmA, const CUtensorMap &tmB, cons
   return cudaGetLastError();
 }
 
-// ring depth of k_conv_halo beside its resident weights (cblocks x 9 x N x 128 B), at most 4
-static int halo_stages(int N, int cblocks) {
-  const long long avail = 232448 - 1024 - 512 - (long long)cblocks * 9 * N * kBlockK * 2;
-  const long long st = avail / (long long)kHaloStride;
+// ring depth of k_conv_halo beside its resident weights (cblocks x 9 x N x KB x 2 B), at most 4
+static int halo_stages(int N, int cblocks, int kb) {
+  const long long stride = kb == 64 ? halo_stride<64>() : halo_stride<32>();
+  const long long avail = 232448 - 1024 - 512 - (long long)cblocks * 9 * N * kb * 2;
+  const long long st = avail / stride;
   return st > 4 ? 4 : (st < 0 ? 0 : (int)st);
 }
 
 bool conv_halo_applies(const ConvArgs &a) {
-  return a.taps == 9 && a.W % kBlockM == 0 && a.N <= 32 && halo_stages(a.N, a.cin_pad / kBlockK) >= 2;
+  return a.taps == 9 && a.W % kBlockM == 0 && a.N <= 32 && halo_stages(a.N, a.cin_pad / kBlockK, 64) >= 2;
 }
 
-cudaError_t launch_conv_halo(const CUtensorMap &tmH, const CUtensorMap &tmW, ConvArgs a, cudaStream_t s) {
+template <int KB>
+static cudaError_t launch_halo_kb(const CUtensorMap &tmH, const CUtensorMap &tmW, ConvArgs a, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_halo<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   uint32_t cols = 32;
   while (cols < (uint32_t)a.N) cols <<= 1;
   a.tmem_cols = cols;
-  const int cblocks = a.cin_pad / kBlockK;
-  const int st = halo_stages(a.N, cblocks);
-  const size_t smem = 1024 + (size_t)cblocks * 9 * a.N * kBlockK * 2 + (size_t)st * kHaloStride + 512;
+  const int cblocks = KB == 64 ? a.cin_pad / kBlockK : 1;
+  const int st = halo_stages(a.N, cblocks, KB);
+  if (st < 2) return cudaErrorInvalidValue;
+  const size_t smem = 1024 + (size_t)cblocks * 9 * a.N * KB * 2 + (size_t)st * halo_stride<KB>() + 512;
   const long long tiles = (long long)a.B * a.H * a.W / kBlockM;
   const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
-  k_conv_halo<<<grid, kWsThreads, smem, s>>>(tmH, tmW, a, st, (int)tiles);
+  k_conv_halo<KB><<<grid, kWsThreads, smem, s>>>(tmH, tmW, a, st, (int)tiles);
   return cudaGetLastError();
+}
+
+cudaError_t launch_conv_halo(const CUtensorMap &tmH, const CUtensorMap &tmW, ConvArgs a, cudaStream_t s, int kb) {
+  return kb == 32 ? launch_halo_kb<32>(tmH, tmW, a, s) : launch_halo_kb<64>(tmH, tmW, a, s);
 }
 
 bool wgrad_halo_applies(int taps, int cout, int W) { return taps == 9 && cout <= 64 && W % 64 == 0; }

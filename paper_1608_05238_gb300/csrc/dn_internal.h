@@ -45,7 +45,9 @@ cudaError_t launch_conv_tc(const CUtensorMap &tmX, const CUtensorMap &tmW, const
 // 3x3 convolution with N <= 32 on rows of whole 128-pixel tiles: one haloed input box {64, 130, 3, 1}
 // and all nine taps' weights per channel block
 bool conv_halo_applies(const ConvArgs &a);
-cudaError_t launch_conv_halo(const CUtensorMap &tmH, const CUtensorMap &tmW, ConvArgs a, cudaStream_t s);
+// kb = 64: channel blocks of 64 (box {64, 130, 3, 1}, 128-byte swizzle); kb = 32: only the first 32
+// channels of each row (box {32, 130, 3, 1} and weight box {32, N}, 64-byte swizzle)
+cudaError_t launch_conv_halo(const CUtensorMap &tmH, const CUtensorMap &tmW, ConvArgs a, cudaStream_t s, int kb);
 
 // Weight-gradient GEMM launch arguments (see k_wgrad_tc).
 struct WgradArgs {

@@ -119,6 +119,18 @@ __device__ __forceinline__ uint64_t sdesc_k128(uint32_t smem_addr) {
   return d;
 }
 
+// The same for K-major rows of 64 bytes (32 bf16) stored with the 64-byte swizzle: 8-row groups
+// 512 B apart, layout type 4.
+__device__ __forceinline__ uint64_t sdesc_k64(uint32_t smem_addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(512u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)4u << 61;
+  return d;
+}
+
 // Shared-memory descriptor of an MN-major operand (the M or N index contiguous) stored with the
 // 128-byte swizzle: each 128-byte row holds 64 consecutive M (N) elements of one K index, 8-row
 // atoms along K are 1024 B apart (stride byte offset) and consecutive 64-element groups along M

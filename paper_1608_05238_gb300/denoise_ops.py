@@ -19,7 +19,7 @@ class _ConvDesc(C.Structure):
                 ("taps", C.c_int32), ("cout", C.c_int32), ("n_pad", C.c_int32), ("w", C.c_void_p),
                 ("bias", C.c_void_p), ("relu", C.c_int32), ("mask", C.c_void_p), ("mask_stride", C.c_int32),
                 ("mask_off", C.c_int32), ("out", C.c_void_p), ("out_f32", C.c_int32), ("out_stride", C.c_int32),
-                ("out_off", C.c_int32)]
+                ("out_off", C.c_int32), ("cin", C.c_int32)]
 
 
 class _HeadDesc(C.Structure):
@@ -242,11 +242,13 @@ def _stream(stream):
 
 
 def conv(x: torch.Tensor, w: torch.Tensor, cout: int, out: torch.Tensor, *, taps: int = 9, bias=None,
-         relu: bool = False, mask: torch.Tensor | None = None, mask_off: int = 0, out_off: int = 0, stream=None):
+         relu: bool = False, mask: torch.Tensor | None = None, mask_off: int = 0, out_off: int = 0,
+         cin: int = 0, stream=None):
     """out[..., out_off:out_off+cout] = epilogue(conv(x, w)) on the tensor cores (``dn_conv``).
 
     x: [B, H, W, cin_pad] bf16; w: [n_pad, taps, cin_pad] bf16; out: [B, H, W, out_stride] bf16 or
-    fp32; mask (optional, bf16 NHWC): zero the outputs where mask[..., mask_off + n] <= 0.
+    fp32; mask (optional, bf16 NHWC): zero the outputs where mask[..., mask_off + n] <= 0; cin: the
+    input channels that hold data (0: all), the rest taken as zero.
     """
     assert x.is_cuda and x.dtype == torch.bfloat16 and x.is_contiguous() and x.dim() == 4
     assert w.is_cuda and w.dtype == torch.bfloat16 and w.is_contiguous() and w.shape[1] == taps
@@ -260,7 +262,7 @@ def conv(x: torch.Tensor, w: torch.Tensor, cout: int, out: torch.Tensor, *, taps
     d = _ConvDesc(B, H, W, cin_pad, x.data_ptr(), taps, cout, w.shape[0], w.data_ptr(),
                   bias.data_ptr() if bias is not None else None, 1 if relu else 0,
                   mask.data_ptr() if mask is not None else None, mask.shape[3] if mask is not None else 0, mask_off,
-                  out.data_ptr(), 1 if out.dtype == torch.float32 else 0, out.shape[3], out_off)
+                  out.data_ptr(), 1 if out.dtype == torch.float32 else 0, out.shape[3], out_off, cin)
     rc = lib().dn_conv(C.byref(d), _stream(stream))
     if rc != 0:
         raise mcr.McrError(rc, "dn_conv")

@@ -69,13 +69,15 @@ class Conv:
 
     def forward(self, x: torch.Tensor, out: Act, f32: bool = False):
         assert x.shape[3] == self.cin_pad, (self.name, x.shape, self.cin_pad)
-        ops.conv(x, self.wf, self.cout, out.t, taps=self.taps, bias=self.b, relu=self.relu, out_off=out.off)
+        ops.conv(x, self.wf, self.cout, out.t, taps=self.taps, bias=self.b, relu=self.relu, out_off=out.off,
+                 cin=self.cin)
 
     def input_grad(self, dz: torch.Tensor, dx: torch.Tensor, mask: torch.Tensor | None):
         """dx[..., :cin] = conv(dz, flipped W^T), times (mask > 0) if a mask is given."""
         for c0 in range(0, self.cin, 256):
             n = min(256, self.cin - c0)
-            ops.conv(dz, self.wd[c0:c0 + r16(n)], n, dx, taps=self.taps, mask=mask, mask_off=c0, out_off=c0)
+            ops.conv(dz, self.wd[c0:c0 + r16(n)], n, dx, taps=self.taps, mask=mask, mask_off=c0, out_off=c0,
+                     cin=self.cout)
 
 
 LAYERS = [  # name, input, output (buffer, offset), cin, cout, taps, relu

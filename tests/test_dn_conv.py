@@ -117,6 +117,36 @@ def test_haloed_conv_epilogue_options():
     assert torch.allclose(out2[..., :cout].double().cpu(), ref2, rtol=1e-4, atol=1e-4 * ref2.abs().max().item())
 
 
+@pytest.mark.parametrize("B,H,W,cin,cout,relu_mask", [(2, 5, 256, 32, 32, False), (1, 7, 128, 20, 16, True),
+                                                      (3, 2, 512, 32, 30, True)])
+def test_haloed_conv_on_32_channel_inputs(B, H, W, cin, cout, relu_mask):
+    """An input with at most 32 channels in use (rows of 64, the rest garbage under zero weights)
+    takes the 32-channel haloed kernel (64-byte rows and swizzle, two K steps per tap): same
+    products as the reference on the used channels, with bias/ReLU or the mask epilogue."""
+    x, w, cin_pad, n_pad = _case(B, H, W, cin, cout, 9, seed=31 + cin)
+    g = torch.Generator().manual_seed(77)
+    garbage = torch.randn(B, H, W, cin_pad - cin, generator=g).bfloat16().cuda()
+    x = torch.cat([x[..., :cin], garbage], dim=3).contiguous()  # padded channels hold data; their weights are 0
+    out = torch.zeros(B, H, W, 32, device="cuda")
+    if relu_mask:
+        mask = torch.randn(B, H, W, 64, generator=g).bfloat16().cuda()
+        ops.conv(x, w, cout, out, mask=mask, mask_off=8, cin=cin)
+        ref = _ref(x, w, cin, cout, 9, mask=mask, mask_off=8)
+    else:
+        bias = torch.randn(cout, generator=g).cuda()
+        ops.conv(x, w, cout, out, bias=bias, relu=True, cin=cin)
+        ref = _ref(x, w, cin, cout, 9, bias=bias, relu=True)
+    ops.check()
+    assert torch.allclose(out[..., :cout].double().cpu(), ref, rtol=1e-4, atol=1e-4 * ref.abs().max().item())
+    # the full-width path on the same data (cin not given) agrees
+    out64 = torch.zeros_like(out)
+    if relu_mask:
+        ops.conv(x, w, cout, out64, mask=mask, mask_off=8)
+    else:
+        ops.conv(x, w, cout, out64, bias=bias, relu=True)
+    assert torch.allclose(out, out64, rtol=1e-5, atol=1e-5 * out64.abs().max().item())
+
+
 def test_conv_rejects_bad_shapes():
     x, w, _, _ = _case(1, 4, 32, 64, 16, 9, seed=1)
     out = torch.zeros(1, 4, 32, 16, device="cuda")
