@@ -25,15 +25,18 @@ def _medium(nz, nx, dx, g, seed):
 def _mixed_problems(K):
     """Forward and adjoint problems on uneven grids with different sources and packet counts."""
     probs, meta = [], []
-    shapes = [(40, 56, 0.1), (33, 33, 0.05), (64, 24, 0.08), (17, 90, 0.12), (50, 50, 0.07)]
+    shapes = [(40, 56, 0.1), (33, 33, 0.05), (64, 24, 0.08), (17, 90, 0.12), (50, 50, 0.07), (26, 38, 0.09),
+              (30, 44, 0.1)]
     for i, (nz, nx, dx) in enumerate(shapes):
         med, mua, mus = _medium(nz, nx, dx, 0.6 + 0.05 * i, seed=30 + i)
         n = 20_000 + 7_777 * i
         if i % 2 == 0:
             kinds = [mcr.Source(mcr.LINE, x0=0.0, z0=0.0, x1=f32(nx * dx), z1=0.0, dir_x=0.0, dir_z=1.0),
                      mcr.Source(mcr.ISO_POINT, x0=f32(0.37 * nx * dx), z0=f32(0.61 * nz * dx), power=2.0),
-                     mcr.Source(mcr.PENCIL, x0=f32(0.5 * nx * dx), z0=0.0, dir_x=0.3, dir_z=0.9)]
-            p = mcr.Problem(med, n, seed=5 + i, stream_id=2 * i, source=kinds[(i // 2) % 3])
+                     mcr.Source(mcr.PENCIL, x0=f32(0.5 * nx * dx), z0=0.0, dir_x=0.3, dir_z=0.9),
+                     mcr.Source(mcr.ANGULAR_POINT, x0=f32(0.41 * nx * dx), z0=f32(0.45 * nz * dx),
+                                ang_c=(0.0, 0.5), ang_s=(0.25,))]
+            p = mcr.Problem(med, n, seed=5 + i, stream_id=2 * i, source=kinds[(i // 2) % 4])
         else:
             q = np.random.default_rng(i).normal(size=(nz, nx)).astype(np.float32)
             q[np.random.default_rng(i + 9).uniform(size=q.shape) < 0.5] = 0

@@ -67,6 +67,15 @@ def test_noalloc_matches_mc_forward_on_consecutive_calls(lib):
     assert torch.cuda.mem_get_info()[0] == free0  # no device memory taken by the later calls
 
 
+def test_noalloc_angular_point_source(lib):
+    """The angular point source (a Sec. 4.1 detector as a source) through the no-allocation call."""
+    med, _, run = _case(48, 40, 0.1, 8, 100_001, seed=8)
+    src = mcr.Source(kind=mcr.ANGULAR_POINT, x0=f32(1.3), z0=f32(2.2), ang_c=(0.0, 0.0, 0.0, -1.0))
+    ref = mcr.forward(med, src, run).double().cpu().numpy()
+    out = torch.empty((2 * run.K + 1,) + med.shape, device="cuda")
+    _assert_close(_noalloc(lib, med, src, run, out), ref)
+
+
 def test_noalloc_refuses_oversize_problems(lib):
     med, src, run = _case(512, 512, 0.02, 32, 1000, seed=1)
     out = torch.empty((2 * run.K + 1, 512, 512), device="cuda")
