@@ -61,6 +61,16 @@ class _Run(C.Structure):
                 ("roulette_p", C.c_float), ("sectors", C.c_uint32)]
 
 
+class _Medium3(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("dx", C.c_double), ("g", C.c_double),
+                ("mua", C.POINTER(C.c_double)), ("mus", C.POINTER(C.c_double))]
+
+
+class _Source3(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
+                ("dir_x", C.c_double), ("dir_y", C.c_double), ("dir_z", C.c_double), ("power", C.c_double)]
+
+
 class _Stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("launched", "flights", "collisions", "segments", "escapes",
                                           "rr_kill", "rr_survive", "scatter_limit", "event_limit")] + \
@@ -79,6 +89,17 @@ def _load():
                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(_Stats),
                                            C.POINTER(C.c_double)]
             lib.orc_volume_raw.restype = C.c_int
+            lib.orc3_forward_raw.argtypes = [C.POINTER(_Medium3), C.POINTER(_Source3), C.POINTER(_Run),
+                                             C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(_Stats)]
+            lib.orc3_forward_raw.restype = C.c_int
+            lib.orc3_volume_raw.argtypes = [C.POINTER(_Medium3), C.POINTER(C.c_float), C.POINTER(_Run), C.c_int,
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(_Stats),
+                                            C.POINTER(C.c_double)]
+            lib.orc3_volume_raw.restype = C.c_int
+            lib.orc3_sh.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]
+            lib.orc3_sh.restype = None
+            lib.orc3_hg_cos.argtypes = [C.c_double, C.c_double]
+            lib.orc3_hg_cos.restype = C.c_double
             lib.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
             lib.orc_philox4x32_10.restype = None
             lib.orc_hg_angle.argtypes = [C.c_double, C.c_double]
@@ -135,10 +156,12 @@ def _stats_dict(st: _Stats) -> dict:
     return {n: getattr(st, n) for n, _ in _Stats._fields_}
 
 
-def _finish(raw, sq, n_packets, S, dx, st, sectors=0) -> Result:
+def _finish(raw, sq, n_packets, S, dx, st, sectors=0, volume_power=2) -> Result:
     """Normalised coefficients: harmonics a_0, a_n, b_n, or with ``sectors`` > 0 the angular
-    integrals of the radiance over each sector (they sum to a_0)."""
-    A = dx * dx
+    integrals of the radiance over each sector (they sum to a_0); in 3D (``volume_power`` 3) the
+    spherical-harmonic coefficients per unit voxel volume.  The variance is that of channel 0's
+    per-packet track-weight sums (the fluence estimate up to the constant of channel 0)."""
+    A = dx ** volume_power
     norm = S / (n_packets * A) if n_packets > 0 else 0.0
     coeff = raw * norm
     var = None
@@ -249,3 +272,70 @@ def volume_pick(q, seed: int, stream_id: int, packet: int) -> int:
     lib = _load()
     q = np.ascontiguousarray(q, dtype=np.float32)
     return int(lib.orc_volume_pick(q.ctypes.data_as(C.POINTER(C.c_float)), q.size, seed, stream_id, packet))
+
+
+# ---------------------------------------------------------------------------------------------- 3D
+def _medium3(mua, mus, dx, g):
+    mua = np.ascontiguousarray(mua, dtype=np.float64)
+    mus = np.ascontiguousarray(mus, dtype=np.float64)
+    assert mua.shape == mus.shape and mua.ndim == 3
+    m = _Medium3(mua.shape[2], mua.shape[1], mua.shape[0], float(dx), float(g),
+                 mua.ctypes.data_as(C.POINTER(C.c_double)), mus.ctypes.data_as(C.POINTER(C.c_double)))
+    return m, (mua, mus)
+
+
+def sh3(L: int, sx: float, sy: float, sz: float) -> np.ndarray:
+    """Orthonormal real spherical harmonics Y_lm(s), l <= L, at index l^2 + l + m (the 3D basis)."""
+    Y = np.zeros((L + 1) ** 2)
+    _load().orc3_sh(L, sx, sy, sz, Y.ctypes.data_as(C.POINTER(C.c_double)))
+    return Y
+
+
+def hg3_cos(g: float, u: float) -> float:
+    """Cosine of a 3D Henyey-Greenstein scattering angle drawn by the inverse CDF at u."""
+    return _load().orc3_hg_cos(g, u)
+
+
+def forward3(mua, mus, dx, g, source: dict, run: RunParams, with_variance: bool = False) -> Result:
+    """3D forward radiance MC (the paper's named 3D extension): voxels [nz, ny, nx], source
+    dict(kind=PENCIL|ISO_POINT, x0, y0, z0, dir_x, dir_y, dir_z, power=1), spherical-harmonic
+    coefficients c_lm up to l = run.K, [(K+1)^2, nz, ny, nx], normalised by power / (N_p dx^3)."""
+    lib = _load()
+    m, keep = _medium3(mua, mus, dx, g)
+    s = _Source3(int(source["kind"]), float(source.get("x0", 0.0)), float(source.get("y0", 0.0)),
+                 float(source.get("z0", 0.0)), float(source.get("dir_x", 0.0)), float(source.get("dir_y", 0.0)),
+                 float(source.get("dir_z", 1.0)), float(source.get("power", 1.0)))
+    shape = keep[0].shape
+    raw = np.zeros(((run.K + 1) ** 2,) + shape, dtype=np.float64)
+    sq = np.zeros(shape, dtype=np.float64) if with_variance else None
+    st = _Stats()
+    rc = lib.orc3_forward_raw(C.byref(m), C.byref(s), C.byref(_run(run)), raw.ctypes.data_as(C.POINTER(C.c_double)),
+                              sq.ctypes.data_as(C.POINTER(C.c_double)) if sq is not None else None, C.byref(st))
+    if rc != 0:
+        raise ValueError(f"oracle forward3: status {rc}")
+    return _finish(raw, sq, run.n_packets, s.power, dx, st, volume_power=3)
+
+
+def volume3(mua, mus, dx, g, q, run: RunParams, adjoint: bool = True, with_variance: bool = False) -> Result:
+    """3D run from the signed volumetric isotropic source q ([nz, ny, nx] float32, per unit volume
+    and solid angle); ``adjoint=True`` tallies at -s (coefficients c*_lm)."""
+    lib = _load()
+    m, keep = _medium3(mua, mus, dx, g)
+    q = np.ascontiguousarray(q, dtype=np.float32)
+    assert q.shape == keep[0].shape
+    raw = np.zeros(((run.K + 1) ** 2,) + q.shape, dtype=np.float64)
+    sq = np.zeros(q.shape, dtype=np.float64) if with_variance else None
+    st = _Stats()
+    S = C.c_double(0.0)
+    rc = lib.orc3_volume_raw(C.byref(m), q.ctypes.data_as(C.POINTER(C.c_float)), C.byref(_run(run)),
+                             1 if adjoint else 0, raw.ctypes.data_as(C.POINTER(C.c_double)),
+                             sq.ctypes.data_as(C.POINTER(C.c_double)) if sq is not None else None, C.byref(st),
+                             C.byref(S))
+    if rc != 0:
+        raise ValueError(f"oracle volume3: status {rc}")
+    return _finish(raw, sq, run.n_packets, S.value, dx, st, volume_power=3)
+
+
+def adjoint3(mua, mus, dx, g, qstar, run: RunParams, with_variance: bool = False) -> Result:
+    """3D adjoint radiance MC from q* (per unit volume and solid angle)."""
+    return volume3(mua, mus, dx, g, qstar, run, adjoint=True, with_variance=with_variance)

@@ -112,3 +112,65 @@ def dL_dmu(coeff, coeff_adj, v, dx, g):
     d_mua = np.asarray(v, dtype=np.float64) * a0 + A * G_a(coeff, coeff_adj)
     d_mus = A * G_s(coeff, coeff_adj, g)
     return d_mua, d_mus
+
+
+# ---------------------------------------------------------------------------------------------- 3D
+# The 3D form (the extension Sec. 3.1 names): coefficients [(L+1)^2, nz, ny, nx] of orthonormal
+# real spherical harmonics, phi(s) = sum c_lm Y_lm(s); fluence sqrt(4 pi) c_00; the HG kernel is
+# sum_l g^l sum_m Y_lm(s) Y_lm(s'), so the angular integrals of Eqs. 22, 26, 28 become sums of
+# c_lm c*_lm (weighted by g^l for the scattering term).  Voxel volume V = dx^3.
+def _l_of(C):
+    return np.array([int(math.isqrt(c)) for c in range(C)])
+
+
+def fluence3(coeff):
+    """Phi = int phi ds = sqrt(4 pi) c_00."""
+    return math.sqrt(4.0 * math.pi) * np.asarray(coeff, dtype=np.float64)[0]
+
+
+def absorbed_energy3(mua, coeff):
+    """H = mu_a Phi (Sec. 2) in 3D."""
+    return np.asarray(mua, dtype=np.float64) * fluence3(coeff)
+
+
+def error_functional3(Hmeas, H, dx):
+    """eps = 1/2 sum_v V (H^meas_v - H_v)^2 (Eq. 2 over voxels)."""
+    r = np.asarray(Hmeas, dtype=np.float64) - np.asarray(H, dtype=np.float64)
+    return 0.5 * dx ** 3 * float(np.sum(r * r))
+
+
+def dL_dH_eps3(Hmeas, H, dx):
+    """dL/dH_v for L = eps: -V (H^meas_v - H_v)."""
+    return -dx ** 3 * (np.asarray(Hmeas, dtype=np.float64) - np.asarray(H, dtype=np.float64))
+
+
+def adjoint_source3(mua, v, dx):
+    """q*_v = -mu_a,v v_v / V, per unit volume and solid angle (isotropic)."""
+    return -np.asarray(mua, dtype=np.float64) * np.asarray(v, dtype=np.float64) / dx ** 3
+
+
+def G_a3(coeff, coeff_adj):
+    """int phi phi* ds = sum_lm c_lm c*_lm (orthonormal basis), in increasing channel order."""
+    c, a = np.asarray(coeff, dtype=np.float64), np.asarray(coeff_adj, dtype=np.float64)
+    out = np.zeros(c.shape[1:])
+    for k in range(c.shape[0]):
+        out = out + c[k] * a[k]
+    return out
+
+
+def G_s3(coeff, coeff_adj, g):
+    """int phi* phi ds - int int phi* P phi = sum_lm (1 - g^l) c_lm c*_lm."""
+    c, a = np.asarray(coeff, dtype=np.float64), np.asarray(coeff_adj, dtype=np.float64)
+    ls = _l_of(c.shape[0])
+    out = np.zeros(c.shape[1:])
+    for k in range(c.shape[0]):
+        out = out + (1.0 - g ** int(ls[k])) * c[k] * a[k]
+    return out
+
+
+def dL_dmu3(coeff, coeff_adj, v, dx, g):
+    """Gradients of a voxel loss L(H) with v = dL/dH: dL/dmu_a = v Phi + V G_a, dL/dmu_s = V G_s."""
+    V = dx ** 3
+    ga = np.asarray(v, dtype=np.float64) * fluence3(coeff) + V * G_a3(coeff, coeff_adj)
+    gs = V * G_s3(coeff, coeff_adj, g)
+    return ga, gs

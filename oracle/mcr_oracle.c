@@ -579,3 +579,420 @@ int64_t orc_volume_pick(const float *q, int64_t npix, uint64_t seed, uint32_t st
   free(vs.cdf);
   return pix;
 }
+
+/* ======================================================================
+ * 3D: the extension the paper names (Sec. 3.1: "in 3D ... spherical
+ * harmonics").  Voxels [nz][ny][nx] of side dx; direction
+ * s = (sin th cos ph, sin th sin ph, cos th), th from +z; the 3D
+ * Henyey-Greenstein phase function; the tally holds c_lm = sum t Y_lm(s)
+ * over orthonormal real spherical harmonics (index l^2 + l + m, l <= L), so
+ * that phi(s) = sum c_lm Y_lm(s) and the fluence is sqrt(4 pi) c_00.
+ * Adjoint runs tally at -s: Y_lm(-s) = (-1)^l Y_lm(s).
+ * Random numbers as in 2D; launch event 0: words 0, 1 -> the voxel of a
+ * volumetric source, word 2 -> cos th = 2u - 1, word 3 -> ph = 2 pi u
+ * (isotropic directions); event 1: words 0..2 -> the position in the voxel;
+ * flight k >= 1, event k+1: word 0 -> free path, 1 -> HG cos, 2 ->
+ * roulette, 3 -> azimuth of the scattering.
+ * ====================================================================== */
+#define ORC3_MAX_L 16
+
+typedef struct {
+  int32_t nx, ny, nz;
+  double dx;
+  double g;
+  const double *mua; /* [nz][ny][nx] */
+  const double *mus;
+} orc3_medium;
+
+typedef struct {
+  int32_t kind;            /* ORC_PENCIL or ORC_ISO_POINT */
+  double x0, y0, z0;       /* mm */
+  double dir_x, dir_y, dir_z; /* unit direction (pencil) */
+  double power;
+} orc3_source;
+
+/* Orthonormal real spherical harmonics Y_lm(s) for l <= L at index l^2 + l + m:
+ * Y_l0 = N_l0 P_l(cos th), Y_lm = sqrt 2 N_lm P_l^m(cos th) cos(m ph) (m > 0),
+ * Y_l,-m = sqrt 2 N_lm P_l^m(cos th) sin(m ph), N_lm^2 = (2l+1)/(4 pi) (l-m)!/(l+m)!,
+ * with the associated Legendre functions from their standard three-term
+ * recurrence in l (no Condon-Shortley sign: any fixed sign is orthonormal). */
+void orc3_sh(int L, double sx, double sy, double sz, double *Y) {
+  const double ct = sz, st = sqrt(fmax(0.0, 1.0 - sz * sz));
+  const double ph = atan2(sy, sx);
+  for (int m = 0; m <= L; ++m) {
+    /* P_m^m = (2m-1)!! st^m */
+    double pmm = 1.0;
+    for (int k = 1; k <= m; ++k) pmm *= (2.0 * k - 1.0) * st;
+    double plm2 = 0.0, plm1 = pmm;
+    for (int l = m; l <= L; ++l) {
+      double plm;
+      if (l == m)
+        plm = pmm;
+      else if (l == m + 1)
+        plm = ct * (2.0 * m + 1.0) * pmm;
+      else
+        plm = ((2.0 * l - 1.0) * ct * plm1 - (l + m - 1.0) * plm2) / (double)(l - m);
+      if (l > m) {
+        plm2 = plm1;
+        plm1 = plm;
+      }
+      double ratio = 1.0; /* (l-m)!/(l+m)! */
+      for (int k = l - m + 1; k <= l + m; ++k) ratio /= (double)k;
+      const double N = sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * ratio);
+      if (m == 0) {
+        Y[l * l + l] = N * plm;
+      } else {
+        Y[l * l + l + m] = M_SQRT2 * N * plm * cos(m * ph);
+        Y[l * l + l - m] = M_SQRT2 * N * plm * sin(m * ph);
+      }
+    }
+  }
+}
+
+/* cos of the scattering angle of the 3D Henyey-Greenstein phase function
+ * p(cos) = (1 - g^2) / (4 pi (1 + g^2 - 2 g cos)^(3/2)), by inverting its
+ * cumulative distribution at u. */
+double orc3_hg_cos(double g, double u) {
+  if (g == 0.0) return 2.0 * u - 1.0;
+  const double f = (1.0 - g * g) / (1.0 - g + 2.0 * g * u);
+  double c = (1.0 + g * g - f * f) / (2.0 * g);
+  if (c > 1.0) c = 1.0;
+  if (c < -1.0) c = -1.0;
+  return c;
+}
+
+/* Turn the unit direction u by polar angle (cos ct) and azimuth psi about it,
+ * in the orthonormal frame (t1, t2, u) of Duff et al., "Building an
+ * orthonormal basis, revisited" (JCGT 2017). */
+static void orc3_turn(double *ux, double *uy, double *uz, double ct, double psi) {
+  const double sgn = *uz >= 0.0 ? 1.0 : -1.0;
+  const double a = -1.0 / (sgn + *uz), b = *ux * *uy * a;
+  const double t1x = 1.0 + sgn * *ux * *ux * a, t1y = sgn * b, t1z = -sgn * *ux;
+  const double t2x = b, t2y = sgn + *uy * *uy * a, t2z = -*uy;
+  const double st = sqrt(fmax(0.0, 1.0 - ct * ct)), cp = cos(psi), sp = sin(psi);
+  double nx = ct * *ux + st * (cp * t1x + sp * t2x);
+  double ny = ct * *uy + st * (cp * t1y + sp * t2y);
+  double nz = ct * *uz + st * (cp * t1z + sp * t2z);
+  const double n = sqrt(nx * nx + ny * ny + nz * nz);
+  *ux = nx / n;
+  *uy = ny / n;
+  *uz = nz / n;
+}
+
+typedef struct {
+  const orc3_medium *med;
+  const orc3_source *src;
+  const orc_volsrc *vol;
+  const orc_run *run;
+  int adjoint;
+  uint64_t p_begin, p_end;
+  double *tally; /* [C][nvox] */
+  double *sq, *pk;
+  int64_t *touched;
+  int64_t n_touched;
+  orc_stats st;
+} orc3_job;
+
+static void orc3_deposit(orc3_job *j, int64_t v, double t, double sx, double sy, double sz) {
+  const int L = j->run->K;
+  const int64_t nvox = (int64_t)j->med->nx * j->med->ny * j->med->nz;
+  double Y[(ORC3_MAX_L + 1) * (ORC3_MAX_L + 1)];
+  if (j->adjoint)
+    orc3_sh(L, -sx, -sy, -sz, Y);
+  else
+    orc3_sh(L, sx, sy, sz, Y);
+  for (int c = 0; c < (L + 1) * (L + 1); ++c) j->tally[(int64_t)c * nvox + v] += t * Y[c];
+  if (j->sq) {
+    if (j->pk[v] == 0.0) j->touched[j->n_touched++] = v;
+    j->pk[v] += t;
+  }
+}
+
+static void orc3_packet(orc3_job *j, uint64_t p) {
+  const orc3_medium *m = j->med;
+  const orc_run *r = j->run;
+  const int nx = m->nx, ny = m->ny, nz = m->nz;
+  const double dx = m->dx;
+  const int64_t nvox = (int64_t)nx * ny * nz;
+  const uint32_t key[2] = {(uint32_t)r->seed, (uint32_t)(r->seed >> 32) ^ r->stream_id};
+  uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0u, 0u};
+  uint32_t b0[4], b1[4], b[4];
+  orc_philox4x32_10(ctr, key, b0);
+  ctr[2] = 1u;
+  orc_philox4x32_10(ctr, key, b1);
+
+  double x, y, z, ux, uy, uz, W0 = 1.0;
+  if (j->vol) {
+    const int64_t v = orc_volsrc_pick(j->vol, nvox, b0[0], b0[1]);
+    const int vx = (int)(v % nx), vy = (int)((v / nx) % ny), vz = (int)(v / ((int64_t)nx * ny));
+    x = (vx + orc_u01(b1[0])) * dx;
+    y = (vy + orc_u01(b1[1])) * dx;
+    z = (vz + orc_u01(b1[2])) * dx;
+    W0 = j->vol->q[v] < 0.0f ? -1.0 : 1.0;
+  } else {
+    x = j->src->x0;
+    y = j->src->y0;
+    z = j->src->z0;
+  }
+  if (j->vol || j->src->kind == ORC_ISO_POINT) {
+    const double ct = 2.0 * orc_u01(b0[2]) - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    const double ph = 2.0 * M_PI * orc_u01(b0[3]);
+    ux = st * cos(ph);
+    uy = st * sin(ph);
+    uz = ct;
+  } else {
+    ux = j->src->dir_x;
+    uy = j->src->dir_y;
+    uz = j->src->dir_z;
+  }
+  double W = W0;
+  j->st.launched++;
+  j->st.launched_w += W0;
+  if (!(x >= 0.0 && x <= nx * dx && y >= 0.0 && y <= ny * dx && z >= 0.0 && z <= nz * dx)) {
+    j->st.escapes++;
+    j->st.escaped_w += W;
+    return;
+  }
+  int ix = (int)floor(x / dx), iy = (int)floor(y / dx), iz = (int)floor(z / dx);
+  if (ix >= nx) ix = nx - 1;
+  if (iy >= ny) iy = ny - 1;
+  if (iz >= nz) iz = nz - 1;
+
+  uint32_t flight = 0, n_scatter = 0;
+  for (;;) {
+    if (flight >= r->max_events) {
+      j->st.event_limit++;
+      j->st.killed_w += W;
+      break;
+    }
+    ++flight;
+    j->st.flights++;
+    ctr[2] = flight + 1u;
+    orc_philox4x32_10(ctr, key, b);
+    double tau = -log(orc_u01(b[0]));
+    int escaped = 0;
+    for (;;) {
+      const int64_t v = ((int64_t)iz * ny + iy) * nx + ix;
+      const double mua = m->mua[v], mus = m->mus[v];
+      double dxf = INFINITY, dyf = INFINITY, dzf = INFINITY;
+      if (ux > 0.0) dxf = ((ix + 1) * dx - x) / ux;
+      if (ux < 0.0) dxf = (ix * dx - x) / ux;
+      if (uy > 0.0) dyf = ((iy + 1) * dx - y) / uy;
+      if (uy < 0.0) dyf = (iy * dx - y) / uy;
+      if (uz > 0.0) dzf = ((iz + 1) * dx - z) / uz;
+      if (uz < 0.0) dzf = (iz * dx - z) / uz;
+      if (dxf < 0.0) dxf = 0.0;
+      if (dyf < 0.0) dyf = 0.0;
+      if (dzf < 0.0) dzf = 0.0;
+      double d_face = dxf;
+      int axis = 0; /* ties: x first, then y, then z */
+      if (dyf < d_face) {
+        d_face = dyf;
+        axis = 1;
+      }
+      if (dzf < d_face) {
+        d_face = dzf;
+        axis = 2;
+      }
+      const double d_coll = mus > 0.0 ? tau / mus : INFINITY;
+      const int collide = d_coll < d_face;
+      const double l = collide ? d_coll : d_face;
+      const double t = mua > 0.0 ? -W * expm1(-mua * l) / mua : W * l;
+      if (t != 0.0) orc3_deposit(j, v, t, ux, uy, uz);
+      j->st.segments++;
+      const double W_next = W * exp(-mua * l);
+      j->st.absorbed_w += W - W_next;
+      W = W_next;
+      x += l * ux;
+      y += l * uy;
+      z += l * uz;
+      if (collide) break;
+      tau -= mus * l;
+      if (axis == 0) {
+        if (ux > 0.0) {
+          ++ix;
+          x = ix * dx;
+        } else {
+          x = ix * dx;
+          --ix;
+        }
+      } else if (axis == 1) {
+        if (uy > 0.0) {
+          ++iy;
+          y = iy * dx;
+        } else {
+          y = iy * dx;
+          --iy;
+        }
+      } else {
+        if (uz > 0.0) {
+          ++iz;
+          z = iz * dx;
+        } else {
+          z = iz * dx;
+          --iz;
+        }
+      }
+      if (ix < 0 || ix >= nx || iy < 0 || iy >= ny || iz < 0 || iz >= nz) {
+        escaped = 1;
+        break;
+      }
+    }
+    if (escaped) {
+      j->st.escapes++;
+      j->st.escaped_w += W;
+      break;
+    }
+    j->st.collisions++;
+    if (n_scatter >= r->max_scatter) {
+      j->st.scatter_limit++;
+      j->st.killed_w += W;
+      break;
+    }
+    orc3_turn(&ux, &uy, &uz, orc3_hg_cos(m->g, orc_u01(b[1])), 2.0 * M_PI * orc_u01(b[3]));
+    ++n_scatter;
+    if (fabs(W) < r->w_threshold * fabs(W0)) {
+      const double pr = (double)r->roulette_p;
+      if (orc_u01(b[2]) < pr) {
+        const double Wn = W / pr;
+        j->st.rr_survive++;
+        j->st.rr_net_w += Wn - W;
+        W = Wn;
+      } else {
+        j->st.rr_kill++;
+        j->st.rr_net_w -= W;
+        break;
+      }
+    }
+  }
+}
+
+static void *orc3_worker(void *arg) {
+  orc3_job *j = (orc3_job *)arg;
+  for (uint64_t p = j->p_begin; p < j->p_end; ++p) {
+    orc3_packet(j, p);
+    if (j->sq) {
+      for (int64_t k = 0; k < j->n_touched; ++k) {
+        const int64_t v = j->touched[k];
+        j->sq[v] += j->pk[v] * j->pk[v];
+        j->pk[v] = 0.0;
+      }
+      j->n_touched = 0;
+    }
+  }
+  return NULL;
+}
+
+static int orc3_check(const orc3_medium *m, const orc_run *r) {
+  if (!m || !r || !m->mua || !m->mus) return ORC_ERR_ARG;
+  if (m->nx <= 0 || m->ny <= 0 || m->nz <= 0 || !(m->dx > 0.0)) return ORC_ERR_ARG;
+  if (!(m->g > -1.0 && m->g < 1.0)) return ORC_ERR_ARG;
+  if (r->K < 0 || r->K > ORC3_MAX_L || r->n_threads <= 0 || r->sectors) return ORC_ERR_ARG;
+  if (!(r->roulette_p > 0.0f && r->roulette_p <= 1.0f)) return ORC_ERR_ARG;
+  const int64_t nvox = (int64_t)m->nx * m->ny * m->nz;
+  for (int64_t i = 0; i < nvox; ++i)
+    if (!(m->mua[i] >= 0.0) || !(m->mus[i] >= 0.0)) return ORC_ERR_ARG;
+  return ORC_OK;
+}
+
+/* Packets [first, first + n) in equal contiguous ranges over threads; ADDS raw
+ * sums to tally ([(L+1)^2][nz][ny][nx]) and sq ([nz][ny][nx] or NULL), thread
+ * tallies summed in thread order. */
+static int orc3_run_packets(const orc3_medium *m, const orc3_source *s, const orc_volsrc *vol, const orc_run *r,
+                            int adjoint, double *tally, double *sq, orc_stats *st) {
+  const int64_t nvox = (int64_t)m->nx * m->ny * m->nz;
+  const int64_t C = (int64_t)(r->K + 1) * (r->K + 1);
+  const int nt = r->n_threads;
+  orc3_job *jobs = (orc3_job *)calloc((size_t)nt, sizeof(orc3_job));
+  pthread_t *th = (pthread_t *)calloc((size_t)nt, sizeof(pthread_t));
+  if (!jobs || !th) {
+    free(jobs);
+    free(th);
+    return ORC_ERR_NOMEM;
+  }
+  int rc = ORC_OK;
+  for (int k = 0; k < nt; ++k) {
+    orc3_job *j = &jobs[k];
+    j->med = m;
+    j->src = s;
+    j->vol = vol;
+    j->run = r;
+    j->adjoint = adjoint;
+    j->p_begin = r->first_packet + r->n_packets * (uint64_t)k / (uint64_t)nt;
+    j->p_end = r->first_packet + r->n_packets * (uint64_t)(k + 1) / (uint64_t)nt;
+    j->tally = (double *)calloc((size_t)(C * nvox), sizeof(double));
+    if (!j->tally) rc = ORC_ERR_NOMEM;
+    if (sq) {
+      j->sq = (double *)calloc((size_t)nvox, sizeof(double));
+      j->pk = (double *)calloc((size_t)nvox, sizeof(double));
+      j->touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)nvox);
+      if (!j->sq || !j->pk || !j->touched) rc = ORC_ERR_NOMEM;
+    }
+  }
+  if (rc == ORC_OK) {
+    for (int k = 0; k < nt; ++k) pthread_create(&th[k], NULL, orc3_worker, &jobs[k]);
+    for (int k = 0; k < nt; ++k) pthread_join(th[k], NULL);
+    memset(st, 0, sizeof(*st));
+    for (int k = 0; k < nt; ++k) {
+      orc3_job *j = &jobs[k];
+      for (int64_t i = 0; i < C * nvox; ++i) tally[i] += j->tally[i];
+      if (sq)
+        for (int64_t i = 0; i < nvox; ++i) sq[i] += j->sq[i];
+      st->launched += j->st.launched;
+      st->flights += j->st.flights;
+      st->collisions += j->st.collisions;
+      st->segments += j->st.segments;
+      st->escapes += j->st.escapes;
+      st->rr_kill += j->st.rr_kill;
+      st->rr_survive += j->st.rr_survive;
+      st->scatter_limit += j->st.scatter_limit;
+      st->event_limit += j->st.event_limit;
+      st->launched_w += j->st.launched_w;
+      st->escaped_w += j->st.escaped_w;
+      st->rr_net_w += j->st.rr_net_w;
+      st->absorbed_w += j->st.absorbed_w;
+      st->killed_w += j->st.killed_w;
+    }
+  }
+  for (int k = 0; k < nt; ++k) {
+    free(jobs[k].tally);
+    free(jobs[k].sq);
+    free(jobs[k].pk);
+    free(jobs[k].touched);
+  }
+  free(jobs);
+  free(th);
+  return rc;
+}
+
+/* 3D forward run from a pencil or isotropic point source.  Adds raw sums. */
+int orc3_forward_raw(const orc3_medium *m, const orc3_source *s, const orc_run *r, double *tally, double *sq,
+                     orc_stats *st) {
+  int rc = orc3_check(m, r);
+  if (rc) return rc;
+  if (!s || !tally || !st || (s->kind != ORC_PENCIL && s->kind != ORC_ISO_POINT)) return ORC_ERR_ARG;
+  return orc3_run_packets(m, s, NULL, r, 0, tally, sq, st);
+}
+
+/* 3D run from the signed volumetric isotropic source q ([nz][ny][nx], per unit
+ * volume and unit solid angle); S = 4 pi dx^3 qmax total / 2^32.  adjoint = 1
+ * tallies at -s. */
+int orc3_volume_raw(const orc3_medium *m, const float *q, const orc_run *r, int adjoint, double *tally, double *sq,
+                    orc_stats *st, double *source_strength) {
+  int rc = orc3_check(m, r);
+  if (rc) return rc;
+  if (!q || !tally || !st || !source_strength) return ORC_ERR_ARG;
+  const int64_t nvox = (int64_t)m->nx * m->ny * m->nz;
+  orc_volsrc vs;
+  rc = orc_volsrc_build(&vs, q, nvox);
+  if (rc) return rc;
+  *source_strength = 4.0 * M_PI * m->dx * m->dx * m->dx * vs.qmax * (double)vs.total / 4294967296.0;
+  if (vs.total == 0) {
+    memset(st, 0, sizeof(*st));
+    free(vs.cdf);
+    return ORC_OK;
+  }
+  rc = orc3_run_packets(m, NULL, &vs, r, adjoint ? 1 : 0, tally, sq, st);
+  free(vs.cdf);
+  return rc;
+}
