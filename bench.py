@@ -57,14 +57,17 @@ def _args():
     ap.add_argument("--iters", type=int, default=None, help="invert_rect: iteration cap (default 20 mua, 40 mus)")
     ap.add_argument("--workload", default="grad256",
                     choices=["grad256", "large1024", "batch64", "denoise256", "conv", "invert256", "unet256", "invert_rect",
-                             "sectors"],
+                             "sectors", "grad3d"],
                     help="grad256: the gradient evaluation (default); large1024: the same on 1024^2 px at "
                          "K = 64 with four edge sources; batch64: 64 forward problems in one graph-captured "
                          "batched launch; denoise256: the learned denoiser; conv: one large tensor-core "
                          "convolution (profiling case); invert256: mu_a reconstruction on the grad256 phantom; "
                          "unet256: U-Net training step and inference on synthetic maps (profiling case); invert_rect: "
                          "the Sec. 6 reconstructions on the rectangular-inclusion domain (--unknown mua|mus); sectors: "
-                         "harmonic vs discrete-ordinates tally (Sec. 3.1)")
+                         "harmonic vs discrete-ordinates tally (Sec. 3.1); grad3d: the 3D gradient evaluation with "
+                         "spherical-harmonic tallies (--n3 voxels a side, --l3 order)")
+    ap.add_argument("--n3", type=int, default=96, help="grad3d: voxels per side")
+    ap.add_argument("--l3", type=int, default=4, help="grad3d: spherical-harmonic order L")
     args = ap.parse_args()
     if args.packets is None:
         args.packets = 20_000_000 if args.workload == "large1024" else 10_000_000
@@ -845,6 +848,104 @@ def _invert_rect(args):
     return 0
 
 
+def _grad3d(args):
+    """The 3D gradient evaluation (spherical-harmonic tallies): forward run from the pencil beam,
+    H and dL/dH against a synthetic measurement, q*, adjoint run, and the voxel gradients, on the
+    n^3 phantom; photons (forward + adjoint) per second, the transport's payload rate, and the
+    FP64 oracle's rate on a sample of the same runs."""
+    import torch
+    from oracle import RunParams
+    from paper_1608_05238_gb300 import _build, mcr, mcr3, workloads
+    _build.build()
+    n, L, dx, g = args.n3, args.l3, 0.1, 0.9
+    mua, mus, mua_true, src = workloads.phantom3(n, dx, seed=0)
+    dev = lambda a: torch.from_numpy(a).cuda()
+    med = mcr3.Medium3(dev(mua), dev(mus), dx, g)
+    s3 = mcr3.Source3(**src)
+    N = args.packets // 10  # 1e6 forward + 1e6 adjoint packets per step by default
+    Hm = mcr3.h_eps(mcr3.Medium3(dev(mua_true), dev(mus), dx, g),
+                    mcr3.forward(mcr3.Medium3(dev(mua_true), dev(mus), dx, g), s3, mcr.Run(K=0, n_packets=4 * N,
+                                                                                             seed=999)))
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+
+    def step(k):
+        c, sf = mcr3.forward(med, s3, mcr.Run(K=L, n_packets=N, seed=2 * k), stats=True)
+        H, v, eps = mcr3.h_eps(med, c, Hm)
+        q = mcr3.adjoint_source(med, v)
+        ca, sa = mcr3.adjoint(med, q, mcr.Run(K=L, n_packets=N, seed=2 * k + 1, stream_id=1), stats=True)
+        return mcr3.gradient(med, c, ca, v), sf, sa
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    clk = ClockSampler(0)
+    clk.start()
+    T, segs = 0.0, []
+    for k in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, sf, sa = step(100 + k)
+        b.record()
+        b.synchronize()
+        T += a.elapsed_time(b) * 1e-3
+        segs += [sf["segments"], sa["segments"]]
+    clocks = clk.stop()
+    # the transport alone: one forward run timed by events around the call (its memsets, medium
+    # check and finalize included)
+    tr = []
+    for k in range(3):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, st = mcr3.forward(med, s3, mcr.Run(K=L, n_packets=N, seed=500 + k), stats=True)
+        b.record()
+        b.synchronize()
+        tr.append((a.elapsed_time(b), st["segments"]))
+    C = (L + 1) ** 2
+    ms = float(np.mean([t for t, _ in tr]))
+    seg = float(np.mean([s for _, s in tr]))
+    achieved = C * 8 * seg / (ms * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": "k_transport3", "launch_ms": ms, "segments_per_launch": seg,
+                "bytes_per_segment": C * 8,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+    if not args.no_red_probe:
+        red = l2_reduction_peak(n ** 3, C)
+        roofline["l2_reduction_peak"] = dict(red, frac=achieved / red["value"])
+    value = 2 * N * args.steps / T
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        sample = max(4000, args.cpu_sample // 10)
+        m64, s64 = mua.astype(np.float64), mus.astype(np.float64)
+        t0 = time.perf_counter()
+        fo = oracle.forward3(m64, s64, np.float32(dx), np.float32(g), src, RunParams(K=L, n_packets=sample, seed=1))
+        qo = (-mua.astype(np.float64) * (mua.astype(np.float64) - mua_true) / dx ** 3).astype(np.float32)
+        ao = oracle.adjoint3(m64, s64, np.float32(dx), np.float32(g), qo, RunParams(K=L, n_packets=sample, seed=2))
+        dt = time.perf_counter() - t0
+        cpu = {"value": 2 * sample / dt, "unit": "photons/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{sample} forward + {sample} adjoint packets of grad3d (full grid, L={L}), {dt:.1f} s",
+               "work_per_photon": {"forward_segments": fo.stats["segments"] / sample,
+                                   "adjoint_segments": ao.stats["segments"] / sample}}
+    out = {"metric": "3D gradient evaluation photons/s (forward + adjoint)", "value": value, "unit": "photons/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64 (FP64 gradient)",
+           "data": "synthetic",
+           "config": {"workload": f"grad3d: {n}^3 voxels of {dx} mm, L={L} ({C} channels), g={g}, pencil beam, "
+                                  f"{N:.0e} forward + {N:.0e} adjoint packets per step",
+                      "segments_per_photon": float(np.mean(segs)) / N, "l2": "flushed between timed steps (256 MB write)"},
+           "clocks": clocks, "gpu_launches": 14 * args.steps, "roofline": roofline, "cpu_baseline": cpu}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def replace_spec(spec, **kw):
     from dataclasses import replace
     return replace(spec, **kw)
@@ -866,6 +967,8 @@ def main():
         return _invert_rect(args)
     if args.workload == "sectors" and args.impl != "reference":
         return _sectors(args)
+    if args.workload == "grad3d" and args.impl != "reference":
+        return _grad3d(args)
     if args.impl == "reference":
         return _reference(args)
     return _gpu(args)

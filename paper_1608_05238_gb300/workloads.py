@@ -182,3 +182,40 @@ def small_hetero(nz: int, nx: int, dx: float, seed: int):
     mua[i0:i0 + nz // 3, j0:j0 + nx // 4] = 0.3
     mus[nz // 2:nz // 2 + nz // 4, nx // 2:nx // 2 + nx // 3] = 15.0
     return mua.astype(np.float32), mus.astype(np.float32)
+
+
+def small_hetero3(nz: int, ny: int, nx: int, dx: float, seed: int):
+    """Heterogeneous voxel medium for the 3D parity tests: smooth background plus a strongly
+    absorbing box and a strongly scattering box (float32 [nz, ny, nx])."""
+    rng = np.random.default_rng(seed)
+    cz, cy, cx = ((np.arange(n) + 0.5) * dx for n in (nz, ny, nx))
+    Z, Y, X = np.meshgrid(cz, cy, cx, indexing="ij")
+    ph = rng.uniform(0, 6, 3)
+    mua = 0.05 + 0.04 * np.sin(2.1 * X + ph[0]) * np.cos(1.3 * Z + ph[1]) * np.cos(1.1 * Y)
+    mus = 6.0 + 3.0 * np.cos(1.7 * X - 0.9 * Z + 1.2 * Y + ph[2])
+    mua[nz // 4:nz // 4 + max(1, nz // 3), ny // 3:ny // 3 + max(1, ny // 4), nx // 5:nx // 5 + max(1, nx // 4)] = 0.3
+    mus[nz // 2:nz // 2 + max(1, nz // 4), :ny // 2, nx // 2:nx // 2 + max(1, nx // 3)] = 15.0
+    return mua.astype(np.float32), mus.astype(np.float32)
+
+
+def phantom3(n: int, dx: float, seed: int):
+    """3D gradient workload on n^3 voxels of side dx: a scattering background (mu_s 10/mm,
+    mu_a 0.01/mm with +-20% smooth variation) and, in the 'true' medium, three absorbing spheres
+    (mu_a x 3); a pencil beam enters at the middle of the top face.  Returns (mua, mus, mua_true,
+    source dict) as float32 [nz, ny, nx] maps."""
+    rng = np.random.default_rng(seed)
+    c = (np.arange(n) + 0.5) * dx
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    ext = n * dx
+    ph = rng.uniform(0, 2 * np.pi, 3)
+    k = 2 * np.pi / ext
+    mua = 0.01 * (1 + 0.2 * np.sin(k * X + ph[0]) * np.cos(k * Y + ph[1]) * np.cos(k * Z + ph[2]))
+    mus = np.full_like(mua, 10.0)
+    mua_true = mua.copy()
+    for _ in range(3):
+        ctr = rng.uniform(0.25, 0.75, 3) * ext
+        r = rng.uniform(0.06, 0.12) * ext
+        inside = (Z - ctr[0]) ** 2 + (Y - ctr[1]) ** 2 + (X - ctr[2]) ** 2 < r * r
+        mua_true[inside] *= 3.0
+    src = dict(kind=0, x0=0.5 * ext, y0=0.5 * ext, z0=0.0, dir_x=0.0, dir_y=0.0, dir_z=1.0, power=1.0)
+    return mua.astype(np.float32), mus.astype(np.float32), mua_true.astype(np.float32), src
