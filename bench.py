@@ -238,14 +238,15 @@ def _reference(args):
 
 
 # ------------------------------------------------------------------------------- GPU leg
-def l2_reduction_peak(rows, n_coeff, blocks=152 * 8, threads=256, iters=20000, reps=3):
+def l2_reduction_peak(rows, n_coeff, blocks=152 * 8, threads=256, iters=20000, reps=3, row_words=None):
     """Measured ceiling of the tally reductions (mc_reduction_probe): warps adding 1 to the first
     n_coeff 64-bit words of pseudo-random rows of a tally of this workload's shape, in the
     deposit's coalesced pattern, with no transport work.  Returns the best payload rate of
     ``reps`` event-timed runs (GB/s of 8-byte reductions) and checks the tally's total."""
     import torch
     from paper_1608_05238_gb300 import mcr
-    row_words = (n_coeff + 15) // 16 * 16 if n_coeff > 32 else (n_coeff + 3) // 4 * 4
+    if row_words is None:
+        row_words = (n_coeff + 15) // 16 * 16 if n_coeff > 32 else (n_coeff + 3) // 4 * 4
     tally = torch.zeros(rows, row_words, dtype=torch.int64, device="cuda")
     mcr.reduction_probe(tally, n_coeff, 100, blocks, threads)  # warm-up
     best = 0.0
@@ -917,7 +918,7 @@ def _grad3d(args):
                 "bytes_per_segment": C * 8,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
     if not args.no_red_probe:
-        red = l2_reduction_peak(n ** 3, C)
+        red = l2_reduction_peak(n ** 3, C, row_words=(C + 15) // 16 * 16 if C > 16 else (C + 3) // 4 * 4)
         roofline["l2_reduction_peak"] = dict(red, frac=achieved / red["value"])
     value = 2 * N * args.steps / T
     cpu = None

@@ -26,7 +26,7 @@ struct Transport3Params {
   int nx, ny, nz;
   float dx, g;
   int L, C, Cpad, row_stride;
-  const float *mua, *mus;
+  const float4 *mu;  // packed (mu_a, mu_s, 1/mu_a, 1/mu_s) per voxel
   unsigned long long *tally;
   const unsigned long long *cdf;  // volumetric source: inclusive prefix of quantised |q|
   const float *q;
@@ -37,6 +37,7 @@ struct Transport3Params {
   unsigned max_scatter, max_events;
   float w_threshold, rr_p, rr_inv_p, qscale;
   float nlm[kMaxC3];  // N_lm (times sqrt 2 for m != 0) at index l^2 + l + |m|
+  float rinv[MCR3_MAX_L + 1];  // 1 / k
   unsigned long long *work;
   DevStats *stats;
   unsigned *flags;
@@ -57,7 +58,7 @@ __device__ __forceinline__ void sh_row(const Transport3Params &p, float ux, floa
       else if (l == m + 1)
         ql = (2.f * m + 1.f) * uz * qmm;
       else
-        ql = ((2.f * l - 1.f) * uz * q1 - (l + m - 1.f) * q2) / (float)(l - m);
+        ql = ((2.f * l - 1.f) * uz * q1 - (l + m - 1.f) * q2) * p.rinv[l - m];
       if (l > m) {
         q2 = q1;
         q1 = ql;
@@ -129,7 +130,7 @@ __device__ __forceinline__ T wsum(T v) {
 }
 
 template <int NCH>
-__global__ void __launch_bounds__(kThreads3) k_transport3(const __grid_constant__ Transport3Params p) {
+__global__ void __launch_bounds__(kThreads3, 8) k_transport3(const __grid_constant__ Transport3Params p) {
   extern __shared__ float rows3[];
   const int lane = threadIdx.x & 31;
   float *const myrow = rows3 + (size_t)threadIdx.x * p.row_stride;
@@ -141,11 +142,42 @@ __global__ void __launch_bounds__(kThreads3) k_transport3(const __grid_constant_
   bool alive = false, exhausted = false;
   unsigned long long pid = 0;
   float fx = 0.f, fy = 0.f, fz = 0.f, ux = 0.f, uy = 0.f, uz = 1.f, W = 0.f, W0 = 1.f, tau = 0.f;
+  float inv_ax = 0.f, inv_ay = 0.f, inv_az = 0.f;  // 1 / |u| per axis, set per flight
   int ix = 0, iy = 0, iz = 0;
   unsigned flight = 0, nscat = 0, cu1 = 0, cu2 = 0, cu3 = 0;
-  unsigned long long n_launch = 0, n_flight = 0, n_coll = 0, n_seg = 0, n_esc = 0, n_rrk = 0, n_rrs = 0, n_scl = 0,
-                     n_evl = 0;
+  // lane counters in 32 bits (segments bound all of them but the launches, which are < 2^26 per
+  // call); the warp flushes them into the 64-bit run totals before any lane's segments pass 2^30
+  unsigned n_launch = 0, n_flight = 0, n_coll = 0, n_seg = 0, n_esc = 0, n_rrk = 0, n_rrs = 0, n_scl = 0, n_evl = 0;
   double w_launch = 0.0, w_esc = 0.0, w_rr = 0.0, w_kill = 0.0;
+  auto flush_counts = [&]() {
+    DevStats *s = p.stats;
+    unsigned long long evl = 0;
+    auto put = [&](unsigned long long *dst, unsigned &v) {
+      const unsigned long long t = wsum((unsigned long long)v);
+      if (lane == 0 && t) atomicAdd(dst, t);
+      v = 0;
+      return t;
+    };
+    auto putw = [&](double *dst, double &v) {
+      const double t = wsum(v);
+      if (lane == 0) atomicAdd(dst, t);
+      v = 0.0;
+    };
+    put(&s->launched, n_launch);
+    put(&s->flights, n_flight);
+    put(&s->collisions, n_coll);
+    put(&s->segments, n_seg);
+    put(&s->escapes, n_esc);
+    put(&s->rr_kill, n_rrk);
+    put(&s->rr_survive, n_rrs);
+    put(&s->scatter_limit, n_scl);
+    evl = put(&s->event_limit, n_evl);
+    putw(&s->launched_w, w_launch);
+    putw(&s->escaped_w, w_esc);
+    putw(&s->rr_net_w, w_rr);
+    putw(&s->killed_w, w_kill);
+    if (lane == 0 && evl) atomicOr(p.flags, kFlagEventLimit);
+  };
 
   // a new free flight (event flight + 1): tau = -ln U, the scattering uniforms, and the harmonics
   // of the direction; false when the event cap ends the packet first
@@ -162,6 +194,9 @@ __global__ void __launch_bounds__(kThreads3) k_transport3(const __grid_constant_
     cu1 = r.y;
     cu2 = r.z;
     cu3 = r.w;
+    inv_ax = __frcp_rn(fabsf(ux));
+    inv_ay = __frcp_rn(fabsf(uy));
+    inv_az = __frcp_rn(fabsf(uz));
     sh_row(p, ux, uy, uz, myrow);
     return true;
   };
@@ -253,10 +288,10 @@ __global__ void __launch_bounds__(kThreads3) k_transport3(const __grid_constant_
     bool collided = false, escaped = false;
     if (alive) {
       const int v = (iz * p.ny + iy) * p.nx + ix;
-      const float mua = __ldg(p.mua + v), mus = __ldg(p.mus + v);
-      const float dxf = ux > 0.f ? (dx - fx) / ux : (ux < 0.f ? fx / -ux : CUDART_INF_F);
-      const float dyf = uy > 0.f ? (dx - fy) / uy : (uy < 0.f ? fy / -uy : CUDART_INF_F);
-      const float dzf = uz > 0.f ? (dx - fz) / uz : (uz < 0.f ? fz / -uz : CUDART_INF_F);
+      const float4 m = __ldg(p.mu + v);
+      const float dxf = ux != 0.f ? (ux > 0.f ? dx - fx : fx) * inv_ax : CUDART_INF_F;
+      const float dyf = uy != 0.f ? (uy > 0.f ? dx - fy : fy) * inv_ay : CUDART_INF_F;
+      const float dzf = uz != 0.f ? (uz > 0.f ? dx - fz : fz) * inv_az : CUDART_INF_F;
       int axis = 0;  // ties: x first, then y, then z
       float d_face = dxf;
       if (dyf < d_face) {
@@ -268,11 +303,11 @@ __global__ void __launch_bounds__(kThreads3) k_transport3(const __grid_constant_
         axis = 2;
       }
       d_face = fmaxf(d_face, 0.f);
-      const float d_coll = mus > 0.f ? tau / mus : CUDART_INF_F;
+      const float d_coll = tau * m.w;  // +inf when mu_s = 0
       collided = d_coll < d_face;
       const float l = collided ? d_coll : d_face;
-      const float em1 = expm1f(-mua * l);
-      const float t = mua > 0.f ? -W * em1 / mua : W * l;
+      const float em1 = expm1f(-m.x * l);
+      const float t = m.x > 0.f ? (-W * em1) * m.z : W * l;
       W = fmaf(W, em1, W);
       ++n_seg;
       if (t != 0.f) {
@@ -284,7 +319,7 @@ __global__ void __launch_bounds__(kThreads3) k_transport3(const __grid_constant_
         fy = clamp3(fmaf(l, uy, fy), dx);
         fz = clamp3(fmaf(l, uz, fz), dx);
       } else {
-        tau = fmaxf(fmaf(-mus, l, tau), 0.f);
+        tau = fmaxf(fmaf(-m.y, l, tau), 0.f);
         if (axis == 0) {
           if (ux > 0.f) {
             ++ix;
@@ -368,47 +403,9 @@ __global__ void __launch_bounds__(kThreads3) k_transport3(const __grid_constant_
         }
       }
     }
-    __syncwarp();
+    if (__any_sync(kFull3, n_seg > (1u << 30))) flush_counts();
   }
-  // ------------------------------------------------------------- counters
-  n_launch = wsum(n_launch);
-  n_flight = wsum(n_flight);
-  n_coll = wsum(n_coll);
-  n_seg = wsum(n_seg);
-  n_esc = wsum(n_esc);
-  n_rrk = wsum(n_rrk);
-  n_rrs = wsum(n_rrs);
-  n_scl = wsum(n_scl);
-  n_evl = wsum(n_evl);
-  w_launch = wsum(w_launch);
-  w_esc = wsum(w_esc);
-  w_rr = wsum(w_rr);
-  w_kill = wsum(w_kill);
-  if (lane == 0) {
-    DevStats *s = p.stats;
-    atomicAdd(&s->launched, n_launch);
-    atomicAdd(&s->flights, n_flight);
-    atomicAdd(&s->collisions, n_coll);
-    atomicAdd(&s->segments, n_seg);
-    atomicAdd(&s->escapes, n_esc);
-    atomicAdd(&s->rr_kill, n_rrk);
-    atomicAdd(&s->rr_survive, n_rrs);
-    atomicAdd(&s->scatter_limit, n_scl);
-    atomicAdd(&s->event_limit, n_evl);
-    atomicAdd(&s->launched_w, w_launch);
-    atomicAdd(&s->escaped_w, w_esc);
-    atomicAdd(&s->rr_net_w, w_rr);
-    atomicAdd(&s->killed_w, w_kill);
-    if (n_evl) atomicOr(p.flags, kFlagEventLimit);
-  }
-}
-
-// medium check: any mu < 0 or NaN sets kFlagMedium
-__global__ void k_check3(const float *mua, const float *mus, int64_t n, unsigned *flags) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float a = mua[i], b = mus[i];
-    if (!(a >= 0.f) || !(b >= 0.f) || !isfinite(a) || !isfinite(b)) atomicOr(flags, kFlagMedium);
-  }
+  flush_counts();
 }
 
 // coeff[c][v] (+)= sum * quantum * scale, (-1)^l on odd l when adjoint; scale = fixed_scale or, for
@@ -493,11 +490,18 @@ struct Work3 {
   size_t tally_bytes = 0;
   unsigned long long *cdf = nullptr, *block_sums = nullptr;
   size_t cdf_bytes = 0, bs_bytes = 0;
+  float4 *mu = nullptr;
+  size_t mu_bytes = 0;
   unsigned char *small = nullptr;  // [0,8) counter, [64,192) stats, [448] flags, [512] qmax bits
   double *partials = nullptr;
 };
 std::mutex g_mu3;
 Work3 g_w3[64];
+
+// Words per voxel row: above 16 channels whole 128-byte lines (each deposit then touches the
+// fewest lines; rows of 28 words for 25 channels reduced 30 % slower from HBM than rows of 32),
+// else a multiple of 4 (32-byte sectors).
+int tally_row_words3(int C) { return C > 16 ? (C + 15) & ~15 : (C + 3) & ~3; }
 
 int grow3(void **p, size_t *have, size_t need) {
   if (need <= *have) return MCR_OK;
@@ -521,6 +525,7 @@ int work3(size_t tally, size_t nvox, Work3 **out) {
   }
   if ((rc = grow3((void **)&w.tally, &w.tally_bytes, tally))) return rc;
   if ((rc = grow3((void **)&w.cdf, &w.cdf_bytes, nvox * 8))) return rc;
+  if ((rc = grow3((void **)&w.mu, &w.mu_bytes, nvox * sizeof(float4)))) return rc;
   if ((rc = grow3((void **)&w.block_sums, &w.bs_bytes, ((nvox + 255) / 256) * 8))) return rc;
   *out = &w;
   return MCR_OK;
@@ -567,7 +572,7 @@ int run3(const mcr3_medium *med, const mcr3_source *src, const float *qstar, con
   } else {
     p.kind = -1;
   }
-  const int L = run->K, C = (L + 1) * (L + 1), Cpad = tally_row_words(C);
+  const int L = run->K, C = (L + 1) * (L + 1), Cpad = tally_row_words3(C);
   const int64_t nvox = (int64_t)med->nx * med->ny * med->nz;
   std::lock_guard<std::mutex> lock(g_mu3);
   Work3 *w = nullptr;
@@ -578,8 +583,7 @@ int run3(const mcr3_medium *med, const mcr3_source *src, const float *qstar, con
   unsigned *qmax = reinterpret_cast<unsigned *>(w->small + 512);
   MCR3_TRY(cudaMemsetAsync(w->small, 0, 512, s));  // counter, stats, flags
   MCR3_TRY(cudaMemsetAsync(w->tally, 0, (size_t)nvox * Cpad * 8, s));
-  k_check3<<<256, 256, 0, s>>>(med->mua, med->mus, nvox, flags);
-  MCR3_TRY(cudaGetLastError());
+  MCR3_TRY(launch_pack_medium(med->mua, med->mus, w->mu, nvox, flags, s));
   if (qstar) MCR3_TRY(launch_source_cdf(qstar, nvox, w->cdf, w->block_sums, (size_t)((nvox + 255) / 256), qmax, s));
   p.nx = med->nx;
   p.ny = med->ny;
@@ -590,8 +594,7 @@ int run3(const mcr3_medium *med, const mcr3_source *src, const float *qstar, con
   p.C = C;
   p.Cpad = Cpad;
   p.row_stride = C | 1;  // odd: the lanes' rows fall in distinct banks
-  p.mua = med->mua;
-  p.mus = med->mus;
+  p.mu = w->mu;
   p.tally = w->tally;
   p.cdf = w->cdf;
   p.q = qstar;
@@ -611,6 +614,7 @@ int run3(const mcr3_medium *med, const mcr3_source *src, const float *qstar, con
   int qe = (int)floor(30.0 - log2(wmax * (double)med->dx * sqrt(3.0) * ymax * 1.001));
   qe = qe > 60 ? 60 : (qe < -60 ? -60 : qe);
   p.qscale = ldexpf(1.f, qe);
+  for (int k = 1; k <= MCR3_MAX_L; ++k) p.rinv[k] = 1.f / (float)k;
   for (int l = 0; l <= L; ++l)
     for (int m = 0; m <= l; ++m) {
       double ratio = 1.0;
