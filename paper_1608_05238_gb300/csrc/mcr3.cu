@@ -129,12 +129,20 @@ __device__ __forceinline__ T wsum(T v) {
   return v;
 }
 
-template <int NCH>
+// NCH: 32-lane passes per voxel row ((L+1)^2 <= 32 NCH).  MERGE: a collision segment of a packet
+// that survives the collision is deposited together with the next flight's first segment (the
+// same voxel), the two rows' products rounded separately and added as integers -- the tally is
+// bit-identical, with one warp pass instead of two; each lane then keeps two rows (the previous
+// flight's and the current one) in shared memory.
+template <int NCH, bool MERGE>
 __global__ void __launch_bounds__(kThreads3, 8) k_transport3(const __grid_constant__ Transport3Params p) {
   extern __shared__ float rows3[];
+  constexpr int kRows = MERGE ? 2 : 1;
   const int lane = threadIdx.x & 31;
-  float *const myrow = rows3 + (size_t)threadIdx.x * p.row_stride;
-  const float *const warprows = rows3 + (size_t)(threadIdx.x & ~31) * p.row_stride;
+  float *const myrows = rows3 + (size_t)threadIdx.x * kRows * p.row_stride;
+  const float *const warprows = rows3 + (size_t)(threadIdx.x & ~31) * kRows * p.row_stride;
+  int rb = 0;         // MERGE: which of the lane's two rows holds the current flight's harmonics
+  float carry = 0.f;  // MERGE: deferred collision segment (track weight x 2^q), previous row
   if (*p.flags & kFlagMedium) return;
   const int nvox = p.nx * p.ny * p.nz;
   const float dx = p.dx;
@@ -197,7 +205,8 @@ __global__ void __launch_bounds__(kThreads3, 8) k_transport3(const __grid_consta
     inv_ax = __frcp_rn(fabsf(ux));
     inv_ay = __frcp_rn(fabsf(uy));
     inv_az = __frcp_rn(fabsf(uz));
-    sh_row(p, ux, uy, uz, myrow);
+    if (MERGE) rb ^= 1;
+    sh_row(p, ux, uy, uz, myrows + rb * p.row_stride);
     return true;
   };
 
@@ -284,7 +293,7 @@ __global__ void __launch_bounds__(kThreads3, 8) k_transport3(const __grid_consta
 
     // ------------------------------------------------------------- one voxel segment
     int seg_v = -1;
-    float seg_ts = 0.f;
+    float seg_ts = 0.f, seg_carry = 0.f;
     bool collided = false, escaped = false;
     if (alive) {
       const int v = (iz * p.ny + iy) * p.nx + ix;
@@ -310,9 +319,23 @@ __global__ void __launch_bounds__(kThreads3, 8) k_transport3(const __grid_consta
       const float t = m.x > 0.f ? (-W * em1) * m.z : W * l;
       W = fmaf(W, em1, W);
       ++n_seg;
-      if (t != 0.f) {
+      if (MERGE) {
+        seg_carry = carry;
+        carry = 0.f;
+      }
+      if (t != 0.f || seg_carry != 0.f) {
         seg_v = v;
         seg_ts = t * p.qscale;
+      }
+      if (MERGE && collided && t != 0.f && seg_carry == 0.f) {
+        // defer it if the packet survives the collision (the tests below, in their order): its
+        // next segment starts in this voxel
+        const bool dies = nscat >= p.max_scatter ||
+                          (fabsf(W) < p.w_threshold * fabsf(W0) && !(u01(cu2) < p.rr_p)) || flight >= p.max_events;
+        if (!dies) {
+          carry = seg_ts;
+          seg_v = -1;
+        }
       }
       if (collided) {
         fx = clamp3(fmaf(l, ux, fx), dx);
@@ -363,11 +386,27 @@ __global__ void __launch_bounds__(kThreads3, 8) k_transport3(const __grid_consta
       const int v = __shfl_sync(kFull3, seg_v, L);
       const float ts = __shfl_sync(kFull3, seg_ts, L);
       unsigned long long *dst = p.tally + (size_t)v * p.Cpad;
-      const float *row = warprows + (size_t)L * p.row_stride;
+      if (MERGE) {
+        const float tc = __shfl_sync(kFull3, seg_carry, L);
+        const int rbl = __shfl_sync(kFull3, rb, L);
+        const float *row = warprows + (size_t)(2 * L + rbl) * p.row_stride;
+        const float *prev = warprows + (size_t)(2 * L + (rbl ^ 1)) * p.row_stride;
 #pragma unroll
-      for (int k = 0; k < NCH; ++k) {
-        const int j = k * 32 + lane;
-        if (j < p.C) atomicAdd(dst + j, (unsigned long long)(long long)__float2int_rn(ts * row[j]));
+        for (int k = 0; k < NCH; ++k) {
+          const int j = k * 32 + lane;
+          if (j < p.C) {
+            long long q = __float2int_rn(ts * row[j]);
+            if (tc != 0.f) q += __float2int_rn(tc * prev[j]);
+            atomicAdd(dst + j, (unsigned long long)q);
+          }
+        }
+      } else {
+        const float *row = warprows + (size_t)L * p.row_stride;
+#pragma unroll
+        for (int k = 0; k < NCH; ++k) {
+          const int j = k * 32 + lane;
+          if (j < p.C) atomicAdd(dst + j, (unsigned long long)(long long)__float2int_rn(ts * row[j]));
+        }
       }
     }
     __syncwarp();
@@ -629,17 +668,21 @@ int run3(const mcr3_medium *med, const mcr3_source *src, const float *qstar, con
     int dev = 0, sms = 0, per_sm = 0;
     MCR3_TRY(cudaGetDevice(&dev));
     MCR3_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const size_t smem = (size_t)kThreads3 * p.row_stride * sizeof(float);
     const int nch = (C + 31) / 32;
-    if (nch == 1) {
-      MCR3_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport3<1>, kThreads3, smem));
-      k_transport3<1><<<sms * (per_sm > 0 ? per_sm : 1), kThreads3, smem, s>>>(p);
+    const bool merge = p.row_stride <= 25;  // two rows per lane still leave 8 blocks per SM
+    const size_t smem = (size_t)kThreads3 * (merge ? 2 : 1) * p.row_stride * sizeof(float);
+    if (merge) {
+      MCR3_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport3<1, true>, kThreads3, smem));
+      k_transport3<1, true><<<sms * (per_sm > 0 ? per_sm : 1), kThreads3, smem, s>>>(p);
+    } else if (nch == 1) {
+      MCR3_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport3<1, false>, kThreads3, smem));
+      k_transport3<1, false><<<sms * (per_sm > 0 ? per_sm : 1), kThreads3, smem, s>>>(p);
     } else if (nch == 2) {
-      MCR3_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport3<2>, kThreads3, smem));
-      k_transport3<2><<<sms * (per_sm > 0 ? per_sm : 1), kThreads3, smem, s>>>(p);
+      MCR3_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport3<2, false>, kThreads3, smem));
+      k_transport3<2, false><<<sms * (per_sm > 0 ? per_sm : 1), kThreads3, smem, s>>>(p);
     } else {
-      MCR3_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport3<3>, kThreads3, smem));
-      k_transport3<3><<<sms * (per_sm > 0 ? per_sm : 1), kThreads3, smem, s>>>(p);
+      MCR3_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport3<3, false>, kThreads3, smem));
+      k_transport3<3, false><<<sms * (per_sm > 0 ? per_sm : 1), kThreads3, smem, s>>>(p);
     }
     MCR3_TRY(cudaGetLastError());
   }
