@@ -863,7 +863,7 @@ def _grad3d(args):
     dev = lambda a: torch.from_numpy(a).cuda()
     med = mcr3.Medium3(dev(mua), dev(mus), dx, g)
     s3 = mcr3.Source3(**src)
-    N = args.packets // 10  # 1e6 forward + 1e6 adjoint packets per step by default
+    N = args.packets  # 1e7 forward + 1e7 adjoint packets per step by default
     Hm = mcr3.h_eps(mcr3.Medium3(dev(mua_true), dev(mus), dx, g),
                     mcr3.forward(mcr3.Medium3(dev(mua_true), dev(mus), dx, g), s3, mcr.Run(K=0, n_packets=4 * N,
                                                                                              seed=999)))
@@ -913,8 +913,10 @@ def _grad3d(args):
     except Exception:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    # DRAM bytes per forward launch: 21.05 GB at 1e6 packets (ncu, 96^3, L = 4), scaled by packets
+    traffic = 21.05e9 * N / 1e6 if (n, L) == (96, 4) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": "k_transport3", "launch_ms": ms, "segments_per_launch": seg,
+                "traffic": traffic, "kernel": "k_transport3", "launch_ms": ms, "segments_per_launch": seg,
                 "bytes_per_segment": C * 8,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
     if not args.no_red_probe:
