@@ -201,8 +201,9 @@ def small_hetero3(nz: int, ny: int, nx: int, dx: float, seed: int):
 def phantom3(n: int, dx: float, seed: int):
     """3D gradient workload on n^3 voxels of side dx: a scattering background (mu_s 10/mm,
     mu_a 0.01/mm with +-20% smooth variation) and, in the 'true' medium, three absorbing spheres
-    (mu_a x 3); a pencil beam enters at the middle of the top face.  Returns (mua, mus, mua_true,
-    source dict) as float32 [nz, ny, nx] maps."""
+    (mu_a x 3); a pencil beam enters the top face at the centre of its middle voxel (not on a voxel
+    face, where FP32 and FP64 would start it in different voxels).  Returns (mua, mus, mua_true,
+    source dict), the maps float32 [nz, ny, nx]."""
     rng = np.random.default_rng(seed)
     c = (np.arange(n) + 0.5) * dx
     Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
@@ -217,5 +218,6 @@ def phantom3(n: int, dx: float, seed: int):
         r = rng.uniform(0.06, 0.12) * ext
         inside = (Z - ctr[0]) ** 2 + (Y - ctr[1]) ** 2 + (X - ctr[2]) ** 2 < r * r
         mua_true[inside] *= 3.0
-    src = dict(kind=0, x0=0.5 * ext, y0=0.5 * ext, z0=0.0, dir_x=0.0, dir_y=0.0, dir_z=1.0, power=1.0)
+    xc = float(np.float32((n // 2 + 0.5) * dx))
+    src = dict(kind=0, x0=xc, y0=xc, z0=0.0, dir_x=0.0, dir_y=0.0, dir_z=1.0, power=1.0)
     return mua.astype(np.float32), mus.astype(np.float32), mua_true.astype(np.float32), src

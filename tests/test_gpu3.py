@@ -214,7 +214,7 @@ def test_gradient3_through_the_gpu_path_matches_the_oracle_gradient():
     mus = (3.0 + 1.0 * np.cos(4 * X + Z - Y)).astype(np.float32)
     Hm = (mua * 1.3).astype(np.float32)
     g, L = f32(0.8), 4
-    src = dict(kind=mcr.PENCIL, x0=f32(0.3), y0=f32(0.27), z0=0.0, dir_x=0.0, dir_y=0.0, dir_z=1.0, power=1.0)
+    src = dict(kind=mcr.PENCIL, x0=f32(0.33), y0=f32(0.27), z0=0.0, dir_x=0.0, dir_y=0.0, dir_z=1.0, power=1.0)
     fwd = mcr.Run(K=L, n_packets=300_000, seed=3)
     adj = mcr.Run(K=L, n_packets=300_000, seed=1003, stream_id=1)
     med = mcr3.Medium3(_dev(mua), _dev(mus), dx, g)
@@ -233,3 +233,49 @@ def test_gradient3_through_the_gpu_path_matches_the_oracle_gradient():
         scale = np.abs(want).max()
         assert np.abs(got - want).max() <= 5e-3 * scale
         assert np.abs(got - want).sum() <= 1e-3 * np.abs(want).sum()
+
+
+def test_grad3d_full_size_sample_and_full_run_properties():
+    """The 96^3, L = 4 workload of the 3D benchmark on its full grid: packets 4,950,000 ..
+    5,049,999 of a forward and an adjoint run against the oracle (1e5 packets, so that one packet
+    whose FP32 and FP64 paths part stays well inside the 1e-4 relative L1 bound), and a
+    1e7-packet forward run that is bit reproducible and whose two halves accumulate to it."""
+    mua, mus, mua_true, src = workloads.phantom3(96, 0.1, seed=0)
+    dx, g, L = f32(0.1), f32(0.9), 4
+    med = mcr3.Medium3(_dev(mua), _dev(mus), dx, g)
+    s3 = mcr3.Source3(**src)
+    first, n = 4_950_000, 100_000
+    run = mcr.Run(K=L, n_packets=n, first_packet=first, seed=77)
+    G = mcr3.forward(med, s3, run).double().cpu().numpy()
+    m64, s64 = mua.astype(np.float64), mus.astype(np.float64)
+    rp = RunParams(K=L, n_packets=n, first_packet=first, seed=77, n_threads=8)
+    O = oracle.forward3(m64, s64, dx, g, src, rp, with_variance=True)
+    s = math.sqrt(2 * L + 1)
+    # grazing segments (along a face or through an edge) that the FP32 and FP64 paths cut
+    # differently: voxels only the GPU enters are held to a share of the total, and visited ones
+    # get an allowance of 1e-3 of one packet's chord (a full chord adds dx / (N_p dx^3) to c_00)
+    chord = s * dx / (n * dx ** 3)
+    assert_parity(G, O.coeff, s * O.coeff[0], s * np.sqrt(O.a0_var), label="grad3d forward sample",
+                  unvisited_share=1e-5, floor=1e-3 * chord)
+    # the adjoint source of this workload, from a 1e6-packet forward estimate against H of the true medium
+    Hm = mcr3.h_eps(mcr3.Medium3(_dev(mua_true), _dev(mus), dx, g),
+                    mcr3.forward(mcr3.Medium3(_dev(mua_true), _dev(mus), dx, g), s3, mcr.Run(K=0, n_packets=1_000_000,
+                                                                                             seed=999)))
+    c = mcr3.forward(med, s3, mcr.Run(K=L, n_packets=1_000_000, seed=5))
+    _, v, _ = mcr3.h_eps(med, c, Hm)
+    q = mcr3.adjoint_source(med, v)
+    arun = mcr.Run(K=L, n_packets=n, first_packet=first, seed=78, stream_id=1)
+    Ga = mcr3.adjoint(med, q, arun).double().cpu().numpy()
+    qn = q.cpu().numpy()
+    rpa = RunParams(K=L, n_packets=n, first_packet=first, seed=78, stream_id=1, n_threads=8)
+    Oa = oracle.adjoint3(m64, s64, dx, g, qn, rpa)
+    Oabs = oracle.volume3(m64, s64, dx, g, np.abs(qn), rpa, adjoint=False, with_variance=True)
+    assert_parity(Ga, Oa.coeff, s * Oabs.coeff[0], s * np.sqrt(Oabs.a0_var), label="grad3d adjoint sample",
+                  unvisited_share=1e-5, floor=1e-3 * chord * Oabs.source_strength)
+    # the full forward run: reproducible, and its halves add up
+    N = 10_000_000
+    full = mcr3.forward(med, s3, mcr.Run(K=L, n_packets=N, seed=9))
+    assert torch.equal(full, mcr3.forward(med, s3, mcr.Run(K=L, n_packets=N, seed=9)))
+    acc = mcr3.forward(med, s3, mcr.Run(K=L, n_packets=N // 2, seed=9))
+    mcr3.forward(med, s3, mcr.Run(K=L, n_packets=N // 2, first_packet=N // 2, seed=9, accumulate=True), out=acc)
+    assert torch.allclose(acc / 2, full, rtol=1e-5, atol=1e-6 * full.abs().max().item())
