@@ -849,13 +849,59 @@ def _invert_rect(args):
     return 0
 
 
+METRIC3 = "3D gradient evaluation photons/s (forward + adjoint)"
+
+
+def cpu_oracle_rate3(mua, mus, mua_true, src, dx, g, L, sample, seed):
+    """The 3D oracle as it stands on the host cores: one forward and one adjoint run of ``sample``
+    packets on the full grid (adjoint source from the true-minus-estimate absorption, the shape
+    of a real one).  Returns (photons/s, seconds, segments per photon)."""
+    import oracle
+    from oracle import RunParams
+    m64, s64 = mua.astype(np.float64), mus.astype(np.float64)
+    t0 = time.perf_counter()
+    fo = oracle.forward3(m64, s64, np.float32(dx), np.float32(g), src, RunParams(K=L, n_packets=sample, seed=seed))
+    qo = (-m64 * (m64 - mua_true) / dx ** 3).astype(np.float32)
+    ao = oracle.adjoint3(m64, s64, np.float32(dx), np.float32(g), qo, RunParams(K=L, n_packets=sample, seed=seed + 1))
+    dt = time.perf_counter() - t0
+    return 2 * sample / dt, dt, {"forward_segments": fo.stats["segments"] / sample,
+                                 "adjoint_segments": ao.stats["segments"] / sample}
+
+
+def _reference3(args):
+    """--impl reference for grad3d: the 3D oracle on the host cores, the same metric and config."""
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1608_05238_gb300 import workloads
+    n, L, dx, g = args.n3, args.l3, 0.1, 0.9
+    mua, mus, mua_true, src = workloads.phantom3(n, dx, seed=0)
+    sample = max(4000, args.cpu_sample // 10)
+    for k in range(args.warmup):
+        cpu_oracle_rate3(mua, mus, mua_true, src, dx, g, L, sample // 4, seed=10 * k)
+    T = 0.0
+    for k in range(args.steps):
+        _, dt, _ = cpu_oracle_rate3(mua, mus, mua_true, src, dx, g, L, sample, seed=100 + 10 * k)
+        T += dt
+    value = 2 * sample * args.steps / T
+    desc = f"{sample} forward + {sample} adjoint packets per step of grad3d (full {n}^3 grid, L={L})"
+    out = {"impl": "reference", "metric": METRIC3, "value": value, "unit": "photons/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"grad3d: {n}^3 voxels of {dx} mm, L={L}, g={g}, pencil beam"},
+           "cpu_baseline": {"value": value, "unit": "photons/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": desc},
+           "e2e": {"value": value, "unit": "photons/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def _grad3d(args):
     """The 3D gradient evaluation (spherical-harmonic tallies): forward run from the pencil beam,
     H and dL/dH against a synthetic measurement, q*, adjoint run, and the voxel gradients, on the
     n^3 phantom; photons (forward + adjoint) per second, the transport's payload rate, and the
     FP64 oracle's rate on a sample of the same runs."""
     import torch
-    from oracle import RunParams
     from paper_1608_05238_gb300 import _build, mcr, mcr3, workloads
     _build.build()
     n, L, dx, g = args.n3, args.l3, 0.1, 0.9
@@ -925,19 +971,12 @@ def _grad3d(args):
     value = 2 * N * args.steps / T
     cpu = None
     if not args.no_cpu_baseline:
-        import oracle
         sample = max(4000, args.cpu_sample // 10)
-        m64, s64 = mua.astype(np.float64), mus.astype(np.float64)
-        t0 = time.perf_counter()
-        fo = oracle.forward3(m64, s64, np.float32(dx), np.float32(g), src, RunParams(K=L, n_packets=sample, seed=1))
-        qo = (-mua.astype(np.float64) * (mua.astype(np.float64) - mua_true) / dx ** 3).astype(np.float32)
-        ao = oracle.adjoint3(m64, s64, np.float32(dx), np.float32(g), qo, RunParams(K=L, n_packets=sample, seed=2))
-        dt = time.perf_counter() - t0
-        cpu = {"value": 2 * sample / dt, "unit": "photons/s", "cores": os.cpu_count(), "kind": "oracle",
+        rate, dt, work = cpu_oracle_rate3(mua, mus, mua_true, src, dx, g, L, sample, seed=1)
+        cpu = {"value": rate, "unit": "photons/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{sample} forward + {sample} adjoint packets of grad3d (full grid, L={L}), {dt:.1f} s",
-               "work_per_photon": {"forward_segments": fo.stats["segments"] / sample,
-                                   "adjoint_segments": ao.stats["segments"] / sample}}
-    out = {"metric": "3D gradient evaluation photons/s (forward + adjoint)", "value": value, "unit": "photons/s",
+               "work_per_photon": work}
+    out = {"metric": METRIC3, "value": value, "unit": "photons/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64 (FP64 gradient)",
            "data": "synthetic",
@@ -973,7 +1012,7 @@ def main():
     if args.workload == "grad3d" and args.impl != "reference":
         return _grad3d(args)
     if args.impl == "reference":
-        return _reference(args)
+        return _reference3(args) if args.workload == "grad3d" else _reference(args)
     return _gpu(args)
 
 
