@@ -279,3 +279,39 @@ def test_grad3d_full_size_sample_and_full_run_properties():
     acc = mcr3.forward(med, s3, mcr.Run(K=L, n_packets=N // 2, seed=9))
     mcr3.forward(med, s3, mcr.Run(K=L, n_packets=N // 2, first_packet=N // 2, seed=9, accumulate=True), out=acc)
     assert torch.allclose(acc / 2, full, rtol=1e-5, atol=1e-6 * full.abs().max().item())
+
+
+@pytest.mark.parametrize("n_packets", [0, 1, 31, 33])
+def test_degenerate_and_ragged_3d(n_packets):
+    """A single voxel, L = 0, and packet counts of 0, 1, 31, 33 (empty, one lane, a partial warp,
+    one warp plus one) against the oracle; no packets gives zero coefficients and no launches."""
+    mua = np.array([[[0.7]]], np.float32)
+    mus = np.array([[[3.0]]], np.float32)
+    dx, g = f32(0.5), f32(0.6)
+    src = dict(kind=mcr.ISO_POINT, x0=f32(0.21), y0=f32(0.33), z0=f32(0.17), power=1.0)
+    med = mcr3.Medium3(_dev(mua), _dev(mus), dx, g)
+    for L in (0, 2):
+        run = mcr.Run(K=L, n_packets=n_packets, seed=4)
+        G, st = mcr3.forward(med, mcr3.Source3(**src), run, stats=True)
+        assert st["launched"] == n_packets
+        if n_packets == 0:
+            assert torch.count_nonzero(G).item() == 0
+            continue
+        O = oracle.forward3(mua.astype(np.float64), mus.astype(np.float64), dx, g, src, _orc_run(run))
+        assert np.allclose(G.double().cpu().numpy(), O.coeff, rtol=2e-5, atol=1e-6 * np.abs(O.coeff).max())
+
+
+def test_maximum_packets_per_call_3d():
+    """2^26 packets, the most one call takes, on a small strongly absorbing grid: the tallies do
+    not overflow, the bookkeeping closes, and the fluence matches a run of 2^20 packets."""
+    mua = np.full((4, 4, 4), 5.0, np.float32)
+    mus = np.full((4, 4, 4), 5.0, np.float32)
+    med = mcr3.Medium3(_dev(mua), _dev(mus), f32(0.25), f32(0.5))
+    src = mcr3.Source3(mcr.ISO_POINT, x0=f32(0.55), y0=f32(0.45), z0=f32(0.6))
+    N = 1 << 26
+    c, st = mcr3.forward(med, src, mcr.Run(K=2, n_packets=N, seed=6), stats=True)
+    assert st["launched"] == N
+    assert abs(st["launched_w"] + st["rr_net_w"] - st["absorbed_w"] - st["escaped_w"] - st["killed_w"]) < 1e-9 * N
+    small = mcr3.forward(med, src, mcr.Run(K=2, n_packets=1 << 20, seed=7))
+    phi, phi_s = c[0].double(), small[0].double()
+    assert torch.allclose(phi, phi_s, rtol=0.02, atol=0.02 * phi.max().item())
