@@ -63,6 +63,9 @@ int mc3_adjoint_source(const mcr3_medium *med, const float *dL_dH, float *qstar,
 /* The gradients above in FP64 (device out [nz][ny][nx] each), L the coefficients' order. */
 int mc3_gradient(const mcr3_medium *med, int32_t L, const float *coeff, const float *coeff_adj, const float *dL_dH,
                  double *d_mua, double *d_mus, void *stream);
+/* The same FP64 sums, each result rounded once to FP32 (device out [nz][ny][nx] each). */
+int mc3_gradient_f32(const mcr3_medium *med, int32_t L, const float *coeff, const float *coeff_adj,
+                     const float *dL_dH, float *d_mua, float *d_mus, void *stream);
 
 #ifdef __cplusplus
 }

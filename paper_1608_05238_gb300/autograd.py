@@ -22,7 +22,7 @@ from dataclasses import dataclass, field, replace
 
 import torch
 
-from . import mcr
+from . import mcr, mcr3
 
 
 @dataclass
@@ -122,3 +122,78 @@ def absorbed_energy(mua: torch.Tensor, mus: torch.Tensor, spec: MCSpec) -> torch
 def error_functional(H: torch.Tensor, Hmeas: torch.Tensor, dx: float) -> torch.Tensor:
     """Eq. 2's eps(H), differentiable with respect to H."""
     return EpsFromH.apply(H, Hmeas, dx)
+
+
+# ------------------------------------------------------------------------------------------ 3D
+@dataclass
+class MCSpec3:
+    """The 3D forward model (Sec. 3.1's spherical-harmonic form): voxel side, HG g, one source,
+    order L and packet budgets."""
+    dx: float
+    g: float
+    source: "mcr3.Source3"
+    L: int
+    n_packets: int
+    n_adjoint: int | None = None
+    seed: int = 0
+    adjoint_seed: int | None = None
+    recompute: bool = False           # recompute the forward coefficients in backward (same seeds)
+    w_threshold: float = 1e-4
+    roulette_p: float = 0.1
+    max_events: int = 10_000_000
+
+    def forward_run(self) -> mcr.Run:
+        return mcr.Run(K=self.L, n_packets=self.n_packets, seed=self.seed, stream_id=0,
+                       w_threshold=self.w_threshold, roulette_p=self.roulette_p, max_events=self.max_events)
+
+    def adjoint_run(self) -> mcr.Run:
+        return mcr.Run(K=self.L, n_packets=self.n_adjoint or self.n_packets,
+                       seed=self.seed if self.adjoint_seed is None else self.adjoint_seed, stream_id=1,
+                       w_threshold=self.w_threshold, roulette_p=self.roulette_p, max_events=self.max_events)
+
+
+class HFromMu3(torch.autograd.Function):
+    """(mu_a, mu_s) [nz, ny, nx] -> H = mu_a sqrt(4 pi) c_00 by 3D forward MC; backward by the 3D
+    adjoint MC from q* = -mu_a v / dx^3 and the voxel combine
+    dL/dmu_a = v sqrt(4 pi) c_00 + dx^3 sum c c*, dL/dmu_s = dx^3 sum (1 - g^l) c c*."""
+
+    @staticmethod
+    def forward(ctx, mua: torch.Tensor, mus: torch.Tensor, spec: MCSpec3):
+        mua_c = mua.detach().contiguous()
+        mus_c = mus.detach().contiguous()
+        med = mcr3.Medium3(mua_c, mus_c, spec.dx, spec.g)
+        coeff = mcr3.forward(med, spec.source, spec.forward_run())
+        H = mcr3.h_eps(med, coeff)
+        ctx.spec = spec
+        if spec.recompute:
+            ctx.save_for_backward(mua_c, mus_c)
+        else:
+            ctx.save_for_backward(mua_c, mus_c, coeff)
+        return H
+
+    @staticmethod
+    def backward(ctx, grad_H: torch.Tensor):
+        spec: MCSpec3 = ctx.spec
+        saved = ctx.saved_tensors
+        med = mcr3.Medium3(saved[0], saved[1], spec.dx, spec.g)
+        v = grad_H.detach().float().contiguous()
+        q = mcr3.adjoint_source(med, v)
+        coeff_adj = mcr3.adjoint(med, q, spec.adjoint_run())
+        coeff = mcr3.forward(med, spec.source, spec.forward_run()) if spec.recompute else saved[2]
+        d_mua, d_mus = mcr3.gradient(med, coeff, coeff_adj, v, dtype=torch.float32)
+        return (d_mua if ctx.needs_input_grad[0] else None, d_mus if ctx.needs_input_grad[1] else None, None)
+
+
+class EpsFromH3(torch.autograd.Function):
+    """eps = 1/2 dx^3 sum (H^meas - H)^2 (FP64) with dL/dH = -dx^3 (H^meas - H)."""
+
+    @staticmethod
+    def forward(ctx, H: torch.Tensor, Hmeas: torch.Tensor, dx: float):
+        e, v = mcr3.eps(H.detach().contiguous(), Hmeas.detach().contiguous(), dx)
+        ctx.save_for_backward(v)
+        return e
+
+    @staticmethod
+    def backward(ctx, grad_eps: torch.Tensor):
+        (v,) = ctx.saved_tensors
+        return v * grad_eps.to(v.dtype), None, None

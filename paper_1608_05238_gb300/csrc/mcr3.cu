@@ -503,9 +503,11 @@ __global__ void k_eps3_final(const double *partials, int n, double half_V, doubl
   *eps = half_V * s;
 }
 
-// d_mua = v sqrt(4 pi) c_00 + V sum_c c c*, d_mus = V sum_c (1 - g^l) c c* (FP64, increasing c)
+// d_mua = v sqrt(4 pi) c_00 + V sum_c c c*, d_mus = V sum_c (1 - g^l) c c* (FP64, increasing c);
+// OUT double, or float (the FP64 result rounded once)
+template <typename OUT>
 __global__ void k_gradient3(const float *__restrict__ co, const float *__restrict__ ca, const float *__restrict__ v,
-                            int64_t n, int C, double g, double V, double *d_mua, double *d_mus) {
+                            int64_t n, int C, double g, double V, OUT *d_mua, OUT *d_mus) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double sa = 0.0, ss = 0.0, gl = 1.0;
     int l = 0;
@@ -518,8 +520,8 @@ __global__ void k_gradient3(const float *__restrict__ co, const float *__restric
       sa += p;
       ss += (1.0 - gl) * p;
     }
-    d_mua[i] = (double)v[i] * sqrt(4.0 * CUDART_PI) * (double)co[i] + V * sa;
-    d_mus[i] = V * ss;
+    d_mua[i] = (OUT)((double)v[i] * sqrt(4.0 * CUDART_PI) * (double)co[i] + V * sa);
+    d_mus[i] = (OUT)(V * ss);
   }
 }
 
@@ -725,6 +727,23 @@ int run3(const mcr3_medium *med, const mcr3_source *src, const float *qstar, con
 
 using namespace mcr;
 
+namespace {
+template <typename OUT>
+int gradient3(const mcr3_medium *med, int32_t L, const float *coeff, const float *coeff_adj, const float *dL_dH,
+              OUT *d_mua, OUT *d_mus, void *stream) {
+  int rc;
+  if ((rc = check_medium3(med))) return rc;
+  if (L < 0 || L > MCR3_MAX_L || !coeff || !coeff_adj || !dL_dH || !d_mua || !d_mus) return MCR_ERR_ARG;
+  const int64_t n = (int64_t)med->nx * med->ny * med->nz;
+  const double V = (double)med->dx * med->dx * med->dx;
+  const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_gradient3<OUT><<<grid, 256, 0, (cudaStream_t)stream>>>(coeff, coeff_adj, dL_dH, n, (L + 1) * (L + 1),
+                                                            (double)med->g, V, d_mua, d_mus);
+  return cudaGetLastError() == cudaSuccess ? MCR_OK : MCR_ERR_CUDA;
+}
+
+}  // namespace
+
 extern "C" {
 
 int mc3_forward(const mcr3_medium *med, const mcr3_source *src, const mcr_run *run, float *coeff, mcr_stats *stats,
@@ -768,15 +787,12 @@ int mc3_adjoint_source(const mcr3_medium *med, const float *dL_dH, float *qstar,
 
 int mc3_gradient(const mcr3_medium *med, int32_t L, const float *coeff, const float *coeff_adj, const float *dL_dH,
                  double *d_mua, double *d_mus, void *stream) {
-  int rc;
-  if ((rc = check_medium3(med))) return rc;
-  if (L < 0 || L > MCR3_MAX_L || !coeff || !coeff_adj || !dL_dH || !d_mua || !d_mus) return MCR_ERR_ARG;
-  const int64_t n = (int64_t)med->nx * med->ny * med->nz;
-  const double V = (double)med->dx * med->dx * med->dx;
-  const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-  k_gradient3<<<grid, 256, 0, (cudaStream_t)stream>>>(coeff, coeff_adj, dL_dH, n, (L + 1) * (L + 1), (double)med->g,
-                                                       V, d_mua, d_mus);
-  return cudaGetLastError() == cudaSuccess ? MCR_OK : MCR_ERR_CUDA;
+  return gradient3(med, L, coeff, coeff_adj, dL_dH, d_mua, d_mus, stream);
+}
+
+int mc3_gradient_f32(const mcr3_medium *med, int32_t L, const float *coeff, const float *coeff_adj,
+                     const float *dL_dH, float *d_mua, float *d_mus, void *stream) {
+  return gradient3(med, L, coeff, coeff_adj, dL_dH, d_mua, d_mus, stream);
 }
 
 }  // extern "C"

@@ -19,7 +19,7 @@ from .mcr import ISO_POINT, PENCIL, McrError, Run  # noqa: F401  (re-exported)
 MAX_L = 8
 
 # every symbol declared in include/mcr3.h
-EXPORTS = ("mc3_forward", "mc3_adjoint", "mc3_h_eps", "mc3_adjoint_source", "mc3_gradient")
+EXPORTS = ("mc3_forward", "mc3_adjoint", "mc3_h_eps", "mc3_adjoint_source", "mc3_gradient", "mc3_gradient_f32")
 
 
 class _Medium3(C.Structure):
@@ -47,6 +47,7 @@ def load() -> C.CDLL:
         lib.mc3_h_eps.argtypes = [C.POINTER(_Medium3), vp, vp, vp, vp, vp, vp]
         lib.mc3_adjoint_source.argtypes = [C.POINTER(_Medium3), vp, vp, vp]
         lib.mc3_gradient.argtypes = [C.POINTER(_Medium3), C.c_int32, vp, vp, vp, vp, vp, vp]
+        lib.mc3_gradient_f32.argtypes = [C.POINTER(_Medium3), C.c_int32, vp, vp, vp, vp, vp, vp]
         for name in EXPORTS:
             getattr(lib, name).restype = C.c_int
         _typed = True
@@ -152,8 +153,10 @@ def adjoint_source(med: Medium3, dL_dH: torch.Tensor, stream=None) -> torch.Tens
     return q
 
 
-def gradient(med: Medium3, coeff: torch.Tensor, coeff_adj: torch.Tensor, dL_dH: torch.Tensor, stream=None):
-    """(dL/dmu_a, dL/dmu_s) per voxel in FP64 (``mc3_gradient``)."""
+def gradient(med: Medium3, coeff: torch.Tensor, coeff_adj: torch.Tensor, dL_dH: torch.Tensor, stream=None,
+             dtype=torch.float64):
+    """(dL/dmu_a, dL/dmu_s) per voxel (``mc3_gradient`` / ``mc3_gradient_f32``): FP64 sums, the
+    results in ``dtype`` (float32 rounds them once)."""
     lib = load()
     for t, n in ((coeff, "coeff"), (coeff_adj, "coeff_adj"), (dL_dH, "dL_dH")):
         mcr._dev_f32(t, n)
@@ -162,8 +165,28 @@ def gradient(med: Medium3, coeff: torch.Tensor, coeff_adj: torch.Tensor, dL_dH: 
     L = int(round(coeff.shape[0] ** 0.5)) - 1
     if (L + 1) ** 2 != coeff.shape[0]:
         raise ValueError("coeff must have (L+1)^2 channels")
-    d_mua = torch.empty(med.shape, dtype=torch.float64, device=coeff.device)
+    if dtype not in (torch.float64, torch.float32):
+        raise TypeError("dtype must be float64 or float32")
+    fn, name = (lib.mc3_gradient, "mc3_gradient") if dtype == torch.float64 else (lib.mc3_gradient_f32,
+                                                                                 "mc3_gradient_f32")
+    d_mua = torch.empty(med.shape, dtype=dtype, device=coeff.device)
     d_mus = torch.empty_like(d_mua)
-    mcr._check(lib.mc3_gradient(C.byref(med.c()), L, mcr._ptr(coeff), mcr._ptr(coeff_adj), mcr._ptr(dL_dH),
-                                mcr._ptr(d_mua), mcr._ptr(d_mus), mcr._stream(stream)), "mc3_gradient")
+    mcr._check(fn(C.byref(med.c()), L, mcr._ptr(coeff), mcr._ptr(coeff_adj), mcr._ptr(dL_dH), mcr._ptr(d_mua),
+                  mcr._ptr(d_mus), mcr._stream(stream)), name)
     return d_mua, d_mus
+
+
+def eps(H: torch.Tensor, Hmeas: torch.Tensor, dx: float, stream=None):
+    """eps = 1/2 dx^3 sum (Hmeas - H)^2 (FP64) and dL/dH = -dx^3 (Hmeas - H) from a given H (``mc_eps``
+    with the voxel volume as the cell measure)."""
+    lib = mcr.load()
+    mcr._dev_f32(H, "H")
+    mcr._dev_f32(Hmeas, "Hmeas")
+    if H.shape != Hmeas.shape:
+        raise ValueError("H and Hmeas must match")
+    v = torch.empty_like(H)
+    e = torch.empty((), dtype=torch.float64, device=H.device)
+    d32 = C.c_float(dx).value  # the voxel side as the medium struct carries it (FP32)
+    mcr._check(lib.mc_eps(H.numel(), d32 * d32 * d32, mcr._ptr(H), mcr._ptr(Hmeas), mcr._ptr(v), mcr._ptr(e),
+                          mcr._stream(stream)), "mc_eps")
+    return e, v

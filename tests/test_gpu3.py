@@ -315,3 +315,33 @@ def test_maximum_packets_per_call_3d():
     small = mcr3.forward(med, src, mcr.Run(K=2, n_packets=1 << 20, seed=7))
     phi, phi_s = c[0].double(), small[0].double()
     assert torch.allclose(phi, phi_s, rtol=0.02, atol=0.02 * phi.max().item())
+
+
+def test_autograd_3d_equals_the_explicit_chain():
+    """HFromMu3 + EpsFromH3: the backward pass is the explicit chain (forward, eps, q*, adjoint,
+    FP32 combine) on the same seeds, bit for bit, kept or recomputed; mc3_gradient_f32 is the FP64
+    combine rounded once; eps and dL/dH match mc3_h_eps."""
+    from paper_1608_05238_gb300.autograd import EpsFromH3, HFromMu3, MCSpec3
+    mua, mus = workloads.small_hetero3(10, 11, 12, 0.1, seed=8)
+    dx, g = f32(0.1), f32(0.8)
+    src = mcr3.Source3(mcr.ISO_POINT, x0=0.61, y0=0.52, z0=0.43)
+    Hm = _dev(mua * 0.7)
+    med = mcr3.Medium3(_dev(mua), _dev(mus), dx, g)
+    grads = []
+    for recompute in (False, True):
+        spec = MCSpec3(dx=dx, g=g, source=src, L=3, n_packets=200_000, seed=5, adjoint_seed=6, recompute=recompute)
+        a, s = _dev(mua).requires_grad_(), _dev(mus).requires_grad_()
+        e = EpsFromH3.apply(HFromMu3.apply(a, s, spec), Hm, dx)
+        e.backward()
+        grads.append((a.grad.clone(), s.grad.clone(), e.item()))
+    assert torch.equal(grads[0][0], grads[1][0]) and torch.equal(grads[0][1], grads[1][1])
+    c = mcr3.forward(med, src, mcr.Run(K=3, n_packets=200_000, seed=5))
+    H, v, eps = mcr3.h_eps(med, c, Hm)
+    assert abs(eps.item() - grads[0][2]) <= 1e-12 * abs(eps.item())
+    ca = mcr3.adjoint(med, mcr3.adjoint_source(med, v), mcr.Run(K=3, n_packets=200_000, seed=6, stream_id=1))
+    ga32, gs32 = mcr3.gradient(med, c, ca, v, dtype=torch.float32)
+    assert torch.equal(ga32, grads[0][0]) and torch.equal(gs32, grads[0][1])
+    ga, gs = mcr3.gradient(med, c, ca, v)
+    assert torch.equal(ga.float(), ga32) and torch.equal(gs.float(), gs32)
+    e2, v2 = mcr3.eps(H, Hm, dx)
+    assert torch.equal(v2, v) and abs(e2.item() - eps.item()) <= 1e-12 * abs(eps.item())
