@@ -275,7 +275,7 @@ int mc_last_run_info(int32_t which, mcr_stats *stats, float *transport_ms);
 int mc_reduction_probe(void *tally, int64_t rows, int32_t row_words, int32_t C, int64_t iters, int32_t blocks,
                        int32_t threads, void *stream);
 
-/* Frees the calling device's workspace (synchronises the device). */
+/* Frees the calling device's workspace, the 3D calls' included (synchronises the device). */
 int mc_release_workspace(void);
 
 /* Static text for a status code. */

@@ -723,6 +723,18 @@ int run3(const mcr3_medium *med, const mcr3_source *src, const float *qstar, con
 }
 
 }  // namespace
+
+// Frees this device's 3D workspace (called by mc_release_workspace).
+int release_workspace3(int dev) {
+  if (dev < 0 || dev >= 64) return MCR_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_mu3);
+  Work3 &w = g_w3[dev];
+  void *ptrs[] = {w.tally, w.cdf, w.block_sums, w.mu, w.small, w.partials};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  w = Work3{};
+  return MCR_OK;
+}
 }  // namespace mcr
 
 using namespace mcr;

@@ -450,7 +450,7 @@ int mc_release_workspace(void) {
     if (w.ev_stop[k]) cudaEventDestroy(w.ev_stop[k]);
   }
   w = Workspace{};
-  return MCR_OK;
+  return release_workspace3(dev);
 }
 
 const char *mc_status_string(int status) {

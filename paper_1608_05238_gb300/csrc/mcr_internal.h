@@ -157,4 +157,7 @@ cudaError_t launch_gradient(const float *coeff, const float *coeff_adj, const fl
 cudaError_t launch_gradient_f32(const float *coeff, const float *coeff_adj, const float *dL_dH, int64_t npix, int K,
                                 double g, double area, float *d_mua, float *d_mus, cudaStream_t s);
 
+// Frees the 3D transport's workspace on device dev (mcr3.cu).
+int release_workspace3(int dev);
+
 }  // namespace mcr

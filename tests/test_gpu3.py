@@ -201,6 +201,9 @@ def test_device_side_errors():
     assert torch.count_nonzero(z).item() == 0
     ok = mcr3.forward(med, mcr3.Source3(mcr.ISO_POINT, 0.3, 0.3, 0.3), mcr.Run(K=1, n_packets=1000))
     assert torch.isfinite(ok).all() and ok[0].sum().item() > 0
+    mcr.release_workspace()  # frees the 3D workspace too; the next call allocates it again
+    again = mcr3.forward(med, mcr3.Source3(mcr.ISO_POINT, 0.3, 0.3, 0.3), mcr.Run(K=1, n_packets=1000))
+    assert torch.equal(again, ok)
 
 
 def test_gradient3_through_the_gpu_path_matches_the_oracle_gradient():
