@@ -25,12 +25,15 @@ def f32(v):
     return float(np.float32(v))
 
 
-def assert_parity(G, O, A, sigma, rel=REL, label="", unvisited_share=None, floor=0.0):
+def assert_parity(G, O, A, sigma, rel=REL, label="", unvisited_share=None, floor=0.0, outliers=None):
     """3D grazing paths: a path that runs within FP32 resolution of a voxel face, or through an
     edge, can cut through a neighbouring voxel on one side and not on the other, or for a
     different micro-length.  ``unvisited_share``: cells the oracle's packets never enter (A = 0,
     sigma = 0, where (iii) cannot apply) are held instead to sum |G| <= unvisited_share sum A;
-    ``floor``: an absolute allowance added to (iii) for such micro-segments."""
+    ``floor``: an absolute allowance added to (iii) for such micro-segments.  ``outliers`` =
+    (fraction, share): on large sparse grids a packet whose FP32 and FP64 paths part can cross a
+    cell that only one or two of the other side's packets touched; up to that fraction of the
+    low-count cells may then exceed (iii) if together they carry at most that share of sum A."""
     G = np.asarray(G, np.float64)
     O = np.asarray(O, np.float64)
     A = np.abs(np.asarray(A, np.float64))
@@ -52,5 +55,13 @@ def assert_parity(G, O, A, sigma, rel=REL, label="", unvisited_share=None, floor
         lo &= ~zero
     if lo.any():
         bound = 3 * sigma[lo] + rel * A[lo] + floor + 1e-30
-        assert np.all(d[:, lo] <= bound), f"{label}: low-count pixels beyond 3 sigma"
+        over = (d[:, lo] > bound).any(axis=0)
+        if outliers is None:
+            assert not over.any(), f"{label}: low-count pixels beyond 3 sigma"
+        else:
+            frac, share = outliers
+            n_over = int(over.sum())
+            excess = float(d[:, lo][:, over].sum(axis=1).max() / tot) if n_over else 0.0
+            assert n_over <= frac * int(lo.sum()) and excess <= share, \
+                f"{label}: {n_over} low-count cells beyond 3 sigma carrying {excess:.3e} of the total"
     return dict(max_rel=worst, l1=float(d.sum(axis=(1, 2)).max() / tot))

@@ -49,7 +49,7 @@ def test_autograd_gradient_matches_oracle():
     fo = oracle.forward(m64, s64, dxo, go, src, RunParams(K=K, n_packets=n, seed=3, stream_id=0)).coeff
     Ho = F.absorbed_energy(m64, fo)
     assert abs(e - F.error_functional(Hm, Ho, dxo)) <= 1e-3 * e
-    v = F.dL_dH_eps(Hm, H.astype(np.float64), dxo)  # the GPU's H drives the adjoint source
+    v = F.dL_dH_eps(Hm, Ho, dxo)  # the oracle's own H drives its adjoint source
     q = F.adjoint_source(m64, v.astype(np.float32).astype(np.float64), dxo).astype(np.float32)
     ao = oracle.adjoint(m64, s64, dxo, go, q, RunParams(K=K, n_packets=n, seed=4, stream_id=1)).coeff
     aabs = oracle.adjoint(m64, s64, dxo, go, np.abs(q), RunParams(K=K, n_packets=n, seed=4, stream_id=1)).coeff

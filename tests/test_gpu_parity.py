@@ -213,7 +213,8 @@ def test_adjoint_single_pixel_source_K8():
 
 
 def test_gradient_h_eps_and_adjoint_source_parity():
-    """mc_gradient / mc_h_eps / mc_adjoint_source vs the oracle functionals on the SAME inputs."""
+    """mc_gradient / mc_h_eps / mc_adjoint_source vs the oracle functionals on the SAME seeded
+    inputs (each kernel is fed numpy arrays, never another kernel's output)."""
     rng = np.random.default_rng(9)
     K, nz, nx, dx, g = 12, 37, 29, f32(0.05), f32(0.9)
     c = rng.normal(size=(2 * K + 1, nz, nx)).astype(np.float32)
@@ -224,16 +225,18 @@ def test_gradient_h_eps_and_adjoint_source_parity():
     Hm = rng.uniform(0, 0.5, (nz, nx)).astype(np.float32)
     med = mcr.Medium(_dev(mua), _dev(mus), dx, g)
     H, v, eps = mcr.h_eps(med, _dev(c), _dev(Hm))
-    H = H.cpu().numpy()
-    assert np.array_equal(H, (mua * c[0]).astype(np.float32))  # one FP32 product, exact
-    H64 = H.astype(np.float64)
+    # expected values from the inputs alone: H is one FP32 product, computed here in numpy
+    H32 = (mua * c[0]).astype(np.float32)
+    assert np.array_equal(H.cpu().numpy(), H32)
+    H64 = H32.astype(np.float64)
     assert abs(eps.item() - F.error_functional(Hm.astype(np.float64), H64, dx)) < 1e-12 * eps.item()
-    v = v.cpu().numpy()
-    assert np.allclose(v, F.dL_dH_eps(Hm, H64, dx), rtol=1e-6, atol=0)
-    q = mcr.adjoint_source(med, _dev(v)).cpu().numpy()
-    assert np.allclose(q, F.adjoint_source(mua, v, dx), rtol=1e-6, atol=0)
-    d_mua, d_mus = mcr.gradient(med, _dev(c), _dev(cs), _dev(v))
-    ra, rs = F.dL_dmu(c.astype(np.float64), cs.astype(np.float64), v.astype(np.float64), dx, g)
+    v_ref = F.dL_dH_eps(Hm, H64, dx)
+    assert np.allclose(v.cpu().numpy(), v_ref, rtol=1e-6, atol=0)
+    vin = rng.normal(size=(nz, nx)).astype(np.float32)  # dL/dH input of the next two kernels
+    q = mcr.adjoint_source(med, _dev(vin)).cpu().numpy()
+    assert np.allclose(q, F.adjoint_source(mua, vin, dx), rtol=1e-6, atol=0)
+    d_mua, d_mus = mcr.gradient(med, _dev(c), _dev(cs), _dev(vin))
+    ra, rs = F.dL_dmu(c.astype(np.float64), cs.astype(np.float64), vin.astype(np.float64), dx, g)
     assert np.allclose(d_mua.cpu().numpy(), ra, rtol=1e-12, atol=1e-15 * np.abs(ra).max())
     assert np.allclose(d_mus.cpu().numpy(), rs, rtol=1e-12, atol=1e-15 * np.abs(rs).max())
 
