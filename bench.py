@@ -200,23 +200,28 @@ def cpu_oracle_rate(w, Hmeas_np, n_sample: int, seed: int = 0):
     return 2 * n_sample / dt, cores, dt, work
 
 
+def oracle_hmeas(w, n):
+    """H^meas for the oracle leg from an oracle run of the true medium (n packets per source, K = 0),
+    so that no input of the oracle comes from the CUDA path."""
+    import oracle
+    from oracle import RunParams
+    from oracle import functionals as F
+    dx, g = float(np.float32(w.dx)), float(np.float32(w.g))
+    mt, st = w.mua_true.astype(np.float64), w.mus_true.astype(np.float64)
+    hm = oracle.forward(mt, st, dx, g, w.sources[0], RunParams(K=0, n_packets=n, seed=1001))
+    for s in range(1, len(w.sources)):
+        hm.coeff += oracle.forward(mt, st, dx, g, w.sources[s], RunParams(K=0, n_packets=n, seed=1001,
+                                                                           stream_id=2 * s)).coeff
+    return F.absorbed_energy(mt, hm.coeff)
+
+
 def _reference(args):
     rank, world, _ = _dist()
     if rank != 0:
         return 0
     w = _grad_workload(args.workload, args.packets)
-    # H^meas for the oracle leg: the phantom's absorbed energy from an oracle run (bounded sample)
-    import oracle
-    from oracle import RunParams
-    from oracle import functionals as F
-    dx, g = float(np.float32(w.dx)), float(np.float32(w.g))
     n = max(1000, args.cpu_sample // (10 if w.name == "grad256" else 200))
-    hm = oracle.forward(w.mua_true.astype(np.float64), w.mus_true.astype(np.float64), dx, g, w.sources[0],
-                        RunParams(K=0, n_packets=n, seed=1001))
-    for s in range(1, len(w.sources)):
-        hm.coeff += oracle.forward(w.mua_true.astype(np.float64), w.mus_true.astype(np.float64), dx, g,
-                                   w.sources[s], RunParams(K=0, n_packets=n, seed=1001, stream_id=2 * s)).coeff
-    Hmeas = F.absorbed_energy(w.mua_true.astype(np.float64), hm.coeff)
+    Hmeas = oracle_hmeas(w, n)
     for k in range(args.warmup):
         cpu_oracle_rate(w, Hmeas, n, seed=10 * k)
     times = []
@@ -407,7 +412,7 @@ def _gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        hm_np = Hmeas.double().cpu().numpy()
+        hm_np = oracle_hmeas(w, max(1000, args.cpu_sample // (10 if w.name == "grad256" else 200)))
         sample = args.cpu_sample if w.name == "grad256" else max(4, args.cpu_sample // 20)
         rate, cores, dt, owork = cpu_oracle_rate(w, hm_np, sample)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
