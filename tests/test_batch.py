@@ -37,12 +37,13 @@ def _mixed_problems(K):
                      mcr.Source(mcr.ANGULAR_POINT, x0=f32(0.41 * nx * dx), z0=f32(0.45 * nz * dx),
                                 ang_c=(0.0, 0.5), ang_s=(0.25,))]
             p = mcr.Problem(med, n, seed=5 + i, stream_id=2 * i, source=kinds[(i // 2) % 4])
+            q = None
         else:
             q = np.random.default_rng(i).normal(size=(nz, nx)).astype(np.float32)
             q[np.random.default_rng(i + 9).uniform(size=q.shape) < 0.5] = 0
             p = mcr.Problem(med, n, seed=5 + i, stream_id=2 * i + 1, qstar=torch.from_numpy(q).cuda())
         probs.append(p)
-        meta.append((mua, mus))
+        meta.append((mua, mus, q))  # the numpy inputs, for the oracle
     return probs, meta
 
 
@@ -64,16 +65,15 @@ def test_batch_problem_matches_oracle():
     probs, meta = _mixed_problems(K)
     outs = mcr.run_batch(probs, common)
     for i in (0, 3):
-        p, (mua, mus) = probs[i], meta[i]
+        p, (mua, mus, qn) = probs[i], meta[i]
         rp = RunParams(K=K, n_packets=p.n_packets, seed=p.seed, stream_id=p.stream_id)
         args = (mua.astype(np.float64), mus.astype(np.float64), p.medium.dx, p.medium.g)
         if p.source is not None:
             O = oracle.forward(*args, p.source.as_dict(), rp, with_variance=True)
             A, sig = O.coeff[0], np.sqrt(O.a0_var)
         else:
-            q = p.qstar.cpu().numpy()
-            O = oracle.adjoint(*args, q, rp)
-            Oa = oracle.adjoint(*args, np.abs(q), rp, with_variance=True)
+            O = oracle.adjoint(*args, qn, rp)
+            Oa = oracle.adjoint(*args, np.abs(qn), rp, with_variance=True)
             A, sig = Oa.coeff[0], np.sqrt(Oa.a0_var)
         assert_parity(outs[i].double().cpu().numpy(), O.coeff, A, sig, label=f"batch problem {i}")
 
