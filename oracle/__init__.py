@@ -1,16 +1,16 @@
-"""FP64 CPU oracle for the 2D forward/adjoint harmonic radiance Monte Carlo
-(Hochuli, Powell, Arridge & Cox, arXiv 1608.05238).
+"""FP64 CPU oracle for the forward/adjoint harmonic radiance Monte Carlo (Hochuli, Powell,
+Arridge & Cox, arXiv 1608.05238): the 2D method and the 3D spherical-harmonic form Sec. 3.1 names.
 
 TEST INFRASTRUCTURE ONLY.  The oracle is the plain, slow, obviously correct
 statement of what the method computes; the CUDA library is checked against
-it.  Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg
-of ``bench.py`` may import or call anything here.  It shares no code with the
+it.  Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline and
+``--impl reference`` legs of ``bench.py`` may import or call anything here.  It shares no code with the
 CUDA path: the transport lives in ``mcr_oracle.c`` (plain C, FP64), the
 pixelwise functionals (H, epsilon, gradients) in :mod:`oracle.functionals`
 (numpy, FP64).
 
 Pins (what fixes each function independently of itself) live in
-``tests/test_oracle_*.py``; see the list in the design doc.
+``tests/test_oracle_pins.py``, ``tests/test_oracle_pins3.py`` and ``tests/test_oracle_gradients.py``.
 """
 from __future__ import annotations
 
