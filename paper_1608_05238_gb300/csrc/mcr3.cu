@@ -337,43 +337,21 @@ __global__ void __launch_bounds__(kThreads3, 8) k_transport3(const __grid_consta
           seg_v = -1;
         }
       }
-      if (collided) {
-        fx = clamp3(fmaf(l, ux, fx), dx);
-        fy = clamp3(fmaf(l, uy, fy), dx);
-        fz = clamp3(fmaf(l, uz, fz), dx);
-      } else {
+      // advance along the path; a face crossing then steps the voxel index on its axis and puts
+      // the offset on the entered face (selects, not branches: the lanes of a warp take
+      // different axes)
+      fx = clamp3(fmaf(l, ux, fx), dx);
+      fy = clamp3(fmaf(l, uy, fy), dx);
+      fz = clamp3(fmaf(l, uz, fz), dx);
+      if (!collided) {
         tau = fmaxf(fmaf(-m.y, l, tau), 0.f);
-        if (axis == 0) {
-          if (ux > 0.f) {
-            ++ix;
-            fx = 0.f;
-          } else {
-            --ix;
-            fx = dx;
-          }
-          fy = clamp3(fmaf(l, uy, fy), dx);
-          fz = clamp3(fmaf(l, uz, fz), dx);
-        } else if (axis == 1) {
-          if (uy > 0.f) {
-            ++iy;
-            fy = 0.f;
-          } else {
-            --iy;
-            fy = dx;
-          }
-          fx = clamp3(fmaf(l, ux, fx), dx);
-          fz = clamp3(fmaf(l, uz, fz), dx);
-        } else {
-          if (uz > 0.f) {
-            ++iz;
-            fz = 0.f;
-          } else {
-            --iz;
-            fz = dx;
-          }
-          fx = clamp3(fmaf(l, ux, fx), dx);
-          fy = clamp3(fmaf(l, uy, fy), dx);
-        }
+        const bool cx = axis == 0, cy = axis == 1, cz = axis == 2;
+        ix += cx ? (ux > 0.f ? 1 : -1) : 0;
+        iy += cy ? (uy > 0.f ? 1 : -1) : 0;
+        iz += cz ? (uz > 0.f ? 1 : -1) : 0;
+        fx = cx ? (ux > 0.f ? 0.f : dx) : fx;
+        fy = cy ? (uy > 0.f ? 0.f : dx) : fy;
+        fz = cz ? (uz > 0.f ? 0.f : dx) : fz;
         escaped = (unsigned)ix >= (unsigned)p.nx || (unsigned)iy >= (unsigned)p.ny || (unsigned)iz >= (unsigned)p.nz;
       }
     }
