@@ -117,7 +117,9 @@ typedef struct {
  * stats (host, may be NULL).  Tallies are 64-bit fixed-point sums of deposits rounded to a
  * quantum 2^-q mm, q chosen per run from dx, w_threshold and roulette_p so that one deposit
  * spans at most 2^30 quanta: the result does not depend on scheduling and is bit-reproducible
- * for a given run.
+ * for a given run.  A medium with a negative or non-finite mu is detected on the device: the run
+ * adds nothing to coeff (all-zero, or unchanged with accumulate = 1) and the next synchronising
+ * call returns MCR_ERR_MEDIUM.
  */
 int mc_forward(const mcr_medium *med, const mcr_source *src, const mcr_run *run, float *coeff,
                mcr_stats *stats, void *stream);
@@ -140,9 +142,13 @@ int mc_forward(const mcr_medium *med, const mcr_source *src, const mcr_run *run,
  *   with that device current) and caches it: make that first call before any stream capture.
  *   All calls share the one array and each call clears what it needs; calls whose work overlaps
  *   on the GPU (different streams, or different host threads) race on it and must be ordered
- *   by the caller.  No run counters are returned and device-side medium checks are not
- *   reported: a negative or non-finite mu gives an all-zero output.
- * Same arguments, layout and results as mc_forward with stats = NULL.
+ *   by the caller.  No run counters are returned.  Errors found on the device (a negative or
+ *   non-finite mu, a packet ended by max_events, a tally near overflow) are latched in the
+ *   array and returned, like mc_forward's, by the next mc_check on this device (which reads and
+ *   clears them without allocating); a run on a bad medium adds nothing to coeff (all-zero,
+ *   or unchanged with accumulate = 1).
+ * Same arguments (checked by the same rules), layout and results as mc_forward with
+ * stats = NULL: for the same inputs the two outputs are bit-identical.
  */
 int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_run *run, float *coeff,
                        void *stream);
@@ -261,19 +267,6 @@ int mc_check(void *stream);
  * call's stream around them.  Waits for that call to finish.  MCR_ERR_ARG if no such call ran.
  */
 int mc_last_run_info(int32_t which, mcr_stats *stats, float *transport_ms);
-
-/*
- * mc_reduction_probe -- measurement kernel (the paper has no counterpart): the ceiling of the
- * deposit step of Sec. 3.1 (Eqs. 9-11), one 64-bit reduction per coefficient per pixel segment.
- * blocks x threads threads (threads a multiple of 32, <= 1024) run `iters` iterations per warp;
- * each picks a pseudo-random row of `tally` (device, rows x row_words uint64, 8-byte aligned,
- * caller-owned) and adds 1 to its words [0, C) in 32-lane coalesced chunks, as the transport's
- * warp-cooperative deposit does.  Afterwards the words of the tally sum to (blocks threads / 32)
- * iters C more than before.  Asynchronous on `stream`; time it with events around the call.
- * The payload rate is 8 C (blocks threads / 32) iters bytes per duration.
- */
-int mc_reduction_probe(void *tally, int64_t rows, int32_t row_words, int32_t C, int64_t iters, int32_t blocks,
-                       int32_t threads, void *stream);
 
 /* Frees the calling device's workspace, the 3D calls' included (synchronises the device). */
 int mc_release_workspace(void);

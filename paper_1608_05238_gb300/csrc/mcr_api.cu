@@ -72,46 +72,6 @@ int workspace(const Need &need, Workspace **out) {
   return MCR_OK;
 }
 
-bool finite_f(float v) { return isfinite(v) != 0; }
-
-int check_medium(const mcr_medium *m) {
-  if (!m || !m->mua || !m->mus) return MCR_ERR_ARG;
-  // the deposit key packs (pixel + 1) into 26 bits
-  if (m->nx <= 0 || m->nz <= 0 || (int64_t)m->nx * m->nz >= (int64_t)1 << 26) return MCR_ERR_ARG;
-  if (!(m->dx > 0.f) || !finite_f(m->dx)) return MCR_ERR_ARG;
-  if (!(m->g > -1.f && m->g < 1.f)) return MCR_ERR_ARG;
-  return MCR_OK;
-}
-
-int check_run(const mcr_run *r) {
-  if (!r) return MCR_ERR_ARG;
-  if (r->K < 0 || r->K > MCR_MAX_K) return MCR_ERR_ARG;
-  if (!(r->roulette_p > 0.f && r->roulette_p <= 1.f)) return MCR_ERR_ARG;
-  if (!(r->w_threshold >= 0.f) || !finite_f(r->w_threshold)) return MCR_ERR_ARG;
-  if (r->first_packet + r->n_packets < r->first_packet) return MCR_ERR_ARG;  // id overflow
-  if (r->accumulate > 1u) return MCR_ERR_ARG;
-  if (r->sectors > 1024u) return MCR_ERR_ARG;
-  return MCR_OK;
-}
-
-// Normalised launch direction of a boundary source, or MCR_ERR_ARG.
-int check_source(const mcr_source *src, float *dirx, float *dirz) {
-  if (!src || src->kind < MCR_PENCIL || src->kind > MCR_ANGULAR_POINT) return MCR_ERR_ARG;
-  if (src->kind == MCR_ANGULAR_POINT && !angular_density_ok(*src)) return MCR_ERR_ARG;
-  if (!finite_f(src->x0) || !finite_f(src->z0) || !finite_f(src->x1) || !finite_f(src->z1) ||
-      !finite_f(src->power))
-    return MCR_ERR_ARG;
-  *dirx = 0.f;
-  *dirz = 1.f;
-  if (src->kind == MCR_PENCIL || src->kind == MCR_LINE) {
-    const double nrm = sqrt((double)src->dir_x * src->dir_x + (double)src->dir_z * src->dir_z);
-    if (!(nrm > 0.0) || !isfinite(nrm)) return MCR_ERR_ARG;
-    *dirx = (float)(src->dir_x / nrm);
-    *dirz = (float)(src->dir_z / nrm);
-  }
-  return MCR_OK;
-}
-
 void fill_stats(const DevStats &d, mcr_stats *s) {
   s->launched = d.launched;
   s->flights = d.flights;
@@ -136,10 +96,7 @@ int take_flags(Workspace *w, cudaStream_t s) {
   MCR_TRY_CUDA(cudaStreamSynchronize(s));
   if (flags) MCR_TRY_CUDA(cudaMemsetAsync(w->flags(), 0, sizeof(unsigned), s));
   MCR_TRY_CUDA(cudaStreamSynchronize(s));
-  if (flags & kFlagMedium) return MCR_ERR_MEDIUM;
-  if (flags & kFlagOverflow) return MCR_ERR_TALLY_OVERFLOW;
-  if (flags & kFlagEventLimit) return MCR_ERR_EVENT_LIMIT;
-  return MCR_OK;
+  return status_from_flags(flags);
 }
 
 // One problem as the host sees it.
@@ -410,13 +367,17 @@ int mc_gradient_f32(const mcr_medium *med, int32_t K, const float *coeff, const 
 int mc_check(void *stream) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MCR_ERR_CUDA;
+  // the no-allocation entry point latches its errors in its own scratch
+  const int rc_noalloc = noalloc_take_flags((cudaStream_t)stream);
   std::lock_guard<std::mutex> lock(g_mu);
   Workspace &w = g_ws[dev];
+  int rc = MCR_OK;
   if (!w.small) {
     MCR_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-    return MCR_OK;
+  } else {
+    rc = take_flags(&w, (cudaStream_t)stream);
   }
-  return take_flags(&w, (cudaStream_t)stream);
+  return rc != MCR_OK ? rc : rc_noalloc;
 }
 
 int mc_last_run_info(int32_t which, mcr_stats *stats, float *transport_ms) {
@@ -472,6 +433,51 @@ const char *mc_version(void) { return "mcr 1.0 sm_103a"; }
 }  // extern "C"
 
 namespace mcr {
+
+int check_medium(const mcr_medium *m) {
+  if (!m || !m->mua || !m->mus) return MCR_ERR_ARG;
+  // the deposit key packs (pixel + 1) into 26 bits
+  if (m->nx <= 0 || m->nz <= 0 || (int64_t)m->nx * m->nz >= (int64_t)1 << 26) return MCR_ERR_ARG;
+  if (!(m->dx > 0.f) || !isfinite(m->dx)) return MCR_ERR_ARG;
+  if (!(m->g > -1.f && m->g < 1.f)) return MCR_ERR_ARG;
+  return MCR_OK;
+}
+
+int check_run(const mcr_run *r) {
+  if (!r) return MCR_ERR_ARG;
+  if (r->K < 0 || r->K > MCR_MAX_K) return MCR_ERR_ARG;
+  if (!(r->roulette_p > 0.f && r->roulette_p <= 1.f)) return MCR_ERR_ARG;
+  if (!(r->w_threshold >= 0.f) || !isfinite(r->w_threshold)) return MCR_ERR_ARG;
+  if (r->first_packet + r->n_packets < r->first_packet) return MCR_ERR_ARG;  // id overflow
+  if (r->accumulate > 1u) return MCR_ERR_ARG;
+  if (r->sectors > 1024u) return MCR_ERR_ARG;
+  return MCR_OK;
+}
+
+// Normalised launch direction of a boundary source, or MCR_ERR_ARG.
+int check_source(const mcr_source *src, float *dirx, float *dirz) {
+  if (!src || src->kind < MCR_PENCIL || src->kind > MCR_ANGULAR_POINT) return MCR_ERR_ARG;
+  if (src->kind == MCR_ANGULAR_POINT && !angular_density_ok(*src)) return MCR_ERR_ARG;
+  if (!isfinite(src->x0) || !isfinite(src->z0) || !isfinite(src->x1) || !isfinite(src->z1) ||
+      !isfinite(src->power))
+    return MCR_ERR_ARG;
+  *dirx = 0.f;
+  *dirz = 1.f;
+  if (src->kind == MCR_PENCIL || src->kind == MCR_LINE) {
+    const double nrm = sqrt((double)src->dir_x * src->dir_x + (double)src->dir_z * src->dir_z);
+    if (!(nrm > 0.0) || !isfinite(nrm)) return MCR_ERR_ARG;
+    *dirx = (float)(src->dir_x / nrm);
+    *dirz = (float)(src->dir_z / nrm);
+  }
+  return MCR_OK;
+}
+
+int status_from_flags(unsigned flags) {
+  if (flags & kFlagMedium) return MCR_ERR_MEDIUM;
+  if (flags & kFlagOverflow) return MCR_ERR_TALLY_OVERFLOW;
+  if (flags & kFlagEventLimit) return MCR_ERR_EVENT_LIMIT;
+  return MCR_OK;
+}
 
 // q such that every deposit |t h| 2^q stays below 2^30 (< 2^31 with margin for |h| rounding):
 // t <= W l with l <= dx sqrt 2 inside one pixel, and |W| <= max(1, w_threshold / p) because the

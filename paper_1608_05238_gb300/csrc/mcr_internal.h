@@ -65,7 +65,8 @@ struct TransportParams {
   unsigned long long total_packets;  // = prob[n_problems-1].end
   unsigned long long *work;          // packet counter
   DevStats *stats;
-  const unsigned *flags;             // medium-invalid flag: transport does nothing if set
+  unsigned *flags;                   // error bits: transport does nothing if kFlagMedium is set; it
+                                     // latches kFlagEventLimit when a packet reached max_events
   ProblemDesc prob[kMaxBatch];
 };
 
@@ -156,6 +157,17 @@ cudaError_t launch_gradient(const float *coeff, const float *coeff_adj, const fl
                             double g, double area, double *d_mua, double *d_mus, cudaStream_t s);
 cudaError_t launch_gradient_f32(const float *coeff, const float *coeff_adj, const float *dL_dH, int64_t npix, int K,
                                 double g, double area, float *d_mua, float *d_mus, cudaStream_t s);
+
+// Host-side argument checks shared by every entry point that takes these structs (mcr_api.cu).
+int check_medium(const mcr_medium *m);
+int check_run(const mcr_run *r);
+// Also yields the normalised launch direction of a boundary source.
+int check_source(const mcr_source *src, float *dirx, float *dirz);
+// Status from the error bits of the given word (medium before overflow before event limit).
+int status_from_flags(unsigned flags);
+// mc_forward_noalloc's latched error bits on the current device, read and cleared on stream s
+// (MCR_OK when that entry point never ran on this device); synchronises s (mcr_noalloc.cu).
+int noalloc_take_flags(cudaStream_t s);
 
 // Frees the 3D transport's workspace on device dev (mcr3.cu).
 int release_workspace3(int dev);

@@ -22,7 +22,15 @@ constexpr size_t kScratchBytes = size_t(16) << 20;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Layout inside g_scratch: [0, 512) counters and flags, then the packed medium, then the tally.
-constexpr size_t kOffWork = 0, kOffStats = 64, kOffFlags = 256, kSmall = 512;
+// The flags word holds the current call's error bits (the transport reads its medium bit);
+// the latched word collects the bits of every call until mc_check reads and clears it.
+constexpr size_t kOffWork = 0, kOffStats = 64, kOffFlags = 256, kOffLatched = 260, kSmall = 512;
+
+// Moves the previous call's error bits into the latched word and clears them for this call.
+__global__ void k_latch_flags(unsigned *flags, unsigned *latched) {
+  *latched |= *flags;
+  *flags = 0u;
+}
 
 constexpr int kMaxDev = 64;
 std::mutex g_setup_mu;
@@ -30,12 +38,13 @@ unsigned char *g_scratch_ptr[kMaxDev];  // device address of g_scratch, per devi
 
 // Device address of g_scratch on the current device.  In host code `g_scratch` names a host-side
 // stand-in, not device memory, so the address is asked from the runtime once per device (with
-// that device current) and cached.
-int scratch_address(unsigned char **out) {
+// that device current) and cached.  With lookup = false only an address already cached is
+// returned (nullptr if this device never ran the entry point).
+int scratch_address(unsigned char **out, bool lookup = true) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return MCR_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] && lookup) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
@@ -56,45 +65,37 @@ extern "C" {
 int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_run *run, float *coeff,
                        void *stream) {
   using namespace mcr;
-  // argument checks (same rules as mc_forward)
-  if (!med || !med->mua || !med->mus || !src || !run || !coeff) return MCR_ERR_ARG;
-  if (med->nx <= 0 || med->nz <= 0 || !(med->dx > 0.f) || !isfinite(med->dx)) return MCR_ERR_ARG;
-  if (!(med->g > -1.f && med->g < 1.f)) return MCR_ERR_ARG;
-  if (run->K < 0 || run->K > MCR_MAX_K || !(run->roulette_p > 0.f && run->roulette_p <= 1.f)) return MCR_ERR_ARG;
-  if (!(run->w_threshold >= 0.f) || !isfinite(run->w_threshold)) return MCR_ERR_ARG;
-  if (run->first_packet + run->n_packets < run->first_packet) return MCR_ERR_ARG;
+  // the same argument checks as mc_forward
+  int rc;
+  if ((rc = check_medium(med)) || (rc = check_run(run))) return rc;
+  if (!coeff) return MCR_ERR_ARG;
   if (run->sectors) return MCR_ERR_ARG;  // the sector tally runs through mc_forward only
-  if (src->kind < MCR_PENCIL || src->kind > MCR_ANGULAR_POINT) return MCR_ERR_ARG;
-  if (src->kind == MCR_ANGULAR_POINT && !angular_density_ok(*src)) return MCR_ERR_ARG;
-  if (!isfinite(src->x0) || !isfinite(src->z0) || !isfinite(src->x1) || !isfinite(src->z1) || !isfinite(src->power))
-    return MCR_ERR_ARG;
   float dirx = 0.f, dirz = 1.f;
-  if (src->kind == MCR_PENCIL || src->kind == MCR_LINE) {
-    const double nrm = sqrt((double)src->dir_x * src->dir_x + (double)src->dir_z * src->dir_z);
-    if (!(nrm > 0.0) || !isfinite(nrm)) return MCR_ERR_ARG;
-    dirx = (float)(src->dir_x / nrm);
-    dirz = (float)(src->dir_z / nrm);
-  }
+  if (!src) return MCR_ERR_ARG;
+  if ((rc = check_source(src, &dirx, &dirz))) return rc;
   // size limits of the fixed scratch: one transport launch (no FP64 chunk accumulator)
   if (run->n_packets > kChunkPackets) return MCR_ERR_SCRATCH;
   const int64_t npix = (int64_t)med->nx * med->nz;
   const int C = 2 * run->K + 1, Cpad = tally_row_words(C);
   const size_t mu_bytes = round256((size_t)npix * sizeof(float4));
   const size_t tally_bytes = (size_t)npix * Cpad * 8;
-  if (npix > ((int64_t)1 << 30) || kSmall + mu_bytes + tally_bytes > kScratchBytes) return MCR_ERR_SCRATCH;
+  if (kSmall + mu_bytes + tally_bytes > kScratchBytes) return MCR_ERR_SCRATCH;
 
   unsigned char *base = nullptr;
-  int rc = scratch_address(&base);
-  if (rc) return rc;
+  if ((rc = scratch_address(&base))) return rc;
   unsigned long long *work = reinterpret_cast<unsigned long long *>(base + kOffWork);
   DevStats *stats = reinterpret_cast<DevStats *>(base + kOffStats);
   unsigned *flags = reinterpret_cast<unsigned *>(base + kOffFlags);
+  unsigned *latched = reinterpret_cast<unsigned *>(base + kOffLatched);
   float4 *mu = reinterpret_cast<float4 *>(base + kSmall);
   unsigned long long *tally = reinterpret_cast<unsigned long long *>(base + kSmall + mu_bytes);
 
   cudaStream_t s = (cudaStream_t)stream;
-  // the array keeps the previous call's contents: clear counters, flags and the tally
-  if (cudaMemsetAsync(base, 0, kSmall, s) != cudaSuccess) return MCR_ERR_CUDA;
+  // the array keeps the previous call's contents: clear the counters and the tally, and move the
+  // previous call's error bits into the latched word (read by mc_check)
+  if (cudaMemsetAsync(base, 0, kOffFlags, s) != cudaSuccess) return MCR_ERR_CUDA;
+  k_latch_flags<<<1, 1, 0, s>>>(flags, latched);
+  if (cudaGetLastError() != cudaSuccess) return MCR_ERR_CUDA;
   if (cudaMemsetAsync(tally, 0, tally_bytes, s) != cudaSuccess) return MCR_ERR_CUDA;
   if (launch_pack_medium(med->mua, med->mus, mu, npix, flags, s) != cudaSuccess) return MCR_ERR_CUDA;
 
@@ -147,3 +148,20 @@ int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_r
 }
 
 }  // extern "C"
+
+namespace mcr {
+
+int noalloc_take_flags(cudaStream_t s) {
+  unsigned char *base = nullptr;
+  if (scratch_address(&base, false) != MCR_OK || !base) return MCR_OK;
+  unsigned w[2] = {0u, 0u};  // the last call's bits and the latched bits of the earlier calls
+  if (cudaMemcpyAsync(w, base + kOffFlags, sizeof(w), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return MCR_ERR_CUDA;
+  if ((w[0] | w[1]) && (cudaMemsetAsync(base + kOffFlags, 0, sizeof(w), s) != cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
+    return MCR_ERR_CUDA;
+  return status_from_flags(w[0] | w[1]);
+}
+
+}  // namespace mcr

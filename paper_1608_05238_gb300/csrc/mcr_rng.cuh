@@ -4,10 +4,9 @@
 namespace mcr {
 
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32->64 products and
-// xors, Weyl-incremented key.
-__device__ __forceinline__ uint4 philox4x32_10(unsigned long long pid, unsigned event, unsigned k0,
-                                               unsigned k1) {
-  unsigned c0 = (unsigned)pid, c1 = (unsigned)(pid >> 32), c2 = event, c3 = 0u;
+// xors, Weyl-incremented key, on a 4-word counter.
+__device__ __forceinline__ uint4 philox4x32_10_block(uint4 c, unsigned k0, unsigned k1) {
+  unsigned c0 = c.x, c1 = c.y, c2 = c.z, c3 = c.w;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const unsigned lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
@@ -21,6 +20,12 @@ __device__ __forceinline__ uint4 philox4x32_10(unsigned long long pid, unsigned 
     k1 += 0xBB67AE85u;
   }
   return make_uint4(c0, c1, c2, c3);
+}
+
+// The block of event `event` of packet `pid`: counter (pid_lo, pid_hi, event, 0).
+__device__ __forceinline__ uint4 philox4x32_10(unsigned long long pid, unsigned event, unsigned k0,
+                                               unsigned k1) {
+  return philox4x32_10_block(make_uint4((unsigned)pid, (unsigned)(pid >> 32), event, 0u), k0, k1);
 }
 
 // Uniform in (0,1): ((x >> 9) + 1/2) 2^-23, exact in FP32.  Built from the bits: 1 + m 2^-23

@@ -32,6 +32,8 @@
 //    64-bit conversion runs on the FP64 pipe, which is narrow on this part).
 #include <math_constants.h>
 
+#include <mutex>
+
 #include "mcr_internal.h"
 #include "mcr_rng.cuh"
 
@@ -530,6 +532,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
   w_esc = warp_sum(w_esc);
   w_rr = warp_sum(w_rr);
   w_kill = warp_sum(w_kill);
+  if (lane == 0 && c_evl) atomicOr(p.flags, kFlagEventLimit);
   if (lane == 0 && c_launch) {
     DevStats *s = p.stats;
     atomicAdd(&s->launched, (unsigned long long)c_launch);
@@ -563,6 +566,10 @@ size_t shared_tally_bytes(const TransportParams &p) {
 
 // Opts the kernel into `smem` bytes of dynamic shared memory (once per device) and returns how
 // many blocks of `threads` fit on one SM.
+// Guards the per-instantiation caches of the opted-in shared-memory size: entry points that
+// do not hold the workspace lock (mc_forward_noalloc) reach them from any host thread.
+std::mutex g_attr_mu;
+
 template <int NP, bool BATCH, bool MERGE, bool STALLY = false>
 cudaError_t blocks_per_sm(int threads, size_t smem, int *per_sm) {
   static int configured[64];  // largest dynamic smem opted in, per device
@@ -573,10 +580,14 @@ cudaError_t blocks_per_sm(int threads, size_t smem, int *per_sm) {
     *per_sm = 0;
     return cudaSuccess;
   }
-  if (dev >= 64 || configured[dev] < (int)smem) {
-    e = cudaFuncSetAttribute(k_transport<NP, BATCH, MERGE, STALLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (dev < 64) configured[dev] = (int)smem;
+  {
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (dev >= 64 || configured[dev] < (int)smem) {
+      e = cudaFuncSetAttribute(k_transport<NP, BATCH, MERGE, STALLY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+      if (dev < 64) configured[dev] = (int)smem;
+    }
   }
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_transport<NP, BATCH, MERGE, STALLY>, threads, smem);
 }

@@ -27,7 +27,9 @@ OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_EVENT_LIMIT, ERR_TALLY_OVERFLOW, ERR_MEDIU
 # every symbol declared in include/mcr.h
 EXPORTS = ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_run_batch", "mc_h_eps", "mc_eps",
            "mc_adjoint_source", "mc_gradient", "mc_gradient_f32", "mc_check", "mc_last_run_info",
-           "mc_release_workspace", "mc_status_string", "mc_version", "mc_reduction_probe")
+           "mc_release_workspace", "mc_status_string", "mc_version")
+# measurement and test entry points (include/mcr_diag.h), not part of the method's interface
+DIAG_EXPORTS = ("mc_reduction_probe", "mc_philox_blocks")
 MAX_BATCH = 64
 ERR_SCRATCH = -7
 
@@ -105,6 +107,9 @@ def load() -> C.CDLL:
         lib.mc_eps.argtypes = [C.c_int64, C.c_double, vp, vp, vp, vp, vp]
         lib.mc_check.argtypes = [vp]
         lib.mc_reduction_probe.argtypes = [vp, C.c_int64, C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32, vp]
+        lib.mc_philox_blocks.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_int32,
+                                         C.POINTER(C.c_uint32)]
+        lib.mc_philox_blocks.restype = C.c_int
         lib.mc_last_run_info.argtypes = [C.c_int32, C.POINTER(_Stats), C.POINTER(C.c_float)]
         lib.mc_release_workspace.argtypes = []
         lib.mc_status_string.argtypes = [C.c_int]
@@ -397,6 +402,19 @@ def last_run_info(which: str = "forward"):
 
 def release_workspace():
     _check(load().mc_release_workspace(), "mc_release_workspace")
+
+
+def philox_blocks(counters, keys):
+    """Philox4x32-10 blocks from the transport's device function (``mc_philox_blocks``):
+    ``counters`` [n][4] and ``keys`` [n][2] 32-bit words in, [n][4] words out (a list of tuples)."""
+    n = len(counters)
+    if n != len(keys) or n < 1:
+        raise ValueError("one key per counter, at least one")
+    ctr = (C.c_uint32 * (4 * n))(*[int(w) & 0xFFFFFFFF for c in counters for w in c])
+    key = (C.c_uint32 * (2 * n))(*[int(w) & 0xFFFFFFFF for k in keys for w in k])
+    out = (C.c_uint32 * (4 * n))()
+    _check(load().mc_philox_blocks(ctr, key, n, out), "mc_philox_blocks")
+    return [tuple(out[4 * i:4 * i + 4]) for i in range(n)]
 
 
 def reduction_probe(tally: torch.Tensor, n_coeff: int, iters: int, blocks: int, threads: int = 256, stream=None):

@@ -32,7 +32,7 @@ def test_header_declares_the_boundary():
     for n in ("mc_forward", "mc_adjoint", "mc_gradient", "mc_h_eps", "mc_adjoint_source", "dn_conv", "dn_wgrad",
               "mc3_forward", "mc3_adjoint", "mc3_gradient"):
         assert n in names
-    assert set(names) == set(mcr.EXPORTS) | set(denoise_ops.EXPORTS) | set(mcr3.EXPORTS)
+    assert set(names) == set(mcr.EXPORTS) | set(mcr.DIAG_EXPORTS) | set(denoise_ops.EXPORTS) | set(mcr3.EXPORTS)
 
 
 def test_library_exports_every_declared_symbol(lib):

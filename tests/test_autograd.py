@@ -36,32 +36,46 @@ def _grads(mua, mus, Hm, spec):
 
 
 def test_autograd_gradient_matches_oracle():
-    """Autograd gradients vs the oracle's forward + adjoint runs on the same packets (Eqs. 22, 28)."""
+    """Autograd gradients vs the oracle's forward + adjoint runs on the same packets (Eqs. 22, 28).
+
+    The incoming gradient v = dL/dH is a seeded input of both sides (L = sum v H), so both build
+    the identical FP32 adjoint source q* = -mu_a v / dx^2 and draw the identical adjoint packets;
+    the gradient then differs only by the transport's FP32 rounding and is held to the tally bar
+    (1e-4 of the absolute scale in L1; 2e-4 per well-resolved pixel, a product of two tallies)."""
     nz, nx, dx, g, K, n = 40, 48, 0.1, 0.8, 8, 200_000
     mua, mus = workloads.small_hetero(nz, nx, dx, seed=21)
     Hm = (1.4 * mua * np.exp(-np.linspace(0, 2, nz))[:, None]).astype(np.float32)
     spec = _spec(nx, dx, g, K, n, seed=3, adjoint_seed=4)
-    ga, gs, H, e = _grads(mua, mus, Hm, spec)
-
     dxo, go = f32(dx), f32(g)
+    A = dxo * dxo
+    rng = np.random.default_rng(41)
+    v = (-A * (Hm - 0.9 * mua * np.exp(-np.linspace(0, 1.5, nz))[:, None]) *
+         (1.0 + 0.3 * rng.normal(size=(nz, nx)))).astype(np.float32)
+
+    a = torch.from_numpy(mua).cuda().requires_grad_(True)
+    s_ = torch.from_numpy(mus).cuda().requires_grad_(True)
+    H = HFromMu.apply(a, s_, spec)
+    H.backward(torch.from_numpy(v).cuda())
+    ga, gs = a.grad.double().cpu().numpy(), s_.grad.double().cpu().numpy()
+    e = EpsFromH.apply(H.detach(), torch.from_numpy(Hm).cuda(), spec.dx).item()
+
     m64, s64 = mua.astype(np.float64), mus.astype(np.float64)
     src = spec.sources[0].as_dict()
     fo = oracle.forward(m64, s64, dxo, go, src, RunParams(K=K, n_packets=n, seed=3, stream_id=0)).coeff
     Ho = F.absorbed_energy(m64, fo)
     assert abs(e - F.error_functional(Hm, Ho, dxo)) <= 1e-3 * e
-    v = F.dL_dH_eps(Hm, Ho, dxo)  # the oracle's own H drives its adjoint source
-    q = F.adjoint_source(m64, v.astype(np.float32).astype(np.float64), dxo).astype(np.float32)
+    v64 = v.astype(np.float64)
+    q = F.adjoint_source(m64, v64, dxo).astype(np.float32)
     ao = oracle.adjoint(m64, s64, dxo, go, q, RunParams(K=K, n_packets=n, seed=4, stream_id=1)).coeff
     aabs = oracle.adjoint(m64, s64, dxo, go, np.abs(q), RunParams(K=K, n_packets=n, seed=4, stream_id=1)).coeff
-    oa, os_ = F.dL_dmu(fo, ao, v, dxo, go)
+    oa, os_ = F.dL_dmu(fo, ao, v64, dxo, go)
     # scale of each pixel's products with absolute values (the sums cancel, their terms do not)
-    A = dxo * dxo
-    S = np.abs(v * fo[0]) + A * (np.abs(fo[0] * aabs[0]) / (2 * math.pi) +
-                                 np.sum(np.abs(fo[1:]) * np.abs(aabs[1:]), axis=0) / math.pi)
+    S = np.abs(v64 * fo[0]) + A * (np.abs(fo[0] * aabs[0]) / (2 * math.pi) +
+                                   np.sum(np.abs(fo[1:]) * np.abs(aabs[1:]), axis=0) / math.pi)
     for G, O in ((ga, oa), (gs, os_)):
-        assert np.sum(np.abs(G - O)) <= 5e-4 * np.sum(S)
+        assert np.sum(np.abs(G - O)) <= 1e-4 * np.sum(S)
         hi = S >= 1e-2 * S.max()
-        assert np.max(np.abs(G - O)[hi] / S[hi]) <= 2e-3
+        assert np.max(np.abs(G - O)[hi] / S[hi]) <= 2e-4
 
 
 def test_recompute_reproduces_stored_coefficients_bit_for_bit():

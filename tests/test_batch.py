@@ -107,6 +107,12 @@ def test_collision_merge_is_bit_identical(K):
             assert torch.equal(outs[0], outs[1])
         both = [[o.clone() for o in mcr.run_batch(probs, run, launch=(128, 0, m))] for m in (1, 2)]
         assert all(torch.equal(a, b) for a, b in zip(*both))
+        # a packet ended by the event cap is latched on the device; mc_check reports and clears it
+        try:
+            mcr.check()
+        except mcr.McrError as e:
+            assert run.max_events == 25 and e.status == mcr.ERR_EVENT_LIMIT
+        mcr.check()
 
 
 def test_graph_replay_reproduces_eager_run():

@@ -319,6 +319,13 @@ def test_device_errors_are_reported():
     with pytest.raises(mcr.McrError) as e:
         _gpu_forward(mua, mus, 0.1, 0.0, src, mcr.Run(K=1, n_packets=100, max_events=3), stats=True)
     assert e.value.status == mcr.ERR_EVENT_LIMIT
+    # without a stats request the event cap is latched on the device and reported by mc_check
+    med_ok = mcr.Medium(_dev(mua), _dev(mus), 0.1, 0.0)
+    mcr.forward(med_ok, mcr.Source(**src), mcr.Run(K=1, n_packets=100, max_events=3))
+    with pytest.raises(mcr.McrError) as e:
+        mcr.check()
+    assert e.value.status == mcr.ERR_EVENT_LIMIT
+    mcr.check()
     bad = mua.copy()
     bad[2, 3] = -1.0
     med = mcr.Medium(_dev(bad), _dev(mus), 0.1, 0.0)

@@ -6,6 +6,7 @@ transport equation, or an independent numerical construction (ray-pixel chords,
 quadrature).  The finite-difference gradient pins live in test_oracle_gradients.py.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -33,6 +34,26 @@ def test_philox_uniform_and_independent():
     # counter and key both matter
     assert not np.array_equal(oracle.philox4x32_10((0, 0, 0, 0), (0, 0)), oracle.philox4x32_10((1, 0, 0, 0), (0, 0)))
     assert not np.array_equal(oracle.philox4x32_10((0, 0, 0, 0), (0, 0)), oracle.philox4x32_10((0, 0, 0, 0), (1, 0)))
+
+
+def _philox_kat():
+    """The published Philox4x32-10 known-answer vectors (tests/golden/philox4x32_10_kat.txt)."""
+    rows = []
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")):
+        if line.strip() and not line.startswith("#"):
+            w = [int(x, 16) for x in line.split()]
+            rows.append((tuple(w[0:4]), tuple(w[4:6]), tuple(w[6:10])))
+    return rows
+
+
+def test_philox_known_answers():
+    """The oracle's Philox4x32-10 reproduces the generator's published known answers (zero counter
+    and key, all-ones counter and key, and the pi-digits vector): a swapped output word, a wrong
+    multiplier or Weyl constant, or a wrong round count fails all three."""
+    kat = _philox_kat()
+    assert len(kat) == 3
+    for ctr, key, want in kat:
+        assert tuple(int(v) for v in oracle.philox4x32_10(ctr, key)) == want
 
 
 def test_uniform_map_exact_in_fp32():
