@@ -9,8 +9,11 @@ mc_gradient_f32), all libmcr kernels on one stream.  Metric: photons/s (forward 
 per second); the gradient evaluations per second are the same number divided by 2e7.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun (N > 1) every rank runs an independent replica (its own seeds) and rank 0
-prints the whole-job rate (weak scaling, no data exchange).
+Under torchrun (N > 1) the ranks share the packets of ONE gradient evaluation: each rank runs its
+contiguous range of every forward and adjoint run (1e7 + 1e7 packets per rank, so the work per GPU
+stays fixed: weak scaling) into 64-bit fixed-point sums, one int64 all-reduce per run makes them
+complete and bit-identical to a single GPU running all packets, and rank 0 prints the whole-job
+rate.  ``--replicas`` runs independent replicas instead (own seeds, no data exchange).
 """
 from __future__ import annotations
 
@@ -49,6 +52,8 @@ def _args():
                     help="packets per forward and per adjoint run (default 1e7 for grad256, 2e7 for large1024)")
     ap.add_argument("--cpu-sample", type=int, default=200_000, help="oracle packets (fwd and adj) for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--replicas", action="store_true",
+                    help="N > 1: independent replicas instead of one packet-sharded gradient evaluation")
     ap.add_argument("--no-grad-error", action="store_true", help="skip the gradient-error measurement")
     ap.add_argument("--no-red-probe", action="store_true", help="skip the tally-reduction ceiling measurement")
     ap.add_argument("--plain-gd", action="store_true", help="invert256: no fluence preconditioning")
@@ -298,11 +303,16 @@ def _gpu(args):
     leaf_a = mua.clone().requires_grad_(True)
     leaf_s = mus.clone().requires_grad_(True)
 
+    # N > 1: one problem whose packets are split over the ranks (same seeds on every rank, each
+    # rank's share fixed at the 1-GPU packet count), or independent replicas (own seeds)
+    sharded = world > 1 and not args.replicas
+    share = world if sharded else 1
+
     def step(k, a=leaf_a, s=leaf_s, hm=Hmeas, scale=1):
         # one gradient evaluation through the autograd.Function: H(mu) -> eps -> backward
-        base = replica_seed(rank, k)
-        spec = MCSpec(dx=dx, g=g, sources=srcs, K=w.K, n_packets=scale * per_src, n_adjoint=scale * n, seed=base,
-                      adjoint_seed=base + 1)
+        base = replica_seed(0 if sharded else rank, k)
+        spec = MCSpec(dx=dx, g=g, sources=srcs, K=w.K, n_packets=scale * per_src * share,
+                      n_adjoint=scale * n * share, seed=base, adjoint_seed=base + 1, sharded=sharded)
         a.grad = None
         s.grad = None
         H = HFromMu.apply(a, s, spec)
@@ -423,15 +433,19 @@ def _gpu(args):
         cfg = _workload_config(w, n)
         cfg["work_per_photon"] = {k: {"segments": v[1] / v[0], "collisions": v[2] / v[0]} for k, v in work.items()
                                   if v[0] > 0}
-        cfg.update({"l2": "flushed between timed steps (256 MB write)", "grad_evals_per_s": value / (n_fwd + n),
+        cfg.update({"l2": "flushed between timed steps (256 MB write)", "grad_evals_per_s": value / ((n_fwd + n) * share),
                     "gradient_error_at_this_packet_count": grad_err,
-                    "parallelism": f"replicas{world}" if world > 1 else "single"})
+                    "parallelism": (f"packet-sharded dp{world} (int64 all-reduce of the fixed-point sums)"
+                                    if sharded else f"replicas{world}") if world > 1 else "single"})
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64 (FP64 gradient)", "data": "synthetic",
                "config": cfg, "clocks": clk,
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-               "gpu_launches": (KERNELS_PER_STEP + 3 * (len(srcs) - 1)) * args.steps, "roofline": roofline,
+               # sharded runs add one raw export per run and, for the adjoint, the source strength
+               # (4 CDF kernels) in the finalisation
+               "gpu_launches": (KERNELS_PER_STEP + 3 * (len(srcs) - 1) + (len(srcs) + 5 if sharded else 0))
+               * args.steps, "roofline": roofline,
                "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
     if world > 1:

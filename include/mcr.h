@@ -165,6 +165,38 @@ int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_r
 int mc_adjoint(const mcr_medium *med, const float *qstar, const mcr_run *run, float *coeff_adj,
                mcr_stats *stats, void *stream);
 
+/*
+ * mc_forward_raw / mc_adjoint_raw -- the transport of mc_forward / mc_adjoint (same arguments,
+ * same packets, same random numbers) without the normalisation: `tally` (device, int64
+ * [2K+1][nz][nx], channel-major, caller-owned) receives the run's 64-bit fixed-point sums of
+ * Eqs. 9-11, in quanta of 2^-q weight x mm (q fixed by dx, w_threshold and roulette_p, so equal for
+ * every range of one run), overwritten or, with run->accumulate = 1, added.  The adjoint's odd
+ * orders are NOT yet turned by (-1)^n.  Integer sums are exact and order-free: the sums of
+ * disjoint packet ranges [first_packet, first_packet + n_packets) added together (on one GPU with
+ * accumulate, or across GPUs with an int64 all-reduce) equal the sums of the whole range bit for
+ * bit -- the packet sharding of one problem over several GPUs (the method's packets are
+ * independent, Sec. 3).  At most 2^26 packets per call (MCR_ERR_ARG; split larger ranges);
+ * sectors must be 0.
+ */
+int mc_forward_raw(const mcr_medium *med, const mcr_source *src, const mcr_run *run, int64_t *tally,
+                   mcr_stats *stats, void *stream);
+int mc_adjoint_raw(const mcr_medium *med, const float *qstar, const mcr_run *run, int64_t *tally,
+                   mcr_stats *stats, void *stream);
+
+/*
+ * mc_finalize -- coefficients from raw sums (Sec. 3.1 normalisation; Sec. 4's turn by pi):
+ * coeff (device [2K+1][nz][nx] FP32, written or, with run->accumulate = 1, added to) =
+ * sign * tally * 2^-q * S / (N_p dx^2), with N_p = run->n_packets (the TOTAL of all ranges
+ * summed into `tally`), q as for the raw calls (run->w_threshold, run->roulette_p, med->dx).
+ * Exactly one of `src` (forward: S = src->power, sign +1) and `qstar` (adjoint: S = 2 pi dx^2
+ * sum|q*| as mc_adjoint quantises it, sign (-1)^n on order n) is non-NULL.  Bit-identical to
+ * what mc_forward / mc_adjoint return for the whole range when N_p <= 2^26 (above, those sum
+ * their 2^26-packet chunks in FP64 and the two agree to FP64 rounding).  A sum within 2 bits of
+ * overflow is latched (MCR_ERR_TALLY_OVERFLOW at the next mc_check).
+ */
+int mc_finalize(const mcr_medium *med, const mcr_source *src, const float *qstar, const mcr_run *run,
+                const int64_t *tally, float *coeff, void *stream);
+
 #define MCR_MAX_BATCH 64
 
 /* One problem of a batched launch: its own medium, source (forward) or q* (adjoint), packets,

@@ -58,7 +58,7 @@ class _Run(C.Structure):
     _fields_ = [("K", C.c_int32), ("n_threads", C.c_int32), ("n_packets", C.c_uint64),
                 ("first_packet", C.c_uint64), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
                 ("max_scatter", C.c_uint32), ("max_events", C.c_uint32), ("w_threshold", C.c_double),
-                ("roulette_p", C.c_float), ("sectors", C.c_uint32)]
+                ("roulette_p", C.c_float), ("sectors", C.c_uint32), ("fixed_q", C.c_int32), ("fixed", C.c_uint32)]
 
 
 class _Medium3(C.Structure):
@@ -126,6 +126,7 @@ class RunParams:
     roulette_p: float = 0.1
     n_threads: int = 0
     sectors: int = 0   # > 0: discrete-ordinates tally in that many equal sectors instead of harmonics
+    fixed_q: int | None = None  # set: every deposit term rounded to a multiple of 2^-fixed_q (integer sums)
 
 
 @dataclass
@@ -149,7 +150,7 @@ def _run(p: RunParams):
     nt = p.n_threads or (os.cpu_count() or 1)
     nt = max(1, min(nt, max(1, p.n_packets)))
     return _Run(p.K, nt, p.n_packets, p.first_packet, p.seed, p.stream_id, p.max_scatter, p.max_events,
-                p.w_threshold, p.roulette_p, p.sectors)
+                p.w_threshold, p.roulette_p, p.sectors, int(p.fixed_q or 0), 1 if p.fixed_q is not None else 0)
 
 
 def _stats_dict(st: _Stats) -> dict:
@@ -171,6 +172,39 @@ def _finish(raw, sq, n_packets, S, dx, st, sectors=0, volume_power=2) -> Result:
         mean = (raw.sum(axis=0) if sectors else raw[0]) / n_packets
         var = np.maximum(sq / n_packets - mean * mean, 0.0) / (n_packets - 1) * (S / A) ** 2
     return Result(coeff, var, _stats_dict(st), S)
+
+
+def _source(source: dict) -> _Source:
+    ac, as_ = list(source.get("ang_c", ())), list(source.get("ang_s", ()))
+    n_ang = max(len(ac), len(as_))
+    if n_ang > MAX_ANG:
+        raise ValueError(f"at most {MAX_ANG} angular harmonics")
+    ac, as_ = ac + [0.0] * (MAX_ANG - len(ac)), as_ + [0.0] * (MAX_ANG - len(as_))
+    return _Source(int(source["kind"]), float(source.get("x0", 0.0)), float(source.get("z0", 0.0)),
+                   float(source.get("x1", 0.0)), float(source.get("z1", 0.0)), float(source.get("dir_x", 0.0)),
+                   float(source.get("dir_z", 1.0)), float(source.get("power", 1.0)), n_ang,
+                   (C.c_double * MAX_ANG)(*map(float, ac)), (C.c_double * MAX_ANG)(*map(float, as_)))
+
+
+def forward_sums(mua, mus, dx, g, source: dict, run: RunParams) -> np.ndarray:
+    """Unnormalised tally sums of a forward run over packets [first_packet, first_packet + n_packets),
+    [2K+1, nz, nx].  With ``run.fixed_q`` set every deposit term is rounded to a multiple of
+    2^-fixed_q, and the sums are returned as int64 in units of that quantum: then the sums of
+    disjoint packet ranges add up exactly to the sums of their union."""
+    lib = _load()
+    m, keep = _medium(mua, mus, dx, g)
+    s = _source(source)
+    nz, nx = keep[0].shape
+    raw = np.zeros((run.sectors or 2 * run.K + 1, nz, nx), dtype=np.float64)
+    st = _Stats()
+    rc = lib.orc_forward_raw(C.byref(m), C.byref(s), C.byref(_run(run)), raw.ctypes.data_as(C.POINTER(C.c_double)),
+                             None, C.byref(st))
+    if rc != 0:
+        raise ValueError(f"oracle forward: status {rc}")
+    if run.fixed_q is None:
+        return raw
+    assert np.abs(raw).max() < 2.0 ** 53, "fixed-point sums beyond FP64's exact integers"
+    return raw.astype(np.int64)
 
 
 def forward(mua, mus, dx, g, source: dict, run: RunParams, with_variance: bool = False) -> Result:

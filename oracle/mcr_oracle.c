@@ -110,6 +110,12 @@ typedef struct {
    * `sectors` equal angular sectors [m dth, (m+1) dth), dth = 2 pi / sectors, of theta in
    * [0, 2 pi) instead of the 2K+1 harmonics; 0: harmonics */
   uint32_t sectors;
+  /* fixed != 0 (2D tally): every deposit term (t, t cos n theta, t sin n theta) is rounded to the nearest
+   * multiple of 2^-fixed_q before it is summed, so that the sums are integers (in units of
+   * 2^-fixed_q, exact in FP64 while below 2^53) and the sums of disjoint packet ranges add up
+   * exactly -- the fixed-point form of the tally (the normalisation of Sec. 3.1 then applies) */
+  int32_t fixed_q;
+  uint32_t fixed;
 } orc_run;
 
 typedef struct {
@@ -258,10 +264,19 @@ static void orc_deposit(orc_job *j, int64_t pix, double t, double theta_tally) {
     }
     return;
   }
-  T[pix] += t; /* a_0: Eq. 9 */
-  for (int n = 1; n <= K; ++n) {
-    T[(int64_t)(2 * n - 1) * npix + pix] += t * cos(n * theta_tally); /* a_n: Eq. 10 */
-    T[(int64_t)(2 * n) * npix + pix] += t * sin(n * theta_tally);     /* b_n: Eq. 11 */
+  if (j->run->fixed) { /* the same terms, each rounded to the quantum 2^-fixed_q */
+    const int q = j->run->fixed_q;
+    T[pix] += nearbyint(ldexp(t, q));
+    for (int n = 1; n <= K; ++n) {
+      T[(int64_t)(2 * n - 1) * npix + pix] += nearbyint(ldexp(t * cos(n * theta_tally), q));
+      T[(int64_t)(2 * n) * npix + pix] += nearbyint(ldexp(t * sin(n * theta_tally), q));
+    }
+  } else {
+    T[pix] += t; /* a_0: Eq. 9 */
+    for (int n = 1; n <= K; ++n) {
+      T[(int64_t)(2 * n - 1) * npix + pix] += t * cos(n * theta_tally); /* a_n: Eq. 10 */
+      T[(int64_t)(2 * n) * npix + pix] += t * sin(n * theta_tally);     /* b_n: Eq. 11 */
+    }
   }
   if (j->sq) {
     if (j->pk[pix] == 0.0) j->touched[j->n_touched++] = pix;

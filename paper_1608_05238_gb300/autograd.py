@@ -22,7 +22,7 @@ from dataclasses import dataclass, field, replace
 
 import torch
 
-from . import mcr, mcr3
+from . import mcr, mcr3, shard
 
 
 @dataclass
@@ -41,6 +41,8 @@ class MCSpec:
     w_threshold: float = 1e-4
     roulette_p: float = 0.1
     max_events: int = 10_000_000
+    sharded: bool = False             # split every run's packets over the ranks of torch.distributed's
+                                      # default group (exact int64 all-reduce of the fixed-point sums)
 
     def forward_run(self, s: int) -> mcr.Run:
         return mcr.Run(K=self.K, n_packets=self.n_packets, seed=self.seed, stream_id=2 * s,
@@ -60,10 +62,16 @@ class MCSpec:
 def forward_coefficients(med: mcr.Medium, spec: MCSpec) -> torch.Tensor:
     """Forward coefficients of the whole illumination (sum over ``spec.sources``, added by the
     library's finalize kernel: the RTE is linear in the source)."""
-    coeff = mcr.forward(med, spec.sources[0], spec.forward_run(0))
+    fwd = shard.forward if spec.sharded else mcr.forward
+    coeff = fwd(med, spec.sources[0], spec.forward_run(0))
     for s in range(1, len(spec.sources)):
-        mcr.forward(med, spec.sources[s], replace(spec.forward_run(s), accumulate=True), out=coeff)
+        fwd(med, spec.sources[s], replace(spec.forward_run(s), accumulate=True), out=coeff)
     return coeff
+
+
+def adjoint_coefficients(med: mcr.Medium, q: torch.Tensor, spec: MCSpec) -> torch.Tensor:
+    """Adjoint coefficients from q* (packets split over the ranks when ``spec.sharded``)."""
+    return (shard.adjoint if spec.sharded else mcr.adjoint)(med, q, spec.adjoint_run())
 
 
 class HFromMu(torch.autograd.Function):
@@ -93,7 +101,7 @@ class HFromMu(torch.autograd.Function):
         med = mcr.Medium(mua_c, mus_c, spec.dx, spec.g)
         v = grad_H.detach().float().contiguous()
         q = mcr.adjoint_source(med, v)
-        coeff_adj = mcr.adjoint(med, q, spec.adjoint_run())
+        coeff_adj = adjoint_coefficients(med, q, spec)
         coeff = forward_coefficients(med, spec) if ctx.recompute else saved[2]
         d_mua, d_mus = mcr.gradient(med, coeff, coeff_adj, v, dtype=torch.float32)
         return (d_mua if ctx.needs_input_grad[0] else None, d_mus if ctx.needs_input_grad[1] else None, None)

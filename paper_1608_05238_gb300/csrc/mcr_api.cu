@@ -112,8 +112,10 @@ struct HostProblem {
 
 // Enqueues the whole sequence for `probs` on stream s: pack media, source CDFs, zero tallies,
 // transport launch(es), finalize per problem.  `slot` selects the run counters / events.
+// With raw_out (one problem of at most kChunkPackets packets) the run's fixed-point sums are
+// exported channel-major instead of being finalised.
 int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const TransportLaunch &cfg, int slot,
-            mcr_stats *stats, cudaStream_t s) {
+            mcr_stats *stats, cudaStream_t s, long long *raw_out = nullptr) {
   const int np = (int)probs.size();
   const int C = common->sectors ? (int)common->sectors : 2 * common->K + 1, Cpad = tally_row_words(C);
   // a single problem may exceed one launch's packet budget (chunks + FP64 flush); a batch may not
@@ -224,7 +226,11 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
     MCR_TRY_CUDA(cudaEventRecord(w->ev_stop[slot], s));
     w->ran[slot] = true;
   }
-  for (int i = 0; i < np; ++i) {
+  if (raw_out) {
+    const int64_t npix = (int64_t)probs[0].med->nx * probs[0].med->nz;
+    MCR_TRY_CUDA(launch_export_raw(w->tally, npix, C, Cpad, common->accumulate != 0, raw_out, s));
+  }
+  for (int i = 0; i < np && !raw_out; ++i) {
     const HostProblem &h = probs[i];
     const int64_t npix = (int64_t)h.med->nx * h.med->nz;
     const double area = (double)h.med->dx * (double)h.med->dx;
@@ -248,17 +254,19 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
   return MCR_OK;
 }
 
-// The shared body of mc_forward and mc_adjoint.
+// The shared body of mc_forward and mc_adjoint (and of their raw forms, raw != NULL).
 int run_mc(const mcr_medium *med, const mcr_source *src, const float *qstar, const mcr_run *run, float *coeff,
-           mcr_stats *stats, cudaStream_t s) {
+           mcr_stats *stats, cudaStream_t s, long long *raw = nullptr) {
   int rc;
   if ((rc = check_medium(med)) || (rc = check_run(run))) return rc;
-  if (!coeff) return MCR_ERR_ARG;
+  if (!coeff && !raw) return MCR_ERR_ARG;
   if (qstar && run->sectors) return MCR_ERR_ARG;  // the sector tally is a forward-only study
+  // raw sums: harmonic tallies of one launch (longer runs add ranges with accumulate)
+  if (raw && (run->sectors || run->n_packets > kChunkPackets)) return MCR_ERR_ARG;
   HostProblem h{med, src, qstar, run->n_packets, run->first_packet, run->seed, run->stream_id, coeff, 0.f, 1.f};
   if (!qstar && (rc = check_source(src, &h.dirx, &h.dirz))) return rc;
   std::lock_guard<std::mutex> lock(g_mu);
-  return enqueue({h}, run, TransportLaunch{0, 0, 0, 0}, qstar ? 1 : 0, stats, s);
+  return enqueue({h}, run, TransportLaunch{0, 0, 0, 0}, qstar ? 1 : 0, stats, s, raw);
 }
 
 }  // namespace
@@ -275,6 +283,51 @@ int mc_adjoint(const mcr_medium *med, const float *qstar, const mcr_run *run, fl
                void *stream) {
   if (!qstar) return MCR_ERR_ARG;
   return run_mc(med, nullptr, qstar, run, coeff_adj, stats, (cudaStream_t)stream);
+}
+
+int mc_forward_raw(const mcr_medium *med, const mcr_source *src, const mcr_run *run, int64_t *tally,
+                   mcr_stats *stats, void *stream) {
+  if (!src || !tally) return MCR_ERR_ARG;
+  return run_mc(med, src, nullptr, run, nullptr, stats, (cudaStream_t)stream, reinterpret_cast<long long *>(tally));
+}
+
+int mc_adjoint_raw(const mcr_medium *med, const float *qstar, const mcr_run *run, int64_t *tally, mcr_stats *stats,
+                   void *stream) {
+  if (!qstar || !tally) return MCR_ERR_ARG;
+  return run_mc(med, nullptr, qstar, run, nullptr, stats, (cudaStream_t)stream, reinterpret_cast<long long *>(tally));
+}
+
+int mc_finalize(const mcr_medium *med, const mcr_source *src, const float *qstar, const mcr_run *run,
+                const int64_t *tally, float *coeff, void *stream) {
+  int rc;
+  if ((rc = check_medium(med)) || (rc = check_run(run))) return rc;
+  if (!tally || !coeff || run->sectors || (src == nullptr) == (qstar == nullptr)) return MCR_ERR_ARG;
+  float dirx, dirz;
+  if (src && (rc = check_source(src, &dirx, &dirz))) return rc;
+  const int64_t npix = (int64_t)med->nx * med->nz;
+  const int C = 2 * run->K + 1;
+  const double area = (double)med->dx * (double)med->dx;
+  const double quantum = ldexp(1.0, -tally_exponent(med->dx, run->w_threshold, run->roulette_p));
+  const double n = (double)(run->n_packets ? run->n_packets : 1);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lock(g_mu);
+  Need need;
+  if (qstar) {
+    need.cdf = ((size_t)npix * 8 + 255) & ~size_t(255);
+    need.block_sums = (size_t)((npix + 255) / 256) * 8;
+  }
+  Workspace *w = nullptr;
+  if ((rc = workspace(need, &w))) return rc;
+  if (qstar) {  // the source strength S of the adjoint run, from q* as mc_adjoint computes it
+    MCR_TRY_CUDA(launch_source_cdf(qstar, npix, w->cdf, w->block_sums, (size_t)((npix + 255) / 256),
+                                   w->qmax_bits(0), s));
+  }
+  const double fixed_scale = (src && run->n_packets) ? (double)src->power / (n * area) : 0.0;
+  MCR_TRY_CUDA(launch_finalize_raw(reinterpret_cast<const long long *>(tally), npix, C, quantum, fixed_scale,
+                                   qstar != nullptr && run->n_packets > 0, w->qmax_bits(0),
+                                   qstar ? w->cdf + (npix - 1) : nullptr, n, qstar != nullptr, run->accumulate != 0,
+                                   coeff, w->flags(), s));
+  return MCR_OK;
 }
 
 int mc_run_batch(const mcr_problem *problems, int32_t n_problems, const mcr_run *common, const mcr_launch *launch,

@@ -149,6 +149,14 @@ cudaError_t launch_finalize(const unsigned long long *tally, const double *acc, 
                             double quantum, double fixed_scale, bool volumetric, const unsigned *qmax_bits,
                             const unsigned long long *cdf_total, double n_packets, bool adjoint, bool accumulate,
                             float *coeff, unsigned *flags, cudaStream_t s);
+// raw fixed-point sums out: out[c][pix] (=, or += with accumulate) tally[pix][c] (int64 quanta)
+cudaError_t launch_export_raw(const unsigned long long *tally, int64_t npix, int C, int Cpad, bool accumulate,
+                              long long *out, cudaStream_t s);
+// channel-major raw sums -> coeff, normalised as launch_finalize
+cudaError_t launch_finalize_raw(const long long *raw, int64_t npix, int C, double quantum, double fixed_scale,
+                                bool volumetric, const unsigned *qmax_bits, const unsigned long long *cdf_total,
+                                double n_packets, bool adjoint, bool accumulate, float *coeff, unsigned *flags,
+                                cudaStream_t s);
 cudaError_t launch_h_eps(const float *mua, const float *a0, const float *Hmeas, int64_t npix, double area, float *H,
                          float *dL_dH, double *partials, size_t partials_cap, double *eps, cudaStream_t s);
 cudaError_t launch_adjoint_source(const float *mua, const float *dL_dH, int64_t npix, double area, float *q,

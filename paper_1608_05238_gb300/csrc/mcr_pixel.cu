@@ -98,6 +98,57 @@ __global__ void k_accumulate(const unsigned long long *__restrict__ tally, int64
   }
 }
 
+// Normalisation S / (N_p A) of a run's sums.  Volumetric: S = 2 pi A qmax total 2^-32 (the source
+// CDF has 2^32 levels of qmax), read on the device; otherwise the host's fixed_scale.
+__device__ __forceinline__ double run_scale(double fixed_scale, int volumetric, const unsigned *qmax_bits,
+                                            const unsigned long long *cdf_total, double n_packets) {
+  if (!volumetric) return fixed_scale;
+  return 2.0 * CUDART_PI * (double)__uint_as_float(*qmax_bits) * (double)(*cdf_total) * (1.0 / 4294967296.0) /
+         n_packets;
+}
+
+// Raw fixed-point sums out, pixel-major [npix][Cpad] -> channel-major [C][npix] int64 (written, or
+// added with `accumulate`); the tile of 32 pixels is staged through shared memory as in k_finalize.
+__global__ void k_export_raw(const unsigned long long *__restrict__ tally, int64_t npix, int C, int Cpad,
+                             int accumulate, long long *__restrict__ out) {
+  extern __shared__ long long tile[];  // [32][Cpad]
+  const int64_t p0 = (int64_t)blockIdx.x * 32;
+  const int npx = npix - p0 < 32 ? (int)(npix - p0) : 32;
+  const int tid = threadIdx.y * 32 + threadIdx.x, nthr = blockDim.x * blockDim.y;
+  const long long *src = reinterpret_cast<const long long *>(tally) + p0 * Cpad;
+  for (int k = tid; k < npx * Cpad; k += nthr) tile[k] = src[k];
+  __syncthreads();
+  for (int c = threadIdx.y; c < C; c += blockDim.y) {
+    if (threadIdx.x < npx) {
+      long long *o = out + (int64_t)c * npix + p0 + threadIdx.x;
+      const long long v = tile[threadIdx.x * Cpad + c];
+      *o = accumulate ? *o + v : v;
+    }
+  }
+}
+
+// Channel-major raw sums (e.g. summed over the packet ranges of several GPUs) -> normalised FP32:
+// coeff[c][pix] (=, or += with `accumulate`) sign * raw * quantum * scale, sign (-1)^n on the
+// channels of order n when `adjoint`.  Flags sums within 2 bits of overflow.
+__global__ void k_finalize_raw(const long long *__restrict__ raw, int64_t npix, int C, double quantum,
+                               double fixed_scale, int volumetric, const unsigned *qmax_bits,
+                               const unsigned long long *cdf_total, double n_packets, int adjoint, int accumulate,
+                               float *__restrict__ coeff, unsigned *flags) {
+  const double scale = run_scale(fixed_scale, volumetric, qmax_bits, cdf_total, n_packets);
+  bool near_overflow = false;
+  const int64_t total = (int64_t)C * npix;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(k / npix);
+    const int n = (c + 1) >> 1;
+    const double sgn = (adjoint && (n & 1)) ? -1.0 : 1.0;
+    const long long v = raw[k];
+    near_overflow |= (v > (1ll << 61)) || (v < -(1ll << 61));
+    const float f = (float)(sgn * ((double)v * quantum * scale));
+    coeff[k] = accumulate ? coeff[k] + f : f;
+  }
+  if (__any_sync(0xFFFFFFFFu, near_overflow) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagOverflow);
+}
+
 // Fixed point (or FP64 accumulator) -> normalised FP32, pixel-major -> channel-major.
 // One block = 32 pixels: the tile [32][Cpad] is staged through shared memory so that both the
 // read (contiguous rows) and the write (32 pixels per channel) are coalesced.
@@ -108,10 +159,7 @@ __global__ void k_finalize(const unsigned long long *__restrict__ tally, const d
   extern __shared__ long long tile[];  // [32][Cpad]
   const int64_t p0 = (int64_t)blockIdx.x * 32;
   const int npx = npix - p0 < 32 ? (int)(npix - p0) : 32;
-  double scale = fixed_scale;
-  // volumetric: S / (N_p A) with S = 2 pi A qmax total 2^-32 (the source CDF has 2^32 levels of qmax)
-  if (volumetric) scale = 2.0 * CUDART_PI * (double)__uint_as_float(*qmax_bits) * (double)(*cdf_total) *
-                          (1.0 / 4294967296.0) / n_packets;
+  const double scale = run_scale(fixed_scale, volumetric, qmax_bits, cdf_total, n_packets);
   const int tid = threadIdx.y * 32 + threadIdx.x, nthr = blockDim.x * blockDim.y;
   bool near_overflow = false;
   if (!acc) {
@@ -249,6 +297,24 @@ cudaError_t launch_finalize(const unsigned long long *tally, const double *acc, 
   k_finalize<<<(unsigned)((npix + 31) / 32), block, smem, s>>>(tally, acc, npix, C, Cpad, quantum, fixed_scale,
                                                               volumetric ? 1 : 0, qmax_bits, cdf_total, n_packets,
                                                               adjoint ? 1 : 0, accumulate ? 1 : 0, coeff, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_raw(const unsigned long long *tally, int64_t npix, int C, int Cpad, bool accumulate,
+                              long long *out, cudaStream_t s) {
+  const dim3 block(32, 8);
+  k_export_raw<<<(unsigned)((npix + 31) / 32), block, (size_t)32 * Cpad * sizeof(long long), s>>>(
+      tally, npix, C, Cpad, accumulate ? 1 : 0, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_raw(const long long *raw, int64_t npix, int C, double quantum, double fixed_scale,
+                                bool volumetric, const unsigned *qmax_bits, const unsigned long long *cdf_total,
+                                double n_packets, bool adjoint, bool accumulate, float *coeff, unsigned *flags,
+                                cudaStream_t s) {
+  k_finalize_raw<<<grid_for((int64_t)C * npix, kThreads), kThreads, 0, s>>>(
+      raw, npix, C, quantum, fixed_scale, volumetric ? 1 : 0, qmax_bits, cdf_total, n_packets, adjoint ? 1 : 0,
+      accumulate ? 1 : 0, coeff, flags);
   return cudaGetLastError();
 }
 

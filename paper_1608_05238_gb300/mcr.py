@@ -25,7 +25,8 @@ MAX_K = 64
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_EVENT_LIMIT, ERR_TALLY_OVERFLOW, ERR_MEDIUM = 0, -1, -2, -3, -4, -5, -6
 
 # every symbol declared in include/mcr.h
-EXPORTS = ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_run_batch", "mc_h_eps", "mc_eps",
+EXPORTS = ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_forward_raw", "mc_adjoint_raw", "mc_finalize",
+           "mc_run_batch", "mc_h_eps", "mc_eps",
            "mc_adjoint_source", "mc_gradient", "mc_gradient_f32", "mc_check", "mc_last_run_info",
            "mc_release_workspace", "mc_status_string", "mc_version")
 # measurement and test entry points (include/mcr_diag.h), not part of the method's interface
@@ -98,6 +99,10 @@ def load() -> C.CDLL:
         lib.mc_forward.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
         lib.mc_forward_noalloc.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run), vp, vp]
         lib.mc_adjoint.argtypes = [C.POINTER(_Medium), vp, C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
+        lib.mc_forward_raw.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run), vp,
+                                       C.POINTER(_Stats), vp]
+        lib.mc_adjoint_raw.argtypes = [C.POINTER(_Medium), vp, C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
+        lib.mc_finalize.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), vp, C.POINTER(_Run), vp, vp, vp]
         lib.mc_run_batch.argtypes = [C.POINTER(_Problem), C.c_int32, C.POINTER(_Run), C.POINTER(_Launch),
                                      C.POINTER(_Stats), vp]
         lib.mc_h_eps.argtypes = [C.POINTER(_Medium), vp, vp, vp, vp, vp, vp]
@@ -116,7 +121,8 @@ def load() -> C.CDLL:
         lib.mc_status_string.restype = C.c_char_p
         lib.mc_version.argtypes = []
         lib.mc_version.restype = C.c_char_p
-        for name in ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_run_batch", "mc_h_eps", "mc_eps",
+        for name in ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_forward_raw", "mc_adjoint_raw",
+                     "mc_finalize", "mc_run_batch", "mc_h_eps", "mc_eps",
                      "mc_adjoint_source", "mc_gradient", "mc_gradient_f32", "mc_check", "mc_last_run_info",
                      "mc_release_workspace"):
             getattr(lib, name).restype = C.c_int
@@ -267,6 +273,63 @@ def adjoint(med: Medium, qstar: torch.Tensor, run: Run, out=None, stats: bool = 
                         C.byref(st) if st is not None else None, _stream(stream))
     _check(rc, "mc_adjoint")
     return (coeff, _stats_dict(st)) if stats else coeff
+
+
+# Packets per raw call (mc_forward_raw / mc_adjoint_raw): longer ranges are added call by call.
+RAW_MAX_PACKETS = 1 << 26
+
+
+def _raw_out(med: Medium, K: int, out):
+    nz, nx = med.shape
+    if out is None:
+        return torch.empty((2 * K + 1, nz, nx), dtype=torch.int64, device=med.mua.device)
+    if not (out.is_cuda and out.dtype == torch.int64 and out.is_contiguous() and
+            tuple(out.shape) == (2 * K + 1, nz, nx)):
+        raise TypeError("raw tally must be a contiguous int64 CUDA tensor [2K+1, nz, nx]")
+    return out
+
+
+def forward_raw(med: Medium, src: Source, run: Run, out=None, stats: bool = False, stream=None):
+    """Raw 64-bit fixed-point sums of a forward run (``mc_forward_raw``), int64 [2K+1, nz, nx];
+    with ``run.accumulate`` added into ``out``.  Sums of disjoint packet ranges add exactly."""
+    lib = load()
+    tally = _raw_out(med, run.K, out)
+    st = _Stats() if stats else None
+    rc = lib.mc_forward_raw(C.byref(med.c()), C.byref(src.c()), C.byref(run.c()), _ptr(tally),
+                            C.byref(st) if st is not None else None, _stream(stream))
+    _check(rc, "mc_forward_raw")
+    return (tally, _stats_dict(st)) if stats else tally
+
+
+def adjoint_raw(med: Medium, qstar: torch.Tensor, run: Run, out=None, stats: bool = False, stream=None):
+    """Raw fixed-point sums of an adjoint run (``mc_adjoint_raw``; odd orders not yet turned)."""
+    lib = load()
+    _dev_f32(qstar, "qstar")
+    if tuple(qstar.shape) != med.shape:
+        raise ValueError("qstar must have the medium's shape")
+    tally = _raw_out(med, run.K, out)
+    st = _Stats() if stats else None
+    rc = lib.mc_adjoint_raw(C.byref(med.c()), _ptr(qstar), C.byref(run.c()), _ptr(tally),
+                            C.byref(st) if st is not None else None, _stream(stream))
+    _check(rc, "mc_adjoint_raw")
+    return (tally, _stats_dict(st)) if stats else tally
+
+
+def finalize(med: Medium, run: Run, tally: torch.Tensor, src: Source | None = None, qstar: torch.Tensor | None = None,
+             out=None, stream=None) -> torch.Tensor:
+    """Coefficients [2K+1, nz, nx] from raw sums (``mc_finalize``): ``run.n_packets`` is the total
+    of all ranges in ``tally``; exactly one of ``src`` (forward) and ``qstar`` (adjoint)."""
+    lib = load()
+    _raw_out(med, run.K, tally)
+    if (src is None) == (qstar is None):
+        raise ValueError("finalize takes exactly one of src / qstar")
+    if qstar is not None:
+        _dev_f32(qstar, "qstar")
+    coeff = _coeff_out(med, run.K, out)
+    rc = lib.mc_finalize(C.byref(med.c()), C.byref(src.c()) if src is not None else None, _ptr(qstar),
+                         C.byref(run.c()), _ptr(tally), _ptr(coeff), _stream(stream))
+    _check(rc, "mc_finalize")
+    return coeff
 
 
 @dataclass
