@@ -36,6 +36,12 @@ UNIT = "photons/s"
 # kernels of libmcr per step: forward (pack, transport, finalize, H) | eps (residual, reduction) |
 # backward (adjoint source | pack, 4 CDF, transport, finalize | gradient)
 KERNELS_PER_STEP = 15
+# The L2's peak rate for reduction sectors on GB300 from ncu (lts__t_sectors_op_red.sum.peak_sustained
+# = 188 sectors per cycle, lts__cycles_elapsed.avg.per_second = 2.017 GHz under load), times 32 B per
+# sector: the ceiling of the transport's 64-bit tally reductions (profiles/k_transport_grad256_l2_reduction.md).
+L2_RED_SECTORS_PER_CYCLE = 188
+L2_CLOCK_HZ = 2.017e9
+L2_RED_PEAK_GBS = L2_RED_SECTORS_PER_CYCLE * L2_CLOCK_HZ * 32 / 1e9
 # DRAM bytes (read + write) per K = 32 transport launch of the grad256 gradient evaluation, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark's forward
 # (40.91 MB) and adjoint (41.56 MB) launches at full size: the tally footprint, read once.
@@ -62,7 +68,7 @@ def _args():
     ap.add_argument("--iters", type=int, default=None, help="invert_rect: iteration cap (default 20 mua, 40 mus)")
     ap.add_argument("--workload", default="grad256",
                     choices=["grad256", "large1024", "batch64", "denoise256", "conv", "invert256", "unet256", "invert_rect",
-                             "sectors", "grad3d"],
+                             "sectors", "grad3d", "equal_error"],
                     help="grad256: the gradient evaluation (default); large1024: the same on 1024^2 px at "
                          "K = 64 with four edge sources; batch64: 64 forward problems in one graph-captured "
                          "batched launch; denoise256: the learned denoiser; conv: one large tensor-core "
@@ -70,7 +76,10 @@ def _args():
                          "unet256: U-Net training step and inference on synthetic maps (profiling case); invert_rect: "
                          "the Sec. 6 reconstructions on the rectangular-inclusion domain (--unknown mua|mus); sectors: "
                          "harmonic vs discrete-ordinates tally (Sec. 3.1); grad3d: the 3D gradient evaluation with "
-                         "spherical-harmonic tallies (--n3 voxels a side, --l3 order)")
+                         "spherical-harmonic tallies (--n3 voxels a side, --l3 order); equal_error: the chosen form "
+                         "(denoised low-count maps) against plain MC at equal reconstruction error (--unknown mua|mus)")
+    ap.add_argument("--pairs", type=int, default=1024, help="equal_error: training pairs per network")
+    ap.add_argument("--train-steps", type=int, default=3000, help="equal_error: Adam steps per network")
     ap.add_argument("--n3", type=int, default=96, help="grad3d: voxels per side")
     ap.add_argument("--l3", type=int, default=4, help="grad3d: spherical-harmonic order L")
     args = ap.parse_args()
@@ -412,13 +421,26 @@ def _gpu(args):
     except Exception:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
-                "traffic": TRANSPORT_DRAM_BYTES.get(w.name), "kernel": "k_transport", "launch_ms": avg_ms, "launches_timed": launches,
+    # the tally reductions go to L2 (the grad256 tally is L2-resident): the bound is the L2's
+    # reduction-sector rate; the HBM ratio is kept as a secondary figure
+    row_words = (C + 15) // 16 * 16 if C > 32 else (C + 3) // 4 * 4
+    in_hbm = w.nx * w.nz * row_words * 8 > 256 << 20  # tallies beyond L2 take their reductions to HBM
+    bound, peak = ("hbm", hbm) if in_hbm else ("l2_reduction", L2_RED_PEAK_GBS)
+    roofline = {"bound": bound, "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
+                "frac": achieved_gbs / peak, "traffic": TRANSPORT_DRAM_BYTES.get(w.name),
+                "kernel": "k_transport", "launch_ms": avg_ms, "launches_timed": launches,
                 "segments_per_launch": avg_segs, "bytes_per_segment": C * 8,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+                "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured): the tally lives in HBM" if in_hbm else
+                                "ncu lts__t_sectors_op_red.sum.peak_sustained (188 sectors/cycle) x L2 clock "
+                                "2.017 GHz x 32 B (of measured peak rate; profiles/k_transport_grad256_l2_reduction.md)"),
+                "achieved_is": "algorithmic reduction payload 8 (2K+1) B per segment / event-timed launch",
+                "hbm": {"peak": hbm, "frac": achieved_gbs / hbm,
+                        "note": "payload rate over the measured HBM copy rate (MEASURED_PEAKS.json hbm_gbs); the "
+                                "payload goes to L2, DRAM sees `traffic` per launch"}}
     if not args.no_red_probe:
         red = l2_reduction_peak(w.nx * w.nz, C)
-        roofline["l2_reduction_peak"] = dict(red, frac=achieved_gbs / red["value"])
+        roofline["reduction_probe"] = dict(red, frac=achieved_gbs / red["value"],
+                                           note="a measured rate of random-row reductions alone, not a ceiling")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -757,6 +779,110 @@ def _invert256(args):
     return 0
 
 
+def _equal_error(args):
+    """The chosen form against plain MC at equal reconstruction error (the paper's Sec. 6 metric,
+    the mean relative error of the reconstructed map).  Both routes run the same reconstruction
+    (inversion.invert: mu_a by fluence-preconditioned descent, or mu_s by backtracking under
+    Eq. 30) on a held-out 256^2 inclusion phantom with K = 16 and the gradient from the autograd
+    Function.  Plain: full MC maps at several packet counts per run.  Chosen: low-count maps
+    through the U-Nets (forward and adjoint, trained here on MC pairs made by the batched launch),
+    judged once per kind by full-count MC (denoised.Denoiser).  The plain curve of error against
+    packets per run, interpolated in log-log, gives the packet count -- and, from the measured time
+    per iteration against packets, the time -- at which plain MC reaches the chosen form's error."""
+    import torch
+    from paper_1608_05238_gb300 import _build, denoise_train as dt, mcr, workloads
+    from paper_1608_05238_gb300.autograd import MCSpec, forward_coefficients
+    from paper_1608_05238_gb300.denoised import Denoiser
+    from paper_1608_05238_gb300.denoiser import UNet
+    from paper_1608_05238_gb300.inversion import invert, mean_relative_error
+    _build.build()
+    K, n, dx, g = 16, 256, 0.05, 0.9
+    n_low, n_high, n_pairs, n_test = 100_000, 10_000_000, args.pairs, 16
+    unknown = args.unknown
+    dev = torch.device("cuda")
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    t0 = time.perf_counter()
+    xf, tf = dt.make_pairs(n_pairs + n_test, n=n, dx=dx, K=K, n_low=n_low, n_high=n_high, vary=True)
+    xa, ta = dt.make_adjoint_pairs(n_pairs + n_test, n=n, dx=dx, K=K, n_low=n_low, n_high=n_high)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    nets = {}
+    t0 = time.perf_counter()
+    for kind, (x, t) in (("forward", (xf, tf)), ("adjoint", (xa, ta))):
+        net = UNet(in_ch=2 * K + 1, seed=1 if kind == "forward" else 2)
+        dt.train(net, x[:n_pairs], t[:n_pairs], steps=args.train_steps, batch=8, lr=1e-3, seed=3)
+        nets[kind] = (net, dt.evaluate(net, x[n_pairs:], t[n_pairs:]))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del xf, tf, xa, ta
+    torch.cuda.empty_cache()
+
+    # the reconstruction: held-out phantom, homogeneous start in the unknown map
+    dx32, g32 = float(np.float32(dx)), float(np.float32(g))
+    mua_t_np, mus_t_np = workloads.inclusion_phantom(n, dx, 3, seed=30_001, mus_range=(5.0, 15.0))
+    mua_t, mus_t = torch.from_numpy(mua_t_np).to(dev), torch.from_numpy(mus_t_np).to(dev)
+    src = [mcr.Source(**workloads.top_line_source(n, dx))]
+    med_t = mcr.Medium(mua_t, mus_t, dx32, g32)
+    Hmeas = mcr.h_eps(med_t, forward_coefficients(med_t, MCSpec(dx=dx32, g=g32, sources=src, K=0,
+                                                                 n_packets=100_000_000, seed=777)))
+    mua0 = torch.full_like(mua_t, 0.01) if unknown == "mua" else mua_t.clone()
+    mus0 = torch.full_like(mus_t, 10.0) if unknown == "mus" else mus_t.clone()
+    iters = args.iters
+    kw = dict(unknowns=(unknown,), iters=iters, tol=1e-12, mua_true=mua_t, mus_true=mus_t)
+    kw.update(precondition=True) if unknown == "mua" else kw.update(armijo=0.2, shrink=0.5)
+    err_of = lambda h: h.rel_err_mua if unknown == "mua" else h.rel_err_mus
+
+    def route(n_pk, denoiser=None):
+        spec = MCSpec(dx=dx32, g=g32, sources=src, K=K, n_packets=n_pk, denoiser=denoiser)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        res = invert(mua0, mus0, Hmeas, spec, seed0=11, **kw)
+        torch.cuda.synchronize()
+        T = time.perf_counter() - a
+        errs = [err_of(h) for h in res.history]
+        tail = errs[-4:] if errs else [mean_relative_error(mua0 if unknown == "mua" else mus0,
+                                                          mua_t if unknown == "mua" else mus_t)]
+        evals = len(res.history) + sum(h.trials for h in res.history)  # gradients + line-search forwards
+        return {"packets_per_run": n_pk, "final_err": float(np.mean(tail)), "errors": errs, "seconds": T,
+                "iterations": len(res.history), "mc_evaluations": evals,
+                "grad_evals_per_s": len(res.history) / T if T > 0 else None}
+
+    route(20_000)  # warm-up (workspaces, kernels)
+    plain = [route(int(m)) for m in (1e5, 2e5, 4e5, 1e6, 2e6, 4e6)]
+    dn = Denoiser(nets["forward"][0], nets["adjoint"][0], n_full=n_high, n_judge=10 * n_low, judge_every=0,
+                  max_rel_err=0.25)
+    chosen = route(n_low, dn)
+    chosen["judge"] = dn.history
+    chosen["fallback"] = dn.fallback
+    # plain MC at the chosen form's error: log-log fit of the plain error against packets per run
+    # (over the counts whose error is still falling), and of its time against packets
+    lm = np.log([p["packets_per_run"] for p in plain])
+    le = np.log([p["final_err"] for p in plain])
+    lt = np.log([p["seconds"] for p in plain])
+    se, ie = np.polyfit(lm, le, 1)
+    st, it_ = np.polyfit(lm, lt, 1)
+    m_eq = float(np.exp((np.log(chosen["final_err"]) - ie) / se)) if se < 0 else None
+    t_eq = float(np.exp(it_ + st * np.log(m_eq))) if m_eq else None
+    e0 = mean_relative_error(mua0 if unknown == "mua" else mus0, mua_t if unknown == "mua" else mus_t)
+    out = {"metric": f"time to equal mean relative {unknown} error: plain MC / (batched + autograd + denoised)",
+           "value": (t_eq / chosen["seconds"]) if t_eq else None, "unit": "speedup at equal error", "n_gpus": 1,
+           "steps": iters, "warmup": 1, "ms_per_step": 1e3 * chosen["seconds"] / max(1, chosen["iterations"]),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64 (FP64 gradient), bf16 U-Net",
+           "data": "synthetic",
+           "config": {"workload": f"equal_error: {unknown} reconstruction, 256x256 px of {dx} mm, held-out 3-inclusion "
+                                  f"phantom (seed 30001), top line source, K={K}, {iters} iterations; U-Nets trained on "
+                                  f"{n_pairs} forward + {n_pairs} adjoint MC pairs ({n_low:.0e} -> {n_high:.0e} packets)",
+                      "initial_err": e0, "pair_generation_s": gen_s, "training_s": train_s,
+                      "heldout_map_errors": {k: v[1] for k, v in nets.items()},
+                      "plain": plain, "chosen": chosen,
+                      "plain_packets_per_run_at_chosen_error": m_eq, "plain_seconds_at_chosen_error": t_eq,
+                      "plain_error_vs_packets_loglog_slope": float(se),
+                      "chosen_grad_evals_per_s": chosen["grad_evals_per_s"]},
+           "cpu_baseline": None}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def _sectors(args):
     """Sec. 3.1's trade-off, measured: the forward transport of the 256^2 workload with the harmonic
     tally at K = 8, 16, 32 against the discrete-ordinates tally at M = 16, 32, 64 sectors -- tally
@@ -1026,6 +1152,8 @@ def main():
         return _unet256(args)
     if args.workload == "invert_rect" and args.impl != "reference":
         return _invert_rect(args)
+    if args.workload == "equal_error" and args.impl != "reference":
+        return _equal_error(args)
     if args.workload == "sectors" and args.impl != "reference":
         return _sectors(args)
     if args.workload == "grad3d" and args.impl != "reference":

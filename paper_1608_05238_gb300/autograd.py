@@ -43,6 +43,8 @@ class MCSpec:
     max_events: int = 10_000_000
     sharded: bool = False             # split every run's packets over the ranks of torch.distributed's
                                       # default group (exact int64 all-reduce of the fixed-point sums)
+    denoiser: object | None = None    # denoised.Denoiser: low-count maps through the U-Nets, judged by
+                                      # (and falling back to) full-count MC
 
     def forward_run(self, s: int) -> mcr.Run:
         return mcr.Run(K=self.K, n_packets=self.n_packets, seed=self.seed, stream_id=2 * s,
@@ -54,24 +56,61 @@ class MCSpec:
                        w_threshold=self.w_threshold, roulette_p=self.roulette_p, max_events=self.max_events)
 
     def should_recompute(self, nz: int, nx: int) -> bool:
+        if self.denoiser is not None:  # keep the (denoised or judged) maps the forward pass used
+            return False
         if self.recompute is not None:
             return bool(self.recompute)
         return self.K > 32 or (2 * self.K + 1) * nz * nx * 4 > self.coeff_budget
 
 
-def forward_coefficients(med: mcr.Medium, spec: MCSpec) -> torch.Tensor:
-    """Forward coefficients of the whole illumination (sum over ``spec.sources``, added by the
-    library's finalize kernel: the RTE is linear in the source)."""
+# seed offset of the full-count runs that judge the denoiser (packets independent of the low-count run)
+JUDGE_SEED = 1_000_003
+
+
+def _mc_forward(med: mcr.Medium, spec: MCSpec, n: int | None = None, seed: int | None = None) -> torch.Tensor:
     fwd = shard.forward if spec.sharded else mcr.forward
-    coeff = fwd(med, spec.sources[0], spec.forward_run(0))
+    run = lambda s: replace(spec.forward_run(s), n_packets=n or spec.n_packets,
+                            seed=spec.seed if seed is None else seed)
+    coeff = fwd(med, spec.sources[0], run(0))
     for s in range(1, len(spec.sources)):
-        fwd(med, spec.sources[s], replace(spec.forward_run(s), accumulate=True), out=coeff)
+        fwd(med, spec.sources[s], replace(run(s), accumulate=True), out=coeff)
     return coeff
 
 
+def _mc_adjoint(med: mcr.Medium, q: torch.Tensor, spec: MCSpec, n: int | None = None,
+                seed: int | None = None) -> torch.Tensor:
+    run = spec.adjoint_run()
+    run = replace(run, n_packets=n or run.n_packets, seed=run.seed if seed is None else seed)
+    return (shard.adjoint if spec.sharded else mcr.adjoint)(med, q, run)
+
+
+def _denoised(kind: str, spec: MCSpec, mc) -> torch.Tensor:
+    """A map through the spec's denoiser: mc(n, seed) runs the MC; full-count MC judges and replaces
+    the denoised map on judged evaluations, and after a failed judgment on every evaluation."""
+    dn = spec.denoiser
+    if dn.fallback:
+        return mc(dn.n_full, None)
+    low = mc(None, None)
+    out = dn.denoise(kind, low)
+    if dn.wants_judge(kind):
+        out = dn.judge(kind, low, out, mc(dn.n_judge or dn.n_full, spec.seed + JUDGE_SEED))
+    return out
+
+
+def forward_coefficients(med: mcr.Medium, spec: MCSpec) -> torch.Tensor:
+    """Forward coefficients of the whole illumination (sum over ``spec.sources``, added by the
+    library's finalize kernel: the RTE is linear in the source); denoised with ``spec.denoiser``."""
+    if spec.denoiser is None:
+        return _mc_forward(med, spec)
+    return _denoised("forward", spec, lambda n, seed: _mc_forward(med, spec, n, seed))
+
+
 def adjoint_coefficients(med: mcr.Medium, q: torch.Tensor, spec: MCSpec) -> torch.Tensor:
-    """Adjoint coefficients from q* (packets split over the ranks when ``spec.sharded``)."""
-    return (shard.adjoint if spec.sharded else mcr.adjoint)(med, q, spec.adjoint_run())
+    """Adjoint coefficients from q* (packets split over the ranks when ``spec.sharded``; denoised
+    with ``spec.denoiser``)."""
+    if spec.denoiser is None:
+        return _mc_adjoint(med, q, spec)
+    return _denoised("adjoint", spec, lambda n, seed: _mc_adjoint(med, q, spec, n, seed))
 
 
 class HFromMu(torch.autograd.Function):

@@ -490,7 +490,7 @@ __global__ void k_sample_scale(const float *__restrict__ src, int C, long long H
   __shared__ double red[kT / 32];
   const float *x = src + (size_t)blockIdx.x * C * HW;
   double acc = 0.0;
-  for (long long i = threadIdx.x; i < HW; i += kT) acc += x[i];
+  for (long long i = threadIdx.x; i < HW; i += kT) acc += fabsf(x[i]);  // signed (adjoint) maps: mean |a_0|
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;

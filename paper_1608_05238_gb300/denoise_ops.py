@@ -210,7 +210,8 @@ def pack_input(src: torch.Tensor, scale: torch.Tensor, dst: torch.Tensor, stream
 
 
 def sample_scale(src: torch.Tensor, scale: torch.Tensor, stream=None):
-    """scale[b] = 1 / mean of channel 0 of the channel-major fp32 maps src [B][C][H][W]."""
+    """scale[b] = 1 / mean |channel 0| of the channel-major fp32 maps src [B][C][H][W] (the mean
+    fluence of forward maps; for the signed adjoint maps the mean magnitude of a_0*)."""
     _call("dn_sample_scale", _p(src), src.shape[0], src.shape[2] * src.shape[3], src.shape[1], _p(scale),
           _stream(stream))
 

@@ -13,10 +13,25 @@ from . import mcr, workloads
 from .denoiser import UNet, sample_scale
 
 
+def training_medium(n: int, dx: float, seed: int, vary: bool):
+    """The medium of training pair ``seed``: a 3-inclusion phantom, or with ``vary`` 0-4 inclusions
+    and, for half the pairs, pixel-scale lognormal noise of up to 20 % on mu_a (the noisy estimates
+    a reconstruction passes through).  Input generator only."""
+    if not vary:
+        return workloads.inclusion_phantom(n, dx, 3, seed=seed, margin=min(2.0, 0.15 * n * dx))
+    rng = np.random.default_rng(seed + 7_777_777)
+    mua, mus = workloads.inclusion_phantom(n, dx, int(rng.integers(0, 5)), seed=seed, margin=min(2.0, 0.15 * n * dx))
+    if rng.uniform() < 0.5:
+        sig = rng.uniform(0.0, 0.2)
+        mua = (mua * np.exp(sig * rng.standard_normal(mua.shape) - 0.5 * sig * sig)).astype(np.float32)
+    return mua, mus
+
+
 def make_pairs(n_pairs: int, n: int = 256, dx: float = 0.05, K: int = 16, n_low: int = 100_000,
-               n_high: int = 10_000_000, seed0: int = 10_000, device="cuda"):
+               n_high: int = 10_000_000, seed0: int = 10_000, device="cuda", vary: bool = False):
     """(x, t): low- and high-count coefficient maps [n_pairs][2K+1][n][n] (fp32, device) of random
-    circular-inclusion phantoms (3 inclusions, g 0.9, collimated line source on the top edge)."""
+    circular-inclusion phantoms (3 inclusions, or varied media with ``vary``; g 0.9, collimated
+    line source on the top edge)."""
     C = 2 * K + 1
     x = torch.empty(n_pairs, C, n, n, device=device)
     t = torch.empty_like(x)
@@ -26,10 +41,34 @@ def make_pairs(n_pairs: int, n: int = 256, dx: float = 0.05, K: int = 16, n_low:
     for start in range(0, n_pairs, 32):
         probs = []
         for i in range(start, min(n_pairs, start + 32)):
-            mua, mus = workloads.inclusion_phantom(n, dx, 3, seed=seed0 + i, margin=min(2.0, 0.15 * n * dx))
+            mua, mus = training_medium(n, dx, seed0 + i, vary)
             med = mcr.Medium(torch.from_numpy(mua).to(device), torch.from_numpy(mus).to(device), dx32, g32)
             probs.append(mcr.Problem(med, n_low, seed=seed0 + i, stream_id=0, source=src, out=x[i]))
             probs.append(mcr.Problem(med, n_high, seed=seed0 + i, stream_id=1, source=src, out=t[i]))
+        mcr.run_batch(probs, common)
+    mcr.check()
+    return x, t
+
+
+def make_adjoint_pairs(n_pairs: int, n: int = 256, dx: float = 0.05, K: int = 16, n_low: int = 100_000,
+                       n_high: int = 10_000_000, seed0: int = 50_000, device="cuda"):
+    """(x, t): low- and high-count ADJOINT coefficient maps (Sec. 4) [n_pairs][2K+1][n][n] of signed
+    sources shaped like a reconstruction's q* (``workloads.residual_source``) in varied media, by
+    the batched launch (adjoint problems: mc_run_batch with qstar)."""
+    C = 2 * K + 1
+    x = torch.empty(n_pairs, C, n, n, device=device)
+    t = torch.empty_like(x)
+    common = mcr.Run(K=K, n_packets=0)
+    dx32, g32 = float(np.float32(dx)), float(np.float32(0.9))
+    for start in range(0, n_pairs, 32):
+        probs, keep = [], []
+        for i in range(start, min(n_pairs, start + 32)):
+            mua, mus = training_medium(n, dx, seed0 + i, True)
+            med = mcr.Medium(torch.from_numpy(mua).to(device), torch.from_numpy(mus).to(device), dx32, g32)
+            q = torch.from_numpy(workloads.residual_source(n, dx, seed0 + i)).to(device)
+            keep.append(q)
+            probs.append(mcr.Problem(med, n_low, seed=seed0 + i, stream_id=1, qstar=q, out=x[i]))
+            probs.append(mcr.Problem(med, n_high, seed=seed0 + i, stream_id=3, qstar=q, out=t[i]))
         mcr.run_batch(probs, common)
     mcr.check()
     return x, t

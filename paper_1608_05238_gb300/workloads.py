@@ -80,6 +80,29 @@ def lognormal_field(n: int, dx: float, mean: float, sigma: float, corr_mm: float
     return (mean * np.exp(sigma * G - 0.5 * sigma * sigma)).astype(np.float32)
 
 
+def residual_source(n: int, dx: float, seed: int, mua_bg: float = 0.01, depth_mm: float = 3.0):
+    """Signed isotropic source [n, n] (float32, per unit area and angle) shaped like the adjoint
+    source q* = mu_a (H^meas - H) of a reconstruction (Sec. 6): a mixture, with random weights, of
+    (a) the mu_a contrast of 1-4 random circular inclusions times an exponential decay with depth
+    (the fluence under a top line source), (b) a smooth zero-mean Gaussian random field (1 mm
+    correlation) with the same decay, and (c) pixel-scale white noise (the residual left once the
+    noise of H^meas and H dominates), with a random overall sign; ``default_rng(seed)``.
+    Scale: |q| ~ mu_a_bg^2 exp(-z / depth_mm).  Input generator only (no transport)."""
+    rng = np.random.default_rng(seed)
+    c = (np.arange(n) + 0.5) * dx
+    decay = np.exp(-c / depth_mm)[:, None] * np.ones((1, n))
+    mua, _ = inclusion_phantom(n, dx, int(rng.integers(1, 5)), seed=int(rng.integers(1 << 30)),
+                               mua_bg=mua_bg, mua_range=(0.005, 0.2), margin=min(2.0, 0.15 * n * dx))
+    contrast = (mua.astype(np.float64) - mua_bg) / mua_bg
+    field = lognormal_field(n, dx, 1.0, 1.0, 1.0, seed=int(rng.integers(1 << 30))).astype(np.float64)
+    smooth = np.log(np.maximum(field, 1e-30))
+    smooth = (smooth - smooth.mean()) / (smooth.std() + 1e-30)
+    white = rng.standard_normal((n, n))
+    w = rng.dirichlet((1.0, 1.0, 1.0))
+    q = (w[0] * contrast + w[1] * 0.5 * smooth + w[2] * 0.5 * white) * decay * mua_bg * mua_bg
+    return (q * (1.0 if rng.uniform() < 0.5 else -1.0)).astype(np.float32)
+
+
 def top_line_source(nx: int, dx: float) -> dict:
     return dict(kind=LINE, x0=0.0, z0=0.0, x1=nx * dx, z1=0.0, dir_x=0.0, dir_z=1.0, power=1.0)
 

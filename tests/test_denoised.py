@@ -1,0 +1,92 @@
+"""The learned part inside the method (denoised.Denoiser through the autograd Function): U-Nets
+trained on MC pairs denoise the low-count forward and adjoint maps of a gradient evaluation,
+full-count MC judges them and takes over when they fail, and the denoised route reconstructs
+mu_a better than plain MC with the same packets (the gain the network brings to the method)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1608_05238_gb300 import _build, denoise_train as dt, mcr, workloads
+from paper_1608_05238_gb300.autograd import MCSpec, forward_coefficients
+from paper_1608_05238_gb300.denoised import Denoiser
+from paper_1608_05238_gb300.denoiser import UNet
+from paper_1608_05238_gb300.inversion import invert
+from parity_util import f32
+
+pytestmark = pytest.mark.gpu
+
+N, DX, K, LOW, HIGH = 128, 0.1, 8, 20_000, 1_000_000
+
+
+@pytest.fixture(scope="module")
+def nets():
+    _build.build()
+    mcr.load()
+    xf, tf = dt.make_pairs(96 + 8, n=N, dx=DX, K=K, n_low=LOW, n_high=HIGH, vary=True, seed0=70_000)
+    xa, ta = dt.make_adjoint_pairs(96 + 8, n=N, dx=DX, K=K, n_low=LOW, n_high=HIGH, seed0=80_000)
+    out = {}
+    for kind, (x, t), seed in (("forward", (xf, tf), 1), ("adjoint", (xa, ta), 2)):
+        net = UNet(in_ch=2 * K + 1, seed=seed)
+        dt.train(net, x[:96], t[:96], steps=600, batch=8, lr=1e-3, seed=seed)
+        out[kind] = (net, dt.evaluate(net, x[96:], t[96:]))
+    return out
+
+
+def test_networks_beat_the_low_count_maps_on_held_out_pairs(nets):
+    for kind, (_, ev) in nets.items():
+        assert ev["err_denoised"] < 0.8 * ev["err_input"], (kind, ev)
+
+
+def _problem(seed=90_001):
+    mua, mus = workloads.inclusion_phantom(N, DX, 3, seed=seed, margin=2.0)
+    med = mcr.Medium(torch.from_numpy(mua).cuda(), torch.from_numpy(mus).cuda(), f32(DX), f32(0.9))
+    return med, [mcr.Source(**workloads.top_line_source(N, DX))]
+
+
+def test_judge_falls_back_to_full_count_mc(nets):
+    med, src = _problem()
+    bad = UNet(in_ch=2 * K + 1, seed=5)
+    head = bad.layers["out"]
+    head.w.normal_(0.0, 1.0)  # a head that scrambles its input: the judge must reject it
+    head.refresh()
+    dn = Denoiser(bad, nets["adjoint"][0], n_full=HIGH, judge_every=0, max_rel_err=0.25)
+    spec = MCSpec(dx=f32(DX), g=f32(0.9), sources=src, K=K, n_packets=LOW, seed=4, denoiser=dn)
+    first = forward_coefficients(med, spec)
+    assert dn.fallback and dn.history[0]["kind"] == "forward" and dn.history[0]["fallback"]
+    full = mcr.forward(med, src[0], mcr.Run(K=K, n_packets=HIGH, seed=4 + 1_000_003))
+    assert torch.equal(first, full)  # the judged evaluation uses the full-count map
+    later = forward_coefficients(med, spec)  # after the fallback: plain full-count MC
+    assert torch.equal(later, mcr.forward(med, src[0], mcr.Run(K=K, n_packets=HIGH, seed=4)))
+
+
+def test_good_denoiser_passes_the_judge_and_is_used(nets):
+    med, src = _problem()
+    dn = Denoiser(nets["forward"][0], nets["adjoint"][0], n_full=HIGH, judge_every=2)
+    spec = MCSpec(dx=f32(DX), g=f32(0.9), sources=src, K=K, n_packets=LOW, seed=6, denoiser=dn)
+    forward_coefficients(med, spec)   # judged (first call)
+    c2 = forward_coefficients(med, spec)  # denoised
+    forward_coefficients(med, spec)   # judged (every 2nd)
+    assert not dn.fallback and [h["call"] for h in dn.history] == [0, 2]
+    assert all(h["err_denoised"] < h["err_low"] for h in dn.history)
+    low = mcr.forward(med, src[0], mcr.Run(K=K, n_packets=LOW, seed=6))
+    assert torch.equal(c2, dn.denoise("forward", low))
+
+
+def test_denoised_route_reconstructs_mua_better_than_plain_mc_with_the_same_packets(nets):
+    mua_t_np, mus_np = workloads.inclusion_phantom(N, DX, 3, seed=90_007, margin=2.0)
+    mua_t, mus = torch.from_numpy(mua_t_np).cuda(), torch.from_numpy(mus_np).cuda()
+    src = [mcr.Source(**workloads.top_line_source(N, DX))]
+    med_t = mcr.Medium(mua_t, mus, f32(DX), f32(0.9))
+    Hm = mcr.h_eps(med_t, forward_coefficients(med_t, MCSpec(dx=f32(DX), g=f32(0.9), sources=src, K=0,
+                                                             n_packets=20_000_000, seed=99)))
+    mua0 = torch.full_like(mua_t, 0.01)
+    errs = {}
+    # the same packets per run on both routes (no judging run)
+    dn = Denoiser(nets["forward"][0], nets["adjoint"][0], n_full=HIGH, judge_first=False)
+    for name, dn in (("plain", None), ("denoised", dn)):
+        spec = MCSpec(dx=f32(DX), g=f32(0.9), sources=src, K=K, n_packets=LOW, denoiser=dn)
+        res = invert(mua0, mus, Hm, spec, unknowns=("mua",), iters=8, tol=1e-12, mua_true=mua_t, precondition=True,
+                     seed0=3)
+        errs[name] = float(np.mean([h.rel_err_mua for h in res.history[-3:]]))
+    assert errs["denoised"] < 0.8 * errs["plain"], errs
+    assert not dn.history  # nothing was judged
