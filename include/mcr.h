@@ -94,6 +94,13 @@ typedef struct {
                             ordinates tally of Sec. 3.1 instead -- coeff [M][nz][nx] holds the radiance
                             integrated over the angular sectors [m 2pi/M, (m+1) 2pi/M) of theta
                             (from +z), summing to a_0; K is ignored */
+  uint32_t time_bins;    /* 0: off.  T in 1..1024 (mc_forward only, not with sectors): the fluence resolved
+                            by the packets' path length since launch (time of flight times c / n, the
+                            radiance of a time-dependent source integrated over bins of equal time) --
+                            coeff [T][nz][nx], bin b holding the track weight of the path-length interval
+                            [b time_bin_mm, (b+1) time_bin_mm) and the last bin everything beyond, so the
+                            bins sum to a_0; K is ignored */
+  float time_bin_mm;     /* bin width in mm of path, > 0 when time_bins > 0 */
 } mcr_run;
 
 /* Run counters (host struct filled when a non-NULL pointer is passed; synchronises). */

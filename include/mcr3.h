@@ -48,7 +48,8 @@ typedef struct {
 } mcr3_source;
 
 /* Forward run: coeff device out [(L+1)^2][nz][ny][nx], L = run->K <= MCR3_MAX_L, n_packets <= 2^26
- * per call (use first_packet and run->accumulate to add further ranges); run->sectors must be 0. */
+ * per call (use first_packet and run->accumulate to add further ranges); run->sectors and
+ * run->time_bins must be 0. */
 int mc3_forward(const mcr3_medium *med, const mcr3_source *src, const mcr_run *run, float *coeff, mcr_stats *stats,
                 void *stream);
 /* Adjoint run from qstar (device [nz][ny][nx], signed, per unit volume and solid angle). */

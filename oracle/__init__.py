@@ -58,7 +58,8 @@ class _Run(C.Structure):
     _fields_ = [("K", C.c_int32), ("n_threads", C.c_int32), ("n_packets", C.c_uint64),
                 ("first_packet", C.c_uint64), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
                 ("max_scatter", C.c_uint32), ("max_events", C.c_uint32), ("w_threshold", C.c_double),
-                ("roulette_p", C.c_float), ("sectors", C.c_uint32), ("fixed_q", C.c_int32), ("fixed", C.c_uint32)]
+                ("roulette_p", C.c_float), ("sectors", C.c_uint32), ("fixed_q", C.c_int32), ("fixed", C.c_uint32),
+                ("time_bins", C.c_uint32), ("time_bin_mm", C.c_double)]
 
 
 class _Medium3(C.Structure):
@@ -127,6 +128,8 @@ class RunParams:
     n_threads: int = 0
     sectors: int = 0   # > 0: discrete-ordinates tally in that many equal sectors instead of harmonics
     fixed_q: int | None = None  # set: every deposit term rounded to a multiple of 2^-fixed_q (integer sums)
+    time_bins: int = 0          # > 0 (2D forward): fluence per path-length bin of width time_bin_mm
+    time_bin_mm: float = 0.0
 
 
 @dataclass
@@ -150,7 +153,8 @@ def _run(p: RunParams):
     nt = p.n_threads or (os.cpu_count() or 1)
     nt = max(1, min(nt, max(1, p.n_packets)))
     return _Run(p.K, nt, p.n_packets, p.first_packet, p.seed, p.stream_id, p.max_scatter, p.max_events,
-                p.w_threshold, p.roulette_p, p.sectors, int(p.fixed_q or 0), 1 if p.fixed_q is not None else 0)
+                p.w_threshold, p.roulette_p, p.sectors, int(p.fixed_q or 0), 1 if p.fixed_q is not None else 0,
+                p.time_bins, p.time_bin_mm)
 
 
 def _stats_dict(st: _Stats) -> dict:
@@ -195,7 +199,7 @@ def forward_sums(mua, mus, dx, g, source: dict, run: RunParams) -> np.ndarray:
     m, keep = _medium(mua, mus, dx, g)
     s = _source(source)
     nz, nx = keep[0].shape
-    raw = np.zeros((run.sectors or 2 * run.K + 1, nz, nx), dtype=np.float64)
+    raw = np.zeros((run.time_bins or run.sectors or 2 * run.K + 1, nz, nx), dtype=np.float64)
     st = _Stats()
     rc = lib.orc_forward_raw(C.byref(m), C.byref(s), C.byref(_run(run)), raw.ctypes.data_as(C.POINTER(C.c_double)),
                              None, C.byref(st))
@@ -228,7 +232,7 @@ def forward(mua, mus, dx, g, source: dict, run: RunParams, with_variance: bool =
                 float(source.get("dir_z", 1.0)), float(source.get("power", 1.0)), n_ang,
                 (C.c_double * MAX_ANG)(*map(float, ac)), (C.c_double * MAX_ANG)(*map(float, as_)))
     nz, nx = keep[0].shape
-    Cc = run.sectors or 2 * run.K + 1
+    Cc = run.time_bins or run.sectors or 2 * run.K + 1
     raw = np.zeros((Cc, nz, nx), dtype=np.float64)
     sq = np.zeros((nz, nx), dtype=np.float64) if with_variance else None
     st = _Stats()
@@ -237,7 +241,7 @@ def forward(mua, mus, dx, g, source: dict, run: RunParams, with_variance: bool =
                              sq.ctypes.data_as(C.POINTER(C.c_double)) if sq is not None else None, C.byref(st))
     if rc != 0:
         raise ValueError(f"oracle forward: status {rc}")
-    return _finish(raw, sq, run.n_packets, s.power, dx, st, run.sectors)
+    return _finish(raw, sq, run.n_packets, s.power, dx, st, run.sectors or run.time_bins)
 
 
 def volume(mua, mus, dx, g, q, run: RunParams, adjoint: bool = True, with_variance: bool = False) -> Result:
@@ -252,7 +256,7 @@ def volume(mua, mus, dx, g, q, run: RunParams, adjoint: bool = True, with_varian
     q = np.ascontiguousarray(q, dtype=np.float32)
     nz, nx = keep[0].shape
     assert q.shape == (nz, nx)
-    Cc = run.sectors or 2 * run.K + 1
+    Cc = run.time_bins or run.sectors or 2 * run.K + 1
     raw = np.zeros((Cc, nz, nx), dtype=np.float64)
     sq = np.zeros((nz, nx), dtype=np.float64) if with_variance else None
     st = _Stats()
@@ -263,7 +267,7 @@ def volume(mua, mus, dx, g, q, run: RunParams, adjoint: bool = True, with_varian
                             C.byref(st), C.byref(S))
     if rc != 0:
         raise ValueError(f"oracle volume: status {rc}")
-    return _finish(raw, sq, run.n_packets, S.value, dx, st, run.sectors)
+    return _finish(raw, sq, run.n_packets, S.value, dx, st, run.sectors or run.time_bins)
 
 
 def adjoint(mua, mus, dx, g, qstar, run: RunParams, with_variance: bool = False) -> Result:

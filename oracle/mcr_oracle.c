@@ -116,6 +116,12 @@ typedef struct {
    * exactly -- the fixed-point form of the tally (the normalisation of Sec. 3.1 then applies) */
   int32_t fixed_q;
   uint32_t fixed;
+  /* time_bins > 0 (2D, forward): the fluence resolved by the packet's path length since launch
+   * (time of flight x c / n): bin b holds the track weight of the path-length interval
+   * [b w, (b+1) w), w = time_bin_mm, the last bin everything beyond (T-1) w, so the bins sum to
+   * a_0; tally [time_bins][nz][nx] instead of the harmonics */
+  uint32_t time_bins;
+  double time_bin_mm;
 } orc_run;
 
 typedef struct {
@@ -284,6 +290,32 @@ static void orc_deposit(orc_job *j, int64_t pix, double t, double theta_tally) {
   }
 }
 
+/* Time-resolved deposit of a segment of length l that starts at path length L0 with weight W:
+ * the piece of the segment inside the path-length bin [b w, (b+1) w) (the last bin open-ended),
+ * s in [s1, s2) measured along the segment, holds the track weight int W e^{-mu_a s} ds =
+ * W (e^{-mu_a s1} - e^{-mu_a s2}) / mu_a (= W (s2 - s1) when mu_a = 0). */
+static void orc_deposit_timed(orc_job *j, int64_t pix, double W, double mua, double L0, double l) {
+  const int64_t npix = (int64_t)j->med->nx * j->med->nz;
+  const uint32_t T = j->run->time_bins;
+  const double w = j->run->time_bin_mm;
+  double sum = 0.0;
+  /* from one bin before floor(L0 / w), so that a quotient rounded up loses no sliver */
+  for (uint32_t b = (uint32_t)fmax(fmin(floor(L0 / w), (double)(T - 1)) - 1.0, 0.0);; ++b) {
+    const double s1 = fmax(b * w - L0, 0.0);
+    const double s2 = (b + 1 == T) ? l : fmin((b + 1) * w - L0, l);
+    if (s2 > s1) {
+      const double tp = mua > 0.0 ? W * (exp(-mua * s1) - exp(-mua * s2)) / mua : W * (s2 - s1);
+      j->tally[(int64_t)b * npix + pix] += tp;
+      sum += tp;
+    }
+    if (s2 >= l || b + 1 == T) break;
+  }
+  if (j->sq && sum != 0.0) {
+    if (j->pk[pix] == 0.0) j->touched[j->n_touched++] = pix;
+    j->pk[pix] += sum;
+  }
+}
+
 static void orc_packet(orc_job *j, uint64_t p) {
   const orc_medium *m = j->med;
   const orc_run *r = j->run;
@@ -350,6 +382,7 @@ static void orc_packet(orc_job *j, uint64_t p) {
   if (iz >= nz) iz = nz - 1;
 
   uint32_t flight = 0, n_scatter = 0;
+  double plen = 0.0; /* path length since launch (time-resolved tally) */
   for (;;) {
     /* ---- a new free flight: s = -ln(U)/mu_s, as optical depth tau */
     if (flight >= r->max_events) {
@@ -380,7 +413,12 @@ static void orc_packet(orc_job *j, uint64_t p) {
       const double l = collide ? d_coll : d_edge;
       /* deposit the track weight of this pixel segment (Sec. 3 + Eq. 9-11) */
       const double t = mua > 0.0 ? -W * expm1(-mua * l) / mua : W * l;
-      if (t != 0.0) orc_deposit(j, pix, t, j->adjoint ? theta + M_PI : theta);
+      if (r->time_bins) {
+        orc_deposit_timed(j, pix, W, mua, plen, l);
+        plen += l;
+      } else if (t != 0.0) {
+        orc_deposit(j, pix, t, j->adjoint ? theta + M_PI : theta);
+      }
       j->st.segments++;
       const double W_next = W * exp(-mua * l); /* W <- W exp(-mu_a s) (Sec. 3) */
       j->st.absorbed_w += W - W_next;          /* weight lost, booked apart from t */
@@ -463,6 +501,7 @@ static int orc_check(const orc_medium *m, const orc_run *r) {
   if (m->nx <= 0 || m->nz <= 0 || !(m->dx > 0.0)) return ORC_ERR_ARG;
   if (!(m->g > -1.0 && m->g < 1.0)) return ORC_ERR_ARG;
   if (r->K < 0 || r->K > 256 || r->n_threads <= 0 || r->sectors > 4096) return ORC_ERR_ARG;
+  if (r->time_bins > 4096 || (r->time_bins && (r->sectors || !(r->time_bin_mm > 0.0)))) return ORC_ERR_ARG;
   if (!(r->roulette_p > 0.0f && r->roulette_p <= 1.0f)) return ORC_ERR_ARG;
   const int64_t npix = (int64_t)m->nx * m->nz;
   for (int64_t i = 0; i < npix; ++i)
@@ -481,7 +520,7 @@ static int orc_check(const orc_medium *m, const orc_run *r) {
 static int orc_run_packets(const orc_medium *m, const orc_source *s, const orc_volsrc *vol,
                            const orc_run *r, int adjoint, double *tally, double *sq, orc_stats *st) {
   const int64_t npix = (int64_t)m->nx * m->nz;
-  const int64_t C = r->sectors ? (int64_t)r->sectors : 2 * (int64_t)r->K + 1;
+  const int64_t C = r->time_bins ? (int64_t)r->time_bins : r->sectors ? (int64_t)r->sectors : 2 * (int64_t)r->K + 1;
   const int nt = r->n_threads;
   orc_job *jobs = (orc_job *)calloc((size_t)nt, sizeof(orc_job));
   pthread_t *th = (pthread_t *)calloc((size_t)nt, sizeof(pthread_t));

@@ -568,7 +568,7 @@ int run3(const mcr3_medium *med, const mcr3_source *src, const float *qstar, con
   int rc;
   if ((rc = check_medium3(med))) return rc;
   if (!run || !coeff) return MCR_ERR_ARG;
-  if (run->K < 0 || run->K > MCR3_MAX_L || run->sectors || run->accumulate > 1u) return MCR_ERR_ARG;
+  if (run->K < 0 || run->K > MCR3_MAX_L || run->sectors || run->time_bins || run->accumulate > 1u) return MCR_ERR_ARG;
   if (!(run->roulette_p > 0.f && run->roulette_p <= 1.f) || !(run->w_threshold >= 0.f)) return MCR_ERR_ARG;
   if (run->n_packets > (1ull << 26) || run->first_packet + run->n_packets < run->first_packet) return MCR_ERR_ARG;
   Transport3Params p;

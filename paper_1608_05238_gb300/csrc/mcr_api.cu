@@ -117,7 +117,8 @@ struct HostProblem {
 int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const TransportLaunch &cfg, int slot,
             mcr_stats *stats, cudaStream_t s, long long *raw_out = nullptr) {
   const int np = (int)probs.size();
-  const int C = common->sectors ? (int)common->sectors : 2 * common->K + 1, Cpad = tally_row_words(C);
+  const int C = common->time_bins ? (int)common->time_bins : common->sectors ? (int)common->sectors : 2 * common->K + 1;
+  const int Cpad = tally_row_words(C);
   // a single problem may exceed one launch's packet budget (chunks + FP64 flush); a batch may not
   const bool chunked = np == 1 && probs[0].n_packets > kChunkPackets;
   Need need;
@@ -151,9 +152,13 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
   p.K = common->K;
   p.C = C;
   p.Cpad = Cpad;
-  p.row_stride = common->sectors ? 1 : transport_row_stride(C);  // no harmonic rows for sectors
+  // no harmonic rows for the sector and time tallies
+  p.row_stride = (common->sectors || common->time_bins) ? 1 : transport_row_stride(C);
   p.sectors = (int)common->sectors;
   p.sector_scale = (float)(common->sectors / (2.0 * 3.14159265358979323846));
+  p.time_bins = (int)common->time_bins;
+  p.time_bin_mm = common->time_bin_mm;
+  p.inv_time_bin = common->time_bins ? 1.f / common->time_bin_mm : 0.f;
   p.max_scatter = common->max_scatter;
   p.max_events = common->max_events;
   p.w_threshold = common->w_threshold;
@@ -260,9 +265,9 @@ int run_mc(const mcr_medium *med, const mcr_source *src, const float *qstar, con
   int rc;
   if ((rc = check_medium(med)) || (rc = check_run(run))) return rc;
   if (!coeff && !raw) return MCR_ERR_ARG;
-  if (qstar && run->sectors) return MCR_ERR_ARG;  // the sector tally is a forward-only study
+  if (qstar && (run->sectors || run->time_bins)) return MCR_ERR_ARG;  // forward-only tallies
   // raw sums: harmonic tallies of one launch (longer runs add ranges with accumulate)
-  if (raw && (run->sectors || run->n_packets > kChunkPackets)) return MCR_ERR_ARG;
+  if (raw && (run->sectors || run->time_bins || run->n_packets > kChunkPackets)) return MCR_ERR_ARG;
   HostProblem h{med, src, qstar, run->n_packets, run->first_packet, run->seed, run->stream_id, coeff, 0.f, 1.f};
   if (!qstar && (rc = check_source(src, &h.dirx, &h.dirz))) return rc;
   std::lock_guard<std::mutex> lock(g_mu);
@@ -301,7 +306,7 @@ int mc_finalize(const mcr_medium *med, const mcr_source *src, const float *qstar
                 const int64_t *tally, float *coeff, void *stream) {
   int rc;
   if ((rc = check_medium(med)) || (rc = check_run(run))) return rc;
-  if (!tally || !coeff || run->sectors || (src == nullptr) == (qstar == nullptr)) return MCR_ERR_ARG;
+  if (!tally || !coeff || run->sectors || run->time_bins || (src == nullptr) == (qstar == nullptr)) return MCR_ERR_ARG;
   float dirx, dirz;
   if (src && (rc = check_source(src, &dirx, &dirz))) return rc;
   const int64_t npix = (int64_t)med->nx * med->nz;
@@ -335,7 +340,7 @@ int mc_run_batch(const mcr_problem *problems, int32_t n_problems, const mcr_run 
   int rc;
   if (!problems || n_problems < 1 || n_problems > MCR_MAX_BATCH) return MCR_ERR_ARG;
   if ((rc = check_run(common))) return rc;
-  if (common->sectors) return MCR_ERR_ARG;  // the sector tally runs through mc_forward only
+  if (common->sectors || common->time_bins) return MCR_ERR_ARG;  // these tallies run through mc_forward only
   TransportLaunch cfg{0, 0, 0, 0};
   if (launch) {
     if (launch->threads_per_block < 0 || launch->threads_per_block > 256 || launch->threads_per_block % 32 ||
@@ -504,6 +509,8 @@ int check_run(const mcr_run *r) {
   if (r->first_packet + r->n_packets < r->first_packet) return MCR_ERR_ARG;  // id overflow
   if (r->accumulate > 1u) return MCR_ERR_ARG;
   if (r->sectors > 1024u) return MCR_ERR_ARG;
+  if (r->time_bins > 1024u) return MCR_ERR_ARG;
+  if (r->time_bins && (r->sectors || !(r->time_bin_mm > 0.f) || !isfinite(r->time_bin_mm))) return MCR_ERR_ARG;
   return MCR_OK;
 }
 

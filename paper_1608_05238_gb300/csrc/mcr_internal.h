@@ -60,6 +60,8 @@ struct TransportParams {
   int K, C, Cpad, row_stride;  // C = 2K+1 channels, Cpad = tally_row_words(C), smem row stride
   int sectors;                 // > 0: discrete-ordinates tally, C = sectors (single forward problem)
   float sector_scale;          // sectors / (2 pi)
+  int time_bins;               // > 0: path-length (time-of-flight) resolved fluence, C = time_bins
+  float time_bin_mm, inv_time_bin;
   unsigned max_scatter, max_events;
   float w_threshold, rr_p, rr_inv_p;
   unsigned long long total_packets;  // = prob[n_problems-1].end

@@ -69,7 +69,7 @@ int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_r
   int rc;
   if ((rc = check_medium(med)) || (rc = check_run(run))) return rc;
   if (!coeff) return MCR_ERR_ARG;
-  if (run->sectors) return MCR_ERR_ARG;  // the sector tally runs through mc_forward only
+  if (run->sectors || run->time_bins) return MCR_ERR_ARG;  // these tallies run through mc_forward only
   float dirx = 0.f, dirz = 1.f;
   if (!src) return MCR_ERR_ARG;
   if ((rc = check_source(src, &dirx, &dirz))) return rc;

@@ -97,10 +97,15 @@ __device__ __forceinline__ float launch_angle(const ProblemDesc &P, float u) {
 // NP = 0: the discrete-ordinates variant (Sec. 3.1's alternative to the harmonics): each segment
 // adds its track weight to one of p.sectors equal angular sectors of its pixel, one per-lane
 // reduction instead of 2K+1 cooperative ones (single forward problem, no merge).
+// NP = -1: the time-resolved variant: each segment's track weight is split over the path-length
+// bins [b w, (b+1) w) it spans (the last bin open-ended), one per-lane reduction per piece; the
+// packet's path and weight updates are those of the plain run.
 template <int NP, bool BATCH, bool MERGE, bool STALLY>
 __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ TransportParams p) {
   constexpr bool SECT = NP == 0;
-  static_assert(!SECT || (!BATCH && !MERGE && !STALLY), "the sector tally runs one plain forward problem");
+  constexpr bool TIMED = NP < 0;
+  constexpr bool ROWLESS = SECT || TIMED;  // no harmonic rows
+  static_assert(!ROWLESS || (!BATCH && !MERGE && !STALLY), "the sector and time tallies run one plain forward problem");
   extern __shared__ float smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -149,6 +154,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
   int ix = 0, iz = 0;
   unsigned flight = 0, nscat = 0, cu1 = 0, cu2 = 0;
   int sect = 0;           // SECT: the current flight's angular sector
+  float plen = 0.f;       // TIMED: path length since launch
   int rb = 0;             // row of the current flight's harmonics
   int carry_rb = 0;       // row of the deferred segment's harmonics
   float carry = 0.f;      // deferred track weight (times 2^q) of a collision segment, 0: none
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
       float th = atan2f(sx, sz);  // (-pi, pi], from +z
       if (th < 0.f) th += 6.28318530717958648f;
       sect = min((int)(th * p.sector_scale), p.sectors - 1);
-    } else {
+    } else if constexpr (!TIMED) {
       write_row();
     }
   };
@@ -279,6 +285,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
           w_launch += W0;
           nscat = 0;
           flight = 0;
+          plen = 0.f;
           if (!inside) {
             ++n_esc;
             w_esc += W;
@@ -299,6 +306,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     // ---------------------------------------------------------------- one pixel segment
     unsigned seg_key = 0u;  // (pixel + 1) << 6 | problem of this lane's segment (0: none)
     float seg_ts = 0.f;     // its track weight times 2^q
+    float seg_w = 0.f, seg_l = 0.f, seg_l0 = 0.f, seg_mua = 0.f, seg_imua = 0.f;  // TIMED: the segment
     float dep_carry = 0.f;  // a deferred segment deposited with this one (same pixel)
     bool collided = false, escaped = false;
     if (alive) {
@@ -314,6 +322,14 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
       // track weight of the segment: W (1 - e^{-mu_a l}) / mu_a, then W <- W e^{-mu_a l}
       const float em1 = expm1f(-m.x * l);
       const float t = m.x > 0.f ? (-W * em1) * m.z : W * l;
+      if constexpr (TIMED) {
+        seg_w = W;
+        seg_l = l;
+        seg_l0 = plen;
+        seg_mua = m.x;
+        seg_imua = m.z;
+        plen += l;
+      }
       W = fmaf(W, em1, W);
       ++n_seg;
       if (MERGE) {
@@ -367,7 +383,27 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     if constexpr (SECT) {
       if (seg_key != 0u) atomicAdd(tally_row(seg_key) + sect, (unsigned long long)(long long)__float2int_rn(seg_ts));
     }
-    unsigned pend = SECT ? 0u : __ballot_sync(kFull, seg_key != 0u);
+    if constexpr (TIMED) {
+      if (seg_key != 0u) {
+        // piece [s1, s2) of the segment in bin b: W e^{-mu_a s1} (1 - e^{-mu_a (s2 - s1)}) / mu_a
+        unsigned long long *row = tally_row(seg_key);
+        const int T = p.time_bins;
+        const float w = p.time_bin_mm;
+        // start one bin early: a rounded-up first index must not drop the segment's first sliver
+        for (int b = max(min((int)(seg_l0 * p.inv_time_bin), T - 1) - 1, 0);; ++b) {
+          const float s1 = fmaxf(fmaf((float)b, w, -seg_l0), 0.f);
+          const float s2 = b + 1 == T ? seg_l : fminf(fmaf((float)(b + 1), w, -seg_l0), seg_l);
+          if (s2 > s1) {
+            const float d = s2 - s1;
+            const float tp = seg_mua > 0.f ? seg_w * expf(-seg_mua * s1) * -expm1f(-seg_mua * d) * seg_imua
+                                           : seg_w * d;
+            atomicAdd(row + b, (unsigned long long)(long long)__float2int_rn(tp * QS()));
+          }
+          if (s2 >= seg_l || b + 1 == T) break;
+        }
+      }
+    }
+    unsigned pend = ROWLESS ? 0u : __ballot_sync(kFull, seg_key != 0u);
     if (pend) {
       const unsigned same = __match_any_sync(kFull, seg_key);
       // Rows of a single lane without a carried segment (nearly all of them away from the source)
@@ -455,7 +491,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
         }
         pend &= ~grp;
       }
-      if (!SECT && Cw < C && seg_key != 0u) {  // the per-lane remainder
+      if (!ROWLESS && Cw < C && seg_key != 0u) {  // the per-lane remainder
         unsigned long long *own = tally_row(seg_key);
         const float *h = rows + ((MERGE ? rb * 32 : 0) + lane) * p.row_stride + 1;
         const float *hc = rows + ((MERGE ? carry_rb * 32 : 0) + lane) * p.row_stride + 1;
@@ -664,10 +700,11 @@ size_t transport_smem_bytes(int row_stride, int threads, bool merge) {
 
 
 cudaError_t launch_transport(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s) {
-  if (p.sectors > 0) {  // discrete ordinates: one plain forward problem
+  if (p.sectors > 0 || p.time_bins > 0) {  // discrete ordinates / time bins: one plain forward problem
     if (p.n_problems != 1) return cudaErrorInvalidValue;
-    return launch_kernel<0, false, false>(p, cfg.threads_per_block > 0 ? cfg.threads_per_block : 128,
-                                          cfg.blocks_per_sm, s);
+    const int threads = cfg.threads_per_block > 0 ? cfg.threads_per_block : 128;
+    return p.sectors > 0 ? launch_kernel<0, false, false>(p, threads, cfg.blocks_per_sm, s)
+                         : launch_kernel<-1, false, false>(p, threads, cfg.blocks_per_sm, s);
   }
   // chunks of 32 coefficients deposited cooperatively (a remainder of <= 4 goes per lane)
   const int cw = (p.C & 31) <= 4 ? (p.C & ~31) : p.C;

@@ -59,7 +59,8 @@ class _Run(C.Structure):
     _fields_ = [("K", C.c_int32), ("max_scatter", C.c_uint32), ("n_packets", C.c_uint64),
                 ("first_packet", C.c_uint64), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
                 ("max_events", C.c_uint32), ("w_threshold", C.c_float), ("roulette_p", C.c_float),
-                ("accumulate", C.c_uint32), ("sectors", C.c_uint32)]
+                ("accumulate", C.c_uint32), ("sectors", C.c_uint32), ("time_bins", C.c_uint32),
+                ("time_bin_mm", C.c_float)]
 
 
 class _Problem(C.Structure):
@@ -225,12 +226,14 @@ class Run:
     roulette_p: float = 0.1
     accumulate: bool = False  # add into ``out`` instead of overwriting it
     sectors: int = 0          # > 0 (forward only): discrete-ordinates tally in that many equal sectors
+    time_bins: int = 0        # > 0 (forward only): fluence per path-length bin of width time_bin_mm (mm)
+    time_bin_mm: float = 0.0
 
     def c(self) -> _Run:
         return _Run(int(self.K), int(self.max_scatter), int(self.n_packets), int(self.first_packet),
                     int(self.seed) & 0xFFFFFFFFFFFFFFFF, int(self.stream_id), int(self.max_events),
                     float(self.w_threshold), float(self.roulette_p), 1 if self.accumulate else 0,
-                    int(self.sectors))
+                    int(self.sectors), int(self.time_bins), float(self.time_bin_mm))
 
 
 def _stats_dict(st: _Stats) -> dict:
@@ -239,7 +242,7 @@ def _stats_dict(st: _Stats) -> dict:
 
 def _coeff_out(med: Medium, K: int, out, sectors: int = 0):
     nz, nx = med.shape
-    C = sectors if sectors > 0 else 2 * K + 1
+    C = sectors if sectors > 0 else 2 * K + 1  # ``sectors``: the channel count of a sector or time tally
     if out is None:
         return torch.empty((C, nz, nx), dtype=torch.float32, device=med.mua.device)
     _dev_f32(out, "out")
@@ -251,9 +254,11 @@ def _coeff_out(med: Medium, K: int, out, sectors: int = 0):
 def forward(med: Medium, src: Source, run: Run, out=None, stats: bool = False, stream=None):
     """Forward harmonic radiance MC (``mc_forward``); returns coeff [2K+1, nz, nx] (and stats dict), or
     with ``run.sectors`` = M > 0 the radiance integrated over each of M equal angular sectors
-    [m 2pi/M, (m+1) 2pi/M) of theta (from +z), [M, nz, nx] (they sum to a_0)."""
+    [m 2pi/M, (m+1) 2pi/M) of theta (from +z), [M, nz, nx] (they sum to a_0), or with
+    ``run.time_bins`` = T > 0 the fluence per path-length bin [b w, (b+1) w), w = ``run.time_bin_mm``
+    (the last bin open-ended), [T, nz, nx] (they sum to a_0)."""
     lib = load()
-    coeff = _coeff_out(med, run.K, out, run.sectors)
+    coeff = _coeff_out(med, run.K, out, run.time_bins or run.sectors)
     st = _Stats() if stats else None
     rc = lib.mc_forward(C.byref(med.c()), C.byref(src.c()), C.byref(run.c()), _ptr(coeff),
                         C.byref(st) if st is not None else None, _stream(stream))

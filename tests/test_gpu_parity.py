@@ -136,6 +136,36 @@ def test_reciprocity_case2_odd_detector_gpu():
     assert abs(det.mean() - rec.mean()) < 4 * se + 0.01 * det.mean(), (det.mean(), rec.mean(), se)
 
 
+def test_reciprocity_case3_distributed_source_odd_detector_gpu():
+    """Case 3 (Eqs. 16, 19) on the GPU: a distributed isotropic source P_s (unit power; the
+    volumetric source q = P_s / (2 pi)) and an odd point detector (1 + sin theta) / (2 pi) at r_d.
+    The forward radiance of a volumetric isotropic source is the adjoint run of the same source
+    with order n turned back by (-1)^n, so the detected signal is (a*_0 - b*_1)(r_d) of mc_adjoint;
+    by reciprocity it equals sum_i dx^2 P_s,i Phi*_i, Phi* the fluence of a run from r_d with the
+    detector's density turned by pi (sin theta -> -sin theta)."""
+    nz = nx = 48
+    dx, g, K = 0.125, 0.5, 2
+    mua, mus = workloads.small_hetero(nz, nx, dx, seed=13)
+    pd = (24, 36)
+    iz, ix = np.mgrid[0:nz, 0:nx]
+    Ps = np.exp(-((iz - 24) ** 2 + (ix - 16) ** 2) / (2.0 * 3.0 ** 2))
+    Ps /= Ps.sum() * f32(dx) ** 2
+    q = (Ps / (2 * math.pi)).astype(np.float32)
+    med = mcr.Medium(_dev(mua), _dev(mus), f32(dx), f32(g))
+    centre = dict(x0=(pd[1] + 0.5) * dx, z0=(pd[0] + 0.5) * dx)
+    det, rec = [], []
+    for k in range(4):
+        a = mcr.adjoint(med, _dev(q), mcr.Run(K=K, n_packets=1_000_000, seed=80 + k, stream_id=1))
+        a = a.double().cpu().numpy()
+        det.append(a[0][pd] - a[2][pd])  # forward b_1 = (-1)^1 b*_1
+        phi = _gpu_forward(mua, mus, dx, g, dict(kind=mcr.ANGULAR_POINT, **centre, ang_s=[-1.0]),
+                           mcr.Run(K=0, n_packets=1_000_000, seed=90 + k))[0]
+        rec.append(float((Ps * phi).sum() * f32(dx) ** 2))
+    det, rec = np.array(det), np.array(rec)
+    se = math.sqrt(det.var(ddof=1) / 4 + rec.var(ddof=1) / 4)
+    assert abs(det.mean() - rec.mean()) < 4 * se + 0.01 * det.mean(), (det.mean(), rec.mean(), se)
+
+
 @pytest.mark.parametrize("M", [8, 37])
 def test_forward_sector_tally_parity(M):
     """The discrete-ordinates tally (Sec. 3.1's alternative basis) against the oracle on the same
@@ -157,6 +187,61 @@ def test_forward_sector_tally_parity(M):
     # the sectors partition the fluence deposits: their sum is the K = 0 run's a_0
     a0 = _gpu_forward(mua, mus, dx, g, src, mcr.Run(K=0, n_packets=40_001, seed=17))[0]
     assert np.allclose(G.sum(axis=0), a0, rtol=2e-6, atol=1e-9 * a0.max())
+
+
+@pytest.mark.parametrize("T,w", [(24, 0.2), (5, 1.3)])
+def test_forward_time_resolved_tally_parity(T, w):
+    """The path-length (time-of-flight) resolved fluence against the oracle on the same streams:
+    per bin relative L1 (a piece within FP32 rounding of a bin edge, or a path length summed in
+    FP32 over hundreds of segments, may move a sliver to the neighbouring bin), and the bins sum
+    to the plain run's a_0."""
+    mua, mus = workloads.small_hetero(40, 52, 0.08, seed=14)
+    src = _src32(dict(kind=mcr.LINE, x0=0.4, z0=0.0, x1=3.6, z1=0.0, dir_x=0.3, dir_z=1.0))
+    dx, g = f32(0.08), f32(0.85)
+    run = mcr.Run(K=0, n_packets=40_001, seed=19, time_bins=T, time_bin_mm=w)
+    G = _gpu_forward(mua, mus, dx, g, src, run)
+    O = oracle.forward(mua.astype(np.float64), mus.astype(np.float64), dx, g, src,
+                       RunParams(K=0, n_packets=run.n_packets, seed=run.seed, time_bins=T, time_bin_mm=f32(w)))
+    assert G.shape == O.coeff.shape == (T, 40, 52)
+    tot = np.abs(O.coeff).sum()
+    for b in range(T):
+        assert np.abs(G[b] - O.coeff[b]).sum() <= 2e-3 * np.abs(O.coeff[b]).sum() + 1e-6 * tot, b
+    a0 = _gpu_forward(mua, mus, dx, g, src, mcr.Run(K=0, n_packets=40_001, seed=19))[0]
+    assert np.allclose(G.sum(axis=0), a0, rtol=2e-5, atol=1e-8 * a0.max())
+
+
+def test_time_resolved_ballistic_closed_form_gpu():
+    """mu_s = 0, pencil straight down the middle of column 4: pixel k is crossed over path lengths
+    [k dx, (k+1) dx), so its fluence in bin b is the integral of e^{-mu_a L} over the overlap with
+    [b w, (b+1) w) divided by dx^2 (FP32 transport: 1e-5)."""
+    n, dx, mu, T, w = 12, 0.125, 0.75, 7, 0.15
+    mua, mus = np.full((n, n), mu, np.float32), np.zeros((n, n), np.float32)
+    G = _gpu_forward(mua, mus, dx, 0.3, dict(kind=mcr.PENCIL, x0=0.5625, z0=0.0, dir_x=0.0, dir_z=1.0),
+                     mcr.Run(K=0, n_packets=1000, seed=2, time_bins=T, time_bin_mm=w))
+    w = f32(w)
+    want = np.zeros((T, n))
+    for k in range(n):
+        for b in range(T):
+            lo, hi = max(k * dx, b * w), min((k + 1) * dx, (b + 1) * w if b < T - 1 else np.inf)
+            if hi > lo:
+                want[b, k] = (math.exp(-mu * lo) - math.exp(-mu * hi)) / mu / (dx * dx)
+    assert np.allclose(G[:, :, 4], want, rtol=1e-5, atol=1e-6 * want.max())
+    G[:, :, 4] = 0
+    assert not G.any()
+
+
+def test_time_resolved_tally_is_forward_only():
+    mua, mus = workloads.small_hetero(8, 8, 0.1, seed=1)
+    med = mcr.Medium(_dev(mua), _dev(mus), 0.1, 0.5)
+    src = mcr.Source(kind=mcr.ISO_POINT, x0=0.4, z0=0.4)
+    with pytest.raises(mcr.McrError):
+        mcr.adjoint(med, torch.ones(8, 8, device="cuda"), mcr.Run(K=0, n_packets=100, time_bins=4, time_bin_mm=0.1))
+    for bad in (dict(time_bins=4, time_bin_mm=0.0), dict(time_bins=4, time_bin_mm=0.1, sectors=3),
+                dict(time_bins=2000, time_bin_mm=0.1)):
+        with pytest.raises(mcr.McrError):
+            mcr.forward(med, src, mcr.Run(K=0, n_packets=100, **bad))
+    with pytest.raises(mcr.McrError):
+        mcr.run_batch([mcr.Problem(med, 100, source=src)], mcr.Run(K=0, n_packets=0, time_bins=4, time_bin_mm=0.1))
 
 
 def test_sector_tally_is_forward_only():

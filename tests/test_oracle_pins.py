@@ -465,6 +465,116 @@ def test_reciprocity_case2_angular_detectors():
             assert abs(det.mean() - unflipped.mean()) > 6 * se + 0.05 * det.mean(), (det.mean(), unflipped.mean(), se)
 
 
+def _blob(nz, nx, dx, centre, sigma_px):
+    """Unit-power distributed source density P_s [nz, nx] (sum P_s dx^2 = 1): a Gaussian blob."""
+    iz, ix = np.mgrid[0:nz, 0:nx]
+    p = np.exp(-((iz - centre[0]) ** 2 + (ix - centre[1]) ** 2) / (2.0 * sigma_px ** 2))
+    return p / (p.sum() * dx * dx)
+
+
+def test_reciprocity_case3_distributed_source_angular_detector():
+    """Case 3 (Eqs. 16, 19): a distributed isotropic source a3 = P_s(r) / (2 pi) (unit power: the
+    volumetric source q = P_s / (2 pi) per unit area and angle) and a point detector at r_d with
+    angular sensitivity p(theta).  <L a3, b3> = (a_0 + sum_n c_n a_n + s_n b_n)(r_d) / (2 pi) of the
+    forward run from the distributed source; <a3, L* b3> = sum_i dx^2 q_i Phi*_i, with Phi* the
+    adjoint fluence of the detector -- the fluence of a forward run from r_d with density
+    p(theta + pi) (reading A3).  So (a_0 + sum c_n a_n + s_n b_n)(r_d) = sum_i dx^2 P_s,i Phi*_i.
+    (The printed Eq. 19 exchanges the roles of P_s and P_d; this is what Eq. 13 gives for the a3,
+    b3 of Eq. 16.)  With the odd detector (1 + sin theta) / (2 pi) the identity fails without the
+    turn by pi."""
+    nz = nx = 24
+    dx, g, K = 0.25, 0.5, 4
+    mua, mus = _hetero(nz, nx, 19)
+    mua, mus = mua * 0.2, mus * 0.5
+    pd = (12, 18)
+    Ps = _blob(nz, nx, dx, (12, 8), 1.5)
+    q = (Ps / (2 * math.pi)).astype(np.float32)
+
+    def flipped(v):
+        return [(-1) ** n * x for n, x in enumerate(v, start=1)]
+
+    centre = dict(x0=(pd[1] + 0.5) * dx, z0=(pd[0] + 0.5) * dx)
+    for ac, as_ in ANG_DENSITIES[:2]:
+        det, rec, unflipped = [], [], []
+        for k in range(6):
+            f = oracle.volume(mua, mus, dx, g, q, RunParams(K=K, n_packets=60000, seed=150 + k), adjoint=False)
+            assert abs(f.source_strength - 1.0) < 1e-6
+            det.append(f.coeff[0][pd] + sum(_ang(ac, n) * f.coeff[2 * n - 1][pd] + _ang(as_, n) * f.coeff[2 * n][pd]
+                                            for n in range(1, K + 1)))
+            run = RunParams(K=0, n_packets=60000, seed=170 + k)
+            phi = oracle.forward(mua, mus, dx, g, dict(kind=oracle.ANGULAR_POINT, **centre, ang_c=flipped(ac),
+                                                       ang_s=flipped(as_)), run).coeff[0]
+            rec.append(float((Ps * phi).sum() * dx * dx))
+            phi_u = oracle.forward(mua, mus, dx, g, dict(kind=oracle.ANGULAR_POINT, **centre, ang_c=ac, ang_s=as_),
+                                   run).coeff[0]
+            unflipped.append(float((Ps * phi_u).sum() * dx * dx))
+        det, rec, unflipped = map(np.array, (det, rec, unflipped))
+        se = math.sqrt(det.var(ddof=1) / 6 + rec.var(ddof=1) / 6)
+        assert abs(det.mean() - rec.mean()) < 4 * se + 0.01 * det.mean(), (ac, as_, det.mean(), rec.mean(), se)
+        if as_:  # the odd detector: the missing turn is detected
+            assert abs(det.mean() - unflipped.mean()) > 6 * se + 0.05 * det.mean(), (det.mean(), unflipped.mean(), se)
+
+
+# ------------------------------------------------------------ time-resolved fluence (Sec. 4.1 detectors)
+def test_time_bins_partition_the_fluence():
+    """The time-resolved tally splits each segment's track weight over path-length bins (the last
+    open-ended): on the same packets the bins sum to a_0 (FP64 rounding), for bins much shorter
+    and much longer than a pixel."""
+    mua, mus, dx, g, src = _sector_case()
+    h = oracle.forward(mua, mus, dx, g, src, RunParams(K=0, n_packets=5000, seed=5))
+    for T, w in ((1, 0.5), (40, 0.01), (16, 0.7)):
+        r = oracle.forward(mua, mus, dx, g, src, RunParams(K=0, n_packets=5000, seed=5, time_bins=T, time_bin_mm=w))
+        assert r.coeff.shape[0] == T
+        assert np.allclose(r.coeff.sum(axis=0), h.coeff[0], rtol=1e-11, atol=1e-14)
+
+
+@pytest.mark.parametrize("direction", ["down", "right"])
+def test_time_bins_ballistic_closed_form(direction):
+    """mu_s = 0: a collimated beam along an axis crosses pixel k over the path lengths
+    [k dx, (k+1) dx); the fluence of that pixel in the bin [b w, (b+1) w) is the integral of
+    e^{-mu_a L} over the overlap, divided by the pixel area (exact, every packet alike)."""
+    n, dx, mu, T, w = 12, 0.1, 0.7, 7, 0.13
+    mua, mus = np.full((n, n), mu), np.zeros((n, n))
+    if direction == "down":
+        src = dict(kind=oracle.PENCIL, x0=0.45, z0=0.0, dir_x=0.0, dir_z=1.0)
+    else:
+        src = dict(kind=oracle.PENCIL, x0=0.0, z0=0.75, dir_x=1.0, dir_z=0.0)
+    r = oracle.forward(mua, mus, dx, 0.3, src, RunParams(K=0, n_packets=16, seed=1, time_bins=T, time_bin_mm=w))
+    line = r.coeff[:, :, 4] if direction == "down" else r.coeff[:, 7, :]
+    want = np.zeros((T, n))
+    for k in range(n):
+        for b in range(T):
+            lo, hi = max(k * dx, b * w), min((k + 1) * dx, (b + 1) * w if b < T - 1 else np.inf)
+            if hi > lo:
+                want[b, k] = (math.exp(-mu * lo) - math.exp(-mu * hi)) / mu / (dx * dx)
+    assert np.allclose(line, want, rtol=1e-12, atol=1e-14)
+    off = r.coeff.copy()
+    if direction == "down":
+        off[:, :, 4] = 0
+    else:
+        off[:, 7, :] = 0
+    assert not off.any()
+
+
+def test_time_bins_decay_with_absorption():
+    """Paths do not depend on mu_a (absorption weighting, reading 1), so with roulette off and the
+    same packets, a pixel's fluence in path-length bin b with uniform mu_a is the mu_a = 0 one
+    weighted by e^{-mu_a L} over that bin: their ratio lies in [e^{-mu_a (b+1) w}, e^{-mu_a b w}]."""
+    n, dx, g, T, w, mu = 16, 0.1, 0.6, 12, 0.35, 0.8
+    mus = _hetero(n, n, 29)[1]
+    src = dict(kind=oracle.ISO_POINT, x0=0.83, z0=0.77)
+    run = RunParams(K=0, n_packets=4000, seed=12, w_threshold=0.0, time_bins=T, time_bin_mm=w)
+    f0 = oracle.forward(np.zeros((n, n)), mus, dx, g, src, run).coeff
+    fa = oracle.forward(np.full((n, n), mu), mus, dx, g, src, run).coeff
+    for b in range(T - 1):
+        m = f0[b] > 0
+        ratio = fa[b][m] / f0[b][m]
+        assert ratio.min() >= math.exp(-mu * (b + 1) * w) * (1 - 1e-12), b
+        assert ratio.max() <= math.exp(-mu * b * w) * (1 + 1e-12), b
+    assert (fa[T - 1] <= f0[T - 1] * math.exp(-mu * (T - 1) * w) * (1 + 1e-12)).all()
+    assert ((f0 > 0) == (fa > 0)).all()
+
+
 # ------------------------------------------------------------ discrete ordinates (Sec. 3.1)
 def _sector_case():
     nz = nx = 20
