@@ -272,6 +272,14 @@ int mc_eps(int64_t npix, double pixel_area, const float *H, const float *Hmeas, 
            void *stream);
 
 /*
+ * mc_dot -- the inner products of the reconstruction's line searches and quasi-Newton updates
+ * (Sec. 6: the directional derivative g.d of the sufficient-decrease test, Eq. 30):
+ * out (device, one double) = sum_i a_i b_i over n FP32 elements (device), FP64 products and sums
+ * in a fixed order (deterministic).
+ */
+int mc_dot(int64_t n, const float *a, const float *b, double *out, void *stream);
+
+/*
  * mc_adjoint_source -- q*_i = -mu_a,i dL_dH_i / dx^2 (device out [nz][nx] FP32).  For the
  * paper's eps (dL_dH = -dx^2 (H^meas - H)) this is q* = mu_a (H^meas - H) of Sec. 6.
  */

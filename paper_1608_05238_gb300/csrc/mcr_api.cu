@@ -393,6 +393,16 @@ int mc_eps(int64_t npix, double pixel_area, const float *H, const float *Hmeas, 
   return MCR_OK;
 }
 
+int mc_dot(int64_t n, const float *a, const float *b, double *out, void *stream) {
+  if (n <= 0 || !a || !b || !out) return MCR_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  Workspace *w = nullptr;
+  int rc;
+  if ((rc = workspace(Need{}, &w))) return rc;
+  MCR_TRY_CUDA(launch_dot(a, b, n, w->partials, w->partials_bytes / sizeof(double), out, (cudaStream_t)stream));
+  return MCR_OK;
+}
+
 int mc_adjoint_source(const mcr_medium *med, const float *dL_dH, float *qstar, void *stream) {
   int rc;
   if ((rc = check_medium(med))) return rc;

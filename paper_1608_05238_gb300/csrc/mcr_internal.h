@@ -163,6 +163,9 @@ cudaError_t launch_h_eps(const float *mua, const float *a0, const float *Hmeas, 
                          float *dL_dH, double *partials, size_t partials_cap, double *eps, cudaStream_t s);
 cudaError_t launch_adjoint_source(const float *mua, const float *dL_dH, int64_t npix, double area, float *q,
                                   cudaStream_t s);
+// *out = sum_i a_i b_i in FP64, per-block partials then one thread in block order (deterministic)
+cudaError_t launch_dot(const float *a, const float *b, int64_t n, double *partials, size_t partials_cap, double *out,
+                       cudaStream_t s);
 cudaError_t launch_gradient(const float *coeff, const float *coeff_adj, const float *dL_dH, int64_t npix, int K,
                             double g, double area, double *d_mua, double *d_mus, cudaStream_t s);
 cudaError_t launch_gradient_f32(const float *coeff, const float *coeff_adj, const float *dL_dH, int64_t npix, int K,

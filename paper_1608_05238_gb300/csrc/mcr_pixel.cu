@@ -216,6 +216,24 @@ __global__ void k_h_eps(const float *__restrict__ mua, const float *__restrict__
   }
 }
 
+// Per-block FP64 partial sums of a_i b_i (grid-stride, a fixed order for a given grid).
+__global__ void k_dot(const float *__restrict__ a, const float *__restrict__ b, int64_t n,
+                      double *__restrict__ partials) {
+  __shared__ double red[kThreads / 32];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+    acc += (double)a[i] * (double)b[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+    partials[blockIdx.x] = s;
+  }
+}
+
 // eps = 1/2 A sum(partials), summed by one thread in block order (deterministic).
 __global__ void k_eps_final(const double *__restrict__ partials, int n, double half_area, double *eps) {
   double s = 0.0;
@@ -324,6 +342,15 @@ cudaError_t launch_h_eps(const float *mua, const float *a0, const float *Hmeas, 
   if ((size_t)grid > partials_cap) grid = (int)partials_cap;
   k_h_eps<<<grid, kThreads, 0, s>>>(mua, a0, Hmeas, npix, area, H, dL_dH, (Hmeas && eps) ? partials : nullptr);
   if (Hmeas && eps) k_eps_final<<<1, 1, 0, s>>>(partials, grid, 0.5 * area, eps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const float *a, const float *b, int64_t n, double *partials, size_t partials_cap, double *out,
+                       cudaStream_t s) {
+  int grid = grid_for(n, kThreads);
+  if ((size_t)grid > partials_cap) grid = (int)partials_cap;
+  k_dot<<<grid, kThreads, 0, s>>>(a, b, n, partials);
+  k_eps_final<<<1, 1, 0, s>>>(partials, grid, 1.0, out);
   return cudaGetLastError();
 }
 

@@ -27,8 +27,18 @@ sufficiently (Eq. 30) and a stop once the relative decrease of eps falls below a
   so pixels deep in the medium move as fast as those near the source.  The line search then uses
   the directional derivative g.d instead of |g|^2.
 
-The step update itself (mu - alpha g, clamp) is a handful of torch elementwise operations: the
-driver is plumbing around the MC gradient, which is where the time goes.
+* or (``method="lbfgs"``; the paper chose gradient descent over L-BFGS for its robustness to MC
+  noise, Sec. 6) limited-memory BFGS: the direction -H g from the two-loop recursion over the
+  last ``memory`` pairs s = mu_new - mu_old, y = g_new - g_old, H_0 scaled by s.y / y.y, with the
+  Hager-Zhang line search starting at the unit step.  Both gradients of a pair come from the same
+  packets (the iteration's seeds: g_old at the start, g_new at the accepted trial), so y holds the
+  change of the gradient and not the difference of two MC noises; pairs with s.y <= 0 are skipped,
+  and a direction that is not a descent direction restarts from -g.
+
+Every inner product (g.d, the line-search slopes, the recursion's s.q and y.r) is ``mc_dot``: FP64
+on the GPU in a fixed order.  The step update itself (mu - alpha g, clamp) and the recursion's
+vector updates are a handful of torch elementwise operations: the driver is plumbing around the MC
+gradient, which is where the time goes.
 """
 from __future__ import annotations
 
@@ -37,6 +47,7 @@ from dataclasses import dataclass, field, replace
 
 import torch
 
+from . import mcr
 from .autograd import EpsFromH, HFromMu, MCSpec
 
 
@@ -62,6 +73,34 @@ class InversionResult:
 def mean_relative_error(est: torch.Tensor, true: torch.Tensor) -> float:
     """Mean over the domain of |mu_true - mu_est| / mu_true (the paper's reconstruction metric)."""
     return float(((est.double() - true.double()).abs() / true.double()).mean())
+
+
+def _dot(us, vs) -> float:
+    """sum over the (non-None) tensor pairs of u.v, each by mc_dot (FP64 on the GPU, fixed order)."""
+    return sum(float(mcr.dot(u.contiguous(), v.contiguous())) for u, v in zip(us, vs)
+               if u is not None and v is not None)
+
+
+def lbfgs_direction(g: list, pairs: list, dot=_dot) -> list:
+    """-H g by the L-BFGS two-loop recursion (Nocedal & Wright, Algorithm 7.4): ``g`` a list of
+    tensors (None entries skipped), ``pairs`` the stored (s, y, 1 / s.y) oldest first, H_0 = gamma I
+    with gamma = s.y / y.y of the newest pair (gamma = 1 without pairs).  ``dot`` computes sums of
+    inner products over the lists."""
+    q = [None if t is None else t.clone() for t in g]
+    alphas = []
+    for s_, y_, rho in reversed(pairs):
+        a = rho * dot(s_, q)
+        alphas.append(a)
+        q = [None if qi is None else qi - a * yi for qi, yi in zip(q, y_)]
+    gamma = 1.0
+    if pairs:
+        s_, y_, _ = pairs[-1]
+        gamma = dot(s_, y_) / dot(y_, y_)
+    r = [None if qi is None else gamma * qi for qi in q]
+    for (s_, y_, rho), a in zip(pairs, reversed(alphas)):
+        b = rho * dot(y_, r)
+        r = [None if ri is None else ri + (a - b) * si for ri, si in zip(r, s_)]
+    return [None if ri is None else -ri for ri in r]
 
 
 def _eps_and_grad(mua, mus, Hmeas, spec, want_a, want_s):
@@ -198,7 +237,7 @@ def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MC
            iters: int = 20, tol: float = 1e-5, line_search: str = "backtracking", step0: float | None = None,
            shrink: float = 0.2, grow: float = 2.0, armijo: float = 1e-4, step_bounds: tuple | None = None,
            max_trials: int = 12, hz: HZParams | None = None, mu_floor: float = 1e-6, mua_true=None, mus_true=None,
-           seed0: int = 1, precondition: bool = False) -> InversionResult:
+           seed0: int = 1, precondition: bool = False, method: str = "gd", memory: int = 5) -> InversionResult:
     """Reconstruct ``unknowns`` (a subset of ("mua", "mus")) from H^meas; the others stay fixed.
 
     ``step0`` defaults to the step that changes the unknowns by 10 % of their norm on the first
@@ -208,6 +247,12 @@ def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MC
     """
     if line_search not in ("backtracking", "hager_zhang"):
         raise ValueError(f"line_search must be 'backtracking' or 'hager_zhang', not {line_search!r}")
+    if method not in ("gd", "lbfgs"):
+        raise ValueError(f"method must be 'gd' or 'lbfgs', not {method!r}")
+    if method == "lbfgs":
+        line_search = "hager_zhang"  # its trials yield the gradients the pairs need
+        precondition = False
+    pairs = []
     want_a, want_s = "mua" in unknowns, "mus" in unknowns
     mua, mus = mua0.detach().clone(), mus0.detach().clone()
     res = InversionResult(mua, mus)
@@ -225,7 +270,12 @@ def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MC
                 phi = H / mua
                 da = da / (float(spec.dx) ** 2 * phi * phi).clamp_min(1e-30)
         ds = -gs if want_s else None
-        slope = -sum(float((g.double() * d.double()).sum()) for g, d in ((ga, da), (gs, ds)) if g is not None)
+        if method == "lbfgs" and pairs:
+            da, ds = lbfgs_direction([ga, gs], pairs)
+            if -_dot([ga, gs], [da, ds]) <= 0.0:  # not a descent direction: restart from -g
+                pairs.clear()
+                da, ds = (-ga if want_a else None), (-gs if want_s else None)
+        slope = -_dot([ga, gs], [da, ds])
         if slope <= 0.0:
             res.converged = True
             break
@@ -236,18 +286,21 @@ def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MC
             return na, ns
 
         if line_search == "hager_zhang":
-            if alpha is None:
+            if method == "lbfgs" and pairs:
+                c = 1.0  # the quasi-Newton step
+            elif alpha is None or method == "lbfgs":
                 amax = max(float(m.abs().max()) for m, w in ((mua, want_a), (mus, want_s)) if w)
                 dmax = max(float(d.abs().max()) for d in (da, ds) if d is not None)
                 c = 0.01 * amax / dmax
             else:
                 c = 2.0 * alpha
+            trial_grads = {}
 
             def phi_fn(a):
                 na, ns = step_to(a)
                 e, ga2, gs2, _ = _eps_and_grad(na, ns, Hmeas, s_it, want_a, want_s)
-                return e, sum(float((g.double() * d.double()).sum()) for g, d in ((ga2, da), (gs2, ds))
-                              if g is not None)
+                trial_grads[a] = (ga2, gs2)
+                return e, _dot([ga2, gs2], [da, ds])
 
             a_acc, e_new, _, trial = hager_zhang(phi_fn, eps, -slope, c, hzp)
             if a_acc is None:
@@ -255,6 +308,14 @@ def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MC
                 break
             alpha = a_acc
             na, ns = step_to(alpha)
+            if method == "lbfgs":  # the pair from gradients of the same packets
+                ga_n, gs_n = trial_grads[alpha]
+                s_ = [(na - mua) if want_a else None, (ns - mus) if want_s else None]
+                y_ = [(ga_n - ga) if want_a else None, (gs_n - gs) if want_s else None]
+                sy = _dot(s_, y_)
+                if sy > 1e-12 * (_dot(s_, s_) * _dot(y_, y_)) ** 0.5:
+                    pairs.append((s_, y_, 1.0 / sy))
+                    del pairs[:-memory]
         else:
             if alpha is None:
                 norm_mu = sum(float((m.double() ** 2).sum()) for m, w in ((mua, want_a), (mus, want_s)) if w) ** 0.5

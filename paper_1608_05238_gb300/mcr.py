@@ -26,7 +26,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_EVENT_LIMIT, ERR_TALLY_OVERFLOW, ERR_MEDIU
 
 # every symbol declared in include/mcr.h
 EXPORTS = ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_forward_raw", "mc_adjoint_raw", "mc_finalize",
-           "mc_run_batch", "mc_h_eps", "mc_eps",
+           "mc_run_batch", "mc_h_eps", "mc_eps", "mc_dot",
            "mc_adjoint_source", "mc_gradient", "mc_gradient_f32", "mc_check", "mc_last_run_info",
            "mc_release_workspace", "mc_status_string", "mc_version")
 # measurement and test entry points (include/mcr_diag.h), not part of the method's interface
@@ -111,6 +111,7 @@ def load() -> C.CDLL:
         lib.mc_gradient.argtypes = [C.POINTER(_Medium), C.c_int32, vp, vp, vp, vp, vp, vp]
         lib.mc_gradient_f32.argtypes = [C.POINTER(_Medium), C.c_int32, vp, vp, vp, vp, vp, vp]
         lib.mc_eps.argtypes = [C.c_int64, C.c_double, vp, vp, vp, vp, vp]
+        lib.mc_dot.argtypes = [C.c_int64, vp, vp, vp, vp]
         lib.mc_check.argtypes = [vp]
         lib.mc_reduction_probe.argtypes = [vp, C.c_int64, C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32, vp]
         lib.mc_philox_blocks.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_int32,
@@ -123,7 +124,7 @@ def load() -> C.CDLL:
         lib.mc_version.argtypes = []
         lib.mc_version.restype = C.c_char_p
         for name in ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_forward_raw", "mc_adjoint_raw",
-                     "mc_finalize", "mc_run_batch", "mc_h_eps", "mc_eps",
+                     "mc_finalize", "mc_run_batch", "mc_h_eps", "mc_eps", "mc_dot",
                      "mc_adjoint_source", "mc_gradient", "mc_gradient_f32", "mc_check", "mc_last_run_info",
                      "mc_release_workspace"):
             getattr(lib, name).restype = C.c_int
@@ -452,6 +453,18 @@ def eps(H: torch.Tensor, Hmeas: torch.Tensor, dx: float, stream=None):
     d32 = C.c_float(dx).value  # the pixel side as the medium struct carries it (FP32)
     _check(lib.mc_eps(H.numel(), d32 * d32, _ptr(H), _ptr(Hmeas), _ptr(v), _ptr(e), _stream(stream)), "mc_eps")
     return e, v
+
+
+def dot(a: torch.Tensor, b: torch.Tensor, stream=None) -> torch.Tensor:
+    """sum a_i b_i of two float32 CUDA tensors of equal size in FP64, fixed order (``mc_dot``);
+    returns a 0-d float64 CUDA tensor."""
+    _dev_f32(a, "a")
+    _dev_f32(b, "b")
+    if a.numel() != b.numel():
+        raise ValueError("a and b must have the same number of elements")
+    out = torch.empty((), dtype=torch.float64, device=a.device)
+    _check(load().mc_dot(a.numel(), _ptr(a), _ptr(b), _ptr(out), _stream(stream)), "mc_dot")
+    return out
 
 
 def check(stream=None):

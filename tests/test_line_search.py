@@ -5,8 +5,9 @@ an exhausted budget falls back to the best step with a sufficient decrease."""
 import math
 
 import pytest
+import torch
 
-from paper_1608_05238_gb300.inversion import HZParams, hager_zhang
+from paper_1608_05238_gb300.inversion import lbfgs_direction, HZParams, hager_zhang
 
 
 def _conditions(f0, g0, a, fa, ga, p):
@@ -64,3 +65,49 @@ def test_exhausted_budget_falls_back_to_sufficient_decrease_or_none():
     # a tiny step that decreases phi but whose slope is still too negative is the fallback
     a, fa, ga, n = hager_zhang(fn, f0, g0, 1e-3, HZParams(max_evals=1))
     assert a == 1e-3 and fa < f0 and n == 1
+
+
+# ------------------------------------------------------------------ L-BFGS two-loop recursion
+def _cpu_dot(us, vs):
+    return sum(float((u.double() * v.double()).sum()) for u, v in zip(us, vs) if u is not None and v is not None)
+
+
+def _quadratic(n, seed):
+    g = torch.Generator().manual_seed(seed)
+    Q = torch.randn(n, n, generator=g, dtype=torch.float64)
+    A = Q @ Q.T + n * torch.eye(n, dtype=torch.float64)
+    b = torch.randn(n, generator=g, dtype=torch.float64)
+    return A, b
+
+
+def test_lbfgs_direction_meets_the_secant_condition():
+    """The BFGS inverse-Hessian estimate maps the newest y to the newest s: -direction(y) = s."""
+    A, _ = _quadratic(6, 1)
+    g = torch.Generator().manual_seed(2)
+    pairs = []
+    for _ in range(4):
+        s_ = torch.randn(6, generator=g, dtype=torch.float64)
+        y_ = A @ s_
+        pairs.append(([s_, None], [y_, None], 1.0 / float(s_ @ y_)))
+    d = lbfgs_direction([pairs[-1][1][0], None], pairs, dot=_cpu_dot)
+    assert d[1] is None
+    assert torch.allclose(-d[0], pairs[-1][0][0], rtol=1e-10, atol=1e-12)
+
+
+def test_lbfgs_with_exact_line_search_minimises_a_quadratic():
+    """With exact line searches on a strictly convex quadratic, BFGS directions are conjugate and
+    the minimiser of an n-dimensional quadratic is reached in n steps (memory >= n)."""
+    n = 5
+    A, b = _quadratic(n, 3)
+    x = torch.zeros(n, dtype=torch.float64)
+    pairs = []
+    grad = lambda v: A @ v - b
+    for _ in range(n):
+        gx = grad(x)
+        d = lbfgs_direction([gx], pairs, dot=_cpu_dot)[0] if pairs else -gx
+        alpha = -float(gx @ d) / float(d @ (A @ d))  # exact minimiser along d
+        x_new = x + alpha * d
+        s_, y_ = x_new - x, grad(x_new) - gx
+        pairs.append(([s_], [y_], 1.0 / float(s_ @ y_)))
+        x = x_new
+    assert torch.allclose(x, torch.linalg.solve(A, b), rtol=1e-8, atol=1e-10)
