@@ -235,6 +235,12 @@ typedef struct {
                                 the end -- applies to a batch of one problem with 2K+1 <= 36
                                 whose tally (pixels x Cpad x 8 B) fits beside the harmonic rows
                                 (e.g. 32x32 at K = 8); otherwise the global tally is used */
+  int32_t launch_order;      /* 0 default, 1 off, 2 on: process the packets in the order of their launch
+                                position (line sources: 1/4096 of the line; volumetric sources: 32 x 32-
+                                pixel tiles; other kinds keep their order), so that the packets in flight
+                                start close together and their tally rows stay in L2.  The tally does not
+                                depend on the order (bit-identical).  Default: on once the tallies of the
+                                launch exceed 96 MB (mc_forward and mc_adjoint always use the default) */
 } mcr_launch;
 
 /*

@@ -42,7 +42,7 @@ int grow(void **ptr, size_t *cap, size_t need) {
 
 // Sizes the workspace of one launch needs (all problems together).
 struct Need {
-  size_t tally = 0, acc = 0, mu = 0, cdf = 0, block_sums = 0;
+  size_t tally = 0, acc = 0, mu = 0, cdf = 0, block_sums = 0, order = 0, order_hist = 0;
 };
 
 // Workspace of the current device, grown to `need`.
@@ -68,6 +68,8 @@ int workspace(const Need &need, Workspace **out) {
   if (need.acc && (rc = grow((void **)&w.acc, &w.acc_bytes, need.acc))) return rc;
   if (need.cdf && (rc = grow((void **)&w.cdf, &w.cdf_bytes, need.cdf))) return rc;
   if (need.block_sums && (rc = grow((void **)&w.block_sums, &w.block_sums_bytes, need.block_sums))) return rc;
+  if (need.order && (rc = grow((void **)&w.order, &w.order_bytes, need.order))) return rc;
+  if (need.order_hist && (rc = grow((void **)&w.order_hist, &w.order_hist_bytes, need.order_hist))) return rc;
   *out = &w;
   return MCR_OK;
 }
@@ -137,6 +139,28 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
     }
     if (chunked) need.acc = (size_t)npix * C * sizeof(double);
   }
+  // launch order: by default once the tallies no longer fit in L2, for the kinds it orders
+  bool ordered = false;
+  unsigned total_bins = 0;
+  {
+    bool orderable = false;
+    uint64_t packets = 0;
+    for (int i = 0; i < np; ++i) {
+      orderable |= probs[i].qstar != nullptr || (probs[i].src && probs[i].src->kind == MCR_LINE);
+      packets += chunked ? kChunkPackets : probs[i].n_packets;
+      ProblemDesc d{};
+      d.kind = probs[i].qstar ? kVolume : probs[i].src->kind;
+      d.nx = probs[i].med->nx;
+      d.nz = probs[i].med->nz;
+      total_bins += order_bins(d);
+    }
+    ordered = orderable && packets > 0 && packets <= 0xFFFFFFFFull && !common->sectors && !common->time_bins &&
+              (cfg.launch_order == 2 || (cfg.launch_order == 0 && (double)need.tally > kOrderTallyBytes));
+    if (ordered) {
+      need.order = (size_t)packets * sizeof(unsigned);
+      need.order_hist = (size_t)total_bins * sizeof(unsigned);
+    }
+  }
   Workspace *w = nullptr;
   int rc;
   if ((rc = workspace(need, &w))) return rc;
@@ -169,6 +193,7 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
   p.flags = w->flags();
   std::vector<int> qexp(np);
   uint64_t end = 0;
+  unsigned bin_base = 0;
   for (int i = 0; i < np; ++i) {
     const HostProblem &h = probs[i];
     const int64_t npix = (int64_t)h.med->nx * h.med->nz;
@@ -204,13 +229,17 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
     }
     end += chunked ? 0 : h.n_packets;
     d.end = end;
+    d.bin_base = bin_base;
+    bin_base += order_bins(d);
   }
+  p.order = ordered ? w->order : nullptr;
   MCR_TRY_CUDA(cudaMemsetAsync(w->tally, 0, need.tally, s));
   if (chunked) MCR_TRY_CUDA(cudaMemsetAsync(w->acc, 0, need.acc, s));
   if (timed) MCR_TRY_CUDA(cudaEventRecord(w->ev_start[slot], s));
   if (!chunked) {
     p.total_packets = end;
     MCR_TRY_CUDA(cudaMemsetAsync(w->work(), 0, 8, s));
+    if (end && ordered) MCR_TRY_CUDA(launch_order(p, total_bins, w->order_hist, w->order, s));
     if (end) MCR_TRY_CUDA(launch_transport(p, cfg, s));
   } else {
     const HostProblem &h = probs[0];
@@ -222,6 +251,7 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
       p.prob[0].first_packet = h.first_packet + done;
       p.prob[0].end = this_n;
       p.total_packets = this_n;
+      if (ordered) MCR_TRY_CUDA(launch_order(p, total_bins, w->order_hist, w->order, s));
       MCR_TRY_CUDA(launch_transport(p, cfg, s));
       MCR_TRY_CUDA(launch_accumulate(w->tally, npix, C, Cpad, ldexp(1.0, -qexp[0]), w->acc, s));
       done += this_n;
@@ -341,14 +371,14 @@ int mc_run_batch(const mcr_problem *problems, int32_t n_problems, const mcr_run 
   if (!problems || n_problems < 1 || n_problems > MCR_MAX_BATCH) return MCR_ERR_ARG;
   if ((rc = check_run(common))) return rc;
   if (common->sectors || common->time_bins) return MCR_ERR_ARG;  // these tallies run through mc_forward only
-  TransportLaunch cfg{0, 0, 0, 0};
+  TransportLaunch cfg{0, 0, 0, 0, 0};
   if (launch) {
     if (launch->threads_per_block < 0 || launch->threads_per_block > 256 || launch->threads_per_block % 32 ||
         launch->blocks_per_sm < 0 || launch->merge_collisions < 0 || launch->merge_collisions > 2 ||
-        launch->shared_tally < 0 || launch->shared_tally > 2)
+        launch->shared_tally < 0 || launch->shared_tally > 2 || launch->launch_order < 0 || launch->launch_order > 2)
       return MCR_ERR_ARG;
     cfg = TransportLaunch{launch->threads_per_block, launch->blocks_per_sm, launch->merge_collisions,
-                          launch->shared_tally};
+                          launch->shared_tally, launch->launch_order};
   }
   std::vector<HostProblem> probs;
   uint64_t total = 0;
@@ -471,7 +501,7 @@ int mc_release_workspace(void) {
   std::lock_guard<std::mutex> lock(g_mu);
   MCR_TRY_CUDA(cudaDeviceSynchronize());
   Workspace &w = g_ws[dev];
-  void *ptrs[] = {w.tally, w.acc, w.mu, w.cdf, w.block_sums, w.partials, w.small};
+  void *ptrs[] = {w.tally, w.acc, w.mu, w.cdf, w.block_sums, w.partials, w.small, w.order, w.order_hist};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int k = 0; k < 3; ++k) {

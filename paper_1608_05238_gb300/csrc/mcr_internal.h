@@ -53,6 +53,7 @@ struct ProblemDesc {
   int n_ang;     // MCR_ANGULAR_POINT: harmonics of the launch-angle density
   float ang_c[MCR_MAX_ANG], ang_s[MCR_MAX_ANG];
   unsigned key0, key1;
+  unsigned bin_base;  // launch order: the problem's first bin in the launch's bin space
 };
 
 struct TransportParams {
@@ -66,6 +67,7 @@ struct TransportParams {
   float w_threshold, rr_p, rr_inv_p;
   unsigned long long total_packets;  // = prob[n_problems-1].end
   unsigned long long *work;          // packet counter
+  const unsigned *order;             // launch order: the launch index taken at step g (nullptr: g)
   DevStats *stats;
   unsigned *flags;                   // error bits: transport does nothing if kFlagMedium is set; it
                                      // latches kFlagEventLimit when a packet reached max_events
@@ -78,7 +80,21 @@ struct TransportLaunch {
   int blocks_per_sm;
   int merge;         // collision merge: 0 library default, 1 off, 2 on
   int shared_tally;  // 0 default (global), 1 global, 2 per-block shared-memory copy where it applies
+  int launch_order;  // 0 library default (on above kOrderTallyBytes of tallies), 1 off, 2 on
 };
+
+// Launch order: packets processed in the order of their launch position (line sources: bins of
+// 1/4096 of the line; volumetric sources: 32 x 32-pixel tiles of the launch pixel; other kinds
+// unordered), so that the packets in flight start close together and share the tally rows in
+// L2.  The integer tally does not depend on the order.  On by default once the launch's tallies
+// exceed kOrderTallyBytes (their reductions would otherwise miss L2).
+constexpr double kOrderTallyBytes = 96.0 * 1024 * 1024;
+// Bins of one problem's launch order (1 for unordered kinds).
+unsigned order_bins(const ProblemDesc &d);
+// Fills order[0, p.total_packets) with the launch indices sorted by bin (p.prob[].bin_base set,
+// total_bins their sum); hist: scratch of total_bins words.
+cudaError_t launch_order(const TransportParams &p, unsigned total_bins, unsigned *hist, unsigned *order,
+                         cudaStream_t s);
 
 // Workspace of one device (grow-only).
 struct Workspace {
@@ -93,6 +109,10 @@ struct Workspace {
   size_t cdf_bytes = 0;
   unsigned long long *block_sums = nullptr;
   size_t block_sums_bytes = 0;
+  unsigned *order = nullptr;  // launch order of the packets of one launch
+  size_t order_bytes = 0;
+  unsigned *order_hist = nullptr;
+  size_t order_hist_bytes = 0;
   double *partials = nullptr;
   size_t partials_bytes = 0;
   // small block: packet counter, run counters per call kind (0 forward, 1 adjoint, 2 batch),

@@ -207,10 +207,11 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
       if (lane == leader) base = atomicAdd(p.work, (unsigned long long)__popc(need));
       base = __shfl_sync(kFull, base, leader);
       if (!alive && !exhausted) {
-        const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
-        if (g >= p.total_packets) {
+        const unsigned long long step = base + __popc(need & ((1u << lane) - 1u));
+        if (step >= p.total_packets) {
           exhausted = true;
         } else {
+          const unsigned long long g = p.order ? (unsigned long long)__ldg(p.order + step) : step;
           // the problem owning launch packet g: smallest pi with prob[pi].end > g
           int lo = 0;
           if (BATCH) {
@@ -596,6 +597,92 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
   }
 }
 
+// ---------------------------------------------------------------- launch order
+constexpr int kLineBinsLog2 = 12;  // bins along a line source
+constexpr int kOrderTile = 32;     // volumetric sources: tiles of kOrderTile^2 pixels
+
+__device__ __forceinline__ int problem_of(const TransportParams &p, unsigned long long g) {
+  int lo = 0, hi = p.n_problems - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (p.prob[mid].end > g)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+// The launch-order bin of launch index g: from the same random numbers the launch draws (line
+// position: block 0 word 0; volumetric pixel: block 0 words 0-1), so it is where the packet starts.
+__device__ unsigned launch_bin(const TransportParams &p, unsigned long long g) {
+  const int pi = problem_of(p, g);
+  const ProblemDesc &P = p.prob[pi];
+  const unsigned long long pid = P.first_packet + (g - (pi ? p.prob[pi - 1].end : 0ull));
+  unsigned bin = 0;
+  if (P.kind == MCR_LINE) {
+    bin = philox4x32_10(pid, 0u, P.key0, P.key1).x >> (32 - kLineBinsLog2);
+  } else if (P.kind == kVolume) {
+    const int npix = P.nx * P.nz;
+    const unsigned long long total = __ldg(P.cdf + npix - 1);
+    if (total != 0ull) {
+      const uint4 r0 = philox4x32_10(pid, 0u, P.key0, P.key1);
+      const int pix = pick_pixel(P.cdf, npix, total, r0.x, r0.y);
+      const int ntx = (P.nx + kOrderTile - 1) / kOrderTile;
+      bin = (unsigned)((pix / P.nx) / kOrderTile * ntx + (pix % P.nx) / kOrderTile);
+    }
+  }
+  return P.bin_base + bin;
+}
+
+__global__ void k_order_count(const __grid_constant__ TransportParams p, unsigned *hist) {
+  for (unsigned long long g = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; g < p.total_packets;
+       g += (unsigned long long)gridDim.x * blockDim.x)
+    atomicAdd(hist + launch_bin(p, g), 1u);
+}
+
+// Exclusive scan of the bin counts in place (one block of 1024 threads, chunks of 1024).
+__global__ void k_order_scan(unsigned *hist, unsigned n) {
+  __shared__ unsigned warp_tot[32];
+  __shared__ unsigned carry;
+  if (threadIdx.x == 0) carry = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (unsigned base = 0; base < n; base += 1024) {
+    const unsigned i = base + threadIdx.x;
+    const unsigned x = i < n ? hist[i] : 0u;
+    unsigned v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(kFull, v, o);
+      if (lane >= o) v += t;
+    }
+    if (lane == 31) warp_tot[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+      unsigned t = warp_tot[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_up_sync(kFull, t, o);
+        if (lane >= o) t += u;
+      }
+      warp_tot[lane] = t;
+    }
+    __syncthreads();
+    const unsigned incl = v + (wid ? warp_tot[wid - 1] : 0u);
+    if (i < n) hist[i] = carry + incl - x;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += incl;
+    __syncthreads();
+  }
+}
+
+__global__ void k_order_place(const __grid_constant__ TransportParams p, unsigned *cursor, unsigned *order) {
+  for (unsigned long long g = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; g < p.total_packets;
+       g += (unsigned long long)gridDim.x * blockDim.x)
+    order[atomicAdd(cursor + launch_bin(p, g), 1u)] = (unsigned)g;
+}
+
 size_t shared_tally_bytes(const TransportParams &p) {
   return (size_t)p.prob[0].nx * p.prob[0].nz * p.Cpad * sizeof(unsigned long long);
 }
@@ -692,6 +779,29 @@ cudaError_t launch_np(const TransportParams &p, const TransportLaunch &cfg, cuda
 }
 
 }  // namespace
+
+unsigned order_bins(const ProblemDesc &d) {
+  if (d.kind == MCR_LINE) return 1u << kLineBinsLog2;
+  if (d.kind == kVolume)
+    return (unsigned)(((d.nx + kOrderTile - 1) / kOrderTile) * ((d.nz + kOrderTile - 1) / kOrderTile));
+  return 1u;
+}
+
+cudaError_t launch_order(const TransportParams &p, unsigned total_bins, unsigned *hist, unsigned *order,
+                         cudaStream_t s) {
+  if (p.total_packets == 0 || p.total_packets > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)total_bins * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned long long want = (p.total_packets + 255) / 256;
+  const unsigned grid = (unsigned)(want < (unsigned long long)sms * 8 ? want : (unsigned long long)sms * 8);
+  k_order_count<<<grid, 256, 0, s>>>(p, hist);
+  k_order_scan<<<1, 1024, 0, s>>>(hist, total_bins);
+  k_order_place<<<grid, 256, 0, s>>>(p, hist, order);
+  return cudaGetLastError();
+}
 
 size_t transport_smem_bytes(int row_stride, int threads, bool merge) {
   return (size_t)threads * row_stride * sizeof(float) * (merge ? 2 : 1);

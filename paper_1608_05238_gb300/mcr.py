@@ -70,7 +70,7 @@ class _Problem(C.Structure):
 
 class _Launch(C.Structure):
     _fields_ = [("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("merge_collisions", C.c_int32),
-                ("shared_tally", C.c_int32)]
+                ("shared_tally", C.c_int32), ("launch_order", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -373,9 +373,10 @@ def run_batch(problems: list, common: Run, launch: tuple | None = None, stats: b
     """All ``problems`` in one persistent transport launch (``mc_run_batch``); returns their outputs.
 
     ``common`` gives K and the termination parameters; ``launch`` = (threads_per_block,
-    blocks_per_sm[, merge_collisions[, shared_tally]]) or None for the defaults (0 in a field: its
-    default; merge_collisions 1 off, 2 on; shared_tally 2: per-block shared-memory tally where
-    it applies).  The call can be captured in a CUDA graph once a
+    blocks_per_sm[, merge_collisions[, shared_tally[, launch_order]]]) or None for the defaults
+    (0 in a field: its default; merge_collisions 1 off, 2 on; shared_tally 2: per-block
+    shared-memory tally where it applies; launch_order 1 off, 2 on: packets in the order of their
+    launch position).  The call can be captured in a CUDA graph once a
     first call has grown the library's workspace to this batch's size.
     """
     lib = load()

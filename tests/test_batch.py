@@ -167,3 +167,38 @@ def test_shared_memory_tally_is_bit_identical(adjoint):
         for shape in ((128, 0, 1, 2), (256, 0, 2, 2), (64, 0, 0, 2)):
             got = mcr.run_batch([prob], run, launch=shape)[0]
             assert torch.equal(got, ref), (n, shape)
+
+
+def test_launch_order_is_bit_identical():
+    """Packets processed in the order of their launch position (line sources by position along the
+    line, volumetric sources by 32 x 32-pixel tile) give the same integer tallies as the launch
+    index order, for single problems and for a mixed batch, with and without the collision merge."""
+    K = 16
+    probs, _ = _mixed_problems(K)
+    common = mcr.Run(K=K, n_packets=0)
+    for merge in (1, 2):
+        ref = [o.clone() for o in mcr.run_batch(probs, common, launch=(128, 0, merge, 0, 1))]
+        got = [o.clone() for o in mcr.run_batch(probs, common, launch=(128, 0, merge, 0, 2))]
+        assert all(torch.equal(a, b) for a, b in zip(ref, got))
+        for pr in probs[:3]:
+            one = mcr.run_batch([pr], common, launch=(128, 0, merge, 0, 2))[0].clone()
+            assert torch.equal(one, mcr.run_batch([pr], common, launch=(128, 0, merge, 0, 1))[0])
+
+
+def test_large_tally_runs_ordered_by_default_and_matches_unordered():
+    """A tally beyond 96 MB (768^2 pixels at K = 32: 377 MB) takes the launch order by default in
+    mc_forward and mc_adjoint; the results equal the unordered batched launch bit for bit."""
+    n, dx, K = 768, 0.02, 32
+    mua, mus = workloads.inclusion_phantom(n, dx, 4, seed=3, margin=2.0)
+    med = mcr.Medium(torch.from_numpy(mua).cuda(), torch.from_numpy(mus).cuda(), f32(dx), f32(0.9))
+    src = mcr.Source(**workloads.top_line_source(n, dx))
+    run = mcr.Run(K=K, n_packets=100_000, seed=5)
+    fwd = mcr.forward(med, src, run)
+    ref = mcr.run_batch([mcr.Problem(med, 100_000, seed=5, source=src)], mcr.Run(K=K, n_packets=0),
+                        launch=(0, 0, 0, 0, 1))[0]
+    assert torch.equal(fwd, ref)
+    q = torch.from_numpy(workloads.residual_source(n, dx, 7)).cuda()
+    adj = mcr.adjoint(med, q, mcr.Run(K=K, n_packets=100_000, seed=6, stream_id=1))
+    ref = mcr.run_batch([mcr.Problem(med, 100_000, seed=6, stream_id=1, qstar=q)], mcr.Run(K=K, n_packets=0),
+                        launch=(0, 0, 0, 0, 1))[0]
+    assert torch.equal(adj, ref)
