@@ -60,6 +60,7 @@ class Iteration:
     seconds: float
     rel_err_mua: float | None = None
     rel_err_mus: float | None = None
+    extra: dict | None = None  # what the caller's monitor reported after the step
 
 
 @dataclass
@@ -237,13 +238,15 @@ def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MC
            iters: int = 20, tol: float = 1e-5, line_search: str = "backtracking", step0: float | None = None,
            shrink: float = 0.2, grow: float = 2.0, armijo: float = 1e-4, step_bounds: tuple | None = None,
            max_trials: int = 12, hz: HZParams | None = None, mu_floor: float = 1e-6, mua_true=None, mus_true=None,
-           seed0: int = 1, precondition: bool = False, method: str = "gd", memory: int = 5) -> InversionResult:
+           seed0: int = 1, precondition: bool = False, method: str = "gd", memory: int = 5,
+           monitor=None) -> InversionResult:
     """Reconstruct ``unknowns`` (a subset of ("mua", "mus")) from H^meas; the others stay fixed.
 
     ``step0`` defaults to the step that changes the unknowns by 10 % of their norm on the first
     iteration (1, a full fixed-point-like step, with ``precondition``; for the Hager-Zhang search
     its first trial is 0.01 max|mu| / max|d|).  Returns the estimates and one ``Iteration``
-    record per accepted step (``trials`` = MC evaluations of the line search).
+    record per accepted step (``trials`` = MC evaluations of the line search; ``extra`` =
+    ``monitor(mua, mus)`` after the step, when a monitor is given).
     """
     if line_search not in ("backtracking", "hager_zhang"):
         raise ValueError(f"line_search must be 'backtracking' or 'hager_zhang', not {line_search!r}")
@@ -344,6 +347,8 @@ def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MC
             rec.rel_err_mua = mean_relative_error(mua, mua_true)
         if mus_true is not None:
             rec.rel_err_mus = mean_relative_error(mus, mus_true)
+        if monitor is not None:
+            rec.extra = monitor(mua, mus)
         res.history.append(rec)
         if abs(e_new - eps) <= tol * abs(e_new):  # Eq. 29 (both values from the same packets)
             res.converged = True
