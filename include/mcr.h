@@ -13,7 +13,8 @@
  *
  * Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy default
  * stream) unless a `stats` pointer is given, in which case the call synchronises that stream
- * to fill it.  Every call returns MCR_OK (0) or a negative status; no C++ exception crosses the
+ * to fill it, or the run takes the sorted-record deposit (one problem whose fixed-point tally
+ * exceeds 256 MB, see mcr_launch.deposit), which synchronises once per chunk of packets.  Every call returns MCR_OK (0) or a negative status; no C++ exception crosses the
  * ABI.  Errors found on the device (negative or NaN mu, a packet that hit its event cap, a tally
  * near overflow) are latched per device and returned by the next call that synchronises
  * (a call with stats != NULL, or mc_check).
@@ -41,6 +42,8 @@ extern "C" {
 #define MCR_ERR_TALLY_OVERFLOW (-5) /* a fixed-point tally came within 2 bits of overflow */
 #define MCR_ERR_MEDIUM (-6)         /* the device medium holds a negative or non-finite mu */
 #define MCR_ERR_SCRATCH (-7)        /* problem too large for mc_forward_noalloc's fixed scratch */
+#define MCR_ERR_CHECK (-8)          /* checked build only: an out-of-range index or a non-finite weight was
+                                       found on the device (the access was skipped) */
 
 #define MCR_PENCIL 0    /* collimated beam from (x0, z0) along (dir_x, dir_z)            */
 #define MCR_LINE 1      /* collimated line source: start uniform on (x0,z0)-(x1,z1)       */
@@ -241,6 +244,18 @@ typedef struct {
                                 start close together and their tally rows stay in L2.  The tally does not
                                 depend on the order (bit-identical).  Default: on once the tallies of the
                                 launch exceed 96 MB (mc_forward and mc_adjoint always use the default) */
+  int32_t deposit;           /* 0 default, 1 direct, 2 sorted records (a batch of one harmonic problem):
+                                the transport writes one 16-byte record per pixel segment instead of its
+                                deposit, the records are sorted by pixel and each pixel's run is summed in
+                                registers before one reduction -- the same rounded products, so the tally is
+                                bit-identical, with far less HBM traffic when the tally does not fit in L2.
+                                Default: on for one problem whose tally exceeds 256 MB (mc_forward and
+                                mc_adjoint included).  It reads the record count back once per chunk of
+                                packets (a stream synchronisation), so it is never used while the stream is
+                                being captured into a graph. */
+  int64_t record_capacity;   /* records per chunk of the sorted-record deposit (0: 2^27, 4 GB of buffers);
+                                chunks are sized from the records per packet seen so far, and a chunk that
+                                overflows the buffer is run again with the direct deposit */
 } mcr_launch;
 
 /*

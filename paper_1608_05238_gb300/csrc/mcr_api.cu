@@ -43,6 +43,7 @@ int grow(void **ptr, size_t *cap, size_t need) {
 // Sizes the workspace of one launch needs (all problems together).
 struct Need {
   size_t tally = 0, acc = 0, mu = 0, cdf = 0, block_sums = 0, order = 0, order_hist = 0;
+  size_t records = 0, rec_hist = 0;  // sorted-record deposit (records: each of the two buffers)
 };
 
 // Workspace of the current device, grown to `need`.
@@ -70,6 +71,12 @@ int workspace(const Need &need, Workspace **out) {
   if (need.block_sums && (rc = grow((void **)&w.block_sums, &w.block_sums_bytes, need.block_sums))) return rc;
   if (need.order && (rc = grow((void **)&w.order, &w.order_bytes, need.order))) return rc;
   if (need.order_hist && (rc = grow((void **)&w.order_hist, &w.order_hist_bytes, need.order_hist))) return rc;
+  if (need.records) {
+    if ((rc = grow((void **)&w.records, &w.records_bytes, need.records))) return rc;
+    if ((rc = grow((void **)&w.sorted, &w.sorted_bytes, need.records))) return rc;
+    if ((rc = grow((void **)&w.rec_hdr, &w.rec_hdr_bytes, sizeof(RecordHeader)))) return rc;
+    if ((rc = grow((void **)&w.rec_hist, &w.rec_hist_bytes, need.rec_hist))) return rc;
+  }
   *out = &w;
   return MCR_OK;
 }
@@ -161,6 +168,19 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
       need.order_hist = (size_t)total_bins * sizeof(unsigned);
     }
   }
+  // sorted-record deposit: one harmonic problem whose tally does not fit in L2 (not while a graph
+  // is being captured: the chunk sizes are read back from the device)
+  cudaStreamCaptureStatus cap0 = cudaStreamCaptureStatusNone;
+  MCR_TRY_CUDA(cudaStreamIsCapturing(s, &cap0));
+  const bool rec_mode = np == 1 && !common->sectors && !common->time_bins && cap0 == cudaStreamCaptureStatusNone &&
+                        probs[0].n_packets > 0 &&
+                        (cfg.deposit == 2 || (cfg.deposit == 0 && (double)need.tally > kRecordTallyBytes));
+  const unsigned long long rec_cap = cfg.record_capacity > 0 ? (unsigned long long)cfg.record_capacity : kRecordCapacity;
+  if (rec_mode) {
+    const int64_t npix = (int64_t)probs[0].med->nx * probs[0].med->nz;
+    need.records = (size_t)rec_cap * sizeof(float4);
+    need.rec_hist = ((size_t)npix * 2 + (npix + 255) / 256 + 1) * sizeof(unsigned);
+  }
   Workspace *w = nullptr;
   int rc;
   if ((rc = workspace(need, &w))) return rc;
@@ -236,23 +256,77 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
   MCR_TRY_CUDA(cudaMemsetAsync(w->tally, 0, need.tally, s));
   if (chunked) MCR_TRY_CUDA(cudaMemsetAsync(w->acc, 0, need.acc, s));
   if (timed) MCR_TRY_CUDA(cudaEventRecord(w->ev_start[slot], s));
+  // one problem's packets [first, first + count) added into the tally: directly ...
+  auto direct = [&](uint64_t first, uint64_t count) -> int {
+    MCR_TRY_CUDA(cudaMemsetAsync(w->work(), 0, 8, s));
+    p.prob[0].first_packet = first;
+    p.prob[0].end = count;
+    p.total_packets = count;
+    if (ordered) MCR_TRY_CUDA(launch_order(p, total_bins, w->order_hist, w->order, s));
+    MCR_TRY_CUDA(launch_transport(p, cfg, s));
+    return MCR_OK;
+  };
+  // ... or by sorted records, in chunks sized so that their records fit the buffer (from the most
+  // records per packet seen so far); a chunk whose records overflow runs again directly
+  double rec_per_packet = 0.0;
+  auto by_records = [&](uint64_t first, uint64_t count) -> int {
+    const int64_t npix = (int64_t)probs[0].med->nx * probs[0].med->nz;
+    unsigned *hist = w->rec_hist, *cursor = w->rec_hist + npix, *bsums = w->rec_hist + 2 * npix;
+    for (uint64_t done = 0; done < count;) {
+      uint64_t chunk = rec_per_packet > 0.0 ? (uint64_t)((double)rec_cap / (1.25 * rec_per_packet)) : rec_cap / 4096;
+      chunk = chunk < 1 ? 1 : (chunk > kChunkPackets ? kChunkPackets : chunk);
+      const uint64_t this_n = count - done < chunk ? count - done : chunk;
+      TransportParams q = p;
+      q.prob[0].first_packet = first + done;
+      q.prob[0].end = this_n;
+      q.total_packets = this_n;
+      q.order = nullptr;
+      q.records = w->records;
+      q.rec_count = &w->rec_hdr->count;
+      q.rec_overflow = &w->rec_hdr->overflow;
+      q.rec_capacity = rec_cap;
+      q.rec_hist = hist;
+      q.stats = &w->rec_hdr->stats;
+      MCR_TRY_CUDA(cudaMemsetAsync(w->work(), 0, 8, s));
+      MCR_TRY_CUDA(cudaMemsetAsync(w->rec_hdr, 0, sizeof(RecordHeader), s));
+      MCR_TRY_CUDA(cudaMemsetAsync(hist, 0, (size_t)npix * sizeof(unsigned), s));
+      MCR_TRY_CUDA(launch_transport_records(q, cfg, s));
+      RecordHeader hdr;
+      MCR_TRY_CUDA(cudaMemcpyAsync(&hdr, w->rec_hdr, sizeof(hdr), cudaMemcpyDeviceToHost, s));
+      MCR_TRY_CUDA(cudaStreamSynchronize(s));
+      if (hdr.overflow) {
+        int rc2 = direct(first + done, this_n);
+        if (rc2) return rc2;
+      } else {
+        MCR_TRY_CUDA(launch_sort_and_deposit(w->records, hdr.count, hist, cursor, bsums, (int)npix, w->sorted,
+                                             common->K, Cpad, w->tally, w->flags(), s));
+        MCR_TRY_CUDA(launch_add_stats(p.stats, &w->rec_hdr->stats, s));
+      }
+      const double r = (double)hdr.count / (double)this_n;
+      if (r > rec_per_packet) rec_per_packet = r;
+      done += this_n;
+    }
+    return MCR_OK;
+  };
+  auto run_range = [&](uint64_t first, uint64_t count) -> int {
+    return rec_mode ? by_records(first, count) : direct(first, count);
+  };
   if (!chunked) {
     p.total_packets = end;
-    MCR_TRY_CUDA(cudaMemsetAsync(w->work(), 0, 8, s));
-    if (end && ordered) MCR_TRY_CUDA(launch_order(p, total_bins, w->order_hist, w->order, s));
-    if (end) MCR_TRY_CUDA(launch_transport(p, cfg, s));
+    if (rec_mode) {
+      if ((rc = run_range(probs[0].first_packet, probs[0].n_packets))) return rc;
+    } else {
+      MCR_TRY_CUDA(cudaMemsetAsync(w->work(), 0, 8, s));
+      if (end && ordered) MCR_TRY_CUDA(launch_order(p, total_bins, w->order_hist, w->order, s));
+      if (end) MCR_TRY_CUDA(launch_transport(p, cfg, s));
+    }
   } else {
     const HostProblem &h = probs[0];
     const int64_t npix = (int64_t)h.med->nx * h.med->nz;
     for (uint64_t done = 0; done < h.n_packets;) {
       const uint64_t this_n = h.n_packets - done < kChunkPackets ? h.n_packets - done : kChunkPackets;
       if (done) MCR_TRY_CUDA(cudaMemsetAsync(w->tally, 0, need.tally, s));
-      MCR_TRY_CUDA(cudaMemsetAsync(w->work(), 0, 8, s));
-      p.prob[0].first_packet = h.first_packet + done;
-      p.prob[0].end = this_n;
-      p.total_packets = this_n;
-      if (ordered) MCR_TRY_CUDA(launch_order(p, total_bins, w->order_hist, w->order, s));
-      MCR_TRY_CUDA(launch_transport(p, cfg, s));
+      if ((rc = run_range(h.first_packet + done, this_n))) return rc;
       MCR_TRY_CUDA(launch_accumulate(w->tally, npix, C, Cpad, ldexp(1.0, -qexp[0]), w->acc, s));
       done += this_n;
     }
@@ -371,14 +445,15 @@ int mc_run_batch(const mcr_problem *problems, int32_t n_problems, const mcr_run 
   if (!problems || n_problems < 1 || n_problems > MCR_MAX_BATCH) return MCR_ERR_ARG;
   if ((rc = check_run(common))) return rc;
   if (common->sectors || common->time_bins) return MCR_ERR_ARG;  // these tallies run through mc_forward only
-  TransportLaunch cfg{0, 0, 0, 0, 0};
+  TransportLaunch cfg{0, 0, 0, 0, 0, 0, 0};
   if (launch) {
     if (launch->threads_per_block < 0 || launch->threads_per_block > 256 || launch->threads_per_block % 32 ||
         launch->blocks_per_sm < 0 || launch->merge_collisions < 0 || launch->merge_collisions > 2 ||
-        launch->shared_tally < 0 || launch->shared_tally > 2 || launch->launch_order < 0 || launch->launch_order > 2)
+        launch->shared_tally < 0 || launch->shared_tally > 2 || launch->launch_order < 0 || launch->launch_order > 2 ||
+        launch->deposit < 0 || launch->deposit > 2 || launch->record_capacity < 0)
       return MCR_ERR_ARG;
     cfg = TransportLaunch{launch->threads_per_block, launch->blocks_per_sm, launch->merge_collisions,
-                          launch->shared_tally, launch->launch_order};
+                          launch->shared_tally, launch->launch_order, launch->deposit, launch->record_capacity};
   }
   std::vector<HostProblem> probs;
   uint64_t total = 0;
@@ -501,7 +576,8 @@ int mc_release_workspace(void) {
   std::lock_guard<std::mutex> lock(g_mu);
   MCR_TRY_CUDA(cudaDeviceSynchronize());
   Workspace &w = g_ws[dev];
-  void *ptrs[] = {w.tally, w.acc, w.mu, w.cdf, w.block_sums, w.partials, w.small, w.order, w.order_hist};
+  void *ptrs[] = {w.tally, w.acc, w.mu, w.cdf, w.block_sums, w.partials, w.small, w.order, w.order_hist,
+                  w.records, w.sorted, w.rec_hdr, w.rec_hist};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int k = 0; k < 3; ++k) {
@@ -522,11 +598,16 @@ const char *mc_status_string(int status) {
     case MCR_ERR_TALLY_OVERFLOW: return "fixed-point tally near overflow";
     case MCR_ERR_MEDIUM: return "medium holds a negative or non-finite coefficient";
     case MCR_ERR_SCRATCH: return "problem exceeds the fixed 16 MiB scratch of mc_forward_noalloc";
+    case MCR_ERR_CHECK: return "checked build: out-of-range index or non-finite weight on the device";
     default: return "unknown status";
   }
 }
 
-const char *mc_version(void) { return "mcr 1.0 sm_103a"; }
+#ifdef MCR_CHECKED
+const char *mc_version(void) { return "mcr 1.1 sm_103a checked"; }
+#else
+const char *mc_version(void) { return "mcr 1.1 sm_103a"; }
+#endif
 
 }  // extern "C"
 
@@ -573,6 +654,7 @@ int check_source(const mcr_source *src, float *dirx, float *dirz) {
 }
 
 int status_from_flags(unsigned flags) {
+  if (flags & kFlagChecked) return MCR_ERR_CHECK;
   if (flags & kFlagMedium) return MCR_ERR_MEDIUM;
   if (flags & kFlagOverflow) return MCR_ERR_TALLY_OVERFLOW;
   if (flags & kFlagEventLimit) return MCR_ERR_EVENT_LIMIT;

@@ -32,6 +32,16 @@ struct DevStats {
 constexpr unsigned kFlagEventLimit = 1u;
 constexpr unsigned kFlagOverflow = 2u;
 constexpr unsigned kFlagMedium = 4u;
+constexpr unsigned kFlagChecked = 16u;  // checked build: an index out of range or a non-finite weight
+
+// Checked build (-DMCR_CHECKED, libmcr_checked.so): MCR_GUARD(flags, cond) is cond, and a false
+// cond latches kFlagChecked (MCR_ERR_CHECK at the next mc_check) -- the caller then skips the
+// access, so a broken index never reaches memory.  In the normal build it is `true`.
+#ifdef MCR_CHECKED
+#define MCR_GUARD(flags, cond) ((cond) ? true : (atomicOr((flags), ::mcr::kFlagChecked), false))
+#else
+#define MCR_GUARD(flags, cond) true
+#endif
 
 // Problems per transport launch (the table travels in kernel parameter space).
 constexpr int kMaxBatch = 64;
@@ -68,6 +78,12 @@ struct TransportParams {
   unsigned long long total_packets;  // = prob[n_problems-1].end
   unsigned long long *work;          // packet counter
   const unsigned *order;             // launch order: the launch index taken at step g (nullptr: g)
+  // sorted-record deposit (transport variant RECS): one record per segment instead of deposits
+  float4 *records;                   // (pixel bits, track weight x 2^q, s_x, s_z), capacity rec_capacity
+  unsigned long long *rec_count;     // records written (may pass the capacity: then rec_overflow is set)
+  unsigned *rec_overflow;
+  unsigned long long rec_capacity;
+  unsigned *rec_hist;                // records per pixel
   DevStats *stats;
   unsigned *flags;                   // error bits: transport does nothing if kFlagMedium is set; it
                                      // latches kFlagEventLimit when a packet reached max_events
@@ -81,7 +97,31 @@ struct TransportLaunch {
   int merge;         // collision merge: 0 library default, 1 off, 2 on
   int shared_tally;  // 0 default (global), 1 global, 2 per-block shared-memory copy where it applies
   int launch_order;  // 0 library default (on above kOrderTallyBytes of tallies), 1 off, 2 on
+  int deposit;       // 0 library default (sorted records above kRecordTallyBytes), 1 direct, 2 sorted records
+  long long record_capacity;  // records per chunk of the sorted-record deposit (0: kRecordCapacity)
 };
+
+// Sorted-record deposit (single problems whose tally lives in HBM): the transport writes one
+// record per pixel segment, the records are sorted by pixel (one counting-sort pass) and a
+// deposit kernel sums each pixel's run in registers before one reduction per run.  The integer
+// tally is bit-identical to the direct deposit.
+constexpr double kRecordTallyBytes = 256.0 * 1024 * 1024;
+constexpr unsigned long long kRecordCapacity = 1ull << 27;  // records per chunk (2 GB per buffer)
+struct RecordHeader {
+  unsigned long long count;
+  unsigned overflow;
+  unsigned pad[13];
+  DevStats stats;  // counters of the record-mode launch, added to the run's once its records are deposited
+};
+// dst += src (run counters)
+cudaError_t launch_add_stats(DevStats *dst, const DevStats *src, cudaStream_t s);
+// Launch the transport in record mode (p.records etc. set; single harmonic problem).
+cudaError_t launch_transport_records(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s);
+// cursor[i] = sum_{k<i} hist[k] (exclusive scan of the per-pixel counts), then the records in
+// pixel order into `sorted` (cursor consumed), then the runs of each pixel deposited into the tally.
+cudaError_t launch_sort_and_deposit(const float4 *records, unsigned long long n, const unsigned *hist,
+                                    unsigned *cursor, unsigned *block_sums, int npix, float4 *sorted, int K, int Cpad,
+                                    unsigned long long *tally, unsigned *flags, cudaStream_t s);
 
 // Launch order: packets processed in the order of their launch position (line sources: bins of
 // 1/4096 of the line; volumetric sources: 32 x 32-pixel tiles of the launch pixel; other kinds
@@ -113,6 +153,15 @@ struct Workspace {
   size_t order_bytes = 0;
   unsigned *order_hist = nullptr;
   size_t order_hist_bytes = 0;
+  // sorted-record deposit: records and their pixel-sorted copy, header, per-pixel counts / cursors
+  float4 *records = nullptr;
+  size_t records_bytes = 0;
+  float4 *sorted = nullptr;
+  size_t sorted_bytes = 0;
+  RecordHeader *rec_hdr = nullptr;
+  size_t rec_hdr_bytes = 0;
+  unsigned *rec_hist = nullptr;  // [npix] counts, then [npix] cursors, then block sums
+  size_t rec_hist_bytes = 0;
   double *partials = nullptr;
   size_t partials_bytes = 0;
   // small block: packet counter, run counters per call kind (0 forward, 1 adjoint, 2 batch),

@@ -34,6 +34,7 @@
 
 #include <mutex>
 
+#include "mcr_harmonics.cuh"
 #include "mcr_internal.h"
 #include "mcr_rng.cuh"
 
@@ -100,11 +101,14 @@ __device__ __forceinline__ float launch_angle(const ProblemDesc &P, float u) {
 // NP = -1: the time-resolved variant: each segment's track weight is split over the path-length
 // bins [b w, (b+1) w) it spans (the last bin open-ended), one per-lane reduction per piece; the
 // packet's path and weight updates are those of the plain run.
-template <int NP, bool BATCH, bool MERGE, bool STALLY>
+// RECS: the harmonic tally by sorted records -- each segment with a deposit writes one record
+// (pixel, track weight x 2^q, direction) and counts it for its pixel; the deposit is done later
+// by k_deposit_sorted with the same harmonic rows and products (single problem, no merge).
+template <int NP, bool BATCH, bool MERGE, bool STALLY, bool RECS = false>
 __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ TransportParams p) {
   constexpr bool SECT = NP == 0;
   constexpr bool TIMED = NP < 0;
-  constexpr bool ROWLESS = SECT || TIMED;  // no harmonic rows
+  constexpr bool ROWLESS = SECT || TIMED || RECS;  // no harmonic rows
   static_assert(!ROWLESS || (!BATCH && !MERGE && !STALLY), "the sector and time tallies run one plain forward problem");
   extern __shared__ float smem[];
   const int lane = threadIdx.x & 31;
@@ -124,6 +128,12 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
   // base of the tally row of a segment key ((pixel + 1) << 6 | problem)
   auto tally_row = [&](unsigned key) -> unsigned long long * {
     return (STALLY ? stally : p.prob[BATCH ? (key & 63u) : 0].tally) + (size_t)((key >> 6) - 1u) * p.Cpad;
+  };
+  // checked build: the key names a pixel of its problem (and a problem of the launch)
+  auto row_ok = [&](unsigned key) -> bool {
+    const unsigned pi = BATCH ? (key & 63u) : 0u;
+    return MCR_GUARD(p.flags, pi < (unsigned)p.n_problems && (key >> 6) >= 1u &&
+                                  (key >> 6) - 1u < (unsigned)(p.prob[pi].nx * p.prob[pi].nz));
   };
 
   const int K = p.K, C = p.C;
@@ -165,20 +175,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
   // harmonic row of the current flight direction, h_n = (s_z + i s_x)^n, stored one slot to the
   // right (my[1 + c] holds channel c) so that each (cos n theta, sin n theta) pair is one
   // 8-byte aligned store; the row stride is 2 mod 4 words, so these stores are conflict-free.
-  auto write_row = [&]() {
-    float *const my = rows + (rb * 32 + lane) * p.row_stride;
-    my[1] = 1.f;
-    float c = sz, s = sx;
-    float2 *pairs = reinterpret_cast<float2 *>(my);
-#pragma unroll 4
-    for (int n = 1; n <= K; ++n) {
-      pairs[n] = make_float2(c, s);
-      const float cn = fmaf(c, sz, -s * sx);
-      const float sn = fmaf(s, sz, c * sx);
-      c = cn;
-      s = sn;
-    }
-  };
+  auto write_row = [&]() { harmonic_row(rows + (rb * 32 + lane) * p.row_stride, sx, sz, K); };
   // start free flight number `flight` (event flight+1): tau = -ln U, keep U for scatter/roulette
   auto begin_flight = [&]() {
     const uint4 r = philox4x32_10(pid, flight + 1u, KEY0(), KEY1());
@@ -193,7 +190,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
       float th = atan2f(sx, sz);  // (-pi, pi], from +z
       if (th < 0.f) th += 6.28318530717958648f;
       sect = min((int)(th * p.sector_scale), p.sectors - 1);
-    } else if constexpr (!TIMED) {
+    } else if constexpr (!TIMED && !RECS) {
       write_row();
     }
   };
@@ -312,7 +309,9 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     bool collided = false, escaped = false;
     if (alive) {
       const int pix = iz * NX() + ix;
-      const float4 m = __ldg(MU() + pix);  // (mu_a, mu_s, 1/mu_a, 1/mu_s)
+      float4 m = make_float4(0.f, 0.f, CUDART_INF_F, CUDART_INF_F);
+      if (MCR_GUARD(p.flags, (unsigned)ix < (unsigned)NX() && (unsigned)iz < (unsigned)NZ()))
+        m = __ldg(MU() + pix);  // (mu_a, mu_s, 1/mu_a, 1/mu_s)
       float dist_x = CUDART_INF_F, dist_z = CUDART_INF_F;
       if (sx != 0.f) dist_x = fmaxf((sx > 0.f ? DX() - fx : fx) * inv_ax, 0.f);
       if (sz != 0.f) dist_z = fmaxf((sz > 0.f ? DX() - fz : fz) * inv_az, 0.f);
@@ -337,7 +336,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
         dep_carry = carry;
         carry = 0.f;
       }
-      if (t != 0.f || dep_carry != 0.f) {
+      if ((t != 0.f || dep_carry != 0.f) && MCR_GUARD(p.flags, isfinite(t))) {
         seg_key = ((unsigned)(pix + 1) << 6) | (unsigned)(BATCH ? prob : 0);
         seg_ts = t * QS();
       }
@@ -382,10 +381,11 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
 
     // ---------------------------------------------------------------- cooperative deposit
     if constexpr (SECT) {
-      if (seg_key != 0u) atomicAdd(tally_row(seg_key) + sect, (unsigned long long)(long long)__float2int_rn(seg_ts));
+      if (seg_key != 0u && row_ok(seg_key) && MCR_GUARD(p.flags, sect >= 0 && sect < p.Cpad))
+        atomicAdd(tally_row(seg_key) + sect, (unsigned long long)(long long)__float2int_rn(seg_ts));
     }
     if constexpr (TIMED) {
-      if (seg_key != 0u) {
+      if (seg_key != 0u && row_ok(seg_key)) {
         // piece [s1, s2) of the segment in bin b: W e^{-mu_a s1} (1 - e^{-mu_a (s2 - s1)}) / mu_a
         unsigned long long *row = tally_row(seg_key);
         const int T = p.time_bins;
@@ -398,9 +398,29 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
             const float d = s2 - s1;
             const float tp = seg_mua > 0.f ? seg_w * expf(-seg_mua * s1) * -expm1f(-seg_mua * d) * seg_imua
                                            : seg_w * d;
-            atomicAdd(row + b, (unsigned long long)(long long)__float2int_rn(tp * QS()));
+            if (MCR_GUARD(p.flags, b >= 0 && b < p.Cpad))
+              atomicAdd(row + b, (unsigned long long)(long long)__float2int_rn(tp * QS()));
           }
           if (s2 >= seg_l || b + 1 == T) break;
+        }
+      }
+    }
+    if constexpr (RECS) {
+      const unsigned has = __ballot_sync(kFull, seg_key != 0u);
+      if (has) {  // one counter update per warp step, coalesced 16-byte record stores
+        const int leader = __ffs(has) - 1;
+        unsigned long long rbase = 0;
+        if (lane == leader) rbase = atomicAdd(p.rec_count, (unsigned long long)__popc(has));
+        rbase = __shfl_sync(kFull, rbase, leader);
+        if (seg_key != 0u) {
+          const unsigned long long slot = rbase + __popc(has & ((1u << lane) - 1u));
+          const unsigned pix = (seg_key >> 6) - 1u;
+          if (slot < p.rec_capacity && row_ok(seg_key)) {
+            p.records[slot] = make_float4(__uint_as_float(pix), seg_ts, sx, sz);
+            atomicAdd(p.rec_hist + pix, 1u);
+          } else {
+            atomicOr(p.rec_overflow, 1u);
+          }
         }
       }
     }
@@ -422,7 +442,11 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
           on[r] = easy != 0u;  // warp-uniform
           const int L = on[r] ? __ffs(easy) - 1 : 0;
           easy &= easy - 1u;
-          const unsigned key = on[r] ? __shfl_sync(kFull, seg_key, L) : 64u;
+          unsigned key = on[r] ? __shfl_sync(kFull, seg_key, L) : 64u;
+          if (on[r] && !row_ok(key)) {  // warp-uniform (checked build only)
+            on[r] = false;
+            key = 64u;
+          }
           ts[r] = __shfl_sync(kFull, seg_ts, L);
           dst[r] = tally_row(key);
           hr[r] = rows + ((MERGE ? __shfl_sync(kFull, rb, L) * 32 : 0) + L) * p.row_stride + 1;
@@ -485,14 +509,16 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
             }
           }
         }
+        if (row_ok(key)) {
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          const int j = q * 32 + lane;
-          if (j < Cw) atomicAdd(dst + j, (unsigned long long)acc[q]);
+          for (int q = 0; q < NP; ++q) {
+            const int j = q * 32 + lane;
+            if (j < Cw) atomicAdd(dst + j, (unsigned long long)acc[q]);
+          }
         }
         pend &= ~grp;
       }
-      if (!ROWLESS && Cw < C && seg_key != 0u) {  // the per-lane remainder
+      if (!ROWLESS && Cw < C && seg_key != 0u && row_ok(seg_key)) {  // the per-lane remainder
         unsigned long long *own = tally_row(seg_key);
         const float *h = rows + ((MERGE ? rb * 32 : 0) + lane) * p.row_stride + 1;
         const float *hc = rows + ((MERGE ? carry_rb * 32 : 0) + lane) * p.row_stride + 1;
@@ -693,7 +719,7 @@ size_t shared_tally_bytes(const TransportParams &p) {
 // do not hold the workspace lock (mc_forward_noalloc) reach them from any host thread.
 std::mutex g_attr_mu;
 
-template <int NP, bool BATCH, bool MERGE, bool STALLY = false>
+template <int NP, bool BATCH, bool MERGE, bool STALLY = false, bool RECS = false>
 cudaError_t blocks_per_sm(int threads, size_t smem, int *per_sm) {
   static int configured[64];  // largest dynamic smem opted in, per device
   int dev = 0;
@@ -706,29 +732,30 @@ cudaError_t blocks_per_sm(int threads, size_t smem, int *per_sm) {
   {
     std::lock_guard<std::mutex> lock(g_attr_mu);
     if (dev >= 64 || configured[dev] < (int)smem) {
-      e = cudaFuncSetAttribute(k_transport<NP, BATCH, MERGE, STALLY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
+      e = cudaFuncSetAttribute(k_transport<NP, BATCH, MERGE, STALLY, RECS>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       if (dev < 64) configured[dev] = (int)smem;
     }
   }
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_transport<NP, BATCH, MERGE, STALLY>, threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_transport<NP, BATCH, MERGE, STALLY, RECS>, threads,
+                                                       smem);
 }
 
-template <int NP, bool BATCH, bool MERGE, bool STALLY = false>
+template <int NP, bool BATCH, bool MERGE, bool STALLY = false, bool RECS = false>
 cudaError_t launch_kernel(const TransportParams &p, int threads, int cap, cudaStream_t s) {
   if (threads % 32 || threads > 256 || threads <= 0) return cudaErrorInvalidValue;
-  const size_t smem = transport_smem_bytes(p.row_stride, threads, MERGE) + (STALLY ? shared_tally_bytes(p) : 0);
+  const size_t smem = RECS ? 16 : transport_smem_bytes(p.row_stride, threads, MERGE) + (STALLY ? shared_tally_bytes(p) : 0);
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = blocks_per_sm<NP, BATCH, MERGE, STALLY>(threads, smem, &per_sm);
+  e = blocks_per_sm<NP, BATCH, MERGE, STALLY, RECS>(threads, smem, &per_sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (cap > 0 && cap < per_sm) per_sm = cap;
-  k_transport<NP, BATCH, MERGE, STALLY><<<sms * per_sm, threads, smem, s>>>(p);
+  k_transport<NP, BATCH, MERGE, STALLY, RECS><<<sms * per_sm, threads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -808,6 +835,12 @@ size_t transport_smem_bytes(int row_stride, int threads, bool merge) {
 }
 
 
+
+cudaError_t launch_transport_records(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s) {
+  if (p.n_problems != 1 || p.sectors > 0 || p.time_bins > 0 || !p.records) return cudaErrorInvalidValue;
+  return launch_kernel<1, false, false, false, true>(p, cfg.threads_per_block > 0 ? cfg.threads_per_block : 128,
+                                                    cfg.blocks_per_sm, s);
+}
 
 cudaError_t launch_transport(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s) {
   if (p.sectors > 0 || p.time_bins > 0) {  // discrete ordinates / time bins: one plain forward problem

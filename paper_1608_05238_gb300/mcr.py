@@ -23,6 +23,7 @@ PENCIL, LINE, ISO_POINT, ANGULAR_POINT = 0, 1, 2, 3
 MAX_K = 64
 
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_EVENT_LIMIT, ERR_TALLY_OVERFLOW, ERR_MEDIUM = 0, -1, -2, -3, -4, -5, -6
+ERR_CHECK = -8  # checked build only
 
 # every symbol declared in include/mcr.h
 EXPORTS = ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_forward_raw", "mc_adjoint_raw", "mc_finalize",
@@ -70,7 +71,8 @@ class _Problem(C.Structure):
 
 class _Launch(C.Structure):
     _fields_ = [("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("merge_collisions", C.c_int32),
-                ("shared_tally", C.c_int32), ("launch_order", C.c_int32)]
+                ("shared_tally", C.c_int32), ("launch_order", C.c_int32), ("deposit", C.c_int32),
+                ("record_capacity", C.c_int64)]
 
 
 class _Stats(C.Structure):
@@ -95,41 +97,61 @@ def load() -> C.CDLL:
             return _lib
         if not os.path.exists(_build.LIB):
             raise RuntimeError(f"libmcr.so is not built ({_build.LIB}); run __graft_entry__.build() first")
-        lib = C.CDLL(_build.LIB)
-        vp = C.c_void_p
-        lib.mc_forward.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
-        lib.mc_forward_noalloc.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run), vp, vp]
-        lib.mc_adjoint.argtypes = [C.POINTER(_Medium), vp, C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
-        lib.mc_forward_raw.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run), vp,
-                                       C.POINTER(_Stats), vp]
-        lib.mc_adjoint_raw.argtypes = [C.POINTER(_Medium), vp, C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
-        lib.mc_finalize.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), vp, C.POINTER(_Run), vp, vp, vp]
-        lib.mc_run_batch.argtypes = [C.POINTER(_Problem), C.c_int32, C.POINTER(_Run), C.POINTER(_Launch),
-                                     C.POINTER(_Stats), vp]
-        lib.mc_h_eps.argtypes = [C.POINTER(_Medium), vp, vp, vp, vp, vp, vp]
-        lib.mc_adjoint_source.argtypes = [C.POINTER(_Medium), vp, vp, vp]
-        lib.mc_gradient.argtypes = [C.POINTER(_Medium), C.c_int32, vp, vp, vp, vp, vp, vp]
-        lib.mc_gradient_f32.argtypes = [C.POINTER(_Medium), C.c_int32, vp, vp, vp, vp, vp, vp]
-        lib.mc_eps.argtypes = [C.c_int64, C.c_double, vp, vp, vp, vp, vp]
-        lib.mc_dot.argtypes = [C.c_int64, vp, vp, vp, vp]
-        lib.mc_check.argtypes = [vp]
-        lib.mc_reduction_probe.argtypes = [vp, C.c_int64, C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32, vp]
-        lib.mc_philox_blocks.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_int32,
-                                         C.POINTER(C.c_uint32)]
-        lib.mc_philox_blocks.restype = C.c_int
-        lib.mc_last_run_info.argtypes = [C.c_int32, C.POINTER(_Stats), C.POINTER(C.c_float)]
-        lib.mc_release_workspace.argtypes = []
-        lib.mc_status_string.argtypes = [C.c_int]
-        lib.mc_status_string.restype = C.c_char_p
-        lib.mc_version.argtypes = []
-        lib.mc_version.restype = C.c_char_p
-        for name in ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_forward_raw", "mc_adjoint_raw",
-                     "mc_finalize", "mc_run_batch", "mc_h_eps", "mc_eps", "mc_dot",
-                     "mc_adjoint_source", "mc_gradient", "mc_gradient_f32", "mc_check", "mc_last_run_info",
-                     "mc_release_workspace"):
-            getattr(lib, name).restype = C.c_int
-        _lib = lib
-        return lib
+        _lib = _declare(C.CDLL(_build.LIB))
+        return _lib
+
+
+_lib_checked = None
+
+
+def load_checked() -> C.CDLL:
+    """The checked build, libmcr_checked.so (the transport library compiled with MCR_CHECKED: every
+    tally, medium and record index range-checked on the device, a failed check latching
+    ERR_CHECK instead of touching memory).  Same C ABI as libmcr.so minus the denoiser calls."""
+    global _lib_checked
+    with _lock:
+        if _lib_checked is None:
+            if not os.path.exists(_build.LIB_CHECKED):
+                raise RuntimeError(f"libmcr_checked.so is not built ({_build.LIB_CHECKED})")
+            _lib_checked = _declare(C.CDLL(_build.LIB_CHECKED))
+        return _lib_checked
+
+
+def _declare(lib: C.CDLL) -> C.CDLL:
+    """Argument and result types of the C ABI on a loaded library."""
+    vp = C.c_void_p
+    lib.mc_forward.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
+    lib.mc_forward_noalloc.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run), vp, vp]
+    lib.mc_adjoint.argtypes = [C.POINTER(_Medium), vp, C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
+    lib.mc_forward_raw.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), C.POINTER(_Run), vp,
+                                   C.POINTER(_Stats), vp]
+    lib.mc_adjoint_raw.argtypes = [C.POINTER(_Medium), vp, C.POINTER(_Run), vp, C.POINTER(_Stats), vp]
+    lib.mc_finalize.argtypes = [C.POINTER(_Medium), C.POINTER(_Source), vp, C.POINTER(_Run), vp, vp, vp]
+    lib.mc_run_batch.argtypes = [C.POINTER(_Problem), C.c_int32, C.POINTER(_Run), C.POINTER(_Launch),
+                                 C.POINTER(_Stats), vp]
+    lib.mc_h_eps.argtypes = [C.POINTER(_Medium), vp, vp, vp, vp, vp, vp]
+    lib.mc_adjoint_source.argtypes = [C.POINTER(_Medium), vp, vp, vp]
+    lib.mc_gradient.argtypes = [C.POINTER(_Medium), C.c_int32, vp, vp, vp, vp, vp, vp]
+    lib.mc_gradient_f32.argtypes = [C.POINTER(_Medium), C.c_int32, vp, vp, vp, vp, vp, vp]
+    lib.mc_eps.argtypes = [C.c_int64, C.c_double, vp, vp, vp, vp, vp]
+    lib.mc_dot.argtypes = [C.c_int64, vp, vp, vp, vp]
+    lib.mc_check.argtypes = [vp]
+    lib.mc_reduction_probe.argtypes = [vp, C.c_int64, C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32, vp]
+    lib.mc_philox_blocks.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_int32,
+                                     C.POINTER(C.c_uint32)]
+    lib.mc_philox_blocks.restype = C.c_int
+    lib.mc_last_run_info.argtypes = [C.c_int32, C.POINTER(_Stats), C.POINTER(C.c_float)]
+    lib.mc_release_workspace.argtypes = []
+    lib.mc_status_string.argtypes = [C.c_int]
+    lib.mc_status_string.restype = C.c_char_p
+    lib.mc_version.argtypes = []
+    lib.mc_version.restype = C.c_char_p
+    for name in ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_forward_raw", "mc_adjoint_raw",
+                 "mc_finalize", "mc_run_batch", "mc_h_eps", "mc_eps", "mc_dot",
+                 "mc_adjoint_source", "mc_gradient", "mc_gradient_f32", "mc_check", "mc_last_run_info",
+                 "mc_release_workspace"):
+        getattr(lib, name).restype = C.c_int
+    return lib
 
 
 def status_string(status: int) -> str:
@@ -376,7 +398,8 @@ def run_batch(problems: list, common: Run, launch: tuple | None = None, stats: b
     blocks_per_sm[, merge_collisions[, shared_tally[, launch_order]]]) or None for the defaults
     (0 in a field: its default; merge_collisions 1 off, 2 on; shared_tally 2: per-block
     shared-memory tally where it applies; launch_order 1 off, 2 on: packets in the order of their
-    launch position).  The call can be captured in a CUDA graph once a
+    launch position; deposit 1 direct, 2 sorted records (a batch of one harmonic problem);
+    record_capacity: records per chunk of the sorted-record deposit).  The call can be captured in a CUDA graph once a
     first call has grown the library's workspace to this batch's size.
     """
     lib = load()

@@ -202,3 +202,36 @@ def test_large_tally_runs_ordered_by_default_and_matches_unordered():
     ref = mcr.run_batch([mcr.Problem(med, 100_000, seed=6, stream_id=1, qstar=q)], mcr.Run(K=K, n_packets=0),
                         launch=(0, 0, 0, 0, 1))[0]
     assert torch.equal(adj, ref)
+
+
+@pytest.mark.parametrize("K", [8, 32, 64])
+def test_sorted_record_deposit_is_bit_identical(K):
+    """The sorted-record deposit (records of every segment, counting-sorted by pixel, each pixel's
+    run summed in registers) against the direct deposit, forward (line source) and adjoint: the
+    integer tallies and the run counters are identical whether the records of a chunk fit the
+    buffer, some chunks overflow it and run again directly, or every chunk does."""
+    med, _, _ = _medium(72, 64, 0.06, 0.85, seed=91)
+    src = mcr.Source(mcr.LINE, x0=0.0, z0=0.0, x1=f32(64 * 0.06), z1=0.0, dir_x=0.2, dir_z=1.0)
+    q = torch.from_numpy(np.random.default_rng(4).normal(size=(72, 64)).astype(np.float32)).cuda()
+    common = mcr.Run(K=K, n_packets=0)
+    for pr in (mcr.Problem(med, 30_001, seed=12, source=src), mcr.Problem(med, 20_003, seed=13, stream_id=1, qstar=q)):
+        ref, st_ref = mcr.run_batch([pr], common, launch=(128, 0, 0, 0, 0, 1, 0), stats=True)
+        ref = ref[0].clone()
+        for cap in (0, 60_000, 100):  # default buffer; chunks that sometimes overflow; always overflows
+            got, st = mcr.run_batch([pr], common, launch=(128, 0, 0, 0, 0, 2, cap), stats=True)
+            assert torch.equal(got[0], ref), cap
+            for k in ("launched", "flights", "collisions", "segments", "escapes", "rr_kill", "rr_survive"):
+                assert st[k] == st_ref[k], (cap, k)
+
+
+def test_large_single_problem_takes_the_sorted_record_deposit_by_default():
+    """Above 256 MB of tally (640^2 px at K = 64: 472 MB) mc_forward takes the sorted-record deposit;
+    it equals the direct deposit of the batched call bit for bit."""
+    n, dx, K = 640, 0.02, 64
+    mua, mus = workloads.inclusion_phantom(n, dx, 4, seed=8, margin=2.0)
+    med = mcr.Medium(torch.from_numpy(mua).cuda(), torch.from_numpy(mus).cuda(), f32(dx), f32(0.9))
+    src = mcr.Source(**workloads.top_line_source(n, dx))
+    fwd = mcr.forward(med, src, mcr.Run(K=K, n_packets=50_000, seed=3))
+    ref = mcr.run_batch([mcr.Problem(med, 50_000, seed=3, source=src)], mcr.Run(K=K, n_packets=0),
+                        launch=(0, 0, 0, 0, 0, 1, 0))[0]
+    assert torch.equal(fwd, ref)
