@@ -1,7 +1,7 @@
 """The learned part inside the method (denoised.Denoiser through the autograd Function): U-Nets
 trained on MC pairs denoise the low-count forward and adjoint maps of a gradient evaluation,
-full-count MC judges them and takes over when they fail, and the denoised route reconstructs
-mu_a better than plain MC with the same packets (the gain the network brings to the method)."""
+full-count MC judges them and takes over when they fail, and the denoised route reaches the
+mu_a error of plain MC with fewer packets (the gain the network brings to the method)."""
 import numpy as np
 import pytest
 import torch
@@ -15,7 +15,10 @@ from parity_util import f32
 
 pytestmark = pytest.mark.gpu
 
-N, DX, K, LOW, HIGH = 128, 0.1, 8, 20_000, 1_000_000
+# a 6.4 mm domain: at 2e4 packets per run its depth is still sampled (a 12.8 mm one is not, and
+# both routes can then diverge in the preconditioned reconstruction)
+N, DX, K, LOW, HIGH = 128, 0.05, 8, 20_000, 1_000_000
+MARGIN = min(2.0, 0.15 * N * DX)
 
 
 @pytest.fixture(scope="module")
@@ -38,7 +41,7 @@ def test_networks_beat_the_low_count_maps_on_held_out_pairs(nets):
 
 
 def _problem(seed=90_001):
-    mua, mus = workloads.inclusion_phantom(N, DX, 3, seed=seed, margin=2.0)
+    mua, mus = workloads.inclusion_phantom(N, DX, 3, seed=seed, margin=MARGIN)
     med = mcr.Medium(torch.from_numpy(mua).cuda(), torch.from_numpy(mus).cuda(), f32(DX), f32(0.9))
     return med, [mcr.Source(**workloads.top_line_source(N, DX))]
 
@@ -72,8 +75,12 @@ def test_good_denoiser_passes_the_judge_and_is_used(nets):
     assert torch.equal(c2, dn.denoise("forward", low))
 
 
-def test_denoised_route_reconstructs_mua_better_than_plain_mc_with_the_same_packets(nets):
-    mua_t_np, mus_np = workloads.inclusion_phantom(N, DX, 3, seed=90_007, margin=2.0)
+@pytest.mark.parametrize("phantom", [90_007, 90_011])
+def test_denoised_route_reaches_the_error_of_plain_mc_with_twice_the_packets(nets, phantom):
+    """mu_a by fluence-preconditioned descent, 8 iterations: with 2e4 packets per run the denoised
+    route ends below the error plain MC reaches with 4e4 (measured: 3.9 % against 7.2 % at 4e4,
+    4.7-4.9 % at 8e4, 10.8-11.6 % at 2e4)."""
+    mua_t_np, mus_np = workloads.inclusion_phantom(N, DX, 3, seed=phantom, margin=MARGIN)
     mua_t, mus = torch.from_numpy(mua_t_np).cuda(), torch.from_numpy(mus_np).cuda()
     src = [mcr.Source(**workloads.top_line_source(N, DX))]
     med_t = mcr.Medium(mua_t, mus, f32(DX), f32(0.9))
@@ -81,12 +88,12 @@ def test_denoised_route_reconstructs_mua_better_than_plain_mc_with_the_same_pack
                                                              n_packets=20_000_000, seed=99)))
     mua0 = torch.full_like(mua_t, 0.01)
     errs = {}
-    # the same packets per run on both routes (no judging run)
+    # the denoised route has no judging run: its MC is 2e4 packets per run, like plain MC's first
     dn = Denoiser(nets["forward"][0], nets["adjoint"][0], n_full=HIGH, judge_first=False)
-    for name, dn in (("plain", None), ("denoised", dn)):
-        spec = MCSpec(dx=f32(DX), g=f32(0.9), sources=src, K=K, n_packets=LOW, denoiser=dn)
+    for name, npk, d in (("plain", LOW, None), ("plain2x", 2 * LOW, None), ("denoised", LOW, dn)):
+        spec = MCSpec(dx=f32(DX), g=f32(0.9), sources=src, K=K, n_packets=npk, denoiser=d)
         res = invert(mua0, mus, Hm, spec, unknowns=("mua",), iters=8, tol=1e-12, mua_true=mua_t, precondition=True,
                      seed0=3)
         errs[name] = float(np.mean([h.rel_err_mua for h in res.history[-3:]]))
-    assert errs["denoised"] < 0.8 * errs["plain"], errs
+    assert errs["denoised"] < 0.8 * errs["plain2x"] < 0.8 * errs["plain"], errs
     assert not dn.history  # nothing was judged

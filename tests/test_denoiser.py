@@ -305,13 +305,23 @@ def test_unet_forward_and_gradients_match_reference():
     s = scale.cpu().view(B, 1, 1, 1)
     rl, ry, rg = ref.loss_and_grads(net.state(), x * s, t * s, bf16=True)
     assert abs(loss - rl) <= 2e-3 * rl
+    # Element by element, per layer: the GPU keeps activations in BF16 (8-bit mantissa, rounding
+    # 2^-9 relative) and accumulates in another order than the reference, so the two sides round
+    # slightly different FP32 values to BF16 and about one activation in 1e3 differs by one BF16
+    # unit (2^-8); propagated through up to 14 layers of the backward chain, a weight-gradient
+    # element then moves by a few percent of its layer's RMS gradient (measured: at most 0.070 of
+    # the RMS for weights, 0.017 for biases, over two inputs).  Bound: 0.15 x RMS for weight
+    # elements, 0.05 x RMS for bias elements, plus the norm and direction of the whole layer.
     for name, lay in net.layers.items():
-        gw, gb = lay.gw.cpu(), lay.gb.cpu()
-        rw, rb = rg[name]
+        gw, gb = lay.gw.cpu().double(), lay.gb.cpu().double()
+        rw, rb = (v.double() for v in rg[name])
         err = (gw - rw).norm() / rw.norm()
         cos = torch.nn.functional.cosine_similarity(gw.flatten(), rw.flatten(), dim=0)
         assert err < 5e-2 and cos > 0.998, (name, err.item(), cos.item())
-        assert (gb - rb).norm() / (rb.norm() + 1e-30) < 5e-2, name
+        rms_w = rw.pow(2).mean().sqrt()
+        assert float((gw - rw).abs().max()) <= 0.15 * float(rms_w), (name, float((gw - rw).abs().max() / rms_w))
+        rms_b = rb.pow(2).mean().sqrt()
+        assert float((gb - rb).abs().max()) <= 0.05 * float(rms_b) + 1e-30, name
 
 
 def test_unet_training_reduces_loss():
