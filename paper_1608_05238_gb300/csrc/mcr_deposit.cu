@@ -72,6 +72,7 @@ __global__ void k_scan_blocks(unsigned *block_sums, int nblocks) {
     if (i < nblocks) block_sums[i] = carry + v - x;
     carry += __shfl_sync(kFull, v, 31);
   }
+  if (lane == 0) block_sums[nblocks] = carry;  // the grand total: the number of records
 }
 
 __global__ void k_scan_add(unsigned *__restrict__ cursor, int n, const unsigned *__restrict__ block_sums) {
@@ -85,6 +86,7 @@ __global__ void k_scatter_records(const float4 *__restrict__ rec, unsigned long 
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const float4 r = rec[i];
+    if (__float_as_uint(r.x) == kRecSentinel) continue;  // an unused slot of a warp's block
     if (MCR_GUARD(flags, __float_as_uint(r.x) < (unsigned)npix)) {
       const unsigned slot = atomicAdd(cursor + __float_as_uint(r.x), 1u);
       if (MCR_GUARD(flags, slot < n)) sorted[slot] = r;
@@ -95,11 +97,12 @@ __global__ void k_scatter_records(const float4 *__restrict__ rec, unsigned long 
 // Pixel runs of the sorted records into the tally.  Each warp owns a contiguous span of records;
 // NPK = ceil((2K+1) / 32) coefficient chunks, coefficient j = 32 q + lane of chunk q.
 template <int NPK>
-__global__ void __launch_bounds__(128) k_deposit_sorted(const float4 *__restrict__ rec, unsigned long long n, int K,
+__global__ void __launch_bounds__(128) k_deposit_sorted(const float4 *__restrict__ rec, const unsigned *n_records, int K,
                                                        int row_stride, int Cpad, int npix,
                                                        unsigned long long *__restrict__ tally, unsigned *flags) {
   extern __shared__ float smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long n = *n_records;  // the records the scan counted (sentinels excluded)
   float *const rows = smem + (size_t)warp * 32 * row_stride;  // the warp's 32 rows
   const int C = 2 * K + 1;
   const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
@@ -158,8 +161,8 @@ int grid_for(unsigned long long n, int threads, int per_sm) {
 }
 
 template <int NPK>
-cudaError_t launch_deposit(const float4 *sorted, unsigned long long n, int K, int Cpad, int npix,
-                           unsigned long long *tally, unsigned *flags, cudaStream_t s) {
+cudaError_t launch_deposit(const float4 *sorted, unsigned long long n, const unsigned *n_records, int K, int Cpad,
+                           int npix, unsigned long long *tally, unsigned *flags, cudaStream_t s) {
   const int row_stride = transport_row_stride(2 * K + 1);
   const int threads = 128;
   const size_t smem = (size_t)(threads / 32) * 32 * row_stride * sizeof(float);
@@ -178,7 +181,7 @@ cudaError_t launch_deposit(const float4 *sorted, unsigned long long n, int K, in
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   // about 32 records per warp at least, so that a span is not shorter than one batch
   const int blocks = grid_for((n + 31) / 32, threads / 32, per_sm);
-  k_deposit_sorted<NPK><<<blocks, threads, smem, s>>>(sorted, n, K, row_stride, Cpad, npix, tally, flags);
+  k_deposit_sorted<NPK><<<blocks, threads, smem, s>>>(sorted, n_records, K, row_stride, Cpad, npix, tally, flags);
   return cudaGetLastError();
 }
 
@@ -217,11 +220,11 @@ cudaError_t launch_sort_and_deposit(const float4 *records, unsigned long long n,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   switch ((2 * K + 1 + 31) / 32) {
-    case 1: return launch_deposit<1>(sorted, n, K, Cpad, npix, tally, flags, s);
-    case 2: return launch_deposit<2>(sorted, n, K, Cpad, npix, tally, flags, s);
-    case 3: return launch_deposit<3>(sorted, n, K, Cpad, npix, tally, flags, s);
-    case 4: return launch_deposit<4>(sorted, n, K, Cpad, npix, tally, flags, s);
-    case 5: return launch_deposit<5>(sorted, n, K, Cpad, npix, tally, flags, s);
+    case 1: return launch_deposit<1>(sorted, n, block_sums + nblocks, K, Cpad, npix, tally, flags, s);
+    case 2: return launch_deposit<2>(sorted, n, block_sums + nblocks, K, Cpad, npix, tally, flags, s);
+    case 3: return launch_deposit<3>(sorted, n, block_sums + nblocks, K, Cpad, npix, tally, flags, s);
+    case 4: return launch_deposit<4>(sorted, n, block_sums + nblocks, K, Cpad, npix, tally, flags, s);
+    case 5: return launch_deposit<5>(sorted, n, block_sums + nblocks, K, Cpad, npix, tally, flags, s);
     default: return cudaErrorInvalidValue;
   }
 }

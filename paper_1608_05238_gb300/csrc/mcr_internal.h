@@ -107,6 +107,8 @@ struct TransportLaunch {
 // tally is bit-identical to the direct deposit.
 constexpr double kRecordTallyBytes = 256.0 * 1024 * 1024;
 constexpr unsigned long long kRecordCapacity = 1ull << 27;  // records per chunk (2 GB per buffer)
+constexpr unsigned kRecBlock = 1024;            // record slots a warp reserves at a time
+constexpr unsigned kRecSentinel = 0xFFFFFFFFu;  // pixel field of an unused slot
 struct RecordHeader {
   unsigned long long count;
   unsigned overflow;

@@ -163,6 +163,15 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
   float fx = 0.f, fz = 0.f, sx = 0.f, sz = 1.f, inv_ax = 0.f, inv_az = 0.f, W = 0.f, tau = 0.f;
   int ix = 0, iz = 0;
   unsigned flight = 0, nscat = 0, cu1 = 0, cu2 = 0;
+  // RECS: the warp's block of record slots [rec_block, rec_block + kRecBlock), filled to rec_fill;
+  // slots left empty when a block is closed hold a sentinel that the sort skips
+  unsigned long long rec_block = 0;
+  unsigned rec_fill = kRecBlock;
+  auto rec_pad = [&]() {
+    if (rec_fill >= kRecBlock) return;
+    for (unsigned j = rec_fill + lane; j < kRecBlock; j += 32)
+      if (rec_block + j < p.rec_capacity) p.records[rec_block + j] = make_float4(__uint_as_float(kRecSentinel), 0.f, 0.f, 1.f);
+  };
   int sect = 0;           // SECT: the current flight's angular sector
   float plen = 0.f;       // TIMED: path length since launch
   int rb = 0;             // row of the current flight's harmonics
@@ -407,13 +416,17 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     }
     if constexpr (RECS) {
       const unsigned has = __ballot_sync(kFull, seg_key != 0u);
-      if (has) {  // one counter update per warp step, coalesced 16-byte record stores
-        const int leader = __ffs(has) - 1;
-        unsigned long long rbase = 0;
-        if (lane == leader) rbase = atomicAdd(p.rec_count, (unsigned long long)__popc(has));
-        rbase = __shfl_sync(kFull, rbase, leader);
+      if (has) {  // coalesced 16-byte record stores into the warp's own block of slots
+        const unsigned n = __popc(has);
+        if (rec_fill + n > kRecBlock) {  // warp-uniform: close the block, reserve the next one
+          rec_pad();
+          unsigned long long nb = 0;
+          if (lane == 0) nb = atomicAdd(p.rec_count, (unsigned long long)kRecBlock);
+          rec_block = __shfl_sync(kFull, nb, 0);
+          rec_fill = 0;
+        }
         if (seg_key != 0u) {
-          const unsigned long long slot = rbase + __popc(has & ((1u << lane) - 1u));
+          const unsigned long long slot = rec_block + rec_fill + __popc(has & ((1u << lane) - 1u));
           const unsigned pix = (seg_key >> 6) - 1u;
           if (slot < p.rec_capacity && row_ok(seg_key)) {
             p.records[slot] = make_float4(__uint_as_float(pix), seg_ts, sx, sz);
@@ -422,6 +435,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
             atomicOr(p.rec_overflow, 1u);
           }
         }
+        rec_fill += n;
       }
     }
     unsigned pend = ROWLESS ? 0u : __ballot_sync(kFull, seg_key != 0u);
@@ -585,6 +599,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     __syncwarp();
   }
 
+  if constexpr (RECS) rec_pad();  // the warp's last block
   // ---------------------------------------------------------------- counters
   const unsigned c_launch = __reduce_add_sync(kFull, n_launch), c_flight = __reduce_add_sync(kFull, n_flight),
                  c_coll = __reduce_add_sync(kFull, n_coll), c_seg = __reduce_add_sync(kFull, n_seg),
