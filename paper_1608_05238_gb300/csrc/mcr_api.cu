@@ -298,7 +298,9 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
         int rc2 = direct(first + done, this_n);
         if (rc2) return rc2;
       } else {
-        MCR_TRY_CUDA(launch_sort_and_deposit(w->records, hdr.count, hist, cursor, bsums, (int)npix, w->sorted,
+        // slots reserved past the capacity (a warp's last block may straddle it) were never written
+        const unsigned long long n_slots = hdr.count < rec_cap ? hdr.count : rec_cap;
+        MCR_TRY_CUDA(launch_sort_and_deposit(w->records, n_slots, hist, cursor, bsums, (int)npix, w->sorted,
                                              common->K, Cpad, w->tally, w->flags(), s));
         MCR_TRY_CUDA(launch_add_stats(p.stats, &w->rec_hdr->stats, s));
       }

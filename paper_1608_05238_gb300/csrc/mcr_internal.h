@@ -121,6 +121,7 @@ cudaError_t launch_add_stats(DevStats *dst, const DevStats *src, cudaStream_t s)
 cudaError_t launch_transport_records(const TransportParams &p, const TransportLaunch &cfg, cudaStream_t s);
 // cursor[i] = sum_{k<i} hist[k] (exclusive scan of the per-pixel counts), then the records in
 // pixel order into `sorted` (cursor consumed), then the runs of each pixel deposited into the tally.
+// n: the written slots to read (at most the records buffer's capacity; sentinels are skipped).
 cudaError_t launch_sort_and_deposit(const float4 *records, unsigned long long n, const unsigned *hist,
                                     unsigned *cursor, unsigned *block_sums, int npix, float4 *sorted, int K, int Cpad,
                                     unsigned long long *tally, unsigned *flags, cudaStream_t s);
