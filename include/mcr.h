@@ -253,9 +253,10 @@ typedef struct {
                                 mc_adjoint included).  It reads the record count back once per chunk of
                                 packets (a stream synchronisation), so it is never used while the stream is
                                 being captured into a graph. */
-  int64_t record_capacity;   /* records per chunk of the sorted-record deposit (0: 2^27, 4 GB of buffers);
-                                chunks are sized from the records per packet seen so far, and a chunk that
-                                overflows the buffer is run again with the direct deposit */
+  int64_t record_capacity;   /* records per chunk of the sorted-record deposit (0: 2^30, two 16 GB buffers;
+                                if they cannot be allocated the run deposits directly); chunks are sized
+                                from the records per packet seen so far, and a chunk that overflows the
+                                buffer is run again with the direct deposit */
 } mcr_launch;
 
 /*

@@ -172,7 +172,7 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
   // is being captured: the chunk sizes are read back from the device)
   cudaStreamCaptureStatus cap0 = cudaStreamCaptureStatusNone;
   MCR_TRY_CUDA(cudaStreamIsCapturing(s, &cap0));
-  const bool rec_mode = np == 1 && !common->sectors && !common->time_bins && cap0 == cudaStreamCaptureStatusNone &&
+  bool rec_mode = np == 1 && !common->sectors && !common->time_bins && cap0 == cudaStreamCaptureStatusNone &&
                         probs[0].n_packets > 0 &&
                         (cfg.deposit == 2 || (cfg.deposit == 0 && (double)need.tally > kRecordTallyBytes));
   const unsigned long long rec_cap = cfg.record_capacity > 0 ? (unsigned long long)cfg.record_capacity : kRecordCapacity;
@@ -182,8 +182,13 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
     need.rec_hist = ((size_t)npix * 2 + (npix + 255) / 256 + 1) * sizeof(unsigned);
   }
   Workspace *w = nullptr;
-  int rc;
-  if ((rc = workspace(need, &w))) return rc;
+  int rc = workspace(need, &w);
+  if (rc == MCR_ERR_NOMEM && rec_mode) {  // no room for the record buffers: deposit directly
+    rec_mode = false;
+    need.records = need.rec_hist = 0;
+    rc = workspace(need, &w);
+  }
+  if (rc) return rc;
 
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   MCR_TRY_CUDA(cudaStreamIsCapturing(s, &cap));
@@ -273,7 +278,8 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
     const int64_t npix = (int64_t)probs[0].med->nx * probs[0].med->nz;
     unsigned *hist = w->rec_hist, *cursor = w->rec_hist + npix, *bsums = w->rec_hist + 2 * npix;
     for (uint64_t done = 0; done < count;) {
-      uint64_t chunk = rec_per_packet > 0.0 ? (uint64_t)((double)rec_cap / (1.25 * rec_per_packet)) : rec_cap / 4096;
+      // first chunk: room for 2048 records per packet; then from the most records per packet seen
+      uint64_t chunk = rec_per_packet > 0.0 ? (uint64_t)((double)rec_cap / (1.25 * rec_per_packet)) : rec_cap / 2048;
       chunk = chunk < 1 ? 1 : (chunk > kChunkPackets ? kChunkPackets : chunk);
       const uint64_t this_n = count - done < chunk ? count - done : chunk;
       TransportParams q = p;

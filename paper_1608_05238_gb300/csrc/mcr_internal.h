@@ -106,7 +106,9 @@ struct TransportLaunch {
 // deposit kernel sums each pixel's run in registers before one reduction per run.  The integer
 // tally is bit-identical to the direct deposit.
 constexpr double kRecordTallyBytes = 256.0 * 1024 * 1024;
-constexpr unsigned long long kRecordCapacity = 1ull << 27;  // records per chunk (2 GB per buffer)
+// Records per chunk (16 GB per buffer, two buffers): a chunk must hold several times the packets
+// in flight (~1.2e5 lanes), or the transport spends it waiting for the last, longest packets.
+constexpr unsigned long long kRecordCapacity = 1ull << 30;
 constexpr unsigned kRecBlock = 1024;            // record slots a warp reserves at a time
 constexpr unsigned kRecSentinel = 0xFFFFFFFFu;  // pixel field of an unused slot
 struct RecordHeader {
