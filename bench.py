@@ -69,7 +69,7 @@ def _args():
     ap.add_argument("--iters", type=int, default=None, help="invert_rect: iteration cap (default 20 mua, 40 mus)")
     ap.add_argument("--workload", default="grad256",
                     choices=["grad256", "large1024", "batch64", "denoise256", "conv", "invert256", "unet256", "invert_rect",
-                             "sectors", "grad3d", "equal_error"],
+                             "sectors", "grad3d", "equal_error", "invert1024"],
                     help="grad256: the gradient evaluation (default); large1024: the same on 1024^2 px at "
                          "K = 64 with four edge sources; batch64: 64 forward problems in one graph-captured "
                          "batched launch; denoise256: the learned denoiser; conv: one large tensor-core "
@@ -78,7 +78,8 @@ def _args():
                          "the Sec. 6 reconstructions on the rectangular-inclusion domain (--unknown mua|mus); sectors: "
                          "harmonic vs discrete-ordinates tally (Sec. 3.1); grad3d: the 3D gradient evaluation with "
                          "spherical-harmonic tallies (--n3 voxels a side, --l3 order); equal_error: the chosen form "
-                         "(denoised low-count maps) against plain MC at equal reconstruction error (--unknown mua|mus)")
+                         "(denoised low-count maps) against plain MC at equal reconstruction error (--unknown mua|mus); "
+                         "invert1024: the 1024^2, K = 64 mu_a reconstruction, L-BFGS and gradient descent (--iters)")
     ap.add_argument("--pairs", type=int, default=1024, help="equal_error: training pairs per network")
     ap.add_argument("--train-steps", type=int, default=3000, help="equal_error: Adam steps per network")
     ap.add_argument("--nets", default=None,
@@ -88,13 +89,13 @@ def _args():
     ap.add_argument("--l3", type=int, default=4, help="grad3d: spherical-harmonic order L")
     args = ap.parse_args()
     if args.packets is None:
-        args.packets = 20_000_000 if args.workload == "large1024" else 10_000_000
+        args.packets = 20_000_000 if args.workload in ("large1024", "invert1024") else 10_000_000
     if args.unknown is None:
         args.unknown = "both" if args.workload == "equal_error" else "mua"
     if args.unknown == "both" and args.workload != "equal_error":
         ap.error("--unknown both applies to --workload equal_error only")
     if args.iters is None:
-        args.iters = 40 if args.unknown == "mus" else 20
+        args.iters = 4 if args.workload == "invert1024" else 40 if args.unknown == "mus" else 20
     return args
 
 
@@ -930,6 +931,62 @@ def _equal_error(args):
     return 0
 
 
+def _invert1024(args):
+    """The 1024^2 configuration's reconstruction: mu_a of the large1024 phantom (1024^2 px of 0.02
+    mm, 8 inclusions, g 0.9, four edge line sources, K = 64, mu_s known), H^meas from 1e8 packets of
+    the true medium, started from the homogeneous background, by L-BFGS (the plan's optimiser) and
+    by gradient descent with the Hager-Zhang line search (the paper's, Sec. 6.1), each --iters
+    iterations with --packets per MC run (split over the four sources for the forward runs).  Both
+    use the gradient of the autograd Function (forward harmonics recomputed at K = 64) and the
+    line searches' FP64 inner products on the GPU (mc_dot); the tallies take the sorted-record
+    deposit (1.2 GB each).  Reports the mean relative mu_a error and eps per iteration and the time
+    per iteration of each method."""
+    import torch
+    from paper_1608_05238_gb300 import _build, mcr, workloads
+    from paper_1608_05238_gb300.autograd import MCSpec, forward_coefficients
+    from paper_1608_05238_gb300.inversion import invert, mean_relative_error
+    _build.build()
+    w = workloads.large1024(args.packets)
+    dx, g = float(np.float32(w.dx)), float(np.float32(w.g))
+    dev = torch.device("cuda")
+    mua_t, mus_t = torch.from_numpy(w.mua_true).to(dev), torch.from_numpy(w.mus_true).to(dev)
+    srcs = [mcr.Source(**s) for s in w.sources]
+    med_t = mcr.Medium(mua_t, mus_t, dx, g)
+    Hmeas = mcr.h_eps(med_t, forward_coefficients(med_t, MCSpec(dx=dx, g=g, sources=srcs, K=0,
+                                                                 n_packets=25_000_000, seed=1001)))
+    spec = MCSpec(dx=dx, g=g, sources=srcs, K=w.K, n_packets=args.packets // len(srcs), n_adjoint=args.packets)
+    mua0 = torch.from_numpy(w.mua).to(dev)  # the homogeneous background
+    e0 = mean_relative_error(mua0, mua_t)
+    results = {}
+    for method in ("lbfgs", "gd"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = invert(mua0, mus_t, Hmeas, spec, unknowns=("mua",), iters=args.iters, tol=1e-12,
+                     line_search="hager_zhang", method=method, mua_true=mua_t, seed0=17)
+        torch.cuda.synchronize()
+        T = time.perf_counter() - t0
+        hist = [{"it": h.it, "eps": h.eps, "rel_err_mua": h.rel_err_mua, "seconds": h.seconds, "trials": h.trials}
+                for h in res.history]
+        evals = len(res.history) + sum(h.trials for h in res.history)
+        results[method] = {"seconds": T, "iterations": len(res.history), "gradient_evaluations": evals,
+                           "seconds_per_iteration": T / max(1, len(res.history)),
+                           "final_rel_err_mua": res.history[-1].rel_err_mua if res.history else e0,
+                           "history": hist}
+    head = results["lbfgs"]
+    out = {"metric": "1024^2 K=64 mu_a reconstruction: seconds per iteration (L-BFGS)", "value":
+           head["seconds_per_iteration"], "unit": "s/iteration", "n_gpus": 1, "steps": head["iterations"],
+           "warmup": 0, "ms_per_step": 1e3 * head["seconds_per_iteration"], "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64 (FP64 gradient and inner products)",
+           "data": "synthetic",
+           "config": {"workload": f"invert1024: large1024 phantom (1024x1024 px of {w.dx} mm, 8 inclusions, g "
+                                  f"{w.g}), mu_s known, homogeneous mu_a start, K={w.K}, {args.packets:.0e} "
+                                  f"packets per forward (4 edge sources) and per adjoint run, H^meas from 1e8",
+                      "initial_rel_err_mua": e0, "results": results},
+           "cpu_baseline": None}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def _sectors(args):
     """Sec. 3.1's trade-off, measured: the forward transport of the 256^2 workload with the harmonic
     tally at K = 8, 16, 32 against the discrete-ordinates tally at M = 16, 32, 64 sectors -- tally
@@ -1201,6 +1258,8 @@ def main():
         return _invert_rect(args)
     if args.workload == "equal_error" and args.impl != "reference":
         return _equal_error(args)
+    if args.workload == "invert1024" and args.impl != "reference":
+        return _invert1024(args)
     if args.workload == "sectors" and args.impl != "reference":
         return _sectors(args)
     if args.workload == "grad3d" and args.impl != "reference":
