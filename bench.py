@@ -46,6 +46,12 @@ L2_RED_PEAK_GBS = L2_RED_SECTORS_PER_CYCLE * L2_CLOCK_HZ * 32 / 1e9
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark's forward
 # (40.91 MB) and adjoint (41.56 MB) launches at full size: the tally footprint, read once.
 TRANSPORT_DRAM_BYTES = {"grad256": 41_236_096}
+# DRAM bytes per pixel segment of the sorted-record deposit (transport in record mode, counting
+# sort, deposit), from one ncu capture at 1024^2, K = 64 (1e6 packets, 1.327e9 segments: 126.3 GB;
+# profiles/k_transport_large1024_records_dram.md), scaled to a launch by its segments.  Its
+# algorithmic DRAM bytes: a 16-byte record written, read and rewritten by the sort, read by the deposit.
+RECORD_DRAM_BYTES_PER_SEGMENT = 95.2
+RECORD_ALG_BYTES_PER_SEGMENT = 64
 
 
 def _args():
@@ -433,19 +439,32 @@ def _gpu(args):
     # the tally reductions go to L2 (the grad256 tally is L2-resident): the bound is the L2's
     # reduction-sector rate; the HBM ratio is kept as a secondary figure
     row_words = (C + 15) // 16 * 16 if C > 32 else (C + 3) // 4 * 4
-    in_hbm = w.nx * w.nz * row_words * 8 > 256 << 20  # tallies beyond L2 take their reductions to HBM
-    bound, peak = ("hbm", hbm) if in_hbm else ("l2_reduction", L2_RED_PEAK_GBS)
+    # tallies beyond 256 MB take the sorted-record deposit: its roofline is HBM for the records
+    in_hbm = w.nx * w.nz * row_words * 8 > 256 << 20
+    if in_hbm:
+        bound, peak = "hbm", hbm
+        achieved_gbs = RECORD_ALG_BYTES_PER_SEGMENT * avg_segs / (avg_ms * 1e-3) / 1e9
+    else:
+        bound, peak = "l2_reduction", L2_RED_PEAK_GBS
     roofline = {"bound": bound, "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
-                "frac": achieved_gbs / peak, "traffic": TRANSPORT_DRAM_BYTES.get(w.name),
+                "frac": achieved_gbs / peak,
+                "traffic": (RECORD_DRAM_BYTES_PER_SEGMENT * avg_segs if in_hbm else TRANSPORT_DRAM_BYTES.get(w.name)),
                 "kernel": "k_transport", "launch_ms": avg_ms, "launches_timed": launches,
-                "segments_per_launch": avg_segs, "bytes_per_segment": C * 8,
+                "segments_per_launch": avg_segs,
+                "bytes_per_segment": RECORD_ALG_BYTES_PER_SEGMENT if in_hbm else C * 8,
                 "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured): the tally lives in HBM" if in_hbm else
                                 "ncu lts__t_sectors_op_red.sum.peak_sustained (188 sectors/cycle) x L2 clock "
                                 "2.017 GHz x 32 B (of measured peak rate; profiles/k_transport_grad256_l2_reduction.md)"),
-                "achieved_is": "algorithmic reduction payload 8 (2K+1) B per segment / event-timed launch",
-                "hbm": {"peak": hbm, "frac": achieved_gbs / hbm,
-                        "note": "payload rate over the measured HBM copy rate (MEASURED_PEAKS.json hbm_gbs); the "
-                                "payload goes to L2, DRAM sees `traffic` per launch"}}
+                "achieved_is": ("sorted-record deposit (transport + sort + deposit, event-timed): algorithmic DRAM "
+                                "bytes 64 per segment (a 16-byte record written, read and rewritten by the sort, read "
+                                "by the deposit); traffic = the measured 95.2 B per segment x segments.  The pipeline "
+                                "is bound by its deposit kernel's instruction issue, far below HBM"
+                                if in_hbm else
+                                "algorithmic reduction payload 8 (2K+1) B per segment / event-timed launch")}
+    if not in_hbm:
+        roofline["hbm"] = {"peak": hbm, "frac": achieved_gbs / hbm,
+                           "note": "payload rate over the measured HBM copy rate (MEASURED_PEAKS.json hbm_gbs); the "
+                                   "payload goes to L2, DRAM sees `traffic` per launch"}
     if not args.no_red_probe:
         red = l2_reduction_peak(w.nx * w.nz, C)
         roofline["reduction_probe"] = dict(red, frac=achieved_gbs / red["value"],
