@@ -39,6 +39,17 @@ int mc_reduction_probe(void *tally, int64_t rows, int32_t row_words, int32_t C, 
  */
 int mc_philox_blocks(const uint32_t *ctr, const uint32_t *key, int32_t n, uint32_t *out);
 
+/*
+ * dn_wait_probe -- test hook (the paper has no counterpart): the denoiser kernels' bounded
+ * mbarrier wait made to run out.  One warp waits, with the same wait function the tensor-core
+ * kernels use but limited to `spins` polls (1 <= spins <= 2^24, else MCR_ERR_ARG), on an mbarrier
+ * that nothing arrives at; when the wait gives up it latches the kernels' wait-failure bit in the
+ * denoiser's device error word -- the status dn_check returns (MCR_ERR_CUDA, then cleared) -- and
+ * *timed_out (host) is 1.  Nothing is left in flight, so the context stays usable.  Synchronises
+ * `stream`.
+ */
+int dn_wait_probe(uint32_t spins, int32_t *timed_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

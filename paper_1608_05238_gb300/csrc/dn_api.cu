@@ -498,6 +498,24 @@ int dn_unpack_output(const float *src, const float *scale, int32_t B, int64_t HW
   DN_TRY(unpack_output(src, scale, B, HW, C, dst, (cudaStream_t)stream));
 }
 
+int dn_wait_probe(uint32_t spins, int32_t *timed_out, void *stream) {
+  if (!timed_out || spins == 0 || spins > (1u << 24)) return MCR_ERR_ARG;
+  unsigned *err = error_word();
+  if (!err) return MCR_ERR_CUDA;
+  int *d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return MCR_ERR_NOMEM;
+  }
+  int rc = MCR_OK;
+  if (launch_wait_probe(err, spins, d, (cudaStream_t)stream) != cudaSuccess ||
+      cudaMemcpyAsync(timed_out, d, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess ||
+      cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+    rc = MCR_ERR_CUDA;
+  cudaFree(d);
+  return rc;
+}
+
 int dn_check(void *stream) {
   unsigned *err = error_word();
   if (!err) return MCR_ERR_CUDA;

@@ -1109,4 +1109,24 @@ cudaError_t launch_wgrad_halo(const CUtensorMap &tmZ, const CUtensorMap &tmH, co
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- bounded-wait test hook
+namespace {
+__global__ void k_wait_probe(unsigned *err, uint32_t spins, int *timed_out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);  // one arrival expected; none will come
+  fence_barrier_init();
+  __syncwarp();
+  const bool done = mbar_wait(&bar, 0, spins);
+  if (threadIdx.x == 0) {
+    if (!done) atomicOr(err, 64u);
+    *timed_out = done ? 0 : 1;
+  }
+}
+}  // namespace
+
+cudaError_t launch_wait_probe(unsigned *err, uint32_t spins, int *timed_out, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(err, spins, timed_out);
+  return cudaGetLastError();
+}
+
 }  // namespace dn

@@ -69,6 +69,11 @@ cudaError_t launch_wgrad_mn(const CUtensorMap &tmA, const CUtensorMap &tmB, cons
 bool wgrad_halo_applies(int taps, int cout, int W);
 cudaError_t launch_wgrad_halo(const CUtensorMap &tmZ, const CUtensorMap &tmH, const WgradArgs &a, cudaStream_t s);
 
+// Test hook (dn_conv.cu): one warp waits, with the kernels' own bounded mbarrier wait limited to
+// `spins` polls, on an mbarrier that nothing arrives at; on the timeout it latches the kernels'
+// wait-failure bit (64) in err and writes 1 to *timed_out (else 0).  Nothing is in flight.
+cudaError_t launch_wait_probe(unsigned *err, uint32_t spins, int *timed_out, cudaStream_t s);
+
 // memory-bound kernels (dn_ops.cu)
 cudaError_t to_ct(const __nv_bfloat16 *src, int B, int HW, int W, int stride, int off, int C, int shifted,
                   __nv_bfloat16 *dst, cudaStream_t s);

@@ -306,6 +306,19 @@ def conv_head(x: torch.Tensor, w: torch.Tensor, cout: int, bias, res: torch.Tens
         raise mcr.McrError(rc, "dn_conv_head")
 
 
+def wait_probe(spins: int, stream=None) -> bool:
+    """``dn_wait_probe``: the tensor-core kernels' bounded mbarrier wait, limited to ``spins`` polls, on
+    a barrier nothing arrives at; True when it gave up (and latched the error dn_check reports)."""
+    out = C.c_int32(-1)
+    L = lib()
+    L.dn_wait_probe.argtypes = [C.c_uint32, C.POINTER(C.c_int32), C.c_void_p]
+    L.dn_wait_probe.restype = C.c_int
+    rc = L.dn_wait_probe(int(spins), C.byref(out), _stream(stream))
+    if rc != 0:
+        raise mcr.McrError(rc, "dn_wait_probe")
+    return out.value == 1
+
+
 def check(stream=None):
     rc = lib().dn_check(_stream(stream))
     if rc != 0:

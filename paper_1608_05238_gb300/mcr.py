@@ -31,7 +31,7 @@ EXPORTS = ("mc_forward", "mc_forward_noalloc", "mc_adjoint", "mc_forward_raw", "
            "mc_adjoint_source", "mc_gradient", "mc_gradient_f32", "mc_check", "mc_last_run_info",
            "mc_release_workspace", "mc_status_string", "mc_version")
 # measurement and test entry points (include/mcr_diag.h), not part of the method's interface
-DIAG_EXPORTS = ("mc_reduction_probe", "mc_philox_blocks")
+DIAG_EXPORTS = ("mc_reduction_probe", "mc_philox_blocks", "dn_wait_probe")
 MAX_BATCH = 64
 ERR_SCRATCH = -7
 

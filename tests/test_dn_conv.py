@@ -4,7 +4,7 @@ import pytest
 import torch
 import torch.nn.functional as Fnn
 
-from paper_1608_05238_gb300 import _build, denoise_ops as ops
+from paper_1608_05238_gb300 import _build, denoise_ops as ops, mcr
 
 pytestmark = pytest.mark.gpu
 
@@ -154,3 +154,21 @@ def test_conv_rejects_bad_shapes():
         ops.conv(x[:, :, :16].contiguous(), w, 16, out[:, :, :16].contiguous())  # W < 32
     with pytest.raises(Exception):
         ops.conv(x, w, 16, torch.zeros(1, 4, 32, 12, device="cuda"))  # out stride not a multiple of 8
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable():
+    """A tensor-core kernel's mbarrier wait gives up after its poll limit instead of hanging: the
+    same wait, limited to 2000 polls on a barrier nothing arrives at, reports the timeout, latches
+    the error that dn_check returns (once: it is cleared), and a convolution afterwards still
+    computes what it should."""
+    ops.check()  # a clean latch to start from
+    assert ops.wait_probe(2000) is True
+    with pytest.raises(mcr.McrError):
+        ops.check()
+    ops.check()
+    x, w, cin_pad, n_pad = _case(1, 8, 64, 64, 32, 9, seed=5)
+    out = torch.full((1, 8, 64, 32), float("nan"), device="cuda")
+    ops.conv(x, w, 32, out, taps=9)
+    ops.check()
+    ref = _ref(x, w, 64, 32, 9)
+    assert torch.allclose(out.double().cpu(), ref, rtol=1e-4, atol=1e-4 * ref.abs().max().item())
