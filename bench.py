@@ -91,6 +91,10 @@ def _args():
     ap.add_argument("--nets", default=None,
                     help="equal_error: file of trained U-Net weights: loaded if it exists (no pairs made, no "
                          "training), else written after training")
+    ap.add_argument("--methods", default="lbfgs_pre,lbfgs,gd",
+                    help="invert1024: comma list of lbfgs_pre, gd_pre (fluence-preconditioned), lbfgs, gd")
+    ap.add_argument("--meas-packets", type=int, default=None,
+                    help="invert1024: packets of the H^meas run (default 4x --packets, at least 1e8)")
     ap.add_argument("--n3", type=int, default=96, help="grad3d: voxels per side")
     ap.add_argument("--l3", type=int, default=4, help="grad3d: spherical-harmonic order L")
     args = ap.parse_args()
@@ -952,36 +956,48 @@ def _equal_error(args):
 
 def _invert1024(args):
     """The 1024^2 configuration's reconstruction: mu_a of the large1024 phantom (1024^2 px of 0.02
-    mm, 8 inclusions, g 0.9, four edge line sources, K = 64, mu_s known), H^meas from 1e8 packets of
-    the true medium, started from the homogeneous background, by L-BFGS (the plan's optimiser) and
-    by gradient descent with the Hager-Zhang line search (the paper's, Sec. 6.1), each --iters
-    iterations with --packets per MC run (split over the four sources for the forward runs).  Both
-    use the gradient of the autograd Function (forward harmonics recomputed at K = 64) and the
-    line searches' FP64 inner products on the GPU (mc_dot); the tallies take the sorted-record
-    deposit (1.2 GB each).  Reports the mean relative mu_a error and eps per iteration and the time
-    per iteration of each method."""
+    mm, 8 inclusions, g 0.9, four edge line sources, K = 64, mu_s known), H^meas from --meas-packets
+    packets of the true medium, started from the homogeneous background, by each of --methods for
+    --iters iterations with --packets per MC run (split over the four sources for the forward runs):
+    L-BFGS (the plan's optimiser) and gradient descent with the Hager-Zhang line search (the
+    paper's, Sec. 6.1), each plain or with the fluence preconditioner (``_pre``: the diagonal
+    1 / (dx^2 Phi^2) as L-BFGS's initial inverse Hessian, or as the descent's step scaling).  All use
+    the gradient of the autograd Function (forward harmonics recomputed at K = 64) and the line
+    searches' FP64 inner products on the GPU (mc_dot); the tallies take the sorted-record deposit
+    (1.2 GB each).  Reports the mean relative mu_a error and eps per iteration and the time per
+    iteration of each method; the headline is the first method's seconds per iteration."""
     import torch
     from paper_1608_05238_gb300 import _build, mcr, workloads
     from paper_1608_05238_gb300.autograd import MCSpec, forward_coefficients
     from paper_1608_05238_gb300.inversion import invert, mean_relative_error
     _build.build()
+    methods = [m.strip() for m in args.methods.split(",") if m.strip()]
+    for m in methods:
+        if m not in ("lbfgs_pre", "gd_pre", "lbfgs", "gd"):
+            raise SystemExit(f"unknown method {m!r}")
     w = workloads.large1024(args.packets)
     dx, g = float(np.float32(w.dx)), float(np.float32(w.g))
     dev = torch.device("cuda")
     mua_t, mus_t = torch.from_numpy(w.mua_true).to(dev), torch.from_numpy(w.mus_true).to(dev)
     srcs = [mcr.Source(**s) for s in w.sources]
     med_t = mcr.Medium(mua_t, mus_t, dx, g)
+    n_meas = args.meas_packets or max(100_000_000, 4 * args.packets)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     Hmeas = mcr.h_eps(med_t, forward_coefficients(med_t, MCSpec(dx=dx, g=g, sources=srcs, K=0,
-                                                                 n_packets=25_000_000, seed=1001)))
+                                                                 n_packets=n_meas // len(srcs), seed=1001)))
+    torch.cuda.synchronize()
+    t_meas = time.perf_counter() - t0
     spec = MCSpec(dx=dx, g=g, sources=srcs, K=w.K, n_packets=args.packets // len(srcs), n_adjoint=args.packets)
     mua0 = torch.from_numpy(w.mua).to(dev)  # the homogeneous background
     e0 = mean_relative_error(mua0, mua_t)
     results = {}
-    for method in ("lbfgs", "gd"):
+    for method in methods:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = invert(mua0, mus_t, Hmeas, spec, unknowns=("mua",), iters=args.iters, tol=1e-12,
-                     line_search="hager_zhang", method=method, mua_true=mua_t, seed0=17)
+                     line_search="hager_zhang", method=method.replace("_pre", ""),
+                     precondition=method.endswith("_pre"), mua_true=mua_t, seed0=17)
         torch.cuda.synchronize()
         T = time.perf_counter() - t0
         hist = [{"it": h.it, "eps": h.eps, "rel_err_mua": h.rel_err_mua, "seconds": h.seconds, "trials": h.trials}
@@ -991,15 +1007,16 @@ def _invert1024(args):
                            "seconds_per_iteration": T / max(1, len(res.history)),
                            "final_rel_err_mua": res.history[-1].rel_err_mua if res.history else e0,
                            "history": hist}
-    head = results["lbfgs"]
-    out = {"metric": "1024^2 K=64 mu_a reconstruction: seconds per iteration (L-BFGS)", "value":
+    head = results[methods[0]]
+    out = {"metric": f"1024^2 K=64 mu_a reconstruction: seconds per iteration ({methods[0]})", "value":
            head["seconds_per_iteration"], "unit": "s/iteration", "n_gpus": 1, "steps": head["iterations"],
            "warmup": 0, "ms_per_step": 1e3 * head["seconds_per_iteration"], "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64 (FP64 gradient and inner products)",
            "data": "synthetic",
            "config": {"workload": f"invert1024: large1024 phantom (1024x1024 px of {w.dx} mm, 8 inclusions, g "
                                   f"{w.g}), mu_s known, homogeneous mu_a start, K={w.K}, {args.packets:.0e} "
-                                  f"packets per forward (4 edge sources) and per adjoint run, H^meas from 1e8",
+                                  f"packets per forward (4 edge sources) and per adjoint run, H^meas from "
+                                  f"{n_meas:.0e} ({t_meas:.1f} s)",
                       "initial_rel_err_mua": e0, "results": results},
            "cpu_baseline": None}
     print(json.dumps(out), flush=True)

@@ -33,7 +33,10 @@ sufficiently (Eq. 30) and a stop once the relative decrease of eps falls below a
   Hager-Zhang line search starting at the unit step.  Both gradients of a pair come from the same
   packets (the iteration's seeds: g_old at the start, g_new at the accepted trial), so y holds the
   change of the gradient and not the difference of two MC noises; pairs with s.y <= 0 are skipped,
-  and a direction that is not a descent direction restarts from -g.
+  and a direction that is not a descent direction restarts from -g.  With ``precondition`` the
+  mu_a part of H_0 is the diagonal 1 / (dx^2 Phi^2) above instead of gamma I (recomputed from
+  each iteration's fluence), and the line search starts at the unit step from the first
+  iteration on.
 
 Every inner product (g.d, the line-search slopes, the recursion's s.q and y.r) is ``mc_dot``: FP64
 on the GPU in a fixed order.  The step update itself (mu - alpha g, clamp) and the recursion's
@@ -82,11 +85,12 @@ def _dot(us, vs) -> float:
                if u is not None and v is not None)
 
 
-def lbfgs_direction(g: list, pairs: list, dot=_dot) -> list:
+def lbfgs_direction(g: list, pairs: list, dot=_dot, h0: list | None = None) -> list:
     """-H g by the L-BFGS two-loop recursion (Nocedal & Wright, Algorithm 7.4): ``g`` a list of
     tensors (None entries skipped), ``pairs`` the stored (s, y, 1 / s.y) oldest first, H_0 = gamma I
-    with gamma = s.y / y.y of the newest pair (gamma = 1 without pairs).  ``dot`` computes sums of
-    inner products over the lists."""
+    with gamma = s.y / y.y of the newest pair (gamma = 1 without pairs), except for the entries
+    where ``h0`` gives a tensor: H_0 is that diagonal there.  ``dot`` computes sums of inner
+    products over the lists."""
     q = [None if t is None else t.clone() for t in g]
     alphas = []
     for s_, y_, rho in reversed(pairs):
@@ -97,7 +101,8 @@ def lbfgs_direction(g: list, pairs: list, dot=_dot) -> list:
     if pairs:
         s_, y_, _ = pairs[-1]
         gamma = dot(s_, y_) / dot(y_, y_)
-    r = [None if qi is None else gamma * qi for qi in q]
+    h0 = h0 if h0 is not None else [None] * len(q)
+    r = [None if qi is None else (gamma * qi if h is None else h * qi) for qi, h in zip(q, h0)]
     for (s_, y_, rho), a in zip(pairs, reversed(alphas)):
         b = rho * dot(y_, r)
         r = [None if ri is None else ri + (a - b) * si for ri, si in zip(r, s_)]
@@ -244,7 +249,7 @@ def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MC
 
     ``step0`` defaults to the step that changes the unknowns by 10 % of their norm on the first
     iteration (1, a full fixed-point-like step, with ``precondition``; for the Hager-Zhang search
-    its first trial is 0.01 max|mu| / max|d|).  Returns the estimates and one ``Iteration``
+    its first trial is 0.01 max|mu| / max|d|, or 1 with ``precondition``).  Returns the estimates and one ``Iteration``
     record per accepted step (``trials`` = MC evaluations of the line search; ``extra`` =
     ``monitor(mua, mus)`` after the step, when a monitor is given).
     """
@@ -254,7 +259,6 @@ def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MC
         raise ValueError(f"method must be 'gd' or 'lbfgs', not {method!r}")
     if method == "lbfgs":
         line_search = "hager_zhang"  # its trials yield the gradients the pairs need
-        precondition = False
     pairs = []
     want_a, want_s = "mua" in unknowns, "mus" in unknowns
     mua, mus = mua0.detach().clone(), mus0.detach().clone()
@@ -266,18 +270,20 @@ def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MC
     for it in range(iters):
         s_it = replace(spec, seed=seed0 + 1009 * it, adjoint_seed=seed0 + 1009 * it + 1)
         eps, ga, gs, H = _eps_and_grad(mua, mus, Hmeas, s_it, want_a, want_s)
-        da = None
+        da, pa = None, None
         if want_a:
             da = -ga
             if precondition:  # 1 / (dx^2 Phi^2), Phi = H / mu_a = a_0
                 phi = H / mua
-                da = da / (float(spec.dx) ** 2 * phi * phi).clamp_min(1e-30)
+                pa = 1.0 / (float(spec.dx) ** 2 * phi * phi).clamp_min(1e-30)
+                da = da * pa
         ds = -gs if want_s else None
         if method == "lbfgs" and pairs:
-            da, ds = lbfgs_direction([ga, gs], pairs)
-            if -_dot([ga, gs], [da, ds]) <= 0.0:  # not a descent direction: restart from -g
+            steepest = (da, ds)
+            da, ds = lbfgs_direction([ga, gs], pairs, h0=[pa, None])
+            if -_dot([ga, gs], [da, ds]) <= 0.0:  # not a descent direction: restart from -g (or -P g)
                 pairs.clear()
-                da, ds = (-ga if want_a else None), (-gs if want_s else None)
+                da, ds = steepest
         slope = -_dot([ga, gs], [da, ds])
         if slope <= 0.0:
             res.converged = True
@@ -289,8 +295,10 @@ def invert(mua0: torch.Tensor, mus0: torch.Tensor, Hmeas: torch.Tensor, spec: MC
             return na, ns
 
         if line_search == "hager_zhang":
-            if method == "lbfgs" and pairs:
-                c = 1.0  # the quasi-Newton step
+            if method == "lbfgs" and (pairs or precondition):
+                c = 1.0  # the quasi-Newton step (the preconditioned full step before any pair)
+            elif alpha is None and precondition:
+                c = 1.0  # the preconditioned full step
             elif alpha is None or method == "lbfgs":
                 amax = max(float(m.abs().max()) for m, w in ((mua, want_a), (mus, want_s)) if w)
                 dmax = max(float(d.abs().max()) for d in (da, ds) if d is not None)

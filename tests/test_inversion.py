@@ -133,3 +133,28 @@ def test_lbfgs_mua_reconstruction_of_the_rectangular_inclusion():
     assert res.history[-1].eps < 1e-2 * res.history[0].eps, [h.eps for h in res.history]
     assert errs[-1] < 0.5 * e0, (e0, errs)
     assert torch.equal(res.mus, mus_t) and torch.all(res.mua > 0)
+
+
+def test_preconditioned_lbfgs_mua_reconstruction():
+    """L-BFGS with the fluence preconditioner as its initial inverse Hessian (the unit step from the
+    first iteration) on the 64^2 two-inclusion phantom: like the preconditioned descent it brings
+    the error well below its start within a few iterations; mu_s is untouched."""
+    n, dx = 64, 0.1
+    mua_t, mus_t = workloads.inclusion_phantom(n, dx, 2, seed=7, margin=1.5, radius=(0.6, 1.2),
+                                               mus_range=(10.0, 10.0))
+    src = mcr.Source(**workloads.top_line_source(n, dx))
+    g = f32(0.9)
+    dev = torch.device("cuda")
+    mua_true, mus = torch.from_numpy(mua_t).to(dev), torch.from_numpy(mus_t).to(dev)
+    med = mcr.Medium(mua_true, mus, f32(dx), g)
+    Hmeas = mcr.h_eps(med, forward_coefficients(med, MCSpec(dx=f32(dx), g=g, sources=[src], K=0,
+                                                           n_packets=8_000_000, seed=99)))
+    spec = MCSpec(dx=f32(dx), g=g, sources=[src], K=8, n_packets=2_000_000)
+    mua0 = torch.full_like(mua_true, 0.02)
+    res = invert(mua0, mus, Hmeas, spec, unknowns=("mua",), iters=6, tol=1e-12, mua_true=mua_true,
+                 precondition=True, method="lbfgs")
+    e0 = mean_relative_error(mua0, mua_true)
+    errs = [h.rel_err_mua for h in res.history]
+    assert len(res.history) >= 2, res.history
+    assert errs[-1] < 0.15 * e0, (e0, errs)
+    assert torch.equal(res.mus, mus) and torch.all(res.mua > 0)

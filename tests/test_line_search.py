@@ -111,3 +111,30 @@ def test_lbfgs_with_exact_line_search_minimises_a_quadratic():
         pairs.append(([s_], [y_], 1.0 / float(s_ @ y_)))
         x = x_new
     assert torch.allclose(x, torch.linalg.solve(A, b), rtol=1e-8, atol=1e-10)
+
+
+def test_lbfgs_with_a_diagonal_initial_inverse_hessian():
+    """A diagonal H_0 (the fluence preconditioner's role): without pairs the direction is -H_0 g,
+    which on a diagonal quadratic with H_0 its inverse Hessian is the Newton step to the minimiser;
+    with pairs the secant condition still holds for the newest pair, and a tensor entry without a
+    diagonal (None in h0) keeps the gamma I scaling."""
+    g = torch.Generator().manual_seed(5)
+    diag = torch.rand(7, generator=g, dtype=torch.float64) * 100 + 0.01
+    b = torch.randn(7, generator=g, dtype=torch.float64)
+    x = torch.zeros(7, dtype=torch.float64)
+    gx = diag * x - b
+    d = lbfgs_direction([gx], [], dot=_cpu_dot, h0=[1.0 / diag])[0]
+    assert torch.allclose(x + d, b / diag, rtol=1e-12, atol=0)
+    A, _ = _quadratic(6, 4)
+    h = torch.rand(6, generator=g, dtype=torch.float64) + 0.5
+    pairs = []
+    for _ in range(3):
+        s_ = torch.randn(6, generator=g, dtype=torch.float64)
+        pairs.append(([s_, s_[:2].clone()], [A @ s_, 3.0 * s_[:2]], 1.0 / (float(s_ @ (A @ s_)) + 3.0 * float(s_[:2] @ s_[:2]))))
+    s_new, y_new = pairs[-1][0], pairs[-1][1]
+    d = lbfgs_direction(y_new, pairs, dot=_cpu_dot, h0=[h, None])
+    assert torch.allclose(-d[0], s_new[0], rtol=1e-10, atol=1e-12)
+    assert torch.allclose(-d[1], s_new[1], rtol=1e-10, atol=1e-12)
+    # without pairs, the None entry is scaled by gamma = 1
+    d0 = lbfgs_direction([gx, b[:2]], [], dot=_cpu_dot, h0=[1.0 / diag, None])
+    assert torch.equal(d0[1], -b[:2])
