@@ -72,7 +72,7 @@ def _args():
     ap.add_argument("--conv", default="128,128", help="conv: input,output channels of the timed 3x3 layer")
     ap.add_argument("--unknown", default=None, choices=["mua", "mus", "both"],
                     help="invert_rect: the reconstructed map (default mua); equal_error: mua, mus or both (default)")
-    ap.add_argument("--iters", type=int, default=None, help="invert_rect: iteration cap (default 20 mua, 40 mus)")
+    ap.add_argument("--iters", type=int, default=None, help="invert_rect, invert1024: iteration cap (default 20; 40 for mus)")
     ap.add_argument("--workload", default="grad256",
                     choices=["grad256", "large1024", "batch64", "denoise256", "conv", "invert256", "unet256", "invert_rect",
                              "sectors", "grad3d", "equal_error", "invert1024"],
@@ -91,7 +91,7 @@ def _args():
     ap.add_argument("--nets", default=None,
                     help="equal_error: file of trained U-Net weights: loaded if it exists (no pairs made, no "
                          "training), else written after training")
-    ap.add_argument("--methods", default="lbfgs_pre,lbfgs,gd",
+    ap.add_argument("--methods", default="lbfgs_pre,gd_pre",
                     help="invert1024: comma list of lbfgs_pre, gd_pre (fluence-preconditioned), lbfgs, gd")
     ap.add_argument("--meas-packets", type=int, default=None,
                     help="invert1024: packets of the H^meas run (default 4x --packets, at least 1e8)")
@@ -105,7 +105,7 @@ def _args():
     if args.unknown == "both" and args.workload != "equal_error":
         ap.error("--unknown both applies to --workload equal_error only")
     if args.iters is None:
-        args.iters = 4 if args.workload == "invert1024" else 40 if args.unknown == "mus" else 20
+        args.iters = 40 if args.unknown == "mus" else 20
     return args
 
 
