@@ -912,6 +912,8 @@ def _equal_error(args):
         plain = [route(int(m)) for m in (1e5, 2e5, 4e5, 1e6, 2e6, 4e6)]
         dn = Denoiser(nets["forward"][0], nets["adjoint"][0], n_full=n_high, n_judge=10 * n_low, judge_every=0,
                       max_rel_err=0.6)
+        for kind in ("forward", "adjoint"):  # warm-up of the U-Net kernels, as route(20_000) is for the MC's
+            dn.denoise(kind, torch.rand((2 * K + 1, n, n), device=dev))
         chosen = route(n_low, dn)
         chosen["judge"] = dn.history
         chosen["fallback"] = dn.fallback

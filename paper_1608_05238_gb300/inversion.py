@@ -119,6 +119,12 @@ def _eps_and_grad(mua, mus, Hmeas, spec, want_a, want_s):
 
 
 def _eps(mua, mus, Hmeas, spec):
+    """eps alone (the backtracking trials).  H needs only the a_0 map, and a_0's tally (each
+    segment's track weight, rounded to the fixed-point quantum, which does not depend on K) and the
+    packets' random numbers are the same at every K, so a K = 0 run gives the same eps bit for bit,
+    at a fraction of the cost -- except through a denoiser, which maps all channels jointly."""
+    if spec.denoiser is None:
+        spec = replace(spec, K=0)
     with torch.no_grad():
         return float(EpsFromH.apply(HFromMu.apply(mua, mus, spec), Hmeas, spec.dx))
 

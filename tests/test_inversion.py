@@ -1,6 +1,8 @@
 """The reconstruction driver (Sec. 6) on the GPU: mu_a-only gradient descent with backtracking on a
 small inclusion phantom, started from a uniform guess twice the background, lowers eps at every
 accepted step and the mean relative error of mu_a over the domain."""
+from dataclasses import replace
+
 import numpy as np
 import pytest
 import torch
@@ -158,3 +160,17 @@ def test_preconditioned_lbfgs_mua_reconstruction():
     assert len(res.history) >= 2, res.history
     assert errs[-1] < 0.15 * e0, (e0, errs)
     assert torch.equal(res.mus, mus) and torch.all(res.mua > 0)
+
+
+def test_eps_trials_at_k0_equal_the_full_order_eps():
+    """The backtracking trials evaluate eps with K = 0 runs: a_0 (and so H and eps) is the same bit
+    for bit as in the run at the spec's K on the same packets."""
+    from paper_1608_05238_gb300.autograd import EpsFromH, HFromMu
+    from paper_1608_05238_gb300.inversion import _eps
+    mua_t, mus_t, Hmeas, spec = _rect_setup(2_000_000, 12, 500_000)
+    mua = torch.full_like(mua_t, 0.012)
+    with torch.no_grad():
+        eps_full = float(EpsFromH.apply(HFromMu.apply(mua, mus_t, spec), Hmeas, spec.dx))
+    assert _eps(mua, mus_t, Hmeas, spec) == eps_full
+    med = mcr.Medium(mua, mus_t, spec.dx, spec.g)
+    assert torch.equal(forward_coefficients(med, replace(spec, K=0))[0], forward_coefficients(med, spec)[0])
