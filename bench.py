@@ -912,8 +912,10 @@ def _equal_error(args):
         plain = [route(int(m)) for m in (1e5, 2e5, 4e5, 1e6, 2e6, 4e6)]
         dn = Denoiser(nets["forward"][0], nets["adjoint"][0], n_full=n_high, n_judge=10 * n_low, judge_every=0,
                       max_rel_err=0.6)
-        for kind in ("forward", "adjoint"):  # warm-up of the U-Net kernels, as route(20_000) is for the MC's
-            dn.denoise(kind, torch.rand((2 * K + 1, n, n), device=dev))
+        # warm-up of everything the chosen route runs first (U-Net kernels, the judge's norms), as
+        # route(20_000) is for the plain route: a throw-away denoiser with a cheap judge and fallback
+        route(20_000, Denoiser(nets["forward"][0], nets["adjoint"][0], n_full=20_000, n_judge=20_000, judge_every=0,
+                               max_rel_err=0.6))
         chosen = route(n_low, dn)
         chosen["judge"] = dn.history
         chosen["fallback"] = dn.fallback
