@@ -128,6 +128,8 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
   const int np = (int)probs.size();
   const int C = common->time_bins ? (int)common->time_bins : common->sectors ? (int)common->sectors : 2 * common->K + 1;
   const int Cpad = tally_row_words(C);
+  // words from a pixel's slot to its row (dense harmonic rows; folded into tally_off)
+  const int roff = (common->time_bins || common->sectors) ? 0 : tally_row_offset(C);
   // a single problem may exceed one launch's packet budget (chunks + FP64 flush); a batch may not
   const bool chunked = np == 1 && probs[0].n_packets > kChunkPackets;
   Need need;
@@ -136,7 +138,7 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
     const int64_t npix = (int64_t)probs[i].med->nx * probs[i].med->nz;
     mu_off[i] = need.mu / sizeof(float4);
     need.mu += ((size_t)npix * sizeof(float4) + 255) & ~size_t(255);
-    tally_off[i] = need.tally / 8;
+    tally_off[i] = need.tally / 8 + roff;
     need.tally += ((size_t)npix * Cpad * 8 + 255) & ~size_t(255);
     if (probs[i].qstar) {
       cdf_off[i] = need.cdf / 8;
@@ -307,7 +309,7 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
         // slots reserved past the capacity (a warp's last block may straddle it) were never written
         const unsigned long long n_slots = hdr.count < rec_cap ? hdr.count : rec_cap;
         MCR_TRY_CUDA(launch_sort_and_deposit(w->records, n_slots, hist, cursor, bsums, (int)npix, w->sorted,
-                                             common->K, Cpad, w->tally, w->flags(), s));
+                                             common->K, Cpad, w->tally + tally_off[0], w->flags(), s));
         MCR_TRY_CUDA(launch_add_stats(p.stats, &w->rec_hdr->stats, s));
       }
       const double r = (double)hdr.count / (double)this_n;
@@ -335,7 +337,7 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
       const uint64_t this_n = h.n_packets - done < kChunkPackets ? h.n_packets - done : kChunkPackets;
       if (done) MCR_TRY_CUDA(cudaMemsetAsync(w->tally, 0, need.tally, s));
       if ((rc = run_range(h.first_packet + done, this_n))) return rc;
-      MCR_TRY_CUDA(launch_accumulate(w->tally, npix, C, Cpad, ldexp(1.0, -qexp[0]), w->acc, s));
+      MCR_TRY_CUDA(launch_accumulate(w->tally + tally_off[0], npix, C, Cpad, ldexp(1.0, -qexp[0]), w->acc, s));
       done += this_n;
     }
   }
@@ -345,7 +347,7 @@ int enqueue(const std::vector<HostProblem> &probs, const mcr_run *common, const 
   }
   if (raw_out) {
     const int64_t npix = (int64_t)probs[0].med->nx * probs[0].med->nz;
-    MCR_TRY_CUDA(launch_export_raw(w->tally, npix, C, Cpad, common->accumulate != 0, raw_out, s));
+    MCR_TRY_CUDA(launch_export_raw(w->tally + tally_off[0], npix, C, Cpad, common->accumulate != 0, raw_out, s));
   }
   for (int i = 0; i < np && !raw_out; ++i) {
     const HostProblem &h = probs[i];

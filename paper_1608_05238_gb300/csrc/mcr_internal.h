@@ -208,6 +208,15 @@ bool angular_density_ok(const mcr_source &src);
 
 inline int tally_row_words(int C) { return C > 32 ? (C + 15) & ~15 : (C + 3) & ~3; }
 
+// Harmonic tallies with 2K+1 = 32 m + 1 > 32 coefficients ("dense" rows): each pixel's row starts
+// 15 words into its tally_row_words(C) = 32 m + 16 word slot, so that coefficients 1..2K fill the
+// slot's last 32 m words, whole 128-byte lines, and go by cooperative reductions of 32 aligned words;
+// coefficient 0 -- the track weight itself -- takes the slot's word 15 and is summed per lane over a
+// packet's consecutive segments in one pixel before its reduction.  The host shifts each problem's
+// tally base by this offset; every kernel then indexes rows as base + pixel * Cpad + c, and the
+// slot's first 15 words stay zero.  0 for every other tally (and for the sector and time tallies).
+__host__ __device__ inline int tally_row_offset(int C) { return (C > 32 && (C & 31) == 1) ? 15 : 0; }
+
 // Words per harmonic row in shared memory: channel c at word 1 + c (so the (cos, sin) pairs are
 // 8-byte aligned), at least C + 1 and = 2 (mod 4), so that the lanes' 8-byte row stores fall in
 // distinct banks.

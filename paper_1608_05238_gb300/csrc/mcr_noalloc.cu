@@ -118,7 +118,7 @@ int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_r
   p.flags = flags;
   ProblemDesc &d = p.prob[0];
   d.mu = mu;
-  d.tally = tally;
+  d.tally = tally + tally_row_offset(C);  // dense harmonic rows start 15 words into their slot
   d.first_packet = run->first_packet;
   d.end = run->n_packets;
   d.nx = med->nx;
@@ -140,7 +140,7 @@ int mc_forward_noalloc(const mcr_medium *med, const mcr_source *src, const mcr_r
   if (run->n_packets && launch_transport(p, TransportLaunch{0, 0, 0, 0}, s) != cudaSuccess) return MCR_ERR_CUDA;
   const double area = (double)med->dx * (double)med->dx;
   const double fixed_scale = run->n_packets ? (double)src->power / ((double)run->n_packets * area) : 0.0;
-  if (launch_finalize(tally, nullptr, npix, C, Cpad, ldexp(1.0, -qexp), fixed_scale, false, nullptr, nullptr,
+  if (launch_finalize(tally + tally_row_offset(C), nullptr, npix, C, Cpad, ldexp(1.0, -qexp), fixed_scale, false, nullptr, nullptr,
                       (double)(run->n_packets ? run->n_packets : 1), false, run->accumulate != 0, coeff, flags,
                       s) != cudaSuccess)
     return MCR_ERR_CUDA;

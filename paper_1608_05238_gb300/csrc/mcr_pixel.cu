@@ -116,7 +116,10 @@ __global__ void k_export_raw(const unsigned long long *__restrict__ tally, int64
   const int npx = npix - p0 < 32 ? (int)(npix - p0) : 32;
   const int tid = threadIdx.y * 32 + threadIdx.x, nthr = blockDim.x * blockDim.y;
   const long long *src = reinterpret_cast<const long long *>(tally) + p0 * Cpad;
-  for (int k = tid; k < npx * Cpad; k += nthr) tile[k] = src[k];
+  // a row's words [C, Cpad) are not read: with a row offset (dense rows) the last pixel's would lie
+  // past the tally
+  for (int k = tid; k < npx * Cpad; k += nthr)
+    if (k % Cpad < C) tile[k] = src[k];
   __syncthreads();
   for (int c = threadIdx.y; c < C; c += blockDim.y) {
     if (threadIdx.x < npx) {
@@ -165,6 +168,7 @@ __global__ void k_finalize(const unsigned long long *__restrict__ tally, const d
   if (!acc) {
     const long long *src = reinterpret_cast<const long long *>(tally) + p0 * Cpad;
     for (int k = tid; k < npx * Cpad; k += nthr) {
+      if (k % Cpad >= C) continue;  // as in k_export_raw: only the row's C words are read
       const long long v = src[k];
       near_overflow |= (v > (1ll << 61)) || (v < -(1ll << 61));
       tile[k] = v;

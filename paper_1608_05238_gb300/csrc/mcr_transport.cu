@@ -137,10 +137,21 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
   };
 
   const int K = p.K, C = p.C;
-  // Coefficients [0, Cw) are deposited warp-cooperatively (32 per instruction); a short remainder
-  // [Cw, C) of at most 4 (the last b_K when 2K+1 = 32 m + 1) is deposited by each lane into its
+  // Coefficients [c0, c0 + Cw) are deposited warp-cooperatively (32 per instruction).  Dense rows
+  // (2K+1 = 32 m + 1, see tally_row_offset) take coefficients 1..2K that way, line-aligned, and
+  // coefficient 0, the track weight itself, per lane: summed in a register over the packet's
+  // consecutive segments in one pixel (collisions split a pixel's path) and reduced when the pixel
+  // changes.  Otherwise a short remainder [Cw, C) of at most 4 is deposited by each lane into its
   // own row, all lanes in one instruction, instead of one nearly empty instruction per row.
-  const int Cw = (C & 31) <= 4 ? (C & ~31) : C;
+  const bool dense = !ROWLESS && tally_row_offset(C) != 0;
+  const int c0 = dense ? 1 : 0;
+  const int Cw = dense ? C - 1 : ((C & 31) <= 4 ? (C & ~31) : C);
+  long long acc0 = 0;     // dense: coefficient 0 of the pending pixel acc0_key
+  unsigned acc0_key = 0u;
+  auto flush0 = [&]() {
+    if (acc0_key != 0u && row_ok(acc0_key)) atomicAdd(tally_row(acc0_key), (unsigned long long)acc0);
+    acc0_key = 0u;
+  };
 
   bool alive = false, exhausted = false;
   unsigned long long pid = 0;
@@ -462,8 +473,8 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
             key = 64u;
           }
           ts[r] = __shfl_sync(kFull, seg_ts, L);
-          dst[r] = tally_row(key);
-          hr[r] = rows + ((MERGE ? __shfl_sync(kFull, rb, L) * 32 : 0) + L) * p.row_stride + 1;
+          dst[r] = tally_row(key) + c0;
+          hr[r] = rows + ((MERGE ? __shfl_sync(kFull, rb, L) * 32 : 0) + L) * p.row_stride + 1 + c0;
         }
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
@@ -479,11 +490,11 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
         const int L = __ffs(pend) - 1;
         const unsigned grp = __shfl_sync(kFull, same, L) & pend;
         const unsigned key = __shfl_sync(kFull, seg_key, L);
-        unsigned long long *dst = tally_row(key);
+        unsigned long long *dst = tally_row(key) + c0;
         long long acc[NP > 0 ? NP : 1];
         // |t h 2^q| < 2^31 by the choice of q, so a 32-bit conversion suffices
         const float tsL = __shfl_sync(kFull, seg_ts, L);
-        const float *hrL = rows + ((MERGE ? __shfl_sync(kFull, rb, L) * 32 : 0) + L) * p.row_stride + 1;
+        const float *hrL = rows + ((MERGE ? __shfl_sync(kFull, rb, L) * 32 : 0) + L) * p.row_stride + 1 + c0;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
           const int j = q * 32 + lane;
@@ -492,7 +503,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
         if (MERGE) {
           const float cL = __shfl_sync(kFull, dep_carry, L);
           if (cL != 0.f) {
-            const float *hc = rows + (__shfl_sync(kFull, carry_rb, L) * 32 + L) * p.row_stride + 1;
+            const float *hc = rows + (__shfl_sync(kFull, carry_rb, L) * 32 + L) * p.row_stride + 1 + c0;
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
               const int j = q * 32 + lane;
@@ -505,7 +516,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
           const int M = __ffs(g) - 1;
           g &= g - 1;
           const float ts = __shfl_sync(kFull, seg_ts, M);
-          const float *hr = rows + ((MERGE ? __shfl_sync(kFull, rb, M) * 32 : 0) + M) * p.row_stride + 1;
+          const float *hr = rows + ((MERGE ? __shfl_sync(kFull, rb, M) * 32 : 0) + M) * p.row_stride + 1 + c0;
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
             const int j = q * 32 + lane;
@@ -514,7 +525,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
           if (MERGE) {
             const float cM = __shfl_sync(kFull, dep_carry, M);
             if (cM != 0.f) {
-              const float *hc = rows + (__shfl_sync(kFull, carry_rb, M) * 32 + M) * p.row_stride + 1;
+              const float *hc = rows + (__shfl_sync(kFull, carry_rb, M) * 32 + M) * p.row_stride + 1 + c0;
 #pragma unroll
               for (int q = 0; q < NP; ++q) {
                 const int j = q * 32 + lane;
@@ -532,7 +543,19 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
         }
         pend &= ~grp;
       }
-      if (!ROWLESS && Cw < C && seg_key != 0u && row_ok(seg_key)) {  // the per-lane remainder
+      if (dense) {  // coefficient 0: h_0 = 1, so each product is the rounded track weight itself
+        if (seg_key != 0u) {
+          long long v = (long long)__float2int_rn(seg_ts);
+          if (MERGE && dep_carry != 0.f) v += (long long)__float2int_rn(dep_carry);
+          if (seg_key != acc0_key) {
+            flush0();
+            acc0_key = seg_key;
+            acc0 = v;
+          } else {
+            acc0 += v;
+          }
+        }
+      } else if (!ROWLESS && Cw < C && seg_key != 0u && row_ok(seg_key)) {  // the per-lane remainder
         unsigned long long *own = tally_row(seg_key);
         const float *h = rows + ((MERGE ? rb * 32 : 0) + lane) * p.row_stride + 1;
         const float *hc = rows + ((MERGE ? carry_rb * 32 : 0) + lane) * p.row_stride + 1;
@@ -600,6 +623,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
   }
 
   if constexpr (RECS) rec_pad();  // the warp's last block
+  if (dense) flush0();            // the lane's last pending coefficient 0
   // ---------------------------------------------------------------- counters
   const unsigned c_launch = __reduce_add_sync(kFull, n_launch), c_flight = __reduce_add_sync(kFull, n_flight),
                  c_coll = __reduce_add_sync(kFull, n_coll), c_seg = __reduce_add_sync(kFull, n_seg),
@@ -627,7 +651,8 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     atomicAdd(&s->rr_net_w, w_rr);
     atomicAdd(&s->killed_w, w_kill);
   }
-  if (STALLY) {  // the block's tally into the global one: coalesced, zero words skipped
+  if (STALLY) {  // the block's tally into the global one: coalesced, zero words skipped (with a row
+                 // offset the last slot's last words map past the tally; they are never written)
     __syncthreads();
     const size_t nw = (size_t)p.prob[0].nx * p.prob[0].nz * p.Cpad;
     unsigned long long *g = p.prob[0].tally;

@@ -150,12 +150,14 @@ def test_batch_limits():
 
 
 @pytest.mark.parametrize("adjoint", [False, True])
-def test_shared_memory_tally_is_bit_identical(adjoint):
-    """A per-block shared-memory copy of a small tally (32x32, K = 8) adds up to the same integer
-    tally as the global one; a tally too large for shared memory falls back to the global one."""
-    K = 8
+@pytest.mark.parametrize("K,n_small", [(8, 32), (16, 16)])
+def test_shared_memory_tally_is_bit_identical(adjoint, K, n_small):
+    """A per-block shared-memory copy of a small tally (32x32 at K = 8; 16x16 at K = 16, whose 33
+    coefficients take the dense rows: 32 cooperative, coefficient 0 summed per lane) adds up to the
+    same integer tally as the global one; a tally too large for shared memory falls back to the
+    global one."""
     run = mcr.Run(K=K, n_packets=0, w_threshold=0.05, roulette_p=0.3)
-    for n in (32, 80):
+    for n in (n_small, 80):
         med, _, _ = _medium(n, n, 0.25, 0.8, seed=91)
         if adjoint:
             q = torch.from_numpy(np.random.default_rng(5).normal(size=(n, n)).astype(np.float32)).cuda()
@@ -204,7 +206,7 @@ def test_large_tally_runs_ordered_by_default_and_matches_unordered():
     assert torch.equal(adj, ref)
 
 
-@pytest.mark.parametrize("K", [8, 32, 64])
+@pytest.mark.parametrize("K", [8, 16, 32, 64])
 def test_sorted_record_deposit_is_bit_identical(K):
     """The sorted-record deposit (records of every segment, counting-sorted by pixel, each pixel's
     run summed in registers) against the direct deposit, forward (line source) and adjoint: the
