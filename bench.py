@@ -44,8 +44,8 @@ L2_CLOCK_HZ = 2.017e9
 L2_RED_PEAK_GBS = L2_RED_SECTORS_PER_CYCLE * L2_CLOCK_HZ * 32 / 1e9
 # DRAM bytes (read + write) per K = 32 transport launch of the grad256 gradient evaluation, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark's forward
-# (40.59 MB) and adjoint (41.55 MB) launches at full size: the tally footprint, read once.
-TRANSPORT_DRAM_BYTES = {"grad256": 41_070_336}
+# (40.32 MB) and adjoint (41.42 MB) launches at full size: the tally footprint, read once.
+TRANSPORT_DRAM_BYTES = {"grad256": 40_873_088}
 # DRAM bytes per pixel segment of the sorted-record deposit (transport in record mode, counting
 # sort, deposit), from one ncu capture at 1024^2, K = 64 (1e6 packets, 1.327e9 segments: 126.3 GB;
 # profiles/k_transport_large1024_records_dram.md), scaled to a launch by its segments.  Its
@@ -95,6 +95,8 @@ def _args():
                     help="invert1024: comma list of lbfgs_pre, gd_pre (fluence-preconditioned), lbfgs, gd")
     ap.add_argument("--meas-packets", type=int, default=None,
                     help="invert1024: packets of the H^meas run (default 4x --packets, at least 1e8)")
+    ap.add_argument("--chosen-packets", type=int, default=None,
+                    help="equal_error: packets per MC run of the denoised route (default: the training inputs' 1e5)")
     ap.add_argument("--n3", type=int, default=96, help="grad3d: voxels per side")
     ap.add_argument("--l3", type=int, default=4, help="grad3d: spherical-harmonic order L")
     args = ap.parse_args()
@@ -817,8 +819,9 @@ def _equal_error(args):
     (inversion.invert: mu_a by fluence-preconditioned descent, or mu_s by backtracking under
     Eq. 30) on a held-out 256^2 inclusion phantom with K = 16 and the gradient from the autograd
     Function.  Plain: full MC maps at several packet counts per run.  Chosen: low-count maps
-    through the U-Nets (forward and adjoint, trained here on MC pairs made by the batched launch),
-    judged once per kind by full-count MC (denoised.Denoiser).  The plain curve of error against
+    (--chosen-packets per run, default the training inputs' 1e5) through the U-Nets (forward and
+    adjoint, trained here on MC pairs made by the batched launch, or loaded with --nets), judged
+    once per kind by an MC run of 10x the packets (denoised.Denoiser).  The plain curve of error against
     packets per run, interpolated in log-log, gives the packet count -- and, from the measured time
     per iteration against packets, the time -- at which plain MC reaches the chosen form's error."""
     import torch
@@ -910,13 +913,14 @@ def _equal_error(args):
 
         route(20_000)  # warm-up (workspaces, kernels)
         plain = [route(int(m)) for m in (1e5, 2e5, 4e5, 1e6, 2e6, 4e6)]
-        dn = Denoiser(nets["forward"][0], nets["adjoint"][0], n_full=n_high, n_judge=10 * n_low, judge_every=0,
+        n_run = args.chosen_packets or n_low  # the denoised route's packets per run
+        dn = Denoiser(nets["forward"][0], nets["adjoint"][0], n_full=n_high, n_judge=10 * n_run, judge_every=0,
                       max_rel_err=0.6)
         # warm-up of everything the chosen route runs first (U-Net kernels, the judge's norms), as
         # route(20_000) is for the plain route: a throw-away denoiser with a cheap judge and fallback
         route(20_000, Denoiser(nets["forward"][0], nets["adjoint"][0], n_full=20_000, n_judge=20_000, judge_every=0,
                                max_rel_err=0.6))
-        chosen = route(n_low, dn)
+        chosen = route(n_run, dn)
         chosen["judge"] = dn.history
         chosen["fallback"] = dn.fallback
         # plain MC at the chosen form's error: log-log fit of the plain error against packets per
@@ -950,7 +954,8 @@ def _equal_error(args):
            "dtype": "f32+i64 (FP64 gradient), bf16 U-Net", "data": "synthetic",
            "config": {"workload": f"equal_error: {'/'.join(unknowns)} reconstruction, 256x256 px of {dx} mm, held-out "
                                   f"3-inclusion phantom (seed 30001), top line source, K={K}; U-Nets trained on "
-                                  f"{n_pairs} forward + {n_pairs} adjoint MC pairs ({n_low:.0e} -> {n_high:.0e} packets)",
+                                  f"{n_pairs} forward + {n_pairs} adjoint MC pairs ({n_low:.0e} -> {n_high:.0e} packets); "
+                                  f"denoised route at {args.chosen_packets or n_low:.0e} packets per run",
                       "pair_generation_s": gen_s, "training_s": train_s, "train_steps": args.train_steps,
                       "heldout_map_errors": {k: v[1] for k, v in nets.items()}, "results": results},
            "cpu_baseline": None}
