@@ -96,7 +96,9 @@ def _args():
     ap.add_argument("--meas-packets", type=int, default=None,
                     help="invert1024: packets of the H^meas run (default 4x --packets, at least 1e8)")
     ap.add_argument("--chosen-packets", type=int, default=None,
-                    help="equal_error: packets per MC run of the denoised route (default: the training inputs' 1e5)")
+                    help="equal_error: packets per MC run of the denoised route (default: the training inputs')")
+    ap.add_argument("--train-low", type=int, default=100_000,
+                    help="equal_error: packets of the training pairs' low-count inputs (targets: 1e7)")
     ap.add_argument("--n3", type=int, default=96, help="grad3d: voxels per side")
     ap.add_argument("--l3", type=int, default=4, help="grad3d: spherical-harmonic order L")
     args = ap.parse_args()
@@ -819,7 +821,7 @@ def _equal_error(args):
     (inversion.invert: mu_a by fluence-preconditioned descent, or mu_s by backtracking under
     Eq. 30) on a held-out 256^2 inclusion phantom with K = 16 and the gradient from the autograd
     Function.  Plain: full MC maps at several packet counts per run.  Chosen: low-count maps
-    (--chosen-packets per run, default the training inputs' 1e5) through the U-Nets (forward and
+    (--chosen-packets per run, default the training inputs' --train-low, 1e5) through the U-Nets (forward and
     adjoint, trained here on MC pairs made by the batched launch, or loaded with --nets), judged
     once per kind by an MC run of 10x the packets (denoised.Denoiser).  The plain curve of error against
     packets per run, interpolated in log-log, gives the packet count -- and, from the measured time
@@ -832,7 +834,7 @@ def _equal_error(args):
     from paper_1608_05238_gb300.inversion import invert, mean_relative_error
     _build.build()
     K, n, dx, g = 16, 256, 0.05, 0.9
-    n_low, n_high, n_pairs, n_test = 100_000, 10_000_000, args.pairs, 16
+    n_low, n_high, n_pairs, n_test = args.train_low, 10_000_000, args.pairs, 16
     dev = torch.device("cuda")
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     nets = {}
@@ -843,6 +845,7 @@ def _equal_error(args):
             net.set_state(saved[kind]["state"])
             nets[kind] = (net, saved[kind]["heldout"])
         gen_s, train_s, n_pairs = saved["pair_generation_s"], saved["training_s"], saved["pairs"]
+        n_low = saved.get("n_low", n_low)  # the inputs the saved networks were trained on
     else:
         t0 = time.perf_counter()
         xf, tf = dt.make_pairs(n_pairs + n_test, n=n, dx=dx, K=K, n_low=n_low, n_high=n_high, vary=True)
@@ -859,7 +862,7 @@ def _equal_error(args):
         del xf, tf, xa, ta
         torch.cuda.empty_cache()
         if args.nets:
-            torch.save({"pairs": n_pairs, "pair_generation_s": gen_s, "training_s": train_s,
+            torch.save({"pairs": n_pairs, "n_low": n_low, "pair_generation_s": gen_s, "training_s": train_s,
                         **{k: {"state": v[0].state(), "heldout": v[1]} for k, v in nets.items()}}, args.nets)
 
     # the reconstructions: held-out phantom, homogeneous start in the unknown map
