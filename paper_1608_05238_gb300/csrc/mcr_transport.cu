@@ -173,6 +173,18 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
   // packet state
   float fx = 0.f, fz = 0.f, sx = 0.f, sz = 1.f, inv_ax = 0.f, inv_az = 0.f, W = 0.f, tau = 0.f;
   int ix = 0, iz = 0;
+  // single problem: (mu_a, mu_s, 1/mu_a, 1/mu_s) of the packet's current pixel, loaded when the
+  // packet enters a pixel -- at launch, and right after a crossing, so that the load's latency
+  // overlaps the deposit and the collision instead of starting the next segment (the pixel is
+  // unchanged after a collision).  Batches load it per segment (the extra registers would cost
+  // their kernels resident warps).
+  float4 mcur = make_float4(0.f, 0.f, CUDART_INF_F, CUDART_INF_F);
+  auto load_mu = [&]() {
+    float4 v = make_float4(0.f, 0.f, CUDART_INF_F, CUDART_INF_F);
+    if (MCR_GUARD(p.flags, (unsigned)ix < (unsigned)NX() && (unsigned)iz < (unsigned)NZ()))
+      v = __ldg(MU() + iz * NX() + ix);
+    return v;
+  };
   unsigned flight = 0, nscat = 0, cu1 = 0, cu2 = 0;
   // RECS: the warp's block of record slots [rec_block, rec_block + kRecBlock), filled to rec_fill;
   // slots left empty when a block is closed hold a sentinel that the sort skips
@@ -314,6 +326,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
             flight = 1;
             begin_flight();
             alive = true;
+            if constexpr (!BATCH) mcur = load_mu();
           }
         }
       }
@@ -329,9 +342,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     bool collided = false, escaped = false;
     if (alive) {
       const int pix = iz * NX() + ix;
-      float4 m = make_float4(0.f, 0.f, CUDART_INF_F, CUDART_INF_F);
-      if (MCR_GUARD(p.flags, (unsigned)ix < (unsigned)NX() && (unsigned)iz < (unsigned)NZ()))
-        m = __ldg(MU() + pix);  // (mu_a, mu_s, 1/mu_a, 1/mu_s)
+      const float4 m = BATCH ? load_mu() : mcur;  // (mu_a, mu_s, 1/mu_a, 1/mu_s)
       float dist_x = CUDART_INF_F, dist_z = CUDART_INF_F;
       if (sx != 0.f) dist_x = fmaxf((sx > 0.f ? DX() - fx : fx) * inv_ax, 0.f);
       if (sz != 0.f) dist_z = fmaxf((sz > 0.f ? DX() - fz : fz) * inv_az, 0.f);
@@ -396,6 +407,7 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
           fx = clamp_dx(fmaf(l, sx, fx), DX());
         }
         escaped = (unsigned)ix >= (unsigned)NX() || (unsigned)iz >= (unsigned)NZ();
+        if (!BATCH && !escaped) mcur = __ldg(MU() + iz * NX() + ix);  // the next segment's pixel
       }
     }
 
