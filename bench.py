@@ -44,8 +44,8 @@ L2_CLOCK_HZ = 2.017e9
 L2_RED_PEAK_GBS = L2_RED_SECTORS_PER_CYCLE * L2_CLOCK_HZ * 32 / 1e9
 # DRAM bytes (read + write) per K = 32 transport launch of the grad256 gradient evaluation, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark's forward
-# (40.32 MB) and adjoint (41.42 MB) launches at full size: the tally footprint, read once.
-TRANSPORT_DRAM_BYTES = {"grad256": 40_873_088}
+# (40.36 MB) and adjoint (41.68 MB) launches at full size: the tally footprint, read once.
+TRANSPORT_DRAM_BYTES = {"grad256": 41_017_344}
 # DRAM bytes per pixel segment of the sorted-record deposit (transport in record mode, counting
 # sort, deposit), from one ncu capture at 1024^2, K = 64 (1e6 packets, 1.327e9 segments: 126.3 GB;
 # profiles/k_transport_large1024_records_dram.md), scaled to a launch by its segments.  Its

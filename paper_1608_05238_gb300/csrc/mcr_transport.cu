@@ -463,7 +463,8 @@ __global__ void __launch_bounds__(256) k_transport(const __grid_constant__ Trans
     }
     unsigned pend = ROWLESS ? 0u : __ballot_sync(kFull, seg_key != 0u);
     if (pend) {
-      const unsigned same = __match_any_sync(kFull, seg_key);
+      // lanes with the same tally row (one pending lane -- the runs' tails -- needs no match)
+      const unsigned same = (pend & (pend - 1u)) == 0u ? (1u << lane) : __match_any_sync(kFull, seg_key);
       // Rows of a single lane without a carried segment (nearly all of them away from the source)
       // go kRowsPerStep at a time: their shuffles, loads, conversions and reductions are
       // independent, so they overlap instead of running as one dependent chain per row.
