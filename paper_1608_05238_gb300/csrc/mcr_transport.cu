@@ -30,6 +30,13 @@
 //    collision.  Deposits are rounded to 2^-q with q
 //    chosen per problem so that one deposit fits in int32: the conversion is a 32-bit one (the
 //    64-bit conversion runs on the FP64 pipe, which is narrow on this part).
+//  * Dense rows (2K+1 = 32 m + 1): each tally row starts 15 words into its 128-byte aligned slot,
+//    so coefficients 1..2K go by whole-line cooperative reductions, and coefficient 0 (h_0 = 1:
+//    the rounded track weight itself) is summed per lane over a packet's consecutive segments in
+//    one pixel and reduced when the pixel changes.
+//  * Single problems keep the current pixel's medium values in registers and load the next
+//    pixel's right after a crossing, off the next segment's critical path (the last packets of a
+//    run advance one latency-bound segment per warp step).
 #include <math_constants.h>
 
 #include <mutex>
